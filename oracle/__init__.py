@@ -1,0 +1,30 @@
+"""CPU oracle for the log-det barrier on chordal sparsity patterns.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library (``paper_1203_2742_gb300``)
+imports, links or executes this package; only ``tests/``, the ``smoke()``
+check in ``__graft_entry__.py`` and the CPU-baseline leg of ``bench.py`` use
+it.  It shares no code with the CUDA path.
+
+Andersen, Dahl, Vandenberghe, "Logarithmic barriers for sparse matrix cones".
+
+Modules
+-------
+``dense``         -- the definitions, computed densely in FP64 (factor, §2;
+                     gradient, Eq. (e-grad-def); Hessian, §1.1 / §5; inverse
+                     Hessian, §5.3; completion, Eq. (e-Xhat-eq) and
+                     (e-dual-barrier-def)).
+``symbolic``      -- filled pattern, elimination tree, monotone degrees,
+                     cliques, supernode partitions (§2, §6, Algorithm 6.1).
+``multifrontal``  -- the paper's scalar recursions (Algorithms 3.1, 3.2, 4.1,
+                     4.2, 5.1, 5.2) taken step by step, used as a second,
+                     independent CPU implementation.
+
+Value layout shared with the library API: a symmetric matrix on the pattern V
+is stored as the lower-triangular compressed columns (CSC) of V, rows sorted
+ascending in each column, the diagonal entry first.  ``colptr`` has n+1
+entries (int64), ``rowind`` holds the row indices (int32).
+
+Every function that has no independent pin says "parity unpinned" in its
+docstring.  At present every function here is pinned by tests under
+``tests/test_oracle_*.py``.
+"""

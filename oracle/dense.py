@@ -1,0 +1,316 @@
+"""Dense FP64 definitions of the barrier quantities (test infrastructure only).
+
+Every routine here computes the mathematical object itself, not the
+multifrontal method that reaches it:
+
+* factor          -- the unique X = L D L^T, L unit lower, D > 0 diagonal (§2,
+                     start of the section; §3.1), from a dense Cholesky.
+* logdet          -- log det X = sum_i log D_ii, and f(X) = -log det X (§1.1).
+* gradient        -- grad f(X) = -P(X^{-1}) (Eq. (e-grad-def)).
+* hessian         -- H(Y) = P(X^{-1} Y X^{-1}) (§1.1, display after
+                     Eq. (e-grad-def); §5).
+* hessian_matrix  -- the same map written as a |V| x |V| matrix on the lower
+                     entries of V.
+* inv_hessian_*   -- Y = H^{-1}(T), the solution in S_V of P(X^{-1}YX^{-1}) = T
+                     (§5.3): dense solve with hessian_matrix, conjugate
+                     gradients in the trace inner product, or the clique-sum
+                     identity of chordal patterns.
+* completion_*    -- X-hat in S_V with P(X-hat^{-1}) = S (Eq. (e-Xhat-eq)),
+                     by Newton's method on the concave problem in
+                     Eq. (e-dual-barrier-def), or by the clique-sum closed form.
+* dual_barrier    -- f_*(S) = log det X-hat - n (§1.2).
+
+Values live on the lower CSC of the pattern V (see ``oracle/__init__``).
+The inner product of symmetric matrices is A.B = tr(AB) (§1.1), so an
+off-diagonal lower entry counts twice.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+# --------------------------------------------------------------------------
+# pattern helpers
+# --------------------------------------------------------------------------
+
+
+def pattern_pairs(n, colptr, rowind):
+    """Return (rows, cols) int64 arrays of the lower entries of V, CSC order."""
+    colptr = np.asarray(colptr, dtype=np.int64)
+    rows = np.asarray(rowind, dtype=np.int64)
+    cols = np.repeat(np.arange(n, dtype=np.int64), np.diff(colptr))
+    return rows, cols
+
+
+def to_dense(n, colptr, rowind, vals):
+    """Symmetric dense matrix whose lower entries on V are ``vals``."""
+    r, c = pattern_pairs(n, colptr, rowind)
+    A = np.zeros((n, n), dtype=np.float64)
+    A[r, c] = vals
+    A[c, r] = vals
+    return A
+
+
+def project(n, colptr, rowind, A):
+    """P(A): the lower entries of the dense symmetric A on V (§1.1)."""
+    r, c = pattern_pairs(n, colptr, rowind)
+    return np.ascontiguousarray(A[r, c], dtype=np.float64)
+
+
+def sym_dot(n, colptr, rowind, a, b):
+    """A.B = tr(AB) for A, B in S_V given by their lower entries (§1.1)."""
+    r, c = pattern_pairs(n, colptr, rowind)
+    w = np.where(r == c, 1.0, 2.0)
+    return float(np.sum(w * np.asarray(a) * np.asarray(b)))
+
+
+def sym_norm(n, colptr, rowind, a):
+    return np.sqrt(max(sym_dot(n, colptr, rowind, a, a), 0.0))
+
+
+def rel_err(n, colptr, rowind, a, ref):
+    """Relative Frobenius error in the symmetric norm ||A||^2 = A.A."""
+    d = np.asarray(a, dtype=np.float64) - np.asarray(ref, dtype=np.float64)
+    den = sym_norm(n, colptr, rowind, ref)
+    num = sym_norm(n, colptr, rowind, d)
+    return num / den if den > 0 else num
+
+
+# --------------------------------------------------------------------------
+# factor, logdet, gradient  (§2, §3.1, Eq. (e-grad-def))
+# --------------------------------------------------------------------------
+
+
+def factor(n, colptr, rowind, x):
+    """Unique X = L D L^T with L unit lower triangular and D > 0 diagonal.
+
+    Computed from the dense Cholesky factor C (X = C C^T): D_ii = C_ii^2 and
+    L = C diag(1/C_ii).  Returns (l_vals, d, outside) where ``l_vals`` are
+    the entries of L on V (diagonal entries equal 1), ``d`` the n pivots, and
+    ``outside`` the largest |L_ij| at a lower position not in V; for a filled
+    pattern V (Eq. (e-filled)) this is zero up to rounding.
+    """
+    X = to_dense(n, colptr, rowind, x)
+    C = np.linalg.cholesky(X)
+    dc = np.diag(C).copy()
+    Lfull = C / dc[None, :]
+    lv = project(n, colptr, rowind, Lfull)
+    mask = np.zeros((n, n), dtype=bool)
+    r, c = pattern_pairs(n, colptr, rowind)
+    mask[r, c] = True
+    low = np.tril(np.ones((n, n), dtype=bool))
+    outside = float(np.max(np.abs(Lfull[low & ~mask]), initial=0.0))
+    return lv, dc * dc, outside
+
+
+def logdet(n, colptr, rowind, x):
+    """log det X = sum_i log D_ii (§1.4 discussion; X = L D L^T)."""
+    X = to_dense(n, colptr, rowind, x)
+    C = np.linalg.cholesky(X)
+    return float(2.0 * np.sum(np.log(np.diag(C))))
+
+
+def inverse(n, colptr, rowind, x):
+    """Dense X^{-1} through its Cholesky factor (LAPACK potrf + potri)."""
+    X = to_dense(n, colptr, rowind, x)
+    cf = sla.cho_factor(X, lower=True)
+    Z = sla.cho_solve(cf, np.eye(n))
+    return 0.5 * (Z + Z.T)
+
+
+def projected_inverse(n, colptr, rowind, x):
+    """S = P(X^{-1})."""
+    return project(n, colptr, rowind, inverse(n, colptr, rowind, x))
+
+
+def gradient(n, colptr, rowind, x):
+    """grad f(X) = -P(X^{-1}) (Eq. (e-grad-def))."""
+    return -projected_inverse(n, colptr, rowind, x)
+
+
+# --------------------------------------------------------------------------
+# Hessian (§1.1, §5)
+# --------------------------------------------------------------------------
+
+
+def hessian(n, colptr, rowind, x, ys, Z=None):
+    """T_k = P(X^{-1} Y_k X^{-1}) for each Y_k (lower entries on V)."""
+    if Z is None:
+        Z = inverse(n, colptr, rowind, x)
+    out = []
+    for y in ys:
+        Y = to_dense(n, colptr, rowind, y)
+        out.append(project(n, colptr, rowind, Z @ Y @ Z))
+    return out
+
+
+def hessian_matrix(n, colptr, rowind, x, Z=None):
+    """The map y -> t of H written as a |V| x |V| matrix on lower entries.
+
+    For a lower position (i, j) of V, the symmetric basis matrix E has ones
+    at (i, j) and (j, i) (one one when i == j), so
+    H(E)_kl = Z_ki Z_lj + Z_kj Z_li   (i != j),   Z_ki Z_li   (i == j),
+    with Z = X^{-1}.  Column (i, j) of the matrix holds H(E) at the lower
+    positions (k, l) of V.
+    """
+    if Z is None:
+        Z = inverse(n, colptr, rowind, x)
+    r, c = pattern_pairs(n, colptr, rowind)
+    Zr = Z[r][:, r]  # Z_{k i}
+    Zc = Z[c][:, c]  # Z_{l j}
+    Zrc = Z[r][:, c]  # Z_{k j}
+    Zcr = Z[c][:, r]  # Z_{l i}
+    Hm = Zr * Zc + Zrc * Zcr
+    diag = r == c
+    Hm[:, diag] *= 0.5
+    return Hm
+
+
+# --------------------------------------------------------------------------
+# inverse Hessian (§5.3)
+# --------------------------------------------------------------------------
+
+
+def inv_hessian_dense(n, colptr, rowind, x, ts, Z=None):
+    """Y = H^{-1}(T) by a dense solve with ``hessian_matrix`` (small |V|)."""
+    Hm = hessian_matrix(n, colptr, rowind, x, Z)
+    lu = sla.lu_factor(Hm)
+    return [sla.lu_solve(lu, np.asarray(t, dtype=np.float64)) for t in ts]
+
+
+def inv_hessian_cg(n, colptr, rowind, x, t, tol=1e-14, maxiter=5000, Z=None):
+    """Y = H^{-1}(T) by conjugate gradients in the inner product A.B = tr(AB).
+
+    H is self-adjoint and positive definite for that inner product, so plain
+    CG applies.  Stops when ||H(Y) - T|| <= tol ||T||.
+    """
+    if Z is None:
+        Z = inverse(n, colptr, rowind, x)
+    dot = lambda a, b: sym_dot(n, colptr, rowind, a, b)
+    H = lambda y: hessian(n, colptr, rowind, x, [y], Z=Z)[0]
+    t = np.asarray(t, dtype=np.float64)
+    y = np.zeros_like(t)
+    res = t.copy()
+    p = res.copy()
+    rr = dot(res, res)
+    tt = dot(t, t)
+    for _ in range(maxiter):
+        if rr <= tol * tol * tt:
+            break
+        hp = H(p)
+        alpha = rr / dot(p, hp)
+        y += alpha * p
+        res -= alpha * hp
+        rr_new = dot(res, res)
+        p = res + (rr_new / rr) * p
+        rr = rr_new
+    return y
+
+
+def _clique_term(n, colptr, rowind, M_of_set, sets, sign, out_pairs):
+    """Accumulate sign * E_W M(W) E_W^T over index sets W into lower entries."""
+    r, c = out_pairs
+    pos = {}
+    for k, (a, b) in enumerate(zip(r.tolist(), c.tolist())):
+        pos[(a, b)] = k
+    acc = np.zeros(len(r), dtype=np.float64)
+    for W in sets:
+        W = np.asarray(sorted(W), dtype=np.int64)
+        M = M_of_set(W)
+        for q in range(len(W)):
+            for p in range(q, len(W)):
+                acc[pos[(int(W[p]), int(W[q]))]] += sign * M[p, q]
+    return acc
+
+
+def inv_hessian_cliquesum(n, colptr, rowind, x, t, cliques, separators, S=None):
+    """Y = H^{-1}(T) from the clique-sum identity of chordal patterns.
+
+    Not in the paper (it is the derivative of the textbook closed form of
+    the maximum-determinant completion, see ``completion_cliquesum``).  With
+    S = P(X^{-1}) and the Legendre relation Eq. (e-legendre-rels),
+    H^{-1}(T) = grad^2 f_*(S)[T]
+              = sum_J E_J S_JJ^{-1} T_JJ S_JJ^{-1} E_J^T
+                - sum_A E_A S_AA^{-1} T_AA S_AA^{-1} E_A^T,
+    over the cliques J and the separators A of a clique tree of V.
+    """
+    if S is None:
+        S = inverse(n, colptr, rowind, x)
+    T = to_dense(n, colptr, rowind, t)
+
+    def term(W):
+        Si = np.linalg.inv(S[np.ix_(W, W)])
+        return Si @ T[np.ix_(W, W)] @ Si
+
+    pairs = pattern_pairs(n, colptr, rowind)
+    return (_clique_term(n, colptr, rowind, term, cliques, 1.0, pairs)
+            + _clique_term(n, colptr, rowind, term, separators, -1.0, pairs))
+
+
+# --------------------------------------------------------------------------
+# completion / dual barrier (§1.2, Eq. (e-Xhat-eq), (e-compl))
+# --------------------------------------------------------------------------
+
+
+def completion_cliquesum(n, colptr, rowind, s, cliques, separators):
+    """X-hat with P(X-hat^{-1}) = S from the closed form for chordal V.
+
+    Not in the paper (classical result on maximum-determinant completions of
+    chordal patterns): the inverse of the max-det completion of S is
+    X-hat = sum_J E_J (S_JJ)^{-1} E_J^T - sum_A E_A (S_AA)^{-1} E_A^T
+    over the cliques J and separators A of a clique tree of V.
+    """
+    S = to_dense(n, colptr, rowind, s)
+    inv = lambda W: np.linalg.inv(S[np.ix_(W, W)])
+    pairs = pattern_pairs(n, colptr, rowind)
+    return (_clique_term(n, colptr, rowind, inv, cliques, 1.0, pairs)
+            + _clique_term(n, colptr, rowind, inv, separators, -1.0, pairs))
+
+
+def completion_newton(n, colptr, rowind, s, tol=1e-14, maxiter=100):
+    """X-hat maximising -S.X + log det X over X in S_V (Eq. (e-dual-barrier-def)).
+
+    The optimality condition is P(X^{-1}) = S (Eq. (e-Xhat-eq)).  Newton's
+    method: the gradient of the objective is P(X^{-1}) - S and its Hessian
+    is -H_X, so the step solves H_X(dX) = P(X^{-1}) - S (a dense solve with
+    ``hessian_matrix``).  A backtracking line search keeps X positive
+    definite and increases the objective.  Start: X0 = diag(1/S_ii).
+    Stops when ||P(X^{-1}) - S|| <= tol ||S||.
+    """
+    s = np.asarray(s, dtype=np.float64)
+    r, c = pattern_pairs(n, colptr, rowind)
+    x = np.zeros_like(s)
+    dg = r == c
+    x[dg] = 1.0 / s[dg]
+    snorm = sym_norm(n, colptr, rowind, s)
+
+    def objective(xv):
+        X = to_dense(n, colptr, rowind, xv)
+        try:
+            C = np.linalg.cholesky(X)
+        except np.linalg.LinAlgError:
+            return -np.inf
+        return -sym_dot(n, colptr, rowind, s, xv) + 2.0 * np.sum(np.log(np.diag(C)))
+
+    for _ in range(maxiter):
+        Z = inverse(n, colptr, rowind, x)
+        g = project(n, colptr, rowind, Z) - s
+        if sym_norm(n, colptr, rowind, g) <= tol * snorm:
+            break
+        Hm = hessian_matrix(n, colptr, rowind, x, Z)
+        dx = np.linalg.solve(Hm, g)
+        f0 = objective(x)
+        slope = sym_dot(n, colptr, rowind, g, dx)
+        step = 1.0
+        while True:
+            f1 = objective(x + step * dx)
+            if f1 >= f0 + 0.25 * step * slope or step < 1e-12:
+                break
+            step *= 0.5
+        x = x + step * dx
+    return x
+
+
+def dual_barrier(n, colptr, rowind, xhat):
+    """f_*(S) = log det X-hat - n (§1.2)."""
+    return logdet(n, colptr, rowind, xhat) - n
