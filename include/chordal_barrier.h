@@ -1,0 +1,219 @@
+/*
+ * chordal_barrier.h -- C ABI of the GB300 library for the log-det barrier on
+ * chordal (filled) sparsity patterns.
+ *
+ * Andersen, Dahl, Vandenberghe, "Logarithmic barriers for sparse matrix
+ * cones".  The library evaluates, for X in S^n_V (symmetric, sparsity
+ * pattern V, positive definite) and S in S^n_V with a positive definite
+ * completion:
+ *   f(X)        = -log det X                         (§1.1)
+ *   grad f(X)   = -P(X^{-1})                         (Eq. (e-grad-def))
+ *   H(Y)        = P(X^{-1} Y X^{-1})                 (§1.1, §5)
+ *   H^{-1}(T)                                        (§5.3)
+ *   X-hat with P(X-hat^{-1}) = S, f_*(S) = log det X-hat - n
+ *                                                    (§1.2, Eq. (e-Xhat-eq))
+ * with supernodal multifrontal recursions over a clique tree (§6, §7).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Value arrays.  A matrix in S^n_V is a double array of nnz_filled entries:
+ *   the lower triangle of the FILLED pattern V (returned by chd_symbolic_info)
+ *   in compressed-column order, in the ANALYSED (permuted) numbering, rows
+ *   ascending within a column, the diagonal first.  Batches of m matrices
+ *   are stored one after another with a stride (ld) >= nnz_filled.
+ * Pointers.  Every double* value argument below is a DEVICE pointer owned
+ *   by the caller, except where the comment says "host".  Symbolic and
+ *   factor objects are owned by the library and freed with the *_free calls.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *   default stream).  Numeric calls enqueue their kernels on it and return
+ *   without synchronising; chd_analyze, chd_logdet, chd_status and
+ *   chd_error_detail synchronise.
+ * Errors.  Every call returns a chd_status; none traps or aborts.  Numeric
+ *   failures found on the device (a non-positive pivot, an S with no
+ *   positive definite completion, a bounded wait that ran out) are recorded
+ *   in the factor object and reported by chd_status / chd_logdet /
+ *   chd_error_detail, which synchronise.
+ * Inner product.  A.B = tr(AB) (§1.1): off-diagonal entries count twice.
+ */
+#ifndef CHORDAL_BARRIER_H
+#define CHORDAL_BARRIER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chd_symbolic chd_symbolic;
+typedef struct chd_factor chd_factor;
+
+typedef enum {
+  CHD_OK = 0,
+  CHD_ERR_INVALID = 1,          /* bad argument or malformed pattern */
+  CHD_ERR_NOT_PD = 2,           /* X not positive definite (non-positive pivot) */
+  CHD_ERR_NOT_COMPLETABLE = 3,  /* S has no positive definite completion */
+  CHD_ERR_OOM = 4,              /* device or host allocation failed */
+  CHD_ERR_CUDA = 5,             /* a CUDA runtime call failed */
+  CHD_ERR_TIMEOUT = 6           /* a bounded device-side wait ran out */
+} chd_status;
+
+typedef enum {
+  CHD_ORDER_NATURAL = 0,  /* keep the given numbering (it must be a perfect
+                             elimination order if no fill is wanted) */
+  CHD_ORDER_USER = 1,     /* use opts.user_perm */
+  CHD_ORDER_MINDEG = 2    /* minimum degree (exact degrees, smallest index on ties) */
+} chd_ordering;
+
+typedef struct {
+  int32_t ordering;        /* chd_ordering */
+  const int64_t* user_perm;/* host, n entries, perm[new] = old; used when ordering == CHD_ORDER_USER */
+  int32_t relax;           /* relaxed supernodes: a merge of a child supernode into its
+                              parent is accepted if it adds at most `relax` explicit zeros
+                              to V; 0 = fundamental partition of Algorithm 6.1 */
+  int32_t tie_last;        /* Algorithm 6.1 step 1 tie-break: 1 = child with the largest
+                              index, 0 = smallest */
+  int32_t reserved[8];
+} chd_opts;
+
+/* Fill `opts` with the defaults: natural order, relax 0, tie_last 1. */
+void chd_opts_default(chd_opts* opts);
+
+/*
+ * Symbolic analysis (§2, §6; Algorithm 6.1).  Host only, no device compute
+ * apart from one upload of the index maps.
+ *   n       order of the matrix (n >= 1)
+ *   colptr  host, n+1 entries: lower-CSC column pointers of the user's pattern
+ *   rowind  host, colptr[n] entries: row indices (row >= column); the
+ *           diagonal may be omitted (it is always part of V)
+ *   opts    NULL for defaults
+ *   out     receives a new symbolic object
+ * The pattern is ordered, filled to a chordal pattern (elimination fill),
+ * postordered so that every supernode is a contiguous column range, and
+ * partitioned into supernodes N_k with ancestor sets A_k and clique-tree
+ * parents par(k) (§6.2-§6.4); optional relaxed amalgamation enlarges V.
+ * Errors: CHD_ERR_INVALID for n < 1, an index out of range, an entry above
+ * the diagonal or a user permutation that is not one; CHD_ERR_OOM.
+ */
+chd_status chd_analyze(int64_t n, const int64_t* colptr, const int32_t* rowind,
+                       const chd_opts* opts, chd_symbolic** out);
+
+/*
+ * Pointers into the symbolic object (host memory, owned by it, valid until
+ * chd_symbolic_free).  Any output pointer may be NULL.
+ *   nnz_filled   entries of the lower triangle of the filled pattern V
+ *   colptr       n+1 entries, rowind nnz_filled entries: V in CSC (analysed order)
+ *   perm         n entries: perm[new] = old (user numbering)
+ *   nsuper       number of supernodes
+ */
+chd_status chd_symbolic_info(const chd_symbolic* sym, int64_t* n, int64_t* nnz_filled,
+                             const int64_t** colptr, const int32_t** rowind,
+                             const int64_t** perm, int64_t* nsuper);
+
+/*
+ * Supernode partition and clique tree (host pointers into the object).
+ *   snode_ptr  nsuper+1 entries: supernode k owns columns [snode_ptr[k], snode_ptr[k+1]) (N_k)
+ *   snode_par  nsuper entries: clique-tree parent supernode, -1 at a root
+ *   rows_ptr   nsuper+1 entries, rows: J_k = N_k followed by A_k, sorted
+ */
+chd_status chd_symbolic_supernodes(const chd_symbolic* sym, const int64_t** snode_ptr,
+                                   const int64_t** snode_par, const int64_t** rows_ptr,
+                                   const int32_t** rows);
+
+/*
+ * Algorithmic flop counts (multiply-add = 2) of one call of each operation
+ * on this pattern, summed over the fronts from (n_k, a_k): out[0] factor,
+ * out[1] gradient, out[2] Hessian per right-hand side, out[3] inverse Hessian
+ * per right-hand side, out[4] completion.
+ */
+chd_status chd_symbolic_flops(const chd_symbolic* sym, double out[5]);
+
+void chd_symbolic_free(chd_symbolic* sym);
+
+/*
+ * Cholesky factorisation X = L D L^T (supernodal Algorithm 7.1, §7.1).
+ *   x_dev   device, nnz_filled values of X on V
+ *   stream  cudaStream_t as void*
+ *   out     receives a new factor object (device memory owned by it)
+ * The factor keeps the supernodal Cholesky factor, D_NN^{-1}, the unit
+ * lower blocks L_{A_k N_k} and D_NN for later calls.  A non-positive pivot
+ * is recorded on the device and reported as CHD_ERR_NOT_PD by chd_status.
+ * Errors returned directly: CHD_ERR_INVALID (NULL arguments), CHD_ERR_OOM,
+ * CHD_ERR_CUDA.
+ */
+chd_status chd_factor_new(chd_symbolic* sym, const double* x_dev, void* stream,
+                          chd_factor** out);
+
+/* Refactor an existing factor object in place with new values of X (same pattern). */
+chd_status chd_refactor(chd_factor* fac, const double* x_dev, void* stream);
+
+/* log det X = sum of log D_ii (§1.1).  Synchronises; host output. */
+chd_status chd_logdet(chd_factor* fac, double* out);
+
+/*
+ * Gradient g = -P(X^{-1}) (Eq. (e-grad-def)) by the supernodal projected
+ * inverse, Algorithm 7.2 (§7.2).  g_dev: device, nnz_filled values.  The
+ * projected inverse S = P(X^{-1}) and the dense blocks V_k = S_{A_k A_k}
+ * are cached in the factor for chd_hessian / chd_inv_hessian.
+ */
+chd_status chd_gradient(chd_factor* fac, double* g_dev, void* stream);
+
+/*
+ * Hessian products T_i = P(X^{-1} Y_i X^{-1}), i < m (§5.2, Algorithm 5.1 in
+ * supernodal block form).  y_dev: m matrices at stride ldy; t_dev: m
+ * outputs at stride ldt (device).  Runs chd_gradient's projected inverse
+ * first if it is not cached.  y_dev and t_dev must not overlap.
+ */
+chd_status chd_hessian(chd_factor* fac, int m, const double* y_dev, int64_t ldy,
+                       double* t_dev, int64_t ldt, void* stream);
+
+/*
+ * Inverse-Hessian products Y_i = H^{-1}(T_i) (§5.3, Algorithm 5.2 in
+ * supernodal block form): the solution in S^n_V of P(X^{-1} Y X^{-1}) = T.
+ * Uses cached Cholesky factors of V_k = S_{A_k A_k}.
+ */
+chd_status chd_inv_hessian(chd_factor* fac, int m, const double* t_dev, int64_t ldt,
+                           double* y_dev, int64_t ldy, void* stream);
+
+/*
+ * Maximum-determinant completion (§4.2; supernodal Algorithm 7.3, §7.2):
+ * the factor of X-hat in S^n_V with P(X-hat^{-1}) = S, returned as a new
+ * factor object (its projected inverse is S itself, so chd_hessian and
+ * chd_inv_hessian on it give the dual barrier's derivatives through
+ * Eq. (e-legendre-rels)).  s_dev: device, nnz_filled values of S.
+ * fstar: host, receives f_*(S) = log det X-hat - n (§1.2); this call
+ * synchronises when fstar is not NULL.  A pivot <= 0 in the Cholesky factor
+ * of S_{A_k A_k} or of D_NN^{-1} is reported as CHD_ERR_NOT_COMPLETABLE.
+ */
+chd_status chd_complete(chd_symbolic* sym, const double* s_dev, void* stream,
+                        chd_factor** xhat, double* fstar);
+
+/*
+ * Export the unique scalar factorisation X = L D L^T (§2, §3.1): l_dev gets
+ * the nnz_filled entries of L on V (unit diagonal), d_dev the n pivots D_ii.
+ */
+chd_status chd_factor_export(chd_factor* fac, double* l_dev, double* d_dev, void* stream);
+
+/*
+ * Synchronise and report the first device-side failure of the factor:
+ * CHD_OK, CHD_ERR_NOT_PD, CHD_ERR_NOT_COMPLETABLE or CHD_ERR_TIMEOUT.
+ */
+chd_status chd_status_get(chd_factor* fac);
+
+/*
+ * Synchronise and return the first failing supernode and column (analysed
+ * numbering) recorded by the device, or -1, -1.
+ */
+chd_status chd_error_detail(chd_factor* fac, int64_t* supernode, int64_t* column);
+
+/* Number of kernels the library has launched since the process started
+   (host counter, for launch accounting). */
+int64_t chd_kernel_launches(void);
+
+void chd_factor_free(chd_factor* fac);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHORDAL_BARRIER_H */

@@ -1,0 +1,343 @@
+"""Thin ctypes binding of the C ABI in ``include/chordal_barrier.h``.
+
+Argument marshalling only: every numeric step runs in the CUDA kernels of
+``libchordal_barrier.so``.  The functions keep the C names (``chd_analyze``,
+``chd_factor_new``, ...); ``Symbolic`` and ``Factor`` are small owners of
+the library objects.  Device arrays are torch tensors (float64, CUDA,
+contiguous) passed as raw pointers together with the current CUDA stream.
+If the shared library cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libchordal_barrier.so")
+
+if not os.path.exists(_LIBPATH):
+    raise ImportError(
+        f"{_LIBPATH} is missing: build it with `python -m paper_1203_2742_gb300.build` "
+        "(the library has no fallback implementation)")
+
+_lib = C.CDLL(_LIBPATH)
+
+CHD_OK, CHD_ERR_INVALID, CHD_ERR_NOT_PD, CHD_ERR_NOT_COMPLETABLE, CHD_ERR_OOM, CHD_ERR_CUDA, \
+    CHD_ERR_TIMEOUT = range(7)
+_STATUS_NAMES = {0: "CHD_OK", 1: "CHD_ERR_INVALID", 2: "CHD_ERR_NOT_PD", 3: "CHD_ERR_NOT_COMPLETABLE",
+                 4: "CHD_ERR_OOM", 5: "CHD_ERR_CUDA", 6: "CHD_ERR_TIMEOUT"}
+ORDERINGS = {"natural": 0, "user": 1, "mindeg": 2}
+
+
+class ChdError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {_STATUS_NAMES.get(code, code)}")
+        self.code = code
+
+
+class chd_opts(C.Structure):
+    _fields_ = [("ordering", C.c_int32), ("user_perm", C.POINTER(C.c_int64)), ("relax", C.c_int32),
+                ("tie_last", C.c_int32), ("reserved", C.c_int32 * 8)]
+
+
+_p = C.c_void_p
+_i64 = C.c_int64
+_lib.chd_opts_default.argtypes = [C.POINTER(chd_opts)]
+_lib.chd_opts_default.restype = None
+_lib.chd_analyze.argtypes = [_i64, _p, _p, C.POINTER(chd_opts), C.POINTER(_p)]
+_lib.chd_symbolic_info.argtypes = [_p, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_p), C.POINTER(_p),
+                                   C.POINTER(_p), C.POINTER(_i64)]
+_lib.chd_symbolic_supernodes.argtypes = [_p, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]
+_lib.chd_symbolic_flops.argtypes = [_p, C.POINTER(C.c_double)]
+_lib.chd_symbolic_free.argtypes = [_p]
+_lib.chd_symbolic_free.restype = None
+_lib.chd_factor_new.argtypes = [_p, _p, _p, C.POINTER(_p)]
+_lib.chd_refactor.argtypes = [_p, _p, _p]
+_lib.chd_logdet.argtypes = [_p, C.POINTER(C.c_double)]
+_lib.chd_gradient.argtypes = [_p, _p, _p]
+_lib.chd_hessian.argtypes = [_p, C.c_int, _p, _i64, _p, _i64, _p]
+_lib.chd_inv_hessian.argtypes = [_p, C.c_int, _p, _i64, _p, _i64, _p]
+_lib.chd_complete.argtypes = [_p, _p, _p, C.POINTER(_p), C.POINTER(C.c_double)]
+_lib.chd_factor_export.argtypes = [_p, _p, _p, _p]
+_lib.chd_status_get.argtypes = [_p]
+_lib.chd_error_detail.argtypes = [_p, C.POINTER(_i64), C.POINTER(_i64)]
+_lib.chd_kernel_launches.argtypes = []
+_lib.chd_kernel_launches.restype = _i64
+_lib.chd_factor_free.argtypes = [_p]
+_lib.chd_factor_free.restype = None
+for _f in ("chd_analyze", "chd_symbolic_info", "chd_symbolic_supernodes", "chd_symbolic_flops",
+           "chd_factor_new", "chd_refactor", "chd_logdet", "chd_gradient", "chd_hessian",
+           "chd_inv_hessian", "chd_complete", "chd_factor_export", "chd_status_get",
+           "chd_error_detail"):
+    getattr(_lib, _f).restype = C.c_int
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+def exported_symbols():
+    return [n for n in dir(_lib) if n.startswith("chd_")]
+
+
+def _check(rc, what):
+    if rc != CHD_OK:
+        raise ChdError(rc, what)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, what, nnz=None, rows=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{what}: expected a CUDA float64 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    if nnz is not None and t.shape[-1] != nnz:
+        raise ValueError(f"{what}: last dimension {t.shape[-1]} != nnz {nnz}")
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# C-named entry points
+# ---------------------------------------------------------------------------
+
+def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True):
+    colptr = np.ascontiguousarray(colptr, dtype=np.int64)
+    rowind = np.ascontiguousarray(rowind, dtype=np.int32)
+    o = chd_opts()
+    _lib.chd_opts_default(C.byref(o))
+    o.ordering = ORDERINGS[ordering]
+    keep = None
+    if perm is not None:
+        keep = np.ascontiguousarray(perm, dtype=np.int64)
+        o.user_perm = keep.ctypes.data_as(C.POINTER(C.c_int64))
+        o.ordering = ORDERINGS["user"]
+    o.relax = int(relax)
+    o.tie_last = 1 if tie_last else 0
+    out = _p()
+    rc = _lib.chd_analyze(int(n), colptr.ctypes.data, rowind.ctypes.data, C.byref(o), C.byref(out))
+    _check(rc, "chd_analyze")
+    return out
+
+
+def chd_symbolic_info(sym):
+    n, nnz, ns = _i64(), _i64(), _i64()
+    cp, ri, pm = _p(), _p(), _p()
+    _check(_lib.chd_symbolic_info(sym, C.byref(n), C.byref(nnz), C.byref(cp), C.byref(ri), C.byref(pm),
+                                  C.byref(ns)), "chd_symbolic_info")
+    n, nnz = n.value, nnz.value
+    colptr = np.ctypeslib.as_array(C.cast(cp, C.POINTER(C.c_int64)), shape=(n + 1,)).copy()
+    rowind = np.ctypeslib.as_array(C.cast(ri, C.POINTER(C.c_int32)), shape=(nnz,)).copy()
+    perm = np.ctypeslib.as_array(C.cast(pm, C.POINTER(C.c_int64)), shape=(n,)).copy()
+    return dict(n=n, nnz=nnz, colptr=colptr, rowind=rowind, perm=perm, nsuper=ns.value)
+
+
+def chd_symbolic_supernodes(sym, nsuper):
+    sp, par, rp, rows = _p(), _p(), _p(), _p()
+    _check(_lib.chd_symbolic_supernodes(sym, C.byref(sp), C.byref(par), C.byref(rp), C.byref(rows)),
+           "chd_symbolic_supernodes")
+    snode_ptr = np.ctypeslib.as_array(C.cast(sp, C.POINTER(C.c_int64)), shape=(nsuper + 1,)).copy()
+    snode_par = np.ctypeslib.as_array(C.cast(par, C.POINTER(C.c_int64)), shape=(nsuper,)).copy()
+    rows_ptr = np.ctypeslib.as_array(C.cast(rp, C.POINTER(C.c_int64)), shape=(nsuper + 1,)).copy()
+    rws = np.ctypeslib.as_array(C.cast(rows, C.POINTER(C.c_int32)), shape=(int(rows_ptr[-1]),)).copy()
+    return snode_ptr, snode_par, rows_ptr, rws
+
+
+def chd_symbolic_flops(sym):
+    out = (C.c_double * 5)()
+    _check(_lib.chd_symbolic_flops(sym, out), "chd_symbolic_flops")
+    return dict(factor=out[0], gradient=out[1], hessian=out[2], inv_hessian=out[3], completion=out[4])
+
+
+def chd_symbolic_free(sym):
+    _lib.chd_symbolic_free(sym)
+
+
+def chd_factor_new(sym, x, nnz, stream=None):
+    out = _p()
+    _check(_lib.chd_factor_new(sym, _dptr(x, "x", nnz), _stream_ptr(stream), C.byref(out)), "chd_factor_new")
+    return out
+
+
+def chd_refactor(fac, x, nnz, stream=None):
+    _check(_lib.chd_refactor(fac, _dptr(x, "x", nnz), _stream_ptr(stream)), "chd_refactor")
+
+
+def chd_logdet(fac):
+    v = C.c_double()
+    _check(_lib.chd_logdet(fac, C.byref(v)), "chd_logdet")
+    return v.value
+
+
+def chd_gradient(fac, g, nnz, stream=None):
+    _check(_lib.chd_gradient(fac, _dptr(g, "g", nnz), _stream_ptr(stream)), "chd_gradient")
+
+
+def _batch(t, nnz, what):
+    if t.dim() == 1:
+        return 1, nnz
+    if t.dim() != 2:
+        raise ValueError(f"{what}: expected (m, ld) or (nnz,)")
+    return t.shape[0], t.stride(0)
+
+
+def chd_hessian(fac, y, t, nnz, stream=None):
+    m, ldy = _batch(y, nnz, "y")
+    m2, ldt = _batch(t, nnz, "t")
+    if m != m2:
+        raise ValueError("y and t batch sizes differ")
+    _check(_lib.chd_hessian(fac, m, _dptr(y, "y"), ldy, _dptr(t, "t"), ldt, _stream_ptr(stream)),
+           "chd_hessian")
+
+
+def chd_inv_hessian(fac, t, y, nnz, stream=None):
+    m, ldt = _batch(t, nnz, "t")
+    m2, ldy = _batch(y, nnz, "y")
+    if m != m2:
+        raise ValueError("t and y batch sizes differ")
+    _check(_lib.chd_inv_hessian(fac, m, _dptr(t, "t"), ldt, _dptr(y, "y"), ldy, _stream_ptr(stream)),
+           "chd_inv_hessian")
+
+
+def chd_complete(sym, s, nnz, stream=None, want_fstar=True):
+    out = _p()
+    f = C.c_double()
+    rc = _lib.chd_complete(sym, _dptr(s, "s", nnz), _stream_ptr(stream), C.byref(out),
+                           C.byref(f) if want_fstar else None)
+    _check(rc, "chd_complete")
+    return out, (f.value if want_fstar else None)
+
+
+def chd_factor_export(fac, l, d, stream=None):
+    _check(_lib.chd_factor_export(fac, _dptr(l, "l"), _dptr(d, "d"), _stream_ptr(stream)),
+           "chd_factor_export")
+
+
+def chd_status_get(fac):
+    return _lib.chd_status_get(fac)
+
+
+def chd_error_detail(fac):
+    s, c = _i64(), _i64()
+    rc = _lib.chd_error_detail(fac, C.byref(s), C.byref(c))
+    return rc, s.value, c.value
+
+
+def chd_kernel_launches():
+    return int(_lib.chd_kernel_launches())
+
+
+def chd_factor_free(fac):
+    _lib.chd_factor_free(fac)
+
+
+# ---------------------------------------------------------------------------
+# owners
+# ---------------------------------------------------------------------------
+
+class Symbolic:
+    """Owner of a ``chd_symbolic``: the analysed pattern and its clique tree."""
+
+    def __init__(self, n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True):
+        self._h = chd_analyze(n, colptr, rowind, ordering=ordering, perm=perm, relax=relax,
+                              tie_last=tie_last)
+        info = chd_symbolic_info(self._h)
+        self.n = info["n"]
+        self.nnz = info["nnz"]
+        self.colptr = info["colptr"]
+        self.rowind = info["rowind"]
+        self.perm = info["perm"]
+        self.nsuper = info["nsuper"]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def supernodes(self):
+        return chd_symbolic_supernodes(self._h, self.nsuper)
+
+    def flops(self):
+        return chd_symbolic_flops(self._h)
+
+    def factor(self, x, stream=None):
+        return Factor(self, chd_factor_new(self._h, x, self.nnz, stream))
+
+    def complete(self, s, stream=None):
+        h, fstar = chd_complete(self._h, s, self.nnz, stream)
+        return Factor(self, h), fstar
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            chd_symbolic_free(h)
+            self._h = None
+
+
+class Factor:
+    """Owner of a ``chd_factor`` (device-resident factor and cached blocks)."""
+
+    def __init__(self, sym, handle):
+        self.sym = sym
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def refactor(self, x, stream=None):
+        chd_refactor(self._h, x, self.sym.nnz, stream)
+
+    def logdet(self):
+        return chd_logdet(self._h)
+
+    def gradient(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.sym.nnz, dtype=torch.float64, device="cuda")
+        chd_gradient(self._h, out, self.sym.nnz, stream)
+        return out
+
+    def hessian(self, y, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(y)
+        chd_hessian(self._h, y, out, self.sym.nnz, stream)
+        return out
+
+    def inv_hessian(self, t, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(t)
+        chd_inv_hessian(self._h, t, out, self.sym.nnz, stream)
+        return out
+
+    def export(self, stream=None):
+        import torch
+        l = torch.empty(self.sym.nnz, dtype=torch.float64, device="cuda")
+        d = torch.empty(self.sym.n, dtype=torch.float64, device="cuda")
+        chd_factor_export(self._h, l, d, stream)
+        return l, d
+
+    def status(self):
+        return chd_status_get(self._h)
+
+    def error_detail(self):
+        return chd_error_detail(self._h)
+
+    def free(self):
+        if self._h:
+            chd_factor_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

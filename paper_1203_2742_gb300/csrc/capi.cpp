@@ -1,0 +1,448 @@
+// C ABI of the chordal log-det barrier library: object lifetime, device
+// memory, argument checks and the launch sequence of every operation.
+// Declarations and the contract of each call: include/chordal_barrier.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "chd_internal.h"
+
+namespace chd_launch {
+int64_t launches();
+void factor(const chd_symbolic* s, cudaStream_t st, const double* X, double* Lc, double* Wc,
+            double* Dd, double* ws, double* ldet, int64_t* status);
+void gradient(const chd_symbolic* s, cudaStream_t st, const double* Wc, double* Sc, double* g,
+              double* Vd, double* ws);
+void hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Vd,
+             const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
+void inv_hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Dd,
+                 const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy, double* ws);
+void complete(const chd_symbolic* s, cudaStream_t st, const double* Sin, double* Lc, double* Wc,
+              double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
+void chol_v(const chd_symbolic* s, cudaStream_t st, const double* Vd, double* Rd, int64_t* status);
+void sum(cudaStream_t st, const double* v, int64_t m, double* out);
+void export_ldl(const chd_symbolic* s, cudaStream_t st, const double* Lc, double* l, double* d);
+}  // namespace chd_launch
+
+struct chd_factor {
+  chd_symbolic* sym = nullptr;
+  cudaStream_t stream = nullptr;
+  void* block = nullptr;  // one allocation holding everything below but ws
+  double* Lc = nullptr;
+  double* Wc = nullptr;
+  double* Sc = nullptr;
+  double* Dd = nullptr;
+  double* Vd = nullptr;
+  double* Rd = nullptr;
+  double* ldet = nullptr;
+  double* scalar = nullptr;  // [0] log det
+  int64_t* status = nullptr; // [0] code, [1] supernode, [2] column
+  double* ws = nullptr;      // per-right-hand-side front workspace
+  int64_t ws_rhs = 0;        // capacity in right-hand sides
+  bool have_S = false;
+  bool have_R = false;
+};
+
+namespace {
+
+// Largest workspace (bytes) a Hessian-type call may hold; larger batches of
+// right-hand sides are processed in chunks.
+constexpr size_t kWorkspaceCap = size_t(16) << 30;
+
+inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+chd_status cuda_ok(cudaError_t e) {
+  if (e == cudaSuccess) return CHD_OK;
+  return e == cudaErrorMemoryAllocation ? CHD_ERR_OOM : CHD_ERR_CUDA;
+}
+
+chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) {
+  chd_factor* f = new (std::nothrow) chd_factor();
+  if (!f) return CHD_ERR_OOM;
+  f->sym = s;
+  f->stream = stream;
+  const size_t nnz = (size_t)s->colptr[s->n];
+  size_t off = 0;
+  const size_t oLc = off; off = align_up(off + nnz * 8);
+  const size_t oWc = off; off = align_up(off + nnz * 8);
+  const size_t oSc = off; off = align_up(off + nnz * 8);
+  const size_t oDd = off; off = align_up(off + (size_t)s->d_off[s->nsn] * 8);
+  const size_t oVd = off; off = align_up(off + (size_t)s->v_off[s->nsn] * 8);
+  const size_t oRd = off; off = align_up(off + (size_t)s->v_off[s->nsn] * 8);
+  const size_t old = off; off = align_up(off + (size_t)s->nsn * 8);
+  const size_t osc = off; off = align_up(off + 4 * 8);
+  const size_t ost = off; off = align_up(off + 4 * 8);
+  void* block = nullptr;
+  chd_status rc = cuda_ok(cudaMalloc(&block, off));
+  if (rc != CHD_OK) { delete f; return rc; }
+  char* b = static_cast<char*>(block);
+  f->block = block;
+  f->Lc = reinterpret_cast<double*>(b + oLc);
+  f->Wc = reinterpret_cast<double*>(b + oWc);
+  f->Sc = reinterpret_cast<double*>(b + oSc);
+  f->Dd = reinterpret_cast<double*>(b + oDd);
+  f->Vd = reinterpret_cast<double*>(b + oVd);
+  f->Rd = reinterpret_cast<double*>(b + oRd);
+  f->ldet = reinterpret_cast<double*>(b + old);
+  f->scalar = reinterpret_cast<double*>(b + osc);
+  f->status = reinterpret_cast<int64_t*>(b + ost);
+  rc = cuda_ok(cudaMemsetAsync(f->status, 0, 4 * 8, stream));
+  if (rc != CHD_OK) { cudaFree(block); delete f; return rc; }
+  *out = f;
+  return CHD_OK;
+}
+
+chd_status ensure_ws(chd_factor* f, int64_t rhs) {
+  if (f->ws_rhs >= rhs) return CHD_OK;
+  if (f->ws) {
+    cudaStreamSynchronize(f->stream);
+    cudaFree(f->ws);
+    f->ws = nullptr;
+    f->ws_rhs = 0;
+  }
+  void* p = nullptr;
+  const size_t bytes = (size_t)f->sym->dev.f_total * 8 * (size_t)rhs;
+  chd_status rc = cuda_ok(cudaMalloc(&p, std::max<size_t>(bytes, 256)));
+  if (rc != CHD_OK) return rc;
+  f->ws = static_cast<double*>(p);
+  f->ws_rhs = rhs;
+  return CHD_OK;
+}
+
+int64_t rhs_chunk(const chd_factor* f, int m) {
+  const size_t per = std::max<size_t>((size_t)f->sym->dev.f_total * 8, 1);
+  int64_t c = (int64_t)(kWorkspaceCap / per);
+  return std::max<int64_t>(1, std::min<int64_t>(c, m));
+}
+
+chd_status launch_status() { return cuda_ok(cudaGetLastError()); }
+
+chd_status ensure_projected_inverse(chd_factor* f) {
+  if (f->have_S) return CHD_OK;
+  chd_status rc = ensure_ws(f, 1);
+  if (rc != CHD_OK) return rc;
+  chd_launch::gradient(f->sym, f->stream, f->Wc, f->Sc, nullptr, f->Vd, f->ws);
+  rc = launch_status();
+  if (rc == CHD_OK) f->have_S = true;
+  return rc;
+}
+
+chd_status read_status(chd_factor* f) {
+  int64_t h[4] = {0, 0, 0, 0};
+  chd_status rc = cuda_ok(cudaMemcpyAsync(h, f->status, sizeof(h), cudaMemcpyDeviceToHost, f->stream));
+  if (rc != CHD_OK) return rc;
+  rc = cuda_ok(cudaStreamSynchronize(f->stream));
+  if (rc != CHD_OK) return rc;
+  return static_cast<chd_status>(h[0]);
+}
+
+}  // namespace
+
+extern "C" {
+
+chd_status chd_analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const chd_opts* opts,
+                       chd_symbolic** out) {
+  if (!out) return CHD_ERR_INVALID;
+  *out = nullptr;
+  chd_opts o;
+  if (opts) o = *opts;
+  else chd_opts_default(&o);
+  chd_symbolic* s = new (std::nothrow) chd_symbolic();
+  if (!s) return CHD_ERR_OOM;
+  chd_status rc;
+  try {
+    rc = chd_symbolic_build(n, colptr, rowind, o, s);
+  } catch (const std::bad_alloc&) {
+    rc = CHD_ERR_OOM;
+  }
+  if (rc == CHD_OK) rc = chd_symbolic_upload(s);
+  if (rc != CHD_OK) {
+    chd_symbolic_free(s);
+    return rc;
+  }
+  *out = s;
+  return CHD_OK;
+}
+
+chd_status chd_symbolic_info(const chd_symbolic* s, int64_t* n, int64_t* nnz, const int64_t** colptr,
+                             const int32_t** rowind, const int64_t** perm, int64_t* nsuper) {
+  if (!s) return CHD_ERR_INVALID;
+  if (n) *n = s->n;
+  if (nnz) *nnz = s->colptr[s->n];
+  if (colptr) *colptr = s->colptr.data();
+  if (rowind) *rowind = s->rowind.data();
+  if (perm) *perm = s->perm.data();
+  if (nsuper) *nsuper = s->nsn;
+  return CHD_OK;
+}
+
+chd_status chd_symbolic_supernodes(const chd_symbolic* s, const int64_t** snode_ptr,
+                                   const int64_t** snode_par, const int64_t** rows_ptr,
+                                   const int32_t** rows) {
+  if (!s) return CHD_ERR_INVALID;
+  if (snode_ptr) *snode_ptr = s->sn_ptr.data();
+  if (snode_par) *snode_par = s->sn_par.data();
+  if (rows_ptr) *rows_ptr = s->rows_ptr.data();
+  if (rows) *rows = s->rows.data();
+  return CHD_OK;
+}
+
+chd_status chd_symbolic_flops(const chd_symbolic* s, double out[5]) {
+  if (!s || !out) return CHD_ERR_INVALID;
+  for (int i = 0; i < 5; ++i) out[i] = s->flops[i];
+  return CHD_OK;
+}
+
+void chd_symbolic_free(chd_symbolic* s) {
+  if (!s) return;
+  if (s->dev_buf) cudaFree(s->dev_buf);
+  delete s;
+}
+
+chd_status chd_factor_new(chd_symbolic* s, const double* x, void* stream, chd_factor** out) {
+  if (!s || !x || !out) return CHD_ERR_INVALID;
+  *out = nullptr;
+  chd_factor* f = nullptr;
+  chd_status rc = alloc_factor(s, static_cast<cudaStream_t>(stream), &f);
+  if (rc != CHD_OK) return rc;
+  rc = chd_refactor(f, x, stream);
+  if (rc != CHD_OK) {
+    chd_factor_free(f);
+    return rc;
+  }
+  *out = f;
+  return CHD_OK;
+}
+
+chd_status chd_refactor(chd_factor* f, const double* x, void* stream) {
+  if (!f || !x) return CHD_ERR_INVALID;
+  f->stream = static_cast<cudaStream_t>(stream);
+  chd_status rc = ensure_ws(f, 1);
+  if (rc != CHD_OK) return rc;
+  f->have_S = f->have_R = false;
+  rc = cuda_ok(cudaMemsetAsync(f->status, 0, 4 * 8, f->stream));
+  if (rc != CHD_OK) return rc;
+  chd_launch::factor(f->sym, f->stream, x, f->Lc, f->Wc, f->Dd, f->ws, f->ldet, f->status);
+  return launch_status();
+}
+
+chd_status chd_logdet(chd_factor* f, double* out) {
+  if (!f || !out) return CHD_ERR_INVALID;
+  chd_launch::sum(f->stream, f->ldet, f->sym->nsn, f->scalar);
+  chd_status rc = launch_status();
+  if (rc != CHD_OK) return rc;
+  rc = cuda_ok(cudaMemcpyAsync(out, f->scalar, 8, cudaMemcpyDeviceToHost, f->stream));
+  if (rc != CHD_OK) return rc;
+  return read_status(f);
+}
+
+chd_status chd_gradient(chd_factor* f, double* g, void* stream) {
+  if (!f || !g) return CHD_ERR_INVALID;
+  f->stream = static_cast<cudaStream_t>(stream);
+  chd_status rc = ensure_ws(f, 1);
+  if (rc != CHD_OK) return rc;
+  chd_launch::gradient(f->sym, f->stream, f->Wc, f->Sc, g, f->Vd, f->ws);
+  rc = launch_status();
+  if (rc == CHD_OK) f->have_S = true;
+  return rc;
+}
+
+chd_status chd_hessian(chd_factor* f, int m, const double* y, int64_t ldy, double* t, int64_t ldt,
+                       void* stream) {
+  if (!f || m < 0 || (m > 0 && (!y || !t))) return CHD_ERR_INVALID;
+  const int64_t nnz = f->sym->colptr[f->sym->n];
+  if (m > 1 && (ldy < nnz || ldt < nnz)) return CHD_ERR_INVALID;
+  if (m == 0) return CHD_OK;
+  f->stream = static_cast<cudaStream_t>(stream);
+  chd_status rc = ensure_projected_inverse(f);
+  if (rc != CHD_OK) return rc;
+  const int64_t chunk = rhs_chunk(f, m);
+  rc = ensure_ws(f, chunk);
+  if (rc != CHD_OK) return rc;
+  for (int64_t i = 0; i < m; i += chunk) {
+    const int mc = (int)std::min<int64_t>(chunk, m - i);
+    chd_launch::hessian(f->sym, f->stream, mc, f->Wc, f->Vd, y + i * ldy, ldy, t + i * ldt, ldt, f->ws);
+    rc = launch_status();
+    if (rc != CHD_OK) return rc;
+  }
+  return CHD_OK;
+}
+
+chd_status chd_inv_hessian(chd_factor* f, int m, const double* t, int64_t ldt, double* y, int64_t ldy,
+                           void* stream) {
+  if (!f || m < 0 || (m > 0 && (!y || !t))) return CHD_ERR_INVALID;
+  const int64_t nnz = f->sym->colptr[f->sym->n];
+  if (m > 1 && (ldy < nnz || ldt < nnz)) return CHD_ERR_INVALID;
+  if (m == 0) return CHD_OK;
+  f->stream = static_cast<cudaStream_t>(stream);
+  chd_status rc = ensure_projected_inverse(f);
+  if (rc != CHD_OK) return rc;
+  if (!f->have_R) {
+    chd_launch::chol_v(f->sym, f->stream, f->Vd, f->Rd, f->status);
+    rc = launch_status();
+    if (rc != CHD_OK) return rc;
+    f->have_R = true;
+  }
+  const int64_t chunk = rhs_chunk(f, m);
+  rc = ensure_ws(f, chunk);
+  if (rc != CHD_OK) return rc;
+  for (int64_t i = 0; i < m; i += chunk) {
+    const int mc = (int)std::min<int64_t>(chunk, m - i);
+    chd_launch::inv_hessian(f->sym, f->stream, mc, f->Wc, f->Dd, f->Rd, t + i * ldt, ldt, y + i * ldy,
+                            ldy, f->ws);
+    rc = launch_status();
+    if (rc != CHD_OK) return rc;
+  }
+  return CHD_OK;
+}
+
+chd_status chd_complete(chd_symbolic* s, const double* sv, void* stream, chd_factor** xhat,
+                        double* fstar) {
+  if (!s || !sv || !xhat) return CHD_ERR_INVALID;
+  *xhat = nullptr;
+  chd_factor* f = nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  chd_status rc = alloc_factor(s, st, &f);
+  if (rc != CHD_OK) return rc;
+  rc = ensure_ws(f, 1);
+  if (rc == CHD_OK)
+    rc = cuda_ok(cudaMemcpyAsync(f->Sc, sv, (size_t)s->colptr[s->n] * 8, cudaMemcpyDeviceToDevice, st));
+  if (rc == CHD_OK) {
+    chd_launch::complete(s, st, sv, f->Lc, f->Wc, f->Dd, f->Vd, f->Rd, f->ws, f->ldet, f->status);
+    rc = launch_status();
+  }
+  if (rc != CHD_OK) {
+    chd_factor_free(f);
+    return rc;
+  }
+  f->have_S = f->have_R = true;
+  if (fstar) {
+    double ld = 0;
+    rc = chd_logdet(f, &ld);
+    if (rc != CHD_OK) {
+      chd_factor_free(f);
+      return rc;
+    }
+    *fstar = ld - (double)s->n;
+  }
+  *xhat = f;
+  return CHD_OK;
+}
+
+chd_status chd_factor_export(chd_factor* f, double* l, double* d, void* stream) {
+  if (!f || !l) return CHD_ERR_INVALID;
+  f->stream = static_cast<cudaStream_t>(stream);
+  chd_launch::export_ldl(f->sym, f->stream, f->Lc, l, d);
+  return launch_status();
+}
+
+chd_status chd_status_get(chd_factor* f) {
+  if (!f) return CHD_ERR_INVALID;
+  return read_status(f);
+}
+
+chd_status chd_error_detail(chd_factor* f, int64_t* supernode, int64_t* column) {
+  if (!f) return CHD_ERR_INVALID;
+  int64_t h[4] = {0, 0, 0, 0};
+  chd_status rc = cuda_ok(cudaMemcpyAsync(h, f->status, sizeof(h), cudaMemcpyDeviceToHost, f->stream));
+  if (rc == CHD_OK) rc = cuda_ok(cudaStreamSynchronize(f->stream));
+  if (rc != CHD_OK) return rc;
+  if (supernode) *supernode = h[0] ? h[1] : -1;
+  if (column) *column = h[0] ? h[2] : -1;
+  return static_cast<chd_status>(h[0]);
+}
+
+int64_t chd_kernel_launches(void) { return chd_launch::launches(); }
+
+void chd_factor_free(chd_factor* f) {
+  if (!f) return;
+  if (f->stream) cudaStreamSynchronize(f->stream);
+  if (f->ws) cudaFree(f->ws);
+  if (f->block) cudaFree(f->block);
+  delete f;
+}
+
+}  // extern "C"
+
+// Device upload of the symbolic arrays the kernels read (one allocation,
+// one host-to-device copy).
+chd_status chd_symbolic_upload(chd_symbolic* s) {
+  struct Piece {
+    const void* src;
+    size_t bytes;
+    size_t off;
+  };
+  std::vector<Piece> pcs;
+  size_t off = 0;
+  auto add = [&](const void* p, size_t bytes) {
+    pcs.push_back({p, bytes, off});
+    off = align_up(off + std::max<size_t>(bytes, 8));
+    return pcs.size() - 1;
+  };
+  size_t iColptr = add(s->colptr.data(), s->colptr.size() * 8);
+  size_t iSn = add(s->sn_ptr.data(), s->sn_ptr.size() * 8);
+  size_t iPar = add(s->sn_par.data(), s->sn_par.size() * 8);
+  size_t iRp = add(s->rows_ptr.data(), s->rows_ptr.size() * 8);
+  size_t iRel = add(s->rel.data(), s->rel.size() * 4);
+  size_t iCp = add(s->ch_ptr.data(), s->ch_ptr.size() * 8);
+  size_t iCh = add(s->ch.data(), s->ch.size() * 4);
+  size_t iF = add(s->f_off.data(), s->f_off.size() * 8);
+  size_t iD = add(s->d_off.data(), s->d_off.size() * 8);
+  size_t iV = add(s->v_off.data(), s->v_off.size() * 8);
+  size_t iTp = add(s->task_ptr.data(), s->task_ptr.size() * 4);
+  size_t iTf = add(s->task_fronts.data(), s->task_fronts.size() * 4);
+  std::vector<char> host(off, 0);
+  for (auto& p : pcs)
+    if (p.bytes) std::memcpy(host.data() + p.off, p.src, p.bytes);
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    // No usable device: the symbolic object stays host-only.  Numeric calls
+    // then fail with CHD_ERR_CUDA.
+    cudaGetLastError();
+    s->dev_buf = nullptr;
+    s->dev = SymDev{};
+    s->dev.f_total = s->f_off[s->nsn];
+    return CHD_OK;
+  }
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, off);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) return CHD_ERR_OOM;
+    // no device present: host-only symbolic object
+    s->dev_buf = nullptr;
+    s->dev = SymDev{};
+    s->dev.f_total = s->f_off[s->nsn];
+    return CHD_OK;
+  }
+  if (cudaMemcpy(buf, host.data(), off, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(buf);
+    return CHD_ERR_CUDA;
+  }
+  s->dev_buf = buf;
+  s->dev_id = dev;
+  char* b = static_cast<char*>(buf);
+  SymDev& d = s->dev;
+  d.n = s->n;
+  d.nsn = s->nsn;
+  d.colptr = reinterpret_cast<const int64_t*>(b + pcs[iColptr].off);
+  d.sn_ptr = reinterpret_cast<const int64_t*>(b + pcs[iSn].off);
+  d.sn_par = reinterpret_cast<const int64_t*>(b + pcs[iPar].off);
+  d.rows_ptr = reinterpret_cast<const int64_t*>(b + pcs[iRp].off);
+  d.rel = reinterpret_cast<const int32_t*>(b + pcs[iRel].off);
+  d.ch_ptr = reinterpret_cast<const int64_t*>(b + pcs[iCp].off);
+  d.ch = reinterpret_cast<const int32_t*>(b + pcs[iCh].off);
+  d.f_off = reinterpret_cast<const int64_t*>(b + pcs[iF].off);
+  d.d_off = reinterpret_cast<const int64_t*>(b + pcs[iD].off);
+  d.v_off = reinterpret_cast<const int64_t*>(b + pcs[iV].off);
+  d.task_ptr = reinterpret_cast<const int32_t*>(b + pcs[iTp].off);
+  d.task_fronts = reinterpret_cast<const int32_t*>(b + pcs[iTf].off);
+  d.f_total = s->f_off[s->nsn];
+  d.d_total = s->d_off[s->nsn];
+  d.v_total = s->v_off[s->nsn];
+  return CHD_OK;
+}

@@ -1,0 +1,62 @@
+// Internal declarations shared by the host symbolic phase, the C ABI and the
+// CUDA kernels of the chordal log-det barrier library.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/chordal_barrier.h"
+
+// Device copy of the symbolic data, passed by value to every kernel.
+struct SymDev {
+  int64_t n = 0;
+  int64_t nsn = 0;             // number of supernodes (fronts)
+  const int64_t* colptr = nullptr;   // n+1: CSC of V (analysed order)
+  const int64_t* sn_ptr = nullptr;   // nsn+1: N_k = [sn_ptr[k], sn_ptr[k+1])
+  const int64_t* sn_par = nullptr;   // nsn: clique-tree parent or -1
+  const int64_t* rows_ptr = nullptr; // nsn+1: offsets of J_k in `rows`/`rel`
+  const int32_t* rel = nullptr;      // position of A_k[r] inside J_par(k) (A part only)
+  const int64_t* ch_ptr = nullptr;   // nsn+1: children of k in ch[ch_ptr[k]..)
+  const int32_t* ch = nullptr;
+  const int64_t* f_off = nullptr;    // nsn+1: per-front workspace offsets (doubles)
+  const int64_t* d_off = nullptr;    // nsn+1: per-front n_k*n_k block offsets
+  const int64_t* v_off = nullptr;    // nsn+1: per-front a_k*a_k block offsets
+  const int32_t* task_ptr = nullptr; // ntask+1
+  const int32_t* task_fronts = nullptr;
+  int64_t f_total = 0;               // workspace doubles per right-hand side
+  int64_t d_total = 0;
+  int64_t v_total = 0;
+};
+
+struct chd_symbolic {
+  int64_t n = 0;
+  std::vector<int64_t> perm;       // perm[new] = old
+  std::vector<int64_t> colptr;     // n+1
+  std::vector<int32_t> rowind;     // nnz(V)
+  int64_t nsn = 0;
+  std::vector<int64_t> sn_ptr;     // nsn+1
+  std::vector<int64_t> sn_par;     // nsn
+  std::vector<int64_t> rows_ptr;   // nsn+1
+  std::vector<int32_t> rows;       // J_k, N_k first then A_k
+  std::vector<int32_t> rel;        // aligned with rows; -1 on the N part
+  std::vector<int64_t> ch_ptr;
+  std::vector<int32_t> ch;
+  std::vector<int64_t> f_off, d_off, v_off;
+  // schedule: tasks are front sequences processed by one CTA; launches
+  // group tasks by level (bottom-up order); lvl_ptr indexes tasks.
+  std::vector<int32_t> task_ptr, task_fronts, lvl_ptr;
+  double flops[5] = {0, 0, 0, 0, 0};
+  int64_t max_front = 0;
+  // device mirror
+  SymDev dev;
+  void* dev_buf = nullptr;
+  int dev_id = -1;
+};
+
+// Host helpers implemented in symbolic.cpp
+chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* rowind,
+                              const chd_opts& opts, chd_symbolic* s);
+chd_status chd_symbolic_upload(chd_symbolic* s);
+
+inline int64_t front_n(const chd_symbolic* s, int64_t k) { return s->sn_ptr[k + 1] - s->sn_ptr[k]; }
+inline int64_t front_J(const chd_symbolic* s, int64_t k) { return s->rows_ptr[k + 1] - s->rows_ptr[k]; }

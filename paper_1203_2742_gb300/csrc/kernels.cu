@@ -1,0 +1,848 @@
+// FP64 supernodal multifrontal kernels for sm_103a.
+//
+// Andersen, Dahl, Vandenberghe, "Logarithmic barriers for sparse matrix
+// cones".  One CTA processes one task (a sequence of fronts in postorder,
+// bottom-up; reversed, top-down) for one right-hand side.  A front k has
+// N_k (n columns, contiguous) and A_k (a rows), J = n + a.  Its workspace in
+// global memory (L2-resident in practice) is the dense J x J front F
+// (column-major, ld = J, lower triangle used) followed by two J x n
+// temporaries T1, T2.  Value arrays (X, Y, S, T, the factor) are in the CSC
+// of the filled pattern: column c of front k holds rows c..J-1 of the
+// front, so element (r, c), r >= c, sits at
+//     base_k + c*(J-1) - c*(c-1)/2 + r,   base_k = colptr[first column of k].
+//
+// Per-front storage kept by a factor object:
+//   Lc  (CSC)  : [C; B], the supernodal Cholesky factor, D_NN = C C^T,
+//                B = L_{AN} C  (Algorithm 7.1: D_NN = F11, L_AN = F21 D^-1)
+//   Wc  (CSC)  : [D_NN^{-1}; L_AN]
+//   Dd  (n x n): D_NN
+//   Vd  (a x a): V_k = S_{A_k A_k}  (Algorithm 7.2)
+//   Rd  (a x a): lower Cholesky factor of V_k (inverse Hessian, §5.3)
+//   Sc  (CSC)  : S = P(X^{-1})
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "chd_internal.h"
+
+namespace chd {
+
+constexpr int NT = 256;      // threads per CTA
+constexpr int TB = 32;       // gemm tile (TB x TB outputs)
+constexpr int TK = 16;       // gemm k-chunk
+constexpr int PB = 32;       // potrf panel width
+constexpr int PCH = 96;      // rows per panel chunk staged in shared memory
+
+// Shared-memory staging buffers, declared once at namespace scope so that
+// every routine of a kernel uses the same 42 KB.
+__shared__ double sh_A[TK][TB + 1];
+__shared__ double sh_B[TK][TB + 1];
+__shared__ double sh_L[PB * (PB + 1)];
+__shared__ double sh_P[PCH * (PB + 1)];
+
+// ---------------------------------------------------------------------------
+// matrix views (element (r, c) accessors)
+// ---------------------------------------------------------------------------
+struct Dn {  // column-major
+  double* p;
+  int64_t ld;
+  __device__ double& at(int r, int c) const { return p[r + (int64_t)c * ld]; }
+};
+struct DnT {  // transpose of a column-major matrix
+  const double* p;
+  int64_t ld;
+  __device__ double at(int r, int c) const { return p[c + (int64_t)r * ld]; }
+};
+struct SymL {  // symmetric, lower triangle stored column-major
+  const double* p;
+  int64_t ld;
+  __device__ double at(int r, int c) const {
+    return r >= c ? p[r + (int64_t)c * ld] : p[c + (int64_t)r * ld];
+  }
+};
+struct TriL {  // lower triangular, stored column-major
+  const double* p;
+  int64_t ld;
+  __device__ double at(int r, int c) const { return r >= c ? p[r + (int64_t)c * ld] : 0.0; }
+};
+struct TriLT {  // transpose of a lower triangular matrix
+  const double* p;
+  int64_t ld;
+  __device__ double at(int r, int c) const { return c >= r ? p[c + (int64_t)r * ld] : 0.0; }
+};
+__device__ __forceinline__ int64_t csc_off(int J, int r, int c) {
+  return (int64_t)c * (J - 1) - (int64_t)c * (c - 1) / 2 + r;
+}
+struct Csc {  // N-part of a front in CSC: (r, c) for r >= c, rows offset by r0
+  double* p;
+  int J;
+  int r0;
+  __device__ double& at(int r, int c) const { return p[csc_off(J, r + r0, c)]; }
+};
+struct CscRO {
+  const double* p;
+  int J;
+  int r0;
+  __device__ double at(int r, int c) const { return p[csc_off(J, r + r0, c)]; }
+};
+struct CscT {  // transpose of rows [r0, ..) of the N-part
+  const double* p;
+  int J;
+  int r0;
+  __device__ double at(int r, int c) const { return p[csc_off(J, c + r0, r)]; }
+};
+struct CscSym {  // symmetric N x N block stored lower in CSC
+  const double* p;
+  int J;
+  __device__ double at(int r, int c) const {
+    return r >= c ? p[csc_off(J, r, c)] : p[csc_off(J, c, r)];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// status
+// ---------------------------------------------------------------------------
+__device__ void record_error(int64_t* st, int64_t code, int64_t snode, int64_t col) {
+  unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(st), 0ull,
+                                     static_cast<unsigned long long>(code));
+  if (old == 0ull) {
+    st[1] = snode;
+    st[2] = col;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CTA GEMM:  C = beta*C + alpha * A(MxK) B(KxN), optionally lower triangle only.
+// 32x32 output tiles, k-chunks of 16 staged in shared memory, 2x2 outputs per
+// thread.  beta == 0 never reads C.
+// ---------------------------------------------------------------------------
+template <class MA, class MB, class MC>
+__device__ void cta_gemm(int M, int N, int K, double alpha, MA A, MB B, double beta, MC C,
+                         bool lower) {
+  if (M <= 0 || N <= 0) return;
+  auto& As = sh_A;
+  auto& Bs = sh_B;
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  for (int tm = 0; tm < M; tm += TB) {
+    for (int tn = 0; tn < N; tn += TB) {
+      if (lower && tn >= tm + TB) continue;
+      double c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+      for (int k0 = 0; k0 < K; k0 += TK) {
+        for (int e = tid; e < TB * TK; e += NT) {
+          int r = e % TB, k = e / TB;
+          As[k][r] = (tm + r < M && k0 + k < K) ? A.at(tm + r, k0 + k) : 0.0;
+        }
+        for (int e = tid; e < TB * TK; e += NT) {
+          int k = e % TK, c = e / TK;
+          Bs[k][c] = (k0 + k < K && tn + c < N) ? B.at(k0 + k, tn + c) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < TK; ++k) {
+          double a0 = As[k][ty], a1 = As[k][ty + 16];
+          double b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
+          c00 = fma(a0, b0, c00);
+          c01 = fma(a0, b1, c01);
+          c10 = fma(a1, b0, c10);
+          c11 = fma(a1, b1, c11);
+        }
+        __syncthreads();
+      }
+      const double acc[2][2] = {{c00, c01}, {c10, c11}};
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          int r = tm + ty + 16 * i, c = tn + tx + 16 * j;
+          if (r < M && c < N && (!lower || r >= c)) {
+            double v = alpha * acc[i][j];
+            if (beta != 0.0) v = fma(beta, C.at(r, c), v);
+            C.at(r, c) = v;
+          }
+        }
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Unblocked Cholesky of a small block held in shared memory (row-major,
+// stride PB+1).  Non-positive pivots are recorded and replaced by 1.
+// ---------------------------------------------------------------------------
+__device__ void smem_potrf(double* Ls, int jb, int64_t* st, int64_t code, int64_t snode,
+                           int64_t col0) {
+  const int tid = threadIdx.x;
+  for (int j = 0; j < jb; ++j) {
+    if (tid == 0) {
+      double d = Ls[j * (PB + 1) + j];
+      if (!(d > 0.0)) {
+        record_error(st, code, snode, col0 + j);
+        d = 1.0;
+      }
+      Ls[j * (PB + 1) + j] = sqrt(d);
+    }
+    __syncthreads();
+    const double piv = Ls[j * (PB + 1) + j];
+    for (int i = j + 1 + tid; i < jb; i += NT) Ls[i * (PB + 1) + j] /= piv;
+    __syncthreads();
+    const int m = jb - j - 1;
+    for (int e = tid; e < m * m; e += NT) {
+      int i = j + 1 + e % m, k = j + 1 + e / m;
+      if (i >= k) Ls[i * (PB + 1) + k] -= Ls[i * (PB + 1) + j] * Ls[k * (PB + 1) + j];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Blocked right-looking Cholesky of the first n columns of the J x J front
+// F (column-major, ld): afterwards F[0:n,0:n] = C (lower), F[n:J,0:n] =
+// F21 C^{-T}, F[n:J,n:J] -= (F21 C^{-T})(F21 C^{-T})^T (lower).  With n == J
+// this is a plain dense Cholesky factorisation.
+// ---------------------------------------------------------------------------
+__device__ void cta_potrf_partial(double* F, int64_t ld, int J, int n, int64_t* st, int64_t code,
+                                  int64_t snode, int64_t col0) {
+  double* Ls = sh_L;
+  double* Ps = sh_P;
+  const int tid = threadIdx.x;
+  for (int j0 = 0; j0 < n; j0 += PB) {
+    const int jb = min(PB, n - j0);
+    for (int e = tid; e < jb * jb; e += NT) {
+      int r = e % jb, c = e / jb;
+      Ls[r * (PB + 1) + c] = (r >= c) ? F[(j0 + r) + (int64_t)(j0 + c) * ld] : 0.0;
+    }
+    __syncthreads();
+    smem_potrf(Ls, jb, st, code, snode, col0 + j0);
+    for (int e = tid; e < jb * jb; e += NT) {
+      int r = e % jb, c = e / jb;
+      if (r >= c) F[(j0 + r) + (int64_t)(j0 + c) * ld] = Ls[r * (PB + 1) + c];
+    }
+    // panel rows below the diagonal block: X := P L11^{-T}
+    const int rbeg = j0 + jb;
+    for (int r0 = rbeg; r0 < J; r0 += PCH) {
+      const int rc = min(PCH, J - r0);
+      for (int e = tid; e < rc * jb; e += NT) {
+        int r = e % rc, c = e / rc;
+        Ps[r * (PB + 1) + c] = F[(r0 + r) + (int64_t)(j0 + c) * ld];
+      }
+      __syncthreads();
+      for (int c = 0; c < jb; ++c) {
+        const double inv = 1.0 / Ls[c * (PB + 1) + c];
+        for (int r = tid; r < rc; r += NT) Ps[r * (PB + 1) + c] *= inv;
+        __syncthreads();
+        const int m = jb - c - 1;
+        for (int e = tid; e < rc * m; e += NT) {
+          int r = e % rc, t = c + 1 + e / rc;
+          Ps[r * (PB + 1) + t] -= Ps[r * (PB + 1) + c] * Ls[t * (PB + 1) + c];
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < rc * jb; e += NT) {
+        int r = e % rc, c = e / rc;
+        F[(r0 + r) + (int64_t)(j0 + c) * ld] = Ps[r * (PB + 1) + c];
+      }
+      __syncthreads();
+    }
+    // trailing update of the lower triangle of F[rbeg:J, rbeg:J]
+    const int m = J - rbeg;
+    if (m > 0) {
+      double* P = F + rbeg + (int64_t)j0 * ld;
+      cta_gemm(m, m, jb, -1.0, Dn{P, ld}, DnT{P, ld}, 1.0, Dn{F + rbeg + (int64_t)rbeg * ld, ld}, true);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Right-side triangular solves on an R x n matrix B (any writable view) with
+// a lower triangular n x n matrix L (column-major, ld), column sweeps:
+//   trsm_rLT:  B := B L^{-T}      trsm_rL:  B := B L^{-1}
+// Left-side solves are the same sweeps on the transposed view of B.
+// ---------------------------------------------------------------------------
+template <class MB>
+__device__ void cta_trsm_rLT(int R, int n, MB B, const double* L, int64_t ld) {
+  const int tid = threadIdx.x;
+  for (int c = 0; c < n; ++c) {
+    const double inv = 1.0 / L[c + (int64_t)c * ld];
+    for (int r = tid; r < R; r += NT) B.at(r, c) *= inv;
+    __syncthreads();
+    const int m = n - c - 1;
+    for (int e = tid; e < R * m; e += NT) {
+      int r = e % R, t = c + 1 + e / R;
+      B.at(r, t) -= B.at(r, c) * L[t + (int64_t)c * ld];
+    }
+    __syncthreads();
+  }
+}
+template <class MB>
+__device__ void cta_trsm_rL(int R, int n, MB B, const double* L, int64_t ld) {
+  const int tid = threadIdx.x;
+  for (int c = n - 1; c >= 0; --c) {
+    const double inv = 1.0 / L[c + (int64_t)c * ld];
+    for (int r = tid; r < R; r += NT) B.at(r, c) *= inv;
+    __syncthreads();
+    for (int e = tid; e < R * c; e += NT) {
+      int r = e % R, t = e / R;
+      B.at(r, t) -= B.at(r, c) * L[c + (int64_t)t * ld];
+    }
+    __syncthreads();
+  }
+}
+// transposed writable view: (r, c) -> B(c, r)
+struct DnTW {
+  double* p;
+  int64_t ld;
+  __device__ double& at(int r, int c) const { return p[c + (int64_t)r * ld]; }
+};
+
+// ---------------------------------------------------------------------------
+// small element-wise helpers
+// ---------------------------------------------------------------------------
+__device__ void csc_to_front(double* F, int J, int n, const double* csc) {
+  for (int e = threadIdx.x; e < J * n; e += NT) {
+    int r = e % J, c = e / J;
+    if (r >= c) F[r + (int64_t)c * J] = csc[csc_off(J, r, c)];
+  }
+}
+__device__ void front_to_csc(double* csc, const double* F, int J, int n, double scale) {
+  for (int e = threadIdx.x; e < J * n; e += NT) {
+    int r = e % J, c = e / J;
+    if (r >= c) csc[csc_off(J, r, c)] = scale * F[r + (int64_t)c * J];
+  }
+}
+__device__ void zero_lower(double* F, int64_t ld, int m, int off) {
+  for (int e = threadIdx.x; e < m * m; e += NT) {
+    int r = e % m, c = e / m;
+    if (r >= c) F[(off + r) + (int64_t)(off + c) * ld] = 0.0;
+  }
+}
+__device__ void copy_lower(double* dst, int64_t ldd, const double* src, int64_t lds, int m) {
+  for (int e = threadIdx.x; e < m * m; e += NT) {
+    int r = e % m, c = e / m;
+    if (r >= c) dst[r + (int64_t)c * ldd] = src[r + (int64_t)c * lds];
+  }
+}
+__device__ void copy_rect(double* dst, int64_t ldd, const double* src, int64_t lds, int R, int C) {
+  for (int e = threadIdx.x; e < R * C; e += NT) {
+    int r = e % R, c = e / R;
+    dst[r + (int64_t)c * ldd] = src[r + (int64_t)c * lds];
+  }
+}
+__device__ void set_identity(double* dst, int64_t ld, int m) {
+  for (int e = threadIdx.x; e < m * m; e += NT) {
+    int r = e % m, c = e / m;
+    dst[r + (int64_t)c * ld] = (r == c) ? 1.0 : 0.0;
+  }
+}
+
+struct FrontInfo {
+  int k, n, a, J;
+  int64_t col0;     // first column of N_k
+  int64_t base;     // colptr[col0]
+  double* F;        // J x J front
+  double* T1;       // J x n
+  double* T2;       // J x n
+};
+
+__device__ FrontInfo front_info(const SymDev& S, int k, double* ws) {
+  FrontInfo f;
+  f.k = k;
+  f.col0 = S.sn_ptr[k];
+  f.n = (int)(S.sn_ptr[k + 1] - f.col0);
+  f.J = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]);
+  f.a = f.J - f.n;
+  f.base = S.colptr[f.col0];
+  f.F = ws + S.f_off[k];
+  f.T1 = f.F + (int64_t)f.J * f.J;
+  f.T2 = f.T1 + (int64_t)f.J * f.n;
+  return f;
+}
+
+// Extend-add of every child's update matrix (the A x A block of the child's
+// front) into this front: F += E_{J A_c} U_c E_{J A_c}^T  (children in a
+// fixed order, entries of one child touch distinct positions).
+__device__ void extend_add_children(const SymDev& S, const FrontInfo& f, double* ws, double sign) {
+  for (int64_t q = S.ch_ptr[f.k]; q < S.ch_ptr[f.k + 1]; ++q) {
+    const int c = S.ch[q];
+    const int nc = (int)(S.sn_ptr[c + 1] - S.sn_ptr[c]);
+    const int Jc = (int)(S.rows_ptr[c + 1] - S.rows_ptr[c]);
+    const int ac = Jc - nc;
+    const int32_t* rel = S.rel + S.rows_ptr[c] + nc;
+    const double* U = ws + S.f_off[c] + nc + (int64_t)nc * Jc;
+    for (int e = threadIdx.x; e < ac * ac; e += NT) {
+      int r = e % ac, s = e / ac;
+      if (r >= s) {
+        int pr = __ldg(rel + r), ps = __ldg(rel + s);
+        f.F[pr + (int64_t)ps * f.J] += sign * __ldcg(U + r + (int64_t)s * Jc);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Gather V_k = E_{J_p A_k}^T F_p E_{J_p A_k} from the parent's full front
+// into the A x A block of this front (top-down propagation, Eq. (e-sn-gradient-2)).
+__device__ void gather_from_parent(const SymDev& S, const FrontInfo& f, double* ws) {
+  const int p = (int)S.sn_par[f.k];
+  if (p < 0 || f.a == 0) return;
+  const int Jp = (int)(S.rows_ptr[p + 1] - S.rows_ptr[p]);
+  const double* Fp = ws + S.f_off[p];
+  const int32_t* rel = S.rel + S.rows_ptr[f.k] + f.n;
+  for (int e = threadIdx.x; e < f.a * f.a; e += NT) {
+    int r = e % f.a, s = e / f.a;
+    if (r >= s) {
+      int pr = __ldg(rel + r), ps = __ldg(rel + s);
+      f.F[(f.n + r) + (int64_t)(f.n + s) * f.J] = __ldcg(Fp + pr + (int64_t)ps * Jp);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Front procedures
+// ---------------------------------------------------------------------------
+
+// Algorithm 7.1 for one front, then the derived blocks D_NN^{-1} and L_AN.
+__device__ void factor_front(const SymDev& S, int k, const double* X, double* Lc, double* Wc,
+                             double* Dd, double* ws, double* ldet, int64_t* st) {
+  FrontInfo f = front_info(S, k, ws);
+  const int J = f.J, n = f.n, a = f.a;
+  csc_to_front(f.F, J, n, X + f.base);
+  zero_lower(f.F, J, a, n);
+  __syncthreads();
+  extend_add_children(S, f, ws, 1.0);
+  // D_NN = F11 (kept for the inverse Hessian)
+  copy_lower(Dd + S.d_off[k], n, f.F, J, n);
+  cta_potrf_partial(f.F, J, J, n, st, CHD_ERR_NOT_PD, k, f.col0);
+  front_to_csc(Lc + f.base, f.F, J, n, 1.0);
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) s += 2.0 * log(f.F[i + (int64_t)i * J]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) ldet[k] = s;
+  }
+  // Cinv = C^{-1} in T1[0:n,0:n]; D^{-1} = Cinv^T Cinv -> T2[0:n,0:n];
+  // L_AN = B C^{-1} -> T2[n:J, 0:n]
+  set_identity(f.T1, J, n);
+  __syncthreads();
+  cta_trsm_rLT(n, n, DnTW{f.T1, J}, f.F, J);  // (I^T C^{-T})^T = C^{-1}
+  cta_gemm(n, n, n, 1.0, TriLT{f.T1, J}, TriL{f.T1, J}, 0.0, Dn{f.T2, J}, true);
+  copy_rect(f.T2 + n, J, f.F + n, J, a, n);
+  __syncthreads();
+  cta_trsm_rL(a, n, Dn{f.T2 + n, J}, f.F, J);
+  front_to_csc(Wc + f.base, f.T2, J, n, 1.0);
+  __syncthreads();
+}
+
+// Algorithm 7.2 for one front: S_AN = -V L_AN, S_NN = D^{-1} - S_AN^T L_AN.
+__device__ void gradient_front(const SymDev& S, int k, const double* Wc, double* Sc, double* g,
+                               double* Vd, double* ws) {
+  FrontInfo f = front_info(S, k, ws);
+  const int J = f.J, n = f.n, a = f.a;
+  gather_from_parent(S, f, ws);
+  const double* W = Wc + f.base;
+  // S_AN = -V L_AN
+  cta_gemm(a, n, a, -1.0, SymL{f.F + n + (int64_t)n * J, J}, CscRO{W, J, n}, 0.0,
+           Dn{f.F + n, J}, false);
+  // S_NN = D^{-1} - S_AN^T L_AN
+  for (int e = threadIdx.x; e < n * n; e += NT) {
+    int r = e % n, c = e / n;
+    if (r >= c) f.F[r + (int64_t)c * J] = W[csc_off(J, r, c)];
+  }
+  __syncthreads();
+  cta_gemm(n, n, a, -1.0, DnT{f.F + n, J}, CscRO{W, J, n}, 1.0, Dn{f.F, J}, true);
+  front_to_csc(Sc + f.base, f.F, J, n, 1.0);
+  if (g) front_to_csc(g + f.base, f.F, J, n, -1.0);
+  copy_lower(Vd + S.v_off[k], a, f.F + n + (int64_t)n * J, J, a);
+  __syncthreads();
+}
+
+// Algorithm 5.1 steps 1-2 (block form) for one front and one right-hand side:
+// K_NN = Yh_NN, K_AN = Yh_AN - L Yh_NN, U' = Yh_AA - K_AN L^T - L Yh_AN^T,
+// M_NN = D^{-1} K_NN D^{-1}, M_AN = V K_AN D^{-1}; M is written to the
+// output array (CSC), U' stays in the front for the parent.
+__device__ void hess_up_front(const SymDev& S, int k, const double* Wc, const double* Vd,
+                              const double* Y, double* T, double* ws) {
+  FrontInfo f = front_info(S, k, ws);
+  const int J = f.J, n = f.n, a = f.a;
+  csc_to_front(f.F, J, n, Y + f.base);
+  zero_lower(f.F, J, a, n);
+  __syncthreads();
+  extend_add_children(S, f, ws, 1.0);
+  const double* W = Wc + f.base;
+  CscRO L{W, J, n};
+  // T1[n:J] = K_AN = Yh_AN - L Yh_NN
+  copy_rect(f.T1 + n, J, f.F + n, J, a, n);
+  __syncthreads();
+  cta_gemm(a, n, n, -1.0, L, SymL{f.F, J}, 1.0, Dn{f.T1 + n, J}, false);
+  // U' = Yh_AA - K_AN L^T - L Yh_AN^T   (lower)
+  cta_gemm(a, a, n, -1.0, Dn{f.T1 + n, J}, CscT{W, J, n}, 1.0, Dn{f.F + n + (int64_t)n * J, J}, true);
+  cta_gemm(a, a, n, -1.0, L, DnT{f.F + n, J}, 1.0, Dn{f.F + n + (int64_t)n * J, J}, true);
+  // M_NN = D^{-1} (K_NN D^{-1})
+  CscSym Dinv{W, J};
+  cta_gemm(n, n, n, 1.0, SymL{f.F, J}, Dinv, 0.0, Dn{f.T2, J}, false);
+  cta_gemm(n, n, n, 1.0, Dinv, Dn{f.T2, J}, 0.0, Csc{T + f.base, J, 0}, true);
+  // M_AN = V (K_AN D^{-1})
+  cta_gemm(a, n, n, 1.0, Dn{f.T1 + n, J}, Dinv, 0.0, Dn{f.T2 + n, J}, false);
+  cta_gemm(a, n, a, 1.0, SymL{Vd + S.v_off[k], a}, Dn{f.T2 + n, J}, 0.0, Csc{T + f.base, J, n}, false);
+}
+
+// Algorithm 5.1 step 3 (block form): V' gathered from the parent,
+// T_AN = M_AN - V' L, T_NN = M_NN - M_AN^T L - L^T T_AN.
+__device__ void hess_down_front(const SymDev& S, int k, const double* Wc, double* T, double* ws) {
+  FrontInfo f = front_info(S, k, ws);
+  const int J = f.J, n = f.n, a = f.a;
+  gather_from_parent(S, f, ws);
+  csc_to_front(f.F, J, n, T + f.base);
+  __syncthreads();
+  const double* W = Wc + f.base;
+  CscRO L{W, J, n};
+  // T1[n:J] = V' L
+  cta_gemm(a, n, a, 1.0, SymL{f.F + n + (int64_t)n * J, J}, L, 0.0, Dn{f.T1 + n, J}, false);
+  // Q = M_AN - 1/2 V'L ; T_NN = M_NN - (Q^T L + L^T Q) ; T_AN = Q - 1/2 V'L
+  for (int e = threadIdx.x; e < a * n; e += NT) {
+    int r = n + e % a, c = e / a;
+    f.F[r + (int64_t)c * J] -= 0.5 * f.T1[r + (int64_t)c * J];
+  }
+  __syncthreads();
+  cta_gemm(n, n, a, -1.0, DnT{f.F + n, J}, L, 1.0, Dn{f.F, J}, true);
+  cta_gemm(n, n, a, -1.0, CscT{W, J, n}, Dn{f.F + n, J}, 1.0, Dn{f.F, J}, true);
+  for (int e = threadIdx.x; e < a * n; e += NT) {
+    int r = n + e % a, c = e / a;
+    f.F[r + (int64_t)c * J] -= 0.5 * f.T1[r + (int64_t)c * J];
+  }
+  __syncthreads();
+  front_to_csc(T + f.base, f.F, J, n, 1.0);
+  __syncthreads();
+}
+
+// Algorithm 5.2 steps 1-2 (block form), top-down:
+// M_AN = T_AN + V' L, M_NN = T_NN + T_AN^T L + L^T M_AN,
+// K_NN = D M_NN D, K_AN = V^{-1} M_AN D.  K is written to the output array.
+__device__ void ihess_down_front(const SymDev& S, int k, const double* Wc, const double* Dd,
+                                 const double* Rd, const double* Tin, double* Yout, double* ws) {
+  FrontInfo f = front_info(S, k, ws);
+  const int J = f.J, n = f.n, a = f.a;
+  gather_from_parent(S, f, ws);
+  csc_to_front(f.F, J, n, Tin + f.base);
+  __syncthreads();
+  const double* W = Wc + f.base;
+  CscRO L{W, J, n};
+  // T1[n:J] = M_AN = T_AN + V' L
+  copy_rect(f.T1 + n, J, f.F + n, J, a, n);
+  __syncthreads();
+  cta_gemm(a, n, a, 1.0, SymL{f.F + n + (int64_t)n * J, J}, L, 1.0, Dn{f.T1 + n, J}, false);
+  // T1[0:n] = M_NN = T_NN + T_AN^T L + L^T M_AN   (full square)
+  for (int e = threadIdx.x; e < n * n; e += NT) {
+    int r = e % n, c = e / n;
+    f.T1[r + (int64_t)c * J] = r >= c ? f.F[r + (int64_t)c * J] : f.F[c + (int64_t)r * J];
+  }
+  __syncthreads();
+  cta_gemm(n, n, a, 1.0, DnT{f.F + n, J}, L, 1.0, Dn{f.T1, J}, false);
+  cta_gemm(n, n, a, 1.0, CscT{W, J, n}, Dn{f.T1 + n, J}, 1.0, Dn{f.T1, J}, false);
+  // K_NN = D (M_NN D)
+  const double* D = Dd + S.d_off[k];
+  cta_gemm(n, n, n, 1.0, Dn{f.T1, J}, SymL{D, n}, 0.0, Dn{f.T2, J}, false);
+  cta_gemm(n, n, n, 1.0, SymL{D, n}, Dn{f.T2, J}, 0.0, Csc{Yout + f.base, J, 0}, true);
+  // K_AN = R^{-T} R^{-1} (M_AN D)
+  if (a > 0) {
+    cta_gemm(a, n, n, 1.0, Dn{f.T1 + n, J}, SymL{D, n}, 0.0, Dn{f.T2 + n, J}, false);
+    const double* R = Rd + S.v_off[k];
+    cta_trsm_rLT(n, a, DnTW{f.T2 + n, J}, R, a);  // (X^T R^{-T})^T = R^{-1} X
+    cta_trsm_rL(n, a, DnTW{f.T2 + n, J}, R, a);   // (X^T R^{-1})^T = R^{-T} X
+    for (int e = threadIdx.x; e < a * n; e += NT) {
+      int r = e % a, c = e / a;
+      Yout[f.base + csc_off(J, n + r, c)] = f.T2[n + r + (int64_t)c * J];
+    }
+  }
+  __syncthreads();
+}
+
+// Algorithm 5.2 step 3 (block form), bottom-up:
+// Z = sum of children's extend-add, Y_NN = K_NN - Z_NN,
+// Y_AN = L K_NN + K_AN - Z_AN, U' = Z_AA - (L K_NN L^T + K_AN L^T + L K_AN^T).
+__device__ void ihess_up_front(const SymDev& S, int k, const double* Wc, double* Y, double* ws) {
+  FrontInfo f = front_info(S, k, ws);
+  const int J = f.J, n = f.n, a = f.a;
+  zero_lower(f.F, J, J, 0);
+  __syncthreads();
+  extend_add_children(S, f, ws, 1.0);
+  const double* W = Wc + f.base;
+  CscRO L{W, J, n};
+  CscSym Kn{Y + f.base, J};
+  // T2[n:J] = P = K_AN + 1/2 L K_NN
+  for (int e = threadIdx.x; e < a * n; e += NT) {
+    int r = e % a, c = e / a;
+    f.T2[n + r + (int64_t)c * J] = Y[f.base + csc_off(J, n + r, c)];
+  }
+  __syncthreads();
+  cta_gemm(a, n, n, 0.5, L, Kn, 1.0, Dn{f.T2 + n, J}, false);
+  // U' = Z_AA - (P L^T + L P^T)
+  cta_gemm(a, a, n, -1.0, Dn{f.T2 + n, J}, CscT{W, J, n}, 1.0, Dn{f.F + n + (int64_t)n * J, J}, true);
+  cta_gemm(a, a, n, -1.0, L, DnT{f.T2 + n, J}, 1.0, Dn{f.F + n + (int64_t)n * J, J}, true);
+  // Y_AN = K_AN + L K_NN - Z_AN = 2P - K_AN - Z_AN ;  Y_NN = K_NN - Z_NN
+  for (int e = threadIdx.x; e < a * n; e += NT) {
+    int r = e % a, c = e / a;
+    int64_t o = f.base + csc_off(J, n + r, c);
+    double kan = Y[o];
+    Y[o] = 2.0 * f.T2[n + r + (int64_t)c * J] - kan - f.F[n + r + (int64_t)c * J];
+  }
+  for (int e = threadIdx.x; e < n * n; e += NT) {
+    int r = e % n, c = e / n;
+    if (r >= c) {
+      int64_t o = f.base + csc_off(J, r, c);
+      Y[o] = Y[o] - f.F[r + (int64_t)c * J];
+    }
+  }
+  __syncthreads();
+}
+
+// Algorithm 7.3 for one front (each front needs only S and V_k = S_AA):
+// R = chol(V), Z = R^{-1} S_AN, P = S_NN - Z^T Z = D_NN^{-1},
+// L_AN = -R^{-T} Z, D_NN = P^{-1}, C = chol(D_NN), B = L_AN C.
+__device__ void complete_front(const SymDev& S, int k, const double* Sin, double* Lc, double* Wc,
+                               double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
+                               int64_t* st) {
+  FrontInfo f = front_info(S, k, ws);
+  const int J = f.J, n = f.n, a = f.a;
+  gather_from_parent(S, f, ws);
+  csc_to_front(f.F, J, n, Sin + f.base);
+  __syncthreads();
+  double* V = Vd + S.v_off[k];
+  double* R = Rd + S.v_off[k];
+  copy_lower(V, a, f.F + n + (int64_t)n * J, J, a);
+  copy_lower(R, a, f.F + n + (int64_t)n * J, J, a);
+  __syncthreads();
+  if (a > 0) cta_potrf_partial(R, a, a, a, st, CHD_ERR_NOT_COMPLETABLE, k, -1);
+  // T1[n:J] = Z = R^{-1} S_AN
+  copy_rect(f.T1 + n, J, f.F + n, J, a, n);
+  __syncthreads();
+  if (a > 0) cta_trsm_rLT(n, a, DnTW{f.T1 + n, J}, R, a);
+  // T1[0:n] (lower) = P = S_NN - Z^T Z
+  copy_lower(f.T1, J, f.F, J, n);
+  __syncthreads();
+  cta_gemm(n, n, a, -1.0, DnT{f.T1 + n, J}, Dn{f.T1 + n, J}, 1.0, Dn{f.T1, J}, true);
+  // T2[n:J] = L_AN = -R^{-T} Z
+  for (int e = threadIdx.x; e < a * n; e += NT) {
+    int r = n + e % a, c = e / a;
+    f.T2[r + (int64_t)c * J] = -f.T1[r + (int64_t)c * J];
+  }
+  __syncthreads();
+  if (a > 0) cta_trsm_rL(n, a, DnTW{f.T2 + n, J}, R, a);
+  // Wc = [P; L_AN]
+  for (int e = threadIdx.x; e < J * n; e += NT) {
+    int r = e % J, c = e / J;
+    if (r >= c) Wc[f.base + csc_off(J, r, c)] = (r < n) ? f.T1[r + (int64_t)c * J] : f.T2[r + (int64_t)c * J];
+  }
+  // T2[0:n] = chol(P) = Q ; D = P^{-1} = Q^{-T} Q^{-1}
+  copy_lower(f.T2, J, f.T1, J, n);
+  __syncthreads();
+  cta_potrf_partial(f.T2, J, n, n, st, CHD_ERR_NOT_COMPLETABLE, k, f.col0);
+  double* Dk = Dd + S.d_off[k];
+  set_identity(Dk, n, n);
+  __syncthreads();
+  cta_trsm_rLT(n, n, DnTW{Dk, n}, f.T2, J);  // Dk = Q^{-1}
+  cta_gemm(n, n, n, 1.0, TriLT{Dk, n}, TriL{Dk, n}, 0.0, Dn{f.T1, J}, true);  // T1 = D (lower)
+  copy_lower(Dk, n, f.T1, J, n);
+  __syncthreads();
+  // C = chol(D) in T1[0:n]; B = L_AN C
+  cta_potrf_partial(f.T1, J, n, n, st, CHD_ERR_NOT_COMPLETABLE, k, f.col0);
+  for (int e = threadIdx.x; e < n * n; e += NT) {
+    int r = e % n, c = e / n;
+    if (r >= c) Lc[f.base + csc_off(J, r, c)] = f.T1[r + (int64_t)c * J];
+  }
+  cta_gemm(a, n, n, 1.0, Dn{f.T2 + n, J}, TriL{f.T1, J}, 0.0, Csc{Lc + f.base, J, n}, false);
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) s += 2.0 * log(f.T1[i + (int64_t)i * J]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) ldet[k] = s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// kernels: blockIdx.x = task within the launch, blockIdx.y = right-hand side
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_factor(SymDev S, int task0, const double* X, double* Lc,
+                                               double* Wc, double* Dd, double* ws, double* ldet,
+                                               int64_t* st) {
+  const int t = task0 + blockIdx.x;
+  for (int q = S.task_ptr[t]; q < S.task_ptr[t + 1]; ++q)
+    factor_front(S, S.task_fronts[q], X, Lc, Wc, Dd, ws, ldet, st);
+}
+__global__ void __launch_bounds__(NT) k_gradient(SymDev S, int task0, const double* Wc, double* Sc,
+                                                 double* g, double* Vd, double* ws) {
+  const int t = task0 + blockIdx.x;
+  for (int q = S.task_ptr[t + 1] - 1; q >= S.task_ptr[t]; --q)
+    gradient_front(S, S.task_fronts[q], Wc, Sc, g, Vd, ws);
+}
+__global__ void __launch_bounds__(NT) k_hess_up(SymDev S, int task0, const double* Wc,
+                                                const double* Vd, const double* Y, int64_t ldy,
+                                                double* T, int64_t ldt, double* ws) {
+  const int t = task0 + blockIdx.x;
+  const int64_t y = blockIdx.y;
+  for (int q = S.task_ptr[t]; q < S.task_ptr[t + 1]; ++q)
+    hess_up_front(S, S.task_fronts[q], Wc, Vd, Y + y * ldy, T + y * ldt, ws + y * S.f_total);
+}
+__global__ void __launch_bounds__(NT) k_hess_down(SymDev S, int task0, const double* Wc, double* T,
+                                                  int64_t ldt, double* ws) {
+  const int t = task0 + blockIdx.x;
+  const int64_t y = blockIdx.y;
+  for (int q = S.task_ptr[t + 1] - 1; q >= S.task_ptr[t]; --q)
+    hess_down_front(S, S.task_fronts[q], Wc, T + y * ldt, ws + y * S.f_total);
+}
+__global__ void __launch_bounds__(NT) k_ihess_down(SymDev S, int task0, const double* Wc,
+                                                   const double* Dd, const double* Rd,
+                                                   const double* Tin, int64_t ldt, double* Y,
+                                                   int64_t ldy, double* ws) {
+  const int t = task0 + blockIdx.x;
+  const int64_t y = blockIdx.y;
+  for (int q = S.task_ptr[t + 1] - 1; q >= S.task_ptr[t]; --q)
+    ihess_down_front(S, S.task_fronts[q], Wc, Dd, Rd, Tin + y * ldt, Y + y * ldy, ws + y * S.f_total);
+}
+__global__ void __launch_bounds__(NT) k_ihess_up(SymDev S, int task0, const double* Wc, double* Y,
+                                                 int64_t ldy, double* ws) {
+  const int t = task0 + blockIdx.x;
+  const int64_t y = blockIdx.y;
+  for (int q = S.task_ptr[t]; q < S.task_ptr[t + 1]; ++q)
+    ihess_up_front(S, S.task_fronts[q], Wc, Y + y * ldy, ws + y * S.f_total);
+}
+__global__ void __launch_bounds__(NT) k_complete(SymDev S, int task0, const double* Sin, double* Lc,
+                                                 double* Wc, double* Dd, double* Vd, double* Rd,
+                                                 double* ws, double* ldet, int64_t* st) {
+  const int t = task0 + blockIdx.x;
+  for (int q = S.task_ptr[t + 1] - 1; q >= S.task_ptr[t]; --q)
+    complete_front(S, S.task_fronts[q], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, st);
+}
+// Cholesky factors of the cached V_k, one CTA per front (no dependencies).
+__global__ void __launch_bounds__(NT) k_chol_v(SymDev S, const double* Vd, double* Rd, int64_t* st) {
+  const int k = blockIdx.x;
+  const int n = (int)(S.sn_ptr[k + 1] - S.sn_ptr[k]);
+  const int a = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]) - n;
+  if (a == 0) return;
+  copy_lower(Rd + S.v_off[k], a, Vd + S.v_off[k], a, a);
+  __syncthreads();
+  cta_potrf_partial(Rd + S.v_off[k], a, a, a, st, CHD_ERR_NOT_PD, k, -1);
+}
+// Deterministic sum of the per-front log det contributions.
+__global__ void k_sum(const double* v, int64_t m, double* out) {
+  __shared__ double red[NT];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += NT) s += v[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = NT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+// Unique scalar L D L^T from the supernodal Cholesky factor G = [C; B]:
+// L = G diag(1/G_ii), D_ii = G_ii^2.
+__global__ void k_export(SymDev S, const double* Lc, double* l, double* d) {
+  const int k = blockIdx.x;
+  const int64_t col0 = S.sn_ptr[k];
+  const int n = (int)(S.sn_ptr[k + 1] - col0);
+  const int J = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]);
+  const int64_t base = S.colptr[col0];
+  for (int e = threadIdx.x; e < J * n; e += NT) {
+    int r = e % J, c = e / J;
+    if (r >= c) {
+      double gcc = Lc[base + csc_off(J, c, c)];
+      l[base + csc_off(J, r, c)] = (r == c) ? 1.0 : Lc[base + csc_off(J, r, c)] / gcc;
+      if (r == c && d) d[col0 + c] = gcc * gcc;
+    }
+  }
+}
+
+}  // namespace chd
+
+// ---------------------------------------------------------------------------
+// host launchers (called from capi.cpp)
+// ---------------------------------------------------------------------------
+namespace chd_launch {
+using namespace chd;
+
+static int64_t g_launches = 0;
+int64_t launches() { return g_launches; }
+
+static inline void count() { ++g_launches; }
+
+void factor(const chd_symbolic* s, cudaStream_t st, const double* X, double* Lc, double* Wc,
+            double* Dd, double* ws, double* ldet, int64_t* status) {
+  const int nl = (int)s->lvl_ptr.size() - 1;
+  for (int l = 0; l < nl; ++l) {
+    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
+    if (nt == 0) continue;
+    k_factor<<<nt, NT, 0, st>>>(s->dev, t0, X, Lc, Wc, Dd, ws, ldet, status);
+    count();
+  }
+}
+void gradient(const chd_symbolic* s, cudaStream_t st, const double* Wc, double* Sc, double* g,
+              double* Vd, double* ws) {
+  const int nl = (int)s->lvl_ptr.size() - 1;
+  for (int l = nl - 1; l >= 0; --l) {
+    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
+    if (nt == 0) continue;
+    k_gradient<<<nt, NT, 0, st>>>(s->dev, t0, Wc, Sc, g, Vd, ws);
+    count();
+  }
+}
+void hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Vd,
+             const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
+  const int nl = (int)s->lvl_ptr.size() - 1;
+  for (int l = 0; l < nl; ++l) {
+    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
+    if (nt == 0) continue;
+    k_hess_up<<<dim3(nt, m), NT, 0, st>>>(s->dev, t0, Wc, Vd, Y, ldy, T, ldt, ws);
+    count();
+  }
+  for (int l = nl - 1; l >= 0; --l) {
+    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
+    if (nt == 0) continue;
+    k_hess_down<<<dim3(nt, m), NT, 0, st>>>(s->dev, t0, Wc, T, ldt, ws);
+    count();
+  }
+}
+void inv_hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Dd,
+                 const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy,
+                 double* ws) {
+  const int nl = (int)s->lvl_ptr.size() - 1;
+  for (int l = nl - 1; l >= 0; --l) {
+    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
+    if (nt == 0) continue;
+    k_ihess_down<<<dim3(nt, m), NT, 0, st>>>(s->dev, t0, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    count();
+  }
+  for (int l = 0; l < nl; ++l) {
+    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
+    if (nt == 0) continue;
+    k_ihess_up<<<dim3(nt, m), NT, 0, st>>>(s->dev, t0, Wc, Y, ldy, ws);
+    count();
+  }
+}
+void complete(const chd_symbolic* s, cudaStream_t st, const double* Sin, double* Lc, double* Wc,
+              double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
+  const int nl = (int)s->lvl_ptr.size() - 1;
+  for (int l = nl - 1; l >= 0; --l) {
+    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
+    if (nt == 0) continue;
+    k_complete<<<nt, NT, 0, st>>>(s->dev, t0, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+    count();
+  }
+}
+void chol_v(const chd_symbolic* s, cudaStream_t st, const double* Vd, double* Rd, int64_t* status) {
+  k_chol_v<<<(int)s->nsn, NT, 0, st>>>(s->dev, Vd, Rd, status);
+  count();
+}
+void sum(cudaStream_t st, const double* v, int64_t m, double* out) {
+  k_sum<<<1, NT, 0, st>>>(v, m, out);
+  count();
+}
+void export_ldl(const chd_symbolic* s, cudaStream_t st, const double* Lc, double* l, double* d) {
+  k_export<<<(int)s->nsn, NT, 0, st>>>(s->dev, Lc, l, d);
+  count();
+}
+}  // namespace chd_launch

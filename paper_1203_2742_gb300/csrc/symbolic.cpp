@@ -1,0 +1,516 @@
+// Host symbolic phase: ordering, elimination fill, elimination tree,
+// supernode partition and clique tree (Algorithm 6.1), relaxed amalgamation,
+// relative index maps for E_{J_p A_k}, workspace offsets and the launch
+// schedule.
+//
+// Andersen, Dahl, Vandenberghe, "Logarithmic barriers for sparse matrix
+// cones": §2 (filled patterns, elimination tree, Eq. (e-filled),
+// Eq. (e-etree-ch)), §6.1 (representative vertices, Eq. (e-repr-test)),
+// §6.2 (supernodes, Eq. (e-new2)), §6.3 (clique tree), §6.4 (Algorithm 6.1),
+// §1.5 (index sets and E_IJ), §8 (relaxed supernodes, tree parallelism).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <set>
+#include <utility>
+#include <vector>
+
+#include "chd_internal.h"
+
+namespace {
+
+using std::vector;
+
+// Off-diagonal adjacency lists (both directions) of the user's pattern.
+bool build_adjacency(int64_t n, const int64_t* colptr, const int32_t* rowind,
+                     vector<vector<int32_t>>& adj) {
+  adj.assign(n, {});
+  if (colptr[0] != 0) return false;
+  for (int64_t j = 0; j < n; ++j) {
+    if (colptr[j + 1] < colptr[j]) return false;
+    for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+      int64_t i = rowind[p];
+      if (i < j || i >= n) return false;
+      if (i == j) continue;
+      adj[j].push_back((int32_t)i);
+      adj[i].push_back((int32_t)j);
+    }
+  }
+  for (auto& a : adj) {
+    std::sort(a.begin(), a.end());
+    a.erase(std::unique(a.begin(), a.end()), a.end());
+  }
+  return true;
+}
+
+// Minimum-degree ordering on the quotient graph (eliminated vertices become
+// "elements", cliques of their uneliminated neighbours; adjacent elements are
+// absorbed).  The vertex of least exact external degree is eliminated next,
+// smallest index on ties; once the least degree equals the number of
+// remaining vertices minus one, the rest is a clique and is appended in
+// index order.  Returns perm[new] = old.
+vector<int64_t> minimum_degree(int64_t n, const vector<vector<int32_t>>& adj0) {
+  vector<vector<int32_t>> vadj = adj0, eadj(n), evars(n);
+  vector<char> state(n, 0);  // 0 variable, 1 element, 2 absorbed
+  vector<int64_t> deg(n), mark(n, -1);
+  int64_t stamp = 0;
+  auto degree = [&](int64_t u) {
+    ++stamp;
+    mark[u] = stamp;
+    int64_t cnt = 0;
+    for (int32_t w : vadj[u])
+      if (state[w] == 0 && mark[w] != stamp) { mark[w] = stamp; ++cnt; }
+    for (int32_t e : eadj[u])
+      for (int32_t w : evars[e])
+        if (state[w] == 0 && mark[w] != stamp) { mark[w] = stamp; ++cnt; }
+    return cnt;
+  };
+  std::set<std::pair<int64_t, int64_t>> pq;
+  for (int64_t v = 0; v < n; ++v) { deg[v] = (int64_t)vadj[v].size(); pq.insert({deg[v], v}); }
+  vector<int64_t> perm;
+  perm.reserve(n);
+  vector<int32_t> Lv;
+  while (!pq.empty()) {
+    auto it = pq.begin();
+    int64_t v = it->second;
+    if (it->first == (int64_t)pq.size() - 1) {  // remaining vertices form a clique
+      vector<int64_t> rest;
+      for (auto& q : pq) rest.push_back(q.second);
+      std::sort(rest.begin(), rest.end());
+      for (int64_t r : rest) perm.push_back(r);
+      break;
+    }
+    pq.erase(it);
+    // Lv = variables adjacent to v directly or through its elements
+    ++stamp;
+    mark[v] = stamp;
+    Lv.clear();
+    for (int32_t w : vadj[v])
+      if (state[w] == 0 && mark[w] != stamp) { mark[w] = stamp; Lv.push_back(w); }
+    for (int32_t e : eadj[v]) {
+      for (int32_t w : evars[e])
+        if (state[w] == 0 && mark[w] != stamp) { mark[w] = stamp; Lv.push_back(w); }
+      state[e] = 2;
+      vector<int32_t>().swap(evars[e]);
+    }
+    state[v] = 1;
+    perm.push_back(v);
+    evars[v] = Lv;
+    vector<int32_t>().swap(vadj[v]);
+    vector<int32_t>().swap(eadj[v]);
+    const int64_t inL = stamp;  // mark[w] == inL  <=>  w in Lv ∪ {v}
+    for (int32_t u : Lv) {
+      vector<int32_t> ne;
+      for (int32_t e : eadj[u])
+        if (state[e] == 1) ne.push_back(e);
+      ne.push_back((int32_t)v);
+      eadj[u].swap(ne);
+      vector<int32_t> nv;
+      for (int32_t w : vadj[u])
+        if (state[w] == 0 && mark[w] != inL) nv.push_back(w);
+      vadj[u].swap(nv);
+    }
+    for (int32_t u : Lv) {
+      pq.erase({deg[u], u});
+      deg[u] = degree(u);
+      pq.insert({deg[u], u});
+    }
+  }
+  return perm;
+}
+
+// Lower pattern (strictly below the diagonal) of P A P^T, perm[new] = old.
+void permuted_lower(int64_t n, const vector<vector<int32_t>>& adj, const vector<int64_t>& perm,
+                    vector<vector<int32_t>>& low) {
+  vector<int64_t> inv(n);
+  for (int64_t i = 0; i < n; ++i) inv[perm[i]] = i;
+  low.assign(n, {});
+  for (int64_t jn = 0; jn < n; ++jn) {
+    int64_t jo = perm[jn];
+    for (int32_t io : adj[jo]) {
+      int64_t in = inv[io];
+      if (in > jn) low[jn].push_back((int32_t)in);
+    }
+    std::sort(low[jn].begin(), low[jn].end());
+  }
+}
+
+// Filled pattern I_k of L: column k of L holds the rows of column k of the
+// matrix below the diagonal together with I_c \ {k} for the children c of
+// k in the elimination tree, whose parent is min I_c (§2; Eq. (e-etree-ch)).
+void row_merge_fill(int64_t n, const vector<vector<int32_t>>& low, vector<vector<int32_t>>& I,
+                    vector<int64_t>& parent) {
+  I.assign(n, {});
+  parent.assign(n, -1);
+  vector<vector<int32_t>> kids(n);
+  vector<int64_t> mark(n, -1);
+  for (int64_t k = 0; k < n; ++k) {
+    vector<int32_t>& s = I[k];
+    for (int32_t r : low[k])
+      if (mark[r] != k) { mark[r] = k; s.push_back(r); }
+    for (int32_t c : kids[k])
+      for (int32_t r : I[c])
+        if (r != k && mark[r] != k) { mark[r] = k; s.push_back(r); }
+    std::sort(s.begin(), s.end());
+    if (!s.empty()) {
+      parent[k] = s[0];
+      kids[s[0]].push_back((int32_t)k);
+    }
+  }
+}
+
+// Algorithm 6.1, step 1: chain child of each vertex (the child whose
+// supernode it joins) or -1 when the vertex is representative
+// (Eq. (e-repr-test)).  Children are scanned in increasing index order;
+// tie_last picks the eligible child of largest index, otherwise smallest.
+vector<int64_t> chain_children(int64_t n, const vector<vector<int32_t>>& I, const vector<int64_t>& parent,
+                               bool tie_last) {
+  vector<int64_t> chain(n, -1);
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t p = parent[j];
+    if (p < 0) continue;
+    if ((int64_t)I[j].size() == (int64_t)I[p].size() + 1) {
+      if (chain[p] < 0) chain[p] = j;
+      else if (tie_last) chain[p] = std::max(chain[p], j);
+      else chain[p] = std::min(chain[p], j);
+    }
+  }
+  return chain;
+}
+
+// Postorder of the elimination forest in which each vertex's chain child
+// is visited last among its children, so supernodes become contiguous.
+vector<int64_t> chain_postorder(int64_t n, const vector<int64_t>& parent, const vector<int64_t>& chain) {
+  vector<vector<int64_t>> kids(n);
+  vector<int64_t> roots;
+  for (int64_t j = 0; j < n; ++j) {
+    if (parent[j] < 0) roots.push_back(j);
+    else kids[parent[j]].push_back(j);
+  }
+  for (int64_t v = 0; v < n; ++v) {
+    if (chain[v] >= 0) {
+      auto& k = kids[v];
+      auto it = std::find(k.begin(), k.end(), chain[v]);
+      if (it != k.end()) { k.erase(it); k.push_back(chain[v]); }
+    }
+  }
+  vector<int64_t> post;
+  post.reserve(n);
+  vector<std::pair<int64_t, size_t>> st;
+  for (int64_t r : roots) {
+    st.push_back({r, 0});
+    while (!st.empty()) {
+      auto& top = st.back();
+      if (top.second < kids[top.first].size()) {
+        int64_t c = kids[top.first][top.second++];
+        st.push_back({c, 0});
+      } else {
+        post.push_back(top.first);
+        st.pop_back();
+      }
+    }
+  }
+  return post;  // post[new] = old (in the current numbering)
+}
+
+}  // namespace
+
+void chd_opts_default(chd_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->ordering = CHD_ORDER_NATURAL;
+  o->user_perm = nullptr;
+  o->relax = 0;
+  o->tie_last = 1;
+}
+
+chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* rowind,
+                              const chd_opts& opts, chd_symbolic* s) {
+  if (n < 1 || !colptr || !rowind) return CHD_ERR_INVALID;
+  vector<vector<int32_t>> adj;
+  if (!build_adjacency(n, colptr, rowind, adj)) return CHD_ERR_INVALID;
+
+  // ---- ordering -----------------------------------------------------------
+  vector<int64_t> perm0(n);
+  if (opts.ordering == CHD_ORDER_NATURAL) {
+    std::iota(perm0.begin(), perm0.end(), 0);
+  } else if (opts.ordering == CHD_ORDER_USER) {
+    if (!opts.user_perm) return CHD_ERR_INVALID;
+    vector<char> seen(n, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t v = opts.user_perm[i];
+      if (v < 0 || v >= n || seen[v]) return CHD_ERR_INVALID;
+      seen[v] = 1;
+      perm0[i] = v;
+    }
+  } else if (opts.ordering == CHD_ORDER_MINDEG) {
+    perm0 = minimum_degree(n, adj);
+  } else {
+    return CHD_ERR_INVALID;
+  }
+
+  // ---- pass 1: fill + Algorithm 6.1 chains -> contiguous postorder --------
+  vector<vector<int32_t>> low, I;
+  vector<int64_t> parent;
+  permuted_lower(n, adj, perm0, low);
+  row_merge_fill(n, low, I, parent);
+  vector<int64_t> chain = chain_children(n, I, parent, opts.tie_last != 0);
+  vector<int64_t> post = chain_postorder(n, parent, chain);
+  vector<int64_t> perm(n);
+  for (int64_t i = 0; i < n; ++i) perm[i] = perm0[post[i]];
+
+  // ---- pass 2: final numbering ---------------------------------------------
+  permuted_lower(n, adj, perm, low);
+  row_merge_fill(n, low, I, parent);
+  low.clear();
+  low.shrink_to_fit();
+  // In the postorder the chain child of i is i-1 (the largest child index).
+  chain = chain_children(n, I, parent, true);
+
+  // Supernodes: maximal runs j0..j1 where chain[j] == j-1 for j in (j0, j1].
+  vector<int64_t> first;  // first column of each fundamental supernode
+  for (int64_t j = 0; j < n; ++j)
+    if (!(chain[j] == j - 1 && j > 0)) first.push_back(j);
+  int64_t ns = (int64_t)first.size();
+  vector<int64_t> last(ns);
+  for (int64_t k = 0; k < ns; ++k) last[k] = (k + 1 < ns ? first[k + 1] : n) - 1;
+  // A_k = I_{last} (the clique's ancestor set, Eq. (e-new2)); n_k, a_k.
+  vector<int64_t> nk(ns), ak(ns);
+  vector<int64_t> snode_of(n);
+  for (int64_t k = 0; k < ns; ++k) {
+    nk[k] = last[k] - first[k] + 1;
+    ak[k] = (int64_t)I[last[k]].size();
+    for (int64_t j = first[k]; j <= last[k]; ++j) snode_of[j] = k;
+  }
+  // Each supernode's structure: I_first = N_k \ {first} ∪ A_k must hold.
+  for (int64_t k = 0; k < ns; ++k) {
+    if ((int64_t)I[first[k]].size() != nk[k] - 1 + ak[k]) return CHD_ERR_INVALID;
+  }
+  vector<vector<int32_t>> A(ns);
+  for (int64_t k = 0; k < ns; ++k) A[k] = I[last[k]];
+  I.clear();
+  I.shrink_to_fit();
+
+  // ---- relaxed amalgamation -------------------------------------------------
+  // Merge the child supernode c whose columns end right before p's first
+  // column (c is then a clique-tree child of p: min A_c = first(p)) when the
+  // merge adds at most `relax` explicit zeros: the merged node has
+  // N = N_c ∪ N_p and A = A_p, so each column of N_c gains
+  // |J_p| - |A_c| new entries.
+  vector<char> alive(ns, 1);
+  if (opts.relax > 0) {
+    vector<int64_t> owner(n);  // column -> current supernode id
+    for (int64_t j = 0; j < n; ++j) owner[j] = snode_of[j];
+    for (int64_t p = 0; p < ns; ++p) {
+      bool merged = true;
+      while (merged) {
+        merged = false;
+        int64_t f = first[p];
+        if (f == 0) break;
+        int64_t c = owner[f - 1];
+        if (!alive[c] || c == p) break;
+        if (A[c].empty() || A[c][0] != f) break;
+        int64_t zeros = nk[c] * (nk[p] + ak[p] - ak[c]);
+        if (zeros <= opts.relax) {
+          alive[c] = 0;
+          first[p] = first[c];
+          nk[p] += nk[c];
+          for (int64_t j = first[c]; j <= last[c]; ++j) owner[j] = p;
+          A[c].clear();
+          merged = true;
+        }
+      }
+    }
+  }
+
+  // ---- final supernodes, clique tree, J lists, relative indices -----------
+  vector<int64_t> ids;
+  for (int64_t k = 0; k < ns; ++k)
+    if (alive[k]) ids.push_back(k);
+  const int64_t nsn = (int64_t)ids.size();
+  s->n = n;
+  s->perm = perm;
+  s->nsn = nsn;
+  s->sn_ptr.assign(nsn + 1, 0);
+  s->sn_par.assign(nsn, -1);
+  s->rows_ptr.assign(nsn + 1, 0);
+  vector<int64_t> col_owner(n);
+  for (int64_t t = 0; t < nsn; ++t) {
+    int64_t k = ids[t];
+    s->sn_ptr[t] = first[k];
+    for (int64_t j = first[k]; j <= last[k]; ++j) col_owner[j] = t;
+  }
+  s->sn_ptr[nsn] = n;
+  for (int64_t t = 0; t < nsn; ++t) {
+    if (s->sn_ptr[t + 1] <= s->sn_ptr[t]) return CHD_ERR_INVALID;
+    s->rows_ptr[t + 1] = s->rows_ptr[t] + (s->sn_ptr[t + 1] - s->sn_ptr[t]) + (int64_t)A[ids[t]].size();
+  }
+  s->rows.assign(s->rows_ptr[nsn], 0);
+  s->rel.assign(s->rows_ptr[nsn], -1);
+  int64_t maxJ = 0;
+  for (int64_t t = 0; t < nsn; ++t) {
+    int64_t k = ids[t];
+    int64_t o = s->rows_ptr[t];
+    for (int64_t j = s->sn_ptr[t]; j < s->sn_ptr[t + 1]; ++j) s->rows[o++] = (int32_t)j;
+    for (int32_t r : A[k]) s->rows[o++] = r;
+    if (!A[k].empty()) s->sn_par[t] = col_owner[A[k][0]];
+    maxJ = std::max(maxJ, s->rows_ptr[t + 1] - s->rows_ptr[t]);
+  }
+  s->max_front = maxJ;
+  // relative positions of A_t inside J_par(t) (E_{J_p A_t}, §1.5)
+  {
+    vector<int32_t> pos(n, -1);
+    vector<vector<int64_t>> kids(nsn);
+    for (int64_t t = 0; t < nsn; ++t)
+      if (s->sn_par[t] >= 0) kids[s->sn_par[t]].push_back(t);
+    s->ch_ptr.assign(nsn + 1, 0);
+    for (int64_t p = 0; p < nsn; ++p) s->ch_ptr[p + 1] = s->ch_ptr[p] + (int64_t)kids[p].size();
+    s->ch.assign(s->ch_ptr[nsn], 0);
+    for (int64_t p = 0; p < nsn; ++p) {
+      for (size_t q = 0; q < kids[p].size(); ++q) s->ch[s->ch_ptr[p] + q] = (int32_t)kids[p][q];
+      for (int64_t o = s->rows_ptr[p]; o < s->rows_ptr[p + 1]; ++o) pos[s->rows[o]] = (int32_t)(o - s->rows_ptr[p]);
+      for (int64_t c : kids[p]) {
+        int64_t nc = s->sn_ptr[c + 1] - s->sn_ptr[c];
+        for (int64_t o = s->rows_ptr[c] + nc; o < s->rows_ptr[c + 1]; ++o) {
+          int32_t r = pos[s->rows[o]];
+          if (r < 0) return CHD_ERR_INVALID;  // A_c ⊄ J_p: not a clique tree
+          s->rel[o] = r;
+        }
+      }
+      for (int64_t o = s->rows_ptr[p]; o < s->rows_ptr[p + 1]; ++o) pos[s->rows[o]] = -1;
+    }
+  }
+
+  // ---- CSC of the filled pattern V (column j of N_k: rows J_k[c:]) -------
+  s->colptr.assign(n + 1, 0);
+  for (int64_t t = 0; t < nsn; ++t) {
+    int64_t J = s->rows_ptr[t + 1] - s->rows_ptr[t];
+    for (int64_t j = s->sn_ptr[t]; j < s->sn_ptr[t + 1]; ++j)
+      s->colptr[j + 1] = J - (j - s->sn_ptr[t]);
+  }
+  for (int64_t j = 0; j < n; ++j) s->colptr[j + 1] += s->colptr[j];
+  s->rowind.assign(s->colptr[n], 0);
+  for (int64_t t = 0; t < nsn; ++t) {
+    for (int64_t j = s->sn_ptr[t]; j < s->sn_ptr[t + 1]; ++j) {
+      int64_t c = j - s->sn_ptr[t];
+      int64_t o = s->colptr[j];
+      for (int64_t q = s->rows_ptr[t] + c; q < s->rows_ptr[t + 1]; ++q) s->rowind[o++] = s->rows[q];
+    }
+  }
+
+  // ---- workspace offsets and algorithmic flop counts (§8 measurement) ----
+  s->f_off.assign(nsn + 1, 0);
+  s->d_off.assign(nsn + 1, 0);
+  s->v_off.assign(nsn + 1, 0);
+  for (double& f : s->flops) f = 0;
+  for (int64_t t = 0; t < nsn; ++t) {
+    int64_t nn = s->sn_ptr[t + 1] - s->sn_ptr[t];
+    int64_t J = s->rows_ptr[t + 1] - s->rows_ptr[t];
+    int64_t a = J - nn;
+    // front F (J x J) + two J x n temporaries; rounded to 4 doubles (32 B)
+    int64_t fsz = J * J + 2 * J * nn;
+    fsz = (fsz + 3) & ~int64_t(3);
+    s->f_off[t + 1] = s->f_off[t] + fsz;
+    s->d_off[t + 1] = s->d_off[t] + ((nn * nn + 3) & ~int64_t(3));
+    s->v_off[t + 1] = s->v_off[t] + ((a * a + 3) & ~int64_t(3));
+    double dn = (double)nn, da = (double)a;
+    s->flops[0] += dn * dn * dn / 3 + da * dn * dn + da * da * dn;
+    s->flops[1] += 2 * da * da * dn + da * dn * dn + 2 * dn * dn * dn / 3;
+    s->flops[2] += 6 * da * da * dn + 8 * da * dn * dn + 2 * dn * dn * dn;
+    s->flops[3] += 6 * da * da * dn + 8 * da * dn * dn + 2 * dn * dn * dn + 4 * da * da * dn;
+    s->flops[4] += da * da * da / 3 + da * da * dn + da * dn * dn + dn * dn * dn;
+  }
+
+  // ---- schedule: subtree tasks at the bottom, chains of large fronts on top
+  // Work estimate per front: Hessian flops plus a fixed per-front latency
+  // cost; a subtree whose total work is at most total/(4*152) becomes one
+  // task processed by one CTA in postorder (tree parallelism, §8).  The
+  // remaining fronts form single-child chains, one task each, grouped into
+  // launches by level.
+  {
+    vector<double> w(nsn), W(nsn, 0.0);
+    double total = 0;
+    for (int64_t t = 0; t < nsn; ++t) {
+      int64_t nn = s->sn_ptr[t + 1] - s->sn_ptr[t];
+      int64_t a = (s->rows_ptr[t + 1] - s->rows_ptr[t]) - nn;
+      double dn = (double)nn, da = (double)a;
+      w[t] = 6 * da * da * dn + 8 * da * dn * dn + 2 * dn * dn * dn + 5.0e4;
+    }
+    for (int64_t t = 0; t < nsn; ++t) {  // children precede parents
+      W[t] += w[t];
+      if (s->sn_par[t] >= 0) W[s->sn_par[t]] += W[t];
+      if (s->sn_par[t] < 0) total += W[t];
+    }
+    const double thr = total / (4.0 * 152.0);
+    vector<char> top(nsn, 0);
+    for (int64_t t = 0; t < nsn; ++t) top[t] = W[t] > thr;
+    vector<int64_t> task_of(nsn, -1);
+    vector<vector<int32_t>> tasks;
+    vector<int64_t> tlevel;
+    // Supernode numbering is a postorder of the clique tree (children
+    // precede parents and subtrees are contiguous), so the subtree of t is
+    // [t - size(t) + 1, t].
+    vector<int64_t> sub(nsn, 1);
+    for (int64_t t = 0; t < nsn; ++t)
+      if (s->sn_par[t] >= 0) sub[s->sn_par[t]] += sub[t];
+    for (int64_t t = 0; t < nsn; ++t) {
+      if (top[t]) continue;
+      int64_t p = s->sn_par[t];
+      if (p >= 0 && !top[p]) continue;
+      vector<int32_t> seq;
+      for (int64_t u = t - sub[t] + 1; u <= t; ++u) { seq.push_back((int32_t)u); task_of[u] = (int64_t)tasks.size(); }
+      tasks.push_back(seq);
+      tlevel.push_back(0);
+    }
+    // top fronts: a top front with exactly one top child joins that child's task
+    vector<int64_t> ntopkids(nsn, 0), onlykid(nsn, -1);
+    for (int64_t t = 0; t < nsn; ++t)
+      if (top[t] && s->sn_par[t] >= 0) { ntopkids[s->sn_par[t]]++; onlykid[s->sn_par[t]] = t; }
+    for (int64_t t = 0; t < nsn; ++t) {
+      if (!top[t]) continue;
+      int64_t lvl = 1;
+      for (int64_t q = s->ch_ptr[t]; q < s->ch_ptr[t + 1]; ++q) {
+        int64_t c = s->ch[q];
+        if (top[c]) lvl = std::max(lvl, tlevel[task_of[c]] + 1);
+      }
+      if (ntopkids[t] == 1) {
+        int64_t tk = task_of[onlykid[t]];
+        tasks[tk].push_back((int32_t)t);
+        task_of[t] = tk;
+        // level stays that of the chain's first front
+      } else {
+        task_of[t] = (int64_t)tasks.size();
+        tasks.push_back({(int32_t)t});
+        tlevel.push_back(lvl);
+      }
+    }
+    // a chain task's level must exceed the levels of all tasks it depends on
+    bool changed = true;
+    while (changed) {
+      changed = false;
+      for (int64_t t = 0; t < nsn; ++t) {
+        int64_t tk = task_of[t];
+        for (int64_t q = s->ch_ptr[t]; q < s->ch_ptr[t + 1]; ++q) {
+          int64_t tc = task_of[s->ch[q]];
+          if (tc != tk && tlevel[tk] <= tlevel[tc]) { tlevel[tk] = tlevel[tc] + 1; changed = true; }
+        }
+      }
+    }
+    int64_t nlev = 0;
+    for (int64_t l : tlevel) nlev = std::max(nlev, l + 1);
+    vector<vector<int64_t>> bylev(nlev);
+    for (size_t q = 0; q < tasks.size(); ++q) bylev[tlevel[q]].push_back((int64_t)q);
+    s->task_ptr.assign(1, 0);
+    s->task_fronts.clear();
+    s->lvl_ptr.assign(1, 0);
+    for (int64_t l = 0; l < nlev; ++l) {
+      for (int64_t q : bylev[l]) {
+        for (int32_t f : tasks[q]) s->task_fronts.push_back(f);
+        s->task_ptr.push_back((int32_t)s->task_fronts.size());
+      }
+      s->lvl_ptr.push_back((int32_t)(s->task_ptr.size() - 1));
+    }
+  }
+  return CHD_OK;
+}

@@ -1,0 +1,209 @@
+"""GPU parity: every operation of the library against the FP64 oracle.
+
+Inputs are seeded and synthetic; the pattern V is produced by chd_analyze
+and validated against the oracle's own fill before any value is drawn on it.
+Tolerance (relative Frobenius error in the symmetric norm, off-diagonals
+counted twice): 1e-10 on well-conditioned inputs, 1e-8 at condition ~1e6.
+"""
+import numpy as np
+import pytest
+
+from oracle import dense as OD
+from oracle import symbolic as OS
+import workloads as W
+from tests.helpers import lib
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def torch():
+    import torch as t
+    return t
+
+
+class Case:
+    def __init__(self, pattern, ordering="natural", perm=None, relax=0, seed=0, x=None):
+        self.B = lib()
+        self.sym = self.B.Symbolic(*pattern, ordering=ordering, perm=perm, relax=relax)
+        s = self.sym
+        self.n, self.cp, self.ri = s.n, s.colptr, s.rowind
+        # V must be filled (Eq. (e-filled)) and contain the permuted input pattern
+        I = [s.rowind[s.colptr[k] + 1:s.colptr[k + 1]] for k in range(s.n)]
+        assert OS.is_filled(s.n, I)
+        rng = np.random.default_rng(seed)
+        self.x = W.diag_dominant(s.n, s.colptr, s.rowind, rng) if x is None else x(s, rng)
+        self.rng = rng
+
+    def dev(self, a):
+        t = torch()
+        return t.as_tensor(np.ascontiguousarray(a), dtype=t.float64, device="cuda")
+
+    def host(self, t_):
+        torch().cuda.synchronize()
+        return t_.cpu().numpy()
+
+    def err(self, a, ref):
+        return OD.rel_err(self.n, self.cp, self.ri, a, ref)
+
+
+def small_cases():
+    return {
+        "band200_w8": lambda: Case(W.band(200, 8), seed=0),
+        "band40_w1": lambda: Case(W.band(40, 1), seed=1),
+        "arrow60_w7": lambda: Case(W.arrow(60, 7), seed=2),
+        "grid14_nd": lambda: Case(W.grid2d(14, 14), ordering="user",
+                                  perm=W.nested_dissection((14, 14), leaf=6), seed=3),
+        "grid3d_5": lambda: Case(W.grid3d(5, 5, 5), ordering="user",
+                                 perm=W.nested_dissection((5, 5, 5), leaf=8), seed=4),
+        "er300_mindeg_relax16": lambda: Case(W.erdos_renyi(300, 0.02, np.random.default_rng(5)),
+                                             ordering="mindeg", relax=16, seed=5),
+        "dense70": lambda: Case(W.band(70, 69), seed=6),
+        "diag30": lambda: Case(W.band(30, 0), seed=7),
+        "wide_front": lambda: Case(W.arrow(200, 120), seed=8),
+    }
+
+
+CASES = small_cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_factor_logdet(name):
+    c = CASES[name]()
+    f = c.sym.factor(c.dev(c.x))
+    ld = f.logdet()
+    assert f.status() == 0
+    l, d = f.export()
+    lv, dv, _ = OD.factor(c.n, c.cp, c.ri, c.x)
+    want_ld = OD.logdet(c.n, c.cp, c.ri, c.x)
+    assert abs(ld - want_ld) <= TOL * max(1.0, abs(want_ld))
+    np.testing.assert_allclose(c.host(d), dv, rtol=1e-11)
+    assert c.err(c.host(l), lv) < TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_gradient(name):
+    c = CASES[name]()
+    f = c.sym.factor(c.dev(c.x))
+    g = c.host(f.gradient())
+    assert c.err(g, OD.gradient(c.n, c.cp, c.ri, c.x)) < TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_hessian(name):
+    c = CASES[name]()
+    f = c.sym.factor(c.dev(c.x))
+    ys = W.uniform_sym(c.n, c.cp, c.ri, c.rng, count=3)
+    t = c.host(f.hessian(c.dev(ys)))
+    want = OD.hessian(c.n, c.cp, c.ri, c.x, list(ys))
+    for i in range(3):
+        assert c.err(t[i], want[i]) < TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_inverse_hessian(name):
+    c = CASES[name]()
+    f = c.sym.factor(c.dev(c.x))
+    ts = W.uniform_sym(c.n, c.cp, c.ri, c.rng, count=2)
+    y = c.host(f.inv_hessian(c.dev(ts)))
+    Z = OD.inverse(c.n, c.cp, c.ri, c.x)
+    for i in range(2):
+        if len(c.ri) <= 2500:
+            want = OD.inv_hessian_dense(c.n, c.cp, c.ri, c.x, [ts[i]], Z=Z)[0]
+        else:
+            I, parent = OS.fill(c.n, OS.columns_from_csc(c.n, c.cp, c.ri))
+            cl, seps = OS.cliques_and_separators(I, parent)
+            want = OD.inv_hessian_cliquesum(c.n, c.cp, c.ri, c.x, ts[i], cl, seps, S=Z)
+        assert c.err(y[i], want) < TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_completion(name):
+    c = CASES[name]()
+    G = c.rng.standard_normal((c.n, 10))
+    s = W.projected_gram(c.n, c.cp, c.ri, G, 0.5)
+    fx, fstar = c.sym.complete(c.dev(s))
+    assert fx.status() == 0
+    I, parent = OS.fill(c.n, OS.columns_from_csc(c.n, c.cp, c.ri))
+    cl, seps = OS.cliques_and_separators(I, parent)
+    xh = OD.completion_cliquesum(c.n, c.cp, c.ri, s, cl, seps)
+    lv, dv, _ = OD.factor(c.n, c.cp, c.ri, xh)
+    l, d = fx.export()
+    np.testing.assert_allclose(c.host(d), dv, rtol=1e-10)
+    assert c.err(c.host(l), lv) < TOL
+    want_fs = OD.dual_barrier(c.n, c.cp, c.ri, xh)
+    assert abs(fstar - want_fs) <= TOL * max(1.0, abs(want_fs))
+    # the completion factor serves the dual barrier's Hessian (Eq. (e-legendre-rels)):
+    # grad^2 f_*(S)[T] = H_{Xhat}^{-1}(T)
+    t = W.uniform_sym(c.n, c.cp, c.ri, c.rng, count=1)
+    yh = c.host(fx.inv_hessian(c.dev(t)))[0]
+    Sd = OD.to_dense(c.n, c.cp, c.ri, s)
+    want = OD.inv_hessian_cliquesum(c.n, c.cp, c.ri, xh, t[0], cl, seps, S=Sd)
+    assert c.err(yh, want) < 1e-9
+
+
+def test_planted_condition_1e6():
+    def planted(s, rng):
+        x, _, _ = W.planted_factor(s.n, s.colptr, s.rowind, rng, dmin=1e-6, dmax=1.0)
+        return x
+    c = Case(W.band(150, 6), x=planted, seed=11)
+    X = OD.to_dense(c.n, c.cp, c.ri, c.x)
+    kappa = np.linalg.cond(X)
+    assert kappa > 1e5
+    f = c.sym.factor(c.dev(c.x))
+    l, d = f.export()
+    lv, dv, _ = OD.factor(c.n, c.cp, c.ri, c.x)
+    assert c.err(c.host(l), lv) < 1e-8
+    g = c.host(f.gradient())
+    assert c.err(g, OD.gradient(c.n, c.cp, c.ri, c.x)) < 1e-8
+    ys = W.uniform_sym(c.n, c.cp, c.ri, c.rng, count=2)
+    t = c.host(f.hessian(c.dev(ys)))
+    want = OD.hessian(c.n, c.cp, c.ri, c.x, list(ys))
+    for i in range(2):
+        assert c.err(t[i], want[i]) < 1e-8
+
+
+def test_not_positive_definite_is_reported():
+    B = lib()
+    c = Case(W.band(50, 3), seed=12)
+    x = c.x.copy()
+    x[c.cp[20]] = -5.0  # a negative diagonal entry: X is indefinite
+    f = c.sym.factor(c.dev(x))
+    assert f.status() == B.CHD_ERR_NOT_PD
+    rc, snode, col = f.error_detail()
+    assert rc == B.CHD_ERR_NOT_PD and 0 <= col <= 20
+
+
+def test_not_completable_is_reported():
+    B = lib()
+    c = Case(W.band(40, 2), seed=13)
+    s = -np.abs(W.diag_dominant(c.n, c.cp, c.ri, c.rng))  # negative diagonal: no PSD completion
+    try:
+        c.sym.complete(c.dev(s))
+        raise AssertionError("expected CHD_ERR_NOT_COMPLETABLE")
+    except B.ChdError as e:
+        assert e.code == B.CHD_ERR_NOT_COMPLETABLE
+
+
+def test_batched_rhs_strides_and_refactor():
+    c = CASES["grid14_nd"]()
+    f = c.sym.factor(c.dev(c.x))
+    t_ = torch()
+    m = 5
+    ld = c.sym.nnz + 7
+    ybuf = t_.zeros((m, ld), dtype=t_.float64, device="cuda")
+    ys = W.uniform_sym(c.n, c.cp, c.ri, c.rng, count=m)
+    ybuf[:, :c.sym.nnz] = c.dev(ys)
+    tbuf = t_.full((m, ld), 7.0, dtype=t_.float64, device="cuda")
+    c.B.chd_hessian(f.handle, ybuf, tbuf, c.sym.nnz)
+    out = c.host(tbuf)
+    want = OD.hessian(c.n, c.cp, c.ri, c.x, list(ys))
+    for i in range(m):
+        assert c.err(out[i, :c.sym.nnz], want[i]) < TOL
+        assert np.all(out[i, c.sym.nnz:] == 7.0)  # padding untouched
+    # refactor with new values invalidates cached blocks
+    x2 = W.diag_dominant(c.n, c.cp, c.ri, np.random.default_rng(99))
+    f.refactor(c.dev(x2))
+    g = c.host(f.gradient())
+    assert c.err(g, OD.gradient(c.n, c.cp, c.ri, x2)) < TOL

@@ -1,0 +1,122 @@
+"""The library's host symbolic phase (chd_analyze) against the paper's worked
+example and the oracle's symbolic routines.  Integer results: bit-exact."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import symbolic as OS
+import workloads as W
+from tests.helpers import lib, product_structure
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def fig1():
+    pairs = np.loadtxt(os.path.join(GOLD, "fig1_pattern.txt"), dtype=np.int64, comments="#")
+    return W.lower_csc_from_pairs(17, pairs[:, 0], pairs[:, 1])
+
+
+@pytest.mark.parametrize("tie,key", [(True, "partition_1"), (False, "partition_2")])
+def test_fig1_supernodes_and_clique_tree(tie, key):
+    B = lib()
+    g = json.load(open(os.path.join(GOLD, "fig1_symbolic.json")))[key]
+    sym = B.Symbolic(*fig1(), tie_last=tie)
+    assert sym.nnz == len(fig1()[2])  # filled already: no fill
+    st = product_structure(B, sym)
+    # map representative (paper label) -> (N, A)
+    got = {}
+    for N, A, par in st:
+        got[str(min(N) + 1)] = ([v + 1 for v in N], [v + 1 for v in A], par)
+    assert {k: v[0] for k, v in got.items()} == g["N"]
+    assert {k: v[1] for k, v in got.items()} == g["A"]
+    rep_of_index = [str(min(N) + 1) for N, A, par in st]
+    par = {rep_of_index[i]: (int(rep_of_index[p]) if p >= 0 else 0) for i, (_, _, p) in enumerate(st)}
+    assert par == g["par"]
+
+
+def _oracle_filled_pairs(pattern, perm):
+    n, cp, ri = W.permute(pattern, perm)
+    I, _ = OS.fill(n, OS.columns_from_csc(n, cp, ri))
+    return {(int(r), k) for k in range(n) for r in I[k]} | {(k, k) for k in range(n)}
+
+
+def _product_pairs(sym):
+    cols = np.repeat(np.arange(sym.n), np.diff(sym.colptr))
+    return set(zip(sym.rowind.astype(int).tolist(), cols.tolist()))
+
+
+CASES = {
+    "band": (lambda: W.band(60, 5), "natural", None),
+    "arrow": (lambda: W.arrow(50, 6), "natural", None),
+    "grid_nd": (lambda: W.grid2d(12, 12), "user", lambda: W.nested_dissection((12, 12), leaf=6)),
+    "grid3d_nd": (lambda: W.grid3d(6, 6, 6), "user", lambda: W.nested_dissection((6, 6, 6), leaf=8)),
+    "er_mindeg": (lambda: W.erdos_renyi(300, 0.02, np.random.default_rng(3)), "mindeg", None),
+    "er_natural": (lambda: W.erdos_renyi(120, 0.03, np.random.default_rng(4)), "natural", None),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fill_and_supernodes_match_oracle(name):
+    B = lib()
+    mk, ordering, permf = CASES[name]
+    pattern = mk()
+    perm_in = permf() if permf else None
+    sym = B.Symbolic(*pattern, ordering=ordering, perm=perm_in)
+    perm = sym.perm
+    assert sorted(perm.tolist()) == list(range(sym.n))
+    # V in the analysed order equals the oracle's filled pattern for that order
+    assert _product_pairs(sym) == _oracle_filled_pairs(pattern, perm)
+    # supernodes: contiguous, and identical to Algorithm 6.1 (tie: last child) run
+    # by the oracle on the analysed order
+    n = sym.n
+    p2 = W.permute(pattern, perm)
+    I, parent = OS.fill(n, OS.columns_from_csc(*p2))
+    N, A, par, snode_of = OS.clique_tree_alg61(I, parent, tie="last")
+    sp, spar, rp, rows = sym.supernodes()
+    got = []
+    for k in range(len(sp) - 1):
+        nk = int(sp[k + 1] - sp[k])
+        J = rows[rp[k]:rp[k + 1]]
+        assert list(J[:nk]) == list(range(sp[k], sp[k + 1]))
+        got.append((tuple(int(v) for v in J[:nk]), tuple(int(v) for v in J[nk:])))
+    want = sorted((tuple(N[k]), tuple(A[k])) for k in N)
+    assert sorted(got) == want
+    # clique tree parents: the supernode containing min A_k
+    owner = np.empty(n, dtype=np.int64)
+    for k in range(len(sp) - 1):
+        owner[sp[k]:sp[k + 1]] = k
+    for k in range(len(sp) - 1):
+        nk = int(sp[k + 1] - sp[k])
+        J = rows[rp[k]:rp[k + 1]]
+        assert spar[k] == (owner[J[nk]] if len(J) > nk else -1)
+        if spar[k] >= 0:
+            assert spar[k] > k  # postorder numbering: parents after children
+
+
+@pytest.mark.parametrize("relax", [4, 16, 64])
+def test_relaxed_supernodes_only_add_entries(relax):
+    B = lib()
+    pattern = W.erdos_renyi(400, 0.01, np.random.default_rng(9))
+    s0 = B.Symbolic(*pattern, ordering="mindeg", relax=0)
+    s1 = B.Symbolic(*pattern, ordering="mindeg", relax=relax)
+    assert (s0.perm == s1.perm).all()
+    p0, p1 = _product_pairs(s0), _product_pairs(s1)
+    assert p0 <= p1
+    assert s1.nsuper <= s0.nsuper
+    # the enlarged pattern is still filled (Eq. (e-filled))
+    n = s1.n
+    I = [np.array(sorted(r for (r, c) in p1 if c == k and r > k)) for k in range(n)]
+    assert OS.is_filled(n, I)
+
+
+def test_flop_counts_band_scaling():
+    # §4.3.1: Cholesky and projected inverse cost O(n w^2) on band patterns
+    B = lib()
+    f1 = B.Symbolic(*W.band(2000, 10)).flops()
+    f2 = B.Symbolic(*W.band(4000, 10)).flops()
+    f3 = B.Symbolic(*W.band(2000, 20)).flops()
+    for op in ("factor", "gradient", "hessian"):
+        assert abs(f2[op] / f1[op] - 2.0) < 0.02
+        assert 3.4 < f3[op] / f1[op] < 4.6
