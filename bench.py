@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: factor, log det, gradient, Hessian products,
+inverse-Hessian products and completion on one synthetic chordal workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload er5000|band200|grid150]
+
+One step = one pass of every operation over one batch of inputs resident in
+HBM: refactor(X), log det, gradient, Hessian of m right-hand sides, inverse
+Hessian of m right-hand sides, completion of S with f_*.  The metric is
+Hessian evaluations per second (m per step) over the whole job; FP64 frontal
+TFLOP/s of the dominant operation (the Hessian) is reported against the
+measured FP64 FMA throughput of the device.  Multi-GPU runs are independent
+replicas (the path has no exchange step); rank 0 prints one JSON line.
+
+``--impl reference`` times the CPU oracle (dense definitions, numpy/LAPACK on
+all host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+os.environ.setdefault("OPENBLAS_NUM_THREADS", os.environ["OMP_NUM_THREADS"])
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "Hessian evals/s"
+UNIT = "evals/s"
+
+
+def make_workload(name):
+    """Pattern, analysis options, right-hand-side count and value recipe."""
+    if name == "er5000":
+        pattern = W.erdos_renyi(5000, 0.001, np.random.default_rng(1))
+        return dict(name=name, pattern=pattern, opts=dict(ordering="mindeg", relax=16), m=8, seed=1,
+                    gram=(50, 0.1),
+                    desc="Erdos-Renyi n=5000 p=0.001, minimum-degree order, relaxed supernodes "
+                         "(<=16 zeros per merge), X diag-dominant, 8 Y uniform[-1,1], "
+                         "S=P(GG^T+0.1I) G 5000x50")
+    if name == "band200":
+        return dict(name=name, pattern=W.band(200, 8), opts=dict(), m=1, seed=0, gram=(20, 1.0),
+                    desc="band n=200 half-bandwidth 8, natural order, X diag-dominant, 1 Y, "
+                         "S=P(GG^T+I) G 200x20")
+    if name == "grid150":
+        return dict(name=name, pattern=W.grid2d(150, 150),
+                    opts=dict(perm=W.nested_dissection((150, 150), leaf=8)), m=64, seed=2,
+                    gram=(20, 0.5),
+                    desc="5-point grid 150x150 (n=22500), geometric nested dissection, "
+                         "X diag-dominant, 64 Y, S=P(GG^T+0.5I) G 22500x20")
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_values(wl, n, cp, ri):
+    rng = np.random.default_rng(wl["seed"])
+    x = W.diag_dominant(n, cp, ri, rng)
+    ys = W.uniform_sym(n, cp, ri, rng, count=wl["m"])
+    k, c = wl["gram"]
+    s = W.projected_gram(n, cp, ri, rng.standard_normal((n, k)), c)
+    return x, ys, s
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_hessian_sample(wl, n, cp, ri, x, ys, count):
+    """Dense oracle: Z = X^{-1} once, then T = P(Z Y Z) for `count` of the Y's.
+    Returns (t_inverse, t_per_eval)."""
+    from oracle import dense as OD
+    t0 = time.perf_counter()
+    Z = OD.inverse(n, cp, ri, x)
+    t1 = time.perf_counter()
+    OD.hessian(n, cp, ri, x, list(ys[:count]), Z=Z)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / count
+
+
+def run_reference(args, wl):
+    from paper_1203_2742_gb300 import build as _b  # noqa: F401  (no GPU use)
+    # analyse with the library's host symbolic phase only when it is built;
+    # else use the oracle's own fill of the same ordering (natural/user orders)
+    n, cp, ri = analysed_pattern_host(wl)
+    x, ys, _ = workload_values(wl, n, cp, ri)
+    m = wl["m"]
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample_evals = min(2, m)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        tz, te = oracle_hessian_sample(wl, n, cp, ri, x, ys, sample_evals)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append((dt, tz, te))
+    step = float(np.mean([t[0] for t in times]))
+    tz = float(np.mean([t[1] for t in times]))
+    te = float(np.mean([t[2] for t in times]))
+    value = m / (tz + m * te)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": wl["desc"], "global_batch": m, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"dense oracle: X^-1 then P(X^-1 Y X^-1) for {sample_evals} of the "
+                                   f"{m} Y per step; value = {m}/(t_inverse + {m}*t_eval)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def analysed_pattern_host(wl):
+    """The analysed (filled, permuted) pattern from the library's host phase."""
+    from paper_1203_2742_gb300 import build
+    build.build()
+    from paper_1203_2742_gb300 import binding as B
+    sym = B.Symbolic(*wl["pattern"], **wl["opts"])
+    return sym.n, sym.colptr, sym.rowind
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, wl, rank, world, local_rank):
+    import torch
+    from paper_1203_2742_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        build.build()
+    from paper_1203_2742_gb300 import binding as B
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    sym = B.Symbolic(*wl["pattern"], **wl["opts"])
+    analyze_ms = (time.perf_counter() - t0) * 1e3
+    n, cp, ri, nnz = sym.n, sym.colptr, sym.rowind, sym.nnz
+    m = wl["m"]
+    x, ys, s = workload_values(wl, n, cp, ri)
+    fl = sym.flops()
+
+    # inputs resident in HBM
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    X, Y, S = d(x), d(ys), d(s)
+    G = torch.empty(nnz, dtype=torch.float64, device=dev)
+    T = torch.empty((m, nnz), dtype=torch.float64, device=dev)
+    YI = torch.empty((m, nnz), dtype=torch.float64, device=dev)
+    fac = sym.factor(X)
+    fx, _ = sym.complete(S)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)  # > L2
+
+    results = {}
+
+    def step():
+        fac.refactor(X)
+        results["logdet"] = fac.logdet()
+        fac.gradient(out=G)
+        fac.hessian(Y, out=T)
+        fac.inv_hessian(T, out=YI)
+        results["fstar"] = fx.recomplete(S)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed between steps ----
+    sampler = ClockSampler(local_rank)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = B.chd_kernel_launches()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = B.chd_kernel_launches() - launches0
+    clocks = sampler.stop()
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dev_ms = float(tt.item())
+        dist.barrier()
+    ms_per_step = dev_ms / args.steps
+    value = world * m * args.steps / (dev_ms * 1e-3)
+
+    # ---- per-operation breakdown and the dominant kernel's roofline ----
+    def time_op(fn, reps):
+        es = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        tot = 0.0
+        for a, b in es:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in es) / reps
+
+    reps = max(1, min(args.steps, 3))
+    ops_ms = {
+        "factor": time_op(lambda: fac.refactor(X), reps),
+        "gradient": time_op(lambda: fac.gradient(out=G), reps),
+        "hessian": time_op(lambda: fac.hessian(Y, out=T), reps),
+        "inv_hessian": time_op(lambda: fac.inv_hessian(T, out=YI), reps),
+        "completion": time_op(lambda: fx.recomplete(S, want_fstar=False), reps),
+    }
+    fp64_peak = B.chd_probe_fp64_peak() / 1e3  # TFLOP/s
+    hess_flops = fl["hessian"] * m
+    achieved = hess_flops / (ops_ms["hessian"] * 1e-3) / 1e12
+    step_flops = fl["factor"] + fl["gradient"] + m * (fl["hessian"] + fl["inv_hessian"]) + fl["completion"]
+
+    # ---- end to end through the C ABI with host buffers ----
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64).pin_memory()
+    hX, hY, hS = pin(x), pin(ys), pin(s)
+    hG = torch.empty(nnz, dtype=torch.float64).pin_memory()
+    hT = torch.empty((m, nnz), dtype=torch.float64).pin_memory()
+    hYI = torch.empty((m, nnz), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        X.copy_(hX, non_blocking=True)
+        Y.copy_(hY, non_blocking=True)
+        S.copy_(hS, non_blocking=True)
+        step()
+        hG.copy_(G, non_blocking=True)
+        hT.copy_(T, non_blocking=True)
+        hYI.copy_(YI, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in eev:
+        flush.zero_()
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in eev)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = world * m * args.steps / (e2e_ms * 1e-3)
+    h2d = 8 * (x.size + ys.size + s.size)
+    d2h = 8 * (nnz + 2 * m * nnz)
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        sample = min(2, m)
+        tz, te = oracle_hessian_sample(wl, n, cp, ri, x, ys, sample)
+        cpu = {"value": m / (tz + m * te), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"dense oracle X^-1 ({tz:.2f} s) then P(X^-1 Y X^-1) for {sample} of the {m} Y "
+                         f"({te:.2f} s each); value = {m}/(t_inverse + {m}*t_eval)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "nnz_filled": nnz, "supernodes": sym.nsuper,
+                       "rhs_per_step": m, "global_batch": world * m,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "roofline": {"bound": "alu", "kernel": "Hessian products (k_hess_up + k_hess_down level launches)",
+                         "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp64_peak, "traffic": None,
+                         "peak_source": "measured FP64 DFMA throughput (chd_probe_fp64_peak), same run"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "ops_ms": {k: round(v, 4) for k, v in ops_ms.items()},
+            "step_tflops_fp64": step_flops / (ms_per_step * 1e-3) / 1e12,
+            "analyze_ms": analyze_ms,
+            "wall_s": wall,
+            "logdet": results.get("logdet"), "fstar": results.get("fstar"),
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="er5000", choices=["er5000", "band200", "grid150"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = make_workload(args.workload)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, wl)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, wl, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -73,10 +73,14 @@ typedef struct {
                               to V; 0 = fundamental partition of Algorithm 6.1 */
   int32_t tie_last;        /* Algorithm 6.1 step 1 tie-break: 1 = child with the largest
                               index, 0 = smallest */
-  int32_t reserved[8];
+  int32_t big_rows;        /* a front with |J_k| >= big_rows (or |N_k| >= big_cols) is
+                              processed by the multi-CTA dense tier; 0 = default 320 */
+  int32_t big_cols;        /* 0 = default 160 */
+  int32_t reserved[6];
 } chd_opts;
 
-/* Fill `opts` with the defaults: natural order, relax 0, tie_last 1. */
+/* Fill `opts` with the defaults: natural order, relax 0, tie_last 1, default
+   dense-tier thresholds. */
 void chd_opts_default(chd_opts* opts);
 
 /*
@@ -189,6 +193,13 @@ chd_status chd_complete(chd_symbolic* sym, const double* s_dev, void* stream,
                         chd_factor** xhat, double* fstar);
 
 /*
+ * Completion into an existing factor object (same pattern), reusing its
+ * device memory: the object is overwritten with the factor of X-hat for
+ * the new S.  Same contract as chd_complete otherwise.
+ */
+chd_status chd_recomplete(chd_factor* xhat, const double* s_dev, void* stream, double* fstar);
+
+/*
  * Export the unique scalar factorisation X = L D L^T (§2, §3.1): l_dev gets
  * the nnz_filled entries of L on V (unit diagonal), d_dev the n pivots D_ii.
  */
@@ -209,6 +220,15 @@ chd_status chd_error_detail(chd_factor* fac, int64_t* supernode, int64_t* column
 /* Number of kernels the library has launched since the process started
    (host counter, for launch accounting). */
 int64_t chd_kernel_launches(void);
+
+/*
+ * Measurement utility (not an operation of the paper): FP64 fused
+ * multiply-add throughput of the current device in GFLOP/s, from a kernel
+ * of independent DFMA chains on every SM timed with CUDA events on
+ * `stream` (synchronises).  It is the denominator of the FP64 roofline of
+ * the front kernels.  Allocates and frees one small device buffer.
+ */
+chd_status chd_probe_fp64_peak(void* stream, double* gflops);
 
 void chd_factor_free(chd_factor* fac);
 

@@ -39,7 +39,8 @@ class ChdError(RuntimeError):
 
 class chd_opts(C.Structure):
     _fields_ = [("ordering", C.c_int32), ("user_perm", C.POINTER(C.c_int64)), ("relax", C.c_int32),
-                ("tie_last", C.c_int32), ("reserved", C.c_int32 * 8)]
+                ("tie_last", C.c_int32), ("big_rows", C.c_int32), ("big_cols", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 _p = C.c_void_p
@@ -60,16 +61,19 @@ _lib.chd_gradient.argtypes = [_p, _p, _p]
 _lib.chd_hessian.argtypes = [_p, C.c_int, _p, _i64, _p, _i64, _p]
 _lib.chd_inv_hessian.argtypes = [_p, C.c_int, _p, _i64, _p, _i64, _p]
 _lib.chd_complete.argtypes = [_p, _p, _p, C.POINTER(_p), C.POINTER(C.c_double)]
+_lib.chd_recomplete.argtypes = [_p, _p, _p, C.POINTER(C.c_double)]
 _lib.chd_factor_export.argtypes = [_p, _p, _p, _p]
 _lib.chd_status_get.argtypes = [_p]
 _lib.chd_error_detail.argtypes = [_p, C.POINTER(_i64), C.POINTER(_i64)]
 _lib.chd_kernel_launches.argtypes = []
 _lib.chd_kernel_launches.restype = _i64
+_lib.chd_probe_fp64_peak.argtypes = [_p, C.POINTER(C.c_double)]
+_lib.chd_probe_fp64_peak.restype = C.c_int
 _lib.chd_factor_free.argtypes = [_p]
 _lib.chd_factor_free.restype = None
 for _f in ("chd_analyze", "chd_symbolic_info", "chd_symbolic_supernodes", "chd_symbolic_flops",
            "chd_factor_new", "chd_refactor", "chd_logdet", "chd_gradient", "chd_hessian",
-           "chd_inv_hessian", "chd_complete", "chd_factor_export", "chd_status_get",
+           "chd_inv_hessian", "chd_complete", "chd_recomplete", "chd_factor_export", "chd_status_get",
            "chd_error_detail"):
     getattr(_lib, _f).restype = C.c_int
 
@@ -108,7 +112,8 @@ def _dptr(t, what, nnz=None, rows=None):
 # C-named entry points
 # ---------------------------------------------------------------------------
 
-def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True):
+def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0,
+                big_cols=0):
     colptr = np.ascontiguousarray(colptr, dtype=np.int64)
     rowind = np.ascontiguousarray(rowind, dtype=np.int32)
     o = chd_opts()
@@ -121,6 +126,8 @@ def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_l
         o.ordering = ORDERINGS["user"]
     o.relax = int(relax)
     o.tie_last = 1 if tie_last else 0
+    o.big_rows = int(big_rows)
+    o.big_cols = int(big_cols)
     out = _p()
     rc = _lib.chd_analyze(int(n), colptr.ctypes.data, rowind.ctypes.data, C.byref(o), C.byref(out))
     _check(rc, "chd_analyze")
@@ -215,6 +222,13 @@ def chd_complete(sym, s, nnz, stream=None, want_fstar=True):
     return out, (f.value if want_fstar else None)
 
 
+def chd_recomplete(fac, s, nnz, stream=None, want_fstar=True):
+    f = C.c_double()
+    rc = _lib.chd_recomplete(fac, _dptr(s, "s", nnz), _stream_ptr(stream), C.byref(f) if want_fstar else None)
+    _check(rc, "chd_recomplete")
+    return f.value if want_fstar else None
+
+
 def chd_factor_export(fac, l, d, stream=None):
     _check(_lib.chd_factor_export(fac, _dptr(l, "l"), _dptr(d, "d"), _stream_ptr(stream)),
            "chd_factor_export")
@@ -234,6 +248,12 @@ def chd_kernel_launches():
     return int(_lib.chd_kernel_launches())
 
 
+def chd_probe_fp64_peak(stream=None):
+    v = C.c_double()
+    _check(_lib.chd_probe_fp64_peak(_stream_ptr(stream), C.byref(v)), "chd_probe_fp64_peak")
+    return v.value
+
+
 def chd_factor_free(fac):
     _lib.chd_factor_free(fac)
 
@@ -245,9 +265,10 @@ def chd_factor_free(fac):
 class Symbolic:
     """Owner of a ``chd_symbolic``: the analysed pattern and its clique tree."""
 
-    def __init__(self, n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True):
+    def __init__(self, n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True,
+                 big_rows=0, big_cols=0):
         self._h = chd_analyze(n, colptr, rowind, ordering=ordering, perm=perm, relax=relax,
-                              tie_last=tie_last)
+                              tie_last=tie_last, big_rows=big_rows, big_cols=big_cols)
         info = chd_symbolic_info(self._h)
         self.n = info["n"]
         self.nnz = info["nnz"]
@@ -296,6 +317,9 @@ class Factor:
 
     def logdet(self):
         return chd_logdet(self._h)
+
+    def recomplete(self, s, stream=None, want_fstar=True):
+        return chd_recomplete(self._h, s, self.sym.nnz, stream, want_fstar)
 
     def gradient(self, out=None, stream=None):
         import torch

@@ -1,0 +1,668 @@
+// Dense tier: fronts too large for one CTA are processed by a host-issued
+// sequence of multi-CTA kernels, each batched over the right-hand sides
+// (blockIdx.z).  The per-front formulas are those of kernels.cu (supernodal
+// Algorithms 7.1-7.3 and the block forms of Algorithms 5.1 and 5.2); only
+// the distribution of the work differs: every dense product is a tiled FP64
+// GEMM over the whole GPU, Cholesky factorisations and triangular solves are
+// blocked right-looking (panel kernel + trailing GEMM).
+//
+// Andersen, Dahl, Vandenberghe, "Logarithmic barriers for sparse matrix cones".
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "chd_internal.h"
+#include "front_views.cuh"
+
+namespace chd_launch {
+void count_launch();
+}
+
+namespace chd {
+namespace big {
+
+constexpr int BT = 256;  // threads per CTA
+constexpr int GT = 64;   // GEMM output tile
+constexpr int GK = 16;   // GEMM k-chunk
+constexpr int PW = 64;   // panel width of blocked factorisations / solves
+constexpr int RB = 64;   // rows per CTA in the panel solve
+
+template <class V>
+__device__ __forceinline__ V shifted(V v, int64_t off) {
+  v.p += off;
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// batched tiled GEMM: C = beta*C + alpha*A(MxK)*B(KxN), lower triangle only
+// if `lower`.  64x64 tiles, 4x4 outputs per thread, k-chunks of 16 in shared
+// memory.  beta == 0 never reads C.
+// ---------------------------------------------------------------------------
+template <class MA, class MB, class MC>
+__global__ void __launch_bounds__(BT) mk_gemm(int M, int N, int K, double alpha, MA A, int64_t sA, MB B,
+                                              int64_t sB, double beta, MC C, int64_t sC, int lower,
+                                              int tiles_n) {
+  const int tm = (blockIdx.x / tiles_n) * GT, tn = (blockIdx.x % tiles_n) * GT;
+  if (lower && tn >= tm + GT) return;
+  const int64_t z = blockIdx.z;
+  A.p += z * sA;
+  B.p += z * sB;
+  C.p += z * sC;
+  __shared__ double As[GK][GT];
+  __shared__ double Bs[GK][GT + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += GK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * BT;
+      const int r = e % GT, k = e / GT;
+      As[k][r] = (tm + r < M && k0 + k < K) ? A.at(tm + r, k0 + k) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * BT;
+      const int k = e % GK, c = e / GK;
+      Bs[k][c] = (k0 + k < K && tn + c < N) ? B.at(k0 + k, tn + c) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = tm + ty + 16 * i, c = tn + tx + 16 * j;
+      if (r < M && c < N && (!lower || r >= c)) {
+        double v = alpha * acc[i][j];
+        if (beta != 0.0) v = fma(beta, C.at(r, c), v);
+        C.at(r, c) = v;
+      }
+    }
+}
+
+template <class MA, class MB, class MC>
+void gemm(cudaStream_t st, int batch, int M, int N, int K, double alpha, MA A, int64_t sA, MB B, int64_t sB,
+          double beta, MC C, int64_t sC, bool lower) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  const int tm = (M + GT - 1) / GT, tn = (N + GT - 1) / GT;
+  mk_gemm<<<dim3(tm * tn, 1, batch), BT, 0, st>>>(M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower ? 1 : 0, tn);
+  chd_launch::count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky of one diagonal block (<= 64 x 64) in shared memory, one CTA.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(BT) mk_potrf_diag(double* F, int64_t ld, int j0, int jb, int64_t* st,
+                                                    int64_t code, int64_t snode, int64_t col0) {
+  __shared__ double Ls[PW][PW + 1];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < jb * jb; e += BT) {
+    const int r = e % jb, c = e / jb;
+    Ls[r][c] = r >= c ? F[(j0 + r) + (int64_t)(j0 + c) * ld] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < jb; ++j) {
+    if (tid == 0) {
+      double d = Ls[j][j];
+      if (!(d > 0.0)) {
+        record_error(st, code, snode, col0 < 0 ? -1 : col0 + j0 + j);
+        d = 1.0;
+      }
+      Ls[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    const double piv = Ls[j][j];
+    for (int i = j + 1 + tid; i < jb; i += BT) Ls[i][j] /= piv;
+    __syncthreads();
+    const int m = jb - j - 1;
+    for (int e = tid; e < m * m; e += BT) {
+      const int i = j + 1 + e % m, k = j + 1 + e / m;
+      if (i >= k) Ls[i][k] -= Ls[i][j] * Ls[k][j];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < jb * jb; e += BT) {
+    const int r = e % jb, c = e / jb;
+    if (r >= c) F[(j0 + r) + (int64_t)(j0 + c) * ld] = Ls[r][c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Panel triangular solve on rows [64*blockIdx.x, +64) of B (R rows), panel
+// columns [p0, p0+pb) against the diagonal block L[p0.., p0..] (lower):
+//   fwd = 1:  B_p := B_p L_pp^{-T}      fwd = 0:  B_p := B_p L_pp^{-1}
+// ---------------------------------------------------------------------------
+template <class MB>
+__global__ void __launch_bounds__(BT) mk_trsm_panel(int R, MB B, int64_t sB, int p0, int pb, const double* L,
+                                                    int64_t ld, int fwd) {
+  extern __shared__ double smem[];
+  double* Ls = smem;                   // PW x (PW+1), row-major
+  double* Bs = smem + PW * (PW + 1);   // RB x (PW+1), row-major
+  const int64_t z = blockIdx.z;
+  B.p += z * sB;
+  const int r0 = blockIdx.x * RB;
+  const int rc = min(RB, R - r0);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < pb * pb; e += BT) {
+    const int i = e % pb, j = e / pb;
+    Ls[i * (PW + 1) + j] = i >= j ? L[(p0 + i) + (int64_t)(p0 + j) * ld] : 0.0;
+  }
+  for (int e = tid; e < rc * pb; e += BT) {
+    const int r = e % rc, c = e / rc;
+    Bs[r * (PW + 1) + c] = B.at(r0 + r, p0 + c);
+  }
+  __syncthreads();
+  if (fwd) {
+    for (int c = 0; c < pb; ++c) {
+      const double inv = 1.0 / Ls[c * (PW + 1) + c];
+      for (int r = tid; r < rc; r += BT) Bs[r * (PW + 1) + c] *= inv;
+      __syncthreads();
+      const int m = pb - c - 1;
+      for (int e = tid; e < rc * m; e += BT) {
+        const int r = e % rc, t = c + 1 + e / rc;
+        Bs[r * (PW + 1) + t] -= Bs[r * (PW + 1) + c] * Ls[t * (PW + 1) + c];
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int c = pb - 1; c >= 0; --c) {
+      const double inv = 1.0 / Ls[c * (PW + 1) + c];
+      for (int r = tid; r < rc; r += BT) Bs[r * (PW + 1) + c] *= inv;
+      __syncthreads();
+      for (int e = tid; e < rc * c; e += BT) {
+        const int r = e % rc, t = e / rc;
+        Bs[r * (PW + 1) + t] -= Bs[r * (PW + 1) + c] * Ls[c * (PW + 1) + t];
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < rc * pb; e += BT) {
+    const int r = e % rc, c = e / rc;
+    B.at(r0 + r, p0 + c) = Bs[r * (PW + 1) + c];
+  }
+}
+constexpr size_t kPanelSmem = sizeof(double) * (PW * (PW + 1) + RB * (PW + 1));
+
+template <class MB>
+void panel_solve(cudaStream_t st, int batch, int R, MB B, int64_t sB, int p0, int pb, const double* L,
+                 int64_t ld, int fwd) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(mk_trsm_panel<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem);
+    attr = true;
+  }
+  mk_trsm_panel<MB><<<dim3((R + RB - 1) / RB, 1, batch), BT, kPanelSmem, st>>>(R, B, sB, p0, pb, L, ld, fwd);
+  chd_launch::count_launch();
+}
+
+// column shift of a view: Dn (col-major) and DnTW (transposed) layouts
+__host__ __device__ inline Dn colshift(Dn v, int c0) { v.p += (int64_t)c0 * v.ld; return v; }
+__host__ __device__ inline DnTW colshift(DnTW v, int c0) { v.p += c0; return v; }
+
+// B := B L^{-T} (R x n view B, n x n lower L), blocked forward.
+template <class MB>
+void trsm_rLT(cudaStream_t st, int batch, int R, int n, MB B, int64_t sB, const double* L, int64_t ld) {
+  if (R <= 0 || n <= 0) return;
+  for (int p0 = 0; p0 < n; p0 += PW) {
+    const int pb = std::min(PW, n - p0);
+    panel_solve(st, batch, R, B, sB, p0, pb, L, ld, 1);
+    const int rest = n - p0 - pb;
+    if (rest > 0)
+      gemm(st, batch, R, rest, pb, -1.0, colshift(B, p0), sB, DnT{L + (p0 + pb) + (int64_t)p0 * ld, ld}, 0,
+           1.0, colshift(B, p0 + pb), sB, false);
+  }
+}
+// B := B L^{-1}, blocked backward.
+template <class MB>
+void trsm_rL(cudaStream_t st, int batch, int R, int n, MB B, int64_t sB, const double* L, int64_t ld) {
+  if (R <= 0 || n <= 0) return;
+  const int np = (n + PW - 1) / PW;
+  for (int p = np - 1; p >= 0; --p) {
+    const int p0 = p * PW, pb = std::min(PW, n - p0);
+    panel_solve(st, batch, R, B, sB, p0, pb, L, ld, 0);
+    if (p0 > 0)
+      gemm(st, batch, R, p0, pb, -1.0, colshift(B, p0), sB, Dn{const_cast<double*>(L) + p0, ld}, 0, 1.0,
+           colshift(B, 0), sB, false);
+  }
+}
+
+// Partial Cholesky of the first n columns of the J x J matrix F (ld): F11 =
+// C C^T, F21 := F21 C^{-T}, F22 -= F21 F21^T (lower).  Not batched.
+void potrf_partial(cudaStream_t st, double* F, int64_t ld, int J, int n, int64_t* status, int64_t code,
+                   int64_t snode, int64_t col0) {
+  for (int j0 = 0; j0 < n; j0 += PW) {
+    const int jb = std::min(PW, n - j0);
+    mk_potrf_diag<<<1, BT, 0, st>>>(F, ld, j0, jb, status, code, snode, col0);
+    chd_launch::count_launch();
+    const int R = J - j0 - jb;
+    if (R > 0) {
+      Dn below{F + j0 + jb, ld};
+      panel_solve(st, 1, R, below, 0, j0, jb, F, ld, 1);
+      double* P = F + (j0 + jb) + (int64_t)j0 * ld;
+      gemm(st, 1, R, R, jb, -1.0, Dn{P, ld}, 0, DnT{P, ld}, 0, 1.0, Dn{F + (j0 + jb) + (int64_t)(j0 + jb) * ld, ld},
+           0, true);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// element-wise kernels (batched over blockIdx.z)
+// ---------------------------------------------------------------------------
+constexpr int EW = 4096;  // elements per CTA
+
+__global__ void __launch_bounds__(BT) mk_csc_to_front(double* F, int64_t sF, int J, int n, const double* csc,
+                                                      int64_t sC) {
+  F += blockIdx.z * sF;
+  csc += blockIdx.z * sC;
+  const int64_t tot = (int64_t)J * n;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % J), c = (int)(e / J);
+    if (r >= c) F[r + (int64_t)c * J] = csc[csc_off(J, r, c)];
+  }
+}
+// csc(r, c) = scale * F(r, c) for rows r_lo <= r < r_hi with r >= c, columns
+// c < n, of a front with J rows
+__global__ void __launch_bounds__(BT) mk_front_to_csc(double* csc, int64_t sC, const double* F, int64_t sF,
+                                                      int64_t ldF, int J, int n, int r_lo, int r_hi,
+                                                      double scale) {
+  F += blockIdx.z * sF;
+  csc += blockIdx.z * sC;
+  const int64_t tot = (int64_t)J * n;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % J), c = (int)(e / J);
+    if (r >= c && r >= r_lo && r < r_hi) csc[csc_off(J, r, c)] = scale * F[r + (int64_t)c * ldF];
+  }
+}
+// dst = alpha * src (+ beta * dst) on an R x C block, or its lower part
+__global__ void __launch_bounds__(BT) mk_copy(double* dst, int64_t sD, int64_t ldd, const double* src, int64_t sS,
+                                              int64_t lds, int R, int C, double alpha, double beta, int lower,
+                                              int transpose_fill) {
+  dst += blockIdx.z * sD;
+  if (src) src += blockIdx.z * sS;
+  const int64_t tot = (int64_t)R * C;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % R), c = (int)(e / R);
+    if (lower && r < c) continue;
+    double v = 0.0;
+    if (src) {
+      // transpose_fill: read the symmetric partner from the lower triangle
+      v = (transpose_fill && r < c) ? src[c + (int64_t)r * lds] : src[r + (int64_t)c * lds];
+    }
+    double* d = dst + r + (int64_t)c * ldd;
+    *d = beta != 0.0 ? fma(beta, *d, alpha * v) : alpha * v;
+  }
+}
+__global__ void __launch_bounds__(BT) mk_identity(double* dst, int64_t ld, int m) {
+  const int64_t tot = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    dst[r + (int64_t)c * ld] = r == c ? 1.0 : 0.0;
+  }
+}
+
+// Extend-add of the children's update blocks into front k, one CTA per 64x64
+// tile of the lower triangle; children are added in a fixed order, and the
+// child rows landing in a tile are a contiguous range because the relative
+// indices are increasing.
+__device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+__global__ void __launch_bounds__(BT) mk_extend_add(SymDev S, int k, double* ws, int64_t sws, int tiles) {
+  const int tm = (blockIdx.x / tiles) * GT, tn = (blockIdx.x % tiles) * GT;
+  if (tn > tm) return;
+  ws += blockIdx.z * sws;
+  const int Jp = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]);
+  double* F = ws + S.f_off[k];
+  for (int64_t q = S.ch_ptr[k]; q < S.ch_ptr[k + 1]; ++q) {
+    const int c = S.ch[q];
+    const int nc = (int)(S.sn_ptr[c + 1] - S.sn_ptr[c]);
+    const int Jc = (int)(S.rows_ptr[c + 1] - S.rows_ptr[c]);
+    const int ac = Jc - nc;
+    const int32_t* rel = S.rel + S.rows_ptr[c] + nc;
+    const int i0 = lower_bound_i32(rel, ac, tm), i1 = lower_bound_i32(rel, ac, tm + GT);
+    const int j0 = lower_bound_i32(rel, ac, tn), j1 = lower_bound_i32(rel, ac, tn + GT);
+    const int ni = i1 - i0, nj = j1 - j0;
+    const double* U = ws + S.f_off[c] + nc + (int64_t)nc * Jc;
+    for (int e = threadIdx.x; e < ni * nj; e += BT) {
+      const int i = i0 + e % ni, j = j0 + e / ni;
+      if (i >= j) F[__ldg(rel + i) + (int64_t)__ldg(rel + j) * Jp] += __ldcg(U + i + (int64_t)j * Jc);
+    }
+    __syncthreads();
+  }
+}
+// V block of front k gathered from the parent's front (top-down passes)
+__global__ void __launch_bounds__(BT) mk_gather_parent(SymDev S, int k, double* ws, int64_t sws) {
+  ws += blockIdx.z * sws;
+  const int p = (int)S.sn_par[k];
+  const int n = (int)(S.sn_ptr[k + 1] - S.sn_ptr[k]);
+  const int J = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]);
+  const int a = J - n;
+  const int Jp = (int)(S.rows_ptr[p + 1] - S.rows_ptr[p]);
+  const double* Fp = ws + S.f_off[p];
+  double* F = ws + S.f_off[k];
+  const int32_t* rel = S.rel + S.rows_ptr[k] + n;
+  const int64_t tot = (int64_t)a * a;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % a), s = (int)(e / a);
+    if (r >= s) F[(n + r) + (int64_t)(n + s) * J] = __ldcg(Fp + __ldg(rel + r) + (int64_t)__ldg(rel + s) * Jp);
+  }
+}
+__global__ void k_logdet_diag(const double* F, int64_t ld, int n, double* out) {
+  __shared__ double red[BT];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += BT) s += 2.0 * log(F[i + (int64_t)i * ld]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = BT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+// inverse-Hessian step 3 finish: Y_AN = 2P - K_AN - Z_AN, Y_NN = K_NN - Z_NN
+__global__ void __launch_bounds__(BT) mk_ihess_finish(double* Y, int64_t sY, const double* F, const double* P,
+                                                      int64_t sF, int J, int n) {
+  Y += blockIdx.z * sY;
+  F += blockIdx.z * sF;
+  P += blockIdx.z * sF;
+  const int64_t tot = (int64_t)J * n;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % J), c = (int)(e / J);
+    if (r < c) continue;
+    const int64_t o = csc_off(J, r, c);
+    const double z = F[r + (int64_t)c * J];
+    if (r >= n) Y[o] = 2.0 * P[r + (int64_t)c * J] - Y[o] - z;
+    else Y[o] = Y[o] - z;
+  }
+}
+
+inline int ew_blocks(int64_t tot) { return (int)std::max<int64_t>(1, (tot + EW - 1) / EW); }
+#define CHD_EW(kernel, tot, batch, st, ...)                                  \
+  do {                                                                       \
+    kernel<<<dim3(ew_blocks(tot), 1, (batch)), BT, 0, (st)>>>(__VA_ARGS__); \
+    chd_launch::count_launch();                                              \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// per-front sequences
+// ---------------------------------------------------------------------------
+struct Front {
+  int k, n, a, J;
+  int64_t base, col0;
+  int64_t foff;
+};
+inline Front front(const chd_symbolic* s, int k) {
+  Front f;
+  f.k = k;
+  f.col0 = s->sn_ptr[k];
+  f.n = (int)(s->sn_ptr[k + 1] - f.col0);
+  f.J = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k]);
+  f.a = f.J - f.n;
+  f.base = s->colptr[f.col0];
+  f.foff = s->f_off[k];
+  return f;
+}
+
+void assemble_children(const chd_symbolic* s, cudaStream_t st, int batch, int k, double* ws, int64_t sws) {
+  if (s->ch_ptr[k + 1] == s->ch_ptr[k]) return;
+  const int J = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k]);
+  const int t = (J + GT - 1) / GT;
+  mk_extend_add<<<dim3(t * t, 1, batch), BT, 0, st>>>(s->dev, k, ws, sws, t);
+  chd_launch::count_launch();
+}
+void gather_parent(const chd_symbolic* s, cudaStream_t st, int batch, const Front& f, double* ws, int64_t sws) {
+  if (s->sn_par[f.k] < 0 || f.a == 0) return;
+  CHD_EW(mk_gather_parent, (int64_t)f.a * f.a, batch, st, s->dev, f.k, ws, sws);
+}
+
+void factor_front(const chd_symbolic* s, cudaStream_t st, int k, const double* X, double* Lc, double* Wc,
+                  double* Dd, double* ws, double* ldet, int64_t* status) {
+  Front f = front(s, k);
+  const int J = f.J, n = f.n, a = f.a;
+  double* F = ws + f.foff;
+  double* T1 = F + (int64_t)J * J;
+  double* T2 = T1 + (int64_t)J * n;
+  CHD_EW(mk_csc_to_front, (int64_t)J * n, 1, st, F, 0, J, n, X + f.base, 0);
+  if (a > 0) CHD_EW(mk_copy, (int64_t)a * a, 1, st, F + n + (int64_t)n * J, 0, J, nullptr, 0, 0, a, a, 0.0, 0.0, 1, 0);
+  assemble_children(s, st, 1, k, ws, 0);
+  CHD_EW(mk_copy, (int64_t)n * n, 1, st, Dd + s->d_off[k], 0, n, F, 0, J, n, n, 1.0, 0.0, 1, 0);
+  potrf_partial(st, F, J, J, n, status, CHD_ERR_NOT_PD, k, f.col0);
+  CHD_EW(mk_front_to_csc, (int64_t)J * n, 1, st, Lc + f.base, 0, F, 0, J, J, n, 0, J, 1.0);
+  k_logdet_diag<<<1, BT, 0, st>>>(F, J, n, ldet + k);
+  chd_launch::count_launch();
+  // Cinv = C^{-1} (T1), D^{-1} = Cinv^T Cinv (T2 top), L_AN = B C^{-1} (T2 bottom)
+  CHD_EW(mk_identity, (int64_t)n * n, 1, st, T1, J, n);
+  trsm_rLT(st, 1, n, n, DnTW{T1, J}, 0, F, J);
+  gemm(st, 1, n, n, n, 1.0, TriLT{T1, J}, 0, TriL{T1, J}, 0, 0.0, Dn{T2, J}, 0, true);
+  if (a > 0) {
+    CHD_EW(mk_copy, (int64_t)a * n, 1, st, T2 + n, 0, J, F + n, 0, J, a, n, 1.0, 0.0, 0, 0);
+    trsm_rL(st, 1, a, n, Dn{T2 + n, J}, 0, F, J);
+  }
+  CHD_EW(mk_front_to_csc, (int64_t)J * n, 1, st, Wc + f.base, 0, T2, 0, J, J, n, 0, J, 1.0);
+}
+
+void gradient_front(const chd_symbolic* s, cudaStream_t st, int k, const double* Wc, double* Sc, double* g,
+                    double* Vd, double* ws) {
+  Front f = front(s, k);
+  const int J = f.J, n = f.n, a = f.a;
+  double* F = ws + f.foff;
+  gather_parent(s, st, 1, f, ws, 0);
+  const double* W = Wc + f.base;
+  CHD_EW(mk_csc_to_front, (int64_t)J * n, 1, st, F, 0, J, n, W, 0);  // D^{-1}; rows >= n overwritten next
+  gemm(st, 1, a, n, a, -1.0, SymL{F + n + (int64_t)n * J, J}, 0, CscRO{W, J, n}, 0, 0.0, Dn{F + n, J}, 0, false);
+  gemm(st, 1, n, n, a, -1.0, DnT{F + n, J}, 0, CscRO{W, J, n}, 0, 1.0, Dn{F, J}, 0, true);
+  CHD_EW(mk_front_to_csc, (int64_t)J * n, 1, st, Sc + f.base, 0, F, 0, J, J, n, 0, J, 1.0);
+  if (g) CHD_EW(mk_front_to_csc, (int64_t)J * n, 1, st, g + f.base, 0, F, 0, J, J, n, 0, J, -1.0);
+  if (a > 0) CHD_EW(mk_copy, (int64_t)a * a, 1, st, Vd + s->v_off[k], 0, a, F + n + (int64_t)n * J, 0, J, a, a, 1.0, 0.0, 1, 0);
+}
+
+void hess_up_front(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, const double* Vd,
+                   const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
+  Front f = front(s, k);
+  const int J = f.J, n = f.n, a = f.a;
+  const int64_t sw = s->dev.f_total;
+  double* F = ws + f.foff;
+  double* T1 = F + (int64_t)J * J;
+  double* T2 = T1 + (int64_t)J * n;
+  const double* W = Wc + f.base;
+  CscRO L{W, J, n};
+  CHD_EW(mk_csc_to_front, (int64_t)J * n, m, st, F, sw, J, n, Y + f.base, ldy);
+  if (a > 0) CHD_EW(mk_copy, (int64_t)a * a, m, st, F + n + (int64_t)n * J, sw, J, nullptr, 0, 0, a, a, 0.0, 0.0, 1, 0);
+  assemble_children(s, st, m, k, ws, sw);
+  if (a > 0) {
+    CHD_EW(mk_copy, (int64_t)a * n, m, st, T1 + n, sw, J, F + n, sw, J, a, n, 1.0, 0.0, 0, 0);
+    gemm(st, m, a, n, n, -1.0, L, 0, SymL{F, J}, sw, 1.0, Dn{T1 + n, J}, sw, false);
+    gemm(st, m, a, a, n, -1.0, Dn{T1 + n, J}, sw, CscT{W, J, n}, 0, 1.0, Dn{F + n + (int64_t)n * J, J}, sw, true);
+    gemm(st, m, a, a, n, -1.0, L, 0, DnT{F + n, J}, sw, 1.0, Dn{F + n + (int64_t)n * J, J}, sw, true);
+  }
+  CscSym Dinv{W, J};
+  gemm(st, m, n, n, n, 1.0, SymL{F, J}, sw, Dinv, 0, 0.0, Dn{T2, J}, sw, false);
+  gemm(st, m, n, n, n, 1.0, Dinv, 0, Dn{T2, J}, sw, 0.0, Csc{T + f.base, J, 0}, ldt, true);
+  if (a > 0) {
+    gemm(st, m, a, n, n, 1.0, Dn{T1 + n, J}, sw, Dinv, 0, 0.0, Dn{T2 + n, J}, sw, false);
+    gemm(st, m, a, n, a, 1.0, SymL{Vd + s->v_off[k], a}, 0, Dn{T2 + n, J}, sw, 0.0, Csc{T + f.base, J, n}, ldt, false);
+  }
+}
+
+void hess_down_front(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, double* T,
+                     int64_t ldt, double* ws) {
+  Front f = front(s, k);
+  const int J = f.J, n = f.n, a = f.a;
+  const int64_t sw = s->dev.f_total;
+  double* F = ws + f.foff;
+  double* T1 = F + (int64_t)J * J;
+  const double* W = Wc + f.base;
+  CscRO L{W, J, n};
+  gather_parent(s, st, m, f, ws, sw);
+  CHD_EW(mk_csc_to_front, (int64_t)J * n, m, st, F, sw, J, n, T + f.base, ldt);
+  if (a > 0) {
+    gemm(st, m, a, n, a, 1.0, SymL{F + n + (int64_t)n * J, J}, sw, L, 0, 0.0, Dn{T1 + n, J}, sw, false);
+    CHD_EW(mk_copy, (int64_t)a * n, m, st, F + n, sw, J, T1 + n, sw, J, a, n, -0.5, 1.0, 0, 0);
+    gemm(st, m, n, n, a, -1.0, DnT{F + n, J}, sw, L, 0, 1.0, Dn{F, J}, sw, true);
+    gemm(st, m, n, n, a, -1.0, CscT{W, J, n}, 0, Dn{F + n, J}, sw, 1.0, Dn{F, J}, sw, true);
+    CHD_EW(mk_copy, (int64_t)a * n, m, st, F + n, sw, J, T1 + n, sw, J, a, n, -0.5, 1.0, 0, 0);
+  }
+  CHD_EW(mk_front_to_csc, (int64_t)J * n, m, st, T + f.base, ldt, F, sw, J, J, n, 0, J, 1.0);
+}
+
+void ihess_down_front(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, const double* Dd,
+                      const double* Rd, const double* Tin, int64_t ldt, double* Yout, int64_t ldy, double* ws) {
+  Front f = front(s, k);
+  const int J = f.J, n = f.n, a = f.a;
+  const int64_t sw = s->dev.f_total;
+  double* F = ws + f.foff;
+  double* T1 = F + (int64_t)J * J;
+  double* T2 = T1 + (int64_t)J * n;
+  const double* W = Wc + f.base;
+  CscRO L{W, J, n};
+  gather_parent(s, st, m, f, ws, sw);
+  CHD_EW(mk_csc_to_front, (int64_t)J * n, m, st, F, sw, J, n, Tin + f.base, ldt);
+  // T1 = [M_NN (full); M_AN]
+  CHD_EW(mk_copy, (int64_t)n * n, m, st, T1, sw, J, F, sw, J, n, n, 1.0, 0.0, 0, 1);
+  if (a > 0) {
+    CHD_EW(mk_copy, (int64_t)a * n, m, st, T1 + n, sw, J, F + n, sw, J, a, n, 1.0, 0.0, 0, 0);
+    gemm(st, m, a, n, a, 1.0, SymL{F + n + (int64_t)n * J, J}, sw, L, 0, 1.0, Dn{T1 + n, J}, sw, false);
+    gemm(st, m, n, n, a, 1.0, DnT{F + n, J}, sw, L, 0, 1.0, Dn{T1, J}, sw, false);
+    gemm(st, m, n, n, a, 1.0, CscT{W, J, n}, 0, Dn{T1 + n, J}, sw, 1.0, Dn{T1, J}, sw, false);
+  }
+  const double* D = Dd + s->d_off[k];
+  gemm(st, m, n, n, n, 1.0, Dn{T1, J}, sw, SymL{D, n}, 0, 0.0, Dn{T2, J}, sw, false);
+  gemm(st, m, n, n, n, 1.0, SymL{D, n}, 0, Dn{T2, J}, sw, 0.0, Csc{Yout + f.base, J, 0}, ldy, true);
+  if (a > 0) {
+    gemm(st, m, a, n, n, 1.0, Dn{T1 + n, J}, sw, SymL{D, n}, 0, 0.0, Dn{T2 + n, J}, sw, false);
+    const double* R = Rd + s->v_off[k];
+    trsm_rLT(st, m, n, a, DnTW{T2 + n, J}, sw, R, a);
+    trsm_rL(st, m, n, a, DnTW{T2 + n, J}, sw, R, a);
+    CHD_EW(mk_front_to_csc, (int64_t)J * n, m, st, Yout + f.base, ldy, T2, sw, J, J, n, n, J, 1.0);
+  }
+}
+
+void ihess_up_front(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, double* Y,
+                    int64_t ldy, double* ws) {
+  Front f = front(s, k);
+  const int J = f.J, n = f.n, a = f.a;
+  const int64_t sw = s->dev.f_total;
+  double* F = ws + f.foff;
+  double* T2 = F + (int64_t)J * J + (int64_t)J * n;
+  const double* W = Wc + f.base;
+  CscRO L{W, J, n};
+  CHD_EW(mk_copy, (int64_t)J * J, m, st, F, sw, J, nullptr, 0, 0, J, J, 0.0, 0.0, 1, 0);
+  assemble_children(s, st, m, k, ws, sw);
+  if (a > 0) {
+    // T2[n:J] = P = K_AN + 1/2 L K_NN   (K in the output array)
+    CHD_EW(mk_csc_to_front, (int64_t)J * n, m, st, T2, sw, J, n, Y + f.base, ldy);
+    gemm(st, m, a, n, n, 0.5, L, 0, CscSym{Y + f.base, J}, ldy, 1.0, Dn{T2 + n, J}, sw, false);
+    gemm(st, m, a, a, n, -1.0, Dn{T2 + n, J}, sw, CscT{W, J, n}, 0, 1.0, Dn{F + n + (int64_t)n * J, J}, sw, true);
+    gemm(st, m, a, a, n, -1.0, L, 0, DnT{T2 + n, J}, sw, 1.0, Dn{F + n + (int64_t)n * J, J}, sw, true);
+  }
+  CHD_EW(mk_ihess_finish, (int64_t)J * n, m, st, Y + f.base, ldy, F, T2, sw, J, n);
+}
+
+void complete_front(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* Lc, double* Wc,
+                    double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
+  Front f = front(s, k);
+  const int J = f.J, n = f.n, a = f.a;
+  double* F = ws + f.foff;
+  double* T1 = F + (int64_t)J * J;
+  double* T2 = T1 + (int64_t)J * n;
+  gather_parent(s, st, 1, f, ws, 0);
+  CHD_EW(mk_csc_to_front, (int64_t)J * n, 1, st, F, 0, J, n, Sin + f.base, 0);
+  double* V = Vd + s->v_off[k];
+  double* R = Rd + s->v_off[k];
+  if (a > 0) {
+    CHD_EW(mk_copy, (int64_t)a * a, 1, st, V, 0, a, F + n + (int64_t)n * J, 0, J, a, a, 1.0, 0.0, 1, 0);
+    CHD_EW(mk_copy, (int64_t)a * a, 1, st, R, 0, a, F + n + (int64_t)n * J, 0, J, a, a, 1.0, 0.0, 1, 0);
+    potrf_partial(st, R, a, a, a, status, CHD_ERR_NOT_COMPLETABLE, k, -1);
+    CHD_EW(mk_copy, (int64_t)a * n, 1, st, T1 + n, 0, J, F + n, 0, J, a, n, 1.0, 0.0, 0, 0);
+    trsm_rLT(st, 1, n, a, DnTW{T1 + n, J}, 0, R, a);  // Z = R^{-1} S_AN
+  }
+  CHD_EW(mk_copy, (int64_t)n * n, 1, st, T1, 0, J, F, 0, J, n, n, 1.0, 0.0, 1, 0);
+  if (a > 0) {
+    gemm(st, 1, n, n, a, -1.0, DnT{T1 + n, J}, 0, Dn{T1 + n, J}, 0, 1.0, Dn{T1, J}, 0, true);  // P
+    CHD_EW(mk_copy, (int64_t)a * n, 1, st, T2 + n, 0, J, T1 + n, 0, J, a, n, -1.0, 0.0, 0, 0);
+    trsm_rL(st, 1, n, a, DnTW{T2 + n, J}, 0, R, a);  // L_AN = -R^{-T} Z
+  }
+  CHD_EW(mk_front_to_csc, (int64_t)J * n, 1, st, Wc + f.base, 0, T1, 0, J, J, n, 0, n, 1.0);
+  if (a > 0) CHD_EW(mk_front_to_csc, (int64_t)J * n, 1, st, Wc + f.base, 0, T2, 0, J, J, n, n, J, 1.0);
+  // Q = chol(P) in T2[0:n]; D = P^{-1} = Q^{-T} Q^{-1}
+  CHD_EW(mk_copy, (int64_t)n * n, 1, st, T2, 0, J, T1, 0, J, n, n, 1.0, 0.0, 1, 0);
+  potrf_partial(st, T2, J, n, n, status, CHD_ERR_NOT_COMPLETABLE, k, f.col0);
+  double* Dk = Dd + s->d_off[k];
+  CHD_EW(mk_identity, (int64_t)n * n, 1, st, Dk, n, n);
+  trsm_rLT(st, 1, n, n, DnTW{Dk, n}, 0, T2, J);
+  gemm(st, 1, n, n, n, 1.0, TriLT{Dk, n}, 0, TriL{Dk, n}, 0, 0.0, Dn{T1, J}, 0, true);
+  CHD_EW(mk_copy, (int64_t)n * n, 1, st, Dk, 0, n, T1, 0, J, n, n, 1.0, 0.0, 1, 0);
+  potrf_partial(st, T1, J, n, n, status, CHD_ERR_NOT_COMPLETABLE, k, f.col0);
+  CHD_EW(mk_front_to_csc, (int64_t)J * n, 1, st, Lc + f.base, 0, T1, 0, J, J, n, 0, n, 1.0);
+  if (a > 0) gemm(st, 1, a, n, n, 1.0, Dn{T2 + n, J}, 0, TriL{T1, J}, 0, 0.0, Csc{Lc + f.base, J, n}, 0, false);
+  k_logdet_diag<<<1, BT, 0, st>>>(T1, J, n, ldet + k);
+  chd_launch::count_launch();
+}
+
+}  // namespace big
+}  // namespace chd
+
+namespace chd_launch {
+void big_factor(const chd_symbolic* s, cudaStream_t st, int k, const double* X, double* Lc, double* Wc,
+                double* Dd, double* ws, double* ldet, int64_t* status) {
+  chd::big::factor_front(s, st, k, X, Lc, Wc, Dd, ws, ldet, status);
+}
+void big_gradient(const chd_symbolic* s, cudaStream_t st, int k, const double* Wc, double* Sc, double* g,
+                  double* Vd, double* ws) {
+  chd::big::gradient_front(s, st, k, Wc, Sc, g, Vd, ws);
+}
+void big_hess_up(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, const double* Vd,
+                 const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
+  chd::big::hess_up_front(s, st, m, k, Wc, Vd, Y, ldy, T, ldt, ws);
+}
+void big_hess_down(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, double* T, int64_t ldt,
+                   double* ws) {
+  chd::big::hess_down_front(s, st, m, k, Wc, T, ldt, ws);
+}
+void big_ihess_down(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, const double* Dd,
+                    const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy, double* ws) {
+  chd::big::ihess_down_front(s, st, m, k, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+}
+void big_ihess_up(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, double* Y, int64_t ldy,
+                  double* ws) {
+  chd::big::ihess_up_front(s, st, m, k, Wc, Y, ldy, ws);
+}
+void big_complete(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* Lc, double* Wc,
+                  double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
+  chd::big::complete_front(s, st, k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+}
+// Cholesky factor of the cached V_k = S_{A_k A_k} of one big front.
+void big_chol_v(const chd_symbolic* s, cudaStream_t st, int k, const double* Vd, double* Rd, int64_t* status) {
+  using namespace chd::big;
+  const int n = (int)(s->sn_ptr[k + 1] - s->sn_ptr[k]);
+  const int a = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k]) - n;
+  if (a == 0) return;
+  double* R = Rd + s->v_off[k];
+  CHD_EW(mk_copy, (int64_t)a * a, 1, st, R, 0, a, Vd + s->v_off[k], 0, a, a, a, 1.0, 0.0, 1, 0);
+  potrf_partial(st, R, a, a, a, status, CHD_ERR_NOT_PD, k, -1);
+}
+}  // namespace chd_launch

@@ -26,6 +26,7 @@ void complete(const chd_symbolic* s, cudaStream_t st, const double* Sin, double*
 void chol_v(const chd_symbolic* s, cudaStream_t st, const double* Vd, double* Rd, int64_t* status);
 void sum(cudaStream_t st, const double* v, int64_t m, double* out);
 void export_ldl(const chd_symbolic* s, cudaStream_t st, const double* Lc, double* l, double* d);
+cudaError_t fp64_peak(cudaStream_t st, double* gflops);
 }  // namespace chd_launch
 
 struct chd_factor {
@@ -300,34 +301,41 @@ chd_status chd_inv_hessian(chd_factor* f, int m, const double* t, int64_t ldt, d
   return CHD_OK;
 }
 
+chd_status chd_recomplete(chd_factor* f, const double* sv, void* stream, double* fstar) {
+  if (!f || !sv) return CHD_ERR_INVALID;
+  chd_symbolic* s = f->sym;
+  f->stream = static_cast<cudaStream_t>(stream);
+  chd_status rc = ensure_ws(f, 1);
+  if (rc == CHD_OK) rc = cuda_ok(cudaMemsetAsync(f->status, 0, 4 * 8, f->stream));
+  if (rc == CHD_OK)
+    rc = cuda_ok(cudaMemcpyAsync(f->Sc, sv, (size_t)s->colptr[s->n] * 8, cudaMemcpyDeviceToDevice, f->stream));
+  if (rc == CHD_OK) {
+    chd_launch::complete(s, f->stream, sv, f->Lc, f->Wc, f->Dd, f->Vd, f->Rd, f->ws, f->ldet, f->status);
+    rc = launch_status();
+  }
+  if (rc != CHD_OK) return rc;
+  f->have_S = f->have_R = true;
+  if (fstar) {
+    double ld = 0;
+    rc = chd_logdet(f, &ld);
+    if (rc == CHD_ERR_NOT_PD) rc = CHD_ERR_NOT_COMPLETABLE;
+    if (rc != CHD_OK) return rc;
+    *fstar = ld - (double)s->n;
+  }
+  return CHD_OK;
+}
+
 chd_status chd_complete(chd_symbolic* s, const double* sv, void* stream, chd_factor** xhat,
                         double* fstar) {
   if (!s || !sv || !xhat) return CHD_ERR_INVALID;
   *xhat = nullptr;
   chd_factor* f = nullptr;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  chd_status rc = alloc_factor(s, st, &f);
+  chd_status rc = alloc_factor(s, static_cast<cudaStream_t>(stream), &f);
   if (rc != CHD_OK) return rc;
-  rc = ensure_ws(f, 1);
-  if (rc == CHD_OK)
-    rc = cuda_ok(cudaMemcpyAsync(f->Sc, sv, (size_t)s->colptr[s->n] * 8, cudaMemcpyDeviceToDevice, st));
-  if (rc == CHD_OK) {
-    chd_launch::complete(s, st, sv, f->Lc, f->Wc, f->Dd, f->Vd, f->Rd, f->ws, f->ldet, f->status);
-    rc = launch_status();
-  }
+  rc = chd_recomplete(f, sv, stream, fstar);
   if (rc != CHD_OK) {
     chd_factor_free(f);
     return rc;
-  }
-  f->have_S = f->have_R = true;
-  if (fstar) {
-    double ld = 0;
-    rc = chd_logdet(f, &ld);
-    if (rc != CHD_OK) {
-      chd_factor_free(f);
-      return rc;
-    }
-    *fstar = ld - (double)s->n;
   }
   *xhat = f;
   return CHD_OK;
@@ -357,6 +365,11 @@ chd_status chd_error_detail(chd_factor* f, int64_t* supernode, int64_t* column) 
 }
 
 int64_t chd_kernel_launches(void) { return chd_launch::launches(); }
+
+chd_status chd_probe_fp64_peak(void* stream, double* gflops) {
+  if (!gflops) return CHD_ERR_INVALID;
+  return cuda_ok(chd_launch::fp64_peak(static_cast<cudaStream_t>(stream), gflops));
+}
 
 void chd_factor_free(chd_factor* f) {
   if (!f) return;
@@ -395,6 +408,7 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   size_t iV = add(s->v_off.data(), s->v_off.size() * 8);
   size_t iTp = add(s->task_ptr.data(), s->task_ptr.size() * 4);
   size_t iTf = add(s->task_fronts.data(), s->task_fronts.size() * 4);
+  size_t iSf = add(s->small_fronts.data(), s->small_fronts.size() * 4);
   std::vector<char> host(off, 0);
   for (auto& p : pcs)
     if (p.bytes) std::memcpy(host.data() + p.off, p.src, p.bytes);
@@ -441,6 +455,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   d.v_off = reinterpret_cast<const int64_t*>(b + pcs[iV].off);
   d.task_ptr = reinterpret_cast<const int32_t*>(b + pcs[iTp].off);
   d.task_fronts = reinterpret_cast<const int32_t*>(b + pcs[iTf].off);
+  d.small_fronts = reinterpret_cast<const int32_t*>(b + pcs[iSf].off);
+  d.small_count = (int64_t)s->small_fronts.size();
   d.f_total = s->f_off[s->nsn];
   d.d_total = s->d_off[s->nsn];
   d.v_total = s->v_off[s->nsn];

@@ -23,6 +23,8 @@ struct SymDev {
   const int64_t* v_off = nullptr;    // nsn+1: per-front a_k*a_k block offsets
   const int32_t* task_ptr = nullptr; // ntask+1
   const int32_t* task_fronts = nullptr;
+  const int32_t* small_fronts = nullptr;  // fronts not in the dense tier
+  int64_t small_count = 0;
   int64_t f_total = 0;               // workspace doubles per right-hand side
   int64_t d_total = 0;
   int64_t v_total = 0;
@@ -45,6 +47,11 @@ struct chd_symbolic {
   // schedule: tasks are front sequences processed by one CTA; launches
   // group tasks by level (bottom-up order); lvl_ptr indexes tasks.
   std::vector<int32_t> task_ptr, task_fronts, lvl_ptr;
+  // per level: the last lvl_big[l] tasks of the level are single big fronts
+  // run by the multi-CTA dense tier
+  std::vector<int32_t> lvl_big;
+  std::vector<char> is_big;  // per supernode
+  std::vector<int32_t> small_fronts;
   double flops[5] = {0, 0, 0, 0, 0};
   int64_t max_front = 0;
   // device mirror

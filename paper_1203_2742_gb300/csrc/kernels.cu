@@ -24,6 +24,7 @@
 #include <cstdint>
 
 #include "chd_internal.h"
+#include "front_views.cuh"
 
 namespace chd {
 
@@ -39,77 +40,6 @@ __shared__ double sh_A[TK][TB + 1];
 __shared__ double sh_B[TK][TB + 1];
 __shared__ double sh_L[PB * (PB + 1)];
 __shared__ double sh_P[PCH * (PB + 1)];
-
-// ---------------------------------------------------------------------------
-// matrix views (element (r, c) accessors)
-// ---------------------------------------------------------------------------
-struct Dn {  // column-major
-  double* p;
-  int64_t ld;
-  __device__ double& at(int r, int c) const { return p[r + (int64_t)c * ld]; }
-};
-struct DnT {  // transpose of a column-major matrix
-  const double* p;
-  int64_t ld;
-  __device__ double at(int r, int c) const { return p[c + (int64_t)r * ld]; }
-};
-struct SymL {  // symmetric, lower triangle stored column-major
-  const double* p;
-  int64_t ld;
-  __device__ double at(int r, int c) const {
-    return r >= c ? p[r + (int64_t)c * ld] : p[c + (int64_t)r * ld];
-  }
-};
-struct TriL {  // lower triangular, stored column-major
-  const double* p;
-  int64_t ld;
-  __device__ double at(int r, int c) const { return r >= c ? p[r + (int64_t)c * ld] : 0.0; }
-};
-struct TriLT {  // transpose of a lower triangular matrix
-  const double* p;
-  int64_t ld;
-  __device__ double at(int r, int c) const { return c >= r ? p[c + (int64_t)r * ld] : 0.0; }
-};
-__device__ __forceinline__ int64_t csc_off(int J, int r, int c) {
-  return (int64_t)c * (J - 1) - (int64_t)c * (c - 1) / 2 + r;
-}
-struct Csc {  // N-part of a front in CSC: (r, c) for r >= c, rows offset by r0
-  double* p;
-  int J;
-  int r0;
-  __device__ double& at(int r, int c) const { return p[csc_off(J, r + r0, c)]; }
-};
-struct CscRO {
-  const double* p;
-  int J;
-  int r0;
-  __device__ double at(int r, int c) const { return p[csc_off(J, r + r0, c)]; }
-};
-struct CscT {  // transpose of rows [r0, ..) of the N-part
-  const double* p;
-  int J;
-  int r0;
-  __device__ double at(int r, int c) const { return p[csc_off(J, c + r0, r)]; }
-};
-struct CscSym {  // symmetric N x N block stored lower in CSC
-  const double* p;
-  int J;
-  __device__ double at(int r, int c) const {
-    return r >= c ? p[csc_off(J, r, c)] : p[csc_off(J, c, r)];
-  }
-};
-
-// ---------------------------------------------------------------------------
-// status
-// ---------------------------------------------------------------------------
-__device__ void record_error(int64_t* st, int64_t code, int64_t snode, int64_t col) {
-  unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(st), 0ull,
-                                     static_cast<unsigned long long>(code));
-  if (old == 0ull) {
-    st[1] = snode;
-    st[2] = col;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // CTA GEMM:  C = beta*C + alpha * A(MxK) B(KxN), optionally lower triangle only.
@@ -289,12 +219,6 @@ __device__ void cta_trsm_rL(int R, int n, MB B, const double* L, int64_t ld) {
     __syncthreads();
   }
 }
-// transposed writable view: (r, c) -> B(c, r)
-struct DnTW {
-  double* p;
-  int64_t ld;
-  __device__ double& at(int r, int c) const { return p[c + (int64_t)r * ld]; }
-};
 
 // ---------------------------------------------------------------------------
 // small element-wise helpers
@@ -716,9 +640,11 @@ __global__ void __launch_bounds__(NT) k_complete(SymDev S, int task0, const doub
   for (int q = S.task_ptr[t + 1] - 1; q >= S.task_ptr[t]; --q)
     complete_front(S, S.task_fronts[q], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, st);
 }
-// Cholesky factors of the cached V_k, one CTA per front (no dependencies).
-__global__ void __launch_bounds__(NT) k_chol_v(SymDev S, const double* Vd, double* Rd, int64_t* st) {
-  const int k = blockIdx.x;
+// Cholesky factors of the cached V_k, one CTA per front (no dependencies);
+// fronts listed in `skip` (big fronts) are done by the dense tier instead.
+__global__ void __launch_bounds__(NT) k_chol_v(SymDev S, const double* Vd, double* Rd, int64_t* st,
+                                               const int32_t* front_list) {
+  const int k = front_list[blockIdx.x];
   const int n = (int)(S.sn_ptr[k + 1] - S.sn_ptr[k]);
   const int a = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]) - n;
   if (a == 0) return;
@@ -757,6 +683,21 @@ __global__ void k_export(SymDev S, const double* Lc, double* l, double* d) {
   }
 }
 
+// FP64 throughput probe: 8 independent DFMA chains per thread.
+__global__ void __launch_bounds__(NT) k_dfma_probe(double* out, int iters, double s) {
+  double a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = fma(a[i], s, 1e-9);
+  }
+  double r = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r += a[i];
+  out[blockIdx.x * NT + threadIdx.x] = r;
+}
+
 }  // namespace chd
 
 // ---------------------------------------------------------------------------
@@ -767,75 +708,127 @@ using namespace chd;
 
 static int64_t g_launches = 0;
 int64_t launches() { return g_launches; }
+void count_launch() { ++g_launches; }
 
 static inline void count() { ++g_launches; }
 
-void factor(const chd_symbolic* s, cudaStream_t st, const double* X, double* Lc, double* Wc,
-            double* Dd, double* ws, double* ldet, int64_t* status) {
+// dense-tier sequences (bigfront.cu)
+void big_factor(const chd_symbolic* s, cudaStream_t st, int k, const double* X, double* Lc, double* Wc,
+                double* Dd, double* ws, double* ldet, int64_t* status);
+void big_gradient(const chd_symbolic* s, cudaStream_t st, int k, const double* Wc, double* Sc, double* g,
+                  double* Vd, double* ws);
+void big_hess_up(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, const double* Vd,
+                 const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
+void big_hess_down(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, double* T, int64_t ldt,
+                   double* ws);
+void big_ihess_down(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, const double* Dd,
+                    const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy, double* ws);
+void big_ihess_up(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, double* Y, int64_t ldy,
+                  double* ws);
+void big_complete(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* Lc, double* Wc,
+                  double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
+
+// Level l: tasks [t0, t0 + nsmall) run as one per-task launch; the next nbig
+// tasks are single big fronts, each run as a dense-tier sequence.
+struct Level {
+  int t0, nsmall, nbig;
+};
+static inline Level level(const chd_symbolic* s, int l) {
+  Level v;
+  v.t0 = s->lvl_ptr[l];
+  const int nt = s->lvl_ptr[l + 1] - v.t0;
+  v.nbig = s->lvl_big[l];
+  v.nsmall = nt - v.nbig;
+  return v;
+}
+static inline int big_front(const chd_symbolic* s, const Level& v, int i) {
+  return s->task_fronts[s->task_ptr[v.t0 + v.nsmall + i]];
+}
+
+void factor(const chd_symbolic* s, cudaStream_t st, const double* X, double* Lc, double* Wc, double* Dd,
+            double* ws, double* ldet, int64_t* status) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = 0; l < nl; ++l) {
-    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
-    if (nt == 0) continue;
-    k_factor<<<nt, NT, 0, st>>>(s->dev, t0, X, Lc, Wc, Dd, ws, ldet, status);
-    count();
+    Level v = level(s, l);
+    if (v.nsmall) {
+      k_factor<<<v.nsmall, NT, 0, st>>>(s->dev, v.t0, X, Lc, Wc, Dd, ws, ldet, status);
+      count();
+    }
+    for (int i = 0; i < v.nbig; ++i) big_factor(s, st, big_front(s, v, i), X, Lc, Wc, Dd, ws, ldet, status);
   }
 }
-void gradient(const chd_symbolic* s, cudaStream_t st, const double* Wc, double* Sc, double* g,
-              double* Vd, double* ws) {
+void gradient(const chd_symbolic* s, cudaStream_t st, const double* Wc, double* Sc, double* g, double* Vd,
+              double* ws) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = nl - 1; l >= 0; --l) {
-    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
-    if (nt == 0) continue;
-    k_gradient<<<nt, NT, 0, st>>>(s->dev, t0, Wc, Sc, g, Vd, ws);
-    count();
+    Level v = level(s, l);
+    for (int i = 0; i < v.nbig; ++i) big_gradient(s, st, big_front(s, v, i), Wc, Sc, g, Vd, ws);
+    if (v.nsmall) {
+      k_gradient<<<v.nsmall, NT, 0, st>>>(s->dev, v.t0, Wc, Sc, g, Vd, ws);
+      count();
+    }
   }
 }
-void hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Vd,
-             const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
+void hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Vd, const double* Y,
+             int64_t ldy, double* T, int64_t ldt, double* ws) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = 0; l < nl; ++l) {
-    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
-    if (nt == 0) continue;
-    k_hess_up<<<dim3(nt, m), NT, 0, st>>>(s->dev, t0, Wc, Vd, Y, ldy, T, ldt, ws);
-    count();
+    Level v = level(s, l);
+    if (v.nsmall) {
+      k_hess_up<<<dim3(v.nsmall, m), NT, 0, st>>>(s->dev, v.t0, Wc, Vd, Y, ldy, T, ldt, ws);
+      count();
+    }
+    for (int i = 0; i < v.nbig; ++i) big_hess_up(s, st, m, big_front(s, v, i), Wc, Vd, Y, ldy, T, ldt, ws);
   }
   for (int l = nl - 1; l >= 0; --l) {
-    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
-    if (nt == 0) continue;
-    k_hess_down<<<dim3(nt, m), NT, 0, st>>>(s->dev, t0, Wc, T, ldt, ws);
-    count();
+    Level v = level(s, l);
+    for (int i = 0; i < v.nbig; ++i) big_hess_down(s, st, m, big_front(s, v, i), Wc, T, ldt, ws);
+    if (v.nsmall) {
+      k_hess_down<<<dim3(v.nsmall, m), NT, 0, st>>>(s->dev, v.t0, Wc, T, ldt, ws);
+      count();
+    }
   }
 }
 void inv_hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Dd,
-                 const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy,
-                 double* ws) {
+                 const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy, double* ws) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = nl - 1; l >= 0; --l) {
-    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
-    if (nt == 0) continue;
-    k_ihess_down<<<dim3(nt, m), NT, 0, st>>>(s->dev, t0, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
-    count();
+    Level v = level(s, l);
+    for (int i = 0; i < v.nbig; ++i) big_ihess_down(s, st, m, big_front(s, v, i), Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    if (v.nsmall) {
+      k_ihess_down<<<dim3(v.nsmall, m), NT, 0, st>>>(s->dev, v.t0, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+      count();
+    }
   }
   for (int l = 0; l < nl; ++l) {
-    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
-    if (nt == 0) continue;
-    k_ihess_up<<<dim3(nt, m), NT, 0, st>>>(s->dev, t0, Wc, Y, ldy, ws);
-    count();
+    Level v = level(s, l);
+    if (v.nsmall) {
+      k_ihess_up<<<dim3(v.nsmall, m), NT, 0, st>>>(s->dev, v.t0, Wc, Y, ldy, ws);
+      count();
+    }
+    for (int i = 0; i < v.nbig; ++i) big_ihess_up(s, st, m, big_front(s, v, i), Wc, Y, ldy, ws);
   }
 }
-void complete(const chd_symbolic* s, cudaStream_t st, const double* Sin, double* Lc, double* Wc,
-              double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
+void complete(const chd_symbolic* s, cudaStream_t st, const double* Sin, double* Lc, double* Wc, double* Dd,
+              double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = nl - 1; l >= 0; --l) {
-    int t0 = s->lvl_ptr[l], nt = s->lvl_ptr[l + 1] - t0;
-    if (nt == 0) continue;
-    k_complete<<<nt, NT, 0, st>>>(s->dev, t0, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
-    count();
+    Level v = level(s, l);
+    for (int i = 0; i < v.nbig; ++i) big_complete(s, st, big_front(s, v, i), Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+    if (v.nsmall) {
+      k_complete<<<v.nsmall, NT, 0, st>>>(s->dev, v.t0, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+      count();
+    }
   }
 }
+void big_chol_v(const chd_symbolic* s, cudaStream_t st, int k, const double* Vd, double* Rd, int64_t* status);
 void chol_v(const chd_symbolic* s, cudaStream_t st, const double* Vd, double* Rd, int64_t* status) {
-  k_chol_v<<<(int)s->nsn, NT, 0, st>>>(s->dev, Vd, Rd, status);
-  count();
+  if (s->dev.small_count > 0) {
+    k_chol_v<<<(int)s->dev.small_count, NT, 0, st>>>(s->dev, Vd, Rd, status, s->dev.small_fronts);
+    count();
+  }
+  for (int64_t k = 0; k < s->nsn; ++k)
+    if (s->is_big[k]) big_chol_v(s, st, (int)k, Vd, Rd, status);
 }
 void sum(cudaStream_t st, const double* v, int64_t m, double* out) {
   k_sum<<<1, NT, 0, st>>>(v, m, out);
@@ -844,5 +837,31 @@ void sum(cudaStream_t st, const double* v, int64_t m, double* out) {
 void export_ldl(const chd_symbolic* s, cudaStream_t st, const double* Lc, double* l, double* d) {
   k_export<<<(int)s->nsn, NT, 0, st>>>(s->dev, Lc, l, d);
   count();
+}
+cudaError_t fp64_peak(cudaStream_t st, double* gflops) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int blocks = sms * 4, iters = 4000;
+  double* buf = nullptr;
+  e = cudaMalloc(&buf, (size_t)blocks * NT * sizeof(double));
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_dfma_probe<<<blocks, NT, 0, st>>>(buf, 50, 0.999);
+  cudaEventRecord(e0, st);
+  k_dfma_probe<<<blocks, NT, 0, st>>>(buf, iters, 0.999);
+  cudaEventRecord(e1, st);
+  e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e == cudaSuccess) *gflops = 2.0 * 8 * iters * (double)blocks * NT / (ms * 1e-3) * 1e-9;
+  return e;
 }
 }  // namespace chd_launch

@@ -443,8 +443,23 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
       if (s->sn_par[t] < 0) total += W[t];
     }
     const double thr = total / (4.0 * 152.0);
+    // Big fronts (dense tier): J >= big_rows or n >= big_cols.
+    const int64_t big_rows = opts.big_rows > 0 ? opts.big_rows : 320;
+    const int64_t big_cols = opts.big_cols > 0 ? opts.big_cols : 160;
+    s->is_big.assign(nsn, 0);
+    for (int64_t t = 0; t < nsn; ++t) {
+      int64_t nn = s->sn_ptr[t + 1] - s->sn_ptr[t];
+      int64_t J = s->rows_ptr[t + 1] - s->rows_ptr[t];
+      s->is_big[t] = (J >= big_rows || nn >= big_cols) ? 1 : 0;
+    }
+    s->small_fronts.clear();
+    for (int64_t t = 0; t < nsn; ++t)
+      if (!s->is_big[t]) s->small_fronts.push_back((int32_t)t);
     vector<char> top(nsn, 0);
-    for (int64_t t = 0; t < nsn; ++t) top[t] = W[t] > thr;
+    for (int64_t t = 0; t < nsn; ++t) top[t] = W[t] > thr || s->is_big[t];
+    // every ancestor of a top front is a top front
+    for (int64_t t = 0; t < nsn; ++t)
+      if (top[t] && s->sn_par[t] >= 0) top[s->sn_par[t]] = 1;
     vector<int64_t> task_of(nsn, -1);
     vector<vector<int32_t>> tasks;
     vector<int64_t> tlevel;
@@ -474,7 +489,7 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
         int64_t c = s->ch[q];
         if (top[c]) lvl = std::max(lvl, tlevel[task_of[c]] + 1);
       }
-      if (ntopkids[t] == 1) {
+      if (ntopkids[t] == 1 && !s->is_big[t] && !s->is_big[onlykid[t]]) {
         int64_t tk = task_of[onlykid[t]];
         tasks[tk].push_back((int32_t)t);
         task_of[t] = tk;
@@ -504,12 +519,20 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     s->task_ptr.assign(1, 0);
     s->task_fronts.clear();
     s->lvl_ptr.assign(1, 0);
+    s->lvl_big.clear();
     for (int64_t l = 0; l < nlev; ++l) {
-      for (int64_t q : bylev[l]) {
-        for (int32_t f : tasks[q]) s->task_fronts.push_back(f);
-        s->task_ptr.push_back((int32_t)s->task_fronts.size());
+      int32_t nbig = 0;
+      for (int pass = 0; pass < 2; ++pass) {  // small tasks first, big fronts last
+        for (int64_t q : bylev[l]) {
+          const bool big = tasks[q].size() == 1 && s->is_big[tasks[q][0]];
+          if (big != (pass == 1)) continue;
+          for (int32_t f : tasks[q]) s->task_fronts.push_back(f);
+          s->task_ptr.push_back((int32_t)s->task_fronts.size());
+          nbig += big ? 1 : 0;
+        }
       }
       s->lvl_ptr.push_back((int32_t)(s->task_ptr.size() - 1));
+      s->lvl_big.push_back(nbig);
     }
   }
   return CHD_OK;

@@ -24,9 +24,10 @@ def torch():
 
 
 class Case:
-    def __init__(self, pattern, ordering="natural", perm=None, relax=0, seed=0, x=None):
+    def __init__(self, pattern, ordering="natural", perm=None, relax=0, seed=0, x=None, big=None):
         self.B = lib()
-        self.sym = self.B.Symbolic(*pattern, ordering=ordering, perm=perm, relax=relax)
+        kw = {} if big is None else dict(big_rows=big[0], big_cols=big[1])
+        self.sym = self.B.Symbolic(*pattern, ordering=ordering, perm=perm, relax=relax, **kw)
         s = self.sym
         self.n, self.cp, self.ri = s.n, s.colptr, s.rowind
         # V must be filled (Eq. (e-filled)) and contain the permuted input pattern
@@ -62,6 +63,14 @@ def small_cases():
         "dense70": lambda: Case(W.band(70, 69), seed=6),
         "diag30": lambda: Case(W.band(30, 0), seed=7),
         "wide_front": lambda: Case(W.arrow(200, 120), seed=8),
+        # the same kinds of pattern with low thresholds, so that many fronts run
+        # through the multi-CTA dense tier and hand over to and from the per-task tier
+        "dense_tier_grid": lambda: Case(W.grid2d(16, 16), ordering="user",
+                                        perm=W.nested_dissection((16, 16), leaf=6), seed=9, big=(20, 8)),
+        "dense_tier_er": lambda: Case(W.erdos_renyi(300, 0.02, np.random.default_rng(5)),
+                                      ordering="mindeg", relax=16, seed=10, big=(40, 20)),
+        "dense_tier_full": lambda: Case(W.band(150, 149), seed=11, big=(64, 64)),
+        "dense_tier_arrow": lambda: Case(W.arrow(260, 100), seed=12, big=(90, 70)),
     }
 
 
