@@ -50,7 +50,10 @@ struct chd_symbolic {
   // per level: the last lvl_big[l] tasks of the level are single big fronts
   // run by the multi-CTA dense tier
   std::vector<int32_t> lvl_big;
+  // per level: the first lvl_warp[l] tasks are warp-tier tasks
+  std::vector<int32_t> lvl_warp;
   std::vector<char> is_big;  // per supernode
+  std::vector<int32_t> tier;  // per supernode: 0 warp, 1 CTA, 2 dense
   std::vector<int32_t> small_fronts;
   double flops[5] = {0, 0, 0, 0, 0};
   int64_t max_front = 0;

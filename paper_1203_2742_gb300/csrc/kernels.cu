@@ -728,21 +728,40 @@ void big_ihess_up(const chd_symbolic* s, cudaStream_t st, int m, int k, const do
 void big_complete(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* Lc, double* Wc,
                   double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
 
-// Level l: tasks [t0, t0 + nsmall) run as one per-task launch; the next nbig
-// tasks are single big fronts, each run as a dense-tier sequence.
+// warp-tier launches (warp_tier.cu)
+void warp_factor(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* X, double* Lc, double* Wc,
+                 double* Dd, double* ws, double* ldet, int64_t* status);
+void warp_gradient(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Wc, double* Sc,
+                   double* g, double* Vd, double* ws);
+void warp_hess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
+                  const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
+void warp_hess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* T,
+                    int64_t ldt, double* ws);
+void warp_ihess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
+                     const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy,
+                     double* ws);
+void warp_ihess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* Y,
+                   int64_t ldy, double* ws);
+void warp_complete(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Sin, double* Lc,
+                   double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
+
+// Level l holds tasks [t0, t0 + nwarp) of the warp tier, then [tc, tc + ncta)
+// of the CTA tier, then nbig single big fronts of the dense tier.
 struct Level {
-  int t0, nsmall, nbig;
+  int t0, nwarp, tc, ncta, nbig;
 };
 static inline Level level(const chd_symbolic* s, int l) {
   Level v;
   v.t0 = s->lvl_ptr[l];
   const int nt = s->lvl_ptr[l + 1] - v.t0;
+  v.nwarp = s->lvl_warp[l];
   v.nbig = s->lvl_big[l];
-  v.nsmall = nt - v.nbig;
+  v.tc = v.t0 + v.nwarp;
+  v.ncta = nt - v.nwarp - v.nbig;
   return v;
 }
 static inline int big_front(const chd_symbolic* s, const Level& v, int i) {
-  return s->task_fronts[s->task_ptr[v.t0 + v.nsmall + i]];
+  return s->task_fronts[s->task_ptr[v.tc + v.ncta + i]];
 }
 
 void factor(const chd_symbolic* s, cudaStream_t st, const double* X, double* Lc, double* Wc, double* Dd,
@@ -750,8 +769,9 @@ void factor(const chd_symbolic* s, cudaStream_t st, const double* X, double* Lc,
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = 0; l < nl; ++l) {
     Level v = level(s, l);
-    if (v.nsmall) {
-      k_factor<<<v.nsmall, NT, 0, st>>>(s->dev, v.t0, X, Lc, Wc, Dd, ws, ldet, status);
+    if (v.nwarp) warp_factor(s, st, v.t0, v.nwarp, X, Lc, Wc, Dd, ws, ldet, status);
+    if (v.ncta) {
+      k_factor<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, X, Lc, Wc, Dd, ws, ldet, status);
       count();
     }
     for (int i = 0; i < v.nbig; ++i) big_factor(s, st, big_front(s, v, i), X, Lc, Wc, Dd, ws, ldet, status);
@@ -763,10 +783,11 @@ void gradient(const chd_symbolic* s, cudaStream_t st, const double* Wc, double* 
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
     for (int i = 0; i < v.nbig; ++i) big_gradient(s, st, big_front(s, v, i), Wc, Sc, g, Vd, ws);
-    if (v.nsmall) {
-      k_gradient<<<v.nsmall, NT, 0, st>>>(s->dev, v.t0, Wc, Sc, g, Vd, ws);
+    if (v.ncta) {
+      k_gradient<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Wc, Sc, g, Vd, ws);
       count();
     }
+    if (v.nwarp) warp_gradient(s, st, v.t0, v.nwarp, Wc, Sc, g, Vd, ws);
   }
 }
 void hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Vd, const double* Y,
@@ -774,8 +795,9 @@ void hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, co
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = 0; l < nl; ++l) {
     Level v = level(s, l);
-    if (v.nsmall) {
-      k_hess_up<<<dim3(v.nsmall, m), NT, 0, st>>>(s->dev, v.t0, Wc, Vd, Y, ldy, T, ldt, ws);
+    if (v.nwarp) warp_hess_up(s, st, v.t0, v.nwarp, m, Wc, Vd, Y, ldy, T, ldt, ws);
+    if (v.ncta) {
+      k_hess_up<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Vd, Y, ldy, T, ldt, ws);
       count();
     }
     for (int i = 0; i < v.nbig; ++i) big_hess_up(s, st, m, big_front(s, v, i), Wc, Vd, Y, ldy, T, ldt, ws);
@@ -783,10 +805,11 @@ void hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, co
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
     for (int i = 0; i < v.nbig; ++i) big_hess_down(s, st, m, big_front(s, v, i), Wc, T, ldt, ws);
-    if (v.nsmall) {
-      k_hess_down<<<dim3(v.nsmall, m), NT, 0, st>>>(s->dev, v.t0, Wc, T, ldt, ws);
+    if (v.ncta) {
+      k_hess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, T, ldt, ws);
       count();
     }
+    if (v.nwarp) warp_hess_down(s, st, v.t0, v.nwarp, m, Wc, T, ldt, ws);
   }
 }
 void inv_hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Dd,
@@ -795,15 +818,17 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
     for (int i = 0; i < v.nbig; ++i) big_ihess_down(s, st, m, big_front(s, v, i), Wc, Dd, Rd, T, ldt, Y, ldy, ws);
-    if (v.nsmall) {
-      k_ihess_down<<<dim3(v.nsmall, m), NT, 0, st>>>(s->dev, v.t0, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    if (v.ncta) {
+      k_ihess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
       count();
     }
+    if (v.nwarp) warp_ihess_down(s, st, v.t0, v.nwarp, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
   }
   for (int l = 0; l < nl; ++l) {
     Level v = level(s, l);
-    if (v.nsmall) {
-      k_ihess_up<<<dim3(v.nsmall, m), NT, 0, st>>>(s->dev, v.t0, Wc, Y, ldy, ws);
+    if (v.nwarp) warp_ihess_up(s, st, v.t0, v.nwarp, m, Wc, Y, ldy, ws);
+    if (v.ncta) {
+      k_ihess_up<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Y, ldy, ws);
       count();
     }
     for (int i = 0; i < v.nbig; ++i) big_ihess_up(s, st, m, big_front(s, v, i), Wc, Y, ldy, ws);
@@ -815,10 +840,11 @@ void complete(const chd_symbolic* s, cudaStream_t st, const double* Sin, double*
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
     for (int i = 0; i < v.nbig; ++i) big_complete(s, st, big_front(s, v, i), Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
-    if (v.nsmall) {
-      k_complete<<<v.nsmall, NT, 0, st>>>(s->dev, v.t0, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+    if (v.ncta) {
+      k_complete<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
       count();
     }
+    if (v.nwarp) warp_complete(s, st, v.t0, v.nwarp, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
   }
 }
 void big_chol_v(const chd_symbolic* s, cudaStream_t st, int k, const double* Vd, double* Rd, int64_t* status);

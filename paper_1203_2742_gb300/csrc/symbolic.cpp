@@ -422,50 +422,52 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     s->flops[4] += da * da * da / 3 + da * da * dn + da * dn * dn + dn * dn * dn;
   }
 
-  // ---- schedule: subtree tasks at the bottom, chains of large fronts on top
-  // Work estimate per front: Hessian flops plus a fixed per-front latency
-  // cost; a subtree whose total work is at most total/(4*152) becomes one
-  // task processed by one CTA in postorder (tree parallelism, §8).  The
-  // remaining fronts form single-child chains, one task each, grouped into
-  // launches by level.
+  // ---- schedule -------------------------------------------------------------
+  // Each front gets a tier: warp (|J| <= 32 and |N| <= 8, one warp per front),
+  // CTA (one 256-thread CTA per front) or dense (|J| >= big_rows or
+  // |N| >= big_cols, multi-CTA sequence).  Maximal subtrees of warp-tier
+  // fronts whose total work is at most total/(8*152) become single-warp
+  // tasks processed in postorder (tree parallelism, §8); the fronts above
+  // form chains (a front joins its only such child when both have the same
+  // tier, dense fronts never chain), one task each.  A task's level exceeds
+  // the levels of the tasks it depends on; every level is launched as one
+  // warp-tier kernel, one CTA-tier kernel and one dense sequence per front.
   {
-    vector<double> w(nsn), W(nsn, 0.0);
-    double total = 0;
-    for (int64_t t = 0; t < nsn; ++t) {
-      int64_t nn = s->sn_ptr[t + 1] - s->sn_ptr[t];
-      int64_t a = (s->rows_ptr[t + 1] - s->rows_ptr[t]) - nn;
-      double dn = (double)nn, da = (double)a;
-      w[t] = 6 * da * da * dn + 8 * da * dn * dn + 2 * dn * dn * dn + 5.0e4;
-    }
-    for (int64_t t = 0; t < nsn; ++t) {  // children precede parents
-      W[t] += w[t];
-      if (s->sn_par[t] >= 0) W[s->sn_par[t]] += W[t];
-      if (s->sn_par[t] < 0) total += W[t];
-    }
-    const double thr = total / (4.0 * 152.0);
-    // Big fronts (dense tier): J >= big_rows or n >= big_cols.
     const int64_t big_rows = opts.big_rows > 0 ? opts.big_rows : 320;
     const int64_t big_cols = opts.big_cols > 0 ? opts.big_cols : 160;
     s->is_big.assign(nsn, 0);
+    vector<int> tier(nsn, 1);
     for (int64_t t = 0; t < nsn; ++t) {
       int64_t nn = s->sn_ptr[t + 1] - s->sn_ptr[t];
       int64_t J = s->rows_ptr[t + 1] - s->rows_ptr[t];
       s->is_big[t] = (J >= big_rows || nn >= big_cols) ? 1 : 0;
+      tier[t] = s->is_big[t] ? 2 : ((J <= 32 && nn <= 8) ? 0 : 1);
     }
+    s->tier.assign(tier.begin(), tier.end());
     s->small_fronts.clear();
     for (int64_t t = 0; t < nsn; ++t)
       if (!s->is_big[t]) s->small_fronts.push_back((int32_t)t);
+    vector<double> W(nsn, 0.0);
+    double total = 0;
+    for (int64_t t = 0; t < nsn; ++t) {  // children precede parents
+      int64_t nn = s->sn_ptr[t + 1] - s->sn_ptr[t];
+      int64_t a = (s->rows_ptr[t + 1] - s->rows_ptr[t]) - nn;
+      double dn = (double)nn, da = (double)a;
+      W[t] += 6 * da * da * dn + 8 * da * dn * dn + 2 * dn * dn * dn + (tier[t] == 0 ? 2.0e4 : 5.0e4);
+      if (s->sn_par[t] >= 0) W[s->sn_par[t]] += W[t];
+      else total += W[t];
+    }
+    const double thr = total / (8.0 * 152.0);
     vector<char> top(nsn, 0);
-    for (int64_t t = 0; t < nsn; ++t) top[t] = W[t] > thr || s->is_big[t];
-    // every ancestor of a top front is a top front
-    for (int64_t t = 0; t < nsn; ++t)
+    for (int64_t t = 0; t < nsn; ++t) top[t] = W[t] > thr || tier[t] != 0;
+    for (int64_t t = 0; t < nsn; ++t)  // ancestors of top fronts are top fronts
       if (top[t] && s->sn_par[t] >= 0) top[s->sn_par[t]] = 1;
     vector<int64_t> task_of(nsn, -1);
     vector<vector<int32_t>> tasks;
     vector<int64_t> tlevel;
-    // Supernode numbering is a postorder of the clique tree (children
-    // precede parents and subtrees are contiguous), so the subtree of t is
-    // [t - size(t) + 1, t].
+    vector<int> ttier;
+    // Supernode numbering is a postorder of the clique tree (children precede
+    // parents, subtrees are contiguous), so the subtree of t is [t - size(t) + 1, t].
     vector<int64_t> sub(nsn, 1);
     for (int64_t t = 0; t < nsn; ++t)
       if (s->sn_par[t] >= 0) sub[s->sn_par[t]] += sub[t];
@@ -477,30 +479,25 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
       for (int64_t u = t - sub[t] + 1; u <= t; ++u) { seq.push_back((int32_t)u); task_of[u] = (int64_t)tasks.size(); }
       tasks.push_back(seq);
       tlevel.push_back(0);
+      ttier.push_back(0);
     }
-    // top fronts: a top front with exactly one top child joins that child's task
     vector<int64_t> ntopkids(nsn, 0), onlykid(nsn, -1);
     for (int64_t t = 0; t < nsn; ++t)
       if (top[t] && s->sn_par[t] >= 0) { ntopkids[s->sn_par[t]]++; onlykid[s->sn_par[t]] = t; }
     for (int64_t t = 0; t < nsn; ++t) {
       if (!top[t]) continue;
-      int64_t lvl = 1;
-      for (int64_t q = s->ch_ptr[t]; q < s->ch_ptr[t + 1]; ++q) {
-        int64_t c = s->ch[q];
-        if (top[c]) lvl = std::max(lvl, tlevel[task_of[c]] + 1);
-      }
-      if (ntopkids[t] == 1 && !s->is_big[t] && !s->is_big[onlykid[t]]) {
+      if (ntopkids[t] == 1 && tier[t] != 2 && tier[onlykid[t]] == tier[t]) {
         int64_t tk = task_of[onlykid[t]];
         tasks[tk].push_back((int32_t)t);
         task_of[t] = tk;
-        // level stays that of the chain's first front
       } else {
         task_of[t] = (int64_t)tasks.size();
         tasks.push_back({(int32_t)t});
-        tlevel.push_back(lvl);
+        tlevel.push_back(1);
+        ttier.push_back(tier[t]);
       }
     }
-    // a chain task's level must exceed the levels of all tasks it depends on
+    // a task's level must exceed the levels of all tasks it depends on
     bool changed = true;
     while (changed) {
       changed = false;
@@ -519,20 +516,21 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     s->task_ptr.assign(1, 0);
     s->task_fronts.clear();
     s->lvl_ptr.assign(1, 0);
+    s->lvl_warp.clear();
     s->lvl_big.clear();
     for (int64_t l = 0; l < nlev; ++l) {
-      int32_t nbig = 0;
-      for (int pass = 0; pass < 2; ++pass) {  // small tasks first, big fronts last
+      int32_t cnt[3] = {0, 0, 0};
+      for (int tr = 0; tr < 3; ++tr) {  // warp tasks, then CTA tasks, then dense fronts
         for (int64_t q : bylev[l]) {
-          const bool big = tasks[q].size() == 1 && s->is_big[tasks[q][0]];
-          if (big != (pass == 1)) continue;
+          if (ttier[q] != tr) continue;
           for (int32_t f : tasks[q]) s->task_fronts.push_back(f);
           s->task_ptr.push_back((int32_t)s->task_fronts.size());
-          nbig += big ? 1 : 0;
+          cnt[tr]++;
         }
       }
       s->lvl_ptr.push_back((int32_t)(s->task_ptr.size() - 1));
-      s->lvl_big.push_back(nbig);
+      s->lvl_warp.push_back(cnt[0]);
+      s->lvl_big.push_back(cnt[2]);
     }
   }
   return CHD_OK;
