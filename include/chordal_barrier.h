@@ -232,6 +232,38 @@ chd_status chd_probe_fp64_peak(void* stream, double* gflops);
 
 void chd_factor_free(chd_factor* fac);
 
+/*
+ * Hessian products that allocate nothing.  The paper has no counterpart:
+ * this is a service entry point of the library.
+ *
+ * For callers that cannot let a library call cudaMalloc while they run:
+ * programs whose device memory is all handed out by their own allocator
+ * (a framework's caching pool, or one arena reserved at start-up), and
+ * services that forbid allocator calls after warm-up because such calls can
+ * block or fragment memory.  It computes the same T_i = P(X^{-1} Y_i X^{-1})
+ * as chd_hessian with the same kernels, but the per-front workspace is a
+ * fixed device array of 2 Mi doubles (16 MiB) compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   fac     a factor whose projected inverse is already cached (call
+ *           chd_gradient or chd_hessian on it once before); it is read only
+ *   m, y_dev, ldy, t_dev, ldt   as for chd_hessian (device pointers, caller-owned)
+ *   stream  cudaStream_t as void*
+ * Returns CHD_ERR_INVALID when the projected inverse is not cached, or when
+ * m times the pattern's per-right-hand-side workspace exceeds the 2 Mi
+ * doubles (small and medium patterns fit; use chd_hessian otherwise);
+ * CHD_ERR_CUDA if a CUDA call fails.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ * Set-up: the first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.
+ * Sharing: all calls on a device share the one array and it keeps the
+ * contents of the last call; calls whose kernels overlap on the GPU (on
+ * different streams, or from several threads) race on it and give wrong
+ * results.  Serialise them, e.g. on one stream.
+ */
+chd_status chd_hessian_noalloc(chd_factor* fac, int m, const double* y_dev, int64_t ldy, double* t_dev,
+                               int64_t ldt, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,8 @@ _lib.chd_status_get.argtypes = [_p]
 _lib.chd_error_detail.argtypes = [_p, C.POINTER(_i64), C.POINTER(_i64)]
 _lib.chd_kernel_launches.argtypes = []
 _lib.chd_kernel_launches.restype = _i64
+_lib.chd_hessian_noalloc.argtypes = [_p, C.c_int, _p, _i64, _p, _i64, _p]
+_lib.chd_hessian_noalloc.restype = C.c_int
 _lib.chd_probe_fp64_peak.argtypes = [_p, C.POINTER(C.c_double)]
 _lib.chd_probe_fp64_peak.restype = C.c_int
 _lib.chd_factor_free.argtypes = [_p]
@@ -202,6 +204,16 @@ def chd_hessian(fac, y, t, nnz, stream=None):
         raise ValueError("y and t batch sizes differ")
     _check(_lib.chd_hessian(fac, m, _dptr(y, "y"), ldy, _dptr(t, "t"), ldt, _stream_ptr(stream)),
            "chd_hessian")
+
+
+def chd_hessian_noalloc(fac, y, t, nnz, stream=None):
+    """Hessian products with the library's fixed workspace (no allocation)."""
+    m, ldy = _batch(y, nnz, "y")
+    m2, ldt = _batch(t, nnz, "t")
+    if m != m2:
+        raise ValueError("y and t batch sizes differ")
+    _check(_lib.chd_hessian_noalloc(fac, m, _dptr(y, "y"), ldy, _dptr(t, "t"), ldt, _stream_ptr(stream)),
+           "chd_hessian_noalloc")
 
 
 def chd_inv_hessian(fac, t, y, nnz, stream=None):

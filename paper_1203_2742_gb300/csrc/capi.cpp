@@ -29,24 +29,6 @@ void export_ldl(const chd_symbolic* s, cudaStream_t st, const double* Lc, double
 cudaError_t fp64_peak(cudaStream_t st, double* gflops);
 }  // namespace chd_launch
 
-struct chd_factor {
-  chd_symbolic* sym = nullptr;
-  cudaStream_t stream = nullptr;
-  void* block = nullptr;  // one allocation holding everything below but ws
-  double* Lc = nullptr;
-  double* Wc = nullptr;
-  double* Sc = nullptr;
-  double* Dd = nullptr;
-  double* Vd = nullptr;
-  double* Rd = nullptr;
-  double* ldet = nullptr;
-  double* scalar = nullptr;  // [0] log det
-  int64_t* status = nullptr; // [0] code, [1] supernode, [2] column
-  double* ws = nullptr;      // per-right-hand-side front workspace
-  int64_t ws_rhs = 0;        // capacity in right-hand sides
-  bool have_S = false;
-  bool have_R = false;
-};
 
 namespace {
 

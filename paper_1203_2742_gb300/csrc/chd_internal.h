@@ -2,6 +2,8 @@
 // CUDA kernels of the chordal log-det barrier library.
 #pragma once
 
+#include <cuda_runtime_api.h>
+
 #include <cstdint>
 #include <vector>
 
@@ -61,6 +63,27 @@ struct chd_symbolic {
   SymDev dev;
   void* dev_buf = nullptr;
   int dev_id = -1;
+};
+
+// A factor object: device-resident factor blocks, cached projected inverse
+// and the per-right-hand-side front workspace (all owned by the object).
+struct chd_factor {
+  chd_symbolic* sym = nullptr;
+  cudaStream_t stream = nullptr;
+  void* block = nullptr;  // one allocation holding everything below but ws
+  double* Lc = nullptr;
+  double* Wc = nullptr;
+  double* Sc = nullptr;
+  double* Dd = nullptr;
+  double* Vd = nullptr;
+  double* Rd = nullptr;
+  double* ldet = nullptr;
+  double* scalar = nullptr;  // [0] log det
+  int64_t* status = nullptr; // [0] code, [1] supernode, [2] column
+  double* ws = nullptr;      // per-right-hand-side front workspace
+  int64_t ws_rhs = 0;        // capacity in right-hand sides
+  bool have_S = false;
+  bool have_R = false;
 };
 
 // Host helpers implemented in symbolic.cpp
