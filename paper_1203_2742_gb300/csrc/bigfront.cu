@@ -34,62 +34,86 @@ __device__ __forceinline__ V shifted(V v, int64_t off) {
   return v;
 }
 
+// Launch context of the dense tier: the stream, and a scratch buffer for
+// split-K partial products (may be absent: then no split).
+struct Ctx {
+  cudaStream_t s;
+  double* xs;
+  int64_t cap;  // doubles
+  operator cudaStream_t() const { return s; }
+};
+
 // ---------------------------------------------------------------------------
 // batched tiled GEMM: C = beta*C + alpha*A(MxK)*B(KxN), lower triangle only
-// if `lower`.  64x64 tiles, 4x4 outputs per thread, k-chunks of 16 in shared
-// memory.  beta == 0 never reads C.
+// if `lower`.  BM x BN output tiles, TM x TN outputs per thread (256
+// threads), k-chunks of up to 16 in shared memory, the k loop runs over the
+// real K only.  The tile shape follows the output shape (skinny products do
+// not pay for padding).  With nsplit > 1 the CTA (tile, split, batch)
+// computes the K range of its split and writes the raw partial tile to
+// `part`; mk_gemm_reduce then sums the splits in a fixed order.
 // ---------------------------------------------------------------------------
-template <class MA, class MB, class MC>
+template <int BM, int BN, int TM, int TN, class MA, class MB, class MC>
 __global__ void __launch_bounds__(BT) mk_gemm(int M, int N, int K, double alpha, MA A, int64_t sA, MB B,
-                                              int64_t sB, double beta, MC C, int64_t sC, int lower,
-                                              int tiles_n) {
-  const int tm = (blockIdx.x / tiles_n) * GT, tn = (blockIdx.x % tiles_n) * GT;
-  if (lower && tn >= tm + GT) return;
+                                              int64_t sB, double beta, MC C, int64_t sC, int lower, int tiles_n,
+                                              int nsplit, double* part) {
+  constexpr int HX = BN / TN, HY = BM / TM;
+  static_assert(HX * HY == BT, "thread layout");
+  const int tile = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
+  const int tm = (tile / tiles_n) * BM, tn = (tile % tiles_n) * BN;
+  if (lower && tn >= tm + BM) return;
   const int64_t z = blockIdx.z;
   A.p += z * sA;
   B.p += z * sB;
   C.p += z * sC;
-  __shared__ double As[GK][GT];
-  __shared__ double Bs[GK][GT + 1];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  double acc[4][4];
+  __shared__ double As[GK * 128];
+  __shared__ double Bs[GK * 128];
+  const int tid = threadIdx.x, tx = tid % HX, ty = tid / HX;
+  const int kper = ((K + nsplit - 1) / nsplit + GK - 1) / GK * GK;
+  const int kbeg = split * kper, kend = min(K, kbeg + kper);
+  double acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (int k0 = 0; k0 < K; k0 += GK) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = tid + q * BT;
-      const int r = e % GT, k = e / GT;
-      As[k][r] = (tm + r < M && k0 + k < K) ? A.at(tm + r, k0 + k) : 0.0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+  for (int k0 = kbeg; k0 < kend; k0 += GK) {
+    const int kc = min(GK, kend - k0);
+    for (int e = tid; e < BM * kc; e += BT) {
+      const int r = e % BM, k = e / BM;
+      As[k * BM + r] = (tm + r < M) ? A.at(tm + r, k0 + k) : 0.0;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = tid + q * BT;
-      const int k = e % GK, c = e / GK;
-      Bs[k][c] = (k0 + k < K && tn + c < N) ? B.at(k0 + k, tn + c) : 0.0;
+    for (int e = tid; e < BN * kc; e += BT) {
+      const int k = e % kc, c = e / kc;
+      Bs[k * BN + c] = (tn + c < N) ? B.at(k0 + k, tn + c) : 0.0;
     }
     __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < kc; ++k) {
+      double a[TM], bb[TN];
 #pragma unroll
-    for (int k = 0; k < GK; ++k) {
-      double a[4], b[4];
+      for (int i = 0; i < TM; ++i) a[i] = As[k * BM + ty + HY * i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+      for (int j = 0; j < TN; ++j) bb[j] = Bs[k * BN + tx + HX * j];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
     }
     __syncthreads();
   }
+  if (nsplit > 1) {
+    const int tiles = gridDim.x / nsplit;
+    double* P = part + (((int64_t)z * nsplit + split) * tiles + tile) * (BM * BN);
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = tm + ty + 16 * i, c = tn + tx + 16 * j;
+      for (int j = 0; j < TN; ++j) P[(ty + HY * i) + (tx + HX * j) * BM] = acc[i][j];
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int r = tm + ty + HY * i, c = tn + tx + HX * j;
       if (r < M && c < N && (!lower || r >= c)) {
         double v = alpha * acc[i][j];
         if (beta != 0.0) v = fma(beta, C.at(r, c), v);
@@ -98,13 +122,61 @@ __global__ void __launch_bounds__(BT) mk_gemm(int M, int N, int K, double alpha,
     }
 }
 
+// Sum of the split partial tiles in split order, then C = beta*C + alpha*sum.
+template <int BM, int BN, class MC>
+__global__ void __launch_bounds__(BT) mk_gemm_reduce(int M, int N, double alpha, double beta, MC C, int64_t sC,
+                                                     int lower, int tiles_n, int tiles, int nsplit,
+                                                     const double* part) {
+  const int tile = blockIdx.x;
+  const int tm = (tile / tiles_n) * BM, tn = (tile % tiles_n) * BN;
+  if (lower && tn >= tm + BM) return;
+  const int64_t z = blockIdx.z;
+  C.p += z * sC;
+  for (int e = threadIdx.x; e < BM * BN; e += BT) {
+    const int lr = e % BM, lc = e / BM;
+    const int r = tm + lr, c = tn + lc;
+    if (r >= M || c >= N || (lower && r < c)) continue;
+    double acc = 0.0;
+    for (int s = 0; s < nsplit; ++s) acc += part[(((int64_t)z * nsplit + s) * tiles + tile) * (BM * BN) + e];
+    double v = alpha * acc;
+    if (beta != 0.0) v = fma(beta, C.at(r, c), v);
+    C.at(r, c) = v;
+  }
+}
+
+template <int BM, int BN, int TM, int TN, class MA, class MB, class MC>
+void gemm_cfg(const Ctx& st, int batch, int M, int N, int K, double alpha, MA A, int64_t sA, MB B, int64_t sB,
+              double beta, MC C, int64_t sC, bool lower) {
+  const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  const int tiles = tm * tn;
+  // split K when the tiles alone cannot fill the GPU and K is long
+  int nsplit = 1;
+  const int64_t ctas = (int64_t)tiles * batch;
+  if (st.xs && ctas < 2 * 152 && K >= 256) {
+    nsplit = (int)std::min<int64_t>((2 * 152 + ctas - 1) / ctas, K / 128);
+    const int64_t need = (int64_t)batch * tiles * (BM * BN);
+    nsplit = (int)std::min<int64_t>(nsplit, need > 0 ? st.cap / need : 1);
+    if (nsplit < 2) nsplit = 1;
+  }
+  mk_gemm<BM, BN, TM, TN><<<dim3(tiles * nsplit, 1, batch), BT, 0, st>>>(
+      M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower ? 1 : 0, tn, nsplit, st.xs);
+  chd_launch::count_launch();
+  if (nsplit > 1) {
+    mk_gemm_reduce<BM, BN><<<dim3(tiles, 1, batch), BT, 0, st>>>(M, N, alpha, beta, C, sC, lower ? 1 : 0, tn,
+                                                                  tiles, nsplit, st.xs);
+    chd_launch::count_launch();
+  }
+}
+
 template <class MA, class MB, class MC>
-void gemm(cudaStream_t st, int batch, int M, int N, int K, double alpha, MA A, int64_t sA, MB B, int64_t sB,
+void gemm(const Ctx& st, int batch, int M, int N, int K, double alpha, MA A, int64_t sA, MB B, int64_t sB,
           double beta, MC C, int64_t sC, bool lower) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
-  const int tm = (M + GT - 1) / GT, tn = (N + GT - 1) / GT;
-  mk_gemm<<<dim3(tm * tn, 1, batch), BT, 0, st>>>(M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower ? 1 : 0, tn);
-  chd_launch::count_launch();
+  if (N <= 8 && M > 64) gemm_cfg<128, 8, 4, 1>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
+  else if (N <= 16 && M > 64) gemm_cfg<128, 16, 4, 2>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
+  else if (M <= 8 && N > 64) gemm_cfg<8, 128, 1, 4>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
+  else if (M <= 16 && N > 64) gemm_cfg<16, 128, 2, 4>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
+  else gemm_cfg<64, 64, 4, 4>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
 }
 
 // ---------------------------------------------------------------------------
@@ -202,7 +274,7 @@ __global__ void __launch_bounds__(BT) mk_trsm_panel(int R, MB B, int64_t sB, int
 constexpr size_t kPanelSmem = sizeof(double) * (PW * (PW + 1) + RB * (PW + 1));
 
 template <class MB>
-void panel_solve(cudaStream_t st, int batch, int R, MB B, int64_t sB, int p0, int pb, const double* L,
+void panel_solve(const Ctx& st, int batch, int R, MB B, int64_t sB, int p0, int pb, const double* L,
                  int64_t ld, int fwd) {
   static bool attr = false;
   if (!attr) {
@@ -219,7 +291,7 @@ __host__ __device__ inline DnTW colshift(DnTW v, int c0) { v.p += c0; return v; 
 
 // B := B L^{-T} (R x n view B, n x n lower L), blocked forward.
 template <class MB>
-void trsm_rLT(cudaStream_t st, int batch, int R, int n, MB B, int64_t sB, const double* L, int64_t ld) {
+void trsm_rLT(const Ctx& st, int batch, int R, int n, MB B, int64_t sB, const double* L, int64_t ld) {
   if (R <= 0 || n <= 0) return;
   for (int p0 = 0; p0 < n; p0 += PW) {
     const int pb = std::min(PW, n - p0);
@@ -232,7 +304,7 @@ void trsm_rLT(cudaStream_t st, int batch, int R, int n, MB B, int64_t sB, const 
 }
 // B := B L^{-1}, blocked backward.
 template <class MB>
-void trsm_rL(cudaStream_t st, int batch, int R, int n, MB B, int64_t sB, const double* L, int64_t ld) {
+void trsm_rL(const Ctx& st, int batch, int R, int n, MB B, int64_t sB, const double* L, int64_t ld) {
   if (R <= 0 || n <= 0) return;
   const int np = (n + PW - 1) / PW;
   for (int p = np - 1; p >= 0; --p) {
@@ -246,7 +318,7 @@ void trsm_rL(cudaStream_t st, int batch, int R, int n, MB B, int64_t sB, const d
 
 // Partial Cholesky of the first n columns of the J x J matrix F (ld): F11 =
 // C C^T, F21 := F21 C^{-T}, F22 -= F21 F21^T (lower).  Not batched.
-void potrf_partial(cudaStream_t st, double* F, int64_t ld, int J, int n, int64_t* status, int64_t code,
+void potrf_partial(const Ctx& st, double* F, int64_t ld, int J, int n, int64_t* status, int64_t code,
                    int64_t snode, int64_t col0) {
   for (int j0 = 0; j0 < n; j0 += PW) {
     const int jb = std::min(PW, n - j0);
@@ -427,19 +499,19 @@ inline Front front(const chd_symbolic* s, int k) {
   return f;
 }
 
-void assemble_children(const chd_symbolic* s, cudaStream_t st, int batch, int k, double* ws, int64_t sws) {
+void assemble_children(const chd_symbolic* s, const Ctx& st, int batch, int k, double* ws, int64_t sws) {
   if (s->ch_ptr[k + 1] == s->ch_ptr[k]) return;
   const int J = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k]);
   const int t = (J + GT - 1) / GT;
   mk_extend_add<<<dim3(t * t, 1, batch), BT, 0, st>>>(s->dev, k, ws, sws, t);
   chd_launch::count_launch();
 }
-void gather_parent(const chd_symbolic* s, cudaStream_t st, int batch, const Front& f, double* ws, int64_t sws) {
+void gather_parent(const chd_symbolic* s, const Ctx& st, int batch, const Front& f, double* ws, int64_t sws) {
   if (s->sn_par[f.k] < 0 || f.a == 0) return;
   CHD_EW(mk_gather_parent, (int64_t)f.a * f.a, batch, st, s->dev, f.k, ws, sws);
 }
 
-void factor_front(const chd_symbolic* s, cudaStream_t st, int k, const double* X, double* Lc, double* Wc,
+void factor_front(const chd_symbolic* s, const Ctx& st, int k, const double* X, double* Lc, double* Wc,
                   double* Dd, double* ws, double* ldet, int64_t* status) {
   Front f = front(s, k);
   const int J = f.J, n = f.n, a = f.a;
@@ -465,7 +537,7 @@ void factor_front(const chd_symbolic* s, cudaStream_t st, int k, const double* X
   CHD_EW(mk_front_to_csc, (int64_t)J * n, 1, st, Wc + f.base, 0, T2, 0, J, J, n, 0, J, 1.0);
 }
 
-void gradient_front(const chd_symbolic* s, cudaStream_t st, int k, const double* Wc, double* Sc, double* g,
+void gradient_front(const chd_symbolic* s, const Ctx& st, int k, const double* Wc, double* Sc, double* g,
                     double* Vd, double* ws) {
   Front f = front(s, k);
   const int J = f.J, n = f.n, a = f.a;
@@ -480,7 +552,7 @@ void gradient_front(const chd_symbolic* s, cudaStream_t st, int k, const double*
   if (a > 0) CHD_EW(mk_copy, (int64_t)a * a, 1, st, Vd + s->v_off[k], 0, a, F + n + (int64_t)n * J, 0, J, a, a, 1.0, 0.0, 1, 0);
 }
 
-void hess_up_front(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, const double* Vd,
+void hess_up_front(const chd_symbolic* s, const Ctx& st, int m, int k, const double* Wc, const double* Vd,
                    const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
   Front f = front(s, k);
   const int J = f.J, n = f.n, a = f.a;
@@ -508,7 +580,7 @@ void hess_up_front(const chd_symbolic* s, cudaStream_t st, int m, int k, const d
   }
 }
 
-void hess_down_front(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, double* T,
+void hess_down_front(const chd_symbolic* s, const Ctx& st, int m, int k, const double* Wc, double* T,
                      int64_t ldt, double* ws) {
   Front f = front(s, k);
   const int J = f.J, n = f.n, a = f.a;
@@ -529,7 +601,7 @@ void hess_down_front(const chd_symbolic* s, cudaStream_t st, int m, int k, const
   CHD_EW(mk_front_to_csc, (int64_t)J * n, m, st, T + f.base, ldt, F, sw, J, J, n, 0, J, 1.0);
 }
 
-void ihess_down_front(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, const double* Dd,
+void ihess_down_front(const chd_symbolic* s, const Ctx& st, int m, int k, const double* Wc, const double* Dd,
                       const double* Rd, const double* Tin, int64_t ldt, double* Yout, int64_t ldy, double* ws) {
   Front f = front(s, k);
   const int J = f.J, n = f.n, a = f.a;
@@ -552,16 +624,14 @@ void ihess_down_front(const chd_symbolic* s, cudaStream_t st, int m, int k, cons
   const double* D = Dd + s->d_off[k];
   gemm(st, m, n, n, n, 1.0, Dn{T1, J}, sw, SymL{D, n}, 0, 0.0, Dn{T2, J}, sw, false);
   gemm(st, m, n, n, n, 1.0, SymL{D, n}, 0, Dn{T2, J}, sw, 0.0, Csc{Yout + f.base, J, 0}, ldy, true);
-  if (a > 0) {
+  if (a > 0) {  // K_AN = V^{-1} (M_AN D), V^{-1} cached per factor
     gemm(st, m, a, n, n, 1.0, Dn{T1 + n, J}, sw, SymL{D, n}, 0, 0.0, Dn{T2 + n, J}, sw, false);
-    const double* R = Rd + s->v_off[k];
-    trsm_rLT(st, m, n, a, DnTW{T2 + n, J}, sw, R, a);
-    trsm_rL(st, m, n, a, DnTW{T2 + n, J}, sw, R, a);
-    CHD_EW(mk_front_to_csc, (int64_t)J * n, m, st, Yout + f.base, ldy, T2, sw, J, J, n, n, J, 1.0);
+    gemm(st, m, a, n, a, 1.0, SymL{Rd + s->v_off[k], a}, 0, Dn{T2 + n, J}, sw, 0.0, Csc{Yout + f.base, J, n}, ldy,
+         false);
   }
 }
 
-void ihess_up_front(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, double* Y,
+void ihess_up_front(const chd_symbolic* s, const Ctx& st, int m, int k, const double* Wc, double* Y,
                     int64_t ldy, double* ws) {
   Front f = front(s, k);
   const int J = f.J, n = f.n, a = f.a;
@@ -582,7 +652,7 @@ void ihess_up_front(const chd_symbolic* s, cudaStream_t st, int m, int k, const 
   CHD_EW(mk_ihess_finish, (int64_t)J * n, m, st, Y + f.base, ldy, F, T2, sw, J, n);
 }
 
-void complete_front(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* Lc, double* Wc,
+void complete_front(const chd_symbolic* s, const Ctx& st, int k, const double* Sin, double* Lc, double* Wc,
                     double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
   Front f = front(s, k);
   const int J = f.J, n = f.n, a = f.a;
@@ -627,42 +697,55 @@ void complete_front(const chd_symbolic* s, cudaStream_t st, int k, const double*
 }  // namespace chd
 
 namespace chd_launch {
-void big_factor(const chd_symbolic* s, cudaStream_t st, int k, const double* X, double* Lc, double* Wc,
-                double* Dd, double* ws, double* ldet, int64_t* status) {
-  chd::big::factor_front(s, st, k, X, Lc, Wc, Dd, ws, ldet, status);
+using chd::big::Ctx;
+void big_factor(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* X,
+                double* Lc, double* Wc, double* Dd, double* ws, double* ldet, int64_t* status) {
+  chd::big::factor_front(s, Ctx{st, xs, xcap}, k, X, Lc, Wc, Dd, ws, ldet, status);
 }
-void big_gradient(const chd_symbolic* s, cudaStream_t st, int k, const double* Wc, double* Sc, double* g,
-                  double* Vd, double* ws) {
-  chd::big::gradient_front(s, st, k, Wc, Sc, g, Vd, ws);
+void big_gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Wc,
+                  double* Sc, double* g, double* Vd, double* ws) {
+  chd::big::gradient_front(s, Ctx{st, xs, xcap}, k, Wc, Sc, g, Vd, ws);
 }
-void big_hess_up(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, const double* Vd,
-                 const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
-  chd::big::hess_up_front(s, st, m, k, Wc, Vd, Y, ldy, T, ldt, ws);
+void big_hess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
+                 const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
+  chd::big::hess_up_front(s, Ctx{st, xs, xcap}, m, k, Wc, Vd, Y, ldy, T, ldt, ws);
 }
-void big_hess_down(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, double* T, int64_t ldt,
-                   double* ws) {
-  chd::big::hess_down_front(s, st, m, k, Wc, T, ldt, ws);
+void big_hess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
+                   double* T, int64_t ldt, double* ws) {
+  chd::big::hess_down_front(s, Ctx{st, xs, xcap}, m, k, Wc, T, ldt, ws);
 }
-void big_ihess_down(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, const double* Dd,
-                    const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy, double* ws) {
-  chd::big::ihess_down_front(s, st, m, k, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+void big_ihess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k,
+                    const double* Wc, const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y,
+                    int64_t ldy, double* ws) {
+  chd::big::ihess_down_front(s, Ctx{st, xs, xcap}, m, k, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
 }
-void big_ihess_up(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, double* Y, int64_t ldy,
-                  double* ws) {
-  chd::big::ihess_up_front(s, st, m, k, Wc, Y, ldy, ws);
+void big_ihess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
+                  double* Y, int64_t ldy, double* ws) {
+  chd::big::ihess_up_front(s, Ctx{st, xs, xcap}, m, k, Wc, Y, ldy, ws);
 }
-void big_complete(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* Lc, double* Wc,
-                  double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
-  chd::big::complete_front(s, st, k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Sin,
+                  double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
+                  int64_t* status) {
+  chd::big::complete_front(s, Ctx{st, xs, xcap}, k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
 }
-// Cholesky factor of the cached V_k = S_{A_k A_k} of one big front.
-void big_chol_v(const chd_symbolic* s, cudaStream_t st, int k, const double* Vd, double* Rd, int64_t* status) {
+// Inverse of the cached V_k = S_{A_k A_k} of one big front: R = chol(V),
+// R^{-1} in the front's workspace, V^{-1} = R^{-T} R^{-1} (lower) into Rd.
+void big_inv_v(const chd_symbolic* s, cudaStream_t stream, double* xs, int64_t xcap, int k, const double* Vd,
+               double* Rd, double* ws, int64_t* status) {
   using namespace chd::big;
+  using chd::DnTW;
+  using chd::TriL;
+  using chd::TriLT;
+  const Ctx st{stream, xs, xcap};
   const int n = (int)(s->sn_ptr[k + 1] - s->sn_ptr[k]);
   const int a = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k]) - n;
   if (a == 0) return;
   double* R = Rd + s->v_off[k];
+  double* Ri = ws + s->f_off[k];
   CHD_EW(mk_copy, (int64_t)a * a, 1, st, R, 0, a, Vd + s->v_off[k], 0, a, a, a, 1.0, 0.0, 1, 0);
   potrf_partial(st, R, a, a, a, status, CHD_ERR_NOT_PD, k, -1);
+  CHD_EW(mk_identity, (int64_t)a * a, 1, st, Ri, a, a);
+  trsm_rLT(st, 1, a, a, DnTW{Ri, a}, 0, R, a);
+  gemm(st, 1, a, a, a, 1.0, TriLT{Ri, a}, 0, TriL{Ri, a}, 0, 0.0, chd::Dn{R, a}, 0, true);
 }
 }  // namespace chd_launch

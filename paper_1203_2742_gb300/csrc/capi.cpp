@@ -13,17 +13,19 @@
 
 namespace chd_launch {
 int64_t launches();
-void factor(const chd_symbolic* s, cudaStream_t st, const double* X, double* Lc, double* Wc,
-            double* Dd, double* ws, double* ldet, int64_t* status);
-void gradient(const chd_symbolic* s, cudaStream_t st, const double* Wc, double* Sc, double* g,
-              double* Vd, double* ws);
-void hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Vd,
-             const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
-void inv_hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Dd,
-                 const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy, double* ws);
-void complete(const chd_symbolic* s, cudaStream_t st, const double* Sin, double* Lc, double* Wc,
-              double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
-void chol_v(const chd_symbolic* s, cudaStream_t st, const double* Vd, double* Rd, int64_t* status);
+void factor(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* X, double* Lc,
+            double* Wc, double* Dd, double* ws, double* ldet, int64_t* status);
+void gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* Wc, double* Sc,
+              double* g, double* Vd, double* ws);
+void hessian(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, const double* Wc,
+             const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
+void inv_hessian(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, const double* Wc,
+                 const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy,
+                 double* ws);
+void complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* Sin, double* Lc,
+              double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
+void inv_v(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* Vd, double* Rd, double* ws,
+           int64_t* status);
 void sum(cudaStream_t st, const double* v, int64_t m, double* out);
 void export_ldl(const chd_symbolic* s, cudaStream_t st, const double* Lc, double* l, double* d);
 cudaError_t fp64_peak(cudaStream_t st, double* gflops);
@@ -37,6 +39,9 @@ namespace {
 constexpr size_t kWorkspaceCap = size_t(16) << 30;
 
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Split-K partial products of the dense tier: 4 Mi doubles (32 MiB) per factor.
+constexpr int64_t kSplitScratch = int64_t(4) << 20;
 
 chd_status cuda_ok(cudaError_t e) {
   if (e == cudaSuccess) return CHD_OK;
@@ -59,6 +64,7 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
   const size_t old = off; off = align_up(off + (size_t)s->nsn * 8);
   const size_t osc = off; off = align_up(off + 4 * 8);
   const size_t ost = off; off = align_up(off + 4 * 8);
+  const size_t oxs = off; off = align_up(off + (size_t)kSplitScratch * 8);
   void* block = nullptr;
   chd_status rc = cuda_ok(cudaMalloc(&block, off));
   if (rc != CHD_OK) { delete f; return rc; }
@@ -73,6 +79,8 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
   f->ldet = reinterpret_cast<double*>(b + old);
   f->scalar = reinterpret_cast<double*>(b + osc);
   f->status = reinterpret_cast<int64_t*>(b + ost);
+  f->xs = reinterpret_cast<double*>(b + oxs);
+  f->xs_cap = kSplitScratch;
   rc = cuda_ok(cudaMemsetAsync(f->status, 0, 4 * 8, stream));
   if (rc != CHD_OK) { cudaFree(block); delete f; return rc; }
   *out = f;
@@ -108,7 +116,7 @@ chd_status ensure_projected_inverse(chd_factor* f) {
   if (f->have_S) return CHD_OK;
   chd_status rc = ensure_ws(f, 1);
   if (rc != CHD_OK) return rc;
-  chd_launch::gradient(f->sym, f->stream, f->Wc, f->Sc, nullptr, f->Vd, f->ws);
+  chd_launch::gradient(f->sym, f->stream, f->xs, f->xs_cap, f->Wc, f->Sc, nullptr, f->Vd, f->ws);
   rc = launch_status();
   if (rc == CHD_OK) f->have_S = true;
   return rc;
@@ -209,7 +217,7 @@ chd_status chd_refactor(chd_factor* f, const double* x, void* stream) {
   f->have_S = f->have_R = false;
   rc = cuda_ok(cudaMemsetAsync(f->status, 0, 4 * 8, f->stream));
   if (rc != CHD_OK) return rc;
-  chd_launch::factor(f->sym, f->stream, x, f->Lc, f->Wc, f->Dd, f->ws, f->ldet, f->status);
+  chd_launch::factor(f->sym, f->stream, f->xs, f->xs_cap, x, f->Lc, f->Wc, f->Dd, f->ws, f->ldet, f->status);
   return launch_status();
 }
 
@@ -228,7 +236,7 @@ chd_status chd_gradient(chd_factor* f, double* g, void* stream) {
   f->stream = static_cast<cudaStream_t>(stream);
   chd_status rc = ensure_ws(f, 1);
   if (rc != CHD_OK) return rc;
-  chd_launch::gradient(f->sym, f->stream, f->Wc, f->Sc, g, f->Vd, f->ws);
+  chd_launch::gradient(f->sym, f->stream, f->xs, f->xs_cap, f->Wc, f->Sc, g, f->Vd, f->ws);
   rc = launch_status();
   if (rc == CHD_OK) f->have_S = true;
   return rc;
@@ -248,7 +256,7 @@ chd_status chd_hessian(chd_factor* f, int m, const double* y, int64_t ldy, doubl
   if (rc != CHD_OK) return rc;
   for (int64_t i = 0; i < m; i += chunk) {
     const int mc = (int)std::min<int64_t>(chunk, m - i);
-    chd_launch::hessian(f->sym, f->stream, mc, f->Wc, f->Vd, y + i * ldy, ldy, t + i * ldt, ldt, f->ws);
+    chd_launch::hessian(f->sym, f->stream, f->xs, f->xs_cap, mc, f->Wc, f->Vd, y + i * ldy, ldy, t + i * ldt, ldt, f->ws);
     rc = launch_status();
     if (rc != CHD_OK) return rc;
   }
@@ -264,18 +272,18 @@ chd_status chd_inv_hessian(chd_factor* f, int m, const double* t, int64_t ldt, d
   f->stream = static_cast<cudaStream_t>(stream);
   chd_status rc = ensure_projected_inverse(f);
   if (rc != CHD_OK) return rc;
-  if (!f->have_R) {
-    chd_launch::chol_v(f->sym, f->stream, f->Vd, f->Rd, f->status);
+  const int64_t chunk = rhs_chunk(f, m);
+  rc = ensure_ws(f, chunk);
+  if (rc != CHD_OK) return rc;
+  if (!f->have_R) {  // V_k^{-1} of every front, once per factor
+    chd_launch::inv_v(f->sym, f->stream, f->xs, f->xs_cap, f->Vd, f->Rd, f->ws, f->status);
     rc = launch_status();
     if (rc != CHD_OK) return rc;
     f->have_R = true;
   }
-  const int64_t chunk = rhs_chunk(f, m);
-  rc = ensure_ws(f, chunk);
-  if (rc != CHD_OK) return rc;
   for (int64_t i = 0; i < m; i += chunk) {
     const int mc = (int)std::min<int64_t>(chunk, m - i);
-    chd_launch::inv_hessian(f->sym, f->stream, mc, f->Wc, f->Dd, f->Rd, t + i * ldt, ldt, y + i * ldy,
+    chd_launch::inv_hessian(f->sym, f->stream, f->xs, f->xs_cap, mc, f->Wc, f->Dd, f->Rd, t + i * ldt, ldt, y + i * ldy,
                             ldy, f->ws);
     rc = launch_status();
     if (rc != CHD_OK) return rc;
@@ -292,11 +300,12 @@ chd_status chd_recomplete(chd_factor* f, const double* sv, void* stream, double*
   if (rc == CHD_OK)
     rc = cuda_ok(cudaMemcpyAsync(f->Sc, sv, (size_t)s->colptr[s->n] * 8, cudaMemcpyDeviceToDevice, f->stream));
   if (rc == CHD_OK) {
-    chd_launch::complete(s, f->stream, sv, f->Lc, f->Wc, f->Dd, f->Vd, f->Rd, f->ws, f->ldet, f->status);
+    chd_launch::complete(s, f->stream, f->xs, f->xs_cap, sv, f->Lc, f->Wc, f->Dd, f->Vd, f->Rd, f->ws, f->ldet, f->status);
     rc = launch_status();
   }
   if (rc != CHD_OK) return rc;
-  f->have_S = f->have_R = true;
+  f->have_S = true;
+  f->have_R = false;  // Rd holds chol(V_k) here; V_k^{-1} is formed on first use
   if (fstar) {
     double ld = 0;
     rc = chd_logdet(f, &ld);

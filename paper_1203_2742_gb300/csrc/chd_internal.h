@@ -76,11 +76,13 @@ struct chd_factor {
   double* Sc = nullptr;
   double* Dd = nullptr;
   double* Vd = nullptr;
-  double* Rd = nullptr;
+  double* Rd = nullptr;      // V_k^{-1} per front (lower), once have_R
   double* ldet = nullptr;
   double* scalar = nullptr;  // [0] log det
   int64_t* status = nullptr; // [0] code, [1] supernode, [2] column
   double* ws = nullptr;      // per-right-hand-side front workspace
+  double* xs = nullptr;      // split-K scratch of the dense tier
+  int64_t xs_cap = 0;        // doubles
   int64_t ws_rhs = 0;        // capacity in right-hand sides
   bool have_S = false;
   bool have_R = false;

@@ -17,7 +17,7 @@
 //   Wc  (CSC)  : [D_NN^{-1}; L_AN]
 //   Dd  (n x n): D_NN
 //   Vd  (a x a): V_k = S_{A_k A_k}  (Algorithm 7.2)
-//   Rd  (a x a): lower Cholesky factor of V_k (inverse Hessian, §5.3)
+//   Rd  (a x a): V_k^{-1} (lower triangle; inverse Hessian, §5.3)
 //   Sc  (CSC)  : S = P(X^{-1})
 #include <cuda_runtime.h>
 
@@ -34,44 +34,49 @@ constexpr int TK = 16;       // gemm k-chunk
 constexpr int PB = 32;       // potrf panel width
 constexpr int PCH = 96;      // rows per panel chunk staged in shared memory
 
-// Shared-memory staging buffers, declared once at namespace scope so that
-// every routine of a kernel uses the same 42 KB.
-__shared__ double sh_A[TK][TB + 1];
-__shared__ double sh_B[TK][TB + 1];
-__shared__ double sh_L[PB * (PB + 1)];
-__shared__ double sh_P[PCH * (PB + 1)];
+// Shared-memory staging pool, declared once at namespace scope so that every
+// routine of a kernel uses the same 34 KB: the GEMM stages its A and B
+// chunks at the start of the pool, the panel Cholesky its diagonal block and
+// row panel (never live at the same time as a GEMM's chunks).
+constexpr int GMAX = 128;  // largest GEMM tile side
+constexpr int POOL_GEMM = 2 * TK * GMAX;
+constexpr int POOL_POTRF = PB * (PB + 1) + PCH * (PB + 1);
+constexpr int POOL = POOL_GEMM > POOL_POTRF ? POOL_GEMM : POOL_POTRF;
+__shared__ double sh_pool[POOL];
 
 // ---------------------------------------------------------------------------
 // CTA GEMM:  C = beta*C + alpha * A(MxK) B(KxN), optionally lower triangle only.
-// 32x32 output tiles, k-chunks of 16 staged in shared memory, 2x2 outputs per
-// thread.  beta == 0 never reads C.
+// Output blocks of BM x BN (BM*BN = 1024, 2x2 outputs per thread) picked from
+// the shape so that skinny products do not pay for padding; k-chunks of up
+// to 16 staged in shared memory, the k loop runs only over real K.
+// beta == 0 never reads C.
 // ---------------------------------------------------------------------------
-template <class MA, class MB, class MC>
-__device__ void cta_gemm(int M, int N, int K, double alpha, MA A, MB B, double beta, MC C,
-                         bool lower) {
-  if (M <= 0 || N <= 0) return;
-  auto& As = sh_A;
-  auto& Bs = sh_B;
+template <int BM, int BN, class MA, class MB, class MC>
+__device__ void cta_gemm_t(int M, int N, int K, double alpha, MA A, MB B, double beta, MC C, bool lower) {
+  double* As = sh_pool;            // TK x BM
+  double* Bs = sh_pool + TK * GMAX;  // TK x BN
   const int tid = threadIdx.x;
-  const int tx = tid % 16, ty = tid / 16;
-  for (int tm = 0; tm < M; tm += TB) {
-    for (int tn = 0; tn < N; tn += TB) {
-      if (lower && tn >= tm + TB) continue;
+  constexpr int HX = BN / 2, HY = BM / 2;
+  const int tx = tid % HX, ty = tid / HX;
+  for (int tm = 0; tm < M; tm += BM) {
+    for (int tn = 0; tn < N; tn += BN) {
+      if (lower && tn >= tm + BM) continue;
       double c00 = 0, c01 = 0, c10 = 0, c11 = 0;
       for (int k0 = 0; k0 < K; k0 += TK) {
-        for (int e = tid; e < TB * TK; e += NT) {
-          int r = e % TB, k = e / TB;
-          As[k][r] = (tm + r < M && k0 + k < K) ? A.at(tm + r, k0 + k) : 0.0;
+        const int kc = min(TK, K - k0);
+        for (int e = tid; e < BM * kc; e += NT) {
+          const int r = e % BM, kk = e / BM;
+          As[kk * BM + r] = (tm + r < M) ? A.at(tm + r, k0 + kk) : 0.0;
         }
-        for (int e = tid; e < TB * TK; e += NT) {
-          int k = e % TK, c = e / TK;
-          Bs[k][c] = (k0 + k < K && tn + c < N) ? B.at(k0 + k, tn + c) : 0.0;
+        for (int e = tid; e < BN * kc; e += NT) {
+          const int kk = e % kc, c = e / kc;
+          Bs[kk * BN + c] = (tn + c < N) ? B.at(k0 + kk, tn + c) : 0.0;
         }
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < TK; ++k) {
-          double a0 = As[k][ty], a1 = As[k][ty + 16];
-          double b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
+#pragma unroll 4
+        for (int kk = 0; kk < kc; ++kk) {
+          const double a0 = As[kk * BM + ty], a1 = As[kk * BM + ty + HY];
+          const double b0 = Bs[kk * BN + tx], b1 = Bs[kk * BN + tx + HX];
           c00 = fma(a0, b0, c00);
           c01 = fma(a0, b1, c01);
           c10 = fma(a1, b0, c10);
@@ -84,7 +89,7 @@ __device__ void cta_gemm(int M, int N, int K, double alpha, MA A, MB B, double b
       for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          int r = tm + ty + 16 * i, c = tn + tx + 16 * j;
+          const int r = tm + ty + HY * i, c = tn + tx + HX * j;
           if (r < M && c < N && (!lower || r >= c)) {
             double v = alpha * acc[i][j];
             if (beta != 0.0) v = fma(beta, C.at(r, c), v);
@@ -94,6 +99,16 @@ __device__ void cta_gemm(int M, int N, int K, double alpha, MA A, MB B, double b
     }
   }
   __syncthreads();
+}
+
+template <class MA, class MB, class MC>
+__device__ void cta_gemm(int M, int N, int K, double alpha, MA A, MB B, double beta, MC C, bool lower) {
+  if (M <= 0 || N <= 0) return;
+  if (N <= 8 && M > 32) cta_gemm_t<128, 8>(M, N, K, alpha, A, B, beta, C, lower);
+  else if (N <= 16 && M > 32) cta_gemm_t<64, 16>(M, N, K, alpha, A, B, beta, C, lower);
+  else if (M <= 8 && N > 32) cta_gemm_t<8, 128>(M, N, K, alpha, A, B, beta, C, lower);
+  else if (M <= 16 && N > 32) cta_gemm_t<16, 64>(M, N, K, alpha, A, B, beta, C, lower);
+  else cta_gemm_t<32, 32>(M, N, K, alpha, A, B, beta, C, lower);
 }
 
 // ---------------------------------------------------------------------------
@@ -133,8 +148,8 @@ __device__ void smem_potrf(double* Ls, int jb, int64_t* st, int64_t code, int64_
 // ---------------------------------------------------------------------------
 __device__ void cta_potrf_partial(double* F, int64_t ld, int J, int n, int64_t* st, int64_t code,
                                   int64_t snode, int64_t col0) {
-  double* Ls = sh_L;
-  double* Ps = sh_P;
+  double* Ls = sh_pool;
+  double* Ps = sh_pool + PB * (PB + 1);
   const int tid = threadIdx.x;
   for (int j0 = 0; j0 < n; j0 += PB) {
     const int jb = min(PB, n - j0);
@@ -469,16 +484,10 @@ __device__ void ihess_down_front(const SymDev& S, int k, const double* Wc, const
   const double* D = Dd + S.d_off[k];
   cta_gemm(n, n, n, 1.0, Dn{f.T1, J}, SymL{D, n}, 0.0, Dn{f.T2, J}, false);
   cta_gemm(n, n, n, 1.0, SymL{D, n}, Dn{f.T2, J}, 0.0, Csc{Yout + f.base, J, 0}, true);
-  // K_AN = R^{-T} R^{-1} (M_AN D)
+  // K_AN = V^{-1} (M_AN D), with V^{-1} cached per factor
   if (a > 0) {
     cta_gemm(a, n, n, 1.0, Dn{f.T1 + n, J}, SymL{D, n}, 0.0, Dn{f.T2 + n, J}, false);
-    const double* R = Rd + S.v_off[k];
-    cta_trsm_rLT(n, a, DnTW{f.T2 + n, J}, R, a);  // (X^T R^{-T})^T = R^{-1} X
-    cta_trsm_rL(n, a, DnTW{f.T2 + n, J}, R, a);   // (X^T R^{-1})^T = R^{-T} X
-    for (int e = threadIdx.x; e < a * n; e += NT) {
-      int r = e % a, c = e / a;
-      Yout[f.base + csc_off(J, n + r, c)] = f.T2[n + r + (int64_t)c * J];
-    }
+    cta_gemm(a, n, a, 1.0, SymL{Rd + S.v_off[k], a}, Dn{f.T2 + n, J}, 0.0, Csc{Yout + f.base, J, n}, false);
   }
   __syncthreads();
 }
@@ -640,17 +649,23 @@ __global__ void __launch_bounds__(NT) k_complete(SymDev S, int task0, const doub
   for (int q = S.task_ptr[t + 1] - 1; q >= S.task_ptr[t]; --q)
     complete_front(S, S.task_fronts[q], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, st);
 }
-// Cholesky factors of the cached V_k, one CTA per front (no dependencies);
-// fronts listed in `skip` (big fronts) are done by the dense tier instead.
-__global__ void __launch_bounds__(NT) k_chol_v(SymDev S, const double* Vd, double* Rd, int64_t* st,
-                                               const int32_t* front_list) {
+// Inverses of the cached V_k (inverse Hessian step 2), one CTA per front of
+// `front_list` (no dependencies between fronts; big fronts use the dense
+// tier): R = chol(V), R^{-1} in the front's workspace, V^{-1} = R^{-T} R^{-1}.
+__global__ void __launch_bounds__(NT) k_inv_v(SymDev S, const double* Vd, double* Rd, double* ws, int64_t* st,
+                                              const int32_t* front_list) {
   const int k = front_list[blockIdx.x];
   const int n = (int)(S.sn_ptr[k + 1] - S.sn_ptr[k]);
   const int a = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]) - n;
   if (a == 0) return;
-  copy_lower(Rd + S.v_off[k], a, Vd + S.v_off[k], a, a);
+  double* R = Rd + S.v_off[k];
+  double* Ri = ws + S.f_off[k];  // a x a scratch inside the front's J x J region
+  copy_lower(R, a, Vd + S.v_off[k], a, a);
+  set_identity(Ri, a, a);
   __syncthreads();
-  cta_potrf_partial(Rd + S.v_off[k], a, a, a, st, CHD_ERR_NOT_PD, k, -1);
+  cta_potrf_partial(R, a, a, a, st, CHD_ERR_NOT_PD, k, -1);
+  cta_trsm_rLT(a, a, DnTW{Ri, a}, R, a);  // Ri = R^{-1}
+  cta_gemm(a, a, a, 1.0, TriLT{Ri, a}, TriL{Ri, a}, 0.0, Dn{R, a}, true);
 }
 // Deterministic sum of the per-front log det contributions.
 __global__ void k_sum(const double* v, int64_t m, double* out) {
@@ -712,21 +727,23 @@ void count_launch() { ++g_launches; }
 
 static inline void count() { ++g_launches; }
 
-// dense-tier sequences (bigfront.cu)
-void big_factor(const chd_symbolic* s, cudaStream_t st, int k, const double* X, double* Lc, double* Wc,
-                double* Dd, double* ws, double* ldet, int64_t* status);
-void big_gradient(const chd_symbolic* s, cudaStream_t st, int k, const double* Wc, double* Sc, double* g,
-                  double* Vd, double* ws);
-void big_hess_up(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, const double* Vd,
-                 const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
-void big_hess_down(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, double* T, int64_t ldt,
-                   double* ws);
-void big_ihess_down(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, const double* Dd,
-                    const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy, double* ws);
-void big_ihess_up(const chd_symbolic* s, cudaStream_t st, int m, int k, const double* Wc, double* Y, int64_t ldy,
-                  double* ws);
-void big_complete(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* Lc, double* Wc,
-                  double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
+// dense-tier sequences (bigfront.cu); xs/xcap: split-K scratch (may be null)
+void big_factor(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* X,
+                double* Lc, double* Wc, double* Dd, double* ws, double* ldet, int64_t* status);
+void big_gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Wc,
+                  double* Sc, double* g, double* Vd, double* ws);
+void big_hess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
+                 const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
+void big_hess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
+                   double* T, int64_t ldt, double* ws);
+void big_ihess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k,
+                    const double* Wc, const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y,
+                    int64_t ldy, double* ws);
+void big_ihess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
+                  double* Y, int64_t ldy, double* ws);
+void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Sin,
+                  double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
+                  int64_t* status);
 
 // warp-tier launches (warp_tier.cu)
 void warp_factor(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* X, double* Lc, double* Wc,
@@ -764,7 +781,7 @@ static inline int big_front(const chd_symbolic* s, const Level& v, int i) {
   return s->task_fronts[s->task_ptr[v.tc + v.ncta + i]];
 }
 
-void factor(const chd_symbolic* s, cudaStream_t st, const double* X, double* Lc, double* Wc, double* Dd,
+void factor(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* X, double* Lc, double* Wc, double* Dd,
             double* ws, double* ldet, int64_t* status) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = 0; l < nl; ++l) {
@@ -774,15 +791,15 @@ void factor(const chd_symbolic* s, cudaStream_t st, const double* X, double* Lc,
       k_factor<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, X, Lc, Wc, Dd, ws, ldet, status);
       count();
     }
-    for (int i = 0; i < v.nbig; ++i) big_factor(s, st, big_front(s, v, i), X, Lc, Wc, Dd, ws, ldet, status);
+    for (int i = 0; i < v.nbig; ++i) big_factor(s, st, xs, xcap, big_front(s, v, i), X, Lc, Wc, Dd, ws, ldet, status);
   }
 }
-void gradient(const chd_symbolic* s, cudaStream_t st, const double* Wc, double* Sc, double* g, double* Vd,
+void gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* Wc, double* Sc, double* g, double* Vd,
               double* ws) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
-    for (int i = 0; i < v.nbig; ++i) big_gradient(s, st, big_front(s, v, i), Wc, Sc, g, Vd, ws);
+    for (int i = 0; i < v.nbig; ++i) big_gradient(s, st, xs, xcap, big_front(s, v, i), Wc, Sc, g, Vd, ws);
     if (v.ncta) {
       k_gradient<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Wc, Sc, g, Vd, ws);
       count();
@@ -790,7 +807,7 @@ void gradient(const chd_symbolic* s, cudaStream_t st, const double* Wc, double* 
     if (v.nwarp) warp_gradient(s, st, v.t0, v.nwarp, Wc, Sc, g, Vd, ws);
   }
 }
-void hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Vd, const double* Y,
+void hessian(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, const double* Wc, const double* Vd, const double* Y,
              int64_t ldy, double* T, int64_t ldt, double* ws) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = 0; l < nl; ++l) {
@@ -800,11 +817,11 @@ void hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, co
       k_hess_up<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Vd, Y, ldy, T, ldt, ws);
       count();
     }
-    for (int i = 0; i < v.nbig; ++i) big_hess_up(s, st, m, big_front(s, v, i), Wc, Vd, Y, ldy, T, ldt, ws);
+    for (int i = 0; i < v.nbig; ++i) big_hess_up(s, st, xs, xcap, m, big_front(s, v, i), Wc, Vd, Y, ldy, T, ldt, ws);
   }
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
-    for (int i = 0; i < v.nbig; ++i) big_hess_down(s, st, m, big_front(s, v, i), Wc, T, ldt, ws);
+    for (int i = 0; i < v.nbig; ++i) big_hess_down(s, st, xs, xcap, m, big_front(s, v, i), Wc, T, ldt, ws);
     if (v.ncta) {
       k_hess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, T, ldt, ws);
       count();
@@ -812,12 +829,12 @@ void hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, co
     if (v.nwarp) warp_hess_down(s, st, v.t0, v.nwarp, m, Wc, T, ldt, ws);
   }
 }
-void inv_hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc, const double* Dd,
+void inv_hessian(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, const double* Wc, const double* Dd,
                  const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy, double* ws) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
-    for (int i = 0; i < v.nbig; ++i) big_ihess_down(s, st, m, big_front(s, v, i), Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    for (int i = 0; i < v.nbig; ++i) big_ihess_down(s, st, xs, xcap, m, big_front(s, v, i), Wc, Dd, Rd, T, ldt, Y, ldy, ws);
     if (v.ncta) {
       k_ihess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
       count();
@@ -831,15 +848,15 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, int m, const double* Wc
       k_ihess_up<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Y, ldy, ws);
       count();
     }
-    for (int i = 0; i < v.nbig; ++i) big_ihess_up(s, st, m, big_front(s, v, i), Wc, Y, ldy, ws);
+    for (int i = 0; i < v.nbig; ++i) big_ihess_up(s, st, xs, xcap, m, big_front(s, v, i), Wc, Y, ldy, ws);
   }
 }
-void complete(const chd_symbolic* s, cudaStream_t st, const double* Sin, double* Lc, double* Wc, double* Dd,
+void complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* Sin, double* Lc, double* Wc, double* Dd,
               double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
-    for (int i = 0; i < v.nbig; ++i) big_complete(s, st, big_front(s, v, i), Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+    for (int i = 0; i < v.nbig; ++i) big_complete(s, st, xs, xcap, big_front(s, v, i), Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
     if (v.ncta) {
       k_complete<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
       count();
@@ -847,14 +864,16 @@ void complete(const chd_symbolic* s, cudaStream_t st, const double* Sin, double*
     if (v.nwarp) warp_complete(s, st, v.t0, v.nwarp, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
   }
 }
-void big_chol_v(const chd_symbolic* s, cudaStream_t st, int k, const double* Vd, double* Rd, int64_t* status);
-void chol_v(const chd_symbolic* s, cudaStream_t st, const double* Vd, double* Rd, int64_t* status) {
+void big_inv_v(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Vd,
+               double* Rd, double* ws, int64_t* status);
+void inv_v(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* Vd, double* Rd, double* ws,
+           int64_t* status) {
   if (s->dev.small_count > 0) {
-    k_chol_v<<<(int)s->dev.small_count, NT, 0, st>>>(s->dev, Vd, Rd, status, s->dev.small_fronts);
+    k_inv_v<<<(int)s->dev.small_count, NT, 0, st>>>(s->dev, Vd, Rd, ws, status, s->dev.small_fronts);
     count();
   }
   for (int64_t k = 0; k < s->nsn; ++k)
-    if (s->is_big[k]) big_chol_v(s, st, (int)k, Vd, Rd, status);
+    if (s->is_big[k]) big_inv_v(s, st, xs, xcap, (int)k, Vd, Rd, ws, status);
 }
 void sum(cudaStream_t st, const double* v, int64_t m, double* out) {
   k_sum<<<1, NT, 0, st>>>(v, m, out);

@@ -464,16 +464,9 @@ __device__ void ihess_down_front(const SymDev& S, int k, const double* Wc, const
   wgemm(n, n, n, 1.0, Bk{m.D2, WN}, GSym{D, n}, 0.0, Bk{m.D1, WN}, false, lane);
   wgemm(n, n, n, 1.0, GSym{D, n}, Bk{m.D1, WN}, 0.0, CscOut{Y + f.base, J, 0}, true, lane);
   if (a > 0) {
-    // A3 = M_AN D ; K_AN = R^{-T} R^{-1} A3 -> Y
+    // A3 = M_AN D ; K_AN = V^{-1} A3 -> Y  (V^{-1} cached per factor)
     wgemm(a, n, n, 1.0, Bk{m.A2, WJ}, GSym{D, n}, 0.0, Bk{m.A3, WJ}, false, lane);
-    const double* R = Rd + S.v_off[k];
-    GL Rv{const_cast<double*>(R), a};
-    wtrsm_r(n, a, BkTW{m.A3, WJ}, Rv, true, lane);
-    wtrsm_r(n, a, BkTW{m.A3, WJ}, Rv, false, lane);
-    for (int e = lane; e < a * n; e += 32) {
-      const int r = e % a, c = e / a;
-      Y[f.base + pk(J, n + r, c)] = m.A3[r + c * WJ];
-    }
+    wgemm(a, n, a, 1.0, GSym{Rd + S.v_off[k], a}, Bk{m.A3, WJ}, 0.0, CscOut{Y + f.base, J, n}, false, lane);
   }
   write_full(f, m, lane);
   __syncwarp();
