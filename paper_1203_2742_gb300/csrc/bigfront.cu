@@ -652,6 +652,14 @@ void ihess_up_front(const chd_symbolic* s, const Ctx& st, int m, int k, const do
   CHD_EW(mk_ihess_finish, (int64_t)J * n, m, st, Y + f.base, ldy, F, T2, sw, J, n);
 }
 
+// S-front of a big front for the completion: V_k from the parent's front,
+// S_NN and S_AN from the input (top-down pass).
+void complete_load_front(const chd_symbolic* s, const Ctx& st, int k, const double* Sin, double* ws) {
+  Front f = front(s, k);
+  gather_parent(s, st, 1, f, ws, 0);
+  CHD_EW(mk_csc_to_front, (int64_t)f.J * f.n, 1, st, ws + f.foff, 0, f.J, f.n, Sin + f.base, 0);
+}
+
 void complete_front(const chd_symbolic* s, const Ctx& st, int k, const double* Sin, double* Lc, double* Wc,
                     double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
   Front f = front(s, k);
@@ -659,8 +667,8 @@ void complete_front(const chd_symbolic* s, const Ctx& st, int k, const double* S
   double* F = ws + f.foff;
   double* T1 = F + (int64_t)J * J;
   double* T2 = T1 + (int64_t)J * n;
-  gather_parent(s, st, 1, f, ws, 0);
-  CHD_EW(mk_csc_to_front, (int64_t)J * n, 1, st, F, 0, J, n, Sin + f.base, 0);
+  // the S-front F (S_NN, S_AN from the input, V_k gathered from the parent)
+  // was loaded by complete_load_front in the top-down pass
   double* V = Vd + s->v_off[k];
   double* R = Rd + s->v_off[k];
   if (a > 0) {
@@ -727,6 +735,9 @@ void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xc
                   double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
                   int64_t* status) {
   chd::big::complete_front(s, Ctx{st, xs, xcap}, k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+}
+void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* ws) {
+  chd::big::complete_load_front(s, Ctx{st, nullptr, 0}, k, Sin, ws);
 }
 // Inverse of the cached V_k = S_{A_k A_k} of one big front: R = chol(V),
 // R^{-1} in the front's workspace, V^{-1} = R^{-T} R^{-1} (lower) into Rd.

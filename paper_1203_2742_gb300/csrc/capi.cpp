@@ -13,18 +13,18 @@
 
 namespace chd_launch {
 int64_t launches();
-void factor(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* X, double* Lc,
+void factor(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* X, double* Lc,
             double* Wc, double* Dd, double* ws, double* ldet, int64_t* status);
-void gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* Wc, double* Sc,
+void gradient(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Wc, double* Sc,
               double* g, double* Vd, double* ws);
-void hessian(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, const double* Wc,
+void hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc,
              const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
-void inv_hessian(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, const double* Wc,
+void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc,
                  const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy,
                  double* ws);
-void complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* Sin, double* Lc,
+void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Sin, double* Lc,
               double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
-void inv_v(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* Vd, double* Rd, double* ws,
+void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* ws,
            int64_t* status);
 void sum(cudaStream_t st, const double* v, int64_t m, double* out);
 void export_ldl(const chd_symbolic* s, cudaStream_t st, const double* Lc, double* l, double* d);
@@ -40,8 +40,8 @@ constexpr size_t kWorkspaceCap = size_t(16) << 30;
 
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Split-K partial products of the dense tier: 4 Mi doubles (32 MiB) per factor.
-constexpr int64_t kSplitScratch = int64_t(4) << 20;
+// Split-K partial products of the dense tier: 2 Mi doubles (16 MiB) per stream.
+constexpr int64_t kSplitScratch = int64_t(2) << 20;
 
 chd_status cuda_ok(cudaError_t e) {
   if (e == cudaSuccess) return CHD_OK;
@@ -64,7 +64,13 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
   const size_t old = off; off = align_up(off + (size_t)s->nsn * 8);
   const size_t osc = off; off = align_up(off + 4 * 8);
   const size_t ost = off; off = align_up(off + 4 * 8);
-  const size_t oxs = off; off = align_up(off + (size_t)kSplitScratch * 8);
+  // split-K scratch: one slice per stream (caller's + side streams), only
+  // for patterns that have dense-tier fronts
+  bool any_big = false;
+  for (char b : s->is_big) any_big = any_big || b;
+  const int nside = any_big ? kSideStreams : 0;
+  const size_t oxs = off;
+  if (any_big) off = align_up(off + (size_t)kSplitScratch * (nside + 1) * 8);
   void* block = nullptr;
   chd_status rc = cuda_ok(cudaMalloc(&block, off));
   if (rc != CHD_OK) { delete f; return rc; }
@@ -79,8 +85,20 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
   f->ldet = reinterpret_cast<double*>(b + old);
   f->scalar = reinterpret_cast<double*>(b + osc);
   f->status = reinterpret_cast<int64_t*>(b + ost);
-  f->xs = reinterpret_cast<double*>(b + oxs);
-  f->xs_cap = kSplitScratch;
+  if (any_big) {
+    f->ex.xs = reinterpret_cast<double*>(b + oxs);
+    f->ex.xs_cap = kSplitScratch;
+    bool ok = cudaEventCreateWithFlags(&f->ex.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int j = 0; ok && j < nside; ++j) {
+      ok = cudaStreamCreateWithFlags(&f->ex.side[j], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&f->ex.join[j], cudaEventDisableTiming) == cudaSuccess;
+      if (ok) f->ex.nside = j + 1;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      f->ex.nside = 0;  // run every big front on the caller's stream
+    }
+  }
   rc = cuda_ok(cudaMemsetAsync(f->status, 0, 4 * 8, stream));
   if (rc != CHD_OK) { cudaFree(block); delete f; return rc; }
   *out = f;
@@ -116,7 +134,7 @@ chd_status ensure_projected_inverse(chd_factor* f) {
   if (f->have_S) return CHD_OK;
   chd_status rc = ensure_ws(f, 1);
   if (rc != CHD_OK) return rc;
-  chd_launch::gradient(f->sym, f->stream, f->xs, f->xs_cap, f->Wc, f->Sc, nullptr, f->Vd, f->ws);
+  chd_launch::gradient(f->sym, f->stream, &f->ex, f->Wc, f->Sc, nullptr, f->Vd, f->ws);
   rc = launch_status();
   if (rc == CHD_OK) f->have_S = true;
   return rc;
@@ -217,7 +235,7 @@ chd_status chd_refactor(chd_factor* f, const double* x, void* stream) {
   f->have_S = f->have_R = false;
   rc = cuda_ok(cudaMemsetAsync(f->status, 0, 4 * 8, f->stream));
   if (rc != CHD_OK) return rc;
-  chd_launch::factor(f->sym, f->stream, f->xs, f->xs_cap, x, f->Lc, f->Wc, f->Dd, f->ws, f->ldet, f->status);
+  chd_launch::factor(f->sym, f->stream, &f->ex, x, f->Lc, f->Wc, f->Dd, f->ws, f->ldet, f->status);
   return launch_status();
 }
 
@@ -236,7 +254,7 @@ chd_status chd_gradient(chd_factor* f, double* g, void* stream) {
   f->stream = static_cast<cudaStream_t>(stream);
   chd_status rc = ensure_ws(f, 1);
   if (rc != CHD_OK) return rc;
-  chd_launch::gradient(f->sym, f->stream, f->xs, f->xs_cap, f->Wc, f->Sc, g, f->Vd, f->ws);
+  chd_launch::gradient(f->sym, f->stream, &f->ex, f->Wc, f->Sc, g, f->Vd, f->ws);
   rc = launch_status();
   if (rc == CHD_OK) f->have_S = true;
   return rc;
@@ -256,7 +274,7 @@ chd_status chd_hessian(chd_factor* f, int m, const double* y, int64_t ldy, doubl
   if (rc != CHD_OK) return rc;
   for (int64_t i = 0; i < m; i += chunk) {
     const int mc = (int)std::min<int64_t>(chunk, m - i);
-    chd_launch::hessian(f->sym, f->stream, f->xs, f->xs_cap, mc, f->Wc, f->Vd, y + i * ldy, ldy, t + i * ldt, ldt, f->ws);
+    chd_launch::hessian(f->sym, f->stream, &f->ex, mc, f->Wc, f->Vd, y + i * ldy, ldy, t + i * ldt, ldt, f->ws);
     rc = launch_status();
     if (rc != CHD_OK) return rc;
   }
@@ -276,14 +294,14 @@ chd_status chd_inv_hessian(chd_factor* f, int m, const double* t, int64_t ldt, d
   rc = ensure_ws(f, chunk);
   if (rc != CHD_OK) return rc;
   if (!f->have_R) {  // V_k^{-1} of every front, once per factor
-    chd_launch::inv_v(f->sym, f->stream, f->xs, f->xs_cap, f->Vd, f->Rd, f->ws, f->status);
+    chd_launch::inv_v(f->sym, f->stream, &f->ex, f->Vd, f->Rd, f->ws, f->status);
     rc = launch_status();
     if (rc != CHD_OK) return rc;
     f->have_R = true;
   }
   for (int64_t i = 0; i < m; i += chunk) {
     const int mc = (int)std::min<int64_t>(chunk, m - i);
-    chd_launch::inv_hessian(f->sym, f->stream, f->xs, f->xs_cap, mc, f->Wc, f->Dd, f->Rd, t + i * ldt, ldt, y + i * ldy,
+    chd_launch::inv_hessian(f->sym, f->stream, &f->ex, mc, f->Wc, f->Dd, f->Rd, t + i * ldt, ldt, y + i * ldy,
                             ldy, f->ws);
     rc = launch_status();
     if (rc != CHD_OK) return rc;
@@ -300,7 +318,7 @@ chd_status chd_recomplete(chd_factor* f, const double* sv, void* stream, double*
   if (rc == CHD_OK)
     rc = cuda_ok(cudaMemcpyAsync(f->Sc, sv, (size_t)s->colptr[s->n] * 8, cudaMemcpyDeviceToDevice, f->stream));
   if (rc == CHD_OK) {
-    chd_launch::complete(s, f->stream, f->xs, f->xs_cap, sv, f->Lc, f->Wc, f->Dd, f->Vd, f->Rd, f->ws, f->ldet, f->status);
+    chd_launch::complete(s, f->stream, &f->ex, sv, f->Lc, f->Wc, f->Dd, f->Vd, f->Rd, f->ws, f->ldet, f->status);
     rc = launch_status();
   }
   if (rc != CHD_OK) return rc;
@@ -365,6 +383,12 @@ chd_status chd_probe_fp64_peak(void* stream, double* gflops) {
 void chd_factor_free(chd_factor* f) {
   if (!f) return;
   if (f->stream) cudaStreamSynchronize(f->stream);
+  for (int j = 0; j < f->ex.nside; ++j) {
+    cudaStreamSynchronize(f->ex.side[j]);
+    cudaStreamDestroy(f->ex.side[j]);
+    if (f->ex.join[j]) cudaEventDestroy(f->ex.join[j]);
+  }
+  if (f->ex.fork) cudaEventDestroy(f->ex.fork);
   if (f->ws) cudaFree(f->ws);
   if (f->block) cudaFree(f->block);
   delete f;

@@ -65,6 +65,20 @@ struct chd_symbolic {
   int dev_id = -1;
 };
 
+// Execution resources of the dense tier: side streams on which the big
+// fronts of one level run concurrently (forked from and joined back to the
+// caller's stream with events), and split-K scratch, one slice of xs_cap
+// doubles per stream (slice 0: the caller's stream).
+constexpr int kSideStreams = 8;
+struct Exec {
+  int nside = 0;
+  cudaStream_t side[kSideStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kSideStreams] = {};
+  double* xs = nullptr;
+  int64_t xs_cap = 0;
+};
+
 // A factor object: device-resident factor blocks, cached projected inverse
 // and the per-right-hand-side front workspace (all owned by the object).
 struct chd_factor {
@@ -81,8 +95,7 @@ struct chd_factor {
   double* scalar = nullptr;  // [0] log det
   int64_t* status = nullptr; // [0] code, [1] supernode, [2] column
   double* ws = nullptr;      // per-right-hand-side front workspace
-  double* xs = nullptr;      // split-K scratch of the dense tier
-  int64_t xs_cap = 0;        // doubles
+  Exec ex;                   // dense-tier streams and split-K scratch
   int64_t ws_rhs = 0;        // capacity in right-hand sides
   bool have_S = false;
   bool have_R = false;

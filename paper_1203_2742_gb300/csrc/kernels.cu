@@ -21,7 +21,9 @@
 //   Sc  (CSC)  : S = P(X^{-1})
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <vector>
 
 #include "chd_internal.h"
 #include "front_views.cuh"
@@ -762,6 +764,42 @@ void warp_ihess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m
 void warp_complete(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Sin, double* Lc,
                    double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
 
+
+// Runs body(i, stream, scratch, cap) for the `count` independent big fronts
+// of one level: on the caller's stream if there is one front or no side
+// streams, else round-robin over the side streams, forked after the work
+// already queued on `st` and joined back into `st` at `join_now` (the caller
+// may queue independent work on `st` in between).
+struct BigFork {
+  const Exec* ex;
+  cudaStream_t st;
+  int used = 0;
+  template <class Body>
+  void run(int count, Body&& body) {
+    if (count <= 0) return;
+    double* xs0 = ex ? ex->xs : nullptr;
+    const int64_t cap = ex ? ex->xs_cap : 0;
+    if (!ex || ex->nside == 0 || count == 1) {
+      for (int i = 0; i < count; ++i) body(i, st, xs0, cap);
+      return;
+    }
+    used = std::min(count, ex->nside);
+    cudaEventRecord(ex->fork, st);
+    for (int j = 0; j < used; ++j) cudaStreamWaitEvent(ex->side[j], ex->fork, 0);
+    for (int i = 0; i < count; ++i) {
+      const int j = i % used;
+      body(i, ex->side[j], ex->xs ? ex->xs + (int64_t)(1 + j) * cap : nullptr, cap);
+    }
+  }
+  void join_now() {
+    for (int j = 0; j < used; ++j) {
+      cudaEventRecord(ex->join[j], ex->side[j]);
+      cudaStreamWaitEvent(st, ex->join[j], 0);
+    }
+    used = 0;
+  }
+};
+
 // Level l holds tasks [t0, t0 + nwarp) of the warp tier, then [tc, tc + ncta)
 // of the CTA tier, then nbig single big fronts of the dense tier.
 struct Level {
@@ -781,99 +819,143 @@ static inline int big_front(const chd_symbolic* s, const Level& v, int i) {
   return s->task_fronts[s->task_ptr[v.tc + v.ncta + i]];
 }
 
-void factor(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* X, double* Lc, double* Wc, double* Dd,
-            double* ws, double* ldet, int64_t* status) {
+void factor(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* X, double* Lc, double* Wc,
+            double* Dd, double* ws, double* ldet, int64_t* status) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = 0; l < nl; ++l) {
     Level v = level(s, l);
+    BigFork bf{ex, st};
+    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
+      big_factor(s, bs, xs, xc, big_front(s, v, i), X, Lc, Wc, Dd, ws, ldet, status);
+    });
     if (v.nwarp) warp_factor(s, st, v.t0, v.nwarp, X, Lc, Wc, Dd, ws, ldet, status);
     if (v.ncta) {
       k_factor<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, X, Lc, Wc, Dd, ws, ldet, status);
       count();
     }
-    for (int i = 0; i < v.nbig; ++i) big_factor(s, st, xs, xcap, big_front(s, v, i), X, Lc, Wc, Dd, ws, ldet, status);
+    bf.join_now();
   }
 }
-void gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* Wc, double* Sc, double* g, double* Vd,
-              double* ws) {
+void gradient(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Wc, double* Sc, double* g,
+              double* Vd, double* ws) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
-    for (int i = 0; i < v.nbig; ++i) big_gradient(s, st, xs, xcap, big_front(s, v, i), Wc, Sc, g, Vd, ws);
+    BigFork bf{ex, st};
+    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
+      big_gradient(s, bs, xs, xc, big_front(s, v, i), Wc, Sc, g, Vd, ws);
+    });
     if (v.ncta) {
       k_gradient<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Wc, Sc, g, Vd, ws);
       count();
     }
     if (v.nwarp) warp_gradient(s, st, v.t0, v.nwarp, Wc, Sc, g, Vd, ws);
+    bf.join_now();
   }
 }
-void hessian(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, const double* Wc, const double* Vd, const double* Y,
-             int64_t ldy, double* T, int64_t ldt, double* ws) {
+void hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Vd,
+             const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = 0; l < nl; ++l) {
     Level v = level(s, l);
+    BigFork bf{ex, st};
+    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
+      big_hess_up(s, bs, xs, xc, m, big_front(s, v, i), Wc, Vd, Y, ldy, T, ldt, ws);
+    });
     if (v.nwarp) warp_hess_up(s, st, v.t0, v.nwarp, m, Wc, Vd, Y, ldy, T, ldt, ws);
     if (v.ncta) {
       k_hess_up<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Vd, Y, ldy, T, ldt, ws);
       count();
     }
-    for (int i = 0; i < v.nbig; ++i) big_hess_up(s, st, xs, xcap, m, big_front(s, v, i), Wc, Vd, Y, ldy, T, ldt, ws);
+    bf.join_now();
   }
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
-    for (int i = 0; i < v.nbig; ++i) big_hess_down(s, st, xs, xcap, m, big_front(s, v, i), Wc, T, ldt, ws);
+    BigFork bf{ex, st};
+    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
+      big_hess_down(s, bs, xs, xc, m, big_front(s, v, i), Wc, T, ldt, ws);
+    });
     if (v.ncta) {
       k_hess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, T, ldt, ws);
       count();
     }
     if (v.nwarp) warp_hess_down(s, st, v.t0, v.nwarp, m, Wc, T, ldt, ws);
+    bf.join_now();
   }
 }
-void inv_hessian(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, const double* Wc, const double* Dd,
+void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Dd,
                  const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy, double* ws) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
-    for (int i = 0; i < v.nbig; ++i) big_ihess_down(s, st, xs, xcap, m, big_front(s, v, i), Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    BigFork bf{ex, st};
+    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
+      big_ihess_down(s, bs, xs, xc, m, big_front(s, v, i), Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    });
     if (v.ncta) {
       k_ihess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
       count();
     }
     if (v.nwarp) warp_ihess_down(s, st, v.t0, v.nwarp, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    bf.join_now();
   }
   for (int l = 0; l < nl; ++l) {
     Level v = level(s, l);
+    BigFork bf{ex, st};
+    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
+      big_ihess_up(s, bs, xs, xc, m, big_front(s, v, i), Wc, Y, ldy, ws);
+    });
     if (v.nwarp) warp_ihess_up(s, st, v.t0, v.nwarp, m, Wc, Y, ldy, ws);
     if (v.ncta) {
       k_ihess_up<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Y, ldy, ws);
       count();
     }
-    for (int i = 0; i < v.nbig; ++i) big_ihess_up(s, st, xs, xcap, m, big_front(s, v, i), Wc, Y, ldy, ws);
+    bf.join_now();
   }
 }
-void complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* Sin, double* Lc, double* Wc, double* Dd,
-              double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
+// Completion: only the S-front loads of the big fronts (gather of V_k from
+// the parent's front, Eq. (e-sn-compl-2)) follow the top-down order; their
+// arithmetic (Algorithm 7.3 for one front) needs nothing from other fronts,
+// so all big fronts run concurrently after the top-down pass.
+void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* ws);
+void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Sin, double* Lc, double* Wc,
+              double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
   const int nl = (int)s->lvl_ptr.size() - 1;
+  std::vector<int> bigs;
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
-    for (int i = 0; i < v.nbig; ++i) big_complete(s, st, xs, xcap, big_front(s, v, i), Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+    for (int i = 0; i < v.nbig; ++i) {
+      big_complete_load(s, st, big_front(s, v, i), Sin, ws);
+      bigs.push_back(big_front(s, v, i));
+    }
     if (v.ncta) {
       k_complete<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
       count();
     }
     if (v.nwarp) warp_complete(s, st, v.t0, v.nwarp, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
   }
+  BigFork bf{ex, st};
+  bf.run((int)bigs.size(), [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
+    big_complete(s, bs, xs, xc, bigs[i], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+  });
+  bf.join_now();
 }
 void big_inv_v(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Vd,
                double* Rd, double* ws, int64_t* status);
-void inv_v(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, const double* Vd, double* Rd, double* ws,
+void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* ws,
            int64_t* status) {
+  std::vector<int> bigs;
+  for (int64_t k = 0; k < s->nsn; ++k)
+    if (s->is_big[k]) bigs.push_back((int)k);
+  BigFork bf{ex, st};
+  bf.run((int)bigs.size(), [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
+    big_inv_v(s, bs, xs, xc, bigs[i], Vd, Rd, ws, status);
+  });
   if (s->dev.small_count > 0) {
     k_inv_v<<<(int)s->dev.small_count, NT, 0, st>>>(s->dev, Vd, Rd, ws, status, s->dev.small_fronts);
     count();
   }
-  for (int64_t k = 0; k < s->nsn; ++k)
-    if (s->is_big[k]) big_inv_v(s, st, xs, xcap, (int)k, Vd, Rd, ws, status);
+  bf.join_now();
 }
 void sum(cudaStream_t st, const double* v, int64_t m, double* out) {
   k_sum<<<1, NT, 0, st>>>(v, m, out);

@@ -18,8 +18,8 @@
 #include "chd_internal.h"
 
 namespace chd_launch {
-void hessian(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, const double* Wc,
-             const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
+void hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Vd,
+             const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
 }
 
 namespace {
@@ -77,8 +77,9 @@ extern "C" chd_status chd_hessian_noalloc(chd_factor* f, int m, const double* y,
   if (rc != CHD_OK) return rc;
   // Every workspace entry the Hessian passes read is written earlier in the
   // same call, so no clearing is needed between calls.
-  // The dense tier runs without split-K here (no scratch beyond the array).
-  chd_launch::hessian(f->sym, static_cast<cudaStream_t>(stream), nullptr, 0, m, f->Wc, f->Vd, y, ldy, t, ldt, ws);
+  // The dense tier runs on the caller's stream without split-K here (no
+  // scratch beyond the array).
+  chd_launch::hessian(f->sym, static_cast<cudaStream_t>(stream), nullptr, m, f->Wc, f->Vd, y, ldy, t, ldt, ws);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CHD_OK : CHD_ERR_CUDA;
 }
