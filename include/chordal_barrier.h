@@ -76,7 +76,10 @@ typedef struct {
   int32_t big_rows;        /* a front with |J_k| >= big_rows (or |N_k| >= big_cols) is
                               processed by the multi-CTA dense tier; 0 = default 320 */
   int32_t big_cols;        /* 0 = default 160 */
-  int32_t reserved[6];
+  int32_t split_cols;      /* supernodes wider than 1.5 x split_cols columns are split into a
+                              chain of supernodes of split_cols columns (V unchanged);
+                              0 = default 256, negative = never split */
+  int32_t reserved[5];
 } chd_opts;
 
 /* Fill `opts` with the defaults: natural order, relax 0, tie_last 1, default

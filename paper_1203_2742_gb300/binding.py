@@ -40,7 +40,7 @@ class ChdError(RuntimeError):
 class chd_opts(C.Structure):
     _fields_ = [("ordering", C.c_int32), ("user_perm", C.POINTER(C.c_int64)), ("relax", C.c_int32),
                 ("tie_last", C.c_int32), ("big_rows", C.c_int32), ("big_cols", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("split_cols", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 _p = C.c_void_p
@@ -115,7 +115,7 @@ def _dptr(t, what, nnz=None, rows=None):
 # ---------------------------------------------------------------------------
 
 def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0,
-                big_cols=0):
+                big_cols=0, split_cols=0):
     colptr = np.ascontiguousarray(colptr, dtype=np.int64)
     rowind = np.ascontiguousarray(rowind, dtype=np.int32)
     o = chd_opts()
@@ -130,6 +130,7 @@ def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_l
     o.tie_last = 1 if tie_last else 0
     o.big_rows = int(big_rows)
     o.big_cols = int(big_cols)
+    o.split_cols = int(split_cols)
     out = _p()
     rc = _lib.chd_analyze(int(n), colptr.ctypes.data, rowind.ctypes.data, C.byref(o), C.byref(out))
     _check(rc, "chd_analyze")
@@ -278,9 +279,10 @@ class Symbolic:
     """Owner of a ``chd_symbolic``: the analysed pattern and its clique tree."""
 
     def __init__(self, n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True,
-                 big_rows=0, big_cols=0):
+                 big_rows=0, big_cols=0, split_cols=0):
         self._h = chd_analyze(n, colptr, rowind, ordering=ordering, perm=perm, relax=relax,
-                              tie_last=tie_last, big_rows=big_rows, big_cols=big_cols)
+                              tie_last=tie_last, big_rows=big_rows, big_cols=big_cols,
+                              split_cols=split_cols)
         info = chd_symbolic_info(self._h)
         self.n = info["n"]
         self.nnz = info["nnz"]

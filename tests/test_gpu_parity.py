@@ -24,9 +24,10 @@ def torch():
 
 
 class Case:
-    def __init__(self, pattern, ordering="natural", perm=None, relax=0, seed=0, x=None, big=None):
+    def __init__(self, pattern, ordering="natural", perm=None, relax=0, seed=0, x=None, big=None, split=0):
         self.B = lib()
         kw = {} if big is None else dict(big_rows=big[0], big_cols=big[1])
+        kw["split_cols"] = split
         self.sym = self.B.Symbolic(*pattern, ordering=ordering, perm=perm, relax=relax, **kw)
         s = self.sym
         self.n, self.cp, self.ri = s.n, s.colptr, s.rowind
@@ -71,6 +72,9 @@ def small_cases():
                                       ordering="mindeg", relax=16, seed=10, big=(40, 20)),
         "dense_tier_full": lambda: Case(W.band(150, 149), seed=11, big=(64, 64)),
         "dense_tier_arrow": lambda: Case(W.arrow(260, 100), seed=12, big=(90, 70)),
+        # wide supernodes split into chains (dense, CTA and warp pieces)
+        "split_dense": lambda: Case(W.band(150, 149), seed=13, big=(64, 64), split=24),
+        "split_arrow": lambda: Case(W.arrow(200, 90), seed=14, split=8),
     }
 
 

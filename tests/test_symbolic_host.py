@@ -120,3 +120,27 @@ def test_flop_counts_band_scaling():
     for op in ("factor", "gradient", "hessian"):
         assert abs(f2[op] / f1[op] - 2.0) < 0.02
         assert 3.4 < f3[op] / f1[op] < 4.6
+
+
+@pytest.mark.parametrize("split", [4, 16])
+def test_supernode_splitting_keeps_the_pattern(split):
+    """Splitting a wide supernode into a chain (V unchanged, each piece's
+    ancestor set = later columns of the original supernode + its A)."""
+    B = lib()
+    pattern = W.arrow(120, 40)  # dense tail of 40 columns: one wide supernode
+    s0 = B.Symbolic(*pattern, split_cols=-1)
+    s1 = B.Symbolic(*pattern, split_cols=split)
+    assert (s0.perm == s1.perm).all()
+    assert _product_pairs(s0) == _product_pairs(s1)
+    assert s1.nsuper > s0.nsuper
+    sp, par, rp, rows = s1.supernodes()
+    widths = np.diff(sp)
+    assert widths.max() <= split + split // 2
+    # every supernode's structure is a clique's tail: J_k = N_k followed by A_k,
+    # and the parent holds min A_k among its columns
+    for k in range(len(sp) - 1):
+        nk = int(sp[k + 1] - sp[k])
+        J = rows[rp[k]:rp[k + 1]]
+        if len(J) > nk:
+            p = par[k]
+            assert sp[p] <= J[nk] < sp[p + 1]
