@@ -285,9 +285,6 @@ void panel_solve(const Ctx& st, int batch, int R, MB B, int64_t sB, int p0, int 
   chd_launch::count_launch();
 }
 
-// column shift of a view: Dn (col-major) and DnTW (transposed) layouts
-__host__ __device__ inline Dn colshift(Dn v, int c0) { v.p += (int64_t)c0 * v.ld; return v; }
-__host__ __device__ inline DnTW colshift(DnTW v, int c0) { v.p += c0; return v; }
 
 // B := B L^{-T} (R x n view B, n x n lower L), blocked forward.
 template <class MB>

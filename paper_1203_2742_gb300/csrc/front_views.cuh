@@ -79,6 +79,16 @@ struct DnTW {
   __device__ double& at(int r, int c) const { return p[c + (int64_t)r * ld]; }
 };
 
+// column shift of a writable view (Dn: column-major; DnTW: transposed)
+__host__ __device__ inline Dn colshift(Dn v, int c0) {
+  v.p += (int64_t)c0 * v.ld;
+  return v;
+}
+__host__ __device__ inline DnTW colshift(DnTW v, int c0) {
+  v.p += c0;
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // status
 // ---------------------------------------------------------------------------

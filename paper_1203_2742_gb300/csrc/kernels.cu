@@ -202,38 +202,83 @@ __device__ void cta_potrf_partial(double* F, int64_t ld, int J, int n, int64_t* 
 }
 
 // ---------------------------------------------------------------------------
-// Right-side triangular solves on an R x n matrix B (any writable view) with
-// a lower triangular n x n matrix L (column-major, ld), column sweeps:
+// Right-side triangular solves on an R x n matrix B (any writable view with
+// colshift) with a lower triangular n x n matrix L (column-major, ld):
 //   trsm_rLT:  B := B L^{-T}      trsm_rL:  B := B L^{-1}
-// Left-side solves are the same sweeps on the transposed view of B.
+// Blocked: 32-column panels solved in shared memory (row chunks of 96,
+// column sweeps against the 32 x 32 diagonal block), the rest of B updated
+// by the tiled CTA GEMM.  Left-side solves are the same on the transposed
+// view of B.
 // ---------------------------------------------------------------------------
 template <class MB>
-__device__ void cta_trsm_rLT(int R, int n, MB B, const double* L, int64_t ld) {
+__device__ void cta_panel_solve(int R, MB B, int p0, int pb, const double* L, int64_t ld, bool fwd) {
+  double* Ls = sh_pool;
+  double* Ps = sh_pool + PB * (PB + 1);
   const int tid = threadIdx.x;
-  for (int c = 0; c < n; ++c) {
-    const double inv = 1.0 / L[c + (int64_t)c * ld];
-    for (int r = tid; r < R; r += NT) B.at(r, c) *= inv;
+  for (int e = tid; e < pb * pb; e += NT) {
+    const int i = e % pb, j = e / pb;
+    Ls[i * (PB + 1) + j] = i >= j ? L[(p0 + i) + (int64_t)(p0 + j) * ld] : 0.0;
+  }
+  for (int r0 = 0; r0 < R; r0 += PCH) {
+    const int rc = min(PCH, R - r0);
+    for (int e = tid; e < rc * pb; e += NT) {
+      const int r = e % rc, c = e / rc;
+      Ps[r * (PB + 1) + c] = B.at(r0 + r, p0 + c);
+    }
     __syncthreads();
-    const int m = n - c - 1;
-    for (int e = tid; e < R * m; e += NT) {
-      int r = e % R, t = c + 1 + e / R;
-      B.at(r, t) -= B.at(r, c) * L[t + (int64_t)c * ld];
+    if (fwd) {
+      for (int c = 0; c < pb; ++c) {
+        const double inv = 1.0 / Ls[c * (PB + 1) + c];
+        for (int r = tid; r < rc; r += NT) Ps[r * (PB + 1) + c] *= inv;
+        __syncthreads();
+        const int m = pb - c - 1;
+        for (int e = tid; e < rc * m; e += NT) {
+          const int r = e % rc, t = c + 1 + e / rc;
+          Ps[r * (PB + 1) + t] -= Ps[r * (PB + 1) + c] * Ls[t * (PB + 1) + c];
+        }
+        __syncthreads();
+      }
+    } else {
+      for (int c = pb - 1; c >= 0; --c) {
+        const double inv = 1.0 / Ls[c * (PB + 1) + c];
+        for (int r = tid; r < rc; r += NT) Ps[r * (PB + 1) + c] *= inv;
+        __syncthreads();
+        for (int e = tid; e < rc * c; e += NT) {
+          const int r = e % rc, t = e / rc;
+          Ps[r * (PB + 1) + t] -= Ps[r * (PB + 1) + c] * Ls[c * (PB + 1) + t];
+        }
+        __syncthreads();
+      }
+    }
+    for (int e = tid; e < rc * pb; e += NT) {
+      const int r = e % rc, c = e / rc;
+      B.at(r0 + r, p0 + c) = Ps[r * (PB + 1) + c];
     }
     __syncthreads();
   }
 }
 template <class MB>
+__device__ void cta_trsm_rLT(int R, int n, MB B, const double* L, int64_t ld) {
+  if (R <= 0 || n <= 0) return;
+  for (int p0 = 0; p0 < n; p0 += PB) {
+    const int pb = min(PB, n - p0);
+    cta_panel_solve(R, B, p0, pb, L, ld, true);
+    const int rest = n - p0 - pb;
+    if (rest > 0)
+      cta_gemm(R, rest, pb, -1.0, colshift(B, p0), DnT{L + (p0 + pb) + (int64_t)p0 * ld, ld}, 1.0,
+               colshift(B, p0 + pb), false);
+  }
+}
+template <class MB>
 __device__ void cta_trsm_rL(int R, int n, MB B, const double* L, int64_t ld) {
-  const int tid = threadIdx.x;
-  for (int c = n - 1; c >= 0; --c) {
-    const double inv = 1.0 / L[c + (int64_t)c * ld];
-    for (int r = tid; r < R; r += NT) B.at(r, c) *= inv;
-    __syncthreads();
-    for (int e = tid; e < R * c; e += NT) {
-      int r = e % R, t = e / R;
-      B.at(r, t) -= B.at(r, c) * L[c + (int64_t)t * ld];
-    }
-    __syncthreads();
+  if (R <= 0 || n <= 0) return;
+  const int np = (n + PB - 1) / PB;
+  for (int q = np - 1; q >= 0; --q) {
+    const int p0 = q * PB, pb = min(PB, n - p0);
+    cta_panel_solve(R, B, p0, pb, L, ld, false);
+    if (p0 > 0)
+      cta_gemm(R, p0, pb, -1.0, colshift(B, p0), Dn{const_cast<double*>(L) + p0, ld}, 1.0, colshift(B, 0),
+               false);
   }
 }
 
