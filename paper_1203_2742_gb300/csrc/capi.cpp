@@ -424,6 +424,7 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   size_t iTp = add(s->task_ptr.data(), s->task_ptr.size() * 4);
   size_t iTf = add(s->task_fronts.data(), s->task_fronts.size() * 4);
   size_t iSf = add(s->small_fronts.data(), s->small_fronts.size() * 4);
+  size_t iCf = add(s->cta_fronts.data(), s->cta_fronts.size() * 4);
   std::vector<char> host(off, 0);
   for (auto& p : pcs)
     if (p.bytes) std::memcpy(host.data() + p.off, p.src, p.bytes);
@@ -472,6 +473,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   d.task_fronts = reinterpret_cast<const int32_t*>(b + pcs[iTf].off);
   d.small_fronts = reinterpret_cast<const int32_t*>(b + pcs[iSf].off);
   d.small_count = (int64_t)s->small_fronts.size();
+  d.cta_fronts = reinterpret_cast<const int32_t*>(b + pcs[iCf].off);
+  d.cta_count = (int64_t)s->cta_fronts.size();
   d.f_total = s->f_off[s->nsn];
   d.d_total = s->d_off[s->nsn];
   d.v_total = s->v_off[s->nsn];

@@ -27,6 +27,8 @@ struct SymDev {
   const int32_t* task_fronts = nullptr;
   const int32_t* small_fronts = nullptr;  // fronts not in the dense tier
   int64_t small_count = 0;
+  const int32_t* cta_fronts = nullptr;    // fronts of the CTA tier
+  int64_t cta_count = 0;
   int64_t f_total = 0;               // workspace doubles per right-hand side
   int64_t d_total = 0;
   int64_t v_total = 0;
@@ -57,6 +59,7 @@ struct chd_symbolic {
   std::vector<char> is_big;  // per supernode
   std::vector<int32_t> tier;  // per supernode: 0 warp, 1 CTA, 2 dense
   std::vector<int32_t> small_fronts;
+  std::vector<int32_t> cta_fronts;
   double flops[5] = {0, 0, 0, 0, 0};
   int64_t max_front = 0;
   // device mirror

@@ -581,14 +581,21 @@ __device__ void ihess_up_front(const SymDev& S, int k, const double* Wc, double*
 // Algorithm 7.3 for one front (each front needs only S and V_k = S_AA):
 // R = chol(V), Z = R^{-1} S_AN, P = S_NN - Z^T Z = D_NN^{-1},
 // L_AN = -R^{-T} Z, D_NN = P^{-1}, C = chol(D_NN), B = L_AN C.
+// S-front of front k: V_k gathered from the parent's S-front, S_NN and S_AN
+// from the input (the top-down part of Algorithm 7.3).
+__device__ void complete_load_front(const SymDev& S, int k, const double* Sin, double* ws) {
+  FrontInfo f = front_info(S, k, ws);
+  gather_from_parent(S, f, ws);
+  csc_to_front(f.F, f.J, f.n, Sin + f.base);
+  __syncthreads();
+}
+
+// Algorithm 7.3 arithmetic for one front whose S-front is loaded.
 __device__ void complete_front(const SymDev& S, int k, const double* Sin, double* Lc, double* Wc,
                                double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
                                int64_t* st) {
   FrontInfo f = front_info(S, k, ws);
   const int J = f.J, n = f.n, a = f.a;
-  gather_from_parent(S, f, ws);
-  csc_to_front(f.F, J, n, Sin + f.base);
-  __syncthreads();
   double* V = Vd + S.v_off[k];
   double* R = Rd + S.v_off[k];
   copy_lower(V, a, f.F + n + (int64_t)n * J, J, a);
@@ -689,12 +696,14 @@ __global__ void __launch_bounds__(NT) k_ihess_up(SymDev S, int task0, const doub
   for (int q = S.task_ptr[t]; q < S.task_ptr[t + 1]; ++q)
     ihess_up_front(S, S.task_fronts[q], Wc, Y + y * ldy, ws + y * S.f_total);
 }
-__global__ void __launch_bounds__(NT) k_complete(SymDev S, int task0, const double* Sin, double* Lc,
-                                                 double* Wc, double* Dd, double* Vd, double* Rd,
-                                                 double* ws, double* ldet, int64_t* st) {
+__global__ void __launch_bounds__(NT) k_complete_load(SymDev S, int task0, const double* Sin, double* ws) {
   const int t = task0 + blockIdx.x;
-  for (int q = S.task_ptr[t + 1] - 1; q >= S.task_ptr[t]; --q)
-    complete_front(S, S.task_fronts[q], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, st);
+  for (int q = S.task_ptr[t + 1] - 1; q >= S.task_ptr[t]; --q) complete_load_front(S, S.task_fronts[q], Sin, ws);
+}
+// all CTA-tier fronts at once (their S-fronts are loaded)
+__global__ void __launch_bounds__(NT) k_complete(SymDev S, const double* Sin, double* Lc, double* Wc, double* Dd,
+                                                 double* Vd, double* Rd, double* ws, double* ldet, int64_t* st) {
+  complete_front(S, S.cta_fronts[blockIdx.x], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, st);
 }
 // Inverses of the cached V_k (inverse Hessian step 2), one CTA per front of
 // `front_list` (no dependencies between fronts; big fronts use the dense
@@ -958,10 +967,11 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
     bf.join_now();
   }
 }
-// Completion: only the S-front loads of the big fronts (gather of V_k from
-// the parent's front, Eq. (e-sn-compl-2)) follow the top-down order; their
-// arithmetic (Algorithm 7.3 for one front) needs nothing from other fronts,
-// so all big fronts run concurrently after the top-down pass.
+// Completion: only the S-front loads (gather of V_k from the parent's front,
+// Eq. (e-sn-compl-2)) follow the top-down order; the arithmetic of Algorithm
+// 7.3 for one front needs nothing from other fronts, so after the top-down
+// pass all big fronts (side streams) and all CTA-tier fronts (one launch)
+// run at once.  Warp-tier fronts load and compute in the pass.
 void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* ws);
 void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Sin, double* Lc, double* Wc,
               double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
@@ -974,7 +984,7 @@ void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
       bigs.push_back(big_front(s, v, i));
     }
     if (v.ncta) {
-      k_complete<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+      k_complete_load<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Sin, ws);
       count();
     }
     if (v.nwarp) warp_complete(s, st, v.t0, v.nwarp, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
@@ -983,6 +993,10 @@ void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
   bf.run((int)bigs.size(), [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
     big_complete(s, bs, xs, xc, bigs[i], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
   });
+  if (s->dev.cta_count > 0) {
+    k_complete<<<(int)s->dev.cta_count, NT, 0, st>>>(s->dev, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+    count();
+  }
   bf.join_now();
 }
 void big_inv_v(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Vd,

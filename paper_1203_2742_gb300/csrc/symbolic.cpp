@@ -489,8 +489,11 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     }
     s->tier.assign(tier.begin(), tier.end());
     s->small_fronts.clear();
-    for (int64_t t = 0; t < nsn; ++t)
+    s->cta_fronts.clear();
+    for (int64_t t = 0; t < nsn; ++t) {
       if (!s->is_big[t]) s->small_fronts.push_back((int32_t)t);
+      if (tier[t] == 1) s->cta_fronts.push_back((int32_t)t);
+    }
     vector<double> W(nsn, 0.0);
     double total = 0;
     for (int64_t t = 0; t < nsn; ++t) {  // children precede parents
