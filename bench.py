@@ -54,6 +54,13 @@ def make_workload(name):
         return dict(name=name, pattern=W.band(200, 8), opts=dict(), m=1, seed=0, gram=(20, 1.0),
                     desc="band n=200 half-bandwidth 8, natural order, X diag-dominant, 1 Y, "
                          "S=P(GG^T+I) G 200x20")
+    if name == "batch256":
+        inst = W.batch_mix(256, 3)
+        return dict(name=name, batch=inst, m=4, seed=3, gram=(20, 0.5),
+                    desc="256 independent instances in one batched symbolic object: n log-uniform in "
+                         "[300, 30000], a third each band (half-bandwidth 4..64), block arrow (width 32), "
+                         "2D grid with nested dissection; X diag-dominant, 4 Y per instance, "
+                         "S=P(GG^T+0.5I) G nx20")
     if name == "grid150":
         return dict(name=name, pattern=W.grid2d(150, 150),
                     opts=dict(perm=W.nested_dissection((150, 150), leaf=8)), m=64, seed=2,
@@ -139,10 +146,56 @@ def oracle_hessian_sample(wl, n, cp, ri, x, ys, count):
     return t1 - t0, (t2 - t1) / count
 
 
+def batch_cpu_baseline(sym, x, ys, m, cores, budget_s=15.0):
+    """Dense oracle on the smallest instances of a batch (within a time budget),
+    extrapolated to every instance by the oracle's n^3 cost."""
+    from oracle import dense as OD
+    order = np.argsort(np.diff(sym.n_off))
+    spent, done, coef = 0.0, 0, []
+    for i in order:
+        (ni, cpi, rii), _ = sym.instance_pattern(int(i))
+        z0, z1 = int(sym.nnz_off[i]), int(sym.nnz_off[i + 1])
+        t0 = time.perf_counter()
+        Z = OD.inverse(ni, cpi, rii, x[z0:z1])
+        OD.hessian(ni, cpi, rii, x[z0:z1], list(ys[:, z0:z1]), Z=Z)
+        dt = time.perf_counter() - t0
+        spent += dt
+        done += 1
+        coef.append(dt / float(ni) ** 3)
+        if spent > budget_s:
+            break
+    c = float(np.median(coef))
+    total = sum(c * float(v) ** 3 for v in np.diff(sym.n_off))
+    return {"value": sym.count * m / total, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"dense oracle (X^-1, then P(X^-1 Y X^-1) for the {m} Y) on the {done} smallest of "
+                      f"{sym.count} instances ({spent:.1f} s); extrapolated to all instances by n^3"}
+
+
 def run_reference(args, wl):
     from paper_1203_2742_gb300 import build as _b  # noqa: F401  (no GPU use)
     # analyse with the library's host symbolic phase only when it is built;
     # else use the oracle's own fill of the same ordering (natural/user orders)
+    if "batch" in wl:
+        from paper_1203_2742_gb300 import build
+        build.build()
+        from paper_1203_2742_gb300 import binding as B
+        sym = make_symbolic(B, wl)
+        x, ys, _ = workload_values(wl, sym.n, sym.colptr, sym.rowind)
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        times, cpu = [], None
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            cpu = batch_cpu_baseline(sym, x, ys, wl["m"], cores, budget_s=5.0)
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        line = {"metric": METRIC, "value": cpu["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": wl["desc"], "global_batch": sym.count * wl["m"], "parallelism": "host cores"},
+                "cpu_baseline": cpu,
+                "e2e": {"value": cpu["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     n, cp, ri = analysed_pattern_host(wl)
     x, ys, _ = workload_values(wl, n, cp, ri)
     m = wl["m"]
@@ -172,12 +225,21 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def make_symbolic(B, wl):
+    if "batch" in wl:
+        pats = [p for p, _, _ in wl["batch"]]
+        perms = [q for _, q, _ in wl["batch"]]
+        ords = ["user" if q is not None else "natural" for q in perms]
+        return B.SymbolicBatch(pats, orderings=ords, perms=perms)
+    return B.Symbolic(*wl["pattern"], **wl["opts"])
+
+
 def analysed_pattern_host(wl):
     """The analysed (filled, permuted) pattern from the library's host phase."""
     from paper_1203_2742_gb300 import build
     build.build()
     from paper_1203_2742_gb300 import binding as B
-    sym = B.Symbolic(*wl["pattern"], **wl["opts"])
+    sym = make_symbolic(B, wl)
     return sym.n, sym.colptr, sym.rowind
 
 
@@ -201,8 +263,9 @@ def run_ours(args, wl, rank, world, local_rank):
     stream = torch.cuda.current_stream()
 
     t0 = time.perf_counter()
-    sym = B.Symbolic(*wl["pattern"], **wl["opts"])
+    sym = make_symbolic(B, wl)
     analyze_ms = (time.perf_counter() - t0) * 1e3
+    count = getattr(sym, "count", 1)
     n, cp, ri, nnz = sym.n, sym.colptr, sym.rowind, sym.nnz
     m = wl["m"]
     x, ys, s = workload_values(wl, n, cp, ri)
@@ -222,7 +285,7 @@ def run_ours(args, wl, rank, world, local_rank):
 
     def step():
         fac.refactor(X)
-        results["logdet"] = fac.logdet()
+        results["logdet"] = float(np.sum(fac.logdet_batch())) if count > 1 else fac.logdet()
         fac.gradient(out=G)
         fac.hessian(Y, out=T)
         fac.inv_hessian(T, out=YI)
@@ -259,7 +322,8 @@ def run_ours(args, wl, rank, world, local_rank):
         dev_ms = float(tt.item())
         dist.barrier()
     ms_per_step = dev_ms / args.steps
-    value = world * m * args.steps / (dev_ms * 1e-3)
+    evals_per_step = count * m  # one Hessian evaluation = one Y of one instance
+    value = world * evals_per_step * args.steps / (dev_ms * 1e-3)
 
     # ---- per-operation breakdown and the dominant kernel's roofline ----
     def time_op(fn, reps):
@@ -285,6 +349,30 @@ def run_ours(args, wl, rank, world, local_rank):
     hess_flops = fl["hessian"] * m
     achieved = hess_flops / (ops_ms["hessian"] * 1e-3) / 1e12
     step_flops = fl["factor"] + fl["gradient"] + m * (fl["hessian"] + fl["inv_hessian"]) + fl["completion"]
+
+    # ---- batched vs one instance at a time (the plain GPU path) ----
+    sequential = None
+    if count > 1:
+        singles = []
+        for i in range(count):
+            (ni, cpi, rii), permi = sym.instance_pattern(i)
+            si = B.Symbolic(ni, cpi, rii)  # already analysed: natural order keeps it
+            z0, z1 = int(sym.nnz_off[i]), int(sym.nnz_off[i + 1])
+            fi = si.factor(X[z0:z1].contiguous())
+            fi.gradient()
+            singles.append((si, fi, Y[:, z0:z1].contiguous(), torch.empty((m, z1 - z0), dtype=torch.float64, device=dev)))
+        torch.cuda.synchronize()
+
+        def seq_hessians():
+            for si, fi, yi, ti in singles:
+                fi.hessian(yi, out=ti)
+        seq_hessians()
+        torch.cuda.synchronize()
+        seq_ms = time_op(seq_hessians, 1)
+        sequential = {"hessian_ms_one_at_a_time": seq_ms, "hessian_ms_batched": ops_ms["hessian"],
+                      "evals_per_s_one_at_a_time": evals_per_step / (seq_ms * 1e-3),
+                      "evals_per_s_batched_hessian_only": evals_per_step / (ops_ms["hessian"] * 1e-3)}
+        del singles
 
     # ---- end to end through the C ABI with host buffers ----
     pin = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64).pin_memory()
@@ -317,7 +405,7 @@ def run_ours(args, wl, rank, world, local_rank):
         tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
-    e2e_value = world * m * args.steps / (e2e_ms * 1e-3)
+    e2e_value = world * evals_per_step * args.steps / (e2e_ms * 1e-3)
     h2d = 8 * (x.size + ys.size + s.size)
     d2h = 8 * (nnz + 2 * m * nnz)
 
@@ -325,11 +413,14 @@ def run_ours(args, wl, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-        sample = min(2, m)
-        tz, te = oracle_hessian_sample(wl, n, cp, ri, x, ys, sample)
-        cpu = {"value": m / (tz + m * te), "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"dense oracle X^-1 ({tz:.2f} s) then P(X^-1 Y X^-1) for {sample} of the {m} Y "
-                         f"({te:.2f} s each); value = {m}/(t_inverse + {m}*t_eval)"}
+        if count > 1:
+            cpu = batch_cpu_baseline(sym, x, ys, m, cores)
+        else:
+            sample = min(2, m)
+            tz, te = oracle_hessian_sample(wl, n, cp, ri, x, ys, sample)
+            cpu = {"value": m / (tz + m * te), "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"dense oracle X^-1 ({tz:.2f} s) then P(X^-1 Y X^-1) for {sample} of the {m} Y "
+                             f"({te:.2f} s each); value = {m}/(t_inverse + {m}*t_eval)"}
 
     if rank == 0:
         line = {
@@ -337,7 +428,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl["desc"], "n": n, "nnz_filled": nnz, "supernodes": sym.nsuper,
-                       "rhs_per_step": m, "global_batch": world * m,
+                       "rhs_per_step": m, "global_batch": world * evals_per_step,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MB write)"},
             "roofline": {"bound": "alu", "kernel": "Hessian products (k_hess_up + k_hess_down level launches)",
@@ -350,6 +441,8 @@ def run_ours(args, wl, rank, world, local_rank):
             "gpu_launches": int(launches),
             "clocks": clocks,
             "ops_ms": {k: round(v, 4) for k, v in ops_ms.items()},
+            "instances": count,
+            "batched_vs_one_at_a_time": sequential,
             "step_tflops_fp64": step_flops / (ms_per_step * 1e-3) / 1e12,
             "analyze_ms": analyze_ms,
             "wall_s": wall,
@@ -364,7 +457,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="er5000", choices=["er5000", "band200", "grid150"])
+    ap.add_argument("--workload", default="er5000", choices=["er5000", "band200", "grid150", "batch256"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

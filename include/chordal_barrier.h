@@ -106,6 +106,33 @@ chd_status chd_analyze(int64_t n, const int64_t* colptr, const int32_t* rowind,
                        const chd_opts* opts, chd_symbolic** out);
 
 /*
+ * Batched analysis of `count` independent patterns, to be processed together
+ * (tree parallelism across problems, §8): the symbolic object describes the
+ * block-diagonal union of the patterns.  Each instance is ordered by its own
+ * options (opts[i]; NULL for defaults) and keeps a contiguous block of the
+ * analysed numbering; relax / tie_last / big_rows / big_cols / split_cols
+ * are taken from opts[0].  Every call on the object (factor, gradient,
+ * Hessian, completion, ...) then runs all instances level by level in the
+ * same launches, and value arrays are the concatenation of the instances'
+ * arrays (see chd_symbolic_batch_info).
+ *   count            number of instances (>= 1)
+ *   n[i]             order of instance i
+ *   colptr[i], rowind[i]   host, lower CSC of instance i (as in chd_analyze)
+ * Errors: as chd_analyze, for any instance.
+ */
+chd_status chd_analyze_batch(int64_t count, const int64_t* n, const int64_t* const* colptr,
+                             const int32_t* const* rowind, const chd_opts* opts, chd_symbolic** out);
+
+/*
+ * Instance ranges of a (batched) symbolic object, host pointers owned by it:
+ * instance i owns columns [n_off[i], n_off[i+1]) of the analysed numbering and
+ * values [nnz_off[i], nnz_off[i+1]) of every value array.  A symbolic object
+ * from chd_analyze has one instance.
+ */
+chd_status chd_symbolic_batch_info(const chd_symbolic* sym, int64_t* count, const int64_t** n_off,
+                                   const int64_t** nnz_off);
+
+/*
  * Pointers into the symbolic object (host memory, owned by it, valid until
  * chd_symbolic_free).  Any output pointer may be NULL.
  *   nnz_filled   entries of the lower triangle of the filled pattern V
@@ -156,6 +183,10 @@ chd_status chd_refactor(chd_factor* fac, const double* x_dev, void* stream);
 
 /* log det X = sum of log D_ii (§1.1).  Synchronises; host output. */
 chd_status chd_logdet(chd_factor* fac, double* out);
+
+/* log det of every instance of a batched factor: out (host) has one entry
+   per instance.  Synchronises. */
+chd_status chd_logdet_batch(chd_factor* fac, double* out);
 
 /*
  * Gradient g = -P(X^{-1}) (Eq. (e-grad-def)) by the supernodal projected

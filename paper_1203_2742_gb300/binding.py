@@ -48,6 +48,9 @@ _i64 = C.c_int64
 _lib.chd_opts_default.argtypes = [C.POINTER(chd_opts)]
 _lib.chd_opts_default.restype = None
 _lib.chd_analyze.argtypes = [_i64, _p, _p, C.POINTER(chd_opts), C.POINTER(_p)]
+_lib.chd_analyze_batch.argtypes = [_i64, _p, _p, _p, _p, C.POINTER(_p)]
+_lib.chd_symbolic_batch_info.argtypes = [_p, C.POINTER(_i64), C.POINTER(_p), C.POINTER(_p)]
+_lib.chd_logdet_batch.argtypes = [_p, _p]
 _lib.chd_symbolic_info.argtypes = [_p, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_p), C.POINTER(_p),
                                    C.POINTER(_p), C.POINTER(_i64)]
 _lib.chd_symbolic_supernodes.argtypes = [_p, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]
@@ -73,7 +76,7 @@ _lib.chd_probe_fp64_peak.argtypes = [_p, C.POINTER(C.c_double)]
 _lib.chd_probe_fp64_peak.restype = C.c_int
 _lib.chd_factor_free.argtypes = [_p]
 _lib.chd_factor_free.restype = None
-for _f in ("chd_analyze", "chd_symbolic_info", "chd_symbolic_supernodes", "chd_symbolic_flops",
+for _f in ("chd_analyze", "chd_analyze_batch", "chd_symbolic_batch_info", "chd_logdet_batch", "chd_symbolic_info", "chd_symbolic_supernodes", "chd_symbolic_flops",
            "chd_factor_new", "chd_refactor", "chd_logdet", "chd_gradient", "chd_hessian",
            "chd_inv_hessian", "chd_complete", "chd_recomplete", "chd_factor_export", "chd_status_get",
            "chd_error_detail"):
@@ -134,6 +137,69 @@ def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_l
     out = _p()
     rc = _lib.chd_analyze(int(n), colptr.ctypes.data, rowind.ctypes.data, C.byref(o), C.byref(out))
     _check(rc, "chd_analyze")
+    return out
+
+
+def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big_cols=0, split_cols=0):
+    o = chd_opts()
+    _lib.chd_opts_default(C.byref(o))
+    o.ordering = ORDERINGS[ordering]
+    keep = None
+    if perm is not None:
+        keep = np.ascontiguousarray(perm, dtype=np.int64)
+        o.user_perm = keep.ctypes.data_as(C.POINTER(C.c_int64))
+        o.ordering = ORDERINGS["user"]
+    o.relax = int(relax)
+    o.tie_last = 1 if tie_last else 0
+    o.big_rows = int(big_rows)
+    o.big_cols = int(big_cols)
+    o.split_cols = int(split_cols)
+    return o, keep
+
+
+def chd_analyze_batch(patterns, orderings=None, perms=None, **shared):
+    """Analyse independent patterns together (one block-diagonal union).
+
+    patterns: list of (n, colptr, rowind); orderings / perms: per-instance
+    lists (None for natural order); shared options (relax, big_rows, ...)
+    are taken from the first instance's options.
+    """
+    count = len(patterns)
+    orderings = orderings or ["natural"] * count
+    perms = perms or [None] * count
+    keep = []
+    ns = np.array([p[0] for p in patterns], dtype=np.int64)
+    cps = [np.ascontiguousarray(p[1], dtype=np.int64) for p in patterns]
+    ris = [np.ascontiguousarray(p[2], dtype=np.int32) for p in patterns]
+    keep += cps + ris
+    OA = chd_opts * count
+    oa = OA()
+    for i in range(count):
+        o, k = _opts(orderings[i], perms[i], **shared)
+        oa[i] = o
+        keep.append(k)
+    cp_ptrs = (C.c_void_p * count)(*[c.ctypes.data for c in cps])
+    ri_ptrs = (C.c_void_p * count)(*[r.ctypes.data for r in ris])
+    out = _p()
+    rc = _lib.chd_analyze_batch(count, ns.ctypes.data, C.cast(cp_ptrs, C.c_void_p), C.cast(ri_ptrs, C.c_void_p),
+                                C.cast(oa, C.c_void_p), C.byref(out))
+    _check(rc, "chd_analyze_batch")
+    return out
+
+
+def chd_symbolic_batch_info(sym):
+    cnt = _i64()
+    no, zo = _p(), _p()
+    _check(_lib.chd_symbolic_batch_info(sym, C.byref(cnt), C.byref(no), C.byref(zo)), "chd_symbolic_batch_info")
+    k = cnt.value
+    n_off = np.ctypeslib.as_array(C.cast(no, C.POINTER(C.c_int64)), shape=(k + 1,)).copy()
+    nnz_off = np.ctypeslib.as_array(C.cast(zo, C.POINTER(C.c_int64)), shape=(k + 1,)).copy()
+    return n_off, nnz_off
+
+
+def chd_logdet_batch(fac, count):
+    out = np.zeros(count, dtype=np.float64)
+    _check(_lib.chd_logdet_batch(fac, out.ctypes.data), "chd_logdet_batch")
     return out
 
 
@@ -295,6 +361,11 @@ class Symbolic:
     def handle(self):
         return self._h
 
+    @property
+    def instances(self):
+        """(n_off, nnz_off): column and value ranges of the instances."""
+        return chd_symbolic_batch_info(self._h)
+
     def supernodes(self):
         return chd_symbolic_supernodes(self._h, self.nsuper)
 
@@ -315,6 +386,30 @@ class Symbolic:
             self._h = None
 
 
+class SymbolicBatch(Symbolic):
+    """Owner of a batched chd_symbolic: independent patterns run together."""
+
+    def __init__(self, patterns, orderings=None, perms=None, **shared):
+        self._h = chd_analyze_batch(patterns, orderings, perms, **shared)
+        info = chd_symbolic_info(self._h)
+        self.n = info["n"]
+        self.nnz = info["nnz"]
+        self.colptr = info["colptr"]
+        self.rowind = info["rowind"]
+        self.perm = info["perm"]
+        self.nsuper = info["nsuper"]
+        self.n_off, self.nnz_off = chd_symbolic_batch_info(self._h)
+        self.count = len(self.n_off) - 1
+
+    def instance_pattern(self, i):
+        """Analysed pattern (n_i, colptr_i, rowind_i) and perm_i of instance i."""
+        a, b_ = int(self.n_off[i]), int(self.n_off[i + 1])
+        z0 = int(self.nnz_off[i])
+        cp = self.colptr[a:b_ + 1] - z0
+        ri = self.rowind[z0:int(self.nnz_off[i + 1])] - a
+        return (b_ - a, cp, ri.astype(np.int32)), self.perm[a:b_] - a
+
+
 class Factor:
     """Owner of a ``chd_factor`` (device-resident factor and cached blocks)."""
 
@@ -331,6 +426,9 @@ class Factor:
 
     def logdet(self):
         return chd_logdet(self._h)
+
+    def logdet_batch(self):
+        return chd_logdet_batch(self._h, len(self.sym.instances[0]) - 1)
 
     def recomplete(self, s, stream=None, want_fstar=True):
         return chd_recomplete(self._h, s, self.sym.nnz, stream, want_fstar)

@@ -27,6 +27,7 @@ void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
 void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* ws,
            int64_t* status);
 void sum(cudaStream_t st, const double* v, int64_t m, double* out);
+void segsum(cudaStream_t st, const double* v, const int64_t* seg, int nseg, double* out);
 void export_ldl(const chd_symbolic* s, cudaStream_t st, const double* Lc, double* l, double* d);
 cudaError_t fp64_peak(cudaStream_t st, double* gflops);
 }  // namespace chd_launch
@@ -36,7 +37,7 @@ namespace {
 
 // Largest workspace (bytes) a Hessian-type call may hold; larger batches of
 // right-hand sides are processed in chunks.
-constexpr size_t kWorkspaceCap = size_t(16) << 30;
+constexpr size_t kWorkspaceCap = size_t(48) << 30;
 
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -168,7 +169,12 @@ chd_status chd_analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, 
   } catch (const std::bad_alloc&) {
     rc = CHD_ERR_OOM;
   }
-  if (rc == CHD_OK) rc = chd_symbolic_upload(s);
+  if (rc == CHD_OK) {
+    s->inst_n = {0, s->n};
+    s->inst_nnz = {0, s->colptr[s->n]};
+    s->inst_sn = {0, s->nsn};
+    rc = chd_symbolic_upload(s);
+  }
   if (rc != CHD_OK) {
     chd_symbolic_free(s);
     return rc;
@@ -186,6 +192,81 @@ chd_status chd_symbolic_info(const chd_symbolic* s, int64_t* n, int64_t* nnz, co
   if (rowind) *rowind = s->rowind.data();
   if (perm) *perm = s->perm.data();
   if (nsuper) *nsuper = s->nsn;
+  return CHD_OK;
+}
+
+chd_status chd_analyze_batch(int64_t count, const int64_t* n, const int64_t* const* colptr,
+                             const int32_t* const* rowind, const chd_opts* opts, chd_symbolic** out) {
+  if (!out || count < 1 || !n || !colptr || !rowind) return CHD_ERR_INVALID;
+  *out = nullptr;
+  chd_symbolic* s = nullptr;
+  chd_status rc = CHD_OK;
+  try {
+    std::vector<int64_t> off(count + 1, 0);
+    for (int64_t i = 0; i < count; ++i) {
+      if (n[i] < 1 || !colptr[i] || !rowind[i]) return CHD_ERR_INVALID;
+      off[i + 1] = off[i] + n[i];
+    }
+    const int64_t N = off[count];
+    std::vector<int64_t> ucp(N + 1, 0), uperm(N);
+    std::vector<int32_t> uri;
+    for (int64_t i = 0; i < count; ++i) {
+      chd_opts oi;
+      if (opts) oi = opts[i];
+      else chd_opts_default(&oi);
+      std::vector<int64_t> pi;
+      rc = chd_order_pattern(n[i], colptr[i], rowind[i], oi, pi);
+      if (rc != CHD_OK) return rc;
+      for (int64_t j = 0; j < n[i]; ++j) {
+        uperm[off[i] + j] = off[i] + pi[j];
+        for (int64_t q = colptr[i][j]; q < colptr[i][j + 1]; ++q) uri.push_back((int32_t)(rowind[i][q] + off[i]));
+        ucp[off[i] + j + 1] = (int64_t)uri.size();
+      }
+    }
+    chd_opts o;
+    if (opts) o = opts[0];
+    else chd_opts_default(&o);
+    o.ordering = CHD_ORDER_USER;
+    o.user_perm = uperm.data();
+    s = new chd_symbolic();
+    rc = chd_symbolic_build(N, ucp.data(), uri.data(), o, s);
+    if (rc == CHD_OK) {
+      // the postorder keeps every instance's columns together and in place
+      for (int64_t i = 0; i < count && rc == CHD_OK; ++i)
+        for (int64_t j = off[i]; j < off[i + 1]; ++j)
+          if (s->perm[j] < off[i] || s->perm[j] >= off[i + 1]) {
+            rc = CHD_ERR_INVALID;
+            break;
+          }
+    }
+    if (rc == CHD_OK) {
+      s->inst_n = off;
+      s->inst_nnz.assign(count + 1, 0);
+      s->inst_sn.assign(count + 1, 0);
+      for (int64_t i = 0; i <= count; ++i) {
+        s->inst_nnz[i] = s->colptr[off[i]];
+        s->inst_sn[i] = std::lower_bound(s->sn_ptr.begin(), s->sn_ptr.end(), off[i]) - s->sn_ptr.begin();
+        if (s->sn_ptr[s->inst_sn[i]] != off[i]) rc = CHD_ERR_INVALID;  // a supernode straddles instances
+      }
+    }
+    if (rc == CHD_OK) rc = chd_symbolic_upload(s);
+  } catch (const std::bad_alloc&) {
+    rc = CHD_ERR_OOM;
+  }
+  if (rc != CHD_OK) {
+    chd_symbolic_free(s);
+    return rc;
+  }
+  *out = s;
+  return CHD_OK;
+}
+
+chd_status chd_symbolic_batch_info(const chd_symbolic* s, int64_t* count, const int64_t** n_off,
+                                   const int64_t** nnz_off) {
+  if (!s) return CHD_ERR_INVALID;
+  if (count) *count = (int64_t)s->inst_n.size() - 1;
+  if (n_off) *n_off = s->inst_n.data();
+  if (nnz_off) *nnz_off = s->inst_nnz.data();
   return CHD_OK;
 }
 
@@ -245,6 +326,28 @@ chd_status chd_logdet(chd_factor* f, double* out) {
   chd_status rc = launch_status();
   if (rc != CHD_OK) return rc;
   rc = cuda_ok(cudaMemcpyAsync(out, f->scalar, 8, cudaMemcpyDeviceToHost, f->stream));
+  if (rc != CHD_OK) return rc;
+  return read_status(f);
+}
+
+chd_status chd_logdet_batch(chd_factor* f, double* out) {
+  if (!f || !out) return CHD_ERR_INVALID;
+  const int64_t count = (int64_t)f->sym->inst_n.size() - 1;
+  double* dsum = nullptr;
+  if (count == 1) {
+    chd_launch::sum(f->stream, f->ldet, f->sym->nsn, f->scalar);
+    dsum = f->scalar;
+  } else {
+    if (!f->inst_sum) {
+      chd_status rc0 = cuda_ok(cudaMalloc(&f->inst_sum, (size_t)count * 8));
+      if (rc0 != CHD_OK) return rc0;
+    }
+    chd_launch::segsum(f->stream, f->ldet, f->sym->dev.inst_sn, (int)count, f->inst_sum);
+    dsum = f->inst_sum;
+  }
+  chd_status rc = launch_status();
+  if (rc != CHD_OK) return rc;
+  rc = cuda_ok(cudaMemcpyAsync(out, dsum, (size_t)count * 8, cudaMemcpyDeviceToHost, f->stream));
   if (rc != CHD_OK) return rc;
   return read_status(f);
 }
@@ -390,6 +493,7 @@ void chd_factor_free(chd_factor* f) {
   }
   if (f->ex.fork) cudaEventDestroy(f->ex.fork);
   if (f->ws) cudaFree(f->ws);
+  if (f->inst_sum) cudaFree(f->inst_sum);
   if (f->block) cudaFree(f->block);
   delete f;
 }
@@ -425,6 +529,7 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   size_t iTf = add(s->task_fronts.data(), s->task_fronts.size() * 4);
   size_t iSf = add(s->small_fronts.data(), s->small_fronts.size() * 4);
   size_t iCf = add(s->cta_fronts.data(), s->cta_fronts.size() * 4);
+  size_t iIs = add(s->inst_sn.data(), s->inst_sn.size() * 8);
   std::vector<char> host(off, 0);
   for (auto& p : pcs)
     if (p.bytes) std::memcpy(host.data() + p.off, p.src, p.bytes);
@@ -475,6 +580,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   d.small_count = (int64_t)s->small_fronts.size();
   d.cta_fronts = reinterpret_cast<const int32_t*>(b + pcs[iCf].off);
   d.cta_count = (int64_t)s->cta_fronts.size();
+  d.inst_sn = reinterpret_cast<const int64_t*>(b + pcs[iIs].off);
+  d.ninst = (int64_t)s->inst_sn.size() - 1;
   d.f_total = s->f_off[s->nsn];
   d.d_total = s->d_off[s->nsn];
   d.v_total = s->v_off[s->nsn];

@@ -29,6 +29,8 @@ struct SymDev {
   int64_t small_count = 0;
   const int32_t* cta_fronts = nullptr;    // fronts of the CTA tier
   int64_t cta_count = 0;
+  const int64_t* inst_sn = nullptr;       // instances x supernode ranges
+  int64_t ninst = 1;
   int64_t f_total = 0;               // workspace doubles per right-hand side
   int64_t d_total = 0;
   int64_t v_total = 0;
@@ -61,6 +63,10 @@ struct chd_symbolic {
   std::vector<int32_t> small_fronts;
   std::vector<int32_t> cta_fronts;
   double flops[5] = {0, 0, 0, 0, 0};
+  // independent instances analysed together (chd_analyze_batch): instance i
+  // owns columns [inst_n[i], inst_n[i+1]), values [inst_nnz[i], inst_nnz[i+1])
+  // and supernodes [inst_sn[i], inst_sn[i+1]) of the analysed numbering
+  std::vector<int64_t> inst_n, inst_nnz, inst_sn;
   int64_t max_front = 0;
   // device mirror
   SymDev dev;
@@ -99,6 +105,7 @@ struct chd_factor {
   int64_t* status = nullptr; // [0] code, [1] supernode, [2] column
   double* ws = nullptr;      // per-right-hand-side front workspace
   Exec ex;                   // dense-tier streams and split-K scratch
+  double* inst_sum = nullptr;  // per-instance log det sums (batched symbolic objects)
   int64_t ws_rhs = 0;        // capacity in right-hand sides
   bool have_S = false;
   bool have_R = false;
@@ -108,6 +115,8 @@ struct chd_factor {
 chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* rowind,
                               const chd_opts& opts, chd_symbolic* s);
 chd_status chd_symbolic_upload(chd_symbolic* s);
+chd_status chd_order_pattern(int64_t n, const int64_t* colptr, const int32_t* rowind, const chd_opts& opts,
+                             std::vector<int64_t>& perm);
 
 inline int64_t front_n(const chd_symbolic* s, int64_t k) { return s->sn_ptr[k + 1] - s->sn_ptr[k]; }
 inline int64_t front_J(const chd_symbolic* s, int64_t k) { return s->rows_ptr[k + 1] - s->rows_ptr[k]; }

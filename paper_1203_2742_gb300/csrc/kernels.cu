@@ -736,6 +736,20 @@ __global__ void k_sum(const double* v, int64_t m, double* out) {
   }
   if (threadIdx.x == 0) *out = red[0];
 }
+// Deterministic sums of v over the segments [seg[i], seg[i+1]), one CTA each.
+__global__ void k_segsum(const double* v, const int64_t* seg, double* out) {
+  __shared__ double red[NT];
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int64_t q = seg[i] + threadIdx.x; q < seg[i + 1]; q += NT) s += v[q];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = NT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[i] = red[0];
+}
 // Unique scalar L D L^T from the supernodal Cholesky factor G = [C; B]:
 // L = G diag(1/G_ii), D_ii = G_ii^2.
 __global__ void k_export(SymDev S, const double* Lc, double* l, double* d) {
@@ -1018,6 +1032,10 @@ void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double*
 }
 void sum(cudaStream_t st, const double* v, int64_t m, double* out) {
   k_sum<<<1, NT, 0, st>>>(v, m, out);
+  count();
+}
+void segsum(cudaStream_t st, const double* v, const int64_t* seg, int nseg, double* out) {
+  k_segsum<<<nseg, NT, 0, st>>>(v, seg, out);
   count();
 }
 void export_ldl(const chd_symbolic* s, cudaStream_t st, const double* Lc, double* l, double* d) {

@@ -216,6 +216,33 @@ vector<int64_t> chain_postorder(int64_t n, const vector<int64_t>& parent, const 
 
 }  // namespace
 
+// Ordering of one pattern by its options (natural, user, minimum degree);
+// validates the pattern.  perm[new] = old.
+chd_status chd_order_pattern(int64_t n, const int64_t* colptr, const int32_t* rowind, const chd_opts& opts,
+                             std::vector<int64_t>& perm) {
+  if (n < 1 || !colptr || !rowind) return CHD_ERR_INVALID;
+  vector<vector<int32_t>> adj;
+  if (!build_adjacency(n, colptr, rowind, adj)) return CHD_ERR_INVALID;
+  perm.assign(n, 0);
+  if (opts.ordering == CHD_ORDER_NATURAL) {
+    std::iota(perm.begin(), perm.end(), 0);
+  } else if (opts.ordering == CHD_ORDER_USER) {
+    if (!opts.user_perm) return CHD_ERR_INVALID;
+    vector<char> seen(n, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t v = opts.user_perm[i];
+      if (v < 0 || v >= n || seen[v]) return CHD_ERR_INVALID;
+      seen[v] = 1;
+      perm[i] = v;
+    }
+  } else if (opts.ordering == CHD_ORDER_MINDEG) {
+    perm = minimum_degree(n, adj);
+  } else {
+    return CHD_ERR_INVALID;
+  }
+  return CHD_OK;
+}
+
 void chd_opts_default(chd_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
@@ -544,16 +571,14 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
         ttier.push_back(tier[t]);
       }
     }
-    // a task's level must exceed the levels of all tasks it depends on
-    bool changed = true;
-    while (changed) {
-      changed = false;
-      for (int64_t t = 0; t < nsn; ++t) {
-        int64_t tk = task_of[t];
-        for (int64_t q = s->ch_ptr[t]; q < s->ch_ptr[t + 1]; ++q) {
-          int64_t tc = task_of[s->ch[q]];
-          if (tc != tk && tlevel[tk] <= tlevel[tc]) { tlevel[tk] = tlevel[tc] + 1; changed = true; }
-        }
+    // A task's level must exceed the levels of all tasks it depends on.  One
+    // pass in postorder suffices: when front t is reached, every child task
+    // that ends below t is complete (its fronts all precede t).
+    for (int64_t t = 0; t < nsn; ++t) {
+      const int64_t tk = task_of[t];
+      for (int64_t q = s->ch_ptr[t]; q < s->ch_ptr[t + 1]; ++q) {
+        const int64_t tc = task_of[s->ch[q]];
+        if (tc != tk && tlevel[tk] <= tlevel[tc]) tlevel[tk] = tlevel[tc] + 1;
       }
     }
     int64_t nlev = 0;

@@ -160,6 +160,11 @@ struct GSym {  // symmetric, lower stored, global memory
     return r >= c ? p[r + (int64_t)c * ld] : p[c + (int64_t)r * ld];
   }
 };
+struct PkBlk {  // the diagonal block starting at row/column o of the packed front (lower use)
+  double* F;
+  int J, o;
+  __device__ double& operator()(int r, int c) const { return F[pk(J, o + r, o + c)]; }
+};
 struct CscOut {  // output rows [ro, ..) of the N-part in a CSC array
   double* p;
   int J, ro;
@@ -526,19 +531,22 @@ __device__ void complete_front(const SymDev& S, int k, const double* Sin, double
   const int nz = nnz_front(f);
   for (int e = lane; e < nz; e += 32) m.F[e] = Sin[f.base + e];
   __syncwarp();
+  // the children gather from the S-front in the workspace; after this copy
+  // the A x A block in shared memory is free to hold R = chol(V)
+  write_full(f, m, lane);
   double* V = Vd + S.v_off[k];
   double* R = Rd + S.v_off[k];
   for (int e = lane; e < a * a; e += 32) {
     const int r = e % a, s = e / a;
-    if (r >= s) {
-      const double v = m.F[pk(J, n + r, n + s)];
-      V[r + s * a] = v;
-      R[r + s * a] = v;
-    }
+    if (r >= s) V[r + s * a] = m.F[pk(J, n + r, n + s)];
   }
   __syncwarp();
-  GL Rv{R, a};
+  PkBlk Rv{m.F, J, n};
   if (a > 0) wpotrf(a, Rv, st, CHD_ERR_NOT_COMPLETABLE, k, -1, lane);
+  for (int e = lane; e < a * a; e += 32) {
+    const int r = e % a, s = e / a;
+    if (r >= s) R[r + s * a] = m.F[pk(J, n + r, n + s)];
+  }
   // A1 = Z = R^{-1} S_AN
   for (int e = lane; e < a * n; e += 32) {
     const int r = e % a, c = e / a;
@@ -609,7 +617,6 @@ __device__ void complete_front(const SymDev& S, int k, const double* Sin, double
     for (int i = 0; i < n; ++i) s += 2.0 * log(m.D2[i + i * WN]);
     ldet[k] = s;
   }
-  write_full(f, m, lane);
   __syncwarp();
 }
 

@@ -144,3 +144,22 @@ def test_supernode_splitting_keeps_the_pattern(split):
         if len(J) > nk:
             p = par[k]
             assert sp[p] <= J[nk] < sp[p + 1]
+
+
+def test_batch_analysis_equals_single_analyses():
+    """chd_analyze_batch: each instance keeps its own ordering, fill and
+    supernodes, in a contiguous block of the union (bit-exact)."""
+    B = lib()
+    rng = np.random.default_rng(31)
+    pats = [W.band(50, 3), W.arrow(40, 5), W.permute(W.grid2d(8, 8), W.nested_dissection((8, 8), leaf=4)),
+            W.erdos_renyi(60, 0.05, rng), W.band(7, 6)]
+    ords = ["natural", "natural", "natural", "mindeg", "natural"]
+    sb = B.SymbolicBatch(pats, orderings=ords)
+    assert sb.count == len(pats)
+    assert sb.nsuper == sum(B.Symbolic(*p, ordering=o).nsuper for p, o in zip(pats, ords))
+    for i, (p, o) in enumerate(zip(pats, ords)):
+        (ni, cp, ri), perm = sb.instance_pattern(i)
+        s1 = B.Symbolic(*p, ordering=o)
+        assert ni == s1.n
+        assert (perm == s1.perm).all()
+        assert (cp == s1.colptr).all() and (ri == s1.rowind).all()

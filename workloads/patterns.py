@@ -173,3 +173,23 @@ def pattern_hash(pattern):
     h.update(np.asarray(colptr, np.int64).tobytes())
     h.update(np.asarray(rowind, np.int32).tobytes())
     return h.hexdigest()[:16]
+
+
+def batch_mix(count, seed, nmin=300, nmax=30000):
+    """Independent instances for batched runs: n log-uniform in [nmin, nmax],
+    a third each band (half-bandwidth uniform in 4..64), block arrow (arrow
+    width 32) and 2D grid (side round(sqrt(n))) with a geometric nested
+    dissection order.  Returns a list of (pattern, perm or None, kind)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(nmin), np.log(nmax)))))
+        kind = ("band", "arrow", "grid")[i % 3]
+        if kind == "band":
+            out.append((band(n, int(rng.integers(4, 65))), None, kind))
+        elif kind == "arrow":
+            out.append((arrow(n, 32), None, kind))
+        else:
+            side = max(2, int(round(np.sqrt(n))))
+            out.append((grid2d(side, side), nested_dissection((side, side), leaf=8), kind))
+    return out
