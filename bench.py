@@ -61,6 +61,25 @@ def make_workload(name):
                          "[300, 30000], a third each band (half-bandwidth 4..64), block arrow (width 32), "
                          "2D grid with nested dissection; X diag-dominant, 4 Y per instance, "
                          "S=P(GG^T+0.5I) G nx20")
+    if name == "serve":
+        rng = np.random.default_rng(4)
+        pool = []
+        for i in range(31):
+            n = int(round(np.exp(rng.uniform(np.log(1000), np.log(60000)))))
+            kind = ("band", "arrow", "grid")[i % 3]
+            if kind == "band":
+                pool.append((W.band(n, int(rng.integers(4, 65))), None))
+            elif kind == "arrow":
+                pool.append((W.arrow(n, 32), None))
+            else:
+                side = max(2, int(round(np.sqrt(n))))
+                pool.append((W.grid2d(side, side), W.nested_dissection((side, side), leaf=8)))
+        pool.append((W.grid3d(40, 40, 40), W.nested_dissection((40, 40, 40), leaf=8)))
+        return dict(name=name, pool=pool, m=16, seed=4, gram=(20, 0.5), rate=2000.0,
+                    mix={"factor": 0.1, "gradient": 0.2, "hessian": 0.5, "inv_hessian": 0.1, "completion": 0.1},
+                    desc="serving: Poisson 2000 req/s over 32 resident patterns (n log-uniform 1k..60k: band, "
+                         "arrow, 2D ND grid; plus the 40x40x40 7-point grid under ND), mix 10% factor, 20% "
+                         "gradient, 50% Hessian (m ~ U{1..16}), 10% inverse Hessian, 10% completion")
     if name == "grid150":
         return dict(name=name, pattern=W.grid2d(150, 150),
                     opts=dict(perm=W.nested_dissection((150, 150), leaf=8)), m=64, seed=2,
@@ -451,14 +470,66 @@ def run_ours(args, wl, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args, wl):
+    """Serving benchmark: the same bounded Poisson trace served with continuous
+    batching on 8 streams and replayed one request at a time."""
+    import torch
+    from paper_1203_2742_gb300 import build
+    build.build()
+    from paper_1203_2742_gb300 import binding as B
+    from paper_1203_2742_gb300 import serve
+    t0 = time.perf_counter()
+    pool = []
+    for (pat, perm) in wl["pool"]:
+        sym = B.Symbolic(*pat, perm=perm) if perm is not None else B.Symbolic(*pat)
+        x, _, s = workload_values(dict(wl, m=1), sym.n, sym.colptr, sym.rowind)
+        pool.append((sym, x, s))
+    analyze_s = time.perf_counter() - t0
+    rng = np.random.default_rng(wl["seed"])
+    duration = args.serve_seconds
+    trace = serve.poisson_trace(len(pool), wl["rate"], duration, wl["mix"], rng, lambda i: pool[i][0].nnz,
+                                max_m=wl["m"])
+    launches0 = B.chd_kernel_launches()
+    srv = serve.Server(pool, workers=8, batching=True)
+    srv.warm()
+    sampler = ClockSampler(0)
+    sampler.start()
+    stats, done = serve.replay(srv, trace)
+    clocks = sampler.stop()
+    launches = B.chd_kernel_launches() - launches0
+    srv = None
+    torch.cuda.empty_cache()
+    one = serve.Server(pool, workers=1, batching=False)
+    one.warm()
+    trace2 = [serve.Request(op=r.op, pattern=r.pattern, arrival=r.arrival, data=r.data, m=r.m, rid=r.rid)
+              for r in trace]
+    stats1, _ = serve.replay(one, trace2)
+    h2d = sum(8 * r.m * pool[r.pattern][0].nnz for r in trace if r.op in ("hessian", "inv_hessian"))
+    line = {
+        "metric": METRIC, "value": stats["hessian_evals_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": 1, "warmup": args.warmup, "ms_per_step": stats["wall_s"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "trace_seconds": duration, "requests": len(trace),
+                   "patterns": len(pool), "workers": 8, "parallelism": "single GPU"},
+        "served": stats, "one_at_a_time": stats1,
+        "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
+        "e2e": {"value": stats["hessian_evals_per_s"], "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(h2d)},
+        "roofline": None, "cpu_baseline": None, "gpu_launches": int(launches), "clocks": clocks,
+        "analyze_s": analyze_s,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="er5000", choices=["er5000", "band200", "grid150", "batch256"])
+    ap.add_argument("--workload", default="er5000", choices=["er5000", "band200", "grid150", "batch256", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=0.5, help="trace length of the serve workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -470,6 +541,10 @@ def main():
         if rank != 0:
             return
         run_reference(args, wl)
+        return
+    if "pool" in wl:
+        if rank == 0:
+            run_serve(args, wl)
         return
     if world > 1:
         import torch

@@ -267,6 +267,21 @@ chd_status chd_probe_fp64_peak(void* stream, double* gflops);
 void chd_factor_free(chd_factor* fac);
 
 /*
+ * Workspace control of a factor object (device memory the library holds for
+ * the per-front workspace of Hessian-type calls; it grows to the largest
+ * batch of right-hand sides a call processes at once).
+ *   chd_factor_set_workspace_limit: cap it at `bytes` (0 = library default,
+ *     48 GiB); larger batches are processed in chunks, at least one
+ *     right-hand side at a time.
+ *   chd_factor_release_workspace: synchronise the factor's stream and free
+ *     the workspace (the next call allocates it again).
+ *   chd_factor_workspace_bytes: bytes currently held.
+ */
+chd_status chd_factor_set_workspace_limit(chd_factor* fac, size_t bytes);
+chd_status chd_factor_release_workspace(chd_factor* fac);
+chd_status chd_factor_workspace_bytes(const chd_factor* fac, size_t* bytes);
+
+/*
  * Hessian products that allocate nothing.  The paper has no counterpart:
  * this is a service entry point of the library.
  *

@@ -74,6 +74,12 @@ _lib.chd_hessian_noalloc.argtypes = [_p, C.c_int, _p, _i64, _p, _i64, _p]
 _lib.chd_hessian_noalloc.restype = C.c_int
 _lib.chd_probe_fp64_peak.argtypes = [_p, C.POINTER(C.c_double)]
 _lib.chd_probe_fp64_peak.restype = C.c_int
+_lib.chd_factor_set_workspace_limit.argtypes = [_p, C.c_size_t]
+_lib.chd_factor_set_workspace_limit.restype = C.c_int
+_lib.chd_factor_release_workspace.argtypes = [_p]
+_lib.chd_factor_release_workspace.restype = C.c_int
+_lib.chd_factor_workspace_bytes.argtypes = [_p, C.POINTER(C.c_size_t)]
+_lib.chd_factor_workspace_bytes.restype = C.c_int
 _lib.chd_factor_free.argtypes = [_p]
 _lib.chd_factor_free.restype = None
 for _f in ("chd_analyze", "chd_analyze_batch", "chd_symbolic_batch_info", "chd_logdet_batch", "chd_symbolic_info", "chd_symbolic_supernodes", "chd_symbolic_flops",
@@ -463,6 +469,17 @@ class Factor:
 
     def status(self):
         return chd_status_get(self._h)
+
+    def set_workspace_limit(self, nbytes):
+        _check(_lib.chd_factor_set_workspace_limit(self._h, int(nbytes)), "chd_factor_set_workspace_limit")
+
+    def release_workspace(self):
+        _check(_lib.chd_factor_release_workspace(self._h), "chd_factor_release_workspace")
+
+    def workspace_bytes(self):
+        v = C.c_size_t()
+        _check(_lib.chd_factor_workspace_bytes(self._h, C.byref(v)), "chd_factor_workspace_bytes")
+        return int(v.value)
 
     def error_detail(self):
         return chd_error_detail(self._h)

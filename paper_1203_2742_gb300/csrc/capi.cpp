@@ -125,7 +125,8 @@ chd_status ensure_ws(chd_factor* f, int64_t rhs) {
 
 int64_t rhs_chunk(const chd_factor* f, int m) {
   const size_t per = std::max<size_t>((size_t)f->sym->dev.f_total * 8, 1);
-  int64_t c = (int64_t)(kWorkspaceCap / per);
+  const size_t cap = f->ws_limit ? std::min(f->ws_limit, kWorkspaceCap) : kWorkspaceCap;
+  int64_t c = (int64_t)(cap / per);
   return std::max<int64_t>(1, std::min<int64_t>(c, m));
 }
 
@@ -477,6 +478,30 @@ chd_status chd_error_detail(chd_factor* f, int64_t* supernode, int64_t* column) 
 }
 
 int64_t chd_kernel_launches(void) { return chd_launch::launches(); }
+
+chd_status chd_factor_set_workspace_limit(chd_factor* f, size_t bytes) {
+  if (!f) return CHD_ERR_INVALID;
+  f->ws_limit = bytes;
+  return CHD_OK;
+}
+
+chd_status chd_factor_release_workspace(chd_factor* f) {
+  if (!f) return CHD_ERR_INVALID;
+  if (f->ws) {
+    chd_status rc = cuda_ok(cudaStreamSynchronize(f->stream));
+    if (rc != CHD_OK) return rc;
+    cudaFree(f->ws);
+    f->ws = nullptr;
+    f->ws_rhs = 0;
+  }
+  return CHD_OK;
+}
+
+chd_status chd_factor_workspace_bytes(const chd_factor* f, size_t* bytes) {
+  if (!f || !bytes) return CHD_ERR_INVALID;
+  *bytes = (size_t)f->ws_rhs * (size_t)f->sym->dev.f_total * 8;
+  return CHD_OK;
+}
 
 chd_status chd_probe_fp64_peak(void* stream, double* gflops) {
   if (!gflops) return CHD_ERR_INVALID;

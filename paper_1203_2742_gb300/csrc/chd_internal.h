@@ -107,6 +107,7 @@ struct chd_factor {
   Exec ex;                   // dense-tier streams and split-K scratch
   double* inst_sum = nullptr;  // per-instance log det sums (batched symbolic objects)
   int64_t ws_rhs = 0;        // capacity in right-hand sides
+  size_t ws_limit = 0;       // caller's cap on the workspace (0: library default)
   bool have_S = false;
   bool have_R = false;
 };

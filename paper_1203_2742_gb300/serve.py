@@ -1,0 +1,284 @@
+"""Request serving on one GPU: resident factors, admission by device-memory
+footprint, continuous batching.
+
+Requests (factor, gradient, Hessian with m right-hand sides, inverse Hessian,
+completion) name one of the registered patterns.  Every pattern is analysed
+once; its factor object, its completion object and their cached blocks stay
+resident on the device, so later calls reuse them.  Worker threads each own a
+CUDA stream and take requests as they arrive: requests that arrive while
+others run are admitted as soon as a worker and enough device memory (the
+footprint of the request's inputs, outputs and workspace, against a budget)
+are free, and their kernels overlap on the device with the running ones.
+A worker that takes a Hessian or inverse-Hessian request also takes the
+waiting requests of the same kind for the same pattern and runs them as one
+call with m = the sum of their right-hand sides (continuous batching).
+Calls on one pattern are serialised by a per-pattern lock (a factor object
+has one workspace); different patterns run concurrently.
+
+The server computes through the C ABI only (``binding``); it holds no
+numerical code of its own.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import binding as B
+
+OPS = ("factor", "gradient", "hessian", "inv_hessian", "completion")
+
+
+@dataclass
+class Request:
+    op: str
+    pattern: int
+    arrival: float                      # seconds on the server clock
+    data: object = None                 # host array (m, nnz) for hessian / inv_hessian
+    m: int = 1
+    rid: int = 0
+    # filled by the server
+    start: float = 0.0
+    done: float = 0.0
+    result: object = None
+    batched_with: int = 1
+
+
+@dataclass
+class PatternState:
+    sym: object
+    x: object          # device values of X (fixed per pattern)
+    s: object          # device values of S (fixed per pattern)
+    fac: object = None
+    cfac: object = None
+    lock: threading.Lock = field(default_factory=threading.Lock)
+    ws_bytes_per_rhs: int = 0
+
+
+class Server:
+    """Continuous-batching server over resident factors.
+
+    patterns: list of (Symbolic, x_host, s_host) -- values already on the
+    analysed pattern.  workers: concurrent streams.  budget_bytes: device
+    memory the in-flight requests may hold (inputs, outputs, workspace).
+    batching: merge waiting same-pattern Hessian / inverse-Hessian requests.
+    """
+
+    def __init__(self, patterns, workers=8, budget_bytes=None, batching=True, max_batch_rhs=64,
+                 keep_workspace_bytes=1 << 30):
+        import torch
+        self.torch = torch
+        self.batching = batching
+        self.max_batch_rhs = max_batch_rhs
+        self.states = []
+        for sym, x, s in patterns:
+            d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+            st = PatternState(sym=sym, x=d(x), s=d(s))
+            sp, par, rp, rows = sym.supernodes()
+            nn, J = np.diff(sp), np.diff(rp)
+            st.ws_bytes_per_rhs = int(8 * np.sum(J * J + 2 * J * nn))
+            self.states.append(st)
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info()
+            budget_bytes = int(0.5 * free)
+        self.budget = budget_bytes
+        # per-request workspace cap: a worker's share of the budget
+        self.ws_limit = max(1, budget_bytes // max(1, workers))
+        self.keep_ws = keep_workspace_bytes
+        self.in_use = 0
+        self.nworkers = workers
+        self.cv = threading.Condition()
+        self.queue = collections.deque()
+        self.closed = False
+        self.completed = []
+        self.t0 = None
+        self.threads = []
+
+    # -- resident state -------------------------------------------------------
+    def warm(self):
+        """Factor every pattern once (resident factors) and cache S for Hessians."""
+        for st in self.states:
+            st.fac = st.sym.factor(st.x)
+            st.fac.set_workspace_limit(self.ws_limit)
+            st.fac.gradient()
+            st.cfac, _ = st.sym.complete(st.s)
+            st.cfac.set_workspace_limit(self.ws_limit)
+            for f in (st.fac, st.cfac):
+                if f.workspace_bytes() > self.keep_ws:
+                    f.release_workspace()
+        self.torch.cuda.synchronize()
+
+    def footprint(self, req):
+        """Device bytes a request may hold: its inputs and outputs and the
+        workspace of the right-hand sides the library processes at once
+        (it works in chunks of at most 48 GiB of workspace)."""
+        st = self.states[req.pattern]
+        nnz = st.sym.nnz
+        per = max(st.ws_bytes_per_rhs, 1)
+        chunk = max(1, self.ws_limit // per)
+        if req.op in ("hessian", "inv_hessian"):
+            return 8 * 2 * req.m * nnz + min(req.m, chunk) * per
+        return 8 * 2 * nnz + per
+
+    # -- request flow ---------------------------------------------------------
+    def now(self):
+        return time.perf_counter() - self.t0
+
+    def submit(self, req):
+        with self.cv:
+            self.queue.append(req)
+            self.cv.notify()
+
+    def close(self):
+        with self.cv:
+            self.closed = True
+            self.cv.notify_all()
+
+    def _take(self):
+        """Next admissible request (FIFO among those that fit), plus, when
+        batching, the waiting same-pattern requests of the same kind."""
+        with self.cv:
+            while True:
+                for i, req in enumerate(self.queue):
+                    need = self.footprint(req)
+                    if self.in_use + need <= self.budget or self.in_use == 0:
+                        del self.queue[i]
+                        group = [req]
+                        if self.batching and req.op in ("hessian", "inv_hessian"):
+                            rhs = req.m
+                            keep = collections.deque()
+                            while self.queue:
+                                r2 = self.queue.popleft()
+                                if (r2.op == req.op and r2.pattern == req.pattern
+                                        and rhs + r2.m <= self.max_batch_rhs):
+                                    group.append(r2)
+                                    rhs += r2.m
+                                    need += self.footprint(r2)
+                                else:
+                                    keep.append(r2)
+                            self.queue = keep
+                        self.in_use += need
+                        return group, need
+                if self.closed and not self.queue:
+                    return None, 0
+                self.cv.wait(timeout=0.05)
+
+    def _release(self, need):
+        with self.cv:
+            self.in_use -= need
+            self.cv.notify_all()
+
+    def _run_group(self, group, stream):
+        torch = self.torch
+        req = group[0]
+        st = self.states[req.pattern]
+        nnz = st.sym.nnz
+        with st.lock, torch.cuda.stream(stream):
+            start = self.now()
+            if req.op == "factor":
+                st.fac.refactor(st.x, stream=stream)
+                res = [st.fac.logdet()]
+            elif req.op == "gradient":
+                g = torch.empty(nnz, dtype=torch.float64, device="cuda")
+                st.fac.gradient(out=g, stream=stream)
+                res = [g.cpu().numpy()]
+            elif req.op == "completion":
+                res = [st.cfac.recomplete(st.s, stream=stream)]
+            else:
+                host = np.concatenate([r.data.reshape(r.m, nnz) for r in group], axis=0)
+                inp = torch.as_tensor(host, dtype=torch.float64).pin_memory().to("cuda", non_blocking=True)
+                out = torch.empty_like(inp)
+                if req.op == "hessian":
+                    st.fac.hessian(inp, out=out, stream=stream)
+                else:
+                    st.fac.inv_hessian(inp, out=out, stream=stream)
+                allr = out.cpu().numpy()
+                res, o = [], 0
+                for r in group:
+                    res.append(allr[o:o + r.m])
+                    o += r.m
+            stream.synchronize()
+            # keep the resident memory of idle patterns small
+            for f in (st.fac, st.cfac):
+                if f.workspace_bytes() > self.keep_ws:
+                    f.release_workspace()
+            done = self.now()
+        for r, v in zip(group, res if len(res) == len(group) else res * len(group)):
+            r.start, r.done, r.result, r.batched_with = start, done, v, len(group)
+
+    def _worker(self):
+        torch = self.torch
+        stream = torch.cuda.Stream()
+        while True:
+            group, need = self._take()
+            if group is None:
+                return
+            try:
+                self._run_group(group, stream)
+            except Exception as e:  # a failed request must not stop the worker
+                t = self.now()
+                for r in group:
+                    r.start, r.done, r.result, r.batched_with = t, t, e, len(group)
+            finally:
+                self._release(need)
+                with self.cv:
+                    self.completed.extend(group)
+
+    def start(self):
+        self.t0 = time.perf_counter()
+        for _ in range(self.nworkers):
+            t = threading.Thread(target=self._worker, daemon=True)
+            t.start()
+            self.threads.append(t)
+
+    def join(self):
+        self.close()
+        for t in self.threads:
+            t.join()
+
+
+def poisson_trace(npatterns, rate, duration, mix, rng, nnz_of, max_m=16):
+    """Requests with exponential inter-arrival times (rate per second) over
+    `duration` seconds; op drawn from `mix` (dict op -> probability), pattern
+    uniform; Hessian-type requests carry m ~ U{1..max_m} right-hand sides
+    uniform[-1, 1] on the pattern."""
+    ops = list(mix)
+    p = np.array([mix[o] for o in ops], dtype=np.float64)
+    p /= p.sum()
+    t, out, rid = 0.0, [], 0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            break
+        op = ops[rng.choice(len(ops), p=p)]
+        pat = int(rng.integers(npatterns))
+        m = int(rng.integers(1, max_m + 1)) if op in ("hessian", "inv_hessian") else 1
+        data = rng.uniform(-1.0, 1.0, size=(m, nnz_of(pat))) if op in ("hessian", "inv_hessian") else None
+        out.append(Request(op=op, pattern=pat, arrival=t, data=data, m=m, rid=rid))
+        rid += 1
+    return out
+
+
+def replay(server, trace):
+    """Feed the trace at its arrival times, wait for every request, and return
+    latency statistics (seconds) and served throughput."""
+    server.start()
+    for req in trace:
+        delay = req.arrival - server.now()
+        if delay > 0:
+            time.sleep(delay)
+        server.submit(req)
+    server.join()
+    done = sorted(server.completed, key=lambda r: r.rid)
+    failed = [r for r in done if isinstance(r.result, Exception)]
+    lat = np.array([r.done - r.arrival for r in done])
+    wall = max(r.done for r in done) - min(r.arrival for r in done)
+    hess = sum(r.m for r in done if r.op == "hessian")
+    evals = sum(r.m for r in done)
+    return {"requests": len(done), "wall_s": wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "hessian_evals_per_s": hess / wall,
+            "evals_per_s": evals / wall, "requests_per_s": len(done) / wall,
+            "mean_batch": float(np.mean([r.batched_with for r in done])), "failed": len(failed)}, done
