@@ -244,13 +244,22 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
-def make_symbolic(B, wl):
+def make_symbolic(B, wl, **cfg):
     if "batch" in wl:
-        pats = [p for p, _, _ in wl["batch"]]
-        perms = [q for _, q, _ in wl["batch"]]
+        inst = wl["batch"] if "subset" not in cfg else [wl["batch"][i] for i in cfg.pop("subset")]
+        pats = [p for p, _, _ in inst]
+        perms = [q for _, q, _ in inst]
         ords = ["user" if q is not None else "natural" for q in perms]
-        return B.SymbolicBatch(pats, orderings=ords, perms=perms)
-    return B.Symbolic(*wl["pattern"], **wl["opts"])
+        return B.SymbolicBatch(pats, orderings=ords, perms=perms, **cfg)
+    return B.Symbolic(*wl["pattern"], **wl["opts"], **cfg)
+
+
+def tuned_config(B, wl):
+    """Tier cutovers of a batch chosen by the autotuner on every 8th instance."""
+    from paper_1203_2742_gb300 import autotune
+    subset = list(range(0, len(wl["batch"]), 8))
+    best, timings = autotune.tune(lambda **c: make_symbolic(B, wl, subset=subset, **c), wl["m"], reps=1)
+    return best, timings
 
 
 def analysed_pattern_host(wl):
@@ -281,8 +290,13 @@ def run_ours(args, wl, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
 
+    tune = None
+    cfg = {}
+    if "batch" in wl:
+        cfg, timings = tuned_config(B, wl)
+        tune = {"chosen": cfg, "timings_ms": timings, "on": "every 8th instance, Hessian with the same m"}
     t0 = time.perf_counter()
-    sym = make_symbolic(B, wl)
+    sym = make_symbolic(B, wl, **cfg)
     analyze_ms = (time.perf_counter() - t0) * 1e3
     count = getattr(sym, "count", 1)
     n, cp, ri, nnz = sym.n, sym.colptr, sym.rowind, sym.nnz
@@ -461,6 +475,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "clocks": clocks,
             "ops_ms": {k: round(v, 4) for k, v in ops_ms.items()},
             "instances": count,
+            "autotune": tune,
             "batched_vs_one_at_a_time": sequential,
             "step_tflops_fp64": step_flops / (ms_per_step * 1e-3) / 1e12,
             "analyze_ms": analyze_ms,

@@ -1,0 +1,74 @@
+"""Autotuner: the tier cutovers change how fronts map onto the GPU, never the
+results (beyond rounding); tuning picks one of the candidates and the table
+persists it."""
+import json
+
+import numpy as np
+import pytest
+
+from oracle import dense as OD
+import workloads as W
+from tests.helpers import lib
+
+pytestmark = pytest.mark.gpu
+
+CONFIGS = [dict(), dict(big_rows=16, big_cols=8), dict(big_rows=4096, big_cols=4096),
+           dict(split_cols=8), dict(big_rows=40, big_cols=12, split_cols=16)]
+
+
+@pytest.mark.parametrize("case", ["grid", "er"])
+def test_results_invariant_under_tier_settings(case):
+    import torch
+    B = lib()
+    if case == "grid":
+        pat, kw = W.permute(W.grid2d(24, 24), W.nested_dissection((24, 24), leaf=6)), {}
+    else:
+        pat, kw = W.erdos_renyi(260, 0.03, np.random.default_rng(61)), dict(ordering="mindeg", relax=8)
+    ref = None
+    for cfg in CONFIGS:
+        sym = B.Symbolic(*pat, **kw, **cfg)
+        rng = np.random.default_rng(62)
+        x = W.diag_dominant(sym.n, sym.colptr, sym.rowind, rng)
+        ys = W.uniform_sym(sym.n, sym.colptr, sym.rowind, rng, count=3)
+        s = W.projected_gram(sym.n, sym.colptr, sym.rowind, rng.standard_normal((sym.n, 6)), 0.5)
+        dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+        f = sym.factor(dev(x))
+        out = dict(ld=f.logdet(), g=f.gradient().cpu().numpy(), t=f.hessian(dev(ys)).cpu().numpy(),
+                   y=f.inv_hessian(dev(ys)).cpu().numpy())
+        fx, fstar = sym.complete(dev(s))
+        out["fstar"] = fstar
+        out["xl"] = fx.export()[0].cpu().numpy()
+        if ref is None:
+            ref, rsym = out, sym
+            want = OD.hessian(sym.n, sym.colptr, sym.rowind, x, list(ys))
+            for j in range(3):
+                assert OD.rel_err(sym.n, sym.colptr, sym.rowind, out["t"][j], want[j]) < 1e-10
+            continue
+        # same analysed pattern whatever the tier settings (splitting keeps V)
+        assert (sym.colptr == rsym.colptr).all() and (sym.rowind == rsym.rowind).all()
+        err = lambda a, b: OD.rel_err(sym.n, sym.colptr, sym.rowind, a, b)
+        assert abs(out["ld"] - ref["ld"]) < 1e-12 * abs(ref["ld"])
+        assert abs(out["fstar"] - ref["fstar"]) < 1e-12 * abs(ref["fstar"])
+        assert err(out["g"], ref["g"]) < 1e-12
+        assert err(out["xl"], ref["xl"]) < 1e-12
+        for j in range(3):
+            assert err(out["t"][j], ref["t"][j]) < 1e-12
+            assert err(out["y"][j], ref["y"][j]) < 1e-12
+
+
+def test_tune_and_table(tmp_path):
+    B = lib()
+    from paper_1203_2742_gb300 import autotune
+    pat = W.permute(W.grid2d(30, 30), W.nested_dissection((30, 30), leaf=6))
+    make = lambda **cfg: B.Symbolic(*pat, **cfg)
+    cands = (dict(big_rows=64, big_cols=32), dict(big_rows=4096, big_cols=4096))
+    path = str(tmp_path / "tune.json")
+    table = autotune.Table(path)
+    sym, cfg, sig = autotune.analyze_tuned(make, 4, table, candidates=cands)
+    assert cfg in [dict(c) for c in cands]
+    assert table.lookup(sig) == cfg
+    again = autotune.Table(path)  # persisted
+    assert again.lookup(sig) == cfg
+    with open(path) as f:
+        data = json.load(f)
+    assert len(data[sig]["timings_ms"]) == len(cands)
