@@ -282,6 +282,21 @@ chd_status chd_factor_release_workspace(chd_factor* fac);
 chd_status chd_factor_workspace_bytes(const chd_factor* fac, size_t* bytes);
 
 /*
+ * CUDA graphs of the launch sequences (not part of the paper; an execution
+ * device of the library).  With graphs on (the default), a call of the same
+ * kind with the same arguments as the previous one (device pointers, m,
+ * strides) replays a graph of its kernel launches: the second such call
+ * captures it, later ones replay it on the factor's private stream, which
+ * waits for `stream` and which `stream` then waits for (events, no host
+ * synchronisation).  Results are bitwise those of the direct launches.  A
+ * graph holds the device pointers it was captured with: the caller must keep
+ * those buffers allocated while it keeps calling with them (a call with other
+ * pointers simply runs directly).  on = 0 destroys the graphs and runs every
+ * call directly.  Returns CHD_ERR_INVALID for a NULL factor.
+ */
+chd_status chd_factor_set_graphs(chd_factor* fac, int on);
+
+/*
  * Hessian products that allocate nothing.  The paper has no counterpart:
  * this is a service entry point of the library.
  *

@@ -80,6 +80,8 @@ _lib.chd_factor_release_workspace.argtypes = [_p]
 _lib.chd_factor_release_workspace.restype = C.c_int
 _lib.chd_factor_workspace_bytes.argtypes = [_p, C.POINTER(C.c_size_t)]
 _lib.chd_factor_workspace_bytes.restype = C.c_int
+_lib.chd_factor_set_graphs.argtypes = [_p, C.c_int]
+_lib.chd_factor_set_graphs.restype = C.c_int
 _lib.chd_factor_free.argtypes = [_p]
 _lib.chd_factor_free.restype = None
 for _f in ("chd_analyze", "chd_analyze_batch", "chd_symbolic_batch_info", "chd_logdet_batch", "chd_symbolic_info", "chd_symbolic_supernodes", "chd_symbolic_flops",
@@ -475,6 +477,10 @@ class Factor:
 
     def release_workspace(self):
         _check(_lib.chd_factor_release_workspace(self._h), "chd_factor_release_workspace")
+
+    def set_graphs(self, on):
+        """Replay repeated calls with the same arguments from CUDA graphs (default on)."""
+        _check(_lib.chd_factor_set_graphs(self._h, 1 if on else 0), "chd_factor_set_graphs")
 
     def workspace_bytes(self):
         v = C.c_size_t()

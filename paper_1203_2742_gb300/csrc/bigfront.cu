@@ -25,8 +25,6 @@ namespace big {
 constexpr int BT = 256;  // threads per CTA
 constexpr int GT = 64;   // GEMM output tile
 constexpr int GK = 16;   // GEMM k-chunk
-constexpr int PW = 64;   // panel width of blocked factorisations / solves
-constexpr int RB = 64;   // rows per CTA in the panel solve
 
 template <class V>
 __device__ __forceinline__ V shifted(V v, int64_t off) {
@@ -34,14 +32,23 @@ __device__ __forceinline__ V shifted(V v, int64_t off) {
   return v;
 }
 
-// Launch context of the dense tier: the stream, and a scratch buffer for
-// split-K partial products (may be absent: then no split).
+// Launch context of the dense tier: the stream, a scratch buffer for split-K
+// partial products and the counter of the Cholesky panel kernel (both may be
+// absent: then no split, and panels take two launches).
 struct Ctx {
   cudaStream_t s;
   double* xs;
   int64_t cap;  // doubles
+  int* ctr;
   operator cudaStream_t() const { return s; }
 };
+// A stream's scratch slice of xcap doubles: the first xcap - kCtrDoubles hold
+// split-K partials, the rest the panel counter (zeroed when allocated).
+constexpr int64_t kCtrDoubles = 8;
+inline Ctx make_ctx(cudaStream_t s, double* xs, int64_t xcap) {
+  if (!xs || xcap <= kCtrDoubles) return Ctx{s, nullptr, 0, nullptr};
+  return Ctx{s, xs, xcap - kCtrDoubles, reinterpret_cast<int*>(xs + (xcap - kCtrDoubles))};
+}
 
 // ---------------------------------------------------------------------------
 // batched tiled GEMM: C = beta*C + alpha*A(MxK)*B(KxN), lower triangle only
@@ -168,120 +175,205 @@ void gemm_cfg(const Ctx& st, int batch, int M, int N, int K, double alpha, MA A,
   }
 }
 
+// Output tiles of a product: the FP64 rate of one SM is low (about 1.6
+// lane-FMAs per clock), so a product is worth splitting into smaller tiles
+// whenever 64 x 64 tiles would leave SMs idle; split-K (gemm_cfg) covers
+// long K on top of that.
+inline int64_t tile_count(int M, int N, int bm, int bn, bool lower) {
+  const int64_t tm = (M + bm - 1) / bm, tn = (N + bn - 1) / bn;
+  return lower && bm == bn && tm == tn ? tm * (tm + 1) / 2 : tm * tn;
+}
+
 template <class MA, class MB, class MC>
 void gemm(const Ctx& st, int batch, int M, int N, int K, double alpha, MA A, int64_t sA, MB B, int64_t sB,
           double beta, MC C, int64_t sC, bool lower) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
+  constexpr int64_t kFill = 2 * 152;
   if (N <= 8 && M > 64) gemm_cfg<128, 8, 4, 1>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
   else if (N <= 16 && M > 64) gemm_cfg<128, 16, 4, 2>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
   else if (M <= 8 && N > 64) gemm_cfg<8, 128, 1, 4>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
   else if (M <= 16 && N > 64) gemm_cfg<16, 128, 2, 4>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
-  else gemm_cfg<64, 64, 4, 4>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
+  else if (tile_count(M, N, 64, 64, lower) * batch >= kFill || K >= 512)
+    gemm_cfg<64, 64, 4, 4>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
+  else if (tile_count(M, N, 32, 32, lower) * batch >= kFill || M <= 32 || N <= 32)
+    gemm_cfg<32, 32, 2, 2>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
+  else
+    gemm_cfg<16, 16, 1, 1>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky of one diagonal block (<= 64 x 64) in shared memory, one CTA.
+// Blocked right-looking Cholesky (panels of PP columns) and triangular
+// solves (panels of TW columns).  FP64 throughput per SM is low (about 1.6
+// lane-FMAs per clock), so the panel kernels give every SM only a few rows:
+// one warp per CTA, 8 rows per warp, 4 lanes per row (lane q of a row owns
+// the panel columns c = q mod 4), the substitution along the panel columns
+// exchanging each solved entry with a shuffle inside the 4-lane group.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(BT) mk_potrf_diag(double* F, int64_t ld, int j0, int jb, int64_t* st,
-                                                    int64_t code, int64_t snode, int64_t col0) {
-  __shared__ double Ls[PW][PW + 1];
-  const int tid = threadIdx.x;
-  for (int e = tid; e < jb * jb; e += BT) {
-    const int r = e % jb, c = e / jb;
-    Ls[r][c] = r >= c ? F[(j0 + r) + (int64_t)(j0 + c) * ld] : 0.0;
-  }
-  __syncthreads();
-  for (int j = 0; j < jb; ++j) {
-    if (tid == 0) {
-      double d = Ls[j][j];
+constexpr int PP = 32;  // Cholesky panel width
+constexpr int TW = 64;  // triangular-solve panel width
+constexpr int PR = 8;   // panel rows per CTA
+
+// Cholesky of the pb x pb (pb <= 32) lower block held by one warp, lane i
+// holding row i in registers (a[c] = A(i, c), c <= i); every column's
+// entries reach the other lanes by shuffles.  On return the lanes hold the
+// rows of C and rinv (shared) the reciprocal pivots.  A non-positive pivot
+// is recorded and replaced by 1.
+__device__ __forceinline__ void warp_potrf32(double (&a)[PP], double* rinv, int pb, int lane, int64_t* st,
+                                             int64_t code, int64_t snode, int64_t col) {
+#pragma unroll
+  for (int j = 0; j < PP; ++j) {
+    if (j < pb) {
+      double d = __shfl_sync(0xffffffffu, a[j], j);
       if (!(d > 0.0)) {
-        record_error(st, code, snode, col0 < 0 ? -1 : col0 + j0 + j);
+        if (lane == 0) record_error(st, code, snode, col < 0 ? -1 : col + j);
         d = 1.0;
       }
-      Ls[j][j] = sqrt(d);
+      const double r = rsqrt(d);
+      const double l = a[j] * r;  // L(lane, j) for lane > j
+      if (lane == j) {
+        a[j] = sqrt(d);
+        rinv[j] = r;
+      } else if (lane > j) {
+        a[j] = l;
+      }
+#pragma unroll
+      for (int k = j + 1; k < PP; ++k) {
+        const double lk = __shfl_sync(0xffffffffu, l, k);
+        if (lane >= k) a[k] = fma(-l, lk, a[k]);
+      }
     }
-    __syncthreads();
-    const double piv = Ls[j][j];
-    for (int i = j + 1 + tid; i < jb; i += BT) Ls[i][j] /= piv;
-    __syncthreads();
-    const int m = jb - j - 1;
-    for (int e = tid; e < m * m; e += BT) {
-      const int i = j + 1 + e % m, k = j + 1 + e / m;
-      if (i >= k) Ls[i][k] -= Ls[i][j] * Ls[k][j];
-    }
-    __syncthreads();
   }
-  for (int e = tid; e < jb * jb; e += BT) {
-    const int r = e % jb, c = e / jb;
-    if (r >= c) F[(j0 + r) + (int64_t)(j0 + c) * ld] = Ls[r][c];
+  __syncwarp();
+}
+
+// One panel of the Cholesky of F (ld): the pb x pb block at (j0, j0) and the
+// R rows below it (rows j0+pb ..).  Every CTA factors the diagonal block
+// (the same arithmetic in every CTA, so the copies agree bitwise) and
+// solves its PR rows, B := B C^{-T}.  The CTA that arrives last at the
+// counter -- when every CTA has read the unfactored block -- writes the
+// factored block back and resets the counter.  ctr == nullptr is allowed
+// for a single-CTA launch with R == 0.
+__global__ void __launch_bounds__(32) mk_potrf_panel(double* F, int64_t ld, int j0, int pb, int R, int* ctr,
+                                                     int64_t* st, int64_t code, int64_t snode, int64_t col0) {
+  __shared__ double Ls[PP][PP + 1];
+  __shared__ double rinv[PP];
+  __shared__ int last;
+  const int lane = threadIdx.x;
+  double* D = F + j0 + (int64_t)j0 * ld;
+  double a[PP];
+#pragma unroll
+  for (int c = 0; c < PP; ++c)
+    a[c] = (lane < pb && c < pb && lane >= c) ? D[lane + (int64_t)c * ld] : (c == lane ? 1.0 : 0.0);
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence();
+    last = (ctr == nullptr) ? 1 : (atomicAdd(ctr, 1) == (int)gridDim.x - 1);
+  }
+  warp_potrf32(a, rinv, pb, lane, st, code, snode, col0 < 0 ? -1 : col0 + j0);
+#pragma unroll
+  for (int c = 0; c < PP; ++c) Ls[lane][c] = a[c];
+  __syncwarp();
+  const int rr = lane >> 2, q = lane & 3;
+  const int i = blockIdx.x * PR + rr;
+  const bool ok = i < R;
+  double* Bi = F + (j0 + pb + (ok ? i : 0)) + (int64_t)j0 * ld;
+  double b[PP / 4];
+#pragma unroll
+  for (int u = 0; u < PP / 4; ++u) {
+    const int c = 4 * u + q;
+    b[u] = (ok && c < pb) ? Bi[(int64_t)c * ld] : 0.0;
+  }
+#pragma unroll
+  for (int c = 0; c < PP; ++c) {
+    if (c < pb) {
+      double x = b[c / 4] * rinv[c];
+      x = __shfl_sync(0xffffffffu, x, (lane & ~3) | (c & 3));
+      if (q == (c & 3)) b[c / 4] = x;
+#pragma unroll
+      for (int u = c / 4; u < PP / 4; ++u) {
+        const int t = 4 * u + q;
+        if (t > c && t < pb) b[u] = fma(-Ls[t][c], x, b[u]);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < PP / 4; ++u) {
+    const int c = 4 * u + q;
+    if (ok && c < pb) Bi[(int64_t)c * ld] = b[u];
+  }
+  if (last) {
+    for (int c = 0; c < pb; ++c)
+      if (lane < pb && lane >= c) D[lane + (int64_t)c * ld] = Ls[lane][c];
+    if (lane == 0 && ctr) *ctr = 0;
   }
 }
 
-// ---------------------------------------------------------------------------
-// Panel triangular solve on rows [64*blockIdx.x, +64) of B (R rows), panel
-// columns [p0, p0+pb) against the diagonal block L[p0.., p0..] (lower):
+// Panel triangular solve on PR rows per CTA of B (R rows), panel columns
+// [p0, p0+pb), pb <= TW, against the diagonal block L[p0.., p0..] (lower):
 //   fwd = 1:  B_p := B_p L_pp^{-T}      fwd = 0:  B_p := B_p L_pp^{-1}
-// ---------------------------------------------------------------------------
 template <class MB>
-__global__ void __launch_bounds__(BT) mk_trsm_panel(int R, MB B, int64_t sB, int p0, int pb, const double* L,
+__global__ void __launch_bounds__(32) mk_trsm_panel(int R, MB B, int64_t sB, int p0, int pb, const double* L,
                                                     int64_t ld, int fwd) {
-  extern __shared__ double smem[];
-  double* Ls = smem;                   // PW x (PW+1), row-major
-  double* Bs = smem + PW * (PW + 1);   // RB x (PW+1), row-major
-  const int64_t z = blockIdx.z;
-  B.p += z * sB;
-  const int r0 = blockIdx.x * RB;
-  const int rc = min(RB, R - r0);
-  const int tid = threadIdx.x;
-  for (int e = tid; e < pb * pb; e += BT) {
+  __shared__ double Ls[TW][TW + 1];
+  __shared__ double rinv[TW];
+  const int lane = threadIdx.x;
+  B.p += (int64_t)blockIdx.z * sB;
+  for (int e = lane; e < pb * pb; e += 32) {
     const int i = e % pb, j = e / pb;
-    Ls[i * (PW + 1) + j] = i >= j ? L[(p0 + i) + (int64_t)(p0 + j) * ld] : 0.0;
+    Ls[i][j] = i >= j ? L[(p0 + i) + (int64_t)(p0 + j) * ld] : 0.0;
   }
-  for (int e = tid; e < rc * pb; e += BT) {
-    const int r = e % rc, c = e / rc;
-    Bs[r * (PW + 1) + c] = B.at(r0 + r, p0 + c);
+  __syncwarp();
+  for (int c = lane; c < pb; c += 32) rinv[c] = 1.0 / Ls[c][c];
+  __syncwarp();
+  const int rr = lane >> 2, q = lane & 3;
+  const int r = blockIdx.x * PR + rr;
+  const bool ok = r < R;
+  double b[TW / 4];
+#pragma unroll
+  for (int u = 0; u < TW / 4; ++u) {
+    const int c = 4 * u + q;
+    b[u] = (ok && c < pb) ? B.at(r, p0 + c) : 0.0;
   }
-  __syncthreads();
   if (fwd) {
-    for (int c = 0; c < pb; ++c) {
-      const double inv = 1.0 / Ls[c * (PW + 1) + c];
-      for (int r = tid; r < rc; r += BT) Bs[r * (PW + 1) + c] *= inv;
-      __syncthreads();
-      const int m = pb - c - 1;
-      for (int e = tid; e < rc * m; e += BT) {
-        const int r = e % rc, t = c + 1 + e / rc;
-        Bs[r * (PW + 1) + t] -= Bs[r * (PW + 1) + c] * Ls[t * (PW + 1) + c];
+#pragma unroll
+    for (int c = 0; c < TW; ++c) {
+      if (c < pb) {
+        double x = b[c / 4] * rinv[c];
+        x = __shfl_sync(0xffffffffu, x, (lane & ~3) | (c & 3));
+        if (q == (c & 3)) b[c / 4] = x;
+#pragma unroll
+        for (int u = c / 4; u < TW / 4; ++u) {
+          const int t = 4 * u + q;
+          if (t > c && t < pb) b[u] = fma(-Ls[t][c], x, b[u]);
+        }
       }
-      __syncthreads();
     }
   } else {
-    for (int c = pb - 1; c >= 0; --c) {
-      const double inv = 1.0 / Ls[c * (PW + 1) + c];
-      for (int r = tid; r < rc; r += BT) Bs[r * (PW + 1) + c] *= inv;
-      __syncthreads();
-      for (int e = tid; e < rc * c; e += BT) {
-        const int r = e % rc, t = e / rc;
-        Bs[r * (PW + 1) + t] -= Bs[r * (PW + 1) + c] * Ls[c * (PW + 1) + t];
+#pragma unroll
+    for (int c = TW - 1; c >= 0; --c) {
+      if (c < pb) {
+        double x = b[c / 4] * rinv[c];
+        x = __shfl_sync(0xffffffffu, x, (lane & ~3) | (c & 3));
+        if (q == (c & 3)) b[c / 4] = x;
+#pragma unroll
+        for (int u = 0; u <= c / 4; ++u) {
+          const int t = 4 * u + q;
+          if (t < c) b[u] = fma(-Ls[c][t], x, b[u]);
+        }
       }
-      __syncthreads();
     }
   }
-  for (int e = tid; e < rc * pb; e += BT) {
-    const int r = e % rc, c = e / rc;
-    B.at(r0 + r, p0 + c) = Bs[r * (PW + 1) + c];
+#pragma unroll
+  for (int u = 0; u < TW / 4; ++u) {
+    const int c = 4 * u + q;
+    if (ok && c < pb) B.at(r, p0 + c) = b[u];
   }
 }
-constexpr size_t kPanelSmem = sizeof(double) * (PW * (PW + 1) + RB * (PW + 1));
 
 template <class MB>
 void panel_solve(const Ctx& st, int batch, int R, MB B, int64_t sB, int p0, int pb, const double* L,
                  int64_t ld, int fwd) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(mk_trsm_panel<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem);
-    attr = true;
-  }
-  mk_trsm_panel<MB><<<dim3((R + RB - 1) / RB, 1, batch), BT, kPanelSmem, st>>>(R, B, sB, p0, pb, L, ld, fwd);
+  mk_trsm_panel<MB><<<dim3((R + PR - 1) / PR, 1, batch), 32, 0, st>>>(R, B, sB, p0, pb, L, ld, fwd);
   chd_launch::count_launch();
 }
 
@@ -290,8 +382,8 @@ void panel_solve(const Ctx& st, int batch, int R, MB B, int64_t sB, int p0, int 
 template <class MB>
 void trsm_rLT(const Ctx& st, int batch, int R, int n, MB B, int64_t sB, const double* L, int64_t ld) {
   if (R <= 0 || n <= 0) return;
-  for (int p0 = 0; p0 < n; p0 += PW) {
-    const int pb = std::min(PW, n - p0);
+  for (int p0 = 0; p0 < n; p0 += TW) {
+    const int pb = std::min(TW, n - p0);
     panel_solve(st, batch, R, B, sB, p0, pb, L, ld, 1);
     const int rest = n - p0 - pb;
     if (rest > 0)
@@ -303,9 +395,9 @@ void trsm_rLT(const Ctx& st, int batch, int R, int n, MB B, int64_t sB, const do
 template <class MB>
 void trsm_rL(const Ctx& st, int batch, int R, int n, MB B, int64_t sB, const double* L, int64_t ld) {
   if (R <= 0 || n <= 0) return;
-  const int np = (n + PW - 1) / PW;
+  const int np = (n + TW - 1) / TW;
   for (int p = np - 1; p >= 0; --p) {
-    const int p0 = p * PW, pb = std::min(PW, n - p0);
+    const int p0 = p * TW, pb = std::min(TW, n - p0);
     panel_solve(st, batch, R, B, sB, p0, pb, L, ld, 0);
     if (p0 > 0)
       gemm(st, batch, R, p0, pb, -1.0, colshift(B, p0), sB, Dn{const_cast<double*>(L) + p0, ld}, 0, 1.0,
@@ -314,19 +406,26 @@ void trsm_rL(const Ctx& st, int batch, int R, int n, MB B, int64_t sB, const dou
 }
 
 // Partial Cholesky of the first n columns of the J x J matrix F (ld): F11 =
-// C C^T, F21 := F21 C^{-T}, F22 -= F21 F21^T (lower).  Not batched.
+// C C^T, F21 := F21 C^{-T}, F22 -= F21 F21^T (lower).  Not batched.  One
+// launch per panel (diagonal block and the rows below) when the context has
+// a panel counter, else the diagonal block and the row solve separately.
 void potrf_partial(const Ctx& st, double* F, int64_t ld, int J, int n, int64_t* status, int64_t code,
                    int64_t snode, int64_t col0) {
-  for (int j0 = 0; j0 < n; j0 += PW) {
-    const int jb = std::min(PW, n - j0);
-    mk_potrf_diag<<<1, BT, 0, st>>>(F, ld, j0, jb, status, code, snode, col0);
-    chd_launch::count_launch();
-    const int R = J - j0 - jb;
+  for (int j0 = 0; j0 < n; j0 += PP) {
+    const int pb = std::min(PP, n - j0);
+    const int R = J - j0 - pb;
+    if (st.ctr) {
+      mk_potrf_panel<<<std::max(1, (R + PR - 1) / PR), 32, 0, st>>>(F, ld, j0, pb, R, st.ctr, status, code,
+                                                                      snode, col0);
+      chd_launch::count_launch();
+    } else {
+      mk_potrf_panel<<<1, 32, 0, st>>>(F, ld, j0, pb, 0, nullptr, status, code, snode, col0);
+      chd_launch::count_launch();
+      if (R > 0) panel_solve(st, 1, R, Dn{F + j0 + pb, ld}, 0, j0, pb, F, ld, 1);
+    }
     if (R > 0) {
-      Dn below{F + j0 + jb, ld};
-      panel_solve(st, 1, R, below, 0, j0, jb, F, ld, 1);
-      double* P = F + (j0 + jb) + (int64_t)j0 * ld;
-      gemm(st, 1, R, R, jb, -1.0, Dn{P, ld}, 0, DnT{P, ld}, 0, 1.0, Dn{F + (j0 + jb) + (int64_t)(j0 + jb) * ld, ld},
+      double* P = F + (j0 + pb) + (int64_t)j0 * ld;
+      gemm(st, 1, R, R, pb, -1.0, Dn{P, ld}, 0, DnT{P, ld}, 0, 1.0, Dn{F + (j0 + pb) + (int64_t)(j0 + pb) * ld, ld},
            0, true);
     }
   }
@@ -438,6 +537,19 @@ __global__ void __launch_bounds__(BT) mk_gather_parent(SymDev S, int k, double* 
   for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
     const int r = (int)(e % a), s = (int)(e / a);
     if (r >= s) F[(n + r) + (int64_t)(n + s) * J] = __ldcg(Fp + __ldg(rel + r) + (int64_t)__ldg(rel + s) * Jp);
+  }
+}
+// V_k = S_{A_k A_k} of front k read directly from the input S (completion)
+__global__ void __launch_bounds__(BT) mk_gather_saa(SymDev S, int k, const double* Sin, double* ws) {
+  const int n = (int)(S.sn_ptr[k + 1] - S.sn_ptr[k]);
+  const int J = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]);
+  const int a = J - n;
+  double* F = ws + S.f_off[k];
+  const int32_t* A = S.rows + S.rows_ptr[k] + n;
+  const int64_t tot = (int64_t)a * a;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % a), c = (int)(e / a);
+    if (r >= c) F[(n + r) + (int64_t)(n + c) * J] = Sin[csc_find(S, __ldg(A + r), __ldg(A + c))];
   }
 }
 __global__ void k_logdet_diag(const double* F, int64_t ld, int n, double* out) {
@@ -649,11 +761,11 @@ void ihess_up_front(const chd_symbolic* s, const Ctx& st, int m, int k, const do
   CHD_EW(mk_ihess_finish, (int64_t)J * n, m, st, Y + f.base, ldy, F, T2, sw, J, n);
 }
 
-// S-front of a big front for the completion: V_k from the parent's front,
-// S_NN and S_AN from the input (top-down pass).
+// S-front of a big front for the completion: S_NN and S_AN from the input's
+// columns N_k, V_k = S_{A_k A_k} from the input's later columns.
 void complete_load_front(const chd_symbolic* s, const Ctx& st, int k, const double* Sin, double* ws) {
   Front f = front(s, k);
-  gather_parent(s, st, 1, f, ws, 0);
+  if (f.a > 0) CHD_EW(mk_gather_saa, (int64_t)f.a * f.a, 1, st, s->dev, k, Sin, ws);
   CHD_EW(mk_csc_to_front, (int64_t)f.J * f.n, 1, st, ws + f.foff, 0, f.J, f.n, Sin + f.base, 0);
 }
 
@@ -664,8 +776,7 @@ void complete_front(const chd_symbolic* s, const Ctx& st, int k, const double* S
   double* F = ws + f.foff;
   double* T1 = F + (int64_t)J * J;
   double* T2 = T1 + (int64_t)J * n;
-  // the S-front F (S_NN, S_AN from the input, V_k gathered from the parent)
-  // was loaded by complete_load_front in the top-down pass
+  // the S-front F was loaded by complete_load_front
   double* V = Vd + s->v_off[k];
   double* R = Rd + s->v_off[k];
   if (a > 0) {
@@ -705,36 +816,36 @@ namespace chd_launch {
 using chd::big::Ctx;
 void big_factor(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* X,
                 double* Lc, double* Wc, double* Dd, double* ws, double* ldet, int64_t* status) {
-  chd::big::factor_front(s, Ctx{st, xs, xcap}, k, X, Lc, Wc, Dd, ws, ldet, status);
+  chd::big::factor_front(s, chd::big::make_ctx(st, xs, xcap), k, X, Lc, Wc, Dd, ws, ldet, status);
 }
 void big_gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Wc,
                   double* Sc, double* g, double* Vd, double* ws) {
-  chd::big::gradient_front(s, Ctx{st, xs, xcap}, k, Wc, Sc, g, Vd, ws);
+  chd::big::gradient_front(s, chd::big::make_ctx(st, xs, xcap), k, Wc, Sc, g, Vd, ws);
 }
 void big_hess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
                  const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
-  chd::big::hess_up_front(s, Ctx{st, xs, xcap}, m, k, Wc, Vd, Y, ldy, T, ldt, ws);
+  chd::big::hess_up_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, Vd, Y, ldy, T, ldt, ws);
 }
 void big_hess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
                    double* T, int64_t ldt, double* ws) {
-  chd::big::hess_down_front(s, Ctx{st, xs, xcap}, m, k, Wc, T, ldt, ws);
+  chd::big::hess_down_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, T, ldt, ws);
 }
 void big_ihess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k,
                     const double* Wc, const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y,
                     int64_t ldy, double* ws) {
-  chd::big::ihess_down_front(s, Ctx{st, xs, xcap}, m, k, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+  chd::big::ihess_down_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
 }
 void big_ihess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
                   double* Y, int64_t ldy, double* ws) {
-  chd::big::ihess_up_front(s, Ctx{st, xs, xcap}, m, k, Wc, Y, ldy, ws);
+  chd::big::ihess_up_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, Y, ldy, ws);
 }
 void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Sin,
                   double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
                   int64_t* status) {
-  chd::big::complete_front(s, Ctx{st, xs, xcap}, k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+  chd::big::complete_front(s, chd::big::make_ctx(st, xs, xcap), k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
 }
 void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* ws) {
-  chd::big::complete_load_front(s, Ctx{st, nullptr, 0}, k, Sin, ws);
+  chd::big::complete_load_front(s, chd::big::make_ctx(st, nullptr, 0), k, Sin, ws);
 }
 // Inverse of the cached V_k = S_{A_k A_k} of one big front: R = chol(V),
 // R^{-1} in the front's workspace, V^{-1} = R^{-T} R^{-1} (lower) into Rd.
@@ -744,7 +855,7 @@ void big_inv_v(const chd_symbolic* s, cudaStream_t stream, double* xs, int64_t x
   using chd::DnTW;
   using chd::TriL;
   using chd::TriLT;
-  const Ctx st{stream, xs, xcap};
+  const Ctx st = chd::big::make_ctx(stream, xs, xcap);
   const int n = (int)(s->sn_ptr[k + 1] - s->sn_ptr[k]);
   const int a = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k]) - n;
   if (a == 0) return;

@@ -13,6 +13,7 @@
 
 namespace chd_launch {
 int64_t launches();
+void add_launches(int64_t d);
 void factor(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* X, double* Lc,
             double* Wc, double* Dd, double* ws, double* ldet, int64_t* status);
 void gradient(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Wc, double* Sc,
@@ -100,7 +101,16 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
       f->ex.nside = 0;  // run every big front on the caller's stream
     }
   }
+  if (cudaStreamCreateWithFlags(&f->gs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&f->g_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&f->g_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    f->graphs_on = false;  // run every sequence directly
+  }
   rc = cuda_ok(cudaMemsetAsync(f->status, 0, 4 * 8, stream));
+  // the scratch slices end with the counters of the Cholesky panel kernel
+  if (rc == CHD_OK && any_big)
+    rc = cuda_ok(cudaMemsetAsync(f->ex.xs, 0, (size_t)kSplitScratch * (nside + 1) * 8, stream));
   if (rc != CHD_OK) { cudaFree(block); delete f; return rc; }
   *out = f;
   return CHD_OK;
@@ -132,12 +142,93 @@ int64_t rhs_chunk(const chd_factor* f, int m) {
 
 chd_status launch_status() { return cuda_ok(cudaGetLastError()); }
 
+// ---------------------------------------------------------------------------
+// CUDA graphs.  The launch sequence of a call depends only on the symbolic
+// object and on the call's arguments (device pointers, m, strides), and a
+// large pattern issues thousands of launches per call.  A call whose
+// arguments equal those of the previous call of the same kind therefore
+// captures the sequence into a graph (stream capture on the object's private
+// stream gs, thread-local mode), and every later call with the same
+// arguments replays it: gs waits for the caller's stream, runs the graph,
+// and the caller's stream waits for gs (events; no host synchronisation).
+// The first call with new arguments runs the sequence directly on the
+// caller's stream, so one-off calls never pay for a capture.  The key holds
+// the workspace pointer too: a reallocated workspace invalidates the graph.
+// ---------------------------------------------------------------------------
+chd_status replay(chd_factor* f, GraphSlot& g) {
+  chd_status rc = cuda_ok(cudaEventRecord(f->g_in, f->stream));
+  if (rc == CHD_OK) rc = cuda_ok(cudaStreamWaitEvent(f->gs, f->g_in, 0));
+  if (rc == CHD_OK) rc = cuda_ok(cudaGraphLaunch(g.exec, f->gs));
+  if (rc == CHD_OK) rc = cuda_ok(cudaEventRecord(f->g_out, f->gs));
+  if (rc == CHD_OK) rc = cuda_ok(cudaStreamWaitEvent(f->stream, f->g_out, 0));
+  if (rc == CHD_OK) chd_launch::add_launches(g.launches);
+  return rc;
+}
+
+void drop_graph(GraphSlot& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  g.seen = false;
+}
+
+// Sequences longer than this are never captured: instantiating a graph of
+// tens of thousands of nodes costs seconds, more than replays save.
+constexpr int64_t kGraphMaxLaunches = 8192;
+
+template <class Body>
+chd_status run_sequence(chd_factor* f, GraphKind kind, GraphKey key, Body&& body) {
+  key.p[3] = f->ws;
+  GraphSlot& g = f->graphs[kind];
+  if (!f->graphs_on || !f->gs) {
+    body(f->stream);
+    return launch_status();
+  }
+  if (g.exec && g.key == key) return replay(f, g);
+  const bool same = g.seen && g.key == key;
+  if (!same) {
+    drop_graph(g);
+    g.key = key;
+    g.seen = true;
+    g.capture_failed = false;
+  }
+  if (!same || g.capture_failed || g.launches > kGraphMaxLaunches) {
+    const int64_t l0 = chd_launch::launches();
+    body(f->stream);
+    g.launches = chd_launch::launches() - l0;  // length of the direct run
+    return launch_status();
+  }
+  const int64_t l0 = chd_launch::launches();
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(f->gs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    body(f->gs);
+    e = cudaStreamEndCapture(f->gs, &graph);
+  }
+  const int64_t captured = chd_launch::launches() - l0;
+  chd_launch::add_launches(-captured);  // captured, not run
+  if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess || !g.exec) {
+    // no graph for this call: run the sequence directly (and do not try to
+    // capture it again for these arguments)
+    cudaGetLastError();
+    g.exec = nullptr;
+    g.capture_failed = true;
+    body(f->stream);
+    return launch_status();
+  }
+  g.launches = captured;
+  return replay(f, g);
+}
+
 chd_status ensure_projected_inverse(chd_factor* f) {
   if (f->have_S) return CHD_OK;
   chd_status rc = ensure_ws(f, 1);
   if (rc != CHD_OK) return rc;
-  chd_launch::gradient(f->sym, f->stream, &f->ex, f->Wc, f->Sc, nullptr, f->Vd, f->ws);
-  rc = launch_status();
+  GraphKey key;
+  rc = run_sequence(f, G_GRADIENT, key, [&](cudaStream_t st) {
+    chd_launch::gradient(f->sym, st, &f->ex, f->Wc, f->Sc, nullptr, f->Vd, f->ws);
+  });
   if (rc == CHD_OK) f->have_S = true;
   return rc;
 }
@@ -317,8 +408,11 @@ chd_status chd_refactor(chd_factor* f, const double* x, void* stream) {
   f->have_S = f->have_R = false;
   rc = cuda_ok(cudaMemsetAsync(f->status, 0, 4 * 8, f->stream));
   if (rc != CHD_OK) return rc;
-  chd_launch::factor(f->sym, f->stream, &f->ex, x, f->Lc, f->Wc, f->Dd, f->ws, f->ldet, f->status);
-  return launch_status();
+  GraphKey key;
+  key.p[0] = x;
+  return run_sequence(f, G_FACTOR, key, [&](cudaStream_t st) {
+    chd_launch::factor(f->sym, st, &f->ex, x, f->Lc, f->Wc, f->Dd, f->ws, f->ldet, f->status);
+  });
 }
 
 chd_status chd_logdet(chd_factor* f, double* out) {
@@ -358,8 +452,11 @@ chd_status chd_gradient(chd_factor* f, double* g, void* stream) {
   f->stream = static_cast<cudaStream_t>(stream);
   chd_status rc = ensure_ws(f, 1);
   if (rc != CHD_OK) return rc;
-  chd_launch::gradient(f->sym, f->stream, &f->ex, f->Wc, f->Sc, g, f->Vd, f->ws);
-  rc = launch_status();
+  GraphKey key;
+  key.p[0] = g;
+  rc = run_sequence(f, G_GRADIENT, key, [&](cudaStream_t st) {
+    chd_launch::gradient(f->sym, st, &f->ex, f->Wc, f->Sc, g, f->Vd, f->ws);
+  });
   if (rc == CHD_OK) f->have_S = true;
   return rc;
 }
@@ -378,8 +475,15 @@ chd_status chd_hessian(chd_factor* f, int m, const double* y, int64_t ldy, doubl
   if (rc != CHD_OK) return rc;
   for (int64_t i = 0; i < m; i += chunk) {
     const int mc = (int)std::min<int64_t>(chunk, m - i);
-    chd_launch::hessian(f->sym, f->stream, &f->ex, mc, f->Wc, f->Vd, y + i * ldy, ldy, t + i * ldt, ldt, f->ws);
-    rc = launch_status();
+    GraphKey key;
+    key.p[0] = y + i * ldy;
+    key.p[1] = t + i * ldt;
+    key.v[0] = mc;
+    key.v[1] = ldy;
+    key.v[2] = ldt;
+    rc = run_sequence(f, G_HESSIAN, key, [&](cudaStream_t st) {
+      chd_launch::hessian(f->sym, st, &f->ex, mc, f->Wc, f->Vd, y + i * ldy, ldy, t + i * ldt, ldt, f->ws);
+    });
     if (rc != CHD_OK) return rc;
   }
   return CHD_OK;
@@ -398,16 +502,24 @@ chd_status chd_inv_hessian(chd_factor* f, int m, const double* t, int64_t ldt, d
   rc = ensure_ws(f, chunk);
   if (rc != CHD_OK) return rc;
   if (!f->have_R) {  // V_k^{-1} of every front, once per factor
-    chd_launch::inv_v(f->sym, f->stream, &f->ex, f->Vd, f->Rd, f->ws, f->status);
-    rc = launch_status();
+    rc = run_sequence(f, G_INV_V, GraphKey{}, [&](cudaStream_t st) {
+      chd_launch::inv_v(f->sym, st, &f->ex, f->Vd, f->Rd, f->ws, f->status);
+    });
     if (rc != CHD_OK) return rc;
     f->have_R = true;
   }
   for (int64_t i = 0; i < m; i += chunk) {
     const int mc = (int)std::min<int64_t>(chunk, m - i);
-    chd_launch::inv_hessian(f->sym, f->stream, &f->ex, mc, f->Wc, f->Dd, f->Rd, t + i * ldt, ldt, y + i * ldy,
-                            ldy, f->ws);
-    rc = launch_status();
+    GraphKey key;
+    key.p[0] = t + i * ldt;
+    key.p[1] = y + i * ldy;
+    key.v[0] = mc;
+    key.v[1] = ldt;
+    key.v[2] = ldy;
+    rc = run_sequence(f, G_INV_HESSIAN, key, [&](cudaStream_t st) {
+      chd_launch::inv_hessian(f->sym, st, &f->ex, mc, f->Wc, f->Dd, f->Rd, t + i * ldt, ldt, y + i * ldy, ldy,
+                              f->ws);
+    });
     if (rc != CHD_OK) return rc;
   }
   return CHD_OK;
@@ -422,8 +534,11 @@ chd_status chd_recomplete(chd_factor* f, const double* sv, void* stream, double*
   if (rc == CHD_OK)
     rc = cuda_ok(cudaMemcpyAsync(f->Sc, sv, (size_t)s->colptr[s->n] * 8, cudaMemcpyDeviceToDevice, f->stream));
   if (rc == CHD_OK) {
-    chd_launch::complete(s, f->stream, &f->ex, sv, f->Lc, f->Wc, f->Dd, f->Vd, f->Rd, f->ws, f->ldet, f->status);
-    rc = launch_status();
+    GraphKey key;
+    key.p[0] = sv;
+    rc = run_sequence(f, G_COMPLETE, key, [&](cudaStream_t st) {
+      chd_launch::complete(s, st, &f->ex, sv, f->Lc, f->Wc, f->Dd, f->Vd, f->Rd, f->ws, f->ldet, f->status);
+    });
   }
   if (rc != CHD_OK) return rc;
   f->have_S = true;
@@ -485,6 +600,16 @@ chd_status chd_factor_set_workspace_limit(chd_factor* f, size_t bytes) {
   return CHD_OK;
 }
 
+chd_status chd_factor_set_graphs(chd_factor* f, int on) {
+  if (!f) return CHD_ERR_INVALID;
+  if (!on) {
+    if (f->gs) cudaStreamSynchronize(f->gs);
+    for (auto& g : f->graphs) drop_graph(g);
+  }
+  f->graphs_on = on && f->gs && f->g_in && f->g_out;
+  return CHD_OK;
+}
+
 chd_status chd_factor_release_workspace(chd_factor* f) {
   if (!f) return CHD_ERR_INVALID;
   if (f->ws) {
@@ -517,6 +642,13 @@ void chd_factor_free(chd_factor* f) {
     if (f->ex.join[j]) cudaEventDestroy(f->ex.join[j]);
   }
   if (f->ex.fork) cudaEventDestroy(f->ex.fork);
+  for (auto& g : f->graphs) drop_graph(g);
+  if (f->gs) {
+    cudaStreamSynchronize(f->gs);
+    cudaStreamDestroy(f->gs);
+  }
+  if (f->g_in) cudaEventDestroy(f->g_in);
+  if (f->g_out) cudaEventDestroy(f->g_out);
   if (f->ws) cudaFree(f->ws);
   if (f->inst_sum) cudaFree(f->inst_sum);
   if (f->block) cudaFree(f->block);
@@ -541,6 +673,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
     return pcs.size() - 1;
   };
   size_t iColptr = add(s->colptr.data(), s->colptr.size() * 8);
+  size_t iRowind = add(s->rowind.data(), s->rowind.size() * 4);
+  size_t iRows = add(s->rows.data(), s->rows.size() * 4);
   size_t iSn = add(s->sn_ptr.data(), s->sn_ptr.size() * 8);
   size_t iPar = add(s->sn_par.data(), s->sn_par.size() * 8);
   size_t iRp = add(s->rows_ptr.data(), s->rows_ptr.size() * 8);
@@ -554,6 +688,7 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   size_t iTf = add(s->task_fronts.data(), s->task_fronts.size() * 4);
   size_t iSf = add(s->small_fronts.data(), s->small_fronts.size() * 4);
   size_t iCf = add(s->cta_fronts.data(), s->cta_fronts.size() * 4);
+  size_t iWf = add(s->warp_fronts.data(), s->warp_fronts.size() * 4);
   size_t iIs = add(s->inst_sn.data(), s->inst_sn.size() * 8);
   std::vector<char> host(off, 0);
   for (auto& p : pcs)
@@ -590,6 +725,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   d.n = s->n;
   d.nsn = s->nsn;
   d.colptr = reinterpret_cast<const int64_t*>(b + pcs[iColptr].off);
+  d.rowind = reinterpret_cast<const int32_t*>(b + pcs[iRowind].off);
+  d.rows = reinterpret_cast<const int32_t*>(b + pcs[iRows].off);
   d.sn_ptr = reinterpret_cast<const int64_t*>(b + pcs[iSn].off);
   d.sn_par = reinterpret_cast<const int64_t*>(b + pcs[iPar].off);
   d.rows_ptr = reinterpret_cast<const int64_t*>(b + pcs[iRp].off);
@@ -605,6 +742,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   d.small_count = (int64_t)s->small_fronts.size();
   d.cta_fronts = reinterpret_cast<const int32_t*>(b + pcs[iCf].off);
   d.cta_count = (int64_t)s->cta_fronts.size();
+  d.warp_fronts = reinterpret_cast<const int32_t*>(b + pcs[iWf].off);
+  d.warp_count = (int64_t)s->warp_fronts.size();
   d.inst_sn = reinterpret_cast<const int64_t*>(b + pcs[iIs].off);
   d.ninst = (int64_t)s->inst_sn.size() - 1;
   d.f_total = s->f_off[s->nsn];

@@ -14,10 +14,12 @@ struct SymDev {
   int64_t n = 0;
   int64_t nsn = 0;             // number of supernodes (fronts)
   const int64_t* colptr = nullptr;   // n+1: CSC of V (analysed order)
+  const int32_t* rowind = nullptr;   // nnz: row indices of the CSC (sorted per column)
   const int64_t* sn_ptr = nullptr;   // nsn+1: N_k = [sn_ptr[k], sn_ptr[k+1])
   const int64_t* sn_par = nullptr;   // nsn: clique-tree parent or -1
   const int64_t* rows_ptr = nullptr; // nsn+1: offsets of J_k in `rows`/`rel`
   const int32_t* rel = nullptr;      // position of A_k[r] inside J_par(k) (A part only)
+  const int32_t* rows = nullptr;     // J_k (N_k then A_k, increasing), at rows_ptr[k]
   const int64_t* ch_ptr = nullptr;   // nsn+1: children of k in ch[ch_ptr[k]..)
   const int32_t* ch = nullptr;
   const int64_t* f_off = nullptr;    // nsn+1: per-front workspace offsets (doubles)
@@ -29,6 +31,8 @@ struct SymDev {
   int64_t small_count = 0;
   const int32_t* cta_fronts = nullptr;    // fronts of the CTA tier
   int64_t cta_count = 0;
+  const int32_t* warp_fronts = nullptr;   // fronts of the warp tier
+  int64_t warp_count = 0;
   const int64_t* inst_sn = nullptr;       // instances x supernode ranges
   int64_t ninst = 1;
   int64_t f_total = 0;               // workspace doubles per right-hand side
@@ -62,6 +66,8 @@ struct chd_symbolic {
   std::vector<int32_t> tier;  // per supernode: 0 warp, 1 CTA, 2 dense
   std::vector<int32_t> small_fronts;
   std::vector<int32_t> cta_fronts;
+  std::vector<int32_t> warp_fronts;
+  std::vector<int32_t> big_fronts;
   double flops[5] = {0, 0, 0, 0, 0};
   // independent instances analysed together (chd_analyze_batch): instance i
   // owns columns [inst_n[i], inst_n[i+1]), values [inst_nnz[i], inst_nnz[i+1])
@@ -88,6 +94,26 @@ struct Exec {
   int64_t xs_cap = 0;
 };
 
+// A captured launch sequence of one kind of call (see capi.cpp): the
+// arguments it was captured with, and the launch count of one replay.
+struct GraphKey {
+  const void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t v[4] = {0, 0, 0, 0};
+  bool operator==(const GraphKey& o) const {
+    for (int i = 0; i < 4; ++i)
+      if (p[i] != o.p[i] || v[i] != o.v[i]) return false;
+    return true;
+  }
+};
+struct GraphSlot {
+  GraphKey key;
+  bool seen = false;
+  bool capture_failed = false;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+};
+enum GraphKind { G_FACTOR = 0, G_GRADIENT, G_HESSIAN, G_INV_HESSIAN, G_INV_V, G_COMPLETE, G_KINDS };
+
 // A factor object: device-resident factor blocks, cached projected inverse
 // and the per-right-hand-side front workspace (all owned by the object).
 struct chd_factor {
@@ -110,6 +136,11 @@ struct chd_factor {
   size_t ws_limit = 0;       // caller's cap on the workspace (0: library default)
   bool have_S = false;
   bool have_R = false;
+  // CUDA graphs of the launch sequences, replayed on the private stream gs
+  bool graphs_on = true;
+  cudaStream_t gs = nullptr;
+  cudaEvent_t g_in = nullptr, g_out = nullptr;
+  GraphSlot graphs[G_KINDS];
 };
 
 // Host helpers implemented in symbolic.cpp

@@ -89,6 +89,21 @@ __host__ __device__ inline DnTW colshift(DnTW v, int c0) {
   return v;
 }
 
+// Position in the CSC value arrays of entry (i, j), i >= j, of V: binary
+// search of row i in column j (rows sorted).  Used where a front reads a
+// submatrix of an input directly (V_k = S_{A_k A_k} in Algorithm 7.3: every
+// such entry is in V because A_k is a clique of the chordal pattern).  The
+// search stays inside column j whatever the arguments.
+__device__ __forceinline__ int64_t csc_find(const SymDev& S, int32_t i, int32_t j) {
+  int64_t lo = S.colptr[j], hi = S.colptr[j + 1] - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(S.rowind + mid) < i) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // ---------------------------------------------------------------------------
 // status
 // ---------------------------------------------------------------------------

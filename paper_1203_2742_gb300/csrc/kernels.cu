@@ -581,11 +581,17 @@ __device__ void ihess_up_front(const SymDev& S, int k, const double* Wc, double*
 // Algorithm 7.3 for one front (each front needs only S and V_k = S_AA):
 // R = chol(V), Z = R^{-1} S_AN, P = S_NN - Z^T Z = D_NN^{-1},
 // L_AN = -R^{-T} Z, D_NN = P^{-1}, C = chol(D_NN), B = L_AN C.
-// S-front of front k: V_k gathered from the parent's S-front, S_NN and S_AN
-// from the input (the top-down part of Algorithm 7.3).
+// S-front of front k: S_NN and S_AN from the input's columns N_k, and
+// V_k = S_{A_k A_k}, a submatrix of the input, read from its later columns
+// (Eq. (e-sn-compl-2) re-extracts exactly these entries from the parent's
+// S-front; reading them from S makes the fronts independent).
 __device__ void complete_load_front(const SymDev& S, int k, const double* Sin, double* ws) {
   FrontInfo f = front_info(S, k, ws);
-  gather_from_parent(S, f, ws);
+  const int32_t* A = S.rows + S.rows_ptr[k] + f.n;
+  for (int e = threadIdx.x; e < f.a * f.a; e += NT) {
+    const int r = e % f.a, c = e / f.a;
+    if (r >= c) f.F[(f.n + r) + (int64_t)(f.n + c) * f.J] = Sin[csc_find(S, __ldg(A + r), __ldg(A + c))];
+  }
   csc_to_front(f.F, f.J, f.n, Sin + f.base);
   __syncthreads();
 }
@@ -696,14 +702,12 @@ __global__ void __launch_bounds__(NT) k_ihess_up(SymDev S, int task0, const doub
   for (int q = S.task_ptr[t]; q < S.task_ptr[t + 1]; ++q)
     ihess_up_front(S, S.task_fronts[q], Wc, Y + y * ldy, ws + y * S.f_total);
 }
-__global__ void __launch_bounds__(NT) k_complete_load(SymDev S, int task0, const double* Sin, double* ws) {
-  const int t = task0 + blockIdx.x;
-  for (int q = S.task_ptr[t + 1] - 1; q >= S.task_ptr[t]; --q) complete_load_front(S, S.task_fronts[q], Sin, ws);
-}
-// all CTA-tier fronts at once (their S-fronts are loaded)
+// all CTA-tier fronts at once, one CTA each
 __global__ void __launch_bounds__(NT) k_complete(SymDev S, const double* Sin, double* Lc, double* Wc, double* Dd,
                                                  double* Vd, double* Rd, double* ws, double* ldet, int64_t* st) {
-  complete_front(S, S.cta_fronts[blockIdx.x], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, st);
+  const int k = S.cta_fronts[blockIdx.x];
+  complete_load_front(S, k, Sin, ws);
+  complete_front(S, k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, st);
 }
 // Inverses of the cached V_k (inverse Hessian step 2), one CTA per front of
 // `front_list` (no dependencies between fronts; big fronts use the dense
@@ -794,6 +798,7 @@ using namespace chd;
 static int64_t g_launches = 0;
 int64_t launches() { return g_launches; }
 void count_launch() { ++g_launches; }
+void add_launches(int64_t d) { g_launches += d; }
 
 static inline void count() { ++g_launches; }
 
@@ -829,8 +834,8 @@ void warp_ihess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int
                      double* ws);
 void warp_ihess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* Y,
                    int64_t ldy, double* ws);
-void warp_complete(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Sin, double* Lc,
-                   double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
+void warp_complete_all(const chd_symbolic* s, cudaStream_t st, const double* Sin, double* Lc, double* Wc,
+                       double* Dd, double* Vd, double* Rd, double* ldet, int64_t* status);
 
 
 // Runs body(i, stream, scratch, cap) for the `count` independent big fronts
@@ -981,36 +986,24 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
     bf.join_now();
   }
 }
-// Completion: only the S-front loads (gather of V_k from the parent's front,
-// Eq. (e-sn-compl-2)) follow the top-down order; the arithmetic of Algorithm
-// 7.3 for one front needs nothing from other fronts, so after the top-down
-// pass all big fronts (side streams) and all CTA-tier fronts (one launch)
-// run at once.  Warp-tier fronts load and compute in the pass.
+// Completion: the arithmetic of Algorithm 7.3 for one front needs only the
+// input S (its columns N_k and the submatrix V_k = S_{A_k A_k}), so every
+// front is independent: the big fronts run on the side streams, all CTA-tier
+// fronts in one launch and all warp-tier fronts in one launch, concurrently.
 void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* ws);
 void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Sin, double* Lc, double* Wc,
               double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
-  const int nl = (int)s->lvl_ptr.size() - 1;
-  std::vector<int> bigs;
-  for (int l = nl - 1; l >= 0; --l) {
-    Level v = level(s, l);
-    for (int i = 0; i < v.nbig; ++i) {
-      big_complete_load(s, st, big_front(s, v, i), Sin, ws);
-      bigs.push_back(big_front(s, v, i));
-    }
-    if (v.ncta) {
-      k_complete_load<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Sin, ws);
-      count();
-    }
-    if (v.nwarp) warp_complete(s, st, v.t0, v.nwarp, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
-  }
+  const std::vector<int32_t>& bigs = s->big_fronts;
   BigFork bf{ex, st};
   bf.run((int)bigs.size(), [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
+    big_complete_load(s, bs, bigs[i], Sin, ws);
     big_complete(s, bs, xs, xc, bigs[i], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
   });
   if (s->dev.cta_count > 0) {
     k_complete<<<(int)s->dev.cta_count, NT, 0, st>>>(s->dev, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
     count();
   }
+  if (s->dev.warp_count > 0) warp_complete_all(s, st, Sin, Lc, Wc, Dd, Vd, Rd, ldet, status);
   bf.join_now();
 }
 void big_inv_v(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Vd,

@@ -517,9 +517,13 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     s->tier.assign(tier.begin(), tier.end());
     s->small_fronts.clear();
     s->cta_fronts.clear();
+    s->warp_fronts.clear();
+    s->big_fronts.clear();
     for (int64_t t = 0; t < nsn; ++t) {
       if (!s->is_big[t]) s->small_fronts.push_back((int32_t)t);
+      if (tier[t] == 0) s->warp_fronts.push_back((int32_t)t);
       if (tier[t] == 1) s->cta_fronts.push_back((int32_t)t);
+      if (tier[t] == 2) s->big_fronts.push_back((int32_t)t);
     }
     vector<double> W(nsn, 0.0);
     double total = 0;

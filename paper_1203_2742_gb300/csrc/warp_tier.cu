@@ -60,7 +60,7 @@ __device__ __forceinline__ Fr fr(const SymDev& S, int k, double* ws) {
   f.J = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]);
   f.a = f.J - f.n;
   f.base = S.colptr[f.col0];
-  f.G = ws + S.f_off[k];
+  f.G = ws ? ws + S.f_off[k] : nullptr;
   return f;
 }
 __device__ __forceinline__ int nnz_front(const Fr& f) { return f.n * f.J - f.n * (f.n - 1) / 2; }
@@ -522,18 +522,21 @@ __device__ void ihess_up_front(const SymDev& S, int k, const double* Wc, double*
   __syncwarp();
 }
 
+// S-front of the completion: S_NN and S_AN from the input's columns N_k,
+// V_k = S_{A_k A_k} from its later columns (a submatrix of S, Algorithm 7.3),
+// so the front depends on no other front.
 __device__ void complete_front(const SymDev& S, int k, const double* Sin, double* Lc, double* Wc, double* Dd,
-                               double* Vd, double* Rd, double* ws, double* ldet, int64_t* st, const Smem& m,
-                               int lane) {
-  Fr f = fr(S, k, ws);
+                               double* Vd, double* Rd, double* ldet, int64_t* st, const Smem& m, int lane) {
+  Fr f = fr(S, k, nullptr);
   const int J = f.J, n = f.n, a = f.a;
-  gather_parent(S, f, m, ws, lane);
+  const int32_t* A = S.rows + S.rows_ptr[k] + n;
+  for (int e = lane; e < a * a; e += 32) {
+    const int r = e % a, c = e / a;
+    if (r >= c) m.F[pk(J, n + r, n + c)] = Sin[csc_find(S, __ldg(A + r), __ldg(A + c))];
+  }
   const int nz = nnz_front(f);
   for (int e = lane; e < nz; e += 32) m.F[e] = Sin[f.base + e];
   __syncwarp();
-  // the children gather from the S-front in the workspace; after this copy
-  // the A x A block in shared memory is free to hold R = chol(V)
-  write_full(f, m, lane);
   double* V = Vd + S.v_off[k];
   double* R = Rd + S.v_off[k];
   for (int e = lane; e < a * a; e += 32) {
@@ -686,12 +689,16 @@ __global__ void __launch_bounds__(WPB * 32) kw_ihess_up(SymDev S, int task0, int
   for (int q = S.task_ptr[t]; q < S.task_ptr[t + 1]; ++q)
     ihess_up_front(S, S.task_fronts[q], Wc, Y + y * ldy, ws + y * S.f_total, m, lane);
 }
-__global__ void __launch_bounds__(WPB * 32) kw_complete(SymDev S, int task0, int task_end, const double* Sin,
-                                                        double* Lc, double* Wc, double* Dd, double* Vd,
-                                                        double* Rd, double* ws, double* ldet, int64_t* st) {
-  WARP_TASK_PROLOGUE
-  for (int q = S.task_ptr[t + 1] - 1; q >= S.task_ptr[t]; --q)
-    complete_front(S, S.task_fronts[q], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, st, m, lane);
+// all warp-tier fronts at once, one warp each (the completion has no
+// dependencies between fronts)
+__global__ void __launch_bounds__(WPB * 32) kw_complete(SymDev S, const double* Sin, double* Lc, double* Wc,
+                                                        double* Dd, double* Vd, double* Rd, double* ldet,
+                                                        int64_t* st) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * WPB + w;
+  if (i >= S.warp_count) return;
+  const Smem m = smem_for_warp(w);
+  complete_front(S, S.warp_fronts[i], Sin, Lc, Wc, Dd, Vd, Rd, ldet, st, m, lane);
 }
 
 }  // namespace warp
@@ -732,9 +739,9 @@ void warp_ihess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m
   kw_ihess_up<<<wgrid(nt, m), WPB * 32, 0, st>>>(s->dev, t0, t0 + nt, Wc, Y, ldy, ws);
   count_launch();
 }
-void warp_complete(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Sin, double* Lc,
-                   double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
-  kw_complete<<<wgrid(nt, 1), WPB * 32, 0, st>>>(s->dev, t0, t0 + nt, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+void warp_complete_all(const chd_symbolic* s, cudaStream_t st, const double* Sin, double* Lc, double* Wc,
+                       double* Dd, double* Vd, double* Rd, double* ldet, int64_t* status) {
+  kw_complete<<<wgrid((int)s->dev.warp_count, 1), WPB * 32, 0, st>>>(s->dev, Sin, Lc, Wc, Dd, Vd, Rd, ldet, status);
   count_launch();
 }
 }  // namespace chd_launch

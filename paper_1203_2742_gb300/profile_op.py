@@ -1,0 +1,110 @@
+"""Run the operations of the library once on a named synthetic workload, for
+a profiler.
+
+    python -m paper_1203_2742_gb300.profile_op WORKLOAD OP [--m M]
+
+WORKLOAD: band200 (band n=200, half-bandwidth 8), er5000 (Erdos-Renyi
+n=5000, p=0.001, minimum degree, relax 16), grid150 (5-point 150x150 grid,
+nested dissection), dense1500 (dense 1500x1500 pattern), grid3d40 (7-point
+40x40x40 grid, nested dissection).  OP: factor, gradient, hessian,
+inv_hessian, completion or all.  M: right-hand sides of the Hessian-type
+operations (default: 1, 8, 64, 8, 1 for the workloads above).
+
+Every operation runs twice as warm-up (the second round captures the CUDA
+graphs of the launch sequences); then the chosen ones run once more inside
+an NVTX range named "timed", so that a profiler can restrict its capture to
+them (``ncu --nvtx --nvtx-include "timed/"``).  --no-graphs launches every
+kernel directly.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+from . import binding as B  # noqa: E402
+
+DEFAULT_M = {"band200": 1, "er5000": 8, "grid150": 64, "dense1500": 8, "grid3d40": 1}
+
+
+def symbolic_for(name):
+    if name == "band200":
+        return B.Symbolic(*W.band(200, 8))
+    if name == "er5000":
+        return B.Symbolic(*W.erdos_renyi(5000, 0.001, np.random.default_rng(1)), ordering="mindeg", relax=16)
+    if name == "grid150":
+        return B.Symbolic(*W.grid2d(150, 150), perm=W.nested_dissection((150, 150), leaf=8))
+    if name == "dense1500":
+        return B.Symbolic(*W.band(1500, 1499))
+    if name == "grid3d40":
+        return B.Symbolic(*W.grid3d(40, 40, 40), perm=W.nested_dissection((40, 40, 40), leaf=8))
+    raise SystemExit(f"unknown workload {name}")
+
+
+def main(argv=None):
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload", choices=sorted(DEFAULT_M))
+    ap.add_argument("op", choices=("factor", "gradient", "hessian", "inv_hessian", "completion", "all"))
+    ap.add_argument("--m", type=int, default=None)
+    ap.add_argument("--no-graphs", action="store_true", help="launch every kernel directly (no CUDA graphs)")
+    a = ap.parse_args(argv)
+    m = a.m if a.m is not None else DEFAULT_M[a.workload]
+    sym = symbolic_for(a.workload)
+    n, cp, ri = sym.n, sym.colptr, sym.rowind
+    rng = np.random.default_rng(0)
+
+    def dev(v):
+        return torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device="cuda")
+
+    x = dev(W.diag_dominant(n, cp, ri, rng))
+    ys = dev(W.uniform_sym(n, cp, ri, rng, count=m))
+    s = dev(W.projected_gram(n, cp, ri, rng.standard_normal((n, 20)), 0.5))
+    fac = sym.factor(x)
+    g = torch.empty_like(x)
+    t = torch.empty_like(ys)
+    cfac, _ = sym.complete(s)
+    if a.no_graphs:
+        fac.set_graphs(False)
+        cfac.set_graphs(False)
+    ops = {
+        "factor": lambda: fac.refactor(x),
+        "gradient": lambda: fac.gradient(out=g),
+        "hessian": lambda: fac.hessian(ys, out=t),
+        "inv_hessian": lambda: fac.inv_hessian(ys, out=t),
+        "completion": lambda: cfac.recomplete(s, want_fstar=False),
+    }
+    import time
+    for rnd in range(2):  # the second round captures the CUDA graphs the timed round replays
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for f in ops.values():
+            f()
+        torch.cuda.synchronize()
+        print(f"  warm-up round {rnd + 1}: {1e3 * (time.perf_counter() - t0):.1f} ms (all operations)")
+    torch.cuda.nvtx.range_push("timed")
+    times = {}
+    for name in (ops if a.op == "all" else [a.op]):
+        l0 = B.chd_kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ops[name]()
+        e1.record()
+        torch.cuda.synchronize()
+        times[name] = (round(e0.elapsed_time(e1), 4), B.chd_kernel_launches() - l0)
+    torch.cuda.nvtx.range_pop()
+    print(f"{a.workload} {a.op} m={m}: n={n} nnz={sym.nnz} supernodes={sym.nsuper}")
+    for name, (ms, nl) in times.items():
+        print(f"  {name:12s} {ms:10.3f} ms  {nl:8d} launches")
+
+
+if __name__ == "__main__":
+    main()
