@@ -184,6 +184,13 @@ inline int64_t tile_count(int M, int N, int bm, int bn, bool lower) {
   return lower && bm == bn && tm == tn ? tm * (tm + 1) / 2 : tm * tn;
 }
 
+// Share of the busiest SM's time that does useful work when `units` equal
+// tiles are spread over the 152 SMs.
+inline double balance(int64_t units) {
+  const int64_t per = (units + 151) / 152;
+  return per > 0 ? (double)units / (double)(per * 152) : 0.0;
+}
+
 template <class MA, class MB, class MC>
 void gemm(const Ctx& st, int batch, int M, int N, int K, double alpha, MA A, int64_t sA, MB B, int64_t sB,
           double beta, MC C, int64_t sC, bool lower) {
@@ -193,12 +200,18 @@ void gemm(const Ctx& st, int batch, int M, int N, int K, double alpha, MA A, int
   else if (N <= 16 && M > 64) gemm_cfg<128, 16, 4, 2>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
   else if (M <= 8 && N > 64) gemm_cfg<8, 128, 1, 4>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
   else if (M <= 16 && N > 64) gemm_cfg<16, 128, 2, 4>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
-  else if (tile_count(M, N, 64, 64, lower) * batch >= kFill || K >= 512)
-    gemm_cfg<64, 64, 4, 4>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
-  else if (tile_count(M, N, 32, 32, lower) * batch >= kFill || M <= 32 || N <= 32)
-    gemm_cfg<32, 32, 2, 2>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
-  else
-    gemm_cfg<16, 16, 1, 1>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
+  else {
+    // 64 x 64 tiles unless 32 x 32 tiles balance the SMs clearly better (the
+    // FP64 pipe, not shared-memory traffic, bounds both tile shapes)
+    const int64_t t64 = tile_count(M, N, 64, 64, lower) * batch;
+    const int64_t t32 = tile_count(M, N, 32, 32, lower) * batch;
+    if (t64 >= kFill && balance(t64) >= 0.9 * balance(t32))
+      gemm_cfg<64, 64, 4, 4>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
+    else if (t32 >= kFill || M <= 32 || N <= 32 || K >= 512)
+      gemm_cfg<32, 32, 2, 2>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
+    else
+      gemm_cfg<16, 16, 1, 1>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -733,10 +746,14 @@ void ihess_down_front(const chd_symbolic* s, const Ctx& st, int m, int k, const 
   const double* D = Dd + s->d_off[k];
   gemm(st, m, n, n, n, 1.0, Dn{T1, J}, sw, SymL{D, n}, 0, 0.0, Dn{T2, J}, sw, false);
   gemm(st, m, n, n, n, 1.0, SymL{D, n}, 0, Dn{T2, J}, sw, 0.0, Csc{Yout + f.base, J, 0}, ldy, true);
-  if (a > 0) {  // K_AN = V^{-1} (M_AN D), V^{-1} cached per factor
+  if (a > 0) {
+    // K_AN = V^{-1} (M_AN D) = R^{-T} R^{-1} (M_AN D) with R = chol(V) cached
+    // per factor: two blocked triangular solves on the transposed block
+    const double* R = Rd + s->v_off[k];
     gemm(st, m, a, n, n, 1.0, Dn{T1 + n, J}, sw, SymL{D, n}, 0, 0.0, Dn{T2 + n, J}, sw, false);
-    gemm(st, m, a, n, a, 1.0, SymL{Rd + s->v_off[k], a}, 0, Dn{T2 + n, J}, sw, 0.0, Csc{Yout + f.base, J, n}, ldy,
-         false);
+    trsm_rLT(st, m, n, a, DnTW{T2 + n, J}, sw, R, a);
+    trsm_rL(st, m, n, a, DnTW{T2 + n, J}, sw, R, a);
+    CHD_EW(mk_front_to_csc, (int64_t)J * n, m, st, Yout + f.base, ldy, T2, sw, J, J, n, n, J, 1.0);
   }
 }
 
@@ -847,8 +864,8 @@ void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xc
 void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* ws) {
   chd::big::complete_load_front(s, chd::big::make_ctx(st, nullptr, 0), k, Sin, ws);
 }
-// Inverse of the cached V_k = S_{A_k A_k} of one big front: R = chol(V),
-// R^{-1} in the front's workspace, V^{-1} = R^{-T} R^{-1} (lower) into Rd.
+// Cholesky factor R of the cached V_k = S_{A_k A_k} of one big front (lower,
+// into Rd); the inverse-Hessian steps apply V^{-1} by triangular solves.
 void big_inv_v(const chd_symbolic* s, cudaStream_t stream, double* xs, int64_t xcap, int k, const double* Vd,
                double* Rd, double* ws, int64_t* status) {
   using namespace chd::big;
@@ -860,11 +877,7 @@ void big_inv_v(const chd_symbolic* s, cudaStream_t stream, double* xs, int64_t x
   const int a = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k]) - n;
   if (a == 0) return;
   double* R = Rd + s->v_off[k];
-  double* Ri = ws + s->f_off[k];
   CHD_EW(mk_copy, (int64_t)a * a, 1, st, R, 0, a, Vd + s->v_off[k], 0, a, a, a, 1.0, 0.0, 1, 0);
   potrf_partial(st, R, a, a, a, status, CHD_ERR_NOT_PD, k, -1);
-  CHD_EW(mk_identity, (int64_t)a * a, 1, st, Ri, a, a);
-  trsm_rLT(st, 1, a, a, DnTW{Ri, a}, 0, R, a);
-  gemm(st, 1, a, a, a, 1.0, TriLT{Ri, a}, 0, TriL{Ri, a}, 0, 0.0, chd::Dn{R, a}, 0, true);
 }
 }  // namespace chd_launch

@@ -42,8 +42,11 @@ constexpr size_t kWorkspaceCap = size_t(48) << 30;
 
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Split-K partial products of the dense tier: 2 Mi doubles (16 MiB) per stream.
+// Scratch of the dense tier per stream: 2 Mi doubles (16 MiB) for the first
+// kWideSlices streams, 64 Ki doubles for the others.
 constexpr int64_t kSplitScratch = int64_t(2) << 20;
+constexpr int64_t kSmallScratch = int64_t(64) << 10;
+inline int64_t slice_doubles(int j) { return j < kWideSlices ? kSplitScratch : kSmallScratch; }
 
 chd_status cuda_ok(cudaError_t e) {
   if (e == cudaSuccess) return CHD_OK;
@@ -72,7 +75,11 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
   for (char b : s->is_big) any_big = any_big || b;
   const int nside = any_big ? kSideStreams : 0;
   const size_t oxs = off;
-  if (any_big) off = align_up(off + (size_t)kSplitScratch * (nside + 1) * 8);
+  size_t xs_doubles = 0;
+  if (any_big) {
+    for (int j = 0; j <= nside; ++j) xs_doubles += (size_t)slice_doubles(j);
+    off = align_up(off + xs_doubles * 8);
+  }
   void* block = nullptr;
   chd_status rc = cuda_ok(cudaMalloc(&block, off));
   if (rc != CHD_OK) { delete f; return rc; }
@@ -88,8 +95,12 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
   f->scalar = reinterpret_cast<double*>(b + osc);
   f->status = reinterpret_cast<int64_t*>(b + ost);
   if (any_big) {
-    f->ex.xs = reinterpret_cast<double*>(b + oxs);
-    f->ex.xs_cap = kSplitScratch;
+    double* x = reinterpret_cast<double*>(b + oxs);
+    for (int j = 0; j <= nside; ++j) {
+      f->ex.slice[j] = x;
+      f->ex.slice_cap[j] = slice_doubles(j);
+      x += slice_doubles(j);
+    }
     bool ok = cudaEventCreateWithFlags(&f->ex.fork, cudaEventDisableTiming) == cudaSuccess;
     for (int j = 0; ok && j < nside; ++j) {
       ok = cudaStreamCreateWithFlags(&f->ex.side[j], cudaStreamNonBlocking) == cudaSuccess &&
@@ -110,7 +121,7 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
   rc = cuda_ok(cudaMemsetAsync(f->status, 0, 4 * 8, stream));
   // the scratch slices end with the counters of the Cholesky panel kernel
   if (rc == CHD_OK && any_big)
-    rc = cuda_ok(cudaMemsetAsync(f->ex.xs, 0, (size_t)kSplitScratch * (nside + 1) * 8, stream));
+    rc = cuda_ok(cudaMemsetAsync(f->ex.slice[0], 0, xs_doubles * 8, stream));
   if (rc != CHD_OK) { cudaFree(block); delete f; return rc; }
   *out = f;
   return CHD_OK;
@@ -686,6 +697,7 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   size_t iV = add(s->v_off.data(), s->v_off.size() * 8);
   size_t iTp = add(s->task_ptr.data(), s->task_ptr.size() * 4);
   size_t iTf = add(s->task_fronts.data(), s->task_fronts.size() * 4);
+  size_t iTm = add(s->tmeta.data(), s->tmeta.size() * sizeof(WMeta));
   size_t iSf = add(s->small_fronts.data(), s->small_fronts.size() * 4);
   size_t iCf = add(s->cta_fronts.data(), s->cta_fronts.size() * 4);
   size_t iWf = add(s->warp_fronts.data(), s->warp_fronts.size() * 4);
@@ -738,6 +750,7 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   d.v_off = reinterpret_cast<const int64_t*>(b + pcs[iV].off);
   d.task_ptr = reinterpret_cast<const int32_t*>(b + pcs[iTp].off);
   d.task_fronts = reinterpret_cast<const int32_t*>(b + pcs[iTf].off);
+  d.tmeta = reinterpret_cast<const WMeta*>(b + pcs[iTm].off);
   d.small_fronts = reinterpret_cast<const int32_t*>(b + pcs[iSf].off);
   d.small_count = (int64_t)s->small_fronts.size();
   d.cta_fronts = reinterpret_cast<const int32_t*>(b + pcs[iCf].off);

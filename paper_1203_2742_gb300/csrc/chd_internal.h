@@ -9,6 +9,24 @@
 
 #include "../../include/chordal_barrier.h"
 
+// One record per position of the task lists (aligned with task_fronts):
+// what a warp needs to start a front with one load.  flags:
+//   WM_PREV_CHILD      the previous front of the task is a child of this one
+//   WM_NEXT_PARENT     the next front of the task is this one's parent
+//   WM_ONLY_CHILD_PREV this front's only child is the previous front of the task
+constexpr int32_t WM_PREV_CHILD = 1, WM_NEXT_PARENT = 2, WM_ONLY_CHILD_PREV = 4;
+struct alignas(16) WMeta {
+  int64_t col0;      // first column of N_k
+  int64_t base;      // colptr[col0]: offset of the front's values
+  int64_t f_off;     // workspace offset (one right-hand side)
+  int64_t rows_off;  // rows_ptr[k]
+  int64_t d_off;     // offset of the n x n block
+  int64_t v_off;     // offset of the a x a block
+  int32_t k, n, J, flags;
+  int32_t ch_beg, ch_end;  // children of k in ch[ch_beg..ch_end)
+  int32_t pad[2];
+};
+
 // Device copy of the symbolic data, passed by value to every kernel.
 struct SymDev {
   int64_t n = 0;
@@ -27,9 +45,10 @@ struct SymDev {
   const int64_t* v_off = nullptr;    // nsn+1: per-front a_k*a_k block offsets
   const int32_t* task_ptr = nullptr; // ntask+1
   const int32_t* task_fronts = nullptr;
+  const WMeta* tmeta = nullptr;      // aligned with task_fronts
   const int32_t* small_fronts = nullptr;  // fronts not in the dense tier
   int64_t small_count = 0;
-  const int32_t* cta_fronts = nullptr;    // fronts of the CTA tier
+  const int32_t* cta_fronts = nullptr;    // fronts of the CTA and wide warp tiers (completion)
   int64_t cta_count = 0;
   const int32_t* warp_fronts = nullptr;   // fronts of the warp tier
   int64_t warp_count = 0;
@@ -57,13 +76,15 @@ struct chd_symbolic {
   // schedule: tasks are front sequences processed by one CTA; launches
   // group tasks by level (bottom-up order); lvl_ptr indexes tasks.
   std::vector<int32_t> task_ptr, task_fronts, lvl_ptr;
+  std::vector<WMeta> tmeta;  // aligned with task_fronts
   // per level: the last lvl_big[l] tasks of the level are single big fronts
   // run by the multi-CTA dense tier
   std::vector<int32_t> lvl_big;
-  // per level: the first lvl_warp[l] tasks are warp-tier tasks
-  std::vector<int32_t> lvl_warp;
+  // per level: the first lvl_warp[l] tasks are warp-tier tasks (|J| <= 32),
+  // the next lvl_w64[l] wide warp-tier tasks (|J| <= 64)
+  std::vector<int32_t> lvl_warp, lvl_w64;
   std::vector<char> is_big;  // per supernode
-  std::vector<int32_t> tier;  // per supernode: 0 warp, 1 CTA, 2 dense
+  std::vector<int32_t> tier;  // per supernode: 0 warp, 3 wide warp, 1 CTA, 2 dense
   std::vector<int32_t> small_fronts;
   std::vector<int32_t> cta_fronts;
   std::vector<int32_t> warp_fronts;
@@ -80,18 +101,21 @@ struct chd_symbolic {
   int dev_id = -1;
 };
 
-// Execution resources of the dense tier: side streams on which the big
-// fronts of one level run concurrently (forked from and joined back to the
-// caller's stream with events), and split-K scratch, one slice of xs_cap
-// doubles per stream (slice 0: the caller's stream).
-constexpr int kSideStreams = 8;
+// Execution resources of the dense tier: side streams on which independent
+// big fronts run concurrently (forked from and joined back to the caller's
+// stream with events), and one scratch slice per stream (slice 0: the
+// caller's stream) for split-K partial products, ending with the counter of
+// the Cholesky panel kernel.  The first kWideSlices slices are large; the
+// rest hold the counter and small partial products only.
+constexpr int kSideStreams = 32;
+constexpr int kWideSlices = 9;
 struct Exec {
   int nside = 0;
   cudaStream_t side[kSideStreams] = {};
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kSideStreams] = {};
-  double* xs = nullptr;
-  int64_t xs_cap = 0;
+  double* slice[kSideStreams + 1] = {};
+  int64_t slice_cap[kSideStreams + 1] = {};
 };
 
 // A captured launch sequence of one kind of call (see capi.cpp): the
@@ -125,7 +149,7 @@ struct chd_factor {
   double* Sc = nullptr;
   double* Dd = nullptr;
   double* Vd = nullptr;
-  double* Rd = nullptr;      // V_k^{-1} per front (lower), once have_R
+  double* Rd = nullptr;      // per front, once have_R: V_k^{-1} (lower), or chol(V_k) for dense-tier fronts
   double* ldet = nullptr;
   double* scalar = nullptr;  // [0] log det
   int64_t* status = nullptr; // [0] code, [1] supernode, [2] column

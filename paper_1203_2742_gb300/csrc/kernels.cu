@@ -17,7 +17,8 @@
 //   Wc  (CSC)  : [D_NN^{-1}; L_AN]
 //   Dd  (n x n): D_NN
 //   Vd  (a x a): V_k = S_{A_k A_k}  (Algorithm 7.2)
-//   Rd  (a x a): V_k^{-1} (lower triangle; inverse Hessian, §5.3)
+//   Rd  (a x a): V_k^{-1} (lower triangle; inverse Hessian, §5.3) for the
+//                warp and CTA tiers, R = chol(V_k) for dense-tier fronts
 //   Sc  (CSC)  : S = P(X^{-1})
 #include <cuda_runtime.h>
 
@@ -820,7 +821,8 @@ void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xc
                   double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
                   int64_t* status);
 
-// warp-tier launches (warp_tier.cu)
+// warp-tier launches (warp_tier.cu): w32 for |J| <= 32, w64 for |J| <= 64
+namespace w32 {
 void warp_factor(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* X, double* Lc, double* Wc,
                  double* Dd, double* ws, double* ldet, int64_t* status);
 void warp_gradient(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Wc, double* Sc,
@@ -836,6 +838,22 @@ void warp_ihess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m
                    int64_t ldy, double* ws);
 void warp_complete_all(const chd_symbolic* s, cudaStream_t st, const double* Sin, double* Lc, double* Wc,
                        double* Dd, double* Vd, double* Rd, double* ldet, int64_t* status);
+}  // namespace w32
+namespace w64 {
+void warp_factor(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* X, double* Lc, double* Wc,
+                 double* Dd, double* ws, double* ldet, int64_t* status);
+void warp_gradient(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Wc, double* Sc,
+                   double* g, double* Vd, double* ws);
+void warp_hess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
+                  const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
+void warp_hess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* T,
+                    int64_t ldt, double* ws);
+void warp_ihess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
+                     const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy,
+                     double* ws);
+void warp_ihess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* Y,
+                   int64_t ldy, double* ws);
+}  // namespace w64
 
 
 // Runs body(i, stream, scratch, cap) for the `count` independent big fronts
@@ -850,10 +868,10 @@ struct BigFork {
   template <class Body>
   void run(int count, Body&& body) {
     if (count <= 0) return;
-    double* xs0 = ex ? ex->xs : nullptr;
-    const int64_t cap = ex ? ex->xs_cap : 0;
+    double* xs0 = ex ? ex->slice[0] : nullptr;
+    const int64_t cap0 = ex ? ex->slice_cap[0] : 0;
     if (!ex || ex->nside == 0 || count == 1) {
-      for (int i = 0; i < count; ++i) body(i, st, xs0, cap);
+      for (int i = 0; i < count; ++i) body(i, st, xs0, cap0);
       return;
     }
     used = std::min(count, ex->nside);
@@ -861,7 +879,7 @@ struct BigFork {
     for (int j = 0; j < used; ++j) cudaStreamWaitEvent(ex->side[j], ex->fork, 0);
     for (int i = 0; i < count; ++i) {
       const int j = i % used;
-      body(i, ex->side[j], ex->xs ? ex->xs + (int64_t)(1 + j) * cap : nullptr, cap);
+      body(i, ex->side[j], ex->slice[1 + j], ex->slice_cap[1 + j]);
     }
   }
   void join_now() {
@@ -873,19 +891,22 @@ struct BigFork {
   }
 };
 
-// Level l holds tasks [t0, t0 + nwarp) of the warp tier, then [tc, tc + ncta)
-// of the CTA tier, then nbig single big fronts of the dense tier.
+// Level l holds tasks [t0, t0 + nwarp) of the warp tier (|J| <= 32), then
+// [tw, tw + nw64) of the wide warp tier (|J| <= 64), then [tc, tc + ncta) of
+// the CTA tier, then nbig single big fronts of the dense tier.
 struct Level {
-  int t0, nwarp, tc, ncta, nbig;
+  int t0, nwarp, tw, nw64, tc, ncta, nbig;
 };
 static inline Level level(const chd_symbolic* s, int l) {
   Level v;
   v.t0 = s->lvl_ptr[l];
   const int nt = s->lvl_ptr[l + 1] - v.t0;
   v.nwarp = s->lvl_warp[l];
+  v.nw64 = s->lvl_w64[l];
   v.nbig = s->lvl_big[l];
-  v.tc = v.t0 + v.nwarp;
-  v.ncta = nt - v.nwarp - v.nbig;
+  v.tw = v.t0 + v.nwarp;
+  v.tc = v.tw + v.nw64;
+  v.ncta = nt - v.nwarp - v.nw64 - v.nbig;
   return v;
 }
 static inline int big_front(const chd_symbolic* s, const Level& v, int i) {
@@ -901,7 +922,8 @@ void factor(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double
     bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
       big_factor(s, bs, xs, xc, big_front(s, v, i), X, Lc, Wc, Dd, ws, ldet, status);
     });
-    if (v.nwarp) warp_factor(s, st, v.t0, v.nwarp, X, Lc, Wc, Dd, ws, ldet, status);
+    if (v.nwarp) w32::warp_factor(s, st, v.t0, v.nwarp, X, Lc, Wc, Dd, ws, ldet, status);
+    if (v.nw64) w64::warp_factor(s, st, v.tw, v.nw64, X, Lc, Wc, Dd, ws, ldet, status);
     if (v.ncta) {
       k_factor<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, X, Lc, Wc, Dd, ws, ldet, status);
       count();
@@ -922,7 +944,8 @@ void gradient(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
       k_gradient<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Wc, Sc, g, Vd, ws);
       count();
     }
-    if (v.nwarp) warp_gradient(s, st, v.t0, v.nwarp, Wc, Sc, g, Vd, ws);
+    if (v.nwarp) w32::warp_gradient(s, st, v.t0, v.nwarp, Wc, Sc, g, Vd, ws);
+    if (v.nw64) w64::warp_gradient(s, st, v.tw, v.nw64, Wc, Sc, g, Vd, ws);
     bf.join_now();
   }
 }
@@ -935,7 +958,8 @@ void hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, cons
     bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
       big_hess_up(s, bs, xs, xc, m, big_front(s, v, i), Wc, Vd, Y, ldy, T, ldt, ws);
     });
-    if (v.nwarp) warp_hess_up(s, st, v.t0, v.nwarp, m, Wc, Vd, Y, ldy, T, ldt, ws);
+    if (v.nwarp) w32::warp_hess_up(s, st, v.t0, v.nwarp, m, Wc, Vd, Y, ldy, T, ldt, ws);
+    if (v.nw64) w64::warp_hess_up(s, st, v.tw, v.nw64, m, Wc, Vd, Y, ldy, T, ldt, ws);
     if (v.ncta) {
       k_hess_up<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Vd, Y, ldy, T, ldt, ws);
       count();
@@ -952,7 +976,8 @@ void hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, cons
       k_hess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, T, ldt, ws);
       count();
     }
-    if (v.nwarp) warp_hess_down(s, st, v.t0, v.nwarp, m, Wc, T, ldt, ws);
+    if (v.nwarp) w32::warp_hess_down(s, st, v.t0, v.nwarp, m, Wc, T, ldt, ws);
+    if (v.nw64) w64::warp_hess_down(s, st, v.tw, v.nw64, m, Wc, T, ldt, ws);
     bf.join_now();
   }
 }
@@ -969,7 +994,8 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
       k_ihess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
       count();
     }
-    if (v.nwarp) warp_ihess_down(s, st, v.t0, v.nwarp, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    if (v.nwarp) w32::warp_ihess_down(s, st, v.t0, v.nwarp, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    if (v.nw64) w64::warp_ihess_down(s, st, v.tw, v.nw64, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
     bf.join_now();
   }
   for (int l = 0; l < nl; ++l) {
@@ -978,7 +1004,8 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
     bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
       big_ihess_up(s, bs, xs, xc, m, big_front(s, v, i), Wc, Y, ldy, ws);
     });
-    if (v.nwarp) warp_ihess_up(s, st, v.t0, v.nwarp, m, Wc, Y, ldy, ws);
+    if (v.nwarp) w32::warp_ihess_up(s, st, v.t0, v.nwarp, m, Wc, Y, ldy, ws);
+    if (v.nw64) w64::warp_ihess_up(s, st, v.tw, v.nw64, m, Wc, Y, ldy, ws);
     if (v.ncta) {
       k_ihess_up<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Y, ldy, ws);
       count();
@@ -1003,7 +1030,7 @@ void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
     k_complete<<<(int)s->dev.cta_count, NT, 0, st>>>(s->dev, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
     count();
   }
-  if (s->dev.warp_count > 0) warp_complete_all(s, st, Sin, Lc, Wc, Dd, Vd, Rd, ldet, status);
+  if (s->dev.warp_count > 0) w32::warp_complete_all(s, st, Sin, Lc, Wc, Dd, Vd, Rd, ldet, status);
   bf.join_now();
 }
 void big_inv_v(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Vd,

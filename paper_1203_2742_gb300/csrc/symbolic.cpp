@@ -494,9 +494,10 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
   }
 
   // ---- schedule -------------------------------------------------------------
-  // Each front gets a tier: warp (|J| <= 32 and |N| <= 8, one warp per front),
-  // CTA (one 256-thread CTA per front) or dense (|J| >= big_rows or
-  // |N| >= big_cols, multi-CTA sequence).  Maximal subtrees of warp-tier
+  // Each front gets a tier: warp (|N| <= 8 and |J| <= 32, one warp per front),
+  // wide warp (|N| <= 8 and |J| <= 64, one warp per front), CTA (one
+  // 256-thread CTA per front) or dense (|J| >= big_rows or |N| >= big_cols,
+  // multi-CTA sequence).  Maximal subtrees of warp-tier
   // fronts whose total work is at most total/(8*152) become single-warp
   // tasks processed in postorder (tree parallelism, §8); the fronts above
   // form chains (a front joins its only such child when both have the same
@@ -512,7 +513,23 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
       int64_t nn = s->sn_ptr[t + 1] - s->sn_ptr[t];
       int64_t J = s->rows_ptr[t + 1] - s->rows_ptr[t];
       s->is_big[t] = (J >= big_rows || nn >= big_cols) ? 1 : 0;
-      tier[t] = s->is_big[t] ? 2 : ((J <= 32 && nn <= 8) ? 0 : 1);
+      tier[t] = s->is_big[t] ? 2 : (nn <= 8 && J <= 32) ? 0 : (nn <= 8 && J <= 64) ? 3 : 1;
+    }
+    // The wide warp tier runs one warp per CTA (its fronts take most of the
+    // shared memory), which pays off for chains, where one front waits for
+    // the previous one, not for many independent fronts: a front keeps it
+    // only when it is linked to another such front as only child or parent.
+    {
+      vector<int64_t> nkids(nsn, 0);
+      for (int64_t t = 0; t < nsn; ++t)
+        if (s->sn_par[t] >= 0) nkids[s->sn_par[t]]++;
+      vector<char> chained(nsn, 0);
+      for (int64_t t = 0; t < nsn; ++t) {
+        const int64_t p = s->sn_par[t];
+        if (p >= 0 && tier[t] == 3 && tier[p] == 3 && nkids[p] == 1) chained[t] = chained[p] = 1;
+      }
+      for (int64_t t = 0; t < nsn; ++t)
+        if (tier[t] == 3 && !chained[t]) tier[t] = 1;
     }
     s->tier.assign(tier.begin(), tier.end());
     s->small_fronts.clear();
@@ -522,7 +539,7 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     for (int64_t t = 0; t < nsn; ++t) {
       if (!s->is_big[t]) s->small_fronts.push_back((int32_t)t);
       if (tier[t] == 0) s->warp_fronts.push_back((int32_t)t);
-      if (tier[t] == 1) s->cta_fronts.push_back((int32_t)t);
+      if (tier[t] == 1 || tier[t] == 3) s->cta_fronts.push_back((int32_t)t);
       if (tier[t] == 2) s->big_fronts.push_back((int32_t)t);
     }
     vector<double> W(nsn, 0.0);
@@ -593,10 +610,11 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     s->task_fronts.clear();
     s->lvl_ptr.assign(1, 0);
     s->lvl_warp.clear();
+    s->lvl_w64.clear();
     s->lvl_big.clear();
     for (int64_t l = 0; l < nlev; ++l) {
-      int32_t cnt[3] = {0, 0, 0};
-      for (int tr = 0; tr < 3; ++tr) {  // warp tasks, then CTA tasks, then dense fronts
+      int32_t cnt[4] = {0, 0, 0, 0};
+      for (int tr : {0, 3, 1, 2}) {  // warp, wide warp, CTA tasks, then dense fronts
         for (int64_t q : bylev[l]) {
           if (ttier[q] != tr) continue;
           for (int32_t f : tasks[q]) s->task_fronts.push_back(f);
@@ -606,7 +624,34 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
       }
       s->lvl_ptr.push_back((int32_t)(s->task_ptr.size() - 1));
       s->lvl_warp.push_back(cnt[0]);
+      s->lvl_w64.push_back(cnt[3]);
       s->lvl_big.push_back(cnt[2]);
+    }
+    // per-position records of the task lists
+    s->tmeta.assign(s->task_fronts.size(), WMeta{});
+    for (size_t t = 0; t + 1 < s->task_ptr.size(); ++t) {
+      const int32_t q0 = s->task_ptr[t], q1 = s->task_ptr[t + 1];
+      for (int32_t q = q0; q < q1; ++q) {
+        const int64_t k = s->task_fronts[q];
+        WMeta& w = s->tmeta[q];
+        w.col0 = s->sn_ptr[k];
+        w.base = s->colptr[w.col0];
+        w.f_off = s->f_off[k];
+        w.rows_off = s->rows_ptr[k];
+        w.d_off = s->d_off[k];
+        w.v_off = s->v_off[k];
+        w.k = (int32_t)k;
+        w.n = (int32_t)(s->sn_ptr[k + 1] - s->sn_ptr[k]);
+        w.J = (int32_t)(s->rows_ptr[k + 1] - s->rows_ptr[k]);
+        w.ch_beg = (int32_t)s->ch_ptr[k];
+        w.ch_end = (int32_t)s->ch_ptr[k + 1];
+        w.flags = 0;
+        if (q > q0 && s->sn_par[s->task_fronts[q - 1]] == k) {
+          w.flags |= WM_PREV_CHILD;
+          if (w.ch_end - w.ch_beg == 1) w.flags |= WM_ONLY_CHILD_PREV;
+        }
+        if (q + 1 < q1 && s->sn_par[k] == s->task_fronts[q + 1]) w.flags |= WM_NEXT_PARENT;
+      }
     }
   }
   return CHD_OK;

@@ -75,6 +75,12 @@ def small_cases():
         # wide supernodes split into chains (dense, CTA and warp pieces)
         "split_dense": lambda: Case(W.band(150, 149), seed=13, big=(64, 64), split=24),
         "split_arrow": lambda: Case(W.arrow(200, 90), seed=14, split=8),
+        # wide warp tier (|N| <= 8, 32 < |J| <= 64, chains only): two chains
+        # handing over to the CTA tier at the root, and thin leaves of one parent
+        # (CTA tier)
+        "band300_w40": lambda: Case(W.band(300, 40), seed=15),
+        "arrow150_w48": lambda: Case(W.arrow(150, 48), seed=16),
+        "band120_w63": lambda: Case(W.band(120, 63), seed=17),
     }
 
 
