@@ -338,12 +338,14 @@ def run_ours(args, wl, rank, world, local_rank):
     sampler.start()
     launches0 = B.chd_kernel_launches()
     wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler capture the timed steps only
     for i in range(args.steps):
         flush.zero_()
         evs[i][0].record(stream)
         step()
         evs[i][1].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     wall = time.perf_counter() - wall0
     launches = B.chd_kernel_launches() - launches0
     clocks = sampler.stop()

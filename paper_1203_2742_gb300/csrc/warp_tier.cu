@@ -25,21 +25,25 @@ namespace chd_launch {
 void count_launch();
 }
 
-// fronts with |J| <= 32: three warps per CTA
+// fronts with |J| <= 32: one warp per front, three per CTA
 #define WT_NS w32
 #define WT_J 32
 #define WT_WPB 3
+#define WT_TPF 32
 #include "warp_tier_body.cuh"
 #undef WT_NS
 #undef WT_J
 #undef WT_WPB
+#undef WT_TPF
 
-// fronts with 32 < |J| <= 64 (bands of half-bandwidth up to 63, thin fronts
-// with a wide separator): one warp per CTA
+// chains of fronts with 32 < |J| <= 64 (bands of half-bandwidth up to 63):
+// four warps (one CTA) per front, which shortens the serial chain
 #define WT_NS w64
 #define WT_J 64
 #define WT_WPB 1
+#define WT_TPF 128
 #include "warp_tier_body.cuh"
 #undef WT_NS
 #undef WT_J
 #undef WT_WPB
+#undef WT_TPF

@@ -1,5 +1,6 @@
 // Warp tier body, compiled twice by warp_tier.cu: WT_J is the largest |J|
-// of the tier (32 or 64), WT_WPB the warps per CTA, WT_NS the namespace.
+// of the tier (32 or 64), WT_TPF the threads that work on one front (a warp,
+// or a whole CTA), WT_WPB the fronts per CTA, WT_NS the namespace.
 // See warp_tier.cu for the description.
 
 namespace chd {
@@ -7,17 +8,41 @@ namespace WT_NS {
 
 constexpr int WJ = WT_J;             // largest |J|
 constexpr int WN = 8;                // largest |N|
-constexpr int WPB = WT_WPB;           // warps per CTA
+constexpr int WPB = WT_WPB;           // fronts (task walkers) per CTA
+constexpr int TPF = WT_TPF;           // threads per front: one warp, or a CTA
 constexpr int PK = WJ * (WJ + 1) / 2;  // packed lower front
 constexpr int BLK = WJ * WN;         // J x n block (column-major, ld WJ)
 constexpr int NN = WN * WN;          // n x n block (column-major, ld WN)
-constexpr int NS = WJ * WN / 32;     // staged values per lane
+constexpr int NS = (WJ * WN + TPF - 1) / TPF;  // staged values per thread
+constexpr int NR = (WJ + TPF - 1) / TPF;       // staged relative indices per thread
 // two packed fronts (the current one and the previous front of the task),
 // three J x n blocks, two n x n blocks, WJ reciprocal pivots, WJ relative
 // indices
 constexpr int PER_WARP = 2 * PK + 3 * BLK + 2 * NN + WJ + WJ / 2;
 
 __device__ __forceinline__ int pk(int J, int r, int c) { return c * J - c * (c - 1) / 2 + (r - c); }
+
+// barrier of the threads working on one front
+__device__ __forceinline__ void fsync() {
+  if (TPF == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// e = q*d + r (0 <= r < d) without the integer-division sequence: an FP32
+// quotient estimate, off by at most one for the small e here, then fixed.
+__device__ __forceinline__ void divmod(int e, int d, int& r, int& q) {
+  int qq = __float2int_rz(__fdividef((float)e, (float)d));
+  int rr = e - qq * d;
+  if (rr < 0) {
+    --qq;
+    rr += d;
+  } else if (rr >= d) {
+    ++qq;
+    rr -= d;
+  }
+  r = rr;
+  q = qq;
+}
 
 struct Smem {
   double* F;   // packed front
@@ -62,19 +87,19 @@ __device__ __forceinline__ Fr fr_meta(const WMeta& w, double* ws) {
 // relative indices.
 struct Stage {
   double v[NS], w[NS];
-  int r[WJ / 32];
+  int r[NR];
 };
 __device__ __forceinline__ void stage_issue(Stage& g, const double* s1, int c1, const double* s2, int c2,
                                             const int32_t* rel, int nrel, int lane) {
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
-    const int e = lane + 32 * i;
+    const int e = lane + TPF * i;
     g.v[i] = (s1 && e < c1) ? s1[e] : 0.0;
     g.w[i] = (s2 && e < c2) ? s2[e] : 0.0;
   }
 #pragma unroll
-  for (int i = 0; i < WJ / 32; ++i) {
-    const int e = lane + 32 * i;
+  for (int i = 0; i < NR; ++i) {
+    const int e = lane + TPF * i;
     g.r[i] = (rel && e < nrel) ? __ldg(rel + e) : 0;
   }
 }
@@ -82,13 +107,13 @@ __device__ __forceinline__ void stage_commit(const Stage& g, double* d1, int c1,
                                              int nrel, int lane) {
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
-    const int e = lane + 32 * i;
+    const int e = lane + TPF * i;
     if (d1 && e < c1) d1[e] = g.v[i];
     if (d2 && e < c2) d2[e] = g.w[i];
   }
 #pragma unroll
-  for (int i = 0; i < WJ / 32; ++i) {
-    const int e = lane + 32 * i;
+  for (int i = 0; i < NR; ++i) {
+    const int e = lane + TPF * i;
     if (rdst && e < nrel) rdst[e] = g.r[i];
   }
 }
@@ -107,7 +132,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // (entry (r, c), r >= c, at pk(m, r, c)); asynchronous
 __device__ __forceinline__ void stage_lower_async(double* dst, const double* M, int m, int lane) {
   for (int c = 0; c < m; ++c)
-    for (int r = c + lane; r < m; r += 32) cp_async8(dst + (c * m - c * (c - 1) / 2 + (r - c)), M + r + (int64_t)c * m);
+    for (int r = c + lane; r < m; r += TPF) cp_async8(dst + (c * m - c * (c - 1) / 2 + (r - c)), M + r + (int64_t)c * m);
 }
 
 // record of front k read from the symbolic arrays (fronts outside a task walk)
@@ -126,7 +151,7 @@ __device__ __forceinline__ int nnz_front(const Fr& f) { return f.n * f.J - f.n *
 
 __device__ void store_front(const Fr& f, const Smem& m, double* dst, double scale, int lane) {
   const int nz = nnz_front(f);
-  for (int e = lane; e < nz; e += 32) dst[f.base + e] = scale * m.F[e];
+  for (int e = lane; e < nz; e += TPF) dst[f.base + e] = scale * m.F[e];
 }
 // extend-add of the children's update blocks (children in a fixed order).
 // A child that is the previous front of the task (flag WM_PREV_CHILD) is read
@@ -137,22 +162,24 @@ __device__ void extend_add(const SymDev& S, const Fr& f, const Fr& prev, const S
   const bool chain = f.flags & WM_PREV_CHILD;
   if (chain && (f.flags & WM_ONLY_CHILD_PREV)) {
     const int ac = prev.a, nc = prev.n, Jc = prev.J;
-    for (int e = lane; e < ac * ac; e += 32) {
-      const int r = e % ac, s = e / ac;
+    for (int e = lane; e < ac * ac; e += TPF) {
+      int r, s;
+    divmod(e, ac, r, s);
       if (r >= s) m.F[pk(f.J, m.rel[r], m.rel[s])] += m.P[pk(Jc, nc + r, nc + s)];
     }
-    __syncwarp();
+    fsync();
     return;
   }
   for (int q = f.ch_beg; q < f.ch_end; ++q) {
     const int c = S.ch[q];
     if (chain && c == prev.k) {
       const int ac = prev.a, nc = prev.n, Jc = prev.J;
-      for (int e = lane; e < ac * ac; e += 32) {
-        const int r = e % ac, s = e / ac;
+      for (int e = lane; e < ac * ac; e += TPF) {
+        int r, s;
+    divmod(e, ac, r, s);
         if (r >= s) m.F[pk(f.J, m.rel[r], m.rel[s])] += m.P[pk(Jc, nc + r, nc + s)];
       }
-      __syncwarp();
+      fsync();
       continue;
     }
     const int nc = (int)(S.sn_ptr[c + 1] - S.sn_ptr[c]);
@@ -160,11 +187,12 @@ __device__ void extend_add(const SymDev& S, const Fr& f, const Fr& prev, const S
     const int ac = Jc - nc;
     const int32_t* rel = S.rel + S.rows_ptr[c] + nc;
     const double* U = ws + S.f_off[c] + nc + (int64_t)nc * Jc;
-    for (int e = lane; e < ac * ac; e += 32) {
-      const int r = e % ac, s = e / ac;
+    for (int e = lane; e < ac * ac; e += TPF) {
+      int r, s;
+    divmod(e, ac, r, s);
       if (r >= s) m.F[pk(f.J, __ldg(rel + r), __ldg(rel + s))] += __ldcg(U + r + (int64_t)s * Jc);
     }
-    __syncwarp();
+    fsync();
   }
 }
 // V block <- parent's front at the relative positions (m.rel holds this
@@ -175,29 +203,32 @@ __device__ void gather_parent(const SymDev& S, const Fr& f, const Fr& prev, cons
   if (f.a == 0) return;
   if (f.flags & WM_NEXT_PARENT) {
     const int Jp = prev.J;
-    for (int e = lane; e < f.a * f.a; e += 32) {
-      const int r = e % f.a, s = e / f.a;
+    for (int e = lane; e < f.a * f.a; e += TPF) {
+      int r, s;
+    divmod(e, f.a, r, s);
       if (r >= s) m.F[pk(f.J, f.n + r, f.n + s)] = m.P[pk(Jp, m.rel[r], m.rel[s])];
     }
-    __syncwarp();
+    fsync();
     return;
   }
   const int p = (int)S.sn_par[f.k];
   if (p < 0) return;
   const int Jp = (int)(S.rows_ptr[p + 1] - S.rows_ptr[p]);
   const double* Fp = ws + S.f_off[p];
-  for (int e = lane; e < f.a * f.a; e += 32) {
-    const int r = e % f.a, s = e / f.a;
+  for (int e = lane; e < f.a * f.a; e += TPF) {
+    int r, s;
+    divmod(e, f.a, r, s);
     if (r >= s) m.F[pk(f.J, f.n + r, f.n + s)] = __ldcg(Fp + m.rel[r] + (int64_t)m.rel[s] * Jp);
   }
-  __syncwarp();
+  fsync();
 }
 // the update block for the parent, unless the parent is the next front of the
 // task (it then reads this front from shared memory)
 __device__ void write_update(const Fr& f, const Smem& m, int lane) {
   if (f.flags & WM_NEXT_PARENT) return;
-  for (int e = lane; e < f.a * f.a; e += 32) {
-    const int r = e % f.a, s = e / f.a;
+  for (int e = lane; e < f.a * f.a; e += TPF) {
+    int r, s;
+    divmod(e, f.a, r, s);
     if (r >= s) f.G[(f.n + r) + (int64_t)(f.n + s) * f.J] = m.F[pk(f.J, f.n + r, f.n + s)];
   }
 }
@@ -206,8 +237,9 @@ __device__ void write_update(const Fr& f, const Smem& m, int lane) {
 __device__ void write_full(const Fr& f, const Smem& m, int lane) {
   if (f.flags & WM_ONLY_CHILD_PREV) return;
   if (f.ch_end == f.ch_beg) return;
-  for (int e = lane; e < f.J * f.J; e += 32) {
-    const int r = e % f.J, s = e / f.J;
+  for (int e = lane; e < f.J * f.J; e += TPF) {
+    int r, s;
+    divmod(e, f.J, r, s);
     if (r >= s) f.G[r + (int64_t)s * f.J] = m.F[pk(f.J, r, s)];
   }
 }
@@ -269,8 +301,9 @@ struct CscOut {  // output rows [ro, ..) of the N-part in a CSC array
 template <class FA, class FB, class FC>
 __device__ void wgemm(int R, int N, int K, double alpha, FA A, FB B, double beta, FC C, bool lower, int lane) {
   const int tot = R * N;
-  for (int e = lane; e < tot; e += 32) {
-    const int r = e % R, c = e / R;
+  for (int e = lane; e < tot; e += TPF) {
+    int r, c;
+    divmod(e, R, r, c);
     if (lower && r < c) continue;
     double acc = 0.0;
     for (int k = 0; k < K; ++k) acc = fma(A(r, k), B(k, c), acc);
@@ -278,7 +311,7 @@ __device__ void wgemm(int R, int N, int K, double alpha, FA A, FB B, double beta
     if (beta != 0.0) v = fma(beta, C(r, c), v);
     C(r, c) = v;
   }
-  __syncwarp();
+  fsync();
 }
 
 // In-place Cholesky of an m x m lower matrix given by accessor (m <= 32);
@@ -293,19 +326,22 @@ __device__ void wpotrf(int m, FM A, double* rv, int64_t* st, int64_t code, int64
       d = 1.0;
     }
     const double r = rsqrt(d);
-    __syncwarp();
+    fsync();
     if (lane == 0) {
       A(j, j) = d * r;
       rv[j] = r;
     }
-    for (int i = j + 1 + lane; i < m; i += 32) A(i, j) = A(i, j) * r;
-    __syncwarp();
+    for (int i = j + 1 + lane; i < m; i += TPF) A(i, j) = A(i, j) * r;
+    fsync();
     const int q = m - j - 1;
-    for (int e = lane; e < q * q; e += 32) {
-      const int i = j + 1 + e % q, k = j + 1 + e / q;
+    for (int e = lane; e < q * q; e += TPF) {
+      int i, k;
+      divmod(e, q, i, k);
+      i += j + 1;
+      k += j + 1;
       if (i >= k) A(i, k) = A(i, k) - A(i, j) * A(k, j);
     }
-    __syncwarp();
+    fsync();
   }
 }
 // B (R x m) := B L^{-T} (fwd) or B L^{-1} (!fwd), L m x m lower (accessor),
@@ -315,34 +351,39 @@ __device__ void wtrsm_r(int R, int m, FB B, FL L, const double* rv, bool fwd, in
   if (fwd) {
     for (int c = 0; c < m; ++c) {
       const double inv = rv[c];
-      for (int r = lane; r < R; r += 32) B(r, c) = B(r, c) * inv;
-      __syncwarp();
+      for (int r = lane; r < R; r += TPF) B(r, c) = B(r, c) * inv;
+      fsync();
       const int q = m - c - 1;
-      for (int e = lane; e < R * q; e += 32) {
-        const int r = e % R, t = c + 1 + e / R;
+      for (int e = lane; e < R * q; e += TPF) {
+        int r, t;
+        divmod(e, R, r, t);
+        t += c + 1;
         B(r, t) = B(r, t) - B(r, c) * L(t, c);
       }
-      __syncwarp();
+      fsync();
     }
   } else {
     for (int c = m - 1; c >= 0; --c) {
       const double inv = rv[c];
-      for (int r = lane; r < R; r += 32) B(r, c) = B(r, c) * inv;
-      __syncwarp();
-      for (int e = lane; e < R * c; e += 32) {
-        const int r = e % R, t = e / R;
+      for (int r = lane; r < R; r += TPF) B(r, c) = B(r, c) * inv;
+      fsync();
+      for (int e = lane; e < R * c; e += TPF) {
+        int r, t;
+    divmod(e, R, r, t);
         B(r, t) = B(r, t) - B(r, c) * L(c, t);
       }
-      __syncwarp();
+      fsync();
     }
   }
 }
 // sum over i < n of 2 log(diag(i)) by the lanes, written by lane 0
 template <class FD>
 __device__ void wlogdet(int n, FD diag, double* out, int lane) {
-  double s = lane < n ? 2.0 * log(diag(lane)) : 0.0;
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) *out = s;
+  if (lane < 32) {  // n <= 8: the first warp holds every term
+    double s = lane < n ? 2.0 * log(diag(lane)) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) *out = s;
+  }
 }
 struct BkTW {  // transposed writable view of a column-major block
   double* p;
@@ -363,15 +404,17 @@ struct GL {  // global column-major (lower triangular use)
 // L_AN (a x n) -> A1, D^{-1} (n x n, lower) -> D1 from the front's Wc values
 // staged (packed, CSC order) in Wp
 __device__ void scatter_w(const Fr& f, const Smem& m, const double* Wp, int lane) {
-  for (int e = lane; e < f.a * f.n; e += 32) {
-    const int r = e % f.a, c = e / f.a;
+  for (int e = lane; e < f.a * f.n; e += TPF) {
+    int r, c;
+    divmod(e, f.a, r, c);
     m.A1[r + c * WJ] = Wp[pk(f.J, f.n + r, c)];
   }
-  for (int e = lane; e < f.n * f.n; e += 32) {
-    const int r = e % f.n, c = e / f.n;
+  for (int e = lane; e < f.n * f.n; e += TPF) {
+    int r, c;
+    divmod(e, f.n, r, c);
     if (r >= c) m.D1[r + c * WN] = Wp[pk(f.J, r, c)];
   }
-  __syncwarp();
+  fsync();
 }
 // inputs of a bottom-up front: values (N-part) into F (A x A block zeroed or
 // the whole front zeroed), Wc into A3 (then A1/D1), the chain child's
@@ -384,10 +427,10 @@ __device__ void load_up(const SymDev& S, const Fr& f, const Fr& prev, const Smem
   stage_issue(g, vals ? vals + f.base : nullptr, nz, Wc ? Wc + f.base : nullptr, nz,
               chain ? S.rel + prev.rows_off + prev.n : nullptr, chain ? prev.a : 0, lane);
   const int tot = f.J * (f.J + 1) / 2;
-  for (int e = (zero_all ? 0 : nz) + lane; e < tot; e += 32) m.F[e] = 0.0;
+  for (int e = (zero_all ? 0 : nz) + lane; e < tot; e += TPF) m.F[e] = 0.0;
   stage_commit(g, vals ? vdst : nullptr, nz, Wc ? m.A3 : nullptr, nz, chain ? m.rel : nullptr,
                chain ? prev.a : 0, lane);
-  __syncwarp();
+  fsync();
   if (Wc) scatter_w(f, m, m.A3, lane);
 }
 // inputs of a top-down front: values (N-part) into F, Wc into A3 (then
@@ -399,7 +442,7 @@ __device__ void load_down(const SymDev& S, const Fr& f, const Smem& m, const dou
   stage_issue(g, vals ? vals + f.base : nullptr, nz, Wc ? Wc + f.base : nullptr, nz, S.rel + f.rows_off + f.n,
               f.a, lane);
   stage_commit(g, vals ? m.F : nullptr, nz, Wc ? m.A3 : nullptr, nz, m.rel, f.a, lane);
-  __syncwarp();
+  fsync();
   if (Wc) scatter_w(f, m, m.A3, lane);
 }
 
@@ -413,54 +456,61 @@ __device__ void factor_front(const SymDev& S, const Fr& f, const Fr& prev, const
   load_up(S, f, prev, m, X, m.F, nullptr, false, lane);
   extend_add(S, f, prev, m, ws, lane);
   double* D = Dd + f.d_off;
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     if (r >= c) D[r + c * n] = m.F[pk(J, r, c)];
   }
   // C = chol(F11), B = F21 C^{-T}, U = F22 - B B^T
   wpotrf(n, PkRect{m.F, J, 0}, m.rv, st, CHD_ERR_NOT_PD, k, f.col0, lane);
   wtrsm_r(a, n, PkRect{m.F, J, n}, PkRect{m.F, J, 0}, m.rv, true, lane);
-  for (int e = lane; e < a * a; e += 32) {
-    const int r = e % a, s = e / a;
+  for (int e = lane; e < a * a; e += TPF) {
+    int r, s;
+    divmod(e, a, r, s);
     if (r < s) continue;
     double acc = 0.0;
     for (int t = 0; t < n; ++t) acc = fma(m.F[pk(J, n + r, t)], m.F[pk(J, n + s, t)], acc);
     m.F[pk(J, n + r, n + s)] -= acc;
   }
-  __syncwarp();
+  fsync();
   store_front(f, m, Lc, 1.0, lane);
   wlogdet(n, [&](int i) { return m.F[pk(J, i, i)]; }, ldet + k, lane);
   // Cinv (D2) = C^{-1}; D^{-1} = Cinv^T Cinv (D1, lower); L_AN = B C^{-1} (A1)
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     m.D2[r + c * WN] = r == c ? 1.0 : 0.0;
   }
-  __syncwarp();
+  fsync();
   wtrsm_r(n, n, BkTW{m.D2, WN}, PkRect{m.F, J, 0}, m.rv, true, lane);
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     if (r < c) continue;
     double acc = 0.0;
     for (int t = r; t < n; ++t) acc = fma(m.D2[t + r * WN], m.D2[t + c * WN], acc);
     m.D1[r + c * WN] = acc;
   }
-  for (int e = lane; e < a * n; e += 32) {
-    const int r = e % a, c = e / a;
+  for (int e = lane; e < a * n; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     m.A1[r + c * WJ] = m.F[pk(J, n + r, c)];
   }
-  __syncwarp();
+  fsync();
   wtrsm_r(a, n, Bk{m.A1, WJ}, PkRect{m.F, J, 0}, m.rv, false, lane);
   double* W = Wc + f.base;
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     if (r >= c) W[pk(J, r, c)] = m.D1[r + c * WN];
   }
-  for (int e = lane; e < a * n; e += 32) {
-    const int r = e % a, c = e / a;
+  for (int e = lane; e < a * n; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     W[pk(J, n + r, c)] = m.A1[r + c * WJ];
   }
   write_update(f, m, lane);
-  __syncwarp();
+  fsync();
 }
 
 __device__ void gradient_front(const SymDev& S, const Fr& f, const Fr& prev, const double* Wc, double* Sc,
@@ -471,23 +521,25 @@ __device__ void gradient_front(const SymDev& S, const Fr& f, const Fr& prev, con
   // S_AN = -V L_AN
   wgemm(a, n, a, -1.0, PkSym{m.F, J, n}, Bk{m.A1, WJ}, 0.0, PkRect{m.F, J, n}, false, lane);
   // S_NN = D^{-1} - S_AN^T L_AN
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     if (r < c) continue;
     double acc = 0.0;
     for (int t = 0; t < a; ++t) acc = fma(m.F[pk(J, n + t, r)], m.A1[t + c * WJ], acc);
     m.F[pk(J, r, c)] = m.D1[r + c * WN] - acc;
   }
-  __syncwarp();
+  fsync();
   store_front(f, m, Sc, 1.0, lane);
   if (g) store_front(f, m, g, -1.0, lane);
   double* V = Vd + f.v_off;
-  for (int e = lane; e < a * a; e += 32) {
-    const int r = e % a, s = e / a;
+  for (int e = lane; e < a * a; e += TPF) {
+    int r, s;
+    divmod(e, a, r, s);
     if (r >= s) V[r + s * a] = m.F[pk(J, n + r, n + s)];
   }
   write_full(f, m, lane);
-  __syncwarp();
+  fsync();
 }
 
 __device__ void hess_up_front(const SymDev& S, const Fr& f, const Fr& prev, const double* Wc, const double* Vd,
@@ -498,17 +550,19 @@ __device__ void hess_up_front(const SymDev& S, const Fr& f, const Fr& prev, cons
   // V_k (lower, packed) into the previous front's buffer, free from here on
   stage_lower_async(m.P, Vd + f.v_off, a, lane);
   // A2 = K_AN = Y_AN - L Y_NN
-  for (int e = lane; e < a * n; e += 32) {
-    const int r = e % a, c = e / a;
+  for (int e = lane; e < a * n; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     double acc = m.F[pk(J, n + r, c)];
     for (int t = 0; t < n; ++t)
       acc = fma(-m.A1[r + t * WJ], t >= c ? m.F[pk(J, t, c)] : m.F[pk(J, c, t)], acc);
     m.A2[r + c * WJ] = acc;
   }
-  __syncwarp();
+  fsync();
   // U' = Y_AA - K_AN L^T - L Y_AN^T  (lower)
-  for (int e = lane; e < a * a; e += 32) {
-    const int r = e % a, s = e / a;
+  for (int e = lane; e < a * a; e += TPF) {
+    int r, s;
+    divmod(e, a, r, s);
     if (r < s) continue;
     double acc = 0.0;
     for (int t = 0; t < n; ++t) {
@@ -517,17 +571,17 @@ __device__ void hess_up_front(const SymDev& S, const Fr& f, const Fr& prev, cons
     }
     m.F[pk(J, n + r, n + s)] -= acc;
   }
-  __syncwarp();
+  fsync();
   // D2 = K_NN D^{-1};  M_NN = D^{-1} D2 -> T (lower)
   wgemm(n, n, n, 1.0, PkSym{m.F, J, 0}, BkSym{m.D1, WN}, 0.0, Bk{m.D2, WN}, false, lane);
   wgemm(n, n, n, 1.0, BkSym{m.D1, WN}, Bk{m.D2, WN}, 0.0, CscOut{T + f.base, J, 0}, true, lane);
   // A3 = K_AN D^{-1};  M_AN = V A3 -> T
   wgemm(a, n, n, 1.0, Bk{m.A2, WJ}, BkSym{m.D1, WN}, 0.0, Bk{m.A3, WJ}, false, lane);
   cp_async_wait_all();
-  __syncwarp();
+  fsync();
   wgemm(a, n, a, 1.0, PkSym{m.P, a, 0}, Bk{m.A3, WJ}, 0.0, CscOut{T + f.base, J, n}, false, lane);
   write_update(f, m, lane);
-  __syncwarp();
+  fsync();
 }
 
 __device__ void hess_down_front(const SymDev& S, const Fr& f, const Fr& prev, const double* Wc, double* T,
@@ -537,14 +591,16 @@ __device__ void hess_down_front(const SymDev& S, const Fr& f, const Fr& prev, co
   gather_parent(S, f, prev, m, ws, lane);
   // A2 = V' L
   wgemm(a, n, a, 1.0, PkSym{m.F, J, n}, Bk{m.A1, WJ}, 0.0, Bk{m.A2, WJ}, false, lane);
-  for (int e = lane; e < a * n; e += 32) {
-    const int r = e % a, c = e / a;
+  for (int e = lane; e < a * n; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     m.F[pk(J, n + r, c)] -= 0.5 * m.A2[r + c * WJ];
   }
-  __syncwarp();
+  fsync();
   // T_NN = M_NN - (Q^T L + L^T Q)
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     if (r < c) continue;
     double acc = 0.0;
     for (int t = 0; t < a; ++t) {
@@ -553,15 +609,16 @@ __device__ void hess_down_front(const SymDev& S, const Fr& f, const Fr& prev, co
     }
     m.F[pk(J, r, c)] -= acc;
   }
-  __syncwarp();
-  for (int e = lane; e < a * n; e += 32) {
-    const int r = e % a, c = e / a;
+  fsync();
+  for (int e = lane; e < a * n; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     m.F[pk(J, n + r, c)] -= 0.5 * m.A2[r + c * WJ];
   }
-  __syncwarp();
+  fsync();
   store_front(f, m, T, 1.0, lane);
   write_full(f, m, lane);
-  __syncwarp();
+  fsync();
 }
 
 __device__ void ihess_down_front(const SymDev& S, const Fr& f, const Fr& prev, const double* Wc,
@@ -577,17 +634,19 @@ __device__ void ihess_down_front(const SymDev& S, const Fr& f, const Fr& prev, c
   stage_lower_async(Rp, Rd + f.v_off, a, lane);
   stage_lower_async(Dp, Dd + f.d_off, n, lane);
   // A2 = M_AN = T_AN + V' L
-  for (int e = lane; e < a * n; e += 32) {
-    const int r = e % a, c = e / a;
+  for (int e = lane; e < a * n; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     double acc = m.F[pk(J, n + r, c)];
     for (int t = 0; t < a; ++t)
       acc = fma(n + r >= n + t ? m.F[pk(J, n + r, n + t)] : m.F[pk(J, n + t, n + r)], m.A1[t + c * WJ], acc);
     m.A2[r + c * WJ] = acc;
   }
-  __syncwarp();
+  fsync();
   // D2 = M_NN = T_NN + T_AN^T L + L^T M_AN  (full)
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     double acc = r >= c ? m.F[pk(J, r, c)] : m.F[pk(J, c, r)];
     for (int t = 0; t < a; ++t) {
       acc = fma(m.F[pk(J, n + t, r)], m.A1[t + c * WJ], acc);
@@ -595,9 +654,9 @@ __device__ void ihess_down_front(const SymDev& S, const Fr& f, const Fr& prev, c
     }
     m.D2[r + c * WN] = acc;
   }
-  __syncwarp();
+  fsync();
   cp_async_wait_all();
-  __syncwarp();
+  fsync();
   const PkSym D{Dp, n, 0};
   // D1 = M_NN D ;  K_NN = D D1 -> Y (lower)
   wgemm(n, n, n, 1.0, Bk{m.D2, WN}, D, 0.0, Bk{m.D1, WN}, false, lane);
@@ -608,7 +667,7 @@ __device__ void ihess_down_front(const SymDev& S, const Fr& f, const Fr& prev, c
     wgemm(a, n, a, 1.0, PkSym{Rp, a, 0}, Bk{m.A3, WJ}, 0.0, CscOut{Y + f.base, J, n}, false, lane);
   }
   write_full(f, m, lane);
-  __syncwarp();
+  fsync();
 }
 
 __device__ void ihess_up_front(const SymDev& S, const Fr& f, const Fr& prev, const double* Wc, double* Y,
@@ -620,16 +679,18 @@ __device__ void ihess_up_front(const SymDev& S, const Fr& f, const Fr& prev, con
   extend_add(S, f, prev, m, ws, lane);
   const double* Kc = m.A2;
   // A3 = P = K_AN + 1/2 L K_NN
-  for (int e = lane; e < a * n; e += 32) {
-    const int r = e % a, c = e / a;
+  for (int e = lane; e < a * n; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     double acc = 0.0;
     for (int t = 0; t < n; ++t) acc = fma(m.A1[r + t * WJ], t >= c ? Kc[pk(J, t, c)] : Kc[pk(J, c, t)], acc);
     m.A3[r + c * WJ] = Kc[pk(J, n + r, c)] + 0.5 * acc;
   }
-  __syncwarp();
+  fsync();
   // U' = Z_AA - (P L^T + L P^T)
-  for (int e = lane; e < a * a; e += 32) {
-    const int r = e % a, s = e / a;
+  for (int e = lane; e < a * a; e += TPF) {
+    int r, s;
+    divmod(e, a, r, s);
     if (r < s) continue;
     double acc = 0.0;
     for (int t = 0; t < n; ++t) {
@@ -638,21 +699,23 @@ __device__ void ihess_up_front(const SymDev& S, const Fr& f, const Fr& prev, con
     }
     m.F[pk(J, n + r, n + s)] -= acc;
   }
-  __syncwarp();
+  fsync();
   double* Yo = Y + f.base;
-  for (int e = lane; e < a * n; e += 32) {
-    const int r = e % a, c = e / a;
+  for (int e = lane; e < a * n; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     const int o = pk(J, n + r, c);
     Yo[o] = 2.0 * m.A3[r + c * WJ] - Kc[o] - m.F[o];
   }
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     if (r < c) continue;
     const int o = pk(J, r, c);
     Yo[o] = Kc[o] - m.F[o];
   }
   write_update(f, m, lane);
-  __syncwarp();
+  fsync();
 }
 
 // S-front of the completion: S_NN and S_AN from the input's columns N_k,
@@ -663,93 +726,106 @@ __device__ void complete_front(const SymDev& S, int k, const double* Sin, double
   Fr f = fr(S, k, nullptr);
   const int J = f.J, n = f.n, a = f.a;
   const int32_t* A = S.rows + S.rows_ptr[k] + n;
-  for (int e = lane; e < a * a; e += 32) {
-    const int r = e % a, c = e / a;
+  for (int e = lane; e < a * a; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     if (r >= c) m.F[pk(J, n + r, n + c)] = Sin[csc_find(S, __ldg(A + r), __ldg(A + c))];
   }
   const int nz = nnz_front(f);
-  for (int e = lane; e < nz; e += 32) m.F[e] = Sin[f.base + e];
-  __syncwarp();
+  for (int e = lane; e < nz; e += TPF) m.F[e] = Sin[f.base + e];
+  fsync();
   double* V = Vd + S.v_off[k];
   double* R = Rd + S.v_off[k];
-  for (int e = lane; e < a * a; e += 32) {
-    const int r = e % a, s = e / a;
+  for (int e = lane; e < a * a; e += TPF) {
+    int r, s;
+    divmod(e, a, r, s);
     if (r >= s) V[r + s * a] = m.F[pk(J, n + r, n + s)];
   }
-  __syncwarp();
+  fsync();
   PkBlk Rv{m.F, J, n};
   if (a > 0) wpotrf(a, Rv, m.rv, st, CHD_ERR_NOT_COMPLETABLE, k, -1, lane);
-  for (int e = lane; e < a * a; e += 32) {
-    const int r = e % a, s = e / a;
+  for (int e = lane; e < a * a; e += TPF) {
+    int r, s;
+    divmod(e, a, r, s);
     if (r >= s) R[r + s * a] = m.F[pk(J, n + r, n + s)];
   }
   // A1 = Z = R^{-1} S_AN
-  for (int e = lane; e < a * n; e += 32) {
-    const int r = e % a, c = e / a;
+  for (int e = lane; e < a * n; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     m.A1[r + c * WJ] = m.F[pk(J, n + r, c)];
   }
-  __syncwarp();
+  fsync();
   if (a > 0) wtrsm_r(n, a, BkTW{m.A1, WJ}, Rv, m.rv, true, lane);
   // D1 = P = S_NN - Z^T Z (lower);  A2 = L_AN = -R^{-T} Z
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     if (r < c) continue;
     double acc = 0.0;
     for (int t = 0; t < a; ++t) acc = fma(m.A1[t + r * WJ], m.A1[t + c * WJ], acc);
     m.D1[r + c * WN] = m.F[pk(J, r, c)] - acc;
   }
-  for (int e = lane; e < a * n; e += 32) {
-    const int r = e % a, c = e / a;
+  for (int e = lane; e < a * n; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     m.A2[r + c * WJ] = -m.A1[r + c * WJ];
   }
-  __syncwarp();
+  fsync();
   if (a > 0) wtrsm_r(n, a, BkTW{m.A2, WJ}, Rv, m.rv, false, lane);
   double* W = Wc + f.base;
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     if (r >= c) W[pk(J, r, c)] = m.D1[r + c * WN];
   }
-  for (int e = lane; e < a * n; e += 32) {
-    const int r = e % a, c = e / a;
+  for (int e = lane; e < a * n; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     W[pk(J, n + r, c)] = m.A2[r + c * WJ];
   }
   // D2 = Q = chol(P); D1 = Q^{-1} ... D = Q^{-T} Q^{-1}
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     m.D2[r + c * WN] = r >= c ? m.D1[r + c * WN] : 0.0;
   }
-  __syncwarp();
+  fsync();
   wpotrf(n, Bk{m.D2, WN}, m.rv, st, CHD_ERR_NOT_COMPLETABLE, k, f.col0, lane);
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     m.D1[r + c * WN] = r == c ? 1.0 : 0.0;
   }
-  __syncwarp();
+  fsync();
   wtrsm_r(n, n, BkTW{m.D1, WN}, Bk{m.D2, WN}, m.rv, true, lane);  // D1 = Q^{-1} (lower)
   double* Dk = Dd + S.d_off[k];
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     if (r < c) continue;
     double acc = 0.0;
     for (int t = r; t < n; ++t) acc = fma(m.D1[t + r * WN], m.D1[t + c * WN], acc);
     m.D2[r + c * WN] = acc;  // D (lower)
     Dk[r + c * n] = acc;
   }
-  __syncwarp();
+  fsync();
   wpotrf(n, Bk{m.D2, WN}, m.rv, st, CHD_ERR_NOT_COMPLETABLE, k, f.col0, lane);  // C
   double* Lo = Lc + f.base;
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e % n, c = e / n;
+  for (int e = lane; e < n * n; e += TPF) {
+    int r, c;
+    divmod(e, n, r, c);
     if (r >= c) Lo[pk(J, r, c)] = m.D2[r + c * WN];
   }
-  for (int e = lane; e < a * n; e += 32) {
-    const int r = e % a, c = e / a;
+  for (int e = lane; e < a * n; e += TPF) {
+    int r, c;
+    divmod(e, a, r, c);
     double acc = 0.0;
     for (int t = c; t < n; ++t) acc = fma(m.A2[r + t * WJ], m.D2[t + c * WN], acc);
     Lo[pk(J, n + r, c)] = acc;
   }
   wlogdet(n, [&](int i) { return m.D2[i + i * WN]; }, ldet + k, lane);
-  __syncwarp();
+  fsync();
 }
 
 // ---------------------------------------------------------------------------
@@ -807,12 +883,12 @@ __device__ __forceinline__ void walk_down(const SymDev& S, int t, double* ws, in
   }
 }
 
-#define WARP_TASK_PROLOGUE                                   \
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;   \
-  const int t = task0 + blockIdx.x * WPB + w;                \
+#define WARP_TASK_PROLOGUE                                     \
+  const int w = threadIdx.x / TPF, lane = threadIdx.x % TPF;   \
+  const int t = task0 + blockIdx.x * WPB + w;                  \
   if (t >= task_end) return;
 
-__global__ void __launch_bounds__(WPB * 32) kw_factor(SymDev S, int task0, int task_end, const double* X,
+__global__ void __launch_bounds__(WPB * TPF) kw_factor(SymDev S, int task0, int task_end, const double* X,
                                                       double* Lc, double* Wc, double* Dd, double* ws,
                                                       double* ldet, int64_t* st) {
   WARP_TASK_PROLOGUE
@@ -820,14 +896,14 @@ __global__ void __launch_bounds__(WPB * 32) kw_factor(SymDev S, int task0, int t
     factor_front(S, f, prev, X, Lc, Wc, Dd, ws, ldet, st, m, lane);
   });
 }
-__global__ void __launch_bounds__(WPB * 32) kw_gradient(SymDev S, int task0, int task_end, const double* Wc,
+__global__ void __launch_bounds__(WPB * TPF) kw_gradient(SymDev S, int task0, int task_end, const double* Wc,
                                                         double* Sc, double* g, double* Vd, double* ws) {
   WARP_TASK_PROLOGUE
   walk_down(S, t, ws, w, [&](const Fr& f, const Fr& prev, const Smem& m) {
     gradient_front(S, f, prev, Wc, Sc, g, Vd, ws, m, lane);
   });
 }
-__global__ void __launch_bounds__(WPB * 32) kw_hess_up(SymDev S, int task0, int task_end, const double* Wc,
+__global__ void __launch_bounds__(WPB * TPF) kw_hess_up(SymDev S, int task0, int task_end, const double* Wc,
                                                        const double* Vd, const double* Y, int64_t ldy, double* T,
                                                        int64_t ldt, double* ws) {
   WARP_TASK_PROLOGUE
@@ -837,7 +913,7 @@ __global__ void __launch_bounds__(WPB * 32) kw_hess_up(SymDev S, int task0, int 
     hess_up_front(S, f, prev, Wc, Vd, Y + y * ldy, T + y * ldt, wsy, m, lane);
   });
 }
-__global__ void __launch_bounds__(WPB * 32) kw_hess_down(SymDev S, int task0, int task_end, const double* Wc,
+__global__ void __launch_bounds__(WPB * TPF) kw_hess_down(SymDev S, int task0, int task_end, const double* Wc,
                                                          double* T, int64_t ldt, double* ws) {
   WARP_TASK_PROLOGUE
   const int64_t y = blockIdx.y;
@@ -846,7 +922,7 @@ __global__ void __launch_bounds__(WPB * 32) kw_hess_down(SymDev S, int task0, in
     hess_down_front(S, f, prev, Wc, T + y * ldt, wsy, m, lane);
   });
 }
-__global__ void __launch_bounds__(WPB * 32) kw_ihess_down(SymDev S, int task0, int task_end, const double* Wc,
+__global__ void __launch_bounds__(WPB * TPF) kw_ihess_down(SymDev S, int task0, int task_end, const double* Wc,
                                                           const double* Dd, const double* Rd, const double* Tin,
                                                           int64_t ldt, double* Y, int64_t ldy, double* ws) {
   WARP_TASK_PROLOGUE
@@ -856,7 +932,7 @@ __global__ void __launch_bounds__(WPB * 32) kw_ihess_down(SymDev S, int task0, i
     ihess_down_front(S, f, prev, Wc, Dd, Rd, Tin + y * ldt, Y + y * ldy, wsy, m, lane);
   });
 }
-__global__ void __launch_bounds__(WPB * 32) kw_ihess_up(SymDev S, int task0, int task_end, const double* Wc,
+__global__ void __launch_bounds__(WPB * TPF) kw_ihess_up(SymDev S, int task0, int task_end, const double* Wc,
                                                         double* Y, int64_t ldy, double* ws) {
   WARP_TASK_PROLOGUE
   const int64_t y = blockIdx.y;
@@ -868,10 +944,10 @@ __global__ void __launch_bounds__(WPB * 32) kw_ihess_up(SymDev S, int task0, int
 #if WT_J == 32
 // all warp-tier fronts at once, one warp each (the completion has no
 // dependencies between fronts)
-__global__ void __launch_bounds__(WPB * 32) kw_complete(SymDev S, const double* Sin, double* Lc, double* Wc,
+__global__ void __launch_bounds__(WPB * TPF) kw_complete(SymDev S, const double* Sin, double* Lc, double* Wc,
                                                         double* Dd, double* Vd, double* Rd, double* ldet,
                                                         int64_t* st) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = threadIdx.x / TPF, lane = threadIdx.x % TPF;
   const int64_t i = (int64_t)blockIdx.x * WPB + w;
   if (i >= S.warp_count) return;
   const Smem m = smem_for_warp(w, 0);
@@ -889,39 +965,39 @@ static inline dim3 wgrid(int nt, int m) { return dim3((nt + WPB - 1) / WPB, m); 
 
 void warp_factor(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* X, double* Lc, double* Wc,
                  double* Dd, double* ws, double* ldet, int64_t* status) {
-  kw_factor<<<wgrid(nt, 1), WPB * 32, 0, st>>>(s->dev, t0, t0 + nt, X, Lc, Wc, Dd, ws, ldet, status);
+  kw_factor<<<wgrid(nt, 1), WPB * TPF, 0, st>>>(s->dev, t0, t0 + nt, X, Lc, Wc, Dd, ws, ldet, status);
   chd_launch::count_launch();
 }
 void warp_gradient(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Wc, double* Sc,
                    double* g, double* Vd, double* ws) {
-  kw_gradient<<<wgrid(nt, 1), WPB * 32, 0, st>>>(s->dev, t0, t0 + nt, Wc, Sc, g, Vd, ws);
+  kw_gradient<<<wgrid(nt, 1), WPB * TPF, 0, st>>>(s->dev, t0, t0 + nt, Wc, Sc, g, Vd, ws);
   chd_launch::count_launch();
 }
 void warp_hess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
                   const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
-  kw_hess_up<<<wgrid(nt, m), WPB * 32, 0, st>>>(s->dev, t0, t0 + nt, Wc, Vd, Y, ldy, T, ldt, ws);
+  kw_hess_up<<<wgrid(nt, m), WPB * TPF, 0, st>>>(s->dev, t0, t0 + nt, Wc, Vd, Y, ldy, T, ldt, ws);
   chd_launch::count_launch();
 }
 void warp_hess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* T,
                     int64_t ldt, double* ws) {
-  kw_hess_down<<<wgrid(nt, m), WPB * 32, 0, st>>>(s->dev, t0, t0 + nt, Wc, T, ldt, ws);
+  kw_hess_down<<<wgrid(nt, m), WPB * TPF, 0, st>>>(s->dev, t0, t0 + nt, Wc, T, ldt, ws);
   chd_launch::count_launch();
 }
 void warp_ihess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
                      const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy,
                      double* ws) {
-  kw_ihess_down<<<wgrid(nt, m), WPB * 32, 0, st>>>(s->dev, t0, t0 + nt, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+  kw_ihess_down<<<wgrid(nt, m), WPB * TPF, 0, st>>>(s->dev, t0, t0 + nt, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
   chd_launch::count_launch();
 }
 void warp_ihess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* Y,
                    int64_t ldy, double* ws) {
-  kw_ihess_up<<<wgrid(nt, m), WPB * 32, 0, st>>>(s->dev, t0, t0 + nt, Wc, Y, ldy, ws);
+  kw_ihess_up<<<wgrid(nt, m), WPB * TPF, 0, st>>>(s->dev, t0, t0 + nt, Wc, Y, ldy, ws);
   chd_launch::count_launch();
 }
 #if WT_J == 32
 void warp_complete_all(const chd_symbolic* s, cudaStream_t st, const double* Sin, double* Lc, double* Wc,
                        double* Dd, double* Vd, double* Rd, double* ldet, int64_t* status) {
-  kw_complete<<<wgrid((int)s->dev.warp_count, 1), WPB * 32, 0, st>>>(s->dev, Sin, Lc, Wc, Dd, Vd, Rd, ldet, status);
+  kw_complete<<<wgrid((int)s->dev.warp_count, 1), WPB * TPF, 0, st>>>(s->dev, Sin, Lc, Wc, Dd, Vd, Rd, ldet, status);
   chd_launch::count_launch();
 }
 #endif

@@ -6,7 +6,8 @@ a profiler.
 WORKLOAD: band200 (band n=200, half-bandwidth 8), er5000 (Erdos-Renyi
 n=5000, p=0.001, minimum degree, relax 16), grid150 (5-point 150x150 grid,
 nested dissection), dense1500 (dense 1500x1500 pattern), grid3d40 (7-point
-40x40x40 grid, nested dissection), batch256 (256 independent band, arrow and
+40x40x40 grid, nested dissection), band20k_w61 (band n=20000,
+half-bandwidth 61: one long chain of thin fronts), batch256 (256 independent band, arrow and
 2D-grid instances, n log-uniform in [300, 30000], in one batched symbolic
 object).  OP: factor, gradient, hessian,
 inv_hessian, completion or all.  M: right-hand sides of the Hessian-type
@@ -34,7 +35,8 @@ import workloads as W  # noqa: E402
 
 from . import binding as B  # noqa: E402
 
-DEFAULT_M = {"band200": 1, "er5000": 8, "grid150": 64, "dense1500": 8, "grid3d40": 1, "batch256": 4}
+DEFAULT_M = {"band200": 1, "er5000": 8, "grid150": 64, "dense1500": 8, "grid3d40": 1, "batch256": 4,
+             "band20k_w61": 4}
 
 
 def symbolic_for(name):
@@ -48,6 +50,8 @@ def symbolic_for(name):
         return B.Symbolic(*W.band(1500, 1499))
     if name == "grid3d40":
         return B.Symbolic(*W.grid3d(40, 40, 40), perm=W.nested_dissection((40, 40, 40), leaf=8))
+    if name == "band20k_w61":
+        return B.Symbolic(*W.band(20000, 61))
     if name == "batch256":
         inst = W.batch_mix(256, 3)
         return B.SymbolicBatch([p for p, _, _ in inst], perms=[q for _, q, _ in inst])
