@@ -39,6 +39,11 @@ import workloads as W  # noqa: E402
 
 METRIC = "Hessian evals/s"
 UNIT = "evals/s"
+# FP64 roofline of the front arithmetic: 152 SMs x 2.07 GHz x 2 FMA per clock per SM
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+# DRAM bytes (read + write) of one Hessian call, from one ncu capture of that call
+# (profiles/dram_traffic_hessian_er5000.md); None where no capture was taken
+TRAFFIC_PER_HESSIAN_CALL = {"er5000": 6.39e9}
 
 
 def make_workload(name):
@@ -466,10 +471,13 @@ def run_ours(args, wl, rank, world, local_rank):
                        "rhs_per_step": m, "global_batch": world * evals_per_step,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MB write)"},
-            "roofline": {"bound": "alu", "kernel": "Hessian products (k_hess_up + k_hess_down level launches)",
-                         "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp64_peak, "traffic": None,
-                         "peak_source": "measured FP64 DFMA throughput (chd_probe_fp64_peak), same run"},
+            "roofline": {"bound": "alu",
+                         "kernel": "one Hessian call (all its launches; the dense-tier FP64 products carry the flops)",
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_HESSIAN_CALL.get(wl["name"]),
+                         "peak_source": "FP64 FMA rate from unit counts and clock: 152 SMs x 2070 MHz x 4 flop/clk",
+                         "peak_probe": fp64_peak, "frac_of_probe": achieved / fp64_peak,
+                         "probe_source": "FP64 DFMA loop on all SMs (chd_probe_fp64_peak), same run"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},

@@ -518,8 +518,8 @@ __global__ void __launch_bounds__(BT) mk_extend_add(SymDev S, int k, double* ws,
   ws += blockIdx.z * sws;
   const int Jp = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]);
   double* F = ws + S.f_off[k];
-  for (int64_t q = S.ch_ptr[k]; q < S.ch_ptr[k + 1]; ++q) {
-    const int c = S.ch[q];
+  for (int64_t q = S.ea_ptr[k]; q < S.ea_ptr[k + 1]; ++q) {
+    const int c = S.ea[q];
     const int nc = (int)(S.sn_ptr[c + 1] - S.sn_ptr[c]);
     const int Jc = (int)(S.rows_ptr[c + 1] - S.rows_ptr[c]);
     const int ac = Jc - nc;
@@ -622,7 +622,7 @@ inline Front front(const chd_symbolic* s, int k) {
 }
 
 void assemble_children(const chd_symbolic* s, const Ctx& st, int batch, int k, double* ws, int64_t sws) {
-  if (s->ch_ptr[k + 1] == s->ch_ptr[k]) return;
+  if (s->ea_ptr[k + 1] == s->ea_ptr[k]) return;
   const int J = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k]);
   const int t = (J + GT - 1) / GT;
   mk_extend_add<<<dim3(t * t, 1, batch), BT, 0, st>>>(s->dev, k, ws, sws, t);
@@ -826,6 +826,323 @@ void complete_front(const chd_symbolic* s, const Ctx& st, int k, const double* S
   chd_launch::count_launch();
 }
 
+// ---------------------------------------------------------------------------
+// Leaf groups: L consecutive one-column leaves c_0 .. c_{L-1} of one parent
+// with the same ancestor set A (a = |A|, J = a + 1).  Their value columns are
+// consecutive in the CSC (J entries each), so the A-parts of X, Y, S, T, the
+// factor blocks and the outputs are a x L blocks with leading dimension J.
+// With n = 1 the per-front formulas reduce to scalar and a-vector operations
+// per leaf (one warp per leaf) and, across the group, to products with the
+// a x L blocks: the update block the parent adds is their sum, and the
+// products with V, V' or V^{-1} (the same for every member) cover all leaves.
+// Scratch: the members' own workspace fronts, beyond the first member's.
+// ---------------------------------------------------------------------------
+struct Group {
+  int c0, L, a, J, Jp;
+  int64_t col0, base0, f0, f1, fp, d0, v0;
+  const int32_t* rel;  // device: positions of A in J_parent
+  const int32_t* rows; // device: A (global rows)
+};
+Group group(const chd_symbolic* s, int g) {
+  Group G;
+  G.c0 = (int)s->grp_first[g];
+  G.L = (int)s->grp_count[g];
+  G.J = (int)(s->rows_ptr[G.c0 + 1] - s->rows_ptr[G.c0]);
+  G.a = G.J - 1;
+  const int64_t p = s->sn_par[G.c0];
+  G.Jp = (int)(s->rows_ptr[p + 1] - s->rows_ptr[p]);
+  G.col0 = s->sn_ptr[G.c0];
+  G.base0 = s->colptr[G.col0];
+  G.f0 = s->f_off[G.c0];
+  G.f1 = s->f_off[G.c0 + 1];
+  G.fp = s->f_off[p];
+  G.d0 = s->d_off[G.c0];
+  G.v0 = s->v_off[G.c0];
+  G.rel = s->dev.rel + s->rows_ptr[G.c0] + 1;
+  G.rows = s->dev.rows + s->rows_ptr[G.c0] + 1;
+  return G;
+}
+constexpr int GW = BT / 32;  // leaves (warps) per CTA
+inline dim3 leaf_grid(int L, int m) { return dim3((L + GW - 1) / GW, 1, m); }
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+#define LEAF_PROLOGUE                                          \
+  const int lane = threadIdx.x & 31;                           \
+  const int i = blockIdx.x * GW + (threadIdx.x >> 5);          \
+  if (i >= L) return;                                          \
+  const int64_t z = blockIdx.z;                                \
+  const int64_t b = base0 + (int64_t)i * J;
+
+// Algorithm 7.1 for one-column leaves: D = x_jj, L = x_Aj / D, and the
+// Cholesky form C = sqrt(D), B = x_Aj / C
+__global__ void __launch_bounds__(BT) mg_factor(const double* X, double* Lc, double* Wc, double* Dd, double* ldet,
+                                                int64_t base0, int J, int L, int c0, int64_t d0, int64_t col0,
+                                                int64_t* st) {
+  LEAF_PROLOGUE
+  (void)z;
+  double d = X[b];
+  if (!(d > 0.0)) {
+    if (lane == 0) record_error(st, CHD_ERR_NOT_PD, c0 + i, col0 + i);
+    d = 1.0;
+  }
+  const double r = rsqrt(d), r2 = r * r;
+  for (int q = 1 + lane; q < J; q += 32) {
+    const double x = X[b + q];
+    Lc[b + q] = x * r;
+    Wc[b + q] = x * r2;
+  }
+  if (lane == 0) {
+    Lc[b] = d * r;
+    Wc[b] = r2;
+    Dd[d0 + 4 * (int64_t)i] = d;
+    ldet[c0 + i] = log(d);
+  }
+}
+// V (a x a, lower) <- parent's front at the relative positions, per RHS z
+__global__ void __launch_bounds__(BT) mg_gather_v(const double* ws, int64_t sws, int64_t fp, int Jp,
+                                                  const int32_t* rel, int a, double* V, int64_t sV) {
+  ws += blockIdx.z * sws;
+  V += blockIdx.z * sV;
+  const double* Fp = ws + fp;
+  const int64_t tot = (int64_t)a * a;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % a), c = (int)(e / a);
+    if (r >= c) V[r + (int64_t)c * a] = __ldcg(Fp + __ldg(rel + r) + (int64_t)__ldg(rel + c) * Jp);
+  }
+}
+// V = S_AA (a x a, lower) read from the input S (completion)
+__global__ void __launch_bounds__(BT) mg_gather_saa(SymDev S, const int32_t* A, int a, const double* Sin,
+                                                    double* V, double* R) {
+  const int64_t tot = (int64_t)a * a;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % a), c = (int)(e / a);
+    if (r >= c) {
+      const double v = Sin[csc_find(S, __ldg(A + r), __ldg(A + c))];
+      V[r + (int64_t)c * a] = v;
+      R[r + (int64_t)c * a] = v;
+    }
+  }
+}
+// Algorithm 7.2, after S_AN = -V L: S_NN = D^{-1} - S_AN^T L; g = -S
+__global__ void __launch_bounds__(BT) mg_grad_finish(double* Sc, double* g, const double* Wc, int64_t base0,
+                                                     int J, int L) {
+  LEAF_PROLOGUE
+  (void)z;
+  double t = 0.0;
+  for (int q = 1 + lane; q < J; q += 32) t = fma(Sc[b + q], Wc[b + q], t);
+  t = warp_sum(t);
+  if (lane == 0) Sc[b] = Wc[b] - t;
+  __syncwarp();
+  if (g)
+    for (int q = lane; q < J; q += 32) g[b + q] = -Sc[b + q];
+}
+// Hessian step 1 per leaf: K_AN = Y_AN - L Y_NN (into the a x L scratch K)
+__global__ void __launch_bounds__(BT) mg_hess_k(const double* Y, int64_t ldy, const double* Wc, double* K,
+                                                int64_t sK, int64_t base0, int J, int L) {
+  LEAF_PROLOGUE
+  const double* y = Y + z * ldy + b;
+  double* k = K + z * sK + (int64_t)i * (J - 1);
+  const double yn = y[0];
+  for (int q = 1 + lane; q < J; q += 32) k[q - 1] = fma(-Wc[b + q], yn, y[q]);
+}
+// Hessian step 2 per leaf: M_NN = D^{-1} K_NN D^{-1} -> T; K_AN D^{-1} in place
+__global__ void __launch_bounds__(BT) mg_hess_m(const double* Y, int64_t ldy, double* T, int64_t ldt,
+                                                const double* Wc, double* K, int64_t sK, int64_t base0, int J,
+                                                int L) {
+  LEAF_PROLOGUE
+  const double dinv = Wc[b];
+  double* k = K + z * sK + (int64_t)i * (J - 1);
+  if (lane == 0) T[z * ldt + b] = dinv * dinv * Y[z * ldy + b];
+  for (int q = 1 + lane; q < J; q += 32) k[q - 1] *= dinv;
+}
+// Hessian step 3 per leaf, after W = V' L: T_NN = M_NN - 2 M_AN^T L + W^T L,
+// T_AN = M_AN - W
+__global__ void __launch_bounds__(BT) mg_hess_down(double* T, int64_t ldt, const double* Wc, const double* W,
+                                                   int64_t sW, int64_t base0, int J, int L) {
+  LEAF_PROLOGUE
+  double* t = T + z * ldt + b;
+  const double* w = W + z * sW + (int64_t)i * (J - 1);
+  double s1 = 0.0, s2 = 0.0;
+  for (int q = 1 + lane; q < J; q += 32) {
+    s1 = fma(t[q], Wc[b + q], s1);
+    s2 = fma(w[q - 1], Wc[b + q], s2);
+  }
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  for (int q = 1 + lane; q < J; q += 32) t[q] -= w[q - 1];
+  if (lane == 0) t[0] = t[0] - 2.0 * s1 + s2;
+}
+// Inverse-Hessian steps 1-2 per leaf, after W = V' L: M_AN = T_AN + W,
+// M_NN = T_NN + T_AN^T L + L^T M_AN, K_NN = D M_NN D -> Y, M_AN D in place of W
+__global__ void __launch_bounds__(BT) mg_ihess_down(const double* Tin, int64_t ldt, double* Y, int64_t ldy,
+                                                    const double* Wc, const double* Dd, int64_t d0, double* W,
+                                                    int64_t sW, int64_t base0, int J, int L) {
+  LEAF_PROLOGUE
+  const double* t = Tin + z * ldt + b;
+  double* w = W + z * sW + (int64_t)i * (J - 1);
+  double s1 = 0.0, s2 = 0.0;
+  for (int q = 1 + lane; q < J; q += 32) {
+    const double l = Wc[b + q], tq = t[q];
+    s1 = fma(tq, l, s1);
+    s2 = fma(tq + w[q - 1], l, s2);
+  }
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  const double d = Dd[d0 + 4 * (int64_t)i];
+  for (int q = 1 + lane; q < J; q += 32) w[q - 1] = (t[q] + w[q - 1]) * d;
+  if (lane == 0) Y[z * ldy + b] = d * d * (t[0] + s1 + s2);
+}
+// Inverse-Hessian step 3 per leaf (no children): P = K_AN + 1/2 L K_NN into
+// the scratch, Y_AN = K_AN + L K_NN (Y_NN = K_NN stays)
+__global__ void __launch_bounds__(BT) mg_ihess_up(double* Y, int64_t ldy, const double* Wc, double* P, int64_t sP,
+                                                  int64_t base0, int J, int L) {
+  LEAF_PROLOGUE
+  double* y = Y + z * ldy + b;
+  double* pp = P + z * sP + (int64_t)i * (J - 1);
+  const double kn = y[0];
+  for (int q = 1 + lane; q < J; q += 32) {
+    const double l = Wc[b + q], ka = y[q];
+    pp[q - 1] = fma(0.5 * l, kn, ka);
+    y[q] = fma(l, kn, ka);
+  }
+}
+// Algorithm 7.3 per leaf, after Z = R^{-1} S_AN (scratch): P = S_NN - Z^T Z
+// (kept in Wc's diagonal entry), scratch <- -Z
+__global__ void __launch_bounds__(BT) mg_comp_mid(const double* Sin, double* Wc, double* Z, int64_t base0, int J,
+                                                  int L) {
+  LEAF_PROLOGUE
+  (void)z;
+  double* zz = Z + (int64_t)i * (J - 1);
+  double t = 0.0;
+  for (int q = lane; q < J - 1; q += 32) t = fma(zz[q], zz[q], t);
+  t = warp_sum(t);
+  for (int q = lane; q < J - 1; q += 32) zz[q] = -zz[q];
+  if (lane == 0) Wc[b] = Sin[b] - t;
+}
+// Algorithm 7.3 per leaf, after L_AN = -R^{-T} Z (scratch): D = P^{-1},
+// C = sqrt(D), factor blocks and log det
+__global__ void __launch_bounds__(BT) mg_comp_finish(double* Lc, double* Wc, double* Dd, double* ldet,
+                                                     const double* Z, int64_t base0, int J, int L, int c0,
+                                                     int64_t d0, int64_t col0, int64_t* st) {
+  LEAF_PROLOGUE
+  (void)z;
+  double P = Wc[b];
+  if (!(P > 0.0)) {
+    if (lane == 0) record_error(st, CHD_ERR_NOT_COMPLETABLE, c0 + i, col0 + i);
+    P = 1.0;
+  }
+  const double D = 1.0 / P, C = sqrt(D);
+  const double* l = Z + (int64_t)i * (J - 1);
+  for (int q = 1 + lane; q < J; q += 32) {
+    Wc[b + q] = l[q - 1];
+    Lc[b + q] = l[q - 1] * C;
+  }
+  if (lane == 0) {
+    Lc[b] = C;
+    Dd[d0 + 4 * (int64_t)i] = D;
+    ldet[c0 + i] = 2.0 * log(C);
+  }
+}
+
+// per-group sequences
+void group_factor(const chd_symbolic* s, const Ctx& st, int g, const double* X, double* Lc, double* Wc, double* Dd,
+                  double* ws, double* ldet, int64_t* status) {
+  const Group G = group(s, g);
+  mg_factor<<<leaf_grid(G.L, 1), BT, 0, st>>>(X, Lc, Wc, Dd, ldet, G.base0, G.J, G.L, G.c0, G.d0, G.col0, status);
+  chd_launch::count_launch();
+  // update block the parent adds: -sum_i B_i B_i^T, in the first member's front
+  gemm(st, 1, G.a, G.a, G.L, -1.0, Dn{Lc + G.base0 + 1, G.J}, 0, DnT{Lc + G.base0 + 1, G.J}, 0, 0.0,
+       Dn{ws + G.f0 + 1 + G.J, G.J}, 0, true);
+}
+void group_gradient(const chd_symbolic* s, const Ctx& st, int g, const double* Wc, double* Sc, double* gr,
+                    double* Vd, double* ws) {
+  const Group G = group(s, g);
+  double* V = Vd + G.v0;
+  CHD_EW(mg_gather_v, (int64_t)G.a * G.a, 1, st, ws, 0, G.fp, G.Jp, G.rel, G.a, V, 0);
+  gemm(st, 1, G.a, G.L, G.a, -1.0, SymL{V, G.a}, 0, Dn{const_cast<double*>(Wc) + G.base0 + 1, G.J}, 0, 0.0,
+       Dn{Sc + G.base0 + 1, G.J}, 0, false);
+  mg_grad_finish<<<leaf_grid(G.L, 1), BT, 0, st>>>(Sc, gr, Wc, G.base0, G.J, G.L);
+  chd_launch::count_launch();
+}
+void group_hess_up(const chd_symbolic* s, const Ctx& st, int m, int g, const double* Wc, const double* Vd,
+                   const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
+  const Group G = group(s, g);
+  const int64_t sw = s->dev.f_total;
+  double* K = ws + G.f1;
+  const Dn Lb{const_cast<double*>(Wc) + G.base0 + 1, G.J};
+  mg_hess_k<<<leaf_grid(G.L, m), BT, 0, st>>>(Y, ldy, Wc, K, sw, G.base0, G.J, G.L);
+  chd_launch::count_launch();
+  // U' = -(K_AN L^T + L Y_AN^T), summed over the group
+  Dn U{ws + G.f0 + 1 + G.J, G.J};
+  gemm(st, m, G.a, G.a, G.L, -1.0, Dn{K, G.a}, sw, DnT{Lb.p, G.J}, 0, 0.0, U, sw, true);
+  gemm(st, m, G.a, G.a, G.L, -1.0, Lb, 0, DnT{const_cast<double*>(Y) + G.base0 + 1, G.J}, ldy, 1.0, U, sw, true);
+  mg_hess_m<<<leaf_grid(G.L, m), BT, 0, st>>>(Y, ldy, T, ldt, Wc, K, sw, G.base0, G.J, G.L);
+  chd_launch::count_launch();
+  // M_AN = V (K_AN D^{-1})
+  gemm(st, m, G.a, G.L, G.a, 1.0, SymL{const_cast<double*>(Vd) + G.v0, G.a}, 0, Dn{K, G.a}, sw, 0.0,
+       Dn{T + G.base0 + 1, G.J}, ldt, false);
+}
+void group_hess_down(const chd_symbolic* s, const Ctx& st, int m, int g, const double* Wc, double* T, int64_t ldt,
+                     double* ws) {
+  const Group G = group(s, g);
+  const int64_t sw = s->dev.f_total;
+  double* Vs = ws + G.f1;
+  double* W = Vs + (int64_t)G.a * G.a;
+  CHD_EW(mg_gather_v, (int64_t)G.a * G.a, m, st, ws, sw, G.fp, G.Jp, G.rel, G.a, Vs, sw);
+  gemm(st, m, G.a, G.L, G.a, 1.0, SymL{Vs, G.a}, sw, Dn{const_cast<double*>(Wc) + G.base0 + 1, G.J}, 0, 0.0,
+       Dn{W, G.a}, sw, false);
+  mg_hess_down<<<leaf_grid(G.L, m), BT, 0, st>>>(T, ldt, Wc, W, sw, G.base0, G.J, G.L);
+  chd_launch::count_launch();
+}
+void group_ihess_down(const chd_symbolic* s, const Ctx& st, int m, int g, const double* Wc, const double* Dd,
+                      const double* Rd, const double* Tin, int64_t ldt, double* Y, int64_t ldy, double* ws) {
+  const Group G = group(s, g);
+  const int64_t sw = s->dev.f_total;
+  double* Vs = ws + G.f1;
+  double* W = Vs + (int64_t)G.a * G.a;
+  CHD_EW(mg_gather_v, (int64_t)G.a * G.a, m, st, ws, sw, G.fp, G.Jp, G.rel, G.a, Vs, sw);
+  gemm(st, m, G.a, G.L, G.a, 1.0, SymL{Vs, G.a}, sw, Dn{const_cast<double*>(Wc) + G.base0 + 1, G.J}, 0, 0.0,
+       Dn{W, G.a}, sw, false);
+  mg_ihess_down<<<leaf_grid(G.L, m), BT, 0, st>>>(Tin, ldt, Y, ldy, Wc, Dd, G.d0, W, sw, G.base0, G.J, G.L);
+  chd_launch::count_launch();
+  // K_AN = V^{-1} (M_AN D), V^{-1} of the group in its first member's slot
+  gemm(st, m, G.a, G.L, G.a, 1.0, SymL{const_cast<double*>(Rd) + G.v0, G.a}, 0, Dn{W, G.a}, sw, 0.0,
+       Dn{Y + G.base0 + 1, G.J}, ldy, false);
+}
+void group_ihess_up(const chd_symbolic* s, const Ctx& st, int m, int g, const double* Wc, double* Y, int64_t ldy,
+                    double* ws) {
+  const Group G = group(s, g);
+  const int64_t sw = s->dev.f_total;
+  double* P = ws + G.f1;
+  mg_ihess_up<<<leaf_grid(G.L, m), BT, 0, st>>>(Y, ldy, Wc, P, sw, G.base0, G.J, G.L);
+  chd_launch::count_launch();
+  // U' = -(P L^T + L P^T), summed over the group
+  const Dn Lb{const_cast<double*>(Wc) + G.base0 + 1, G.J};
+  Dn U{ws + G.f0 + 1 + G.J, G.J};
+  gemm(st, m, G.a, G.a, G.L, -1.0, Dn{P, G.a}, sw, DnT{Lb.p, G.J}, 0, 0.0, U, sw, true);
+  gemm(st, m, G.a, G.a, G.L, -1.0, Lb, 0, DnT{P, G.a}, sw, 1.0, U, sw, true);
+}
+void group_complete(const chd_symbolic* s, const Ctx& st, int g, const double* Sin, double* Lc, double* Wc,
+                    double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
+  const Group G = group(s, g);
+  double* V = Vd + G.v0;
+  double* R = Rd + G.v0;
+  double* Z = ws + G.f1;
+  CHD_EW(mg_gather_saa, (int64_t)G.a * G.a, 1, st, s->dev, G.rows, G.a, Sin, V, R);
+  potrf_partial(st, R, G.a, G.a, G.a, status, CHD_ERR_NOT_COMPLETABLE, G.c0, -1);
+  // Z = R^{-1} S_AN for all leaves, then P per leaf, then L_AN = -R^{-T} Z
+  CHD_EW(mk_copy, (int64_t)G.a * G.L, 1, st, Z, 0, G.a, Sin + G.base0 + 1, 0, G.J, G.a, G.L, 1.0, 0.0, 0, 0);
+  trsm_rLT(st, 1, G.L, G.a, DnTW{Z, G.a}, 0, R, G.a);
+  mg_comp_mid<<<leaf_grid(G.L, 1), BT, 0, st>>>(Sin, Wc, Z, G.base0, G.J, G.L);
+  chd_launch::count_launch();
+  trsm_rL(st, 1, G.L, G.a, DnTW{Z, G.a}, 0, R, G.a);
+  mg_comp_finish<<<leaf_grid(G.L, 1), BT, 0, st>>>(Lc, Wc, Dd, ldet, Z, G.base0, G.J, G.L, G.c0, G.d0, G.col0,
+                                                   status);
+  chd_launch::count_launch();
+}
+
 }  // namespace big
 }  // namespace chd
 
@@ -833,35 +1150,43 @@ namespace chd_launch {
 using chd::big::Ctx;
 void big_factor(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* X,
                 double* Lc, double* Wc, double* Dd, double* ws, double* ldet, int64_t* status) {
+  if (s->grp_of[k] >= 0) return chd::big::group_factor(s, chd::big::make_ctx(st, xs, xcap), s->grp_of[k], X, Lc, Wc, Dd, ws, ldet, status);
   chd::big::factor_front(s, chd::big::make_ctx(st, xs, xcap), k, X, Lc, Wc, Dd, ws, ldet, status);
 }
 void big_gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Wc,
                   double* Sc, double* g, double* Vd, double* ws) {
+  if (s->grp_of[k] >= 0) return chd::big::group_gradient(s, chd::big::make_ctx(st, xs, xcap), s->grp_of[k], Wc, Sc, g, Vd, ws);
   chd::big::gradient_front(s, chd::big::make_ctx(st, xs, xcap), k, Wc, Sc, g, Vd, ws);
 }
 void big_hess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
                  const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
+  if (s->grp_of[k] >= 0) return chd::big::group_hess_up(s, chd::big::make_ctx(st, xs, xcap), m, s->grp_of[k], Wc, Vd, Y, ldy, T, ldt, ws);
   chd::big::hess_up_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, Vd, Y, ldy, T, ldt, ws);
 }
 void big_hess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
                    double* T, int64_t ldt, double* ws) {
+  if (s->grp_of[k] >= 0) return chd::big::group_hess_down(s, chd::big::make_ctx(st, xs, xcap), m, s->grp_of[k], Wc, T, ldt, ws);
   chd::big::hess_down_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, T, ldt, ws);
 }
 void big_ihess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k,
                     const double* Wc, const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y,
                     int64_t ldy, double* ws) {
+  if (s->grp_of[k] >= 0) return chd::big::group_ihess_down(s, chd::big::make_ctx(st, xs, xcap), m, s->grp_of[k], Wc, Dd, Rd, T, ldt, Y, ldy, ws);
   chd::big::ihess_down_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
 }
 void big_ihess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
                   double* Y, int64_t ldy, double* ws) {
+  if (s->grp_of[k] >= 0) return chd::big::group_ihess_up(s, chd::big::make_ctx(st, xs, xcap), m, s->grp_of[k], Wc, Y, ldy, ws);
   chd::big::ihess_up_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, Y, ldy, ws);
 }
 void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Sin,
                   double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
                   int64_t* status) {
+  if (s->grp_of[k] >= 0) return chd::big::group_complete(s, chd::big::make_ctx(st, xs, xcap), s->grp_of[k], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
   chd::big::complete_front(s, chd::big::make_ctx(st, xs, xcap), k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
 }
 void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* ws) {
+  if (s->grp_of[k] >= 0) return;  // a leaf group reads S itself
   chd::big::complete_load_front(s, chd::big::make_ctx(st, nullptr, 0), k, Sin, ws);
 }
 // Cholesky factor R of the cached V_k = S_{A_k A_k} of one big front (lower,

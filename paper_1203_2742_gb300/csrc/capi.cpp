@@ -692,6 +692,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   size_t iRel = add(s->rel.data(), s->rel.size() * 4);
   size_t iCp = add(s->ch_ptr.data(), s->ch_ptr.size() * 8);
   size_t iCh = add(s->ch.data(), s->ch.size() * 4);
+  size_t iEp = add(s->ea_ptr.data(), s->ea_ptr.size() * 8);
+  size_t iEa = add(s->ea.data(), s->ea.size() * 4);
   size_t iF = add(s->f_off.data(), s->f_off.size() * 8);
   size_t iD = add(s->d_off.data(), s->d_off.size() * 8);
   size_t iV = add(s->v_off.data(), s->v_off.size() * 8);
@@ -745,6 +747,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   d.rel = reinterpret_cast<const int32_t*>(b + pcs[iRel].off);
   d.ch_ptr = reinterpret_cast<const int64_t*>(b + pcs[iCp].off);
   d.ch = reinterpret_cast<const int32_t*>(b + pcs[iCh].off);
+  d.ea_ptr = reinterpret_cast<const int64_t*>(b + pcs[iEp].off);
+  d.ea = reinterpret_cast<const int32_t*>(b + pcs[iEa].off);
   d.f_off = reinterpret_cast<const int64_t*>(b + pcs[iF].off);
   d.d_off = reinterpret_cast<const int64_t*>(b + pcs[iD].off);
   d.v_off = reinterpret_cast<const int64_t*>(b + pcs[iV].off);

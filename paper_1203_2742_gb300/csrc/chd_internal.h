@@ -40,6 +40,8 @@ struct SymDev {
   const int32_t* rows = nullptr;     // J_k (N_k then A_k, increasing), at rows_ptr[k]
   const int64_t* ch_ptr = nullptr;   // nsn+1: children of k in ch[ch_ptr[k]..)
   const int32_t* ch = nullptr;
+  const int64_t* ea_ptr = nullptr;   // nsn+1: children whose update blocks k adds (a leaf
+  const int32_t* ea = nullptr;       //   group contributes through its first member only)
   const int64_t* f_off = nullptr;    // nsn+1: per-front workspace offsets (doubles)
   const int64_t* d_off = nullptr;    // nsn+1: per-front n_k*n_k block offsets
   const int64_t* v_off = nullptr;    // nsn+1: per-front a_k*a_k block offsets
@@ -72,6 +74,12 @@ struct chd_symbolic {
   std::vector<int32_t> rel;        // aligned with rows; -1 on the N part
   std::vector<int64_t> ch_ptr;
   std::vector<int32_t> ch;
+  std::vector<int64_t> ea_ptr;  // children for the extend-add (see SymDev)
+  std::vector<int32_t> ea;
+  // leaf groups: supernodes [grp_first[g], grp_first[g] + grp_count[g]) are
+  // one-column leaves of one parent with the same A; grp_of[k] = g or -1
+  std::vector<int64_t> grp_first, grp_count;
+  std::vector<int32_t> grp_of;
   std::vector<int64_t> f_off, d_off, v_off;
   // schedule: tasks are front sequences processed by one CTA; launches
   // group tasks by level (bottom-up order); lvl_ptr indexes tasks.
@@ -84,7 +92,7 @@ struct chd_symbolic {
   // the next lvl_w64[l] wide warp-tier tasks (|J| <= 64)
   std::vector<int32_t> lvl_warp, lvl_w64;
   std::vector<char> is_big;  // per supernode
-  std::vector<int32_t> tier;  // per supernode: 0 warp, 3 wide warp, 1 CTA, 2 dense
+  std::vector<int32_t> tier;  // per supernode: 0 warp, 3 wide warp, 1 CTA, 2 dense, 4 leaf group
   std::vector<int32_t> small_fronts;
   std::vector<int32_t> cta_fronts;
   std::vector<int32_t> warp_fronts;

@@ -350,8 +350,8 @@ __device__ FrontInfo front_info(const SymDev& S, int k, double* ws) {
 // front) into this front: F += E_{J A_c} U_c E_{J A_c}^T  (children in a
 // fixed order, entries of one child touch distinct positions).
 __device__ void extend_add_children(const SymDev& S, const FrontInfo& f, double* ws, double sign) {
-  for (int64_t q = S.ch_ptr[f.k]; q < S.ch_ptr[f.k + 1]; ++q) {
-    const int c = S.ch[q];
+  for (int64_t q = S.ea_ptr[f.k]; q < S.ea_ptr[f.k + 1]; ++q) {
+    const int c = S.ea[q];
     const int nc = (int)(S.sn_ptr[c + 1] - S.sn_ptr[c]);
     const int Jc = (int)(S.rows_ptr[c + 1] - S.rows_ptr[c]);
     const int ac = Jc - nc;
@@ -1020,7 +1020,8 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
 void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* ws);
 void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Sin, double* Lc, double* Wc,
               double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
-  const std::vector<int32_t>& bigs = s->big_fronts;
+  std::vector<int32_t> bigs = s->big_fronts;  // dense fronts and leaf groups
+  for (int64_t g0 : s->grp_first) bigs.push_back((int32_t)g0);
   BigFork bf{ex, st};
   bf.run((int)bigs.size(), [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
     big_complete_load(s, bs, bigs[i], Sin, ws);

@@ -453,6 +453,58 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     }
   }
 
+  // ---- leaf groups -----------------------------------------------------------
+  // A run of at least kMinLeafGroup consecutive supernodes that are leaves
+  // with one column each, below the dense-tier size, sharing their parent and
+  // their ancestor set A (the border of a block-arrow pattern, for instance)
+  // forms a group.  With n_k = 1 the per-front formulas of Algorithms 7.1-7.3
+  // and of the Hessian recursions become, over the whole group, products of
+  // the a x L block of the leaves' columns (L leaves), and the update blocks
+  // the parent adds are one sum over the group, computed as such products.
+  {
+    constexpr int64_t kMinLeafGroup = 16;
+    const int64_t big_rows = opts.big_rows > 0 ? opts.big_rows : 320;
+    s->grp_first.clear();
+    s->grp_count.clear();
+    s->grp_of.assign(nsn, -1);
+    auto leaf1 = [&](int64_t t) {
+      const int64_t J = s->rows_ptr[t + 1] - s->rows_ptr[t];
+      return s->ch_ptr[t + 1] == s->ch_ptr[t] && s->sn_ptr[t + 1] - s->sn_ptr[t] == 1 && s->sn_par[t] >= 0 &&
+             J > 1 && J < big_rows;
+    };
+    auto sameA = [&](int64_t t, int64_t u) {
+      const int64_t Jt = s->rows_ptr[t + 1] - s->rows_ptr[t];
+      if (s->rows_ptr[u + 1] - s->rows_ptr[u] != Jt) return false;
+      for (int64_t q = 1; q < Jt; ++q)
+        if (s->rows[s->rows_ptr[t] + q] != s->rows[s->rows_ptr[u] + q]) return false;
+      return true;
+    };
+    for (int64_t t = 0; t < nsn;) {
+      if (!leaf1(t)) {
+        ++t;
+        continue;
+      }
+      int64_t u = t + 1;
+      while (u < nsn && leaf1(u) && s->sn_par[u] == s->sn_par[t] && sameA(t, u)) ++u;
+      if (u - t >= kMinLeafGroup) {
+        for (int64_t k = t; k < u; ++k) s->grp_of[k] = (int32_t)s->grp_first.size();
+        s->grp_first.push_back(t);
+        s->grp_count.push_back(u - t);
+      }
+      t = u;
+    }
+    s->ea_ptr.assign(nsn + 1, 0);
+    s->ea.clear();
+    for (int64_t p = 0; p < nsn; ++p) {
+      for (int64_t q = s->ch_ptr[p]; q < s->ch_ptr[p + 1]; ++q) {
+        const int32_t c = s->ch[q];
+        if (s->grp_of[c] >= 0 && s->grp_first[s->grp_of[c]] != c) continue;
+        s->ea.push_back(c);
+      }
+      s->ea_ptr[p + 1] = (int64_t)s->ea.size();
+    }
+  }
+
   // ---- CSC of the filled pattern V (column j of N_k: rows J_k[c:]) -------
   s->colptr.assign(n + 1, 0);
   for (int64_t t = 0; t < nsn; ++t) {
@@ -484,7 +536,9 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     fsz = (fsz + 3) & ~int64_t(3);
     s->f_off[t + 1] = s->f_off[t] + fsz;
     s->d_off[t + 1] = s->d_off[t] + ((nn * nn + 3) & ~int64_t(3));
-    s->v_off[t + 1] = s->v_off[t] + ((a * a + 3) & ~int64_t(3));
+    // a leaf group keeps one V (its members share A) in its first member's slot
+    const bool v_shared = s->grp_of[t] >= 0 && s->grp_first[s->grp_of[t]] != t;
+    s->v_off[t + 1] = s->v_off[t] + (v_shared ? 0 : ((a * a + 3) & ~int64_t(3)));
     double dn = (double)nn, da = (double)a;
     s->flops[0] += dn * dn * dn / 3 + da * dn * dn + da * da * dn;
     s->flops[1] += 2 * da * da * dn + da * dn * dn + 2 * dn * dn * dn / 3;
@@ -514,6 +568,10 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
       int64_t J = s->rows_ptr[t + 1] - s->rows_ptr[t];
       s->is_big[t] = (J >= big_rows || nn >= big_cols) ? 1 : 0;
       tier[t] = s->is_big[t] ? 2 : (nn <= 8 && J <= 32) ? 0 : (nn <= 8 && J <= 64) ? 3 : 1;
+      if (s->grp_of[t] >= 0) {
+        tier[t] = 4;
+        s->is_big[t] = 0;
+      }
     }
     // The wide warp tier runs one warp per CTA (its fronts take most of the
     // shared memory), which pays off for chains, where one front waits for
@@ -537,7 +595,9 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     s->warp_fronts.clear();
     s->big_fronts.clear();
     for (int64_t t = 0; t < nsn; ++t) {
-      if (!s->is_big[t]) s->small_fronts.push_back((int32_t)t);
+      // V^{-1} per front (a group's members share their first member's)
+      const bool member = s->grp_of[t] >= 0 && s->grp_first[s->grp_of[t]] != t;
+      if (!s->is_big[t] && !member) s->small_fronts.push_back((int32_t)t);
       if (tier[t] == 0) s->warp_fronts.push_back((int32_t)t);
       if (tier[t] == 1 || tier[t] == 3) s->cta_fronts.push_back((int32_t)t);
       if (tier[t] == 2) s->big_fronts.push_back((int32_t)t);
@@ -581,6 +641,18 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
       if (top[t] && s->sn_par[t] >= 0) { ntopkids[s->sn_par[t]]++; onlykid[s->sn_par[t]] = t; }
     for (int64_t t = 0; t < nsn; ++t) {
       if (!top[t]) continue;
+      if (tier[t] == 4) {  // leaf group: one task, run with the dense fronts
+        const int64_t g0 = s->grp_first[s->grp_of[t]];
+        if (g0 == t) {
+          task_of[t] = (int64_t)tasks.size();
+          tasks.push_back({(int32_t)t});
+          tlevel.push_back(1);
+          ttier.push_back(2);
+        } else {
+          task_of[t] = task_of[g0];
+        }
+        continue;
+      }
       if (ntopkids[t] == 1 && tier[t] != 2 && tier[onlykid[t]] == tier[t]) {
         int64_t tk = task_of[onlykid[t]];
         tasks[tk].push_back((int32_t)t);
@@ -643,8 +715,8 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
         w.k = (int32_t)k;
         w.n = (int32_t)(s->sn_ptr[k + 1] - s->sn_ptr[k]);
         w.J = (int32_t)(s->rows_ptr[k + 1] - s->rows_ptr[k]);
-        w.ch_beg = (int32_t)s->ch_ptr[k];
-        w.ch_end = (int32_t)s->ch_ptr[k + 1];
+        w.ch_beg = (int32_t)s->ea_ptr[k];
+        w.ch_end = (int32_t)s->ea_ptr[k + 1];
         w.flags = 0;
         if (q > q0 && s->sn_par[s->task_fronts[q - 1]] == k) {
           w.flags |= WM_PREV_CHILD;

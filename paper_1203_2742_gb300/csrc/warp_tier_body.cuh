@@ -171,7 +171,7 @@ __device__ void extend_add(const SymDev& S, const Fr& f, const Fr& prev, const S
     return;
   }
   for (int q = f.ch_beg; q < f.ch_end; ++q) {
-    const int c = S.ch[q];
+    const int c = S.ea[q];
     if (chain && c == prev.k) {
       const int ac = prev.a, nc = prev.n, Jc = prev.J;
       for (int e = lane; e < ac * ac; e += TPF) {
