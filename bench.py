@@ -260,11 +260,13 @@ def make_symbolic(B, wl, **cfg):
 
 
 def tuned_config(B, wl):
-    """Tier cutovers of a batch chosen by the autotuner on every 8th instance."""
+    """Tier cutovers chosen by the autotuner (Hessian with the workload's m):
+    on every 8th instance of a batch, else on the pattern itself."""
     from paper_1203_2742_gb300 import autotune
-    subset = list(range(0, len(wl["batch"]), 8))
-    best, timings = autotune.tune(lambda **c: make_symbolic(B, wl, subset=subset, **c), wl["m"], reps=1)
-    return best, timings
+    if "batch" in wl:
+        subset = list(range(0, len(wl["batch"]), 8))
+        return autotune.tune(lambda **c: make_symbolic(B, wl, subset=subset, **c), wl["m"], reps=1)
+    return autotune.tune(lambda **c: make_symbolic(B, wl, **c), wl["m"], reps=2)
 
 
 def analysed_pattern_host(wl):
@@ -297,9 +299,10 @@ def run_ours(args, wl, rank, world, local_rank):
 
     tune = None
     cfg = {}
-    if "batch" in wl:
+    if not args.no_tune:
         cfg, timings = tuned_config(B, wl)
-        tune = {"chosen": cfg, "timings_ms": timings, "on": "every 8th instance, Hessian with the same m"}
+        tune = {"chosen": cfg, "timings_ms": timings,
+                "on": ("every 8th instance" if "batch" in wl else "the pattern") + ", Hessian with the same m"}
     t0 = time.perf_counter()
     sym = make_symbolic(B, wl, **cfg)
     analyze_ms = (time.perf_counter() - t0) * 1e3
@@ -554,6 +557,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="er5000", choices=["er5000", "band200", "grid150", "batch256", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="library default tier cutovers instead of the autotuner's")
     ap.add_argument("--serve-seconds", type=float, default=0.5, help="trace length of the serve workload")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -22,8 +22,10 @@ import numpy as np
 from . import binding as B
 
 DEFAULT_CANDIDATES = (
-    dict(big_rows=192, big_cols=96, split_cols=256),
     dict(big_rows=320, big_cols=160, split_cols=256),
+    dict(big_rows=96, big_cols=48, split_cols=256),
+    dict(big_rows=128, big_cols=64, split_cols=256),
+    dict(big_rows=192, big_cols=96, split_cols=256),
     dict(big_rows=512, big_cols=256, split_cols=256),
     dict(big_rows=320, big_cols=160, split_cols=128),
     dict(big_rows=320, big_cols=160, split_cols=512),

@@ -37,11 +37,11 @@ void count_launch();
 #undef WT_TPF
 
 // chains of fronts with 32 < |J| <= 64 (bands of half-bandwidth up to 63):
-// four warps (one CTA) per front, which shortens the serial chain
+// eight warps (one CTA) per front, which shortens the serial chain
 #define WT_NS w64
 #define WT_J 64
 #define WT_WPB 1
-#define WT_TPF 128
+#define WT_TPF 256
 #include "warp_tier_body.cuh"
 #undef WT_NS
 #undef WT_J

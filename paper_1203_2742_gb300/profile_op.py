@@ -39,22 +39,23 @@ DEFAULT_M = {"band200": 1, "er5000": 8, "grid150": 64, "dense1500": 8, "grid3d40
              "band20k_w61": 4}
 
 
-def symbolic_for(name):
+def symbolic_for(name, **tiers):
     if name == "band200":
-        return B.Symbolic(*W.band(200, 8))
+        return B.Symbolic(*W.band(200, 8), **tiers)
     if name == "er5000":
-        return B.Symbolic(*W.erdos_renyi(5000, 0.001, np.random.default_rng(1)), ordering="mindeg", relax=16)
+        return B.Symbolic(*W.erdos_renyi(5000, 0.001, np.random.default_rng(1)), ordering="mindeg", relax=16,
+                          **tiers)
     if name == "grid150":
-        return B.Symbolic(*W.grid2d(150, 150), perm=W.nested_dissection((150, 150), leaf=8))
+        return B.Symbolic(*W.grid2d(150, 150), perm=W.nested_dissection((150, 150), leaf=8), **tiers)
     if name == "dense1500":
-        return B.Symbolic(*W.band(1500, 1499))
+        return B.Symbolic(*W.band(1500, 1499), **tiers)
     if name == "grid3d40":
-        return B.Symbolic(*W.grid3d(40, 40, 40), perm=W.nested_dissection((40, 40, 40), leaf=8))
+        return B.Symbolic(*W.grid3d(40, 40, 40), perm=W.nested_dissection((40, 40, 40), leaf=8), **tiers)
     if name == "band20k_w61":
-        return B.Symbolic(*W.band(20000, 61))
+        return B.Symbolic(*W.band(20000, 61), **tiers)
     if name == "batch256":
         inst = W.batch_mix(256, 3)
-        return B.SymbolicBatch([p for p, _, _ in inst], perms=[q for _, q, _ in inst])
+        return B.SymbolicBatch([p for p, _, _ in inst], perms=[q for _, q, _ in inst], **tiers)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -65,9 +66,11 @@ def main(argv=None):
     ap.add_argument("op", choices=("factor", "gradient", "hessian", "inv_hessian", "completion", "all"))
     ap.add_argument("--m", type=int, default=None)
     ap.add_argument("--no-graphs", action="store_true", help="launch every kernel directly (no CUDA graphs)")
+    ap.add_argument("--big-rows", type=int, default=0, help="dense-tier cutover |J| (0: library default)")
+    ap.add_argument("--big-cols", type=int, default=0, help="dense-tier cutover |N| (0: library default)")
     a = ap.parse_args(argv)
     m = a.m if a.m is not None else DEFAULT_M[a.workload]
-    sym = symbolic_for(a.workload)
+    sym = symbolic_for(a.workload, big_rows=a.big_rows, big_cols=a.big_cols)
     n, cp, ri = sym.n, sym.colptr, sym.rowind
     rng = np.random.default_rng(0)
 
