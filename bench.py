@@ -498,6 +498,33 @@ def run_ours(args, wl, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def serve_cpu_baseline(pool, trace, cores, budget_s=15.0):
+    """Dense oracle Hessian evaluations on the smallest patterns of the pool
+    (X^{-1} cached per pattern, as a server would), extrapolated by n^3 to the
+    trace's Hessian requests."""
+    from oracle import dense as OD
+    order = sorted(range(len(pool)), key=lambda i: pool[i][0].n)
+    coef, spent, done = [], 0.0, 0
+    for i in order:
+        sym, x, _ = pool[i]
+        y = np.random.default_rng(i).uniform(-1.0, 1.0, size=sym.nnz)
+        Z = OD.inverse(sym.n, sym.colptr, sym.rowind, x)
+        t0 = time.perf_counter()
+        OD.hessian(sym.n, sym.colptr, sym.rowind, x, [y], Z=Z)
+        dt = time.perf_counter() - t0
+        spent += dt
+        done += 1
+        coef.append(dt / float(sym.n) ** 3)
+        if spent > budget_s or done >= 4:
+            break
+    c = float(np.median(coef))
+    evals = sum(r.m for r in trace if r.op == "hessian")
+    secs = sum(r.m * c * float(pool[r.pattern][0].n) ** 3 for r in trace if r.op == "hessian")
+    return {"value": evals / secs if secs > 0 else None, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"dense oracle P(X^-1 Y X^-1) on the {done} smallest of {len(pool)} patterns "
+                      f"(X^-1 cached per pattern), extrapolated by n^3 to the trace's {evals} Hessian evaluations"}
+
+
 def run_serve(args, wl):
     """Serving benchmark: the same bounded Poisson trace served with continuous
     batching on 8 streams and replayed one request at a time."""
@@ -533,6 +560,7 @@ def run_serve(args, wl):
               for r in trace]
     stats1, _ = serve.replay(one, trace2)
     h2d = sum(8 * r.m * pool[r.pattern][0].nnz for r in trace if r.op in ("hessian", "inv_hessian"))
+    cpu = None if args.no_cpu_baseline else serve_cpu_baseline(pool, trace, os.cpu_count() or 1)
     line = {
         "metric": METRIC, "value": stats["hessian_evals_per_s"], "unit": UNIT, "n_gpus": 1,
         "steps": 1, "warmup": args.warmup, "ms_per_step": stats["wall_s"] * 1e3, "higher_is_better": True,
@@ -543,7 +571,7 @@ def run_serve(args, wl):
         "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
         "e2e": {"value": stats["hessian_evals_per_s"], "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(h2d)},
-        "roofline": None, "cpu_baseline": None, "gpu_launches": int(launches), "clocks": clocks,
+        "roofline": None, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks,
         "analyze_s": analyze_s,
     }
     print(json.dumps(line), flush=True)
