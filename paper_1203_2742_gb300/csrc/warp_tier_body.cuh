@@ -305,8 +305,17 @@ __device__ void wgemm(int R, int N, int K, double alpha, FA A, FB B, double beta
     int r, c;
     divmod(e, R, r, c);
     if (lower && r < c) continue;
-    double acc = 0.0;
-    for (int k = 0; k < K; ++k) acc = fma(A(r, k), B(k, c), acc);
+    // four independent partial sums: the dependent FP64 chain is a quarter as long
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int k = 0;
+    for (; k + 3 < K; k += 4) {
+      a0 = fma(A(r, k), B(k, c), a0);
+      a1 = fma(A(r, k + 1), B(k + 1, c), a1);
+      a2 = fma(A(r, k + 2), B(k + 2, c), a2);
+      a3 = fma(A(r, k + 3), B(k + 3, c), a3);
+    }
+    for (; k < K; ++k) a0 = fma(A(r, k), B(k, c), a0);
+    const double acc = (a0 + a1) + (a2 + a3);
     double v = alpha * acc;
     if (beta != 0.0) v = fma(beta, C(r, c), v);
     C(r, c) = v;
@@ -376,6 +385,24 @@ __device__ void wtrsm_r(int R, int m, FB B, FL L, const double* rv, bool fwd, in
     }
   }
 }
+// out(r, c, sum_{t < K} term(t, r, c)) for the n x n outputs (lower only if
+// `lower`), one warp per output: the K terms are split over the lanes and
+// summed by shuffles, so a long K costs K/32 dependent steps, not K
+template <class Term, class Out>
+__device__ void wreduce_nn(int n, int K, bool lower, Term term, Out out, int lane) {
+  const int warp = lane >> 5, wl = lane & 31;
+  for (int o = warp; o < n * n; o += TPF / 32) {
+    int r, c;
+    divmod(o, n, r, c);
+    if (lower && r < c) continue;  // the same for the whole warp
+    double acc = 0.0;
+    for (int t = wl; t < K; t += 32) acc += term(t, r, c);
+    for (int x = 16; x > 0; x >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, x);
+    if (wl == 0) out(r, c, acc);
+  }
+  fsync();
+}
+
 // sum over i < n of 2 log(diag(i)) by the lanes, written by lane 0
 template <class FD>
 __device__ void wlogdet(int n, FD diag, double* out, int lane) {
@@ -455,6 +482,38 @@ __device__ void factor_front(const SymDev& S, const Fr& f, const Fr& prev, const
   const int k = f.k, J = f.J, n = f.n, a = f.a;
   load_up(S, f, prev, m, X, m.F, nullptr, false, lane);
   extend_add(S, f, prev, m, ws, lane);
+  if (n == 1) {
+    // one column (chains of bands, leaves): D = F_11, C = sqrt(D),
+    // B = F_21 / C, L_AN = F_21 / D, U = F_22 - F_21 F_21^T / D
+    double d = m.F[0];
+    if (!(d > 0.0)) {
+      if (lane == 0) record_error(st, CHD_ERR_NOT_PD, k, f.col0);
+      d = 1.0;
+    }
+    const double r = rsqrt(d), r2 = r * r;
+    for (int e = lane; e < a * a; e += TPF) {
+      int i, j;
+      divmod(e, a, i, j);
+      if (i >= j) m.F[pk(J, 1 + i, 1 + j)] -= m.F[1 + i] * m.F[1 + j] * r2;
+    }
+    double* Lo = Lc + f.base;
+    double* W = Wc + f.base;
+    for (int i = lane; i < a; i += TPF) {
+      const double x = m.F[1 + i];
+      Lo[1 + i] = x * r;
+      W[1 + i] = x * r2;
+    }
+    if (lane == 0) {
+      Lo[0] = d * r;
+      W[0] = r2;
+      Dd[f.d_off] = d;
+      ldet[k] = log(d);
+    }
+    fsync();
+    write_update(f, m, lane);
+    fsync();
+    return;
+  }
   double* D = Dd + f.d_off;
   for (int e = lane; e < n * n; e += TPF) {
     int r, c;
@@ -521,15 +580,9 @@ __device__ void gradient_front(const SymDev& S, const Fr& f, const Fr& prev, con
   // S_AN = -V L_AN
   wgemm(a, n, a, -1.0, PkSym{m.F, J, n}, Bk{m.A1, WJ}, 0.0, PkRect{m.F, J, n}, false, lane);
   // S_NN = D^{-1} - S_AN^T L_AN
-  for (int e = lane; e < n * n; e += TPF) {
-    int r, c;
-    divmod(e, n, r, c);
-    if (r < c) continue;
-    double acc = 0.0;
-    for (int t = 0; t < a; ++t) acc = fma(m.F[pk(J, n + t, r)], m.A1[t + c * WJ], acc);
-    m.F[pk(J, r, c)] = m.D1[r + c * WN] - acc;
-  }
-  fsync();
+  wreduce_nn(
+      n, a, true, [&](int t, int r, int c) { return m.F[pk(J, n + t, r)] * m.A1[t + c * WJ]; },
+      [&](int r, int c, double acc) { m.F[pk(J, r, c)] = m.D1[r + c * WN] - acc; }, lane);
   store_front(f, m, Sc, 1.0, lane);
   if (g) store_front(f, m, g, -1.0, lane);
   double* V = Vd + f.v_off;
@@ -598,18 +651,12 @@ __device__ void hess_down_front(const SymDev& S, const Fr& f, const Fr& prev, co
   }
   fsync();
   // T_NN = M_NN - (Q^T L + L^T Q)
-  for (int e = lane; e < n * n; e += TPF) {
-    int r, c;
-    divmod(e, n, r, c);
-    if (r < c) continue;
-    double acc = 0.0;
-    for (int t = 0; t < a; ++t) {
-      acc = fma(m.F[pk(J, n + t, r)], m.A1[t + c * WJ], acc);
-      acc = fma(m.A1[t + r * WJ], m.F[pk(J, n + t, c)], acc);
-    }
-    m.F[pk(J, r, c)] -= acc;
-  }
-  fsync();
+  wreduce_nn(
+      n, a, true,
+      [&](int t, int r, int c) {
+        return fma(m.F[pk(J, n + t, r)], m.A1[t + c * WJ], m.A1[t + r * WJ] * m.F[pk(J, n + t, c)]);
+      },
+      [&](int r, int c, double acc) { m.F[pk(J, r, c)] -= acc; }, lane);
   for (int e = lane; e < a * n; e += TPF) {
     int r, c;
     divmod(e, a, r, c);
@@ -633,28 +680,31 @@ __device__ void ihess_down_front(const SymDev& S, const Fr& f, const Fr& prev, c
   double* Dp = m.P + a * (a + 1) / 2;
   stage_lower_async(Rp, Rd + f.v_off, a, lane);
   stage_lower_async(Dp, Dd + f.d_off, n, lane);
-  // A2 = M_AN = T_AN + V' L
+  // A2 = M_AN = T_AN + V' L  (four partial sums per output)
   for (int e = lane; e < a * n; e += TPF) {
     int r, c;
     divmod(e, a, r, c);
-    double acc = m.F[pk(J, n + r, c)];
-    for (int t = 0; t < a; ++t)
-      acc = fma(n + r >= n + t ? m.F[pk(J, n + r, n + t)] : m.F[pk(J, n + t, n + r)], m.A1[t + c * WJ], acc);
-    m.A2[r + c * WJ] = acc;
+    const PkSym Vp{m.F, J, n};
+    double a0 = m.F[pk(J, n + r, c)], a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int t = 0;
+    for (; t + 3 < a; t += 4) {
+      a0 = fma(Vp(r, t), m.A1[t + c * WJ], a0);
+      a1 = fma(Vp(r, t + 1), m.A1[t + 1 + c * WJ], a1);
+      a2 = fma(Vp(r, t + 2), m.A1[t + 2 + c * WJ], a2);
+      a3 = fma(Vp(r, t + 3), m.A1[t + 3 + c * WJ], a3);
+    }
+    for (; t < a; ++t) a0 = fma(Vp(r, t), m.A1[t + c * WJ], a0);
+    m.A2[r + c * WJ] = (a0 + a1) + (a2 + a3);
   }
   fsync();
   // D2 = M_NN = T_NN + T_AN^T L + L^T M_AN  (full)
-  for (int e = lane; e < n * n; e += TPF) {
-    int r, c;
-    divmod(e, n, r, c);
-    double acc = r >= c ? m.F[pk(J, r, c)] : m.F[pk(J, c, r)];
-    for (int t = 0; t < a; ++t) {
-      acc = fma(m.F[pk(J, n + t, r)], m.A1[t + c * WJ], acc);
-      acc = fma(m.A1[t + r * WJ], m.A2[t + c * WJ], acc);
-    }
-    m.D2[r + c * WN] = acc;
-  }
-  fsync();
+  wreduce_nn(
+      n, a, false,
+      [&](int t, int r, int c) {
+        return fma(m.F[pk(J, n + t, r)], m.A1[t + c * WJ], m.A1[t + r * WJ] * m.A2[t + c * WJ]);
+      },
+      [&](int r, int c, double acc) { m.D2[r + c * WN] = acc + (r >= c ? m.F[pk(J, r, c)] : m.F[pk(J, c, r)]); },
+      lane);
   cp_async_wait_all();
   fsync();
   const PkSym D{Dp, n, 0};
