@@ -234,6 +234,32 @@ chd_status chd_complete(chd_symbolic* sym, const double* s_dev, void* stream,
 chd_status chd_recomplete(chd_factor* xhat, const double* s_dev, void* stream, double* fstar);
 
 /*
+ * Schur complement of the barrier Hessian for m matrices A_1..A_m in S^n_V
+ * (the coefficients an interior-point method needs, §5.5):
+ *   H_ij = A_i . grad^2 f(X)[A_j] = A_i . P(X^{-1} A_j X^{-1}),
+ * the inner product counting off-diagonal entries twice.
+ *   a_dev   m value arrays at stride lda (device, caller-owned)
+ *   t_dev   caller-owned device workspace of m value arrays at stride ldt;
+ *           receives T_j = P(X^{-1} A_j X^{-1})
+ *   h_dev   device, m x m column-major (ld m), receives H (symmetric)
+ * Same preconditions and error behaviour as chd_hessian; m*m <= 2^24.
+ */
+chd_status chd_schur(chd_factor* fac, int m, const double* a_dev, int64_t lda, double* t_dev, int64_t ldt,
+                     double* h_dev, void* stream);
+
+/*
+ * Cholesky product (Algorithm 3.2, in the supernodal form of §7): x_dev
+ * (device, nnz_filled values, caller-owned) receives the values on V of the
+ * matrix L D L^T the factor object holds -- X itself for an object made by
+ * chd_factor_new / chd_refactor, the maximum-determinant completion X-hat
+ * for one made by chd_complete, so that the dual gradient is
+ * grad f_*(S) = -X-hat (§1.2).  Uses the factor's workspace of one
+ * right-hand side; asynchronous on `stream`.  Returns CHD_ERR_INVALID for a
+ * NULL argument.
+ */
+chd_status chd_product(chd_factor* fac, double* x_dev, void* stream);
+
+/*
  * Export the unique scalar factorisation X = L D L^T (§2, §3.1): l_dev gets
  * the nnz_filled entries of L on V (unit diagonal), d_dev the n pivots D_ii.
  */

@@ -84,6 +84,10 @@ _lib.chd_factor_set_graphs.argtypes = [_p, C.c_int]
 _lib.chd_factor_set_graphs.restype = C.c_int
 _lib.chd_factor_free.argtypes = [_p]
 _lib.chd_factor_free.restype = None
+_lib.chd_product.argtypes = [_p, _p, _p]
+_lib.chd_product.restype = C.c_int
+_lib.chd_schur.argtypes = [_p, C.c_int, _p, C.c_int64, _p, C.c_int64, _p, _p]
+_lib.chd_schur.restype = C.c_int
 for _f in ("chd_analyze", "chd_analyze_batch", "chd_symbolic_batch_info", "chd_logdet_batch", "chd_symbolic_info", "chd_symbolic_supernodes", "chd_symbolic_flops",
            "chd_factor_new", "chd_refactor", "chd_logdet", "chd_gradient", "chd_hessian",
            "chd_inv_hessian", "chd_complete", "chd_recomplete", "chd_factor_export", "chd_status_get",
@@ -460,6 +464,28 @@ class Factor:
         if out is None:
             out = torch.empty_like(t)
         chd_inv_hessian(self._h, t, out, self.sym.nnz, stream)
+        return out
+
+    def schur(self, a, t=None, h=None, stream=None):
+        """H_ij = A_i . H(A_j) for the rows A_i of `a` (m x nnz); returns (H, T)."""
+        import torch
+        a = a if a.dim() == 2 else a.reshape(1, -1)
+        m = a.shape[0]
+        if t is None:
+            t = torch.empty_like(a)
+        if h is None:
+            h = torch.empty((m, m), dtype=torch.float64, device="cuda")
+        _check(_lib.chd_schur(self._h, m, _dptr(a, "a", self.sym.nnz, rows=m), a.stride(0),
+                              _dptr(t, "t", self.sym.nnz, rows=m), t.stride(0), _dptr(h, "h"),
+                              _stream_ptr(stream)), "chd_schur")
+        return h.t(), t
+
+    def product(self, out=None, stream=None):
+        """Values on V of L D L^T (Algorithm 3.2): X, or X-hat for a completion."""
+        import torch
+        if out is None:
+            out = torch.empty(self.sym.nnz, dtype=torch.float64, device="cuda")
+        _check(_lib.chd_product(self._h, _dptr(out, "out", self.sym.nnz), _stream_ptr(stream)), "chd_product")
         return out
 
     def export(self, stream=None):

@@ -778,6 +778,18 @@ void ihess_up_front(const chd_symbolic* s, const Ctx& st, int m, int k, const do
   CHD_EW(mk_ihess_finish, (int64_t)J * n, m, st, Y + f.base, ldy, F, T2, sw, J, n);
 }
 
+// Algorithm 3.2 (Cholesky product) for one big front: F = the children's
+// blocks + G G^T, G = [C; B]; the N-part of F is X, the A x A block stays.
+void product_front(const chd_symbolic* s, const Ctx& st, int k, const double* Lc, double* Xo, double* ws) {
+  Front f = front(s, k);
+  const int J = f.J, n = f.n;
+  double* F = ws + f.foff;
+  CHD_EW(mk_copy, (int64_t)J * J, 1, st, F, 0, J, nullptr, 0, 0, J, J, 0.0, 0.0, 1, 0);
+  assemble_children(s, st, 1, k, ws, 0);
+  gemm(st, 1, J, J, n, 1.0, CscL{Lc + f.base, J}, 0, CscLT{Lc + f.base, J}, 0, 1.0, Dn{F, J}, 0, true);
+  CHD_EW(mk_front_to_csc, (int64_t)J * n, 1, st, Xo + f.base, 0, F, 0, J, J, n, 0, J, 1.0);
+}
+
 // S-front of a big front for the completion: S_NN and S_AN from the input's
 // columns N_k, V_k = S_{A_k A_k} from the input's later columns.
 void complete_load_front(const chd_symbolic* s, const Ctx& st, int k, const double* Sin, double* ws) {
@@ -1046,7 +1058,23 @@ __global__ void __launch_bounds__(BT) mg_comp_finish(double* Lc, double* Wc, dou
   }
 }
 
+// Algorithm 3.2 per leaf: X_jj = C^2, X_Aj = B C (the group adds +B B^T)
+__global__ void __launch_bounds__(BT) mg_product(const double* Lc, double* X, int64_t base0, int J, int L) {
+  LEAF_PROLOGUE
+  (void)z;
+  const double c = Lc[b];
+  for (int q = 1 + lane; q < J; q += 32) X[b + q] = Lc[b + q] * c;
+  if (lane == 0) X[b] = c * c;
+}
+
 // per-group sequences
+void group_product(const chd_symbolic* s, const Ctx& st, int g, const double* Lc, double* X, double* ws) {
+  const Group G = group(s, g);
+  mg_product<<<leaf_grid(G.L, 1), BT, 0, st>>>(Lc, X, G.base0, G.J, G.L);
+  chd_launch::count_launch();
+  gemm(st, 1, G.a, G.a, G.L, 1.0, Dn{const_cast<double*>(Lc) + G.base0 + 1, G.J}, 0,
+       DnT{const_cast<double*>(Lc) + G.base0 + 1, G.J}, 0, 0.0, Dn{ws + G.f0 + 1 + G.J, G.J}, 0, true);
+}
 void group_factor(const chd_symbolic* s, const Ctx& st, int g, const double* X, double* Lc, double* Wc, double* Dd,
                   double* ws, double* ldet, int64_t* status) {
   const Group G = group(s, g);
@@ -1153,6 +1181,11 @@ void big_factor(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap
   if (s->grp_of[k] >= 0) return chd::big::group_factor(s, chd::big::make_ctx(st, xs, xcap), s->grp_of[k], X, Lc, Wc, Dd, ws, ldet, status);
   chd::big::factor_front(s, chd::big::make_ctx(st, xs, xcap), k, X, Lc, Wc, Dd, ws, ldet, status);
 }
+void big_product(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Lc,
+                 double* X, double* ws) {
+  if (s->grp_of[k] >= 0) return chd::big::group_product(s, chd::big::make_ctx(st, xs, xcap), s->grp_of[k], Lc, X, ws);
+  chd::big::product_front(s, chd::big::make_ctx(st, xs, xcap), k, Lc, X, ws);
+}
 void big_gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Wc,
                   double* Sc, double* g, double* Vd, double* ws) {
   if (s->grp_of[k] >= 0) return chd::big::group_gradient(s, chd::big::make_ctx(st, xs, xcap), s->grp_of[k], Wc, Sc, g, Vd, ws);
@@ -1194,9 +1227,6 @@ void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const doub
 void big_inv_v(const chd_symbolic* s, cudaStream_t stream, double* xs, int64_t xcap, int k, const double* Vd,
                double* Rd, double* ws, int64_t* status) {
   using namespace chd::big;
-  using chd::DnTW;
-  using chd::TriL;
-  using chd::TriLT;
   const Ctx st = chd::big::make_ctx(stream, xs, xcap);
   const int n = (int)(s->sn_ptr[k + 1] - s->sn_ptr[k]);
   const int a = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k]) - n;

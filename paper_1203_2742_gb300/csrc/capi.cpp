@@ -27,6 +27,10 @@ void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
               double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
 void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* ws,
            int64_t* status);
+void product(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Lc, double* X, double* ws);
+int64_t schur_scratch(const chd_symbolic* s, int m);
+void schur(const chd_symbolic* s, cudaStream_t st, int m, const double* A, int64_t lda, const double* T, int64_t ldt,
+           double* H, double* scratch);
 void sum(cudaStream_t st, const double* v, int64_t m, double* out);
 void segsum(cudaStream_t st, const double* v, const int64_t* seg, int nseg, double* out);
 void export_ldl(const chd_symbolic* s, cudaStream_t st, const double* Lc, double* l, double* d);
@@ -578,6 +582,36 @@ chd_status chd_complete(chd_symbolic* s, const double* sv, void* stream, chd_fac
   }
   *xhat = f;
   return CHD_OK;
+}
+
+chd_status chd_schur(chd_factor* f, int m, const double* a, int64_t lda, double* t, int64_t ldt, double* h,
+                     void* stream) {
+  if (!f || m < 1 || !a || !t || !h) return CHD_ERR_INVALID;
+  const int64_t nnz = f->sym->colptr[f->sym->n];
+  if (m > 1 && (lda < nnz || ldt < nnz)) return CHD_ERR_INVALID;
+  if ((int64_t)m * m > (int64_t(1) << 24)) return CHD_ERR_INVALID;
+  if ((std::max<int64_t>(nnz, f->sym->n) + 65535) / 65536 > 65535) return CHD_ERR_INVALID;
+  chd_status rc = chd_hessian(f, m, a, lda, t, ldt, stream);
+  if (rc != CHD_OK) return rc;
+  // the partial sums live in the factor's workspace (free once the Hessian
+  // products are queued before them on the same stream)
+  rc = ensure_ws(f, std::max<int64_t>(1, (chd_launch::schur_scratch(f->sym, m) + f->sym->dev.f_total - 1) /
+                                              std::max<int64_t>(1, f->sym->dev.f_total)));
+  if (rc != CHD_OK) return rc;
+  chd_launch::schur(f->sym, f->stream, m, a, lda, t, ldt, h, f->ws);
+  return launch_status();
+}
+
+chd_status chd_product(chd_factor* f, double* x, void* stream) {
+  if (!f || !x) return CHD_ERR_INVALID;
+  f->stream = static_cast<cudaStream_t>(stream);
+  chd_status rc = ensure_ws(f, 1);
+  if (rc != CHD_OK) return rc;
+  GraphKey key;
+  key.p[0] = x;
+  return run_sequence(f, G_PRODUCT, key, [&](cudaStream_t st) {
+    chd_launch::product(f->sym, st, &f->ex, f->Lc, x, f->ws);
+  });
 }
 
 chd_status chd_factor_export(chd_factor* f, double* l, double* d, void* stream) {

@@ -144,7 +144,7 @@ struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0;
 };
-enum GraphKind { G_FACTOR = 0, G_GRADIENT, G_HESSIAN, G_INV_HESSIAN, G_INV_V, G_COMPLETE, G_KINDS };
+enum GraphKind { G_FACTOR = 0, G_GRADIENT, G_HESSIAN, G_INV_HESSIAN, G_INV_V, G_COMPLETE, G_PRODUCT, G_KINDS };
 
 // A factor object: device-resident factor blocks, cached projected inverse
 // and the per-right-hand-side front workspace (all owned by the object).

@@ -64,6 +64,16 @@ struct CscT {  // transpose of rows [r0, ..) of the N-part
   int r0;
   __device__ double at(int r, int c) const { return p[csc_off(J, c + r0, r)]; }
 };
+struct CscL {  // the whole J x n N-part as a lower trapezoid (zero above the diagonal)
+  const double* p;
+  int J;
+  __device__ double at(int r, int c) const { return r >= c ? p[csc_off(J, r, c)] : 0.0; }
+};
+struct CscLT {  // its transpose (n x J)
+  const double* p;
+  int J;
+  __device__ double at(int r, int c) const { return c >= r ? p[csc_off(J, c, r)] : 0.0; }
+};
 struct CscSym {  // symmetric N x N block stored lower in CSC
   const double* p;
   int J;

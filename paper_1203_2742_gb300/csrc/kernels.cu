@@ -422,6 +422,21 @@ __device__ void factor_front(const SymDev& S, int k, const double* X, double* Lc
   __syncthreads();
 }
 
+// Algorithm 3.2 (Cholesky product) for one front, supernodal form: F = the
+// children's blocks + G G^T with G = [C; B] = [I; L_AN] C (so G G^T =
+// [I; L_AN] D_NN [I; L_AN]^T); the N-part of F is X_{J N}, and the A x A
+// block (-U in Eq. (e-mf-prod)) stays in the front for the parent.
+__device__ void product_front(const SymDev& S, int k, const double* Lc, double* Xo, double* ws) {
+  FrontInfo f = front_info(S, k, ws);
+  const int J = f.J, n = f.n;
+  zero_lower(f.F, J, J, 0);
+  __syncthreads();
+  extend_add_children(S, f, ws, 1.0);
+  cta_gemm(J, J, n, 1.0, CscL{Lc + f.base, J}, CscLT{Lc + f.base, J}, 1.0, Dn{f.F, J}, true);
+  front_to_csc(Xo + f.base, f.F, J, n, 1.0);
+  __syncthreads();
+}
+
 // Algorithm 7.2 for one front: S_AN = -V L_AN, S_NN = D^{-1} - S_AN^T L_AN.
 __device__ void gradient_front(const SymDev& S, int k, const double* Wc, double* Sc, double* g,
                                double* Vd, double* ws) {
@@ -666,6 +681,10 @@ __global__ void __launch_bounds__(NT) k_factor(SymDev S, int task0, const double
   for (int q = S.task_ptr[t]; q < S.task_ptr[t + 1]; ++q)
     factor_front(S, S.task_fronts[q], X, Lc, Wc, Dd, ws, ldet, st);
 }
+__global__ void __launch_bounds__(NT) k_product(SymDev S, int task0, const double* Lc, double* X, double* ws) {
+  const int t = task0 + blockIdx.x;
+  for (int q = S.task_ptr[t]; q < S.task_ptr[t + 1]; ++q) product_front(S, S.task_fronts[q], Lc, X, ws);
+}
 __global__ void __launch_bounds__(NT) k_gradient(SymDev S, int task0, const double* Wc, double* Sc,
                                                  double* g, double* Vd, double* ws) {
   const int t = task0 + blockIdx.x;
@@ -741,6 +760,41 @@ __global__ void k_sum(const double* v, int64_t m, double* out) {
   }
   if (threadIdx.x == 0) *out = red[0];
 }
+// Schur complement H_ij = A_i . T_j (T_j = H(A_j)) in the trace inner product
+// (§5.5): partial sums over chunks of the value arrays, CTA (chunk, pair):
+// 2 sum_e a_i[e] t_j[e] minus the diagonal entries (at colptr[c]) once.
+constexpr int64_t kSchurChunk = 65536;
+__global__ void __launch_bounds__(NT) k_schur_partial(int m, const double* A, int64_t lda, const double* T,
+                                                      int64_t ldt, int64_t nnz, const int64_t* colptr, int64_t n,
+                                                      double* partial) {
+  __shared__ double red[NT];
+  const int64_t chunk = blockIdx.y;
+  const int pair = blockIdx.x, i = pair % m, j = pair / m;
+  const double* a = A + i * lda;
+  const double* t = T + j * ldt;
+  const int64_t e0 = chunk * kSchurChunk;
+  double s = 0.0;
+  for (int64_t e = e0 + threadIdx.x; e < min(nnz, e0 + kSchurChunk); e += NT) s = fma(2.0 * a[e], t[e], s);
+  for (int64_t c = e0 + threadIdx.x; c < min(n, e0 + kSchurChunk); c += NT) {
+    const int64_t d = colptr[c];
+    s = fma(-a[d], t[d], s);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = NT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[(int64_t)pair * gridDim.y + chunk] = red[0];
+}
+// sum of the chunk partials in chunk order, H column-major (ld m)
+__global__ void k_schur_sum(int m, int64_t nchunk, const double* partial, double* H) {
+  const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pair >= m * m) return;
+  double s = 0.0;
+  for (int64_t c = 0; c < nchunk; ++c) s += partial[(int64_t)pair * nchunk + c];
+  H[pair] = s;
+}
 // Deterministic sums of v over the segments [seg[i], seg[i+1]), one CTA each.
 __global__ void k_segsum(const double* v, const int64_t* seg, double* out) {
   __shared__ double red[NT];
@@ -806,6 +860,8 @@ static inline void count() { ++g_launches; }
 // dense-tier sequences (bigfront.cu); xs/xcap: split-K scratch (may be null)
 void big_factor(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* X,
                 double* Lc, double* Wc, double* Dd, double* ws, double* ldet, int64_t* status);
+void big_product(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Lc,
+                 double* X, double* ws);
 void big_gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Wc,
                   double* Sc, double* g, double* Vd, double* ws);
 void big_hess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
@@ -823,6 +879,7 @@ void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xc
 
 // warp-tier launches (warp_tier.cu): w32 for |J| <= 32, w64 for |J| <= 64
 namespace w32 {
+void warp_product(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Lc, double* X, double* ws);
 void warp_factor(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* X, double* Lc, double* Wc,
                  double* Dd, double* ws, double* ldet, int64_t* status);
 void warp_gradient(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Wc, double* Sc,
@@ -840,6 +897,7 @@ void warp_complete_all(const chd_symbolic* s, cudaStream_t st, const double* Sin
                        double* Dd, double* Vd, double* Rd, double* ldet, int64_t* status);
 }  // namespace w32
 namespace w64 {
+void warp_product(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Lc, double* X, double* ws);
 void warp_factor(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* X, double* Lc, double* Wc,
                  double* Dd, double* ws, double* ldet, int64_t* status);
 void warp_gradient(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Wc, double* Sc,
@@ -926,6 +984,24 @@ void factor(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double
     if (v.nw64) w64::warp_factor(s, st, v.tw, v.nw64, X, Lc, Wc, Dd, ws, ldet, status);
     if (v.ncta) {
       k_factor<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, X, Lc, Wc, Dd, ws, ldet, status);
+      count();
+    }
+    bf.join_now();
+  }
+}
+// Cholesky product X = L D L^T on V (Algorithm 3.2), bottom-up like the factor.
+void product(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Lc, double* X, double* ws) {
+  const int nl = (int)s->lvl_ptr.size() - 1;
+  for (int l = 0; l < nl; ++l) {
+    Level v = level(s, l);
+    BigFork bf{ex, st};
+    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
+      big_product(s, bs, xs, xc, big_front(s, v, i), Lc, X, ws);
+    });
+    if (v.nwarp) w32::warp_product(s, st, v.t0, v.nwarp, Lc, X, ws);
+    if (v.nw64) w64::warp_product(s, st, v.tw, v.nw64, Lc, X, ws);
+    if (v.ncta) {
+      k_product<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Lc, X, ws);
       count();
     }
     bf.join_now();
@@ -1050,6 +1126,21 @@ void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double*
     count();
   }
   bf.join_now();
+}
+// H (m x m) = [A_i . T_j]; `scratch` holds m*m*ceil(max(nnz, n)/chunk) doubles
+int64_t schur_scratch(const chd_symbolic* s, int m) {
+  const int64_t len = std::max<int64_t>(s->colptr[s->n], s->n);
+  return (int64_t)m * m * ((len + kSchurChunk - 1) / kSchurChunk);
+}
+void schur(const chd_symbolic* s, cudaStream_t st, int m, const double* A, int64_t lda, const double* T, int64_t ldt,
+           double* H, double* scratch) {
+  const int64_t nnz = s->colptr[s->n];
+  const int64_t nchunk = (std::max<int64_t>(nnz, s->n) + kSchurChunk - 1) / kSchurChunk;
+  k_schur_partial<<<dim3((unsigned)(m * m), (unsigned)nchunk), NT, 0, st>>>(m, A, lda, T, ldt, nnz, s->dev.colptr,
+                                                                           s->n, scratch);
+  count();
+  k_schur_sum<<<(m * m + NT - 1) / NT, NT, 0, st>>>(m, nchunk, scratch, H);
+  count();
 }
 void sum(cudaStream_t st, const double* v, int64_t m, double* out) {
   k_sum<<<1, NT, 0, st>>>(v, m, out);

@@ -572,6 +572,30 @@ __device__ void factor_front(const SymDev& S, const Fr& f, const Fr& prev, const
   fsync();
 }
 
+// Algorithm 3.2 (Cholesky product) for one front: F = the children's blocks
+// + G G^T with G = [C; B] (the front's N-part of Lc, staged and scattered
+// into D1 = C and A1 = B); the N-part of F is X, the A x A block stays.
+__device__ void product_front(const SymDev& S, const Fr& f, const Fr& prev, const double* Lc, double* Xo,
+                              const double* ws, const Smem& m, int lane) {
+  const int J = f.J, n = f.n;
+  load_up(S, f, prev, m, nullptr, nullptr, Lc, true, lane);
+  extend_add(S, f, prev, m, ws, lane);
+  // G(r, t): C(r, t) for r < n (lower), B(r - n, t) below
+  auto G = [&](int r, int t) { return r < n ? (r >= t ? m.D1[r + t * WN] : 0.0) : m.A1[(r - n) + t * WJ]; };
+  for (int e = lane; e < J * J; e += TPF) {
+    int r, c;
+    divmod(e, J, r, c);
+    if (r < c) continue;
+    double acc = 0.0;
+    for (int t = 0; t < n; ++t) acc = fma(G(r, t), G(c, t), acc);
+    m.F[pk(J, r, c)] += acc;
+  }
+  fsync();
+  store_front(f, m, Xo, 1.0, lane);
+  write_update(f, m, lane);
+  fsync();
+}
+
 __device__ void gradient_front(const SymDev& S, const Fr& f, const Fr& prev, const double* Wc, double* Sc,
                                double* g, double* Vd, const double* ws, const Smem& m, int lane) {
   const int J = f.J, n = f.n, a = f.a;
@@ -946,6 +970,13 @@ __global__ void __launch_bounds__(WPB * TPF) kw_factor(SymDev S, int task0, int 
     factor_front(S, f, prev, X, Lc, Wc, Dd, ws, ldet, st, m, lane);
   });
 }
+__global__ void __launch_bounds__(WPB * TPF) kw_product(SymDev S, int task0, int task_end, const double* Lc,
+                                                         double* X, double* ws) {
+  WARP_TASK_PROLOGUE
+  walk_up(S, t, ws, w, [&](const Fr& f, const Fr& prev, const Smem& m) {
+    product_front(S, f, prev, Lc, X, ws, m, lane);
+  });
+}
 __global__ void __launch_bounds__(WPB * TPF) kw_gradient(SymDev S, int task0, int task_end, const double* Wc,
                                                         double* Sc, double* g, double* Vd, double* ws) {
   WARP_TASK_PROLOGUE
@@ -1013,6 +1044,10 @@ namespace WT_NS {
 using namespace chd::WT_NS;
 static inline dim3 wgrid(int nt, int m) { return dim3((nt + WPB - 1) / WPB, m); }
 
+void warp_product(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Lc, double* X, double* ws) {
+  kw_product<<<wgrid(nt, 1), WPB * TPF, 0, st>>>(s->dev, t0, t0 + nt, Lc, X, ws);
+  chd_launch::count_launch();
+}
 void warp_factor(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* X, double* Lc, double* Wc,
                  double* Dd, double* ws, double* ldet, int64_t* status) {
   kw_factor<<<wgrid(nt, 1), WPB * TPF, 0, st>>>(s->dev, t0, t0 + nt, X, Lc, Wc, Dd, ws, ldet, status);

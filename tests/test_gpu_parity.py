@@ -162,6 +162,38 @@ def test_completion(name):
     assert c.err(yh, want) < 1e-9
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_cholesky_product(name):
+    """Algorithm 3.2: L D L^T on V from a factor object is X; from a completion
+    object it is X-hat, whose negative is the dual gradient (§1.2)."""
+    c = CASES[name]()
+    f = c.sym.factor(c.dev(c.x))
+    assert c.err(c.host(f.product()), c.x) < 1e-12
+    G = c.rng.standard_normal((c.n, 10))
+    s = W.projected_gram(c.n, c.cp, c.ri, G, 0.5)
+    fx, _ = c.sym.complete(c.dev(s))
+    I, parent = OS.fill(c.n, OS.columns_from_csc(c.n, c.cp, c.ri))
+    cl, seps = OS.cliques_and_separators(I, parent)
+    xh = OD.completion_cliquesum(c.n, c.cp, c.ri, s, cl, seps)
+    assert c.err(c.host(fx.product()), xh) < TOL
+
+
+@pytest.mark.parametrize("name", ["grid14_nd", "er300_mindeg_relax16", "dense_tier_er", "arrow150_w48"])
+def test_schur_complement(name):
+    """H_ij = A_i . H(A_j) (§5.5) against the oracle's Hessian and inner product."""
+    c = CASES[name]()
+    m = 5
+    A = W.uniform_sym(c.n, c.cp, c.ri, c.rng, count=m)
+    f = c.sym.factor(c.dev(c.x))
+    H, T = f.schur(c.dev(A))
+    H = c.host(H)
+    Th = OD.hessian(c.n, c.cp, c.ri, c.x, list(A))
+    want = np.array([[OD.sym_dot(c.n, c.cp, c.ri, A[i], Th[j]) for j in range(m)] for i in range(m)])
+    assert np.abs(H - want).max() <= 1e-10 * np.abs(want).max()
+    assert np.abs(H - H.T).max() <= 1e-10 * np.abs(want).max()
+    assert np.linalg.eigvalsh(0.5 * (H + H.T)).min() > 0  # H is positive definite
+
+
 def test_planted_condition_1e6():
     def planted(s, rng):
         x, _, _ = W.planted_factor(s.n, s.colptr, s.rowind, rng, dmin=1e-6, dmax=1.0)
