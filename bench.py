@@ -279,6 +279,28 @@ def analysed_pattern_host(wl):
 
 
 # ---------------------------------------------------------------------------
+# replicas: every rank runs the whole step on its own GPU (the path has no
+# exchange step); the job's time is the slowest rank's
+# ---------------------------------------------------------------------------
+
+def replica_max_ms(dev_ms, device):
+    """Max over the ranks of the timed region's device milliseconds."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return dev_ms
+    t = torch.tensor([dev_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_value(world, evals_per_step, steps, max_ms):
+    """Whole-job throughput: every replica's evaluations over the slowest time."""
+    return world * evals_per_step * steps / (max_ms * 1e-3)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -357,16 +379,10 @@ def run_ours(args, wl, rank, world, local_rank):
     wall = time.perf_counter() - wall0
     launches = B.chd_kernel_launches() - launches0
     clocks = sampler.stop()
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dev_ms = float(tt.item())
-        dist.barrier()
+    dev_ms = replica_max_ms(sum(a.elapsed_time(b) for a, b in evs), dev)
     ms_per_step = dev_ms / args.steps
     evals_per_step = count * m  # one Hessian evaluation = one Y of one instance
-    value = world * evals_per_step * args.steps / (dev_ms * 1e-3)
+    value = job_value(world, evals_per_step, args.steps, dev_ms)
 
     # ---- per-operation breakdown and the dominant kernel's roofline ----
     def time_op(fn, reps):
