@@ -15,9 +15,6 @@ Modules
                      (e-dual-barrier-def)).
 ``symbolic``      -- filled pattern, elimination tree, monotone degrees,
                      cliques, supernode partitions (§2, §6, Algorithm 6.1).
-``multifrontal``  -- the paper's scalar recursions (Algorithms 3.1, 3.2, 4.1,
-                     4.2, 5.1, 5.2) taken step by step, used as a second,
-                     independent CPU implementation.
 
 Value layout shared with the library API: a symmetric matrix on the pattern V
 is stored as the lower-triangular compressed columns (CSC) of V, rows sorted

@@ -19,6 +19,10 @@ multifrontal method that reaches it:
                      by Newton's method on the concave problem in
                      Eq. (e-dual-barrier-def), or by the clique-sum closed form.
 * dual_barrier    -- f_*(S) = log det X-hat - n (§1.2).
+* linearized_factor -- L', D' of X + tY = L(t) D(t) L(t)^T at t = 0 (§5.1).
+* hessian_factor, hessian_factor_adj -- W = R(Y) and T = R^adj(W) with
+                     H = R^adj o R (§5.4, Algorithms 5.3 and 5.4), R_j the
+                     upper triangular factor of S_{I_j I_j} = R_j R_j^T.
 
 Values live on the lower CSC of the pattern V (see ``oracle/__init__``).
 The inner product of symmetric matrices is A.B = tr(AB) (§1.1), so an
@@ -245,6 +249,116 @@ def inv_hessian_cliquesum(n, colptr, rowind, x, t, cliques, separators, S=None):
     pairs = pattern_pairs(n, colptr, rowind)
     return (_clique_term(n, colptr, rowind, term, cliques, 1.0, pairs)
             + _clique_term(n, colptr, rowind, term, separators, -1.0, pairs))
+
+
+# --------------------------------------------------------------------------
+# linearized factorization and Hessian factor (§5.1, §5.4)
+# --------------------------------------------------------------------------
+
+
+def linearized_factor(n, colptr, rowind, x, y):
+    """Derivatives L', D' at t = 0 of X + tY = L(t) D(t) L(t)^T (§5.1).
+
+    Differentiating X + tY = L D L^T gives Y = L' D L^T + L D' L^T + L D L'^T,
+    so L^{-1} Y L^{-T} = G D + D' + D G^T with G = L^{-1} L' strictly lower
+    (L' is zero on and above the diagonal).  Hence D' is the diagonal of
+    L^{-1} Y L^{-T} and G its strictly lower part times D^{-1}; L' = L G.
+    Returns dense (Lp, dp, L, d).
+    """
+    X = to_dense(n, colptr, rowind, x)
+    Y = to_dense(n, colptr, rowind, y)
+    C = np.linalg.cholesky(X)
+    dc = np.diag(C).copy()
+    L = C / dc[None, :]
+    d = dc * dc
+    Z = sla.solve_triangular(L, Y, lower=True, unit_diagonal=True)
+    Z = sla.solve_triangular(L, Z.T, lower=True, unit_diagonal=True)
+    Lp = L @ (np.tril(Z, -1) / d[None, :])
+    return Lp, np.diag(Z).copy(), L, d
+
+
+def reverse_cholesky(A):
+    """Upper triangular R with positive diagonal and A = R R^T.
+
+    With P the reversal of the index order, P A P = C C^T (lower Cholesky C)
+    gives A = (P C P)(P C P)^T, and P C P is upper triangular.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    C = np.linalg.cholesky(A[::-1, ::-1])
+    return np.ascontiguousarray(C[::-1, ::-1])
+
+
+def _below(n, colptr, rowind):
+    """I_j: the rows i > j of column j of V, in increasing order."""
+    colptr = np.asarray(colptr, dtype=np.int64)
+    rows = np.asarray(rowind, dtype=np.int64)
+    out = []
+    for j in range(n):
+        r = rows[colptr[j]:colptr[j + 1]]
+        out.append(r[r > j])
+    return out
+
+
+def hessian_factor_parts(n, colptr, rowind, x):
+    """(I_j, R_j) of every vertex j: S_{I_j I_j} = R_j R_j^T with R_j upper
+    triangular (§5.4), S = P(X^{-1})."""
+    Zi = inverse(n, colptr, rowind, x)
+    out = []
+    for j, I in enumerate(_below(n, colptr, rowind)):
+        out.append((I, reverse_cholesky(Zi[np.ix_(I, I)]) if len(I) else np.zeros((0, 0))))
+    return out
+
+
+def hessian_factor(n, colptr, rowind, x, ys, parts=None):
+    """W = R(Y) for each Y (Algorithm 5.3): K from the linearized
+    factorization (Eq. (e-mf-hess-vars): K_jj = D'_jj, K_{I_j j} = D_jj L'_{I_j j}),
+    then W_jj = K_jj / D_jj and W_{I_j j} = R_j^T K_{I_j j} / sqrt(D_jj)."""
+    if parts is None:
+        parts = hessian_factor_parts(n, colptr, rowind, x)
+    out = []
+    for y in ys:
+        Lp, dp, _, d = linearized_factor(n, colptr, rowind, x, y)
+        W = np.zeros((n, n))
+        for j, (I, R) in enumerate(parts):
+            W[j, j] = dp[j] / d[j]
+            if len(I):
+                W[I, j] = R.T @ (d[j] * Lp[I, j]) / np.sqrt(d[j])
+        out.append(project(n, colptr, rowind, W))
+    return out
+
+
+def hessian_factor_adj(n, colptr, rowind, x, ws, parts=None):
+    """T = R^adj(W) for each W (Algorithm 5.4).
+
+    Step 1 gives M_jj = W_jj / D_jj and M_{I_j j} = R_j W_{I_j j} / sqrt(D_jj);
+    by Eq. (e-mf-hess-vars) these are D'_jj / D_jj^2 and S_{I_j I_j} L'_{I_j j}
+    of a direction Y' (so D'_jj = D_jj W_jj, L'_{I_j j} = R_j^{-T} W_{I_j j} /
+    sqrt(D_jj)).  Step 2 is the linearized projected inverse (Eq.
+    (e-compl-lin)), whose result is T = -dS/dt = P(X^{-1} Y' X^{-1}) with
+    Y' = L' D L^T + L D' L^T + L D L'^T.
+    """
+    if parts is None:
+        parts = hessian_factor_parts(n, colptr, rowind, x)
+    X = to_dense(n, colptr, rowind, x)
+    C = np.linalg.cholesky(X)
+    dc = np.diag(C).copy()
+    L = C / dc[None, :]
+    d = dc * dc
+    Zi = inverse(n, colptr, rowind, x)
+    rr, cc = pattern_pairs(n, colptr, rowind)
+    out = []
+    for w in ws:
+        Wl = np.zeros((n, n))
+        Wl[rr, cc] = w
+        Lp = np.zeros((n, n))
+        dp = np.zeros(n)
+        for j, (I, R) in enumerate(parts):
+            dp[j] = d[j] * Wl[j, j]
+            if len(I):
+                Lp[I, j] = sla.solve_triangular(R.T, Wl[I, j], lower=True) / np.sqrt(d[j])
+        Yd = Lp @ (d[:, None] * L.T) + L @ (dp[:, None] * L.T) + L @ (d[:, None] * Lp.T)
+        out.append(project(n, colptr, rowind, Zi @ Yd @ Zi))
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -360,3 +360,96 @@ def test_exact_rational_inverse_hessian_and_completion(seed):
     # completion of S = P(X^{-1}) is X itself (Eq. (e-Xhat-eq) has the unique solution X)
     s = np.array([float(Z[int(a), int(b)]) for a, b in zip(r, c)])
     np.testing.assert_allclose(OD.completion_newton(n, cp, ri, s), x, rtol=1e-11, atol=1e-11)
+
+
+# ---------------------------------------------------------------------------
+# linearized factorization and Hessian factor (§5.1, §5.4)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(PATTERNS))
+def test_linearized_factor_is_the_derivative(name):
+    """L', D' against central differences of the dense LDL^T factor."""
+    p = PATTERNS[name]()
+    n, cp, ri = p
+    rng = np.random.default_rng(91)
+    x = spd_values(p, 92)
+    y = W.uniform_sym(n, cp, ri, rng, count=1)[0]
+    Lp, dp, L, d = OD.linearized_factor(n, cp, ri, x, y)
+    h = 1e-5
+
+    def ldl(v):
+        C = np.linalg.cholesky(OD.to_dense(n, cp, ri, v))
+        return C / np.diag(C)[None, :], np.diag(C) ** 2
+
+    (La, da), (Lb, db) = ldl(x + h * y), ldl(x - h * y)
+    np.testing.assert_allclose(dp, (da - db) / (2 * h), rtol=0, atol=1e-7 * np.max(np.abs(dp)))
+    np.testing.assert_allclose(Lp, (La - Lb) / (2 * h), rtol=0, atol=1e-7 * max(1.0, np.max(np.abs(Lp))))
+    # L' lives on the strictly lower part of the filled pattern
+    mask = np.zeros((n, n), bool)
+    rr, cc = OD.pattern_pairs(n, cp, ri)
+    mask[rr, cc] = True
+    assert np.max(np.abs(Lp[~mask | np.eye(n, dtype=bool)]), initial=0.0) < 1e-12 * max(1.0, np.max(np.abs(Lp)))
+
+
+def test_reverse_cholesky_is_upper_factor():
+    rng = np.random.default_rng(93)
+    B = rng.standard_normal((7, 7))
+    A = B @ B.T + 7 * np.eye(7)
+    R = OD.reverse_cholesky(A)
+    assert np.allclose(np.tril(R, -1), 0.0)
+    assert np.all(np.diag(R) > 0)
+    np.testing.assert_allclose(R @ R.T, A, rtol=1e-13, atol=1e-12)
+
+
+@pytest.mark.parametrize("name", list(PATTERNS))
+def test_hessian_factor_composes_to_hessian(name):
+    """H = R^adj o R (§5.4) against the dense definition of H, and R^adj is
+    the adjoint of R in the trace inner product."""
+    p = PATTERNS[name]()
+    n, cp, ri = p
+    rng = np.random.default_rng(94)
+    x = spd_values(p, 95)
+    ys = W.uniform_sym(n, cp, ri, rng, count=2)
+    parts = OD.hessian_factor_parts(n, cp, ri, x)
+    for I, R in parts:  # the factor the paper prescribes: upper, S_II = R R^T
+        assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
+    w = OD.hessian_factor(n, cp, ri, x, list(ys), parts=parts)
+    t = OD.hessian_factor_adj(n, cp, ri, x, w, parts=parts)
+    h = OD.hessian(n, cp, ri, x, list(ys))
+    for j in range(2):
+        assert OD.rel_err(n, cp, ri, t[j], h[j]) < 1e-11
+    # <R(Y0), W1> = <Y0, R^adj(W1)> for an unrelated W1
+    w1 = W.uniform_sym(n, cp, ri, rng, count=1)[0]
+    lhs = OD.sym_dot(n, cp, ri, w[0], w1)
+    rhs = OD.sym_dot(n, cp, ri, ys[0], OD.hessian_factor_adj(n, cp, ri, x, [w1], parts=parts)[0])
+    assert abs(lhs - rhs) < 1e-11 * max(1.0, abs(lhs))
+    # <Y, H(Y)> = ||R(Y)||^2
+    assert abs(OD.sym_dot(n, cp, ri, ys[0], h[0]) - OD.sym_dot(n, cp, ri, w[0], w[0])) < 1e-10 * abs(
+        OD.sym_dot(n, cp, ri, ys[0], h[0]))
+
+
+def test_hessian_factor_diagonal_x_closed_form():
+    """X diagonal: L = I, D = diag(x), S = diag(1/x), so R_j = diag(1/sqrt(x_I))
+    and W_ij = Y_ij / sqrt(x_i x_j)."""
+    n, cp, ri = W.band(12, 3)
+    rng = np.random.default_rng(96)
+    rr, cc = OD.pattern_pairs(n, cp, ri)
+    xd = rng.uniform(0.5, 2.0, n)
+    x = np.where(rr == cc, xd[rr], 0.0)
+    y = W.uniform_sym(n, cp, ri, rng, count=1)[0]
+    w = OD.hessian_factor(n, cp, ri, x, [y])[0]
+    np.testing.assert_allclose(w, y / np.sqrt(xd[rr] * xd[cc]), rtol=1e-13, atol=0)
+
+
+def test_hessian_factor_dense_2x2_by_hand():
+    """Dense 2 x 2 pattern: X = [[a, b], [b, c]], D_11 = a, L_21 = b/a,
+    D_22 = c - b^2/a.  For Y = E_21 + E_12: D'_11 = 0, L'_21 = 1/a,
+    D'_22 = -2b/a; S_22 = 1/D_22 gives R_1 = 1/sqrt(D_22).  So
+    W_11 = 0, W_21 = sqrt(a) (1/a) / sqrt(D_22), W_22 = D'_22 / D_22."""
+    n, cp, ri = 2, np.array([0, 2, 3], np.int64), np.array([0, 1, 1], np.int32)
+    a, b, c = 3.0, 1.0, 2.0
+    x = np.array([a, b, c])
+    y = np.array([0.0, 1.0, 0.0])
+    d22 = c - b * b / a
+    w = OD.hessian_factor(n, cp, ri, x, [y])[0]
+    np.testing.assert_allclose(w, [0.0, np.sqrt(a) / a / np.sqrt(d22), (-2 * b / a) / d22], rtol=1e-14, atol=1e-15)
