@@ -206,6 +206,29 @@ chd_status chd_hessian(chd_factor* fac, int m, const double* y_dev, int64_t ldy,
                        double* t_dev, int64_t ldt, void* stream);
 
 /*
+ * Hessian factor (§5.4, Algorithms 5.3 and 5.4 in supernodal block form):
+ * H = R^adj o R with W = R(Y) given per column j by W_jj = K_jj / D_jj and
+ * W_{I_j j} = R_j^T K_{I_j j} / sqrt(D_jj), K the linearized factors of Y
+ * (Eq. (e-mf-hess-vars)) and R_j the UPPER triangular factor of
+ * S_{I_j I_j} = R_j R_j^T.  R^adj is its adjoint in the trace inner
+ * product, so H_ij = A_i . H(A_j) = R(A_i) . R(A_j).
+ *   chd_hessian_factor:      w_i = R(y_i), i < m
+ *   chd_hessian_factor_adj:  t_i = R^adj(w_i), i < m; t_dev may equal w_dev
+ *                            (in place), other overlaps are not allowed
+ * Device arrays of m matrices at strides ldy/ldw/ldt (>= nnz_filled when
+ * m > 1), values on V in the library's CSC layout.  The first call on a
+ * factor computes the projected inverse (as chd_gradient) and the upper
+ * factors of every V_k = S_{A_k A_k}; a pivot <= 0 there is recorded and
+ * reported as CHD_ERR_NOT_PD by chd_status.  Errors returned directly:
+ * CHD_ERR_INVALID (NULL arguments, m < 0, short strides), CHD_ERR_OOM,
+ * CHD_ERR_CUDA.
+ */
+chd_status chd_hessian_factor(chd_factor* fac, int m, const double* y_dev, int64_t ldy,
+                              double* w_dev, int64_t ldw, void* stream);
+chd_status chd_hessian_factor_adj(chd_factor* fac, int m, const double* w_dev, int64_t ldw,
+                                  double* t_dev, int64_t ldt, void* stream);
+
+/*
  * Inverse-Hessian products Y_i = H^{-1}(T_i) (§5.3, Algorithm 5.2 in
  * supernodal block form): the solution in S^n_V of P(X^{-1} Y X^{-1}) = T.
  * Uses cached Cholesky factors of V_k = S_{A_k A_k}.

@@ -88,6 +88,9 @@ _lib.chd_product.argtypes = [_p, _p, _p]
 _lib.chd_product.restype = C.c_int
 _lib.chd_schur.argtypes = [_p, C.c_int, _p, C.c_int64, _p, C.c_int64, _p, _p]
 _lib.chd_schur.restype = C.c_int
+for _f in ("chd_hessian_factor", "chd_hessian_factor_adj"):
+    getattr(_lib, _f).argtypes = [_p, C.c_int, _p, _i64, _p, _i64, _p]
+    getattr(_lib, _f).restype = C.c_int
 for _f in ("chd_analyze", "chd_analyze_batch", "chd_symbolic_batch_info", "chd_logdet_batch", "chd_symbolic_info", "chd_symbolic_supernodes", "chd_symbolic_flops",
            "chd_factor_new", "chd_refactor", "chd_logdet", "chd_gradient", "chd_hessian",
            "chd_inv_hessian", "chd_complete", "chd_recomplete", "chd_factor_export", "chd_status_get",
@@ -295,6 +298,26 @@ def chd_hessian_noalloc(fac, y, t, nnz, stream=None):
            "chd_hessian_noalloc")
 
 
+def chd_hessian_factor(fac, y, w, nnz, stream=None):
+    """W = R(Y), H = R^adj o R (Algorithm 5.3)."""
+    m, ldy = _batch(y, nnz, "y")
+    m2, ldw = _batch(w, nnz, "w")
+    if m != m2:
+        raise ValueError("y and w batch sizes differ")
+    _check(_lib.chd_hessian_factor(fac, m, _dptr(y, "y"), ldy, _dptr(w, "w"), ldw, _stream_ptr(stream)),
+           "chd_hessian_factor")
+
+
+def chd_hessian_factor_adj(fac, w, t, nnz, stream=None):
+    """T = R^adj(W) (Algorithm 5.4)."""
+    m, ldw = _batch(w, nnz, "w")
+    m2, ldt = _batch(t, nnz, "t")
+    if m != m2:
+        raise ValueError("w and t batch sizes differ")
+    _check(_lib.chd_hessian_factor_adj(fac, m, _dptr(w, "w"), ldw, _dptr(t, "t"), ldt, _stream_ptr(stream)),
+           "chd_hessian_factor_adj")
+
+
 def chd_inv_hessian(fac, t, y, nnz, stream=None):
     m, ldt = _batch(t, nnz, "t")
     m2, ldy = _batch(y, nnz, "y")
@@ -457,6 +480,22 @@ class Factor:
         if out is None:
             out = torch.empty_like(y)
         chd_hessian(self._h, y, out, self.sym.nnz, stream)
+        return out
+
+    def hessian_factor(self, y, out=None, stream=None):
+        """W = R(Y) with H = R^adj o R (Algorithm 5.3)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(y)
+        chd_hessian_factor(self._h, y, out, self.sym.nnz, stream)
+        return out
+
+    def hessian_factor_adj(self, w, out=None, stream=None):
+        """T = R^adj(W) (Algorithm 5.4); `out` may be `w` itself."""
+        import torch
+        if out is None:
+            out = torch.empty_like(w)
+        chd_hessian_factor_adj(self._h, w, out, self.sym.nnz, stream)
         return out
 
     def inv_hessian(self, t, out=None, stream=None):

@@ -491,6 +491,15 @@ __global__ void __launch_bounds__(BT) mk_copy(double* dst, int64_t sD, int64_t l
     *d = beta != 0.0 ? fma(beta, *d, alpha * v) : alpha * v;
   }
 }
+// dst (lower, ld m) = P src P for the symmetric src stored lower, P the
+// order reversal
+__global__ void __launch_bounds__(BT) mk_rev_lower(double* dst, const double* src, int m) {
+  const int64_t tot = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    if (r >= c) dst[r + (int64_t)c * m] = src[(m - 1 - c) + (int64_t)(m - 1 - r) * m];
+  }
+}
 __global__ void __launch_bounds__(BT) mk_identity(double* dst, int64_t ld, int m) {
   const int64_t tot = (int64_t)m * m;
   for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
@@ -776,6 +785,59 @@ void ihess_up_front(const chd_symbolic* s, const Ctx& st, int m, int k, const do
     gemm(st, m, a, a, n, -1.0, L, 0, DnT{T2 + n, J}, sw, 1.0, Dn{F + n + (int64_t)n * J, J}, sw, true);
   }
   CHD_EW(mk_ihess_finish, (int64_t)J * n, m, st, Y + f.base, ldy, F, T2, sw, J, n);
+}
+
+// Hessian factor (§5.4) for one big front, M <-> W in place on the N-part
+// of Z: dir 0: W_NN = C^T M_NN C, W_AN = Q^{-1} (M_AN C); dir 1: M_NN =
+// C^{-T} W_NN C^{-1}, M_AN = Q (W_AN C^{-1}); C = chol(D_NN) from the
+// factor, Q the upper factor of V held as Q' = P Q P (A-rows reversed).
+template <class MD, class MS>
+__global__ void __launch_bounds__(BT) mk_copy_view(MD D, int64_t sD, MS S, int64_t sS, int R, int C) {
+  D.p += blockIdx.z * sD;
+  S.p += blockIdx.z * sS;
+  const int64_t tot = (int64_t)R * C;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % R), c = (int)(e / R);
+    D.at(r, c) = S.at(r, c);
+  }
+}
+template <class MD, class MS>
+void copy_view(const Ctx& st, int batch, MD D, int64_t sD, MS S, int64_t sS, int R, int C) {
+  if ((int64_t)R * C <= 0 || batch <= 0) return;
+  mk_copy_view<<<dim3(ew_blocks((int64_t)R * C), 1, batch), BT, 0, st>>>(D, sD, S, sS, R, C);
+  chd_launch::count_launch();
+}
+void rtrans_front(const chd_symbolic* s, const Ctx& st, int m, int k, int dir, const double* Lc, const double* Qd,
+                  double* Z, int64_t ldz, double* ws) {
+  Front f = front(s, k);
+  const int J = f.J, n = f.n, a = f.a;
+  const int64_t sw = s->dev.f_total;
+  double* F = ws + f.foff;
+  double* T1 = F + (int64_t)J * J;
+  double* T2 = T1 + (int64_t)J * n;
+  const double* Q = Qd + s->v_off[k];
+  const double* Lk = Lc + f.base;
+  double* Zk = Z + f.base;
+  if (dir == 0) {
+    // T1 = [M_NN C; P M_AN C], W_NN = C^T (M_NN C), then Q'^{-1} on the A-rows
+    gemm(st, m, n, n, n, 1.0, CscSym{Zk, J}, ldz, CscL{Lk, J}, 0, 0.0, Dn{T1, J}, sw, false);
+    if (a > 0)
+      gemm(st, m, a, n, n, 1.0, CscRO{Zk, J, n}, ldz, CscL{Lk, J}, 0, 0.0, DnRev{T1 + n, J, a}, sw, false);
+    gemm(st, m, n, n, n, 1.0, CscLT{Lk, J}, 0, Dn{T1, J}, sw, 0.0, Csc{Zk, J, 0}, ldz, true);
+    if (a > 0) {
+      trsm_rLT(st, m, n, a, DnTW{T1 + n, J}, sw, Q, a);
+      copy_view(st, m, Csc{Zk, J, n}, ldz, DnRev{T1 + n, J, a}, sw, a, n);
+    }
+  } else {
+    // C (dense lower, ld J) in the first right-hand side's T2; T1 = [W_NN; P W_AN]
+    CHD_EW(mk_csc_to_front, (int64_t)J * n, 1, st, T2, 0, J, n, Lk, 0);
+    copy_view(st, m, Dn{T1, J}, sw, CscSym{Zk, J}, ldz, n, n);
+    if (a > 0) copy_view(st, m, DnRev{T1 + n, J, a}, sw, CscRO{Zk, J, n}, ldz, a, n);
+    trsm_rL(st, m, J, n, Dn{T1, J}, sw, T2, J);
+    trsm_rL(st, m, n, n, DnTW{T1, J}, sw, T2, J);
+    CHD_EW(mk_front_to_csc, (int64_t)J * n, m, st, Zk, ldz, T1, sw, J, J, n, 0, n, 1.0);
+    if (a > 0) gemm(st, m, a, n, a, 1.0, TriL{Q, a}, 0, Dn{T1 + n, J}, sw, 0.0, CscRev{Zk, J, n, a}, ldz, false);
+  }
 }
 
 // Algorithm 3.2 (Cholesky product) for one big front: F = the children's
@@ -1067,6 +1129,47 @@ __global__ void __launch_bounds__(BT) mg_product(const double* Lc, double* X, in
   if (lane == 0) X[b] = c * c;
 }
 
+// Hessian factor (§5.4): M <-> W of a leaf group (n = 1, C = sqrt(d)):
+// dir 0: W_jj = d M_jj, W_Aj = Q^{-1} (C M_Aj); dir 1: M_jj = W_jj / d,
+// M_Aj = Q (W_Aj / C).  Q is the group's shared upper factor of V, held as
+// Q' = P Q P; the scaled A-rows go to the scratch P in reverse order.
+__global__ void __launch_bounds__(BT) mg_rscale(double* Z, int64_t ldz, const double* Lc, double* Pr, int64_t sP,
+                                                int dir, int64_t base0, int J, int L) {
+  LEAF_PROLOGUE
+  double* zz = Z + z * ldz + b;
+  const int a = J - 1;
+  double* pr = Pr + z * sP + (int64_t)i * a;
+  const double c = Lc[b];
+  const double s = dir == 0 ? c : 1.0 / c;
+  for (int q = 1 + lane; q < J; q += 32) pr[a - q] = zz[q] * s;
+  if (lane == 0) zz[0] *= s * s;
+}
+__global__ void __launch_bounds__(BT) mg_unreverse(double* Z, int64_t ldz, const double* Pr, int64_t sP,
+                                                   int64_t base0, int J, int L) {
+  LEAF_PROLOGUE
+  double* zz = Z + z * ldz + b;
+  const int a = J - 1;
+  const double* pr = Pr + z * sP + (int64_t)i * a;
+  for (int q = 1 + lane; q < J; q += 32) zz[q] = pr[a - q];
+}
+void group_rtrans(const chd_symbolic* s, const Ctx& st, int m, int g, int dir, const double* Lc, const double* Qd,
+                  double* Z, int64_t ldz, double* ws) {
+  const Group G = group(s, g);
+  const int64_t sw = s->dev.f_total;
+  const double* Q = Qd + G.v0;
+  double* P = ws + G.f1;  // a x L per RHS
+  mg_rscale<<<leaf_grid(G.L, m), BT, 0, st>>>(Z, ldz, Lc, P, sw, dir, G.base0, G.J, G.L);
+  chd_launch::count_launch();
+  if (dir == 0) {
+    trsm_rLT(st, m, G.L, G.a, DnTW{P, G.a}, sw, Q, G.a);
+    mg_unreverse<<<leaf_grid(G.L, m), BT, 0, st>>>(Z, ldz, P, sw, G.base0, G.J, G.L);
+    chd_launch::count_launch();
+  } else {
+    gemm(st, m, G.a, G.L, G.a, 1.0, TriL{Q, G.a}, 0, Dn{P, G.a}, sw, 0.0, DnRev{Z + G.base0 + 1, G.J, G.a}, ldz,
+         false);
+  }
+}
+
 // per-group sequences
 void group_product(const chd_symbolic* s, const Ctx& st, int g, const double* Lc, double* X, double* ws) {
   const Group G = group(s, g);
@@ -1218,6 +1321,12 @@ void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xc
   if (s->grp_of[k] >= 0) return chd::big::group_complete(s, chd::big::make_ctx(st, xs, xcap), s->grp_of[k], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
   chd::big::complete_front(s, chd::big::make_ctx(st, xs, xcap), k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
 }
+void big_rtrans(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, int dir,
+                const double* Lc, const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws) {
+  (void)Dd;
+  if (s->grp_of[k] >= 0) return chd::big::group_rtrans(s, chd::big::make_ctx(st, xs, xcap), m, s->grp_of[k], dir, Lc, Qd, Z, ldz, ws);
+  chd::big::rtrans_front(s, chd::big::make_ctx(st, xs, xcap), m, k, dir, Lc, Qd, Z, ldz, ws);
+}
 void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* ws) {
   if (s->grp_of[k] >= 0) return;  // a leaf group reads S itself
   chd::big::complete_load_front(s, chd::big::make_ctx(st, nullptr, 0), k, Sin, ws);
@@ -1225,7 +1334,7 @@ void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const doub
 // Cholesky factor R of the cached V_k = S_{A_k A_k} of one big front (lower,
 // into Rd); the inverse-Hessian steps apply V^{-1} by triangular solves.
 void big_inv_v(const chd_symbolic* s, cudaStream_t stream, double* xs, int64_t xcap, int k, const double* Vd,
-               double* Rd, double* ws, int64_t* status) {
+               double* Rd, double* Qd, double* ws, int64_t* status) {
   using namespace chd::big;
   const Ctx st = chd::big::make_ctx(stream, xs, xcap);
   const int n = (int)(s->sn_ptr[k + 1] - s->sn_ptr[k]);
@@ -1234,5 +1343,10 @@ void big_inv_v(const chd_symbolic* s, cudaStream_t stream, double* xs, int64_t x
   double* R = Rd + s->v_off[k];
   CHD_EW(mk_copy, (int64_t)a * a, 1, st, R, 0, a, Vd + s->v_off[k], 0, a, a, a, 1.0, 0.0, 1, 0);
   potrf_partial(st, R, a, a, a, status, CHD_ERR_NOT_PD, k, -1);
+  // the upper factor Q of V = Q Q^T (Hessian factor, §5.4), held as
+  // Q' = chol(P V P) = P Q P
+  double* Qk = Qd + s->v_off[k];
+  CHD_EW(mk_rev_lower, (int64_t)a * a, 1, st, Qk, Vd + s->v_off[k], a);
+  potrf_partial(st, Qk, a, a, a, status, CHD_ERR_NOT_PD, k, -1);
 }
 }  // namespace chd_launch

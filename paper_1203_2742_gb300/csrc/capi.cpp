@@ -25,8 +25,14 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
                  double* ws);
 void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Sin, double* Lc,
               double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
-void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* ws,
-           int64_t* status);
+void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* Qd,
+           double* ws, int64_t* status);
+void hess_up_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Vd,
+                  const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
+void hess_down_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, double* T,
+                    int64_t ldt, double* ws);
+void rtrans(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, int dir, const double* Lc,
+            const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws);
 void product(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Lc, double* X, double* ws);
 int64_t schur_scratch(const chd_symbolic* s, int m);
 void schur(const chd_symbolic* s, cudaStream_t st, int m, const double* A, int64_t lda, const double* T, int64_t ldt,
@@ -70,6 +76,7 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
   const size_t oDd = off; off = align_up(off + (size_t)s->d_off[s->nsn] * 8);
   const size_t oVd = off; off = align_up(off + (size_t)s->v_off[s->nsn] * 8);
   const size_t oRd = off; off = align_up(off + (size_t)s->v_off[s->nsn] * 8);
+  const size_t oQd = off; off = align_up(off + (size_t)s->v_off[s->nsn] * 8);
   const size_t old = off; off = align_up(off + (size_t)s->nsn * 8);
   const size_t osc = off; off = align_up(off + 4 * 8);
   const size_t ost = off; off = align_up(off + 4 * 8);
@@ -95,6 +102,7 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
   f->Dd = reinterpret_cast<double*>(b + oDd);
   f->Vd = reinterpret_cast<double*>(b + oVd);
   f->Rd = reinterpret_cast<double*>(b + oRd);
+  f->Qd = reinterpret_cast<double*>(b + oQd);
   f->ldet = reinterpret_cast<double*>(b + old);
   f->scalar = reinterpret_cast<double*>(b + osc);
   f->status = reinterpret_cast<int64_t*>(b + ost);
@@ -245,6 +253,17 @@ chd_status ensure_projected_inverse(chd_factor* f) {
     chd_launch::gradient(f->sym, st, &f->ex, f->Wc, f->Sc, nullptr, f->Vd, f->ws);
   });
   if (rc == CHD_OK) f->have_S = true;
+  return rc;
+}
+
+// chol(V_k) (Qd) and V_k^{-1} or its factor (Rd) of every front, once per
+// factor; needs the projected inverse.
+chd_status ensure_inv_v(chd_factor* f) {
+  if (f->have_R) return CHD_OK;
+  chd_status rc = run_sequence(f, G_INV_V, GraphKey{}, [&](cudaStream_t st) {
+    chd_launch::inv_v(f->sym, st, &f->ex, f->Vd, f->Rd, f->Qd, f->ws, f->status);
+  });
+  if (rc == CHD_OK) f->have_R = true;
   return rc;
 }
 
@@ -504,6 +523,71 @@ chd_status chd_hessian(chd_factor* f, int m, const double* y, int64_t ldy, doubl
   return CHD_OK;
 }
 
+chd_status chd_hessian_factor(chd_factor* f, int m, const double* y, int64_t ldy, double* w, int64_t ldw,
+                              void* stream) {
+  if (!f || m < 0 || (m > 0 && (!y || !w))) return CHD_ERR_INVALID;
+  const int64_t nnz = f->sym->colptr[f->sym->n];
+  if (m > 1 && (ldy < nnz || ldw < nnz)) return CHD_ERR_INVALID;
+  if (m == 0) return CHD_OK;
+  f->stream = static_cast<cudaStream_t>(stream);
+  chd_status rc = ensure_projected_inverse(f);
+  if (rc != CHD_OK) return rc;
+  const int64_t chunk = rhs_chunk(f, m);
+  rc = ensure_ws(f, chunk);
+  if (rc == CHD_OK) rc = ensure_inv_v(f);
+  if (rc != CHD_OK) return rc;
+  for (int64_t i = 0; i < m; i += chunk) {
+    const int mc = (int)std::min<int64_t>(chunk, m - i);
+    GraphKey key;
+    key.p[0] = y + i * ldy;
+    key.p[1] = w + i * ldw;
+    key.v[0] = mc;
+    key.v[1] = ldy;
+    key.v[2] = ldw;
+    rc = run_sequence(f, G_HFACTOR, key, [&](cudaStream_t st) {
+      chd_launch::hess_up_pass(f->sym, st, &f->ex, mc, f->Wc, f->Vd, y + i * ldy, ldy, w + i * ldw, ldw, f->ws);
+      chd_launch::rtrans(f->sym, st, &f->ex, mc, 0, f->Lc, f->Dd, f->Qd, w + i * ldw, ldw, f->ws);
+    });
+    if (rc != CHD_OK) return rc;
+  }
+  return CHD_OK;
+}
+
+chd_status chd_hessian_factor_adj(chd_factor* f, int m, const double* w, int64_t ldw, double* t, int64_t ldt,
+                                  void* stream) {
+  if (!f || m < 0 || (m > 0 && (!w || !t))) return CHD_ERR_INVALID;
+  const int64_t nnz = f->sym->colptr[f->sym->n];
+  if (m > 1 && (ldw < nnz || ldt < nnz)) return CHD_ERR_INVALID;
+  if (m == 0) return CHD_OK;
+  f->stream = static_cast<cudaStream_t>(stream);
+  chd_status rc = ensure_projected_inverse(f);
+  if (rc != CHD_OK) return rc;
+  const int64_t chunk = rhs_chunk(f, m);
+  rc = ensure_ws(f, chunk);
+  if (rc == CHD_OK) rc = ensure_inv_v(f);
+  if (rc != CHD_OK) return rc;
+  for (int64_t i = 0; i < m; i += chunk) {
+    const int mc = (int)std::min<int64_t>(chunk, m - i);
+    GraphKey key;
+    key.p[0] = w + i * ldw;
+    key.p[1] = t + i * ldt;
+    key.v[0] = mc;
+    key.v[1] = ldw;
+    key.v[2] = ldt;
+    double* ti = t + i * ldt;
+    const double* wi = w + i * ldw;
+    rc = run_sequence(f, G_HFACTOR_ADJ, key, [&](cudaStream_t st) {
+      if (ti != wi)
+        cudaMemcpy2DAsync(ti, (size_t)(mc > 1 ? ldt : nnz) * 8, wi, (size_t)(mc > 1 ? ldw : nnz) * 8,
+                          (size_t)nnz * 8, (size_t)mc, cudaMemcpyDeviceToDevice, st);
+      chd_launch::rtrans(f->sym, st, &f->ex, mc, 1, f->Lc, f->Dd, f->Qd, ti, ldt, f->ws);
+      chd_launch::hess_down_pass(f->sym, st, &f->ex, mc, f->Wc, ti, ldt, f->ws);
+    });
+    if (rc != CHD_OK) return rc;
+  }
+  return CHD_OK;
+}
+
 chd_status chd_inv_hessian(chd_factor* f, int m, const double* t, int64_t ldt, double* y, int64_t ldy,
                            void* stream) {
   if (!f || m < 0 || (m > 0 && (!y || !t))) return CHD_ERR_INVALID;
@@ -516,13 +600,8 @@ chd_status chd_inv_hessian(chd_factor* f, int m, const double* t, int64_t ldt, d
   const int64_t chunk = rhs_chunk(f, m);
   rc = ensure_ws(f, chunk);
   if (rc != CHD_OK) return rc;
-  if (!f->have_R) {  // V_k^{-1} of every front, once per factor
-    rc = run_sequence(f, G_INV_V, GraphKey{}, [&](cudaStream_t st) {
-      chd_launch::inv_v(f->sym, st, &f->ex, f->Vd, f->Rd, f->ws, f->status);
-    });
-    if (rc != CHD_OK) return rc;
-    f->have_R = true;
-  }
+  rc = ensure_inv_v(f);
+  if (rc != CHD_OK) return rc;
   for (int64_t i = 0; i < m; i += chunk) {
     const int mc = (int)std::min<int64_t>(chunk, m - i);
     GraphKey key;
@@ -737,6 +816,7 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   size_t iSf = add(s->small_fronts.data(), s->small_fronts.size() * 4);
   size_t iCf = add(s->cta_fronts.data(), s->cta_fronts.size() * 4);
   size_t iWf = add(s->warp_fronts.data(), s->warp_fronts.size() * 4);
+  size_t iPf = add(s->plain_fronts.data(), s->plain_fronts.size() * 4);
   size_t iIs = add(s->inst_sn.data(), s->inst_sn.size() * 8);
   std::vector<char> host(off, 0);
   for (auto& p : pcs)
@@ -795,6 +875,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   d.cta_count = (int64_t)s->cta_fronts.size();
   d.warp_fronts = reinterpret_cast<const int32_t*>(b + pcs[iWf].off);
   d.warp_count = (int64_t)s->warp_fronts.size();
+  d.plain_fronts = reinterpret_cast<const int32_t*>(b + pcs[iPf].off);
+  d.plain_count = (int64_t)s->plain_fronts.size();
   d.inst_sn = reinterpret_cast<const int64_t*>(b + pcs[iIs].off);
   d.ninst = (int64_t)s->inst_sn.size() - 1;
   d.f_total = s->f_off[s->nsn];

@@ -54,6 +54,8 @@ struct SymDev {
   int64_t cta_count = 0;
   const int32_t* warp_fronts = nullptr;   // fronts of the warp tier
   int64_t warp_count = 0;
+  const int32_t* plain_fronts = nullptr;  // fronts of the warp, wide and CTA tiers (no dense, no group)
+  int64_t plain_count = 0;
   const int64_t* inst_sn = nullptr;       // instances x supernode ranges
   int64_t ninst = 1;
   int64_t f_total = 0;               // workspace doubles per right-hand side
@@ -97,6 +99,7 @@ struct chd_symbolic {
   std::vector<int32_t> cta_fronts;
   std::vector<int32_t> warp_fronts;
   std::vector<int32_t> big_fronts;
+  std::vector<int32_t> plain_fronts;
   double flops[5] = {0, 0, 0, 0, 0};
   // independent instances analysed together (chd_analyze_batch): instance i
   // owns columns [inst_n[i], inst_n[i+1]), values [inst_nnz[i], inst_nnz[i+1])
@@ -144,7 +147,18 @@ struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0;
 };
-enum GraphKind { G_FACTOR = 0, G_GRADIENT, G_HESSIAN, G_INV_HESSIAN, G_INV_V, G_COMPLETE, G_PRODUCT, G_KINDS };
+enum GraphKind {
+  G_FACTOR = 0,
+  G_GRADIENT,
+  G_HESSIAN,
+  G_INV_HESSIAN,
+  G_INV_V,
+  G_COMPLETE,
+  G_PRODUCT,
+  G_HFACTOR,
+  G_HFACTOR_ADJ,
+  G_KINDS
+};
 
 // A factor object: device-resident factor blocks, cached projected inverse
 // and the per-right-hand-side front workspace (all owned by the object).
@@ -158,6 +172,7 @@ struct chd_factor {
   double* Dd = nullptr;
   double* Vd = nullptr;
   double* Rd = nullptr;      // per front, once have_R: V_k^{-1} (lower), or chol(V_k) for dense-tier fronts
+  double* Qd = nullptr;      // per front, once have_R: chol(V_k) (lower; Hessian factor R, §5.4)
   double* ldet = nullptr;
   double* scalar = nullptr;  // [0] log det
   int64_t* status = nullptr; // [0] code, [1] supernode, [2] column

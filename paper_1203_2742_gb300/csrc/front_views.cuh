@@ -82,6 +82,23 @@ struct CscSym {  // symmetric N x N block stored lower in CSC
   }
 };
 
+// rows in reverse order: (r, c) -> B(R - 1 - r, c); with Q' = P Q P (P the
+// order reversal) products and solves with an upper triangular Q become
+// lower triangular ones on the reversed rows
+struct DnRev {
+  double* p;
+  int64_t ld;
+  int R;
+  __device__ double& at(int r, int c) const { return p[(R - 1 - r) + (int64_t)c * ld]; }
+};
+struct CscRev {  // rows r0 .. r0 + R - 1 of the N-part, in reverse order
+  double* p;
+  int J;
+  int r0;
+  int R;
+  __device__ double& at(int r, int c) const { return p[csc_off(J, r0 + R - 1 - r, c)]; }
+};
+
 // transposed writable view: (r, c) -> B(c, r)
 struct DnTW {
   double* p;

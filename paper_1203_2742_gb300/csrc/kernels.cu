@@ -490,6 +490,61 @@ __device__ void hess_up_front(const SymDev& S, int k, const double* Wc, const do
   cta_gemm(a, n, a, 1.0, SymL{Vd + S.v_off[k], a}, Dn{f.T2 + n, J}, 0.0, Csc{T + f.base, J, n}, false);
 }
 
+// Hessian factor (§5.4, block form).  Step 2 of Algorithm 5.1 maps K to
+// M = (D^{-1} K_NN D^{-1}, V K_AN D^{-1}).  With D = C C^T (C the lower
+// Cholesky factor of the factor's D_NN) and V = Q Q^T (Q upper triangular,
+// the factor §5.4 prescribes), W = R(Y) ends with W_NN = C^{-1} K_NN C^{-T},
+// W_AN = Q^T K_AN C^{-T}: for a supernode this equals the per-column
+// formulas of Algorithm 5.3, since C = L_NN D_NN^{1/2} in terms of the
+// scalar factors and the R_j of the columns of N_k are trailing blocks of
+// the upper factor of S_{J_k J_k}.  In terms of M: W_NN = C^T M_NN C,
+// W_AN = Q^{-1} M_AN C; and R^adj starts with M_NN = C^{-T} W_NN C^{-1},
+// M_AN = Q W_AN C^{-1}.  Q is held as Q' = P Q P (lower, P the order
+// reversal), applied to the A-rows in reverse order.  dir = 0: M -> W,
+// 1: W -> M, in place on the front's N-part of `Z` (one right-hand side).
+__device__ void rtrans_front(const SymDev& S, int k, int dir, const double* Lc, const double* Qd, double* Z,
+                             double* ws) {
+  FrontInfo f = front_info(S, k, ws);
+  const int J = f.J, n = f.n, a = f.a;
+  const double* Q = Qd + S.v_off[k];
+  double* C = f.T2;  // n x n, ld J, lower: C from the factor
+  double* B = f.T1;  // J x n, ld J: the N-part of Z (NN block full, A-rows reversed for dir 1)
+  for (int e = threadIdx.x; e < n * n; e += NT) {
+    const int r = e % n, c = e / n;
+    C[r + (int64_t)c * J] = r >= c ? Lc[f.base + csc_off(J, r, c)] : 0.0;
+  }
+  for (int e = threadIdx.x; e < J * n; e += NT) {
+    const int r = e % J, c = e / J;
+    const int rb = (dir == 1 && r >= n) ? n + a - 1 - (r - n) : r;
+    B[rb + (int64_t)c * J] = Z[f.base + (r >= c ? csc_off(J, r, c) : csc_off(J, c, r))];
+  }
+  __syncthreads();
+  if (dir == 0) {
+    // W_NN = C^T (M_NN C);  W_AN = Q^{-1} (M_AN C) = P Q'^{-1} P (M_AN C)
+    cta_gemm(n, n, n, 1.0, Dn{B, J}, TriL{C, J}, 0.0, Dn{f.F, J}, false);
+    cta_gemm(n, n, n, 1.0, TriLT{C, J}, Dn{f.F, J}, 0.0, Csc{Z + f.base, J, 0}, true);
+    if (a > 0) {
+      cta_gemm(a, n, n, 1.0, Dn{B + n, J}, TriL{C, J}, 0.0, DnRev{f.F + n, J, a}, false);
+      cta_trsm_rLT(n, a, DnTW{f.F + n, J}, Q, a);
+      for (int e = threadIdx.x; e < a * n; e += NT) {
+        const int r = e % a, c = e / a;
+        Z[f.base + csc_off(J, n + r, c)] = f.F[(n + a - 1 - r) + (int64_t)c * J];
+      }
+    }
+  } else {
+    // M_NN = C^{-T} (W_NN C^{-1});  M_AN = Q (W_AN C^{-1}) = P Q' P (W_AN C^{-1})
+    cta_trsm_rL(J, n, Dn{B, J}, C, J);
+    cta_trsm_rL(n, n, DnTW{B, J}, C, J);
+    for (int e = threadIdx.x; e < n * n; e += NT) {
+      const int r = e % n, c = e / n;
+      if (r >= c) Z[f.base + csc_off(J, r, c)] = B[r + (int64_t)c * J];
+    }
+    if (a > 0)
+      cta_gemm(a, n, a, 1.0, TriL{Q, a}, Dn{B + n, J}, 0.0, CscRev{Z + f.base, J, n, a}, false);
+  }
+  __syncthreads();
+}
+
 // Algorithm 5.1 step 3 (block form): V' gathered from the parent,
 // T_AN = M_AN - V' L, T_NN = M_NN - M_AN^T L - L^T T_AN.
 __device__ void hess_down_front(const SymDev& S, int k, const double* Wc, double* T, double* ws) {
@@ -722,6 +777,12 @@ __global__ void __launch_bounds__(NT) k_ihess_up(SymDev S, int task0, const doub
   for (int q = S.task_ptr[t]; q < S.task_ptr[t + 1]; ++q)
     ihess_up_front(S, S.task_fronts[q], Wc, Y + y * ldy, ws + y * S.f_total);
 }
+// M <-> W of every front of the warp and CTA tiers, one CTA per (front, RHS)
+__global__ void __launch_bounds__(NT) k_rtrans(SymDev S, int dir, const double* Lc, const double* Qd, double* Z,
+                                               int64_t ldz, double* ws) {
+  const int64_t y = blockIdx.y;
+  rtrans_front(S, S.plain_fronts[blockIdx.x], dir, Lc, Qd, Z + y * ldz, ws + y * S.f_total);
+}
 // all CTA-tier fronts at once, one CTA each
 __global__ void __launch_bounds__(NT) k_complete(SymDev S, const double* Sin, double* Lc, double* Wc, double* Dd,
                                                  double* Vd, double* Rd, double* ws, double* ldet, int64_t* st) {
@@ -732,17 +793,26 @@ __global__ void __launch_bounds__(NT) k_complete(SymDev S, const double* Sin, do
 // Inverses of the cached V_k (inverse Hessian step 2), one CTA per front of
 // `front_list` (no dependencies between fronts; big fronts use the dense
 // tier): R = chol(V), R^{-1} in the front's workspace, V^{-1} = R^{-T} R^{-1}.
-__global__ void __launch_bounds__(NT) k_inv_v(SymDev S, const double* Vd, double* Rd, double* ws, int64_t* st,
-                                              const int32_t* front_list) {
+__global__ void __launch_bounds__(NT) k_inv_v(SymDev S, const double* Vd, double* Rd, double* Qd, double* ws,
+                                              int64_t* st, const int32_t* front_list) {
   const int k = front_list[blockIdx.x];
   const int n = (int)(S.sn_ptr[k + 1] - S.sn_ptr[k]);
   const int a = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]) - n;
   if (a == 0) return;
   double* R = Rd + S.v_off[k];
   double* Ri = ws + S.f_off[k];  // a x a scratch inside the front's J x J region
-  copy_lower(R, a, Vd + S.v_off[k], a, a);
+  const double* V = Vd + S.v_off[k];
+  // Hessian factor (§5.4): V = Q Q^T with Q upper triangular, kept as
+  // Q' = chol(P V P) = P Q P, P the order reversal
+  double* Qk = Qd + S.v_off[k];
+  for (int e = threadIdx.x; e < a * a; e += NT) {
+    const int r = e % a, c = e / a;
+    if (r >= c) Qk[r + (int64_t)c * a] = V[(a - 1 - c) + (int64_t)(a - 1 - r) * a];
+  }
+  copy_lower(R, a, V, a, a);
   set_identity(Ri, a, a);
   __syncthreads();
+  cta_potrf_partial(Qk, a, a, a, st, CHD_ERR_NOT_PD, k, -1);
   cta_potrf_partial(R, a, a, a, st, CHD_ERR_NOT_PD, k, -1);
   cta_trsm_rLT(a, a, DnTW{Ri, a}, R, a);  // Ri = R^{-1}
   cta_gemm(a, a, a, 1.0, TriLT{Ri, a}, TriL{Ri, a}, 0.0, Dn{R, a}, true);
@@ -1025,8 +1095,8 @@ void gradient(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
     bf.join_now();
   }
 }
-void hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Vd,
-             const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
+void hess_up_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Vd,
+                  const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
   const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = 0; l < nl; ++l) {
     Level v = level(s, l);
@@ -1042,6 +1112,10 @@ void hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, cons
     }
     bf.join_now();
   }
+}
+void hess_down_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, double* T,
+                    int64_t ldt, double* ws) {
+  const int nl = (int)s->lvl_ptr.size() - 1;
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
     BigFork bf{ex, st};
@@ -1056,6 +1130,29 @@ void hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, cons
     if (v.nw64) w64::warp_hess_down(s, st, v.tw, v.nw64, m, Wc, T, ldt, ws);
     bf.join_now();
   }
+}
+void hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Vd,
+             const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
+  hess_up_pass(s, st, ex, m, Wc, Vd, Y, ldy, T, ldt, ws);
+  hess_down_pass(s, st, ex, m, Wc, T, ldt, ws);
+}
+// M <-> W for every front (independent fronts): plain fronts in one launch,
+// dense fronts and leaf groups on the side streams
+void big_rtrans(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, int dir,
+                const double* Lc, const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws);
+void rtrans(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, int dir, const double* Lc,
+            const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws) {
+  std::vector<int32_t> dense = s->big_fronts;
+  for (int64_t g0 : s->grp_first) dense.push_back((int32_t)g0);
+  BigFork bf{ex, st};
+  bf.run((int)dense.size(), [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
+    big_rtrans(s, bs, xs, xc, m, dense[i], dir, Lc, Dd, Qd, Z, ldz, ws);
+  });
+  if (s->dev.plain_count > 0) {
+    k_rtrans<<<dim3((unsigned)s->dev.plain_count, m), NT, 0, st>>>(s->dev, dir, Lc, Qd, Z, ldz, ws);
+    count();
+  }
+  bf.join_now();
 }
 void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Dd,
                  const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy, double* ws) {
@@ -1111,18 +1208,18 @@ void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
   bf.join_now();
 }
 void big_inv_v(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Vd,
-               double* Rd, double* ws, int64_t* status);
-void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* ws,
-           int64_t* status) {
+               double* Rd, double* Qd, double* ws, int64_t* status);
+void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* Qd,
+           double* ws, int64_t* status) {
   std::vector<int> bigs;
   for (int64_t k = 0; k < s->nsn; ++k)
     if (s->is_big[k]) bigs.push_back((int)k);
   BigFork bf{ex, st};
   bf.run((int)bigs.size(), [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-    big_inv_v(s, bs, xs, xc, bigs[i], Vd, Rd, ws, status);
+    big_inv_v(s, bs, xs, xc, bigs[i], Vd, Rd, Qd, ws, status);
   });
   if (s->dev.small_count > 0) {
-    k_inv_v<<<(int)s->dev.small_count, NT, 0, st>>>(s->dev, Vd, Rd, ws, status, s->dev.small_fronts);
+    k_inv_v<<<(int)s->dev.small_count, NT, 0, st>>>(s->dev, Vd, Rd, Qd, ws, status, s->dev.small_fronts);
     count();
   }
   bf.join_now();

@@ -594,6 +594,7 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     s->cta_fronts.clear();
     s->warp_fronts.clear();
     s->big_fronts.clear();
+    s->plain_fronts.clear();
     for (int64_t t = 0; t < nsn; ++t) {
       // V^{-1} per front (a group's members share their first member's)
       const bool member = s->grp_of[t] >= 0 && s->grp_first[s->grp_of[t]] != t;
@@ -601,6 +602,7 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
       if (tier[t] == 0) s->warp_fronts.push_back((int32_t)t);
       if (tier[t] == 1 || tier[t] == 3) s->cta_fronts.push_back((int32_t)t);
       if (tier[t] == 2) s->big_fronts.push_back((int32_t)t);
+      if (tier[t] == 0 || tier[t] == 1 || tier[t] == 3) s->plain_fronts.push_back((int32_t)t);
     }
     vector<double> W(nsn, 0.0);
     double total = 0;

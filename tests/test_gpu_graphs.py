@@ -27,6 +27,8 @@ def _run_all(B, sym, x, ys, s, graphs, reps):
     g = torch.empty_like(xd)
     t = torch.empty_like(yd)
     yi = torch.empty_like(yd)
+    w = torch.empty_like(yd)
+    ta = torch.empty_like(yd)
     out = []
     for _ in range(reps):
         l0 = B.chd_kernel_launches()
@@ -34,11 +36,14 @@ def _run_all(B, sym, x, ys, s, graphs, reps):
         fac.gradient(out=g)
         fac.hessian(yd, out=t)
         fac.inv_hessian(yd, out=yi)
+        fac.hessian_factor(yd, out=w)
+        fac.hessian_factor_adj(w, out=ta)
         cfac.recomplete(sd, want_fstar=False)
         lx, dx = cfac.export()
         torch.cuda.synchronize()
         out.append(dict(logdet=fac.logdet(), g=g.cpu().numpy().copy(), t=t.cpu().numpy().copy(),
                         yi=yi.cpu().numpy().copy(), lx=lx.cpu().numpy().copy(), dx=dx.cpu().numpy().copy(),
+                        w=w.cpu().numpy().copy(), ta=ta.cpu().numpy().copy(),
                         launches=B.chd_kernel_launches() - l0))
     return out
 
@@ -59,7 +64,7 @@ def test_graph_replays_are_bitwise_direct_runs(case):
     direct = _run_all(B, sym, x, ys, s, graphs=False, reps=1)[0]
     replayed = _run_all(B, sym, x, ys, s, graphs=True, reps=4)
     for r in replayed:
-        for key in ("g", "t", "yi", "lx", "dx"):
+        for key in ("g", "t", "yi", "lx", "dx", "w", "ta"):
             assert np.array_equal(r[key], direct[key]), key
         assert r["logdet"] == direct["logdet"]
     # replays count the kernels the graph runs: the same as a direct call

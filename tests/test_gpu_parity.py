@@ -178,6 +178,46 @@ def test_cholesky_product(name):
     assert c.err(c.host(fx.product()), xh) < TOL
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_hessian_factor(name):
+    """W = R(Y) (Algorithm 5.3, R_j upper) and T = R^adj(W) (Algorithm 5.4)
+    against the oracle's per-column definitions; R^adj(R(Y)) = H(Y)."""
+    c = CASES[name]()
+    f = c.sym.factor(c.dev(c.x))
+    ys = W.uniform_sym(c.n, c.cp, c.ri, c.rng, count=3)
+    ws = W.uniform_sym(c.n, c.cp, c.ri, c.rng, count=2)
+    parts = OD.hessian_factor_parts(c.n, c.cp, c.ri, c.x)
+    w = f.hessian_factor(c.dev(ys))
+    want_w = OD.hessian_factor(c.n, c.cp, c.ri, c.x, list(ys), parts=parts)
+    wh = c.host(w)
+    for i in range(3):
+        assert c.err(wh[i], want_w[i]) < TOL
+    # R^adj o R = H, computed in place
+    t = c.host(f.hessian_factor_adj(w, out=w))
+    want_t = OD.hessian(c.n, c.cp, c.ri, c.x, list(ys))
+    for i in range(3):
+        assert c.err(t[i], want_t[i]) < TOL
+    # R^adj of unrelated W, out of place
+    ta = c.host(f.hessian_factor_adj(c.dev(ws)))
+    want_a = OD.hessian_factor_adj(c.n, c.cp, c.ri, c.x, list(ws), parts=parts)
+    for i in range(2):
+        assert c.err(ta[i], want_a[i]) < TOL
+
+
+@pytest.mark.parametrize("name", ["grid14_nd", "dense_tier_er", "arrow150_w48", "wide_front"])
+def test_schur_by_hessian_factor(name):
+    """H_ij = R(A_i) . R(A_j) (§5.4) equals A_i . H(A_j)."""
+    c = CASES[name]()
+    m = 6
+    A = W.uniform_sym(c.n, c.cp, c.ri, c.rng, count=m)
+    f = c.sym.factor(c.dev(c.x))
+    R = c.host(f.hessian_factor(c.dev(A)))
+    got = np.array([[OD.sym_dot(c.n, c.cp, c.ri, R[i], R[j]) for j in range(m)] for i in range(m)])
+    Th = OD.hessian(c.n, c.cp, c.ri, c.x, list(A))
+    want = np.array([[OD.sym_dot(c.n, c.cp, c.ri, A[i], Th[j]) for j in range(m)] for i in range(m)])
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+
+
 @pytest.mark.parametrize("name", ["grid14_nd", "er300_mindeg_relax16", "dense_tier_er", "arrow150_w48"])
 def test_schur_complement(name):
     """H_ij = A_i . H(A_j) (§5.5) against the oracle's Hessian and inner product."""
