@@ -229,6 +229,18 @@ chd_status chd_hessian_factor_adj(chd_factor* fac, int m, const double* w_dev, i
                                   double* t_dev, int64_t ldt, void* stream);
 
 /*
+ * R(Y) for sparse arguments (§5.5): the same result as chd_hessian_factor,
+ * computed per right-hand side only on the fronts whose subtrees of the
+ * clique tree hold a nonzero of Y (a front whose descendants' columns of Y
+ * are all zero has K = 0, U' = 0 and W = 0 there).  Meant for Y with few
+ * nonzeros relative to V, such as the constraint matrices A_i of a cone
+ * program.  Holds nsn * 5 bytes per right-hand side of extra device
+ * scratch.  Arguments, errors and overlap rules as chd_hessian_factor.
+ */
+chd_status chd_hessian_factor_sparse(chd_factor* fac, int m, const double* y_dev, int64_t ldy,
+                                     double* w_dev, int64_t ldw, void* stream);
+
+/*
  * Inverse-Hessian products Y_i = H^{-1}(T_i) (§5.3, Algorithm 5.2 in
  * supernodal block form): the solution in S^n_V of P(X^{-1} Y X^{-1}) = T.
  * Uses cached Cholesky factors of V_k = S_{A_k A_k}.

@@ -88,7 +88,7 @@ _lib.chd_product.argtypes = [_p, _p, _p]
 _lib.chd_product.restype = C.c_int
 _lib.chd_schur.argtypes = [_p, C.c_int, _p, C.c_int64, _p, C.c_int64, _p, _p]
 _lib.chd_schur.restype = C.c_int
-for _f in ("chd_hessian_factor", "chd_hessian_factor_adj"):
+for _f in ("chd_hessian_factor", "chd_hessian_factor_adj", "chd_hessian_factor_sparse"):
     getattr(_lib, _f).argtypes = [_p, C.c_int, _p, _i64, _p, _i64, _p]
     getattr(_lib, _f).restype = C.c_int
 for _f in ("chd_analyze", "chd_analyze_batch", "chd_symbolic_batch_info", "chd_logdet_batch", "chd_symbolic_info", "chd_symbolic_supernodes", "chd_symbolic_flops",
@@ -308,6 +308,16 @@ def chd_hessian_factor(fac, y, w, nnz, stream=None):
            "chd_hessian_factor")
 
 
+def chd_hessian_factor_sparse(fac, y, w, nnz, stream=None):
+    """W = R(Y) with the clique tree pruned per Y (§5.5)."""
+    m, ldy = _batch(y, nnz, "y")
+    m2, ldw = _batch(w, nnz, "w")
+    if m != m2:
+        raise ValueError("y and w batch sizes differ")
+    _check(_lib.chd_hessian_factor_sparse(fac, m, _dptr(y, "y"), ldy, _dptr(w, "w"), ldw, _stream_ptr(stream)),
+           "chd_hessian_factor_sparse")
+
+
 def chd_hessian_factor_adj(fac, w, t, nnz, stream=None):
     """T = R^adj(W) (Algorithm 5.4)."""
     m, ldw = _batch(w, nnz, "w")
@@ -482,12 +492,13 @@ class Factor:
         chd_hessian(self._h, y, out, self.sym.nnz, stream)
         return out
 
-    def hessian_factor(self, y, out=None, stream=None):
-        """W = R(Y) with H = R^adj o R (Algorithm 5.3)."""
+    def hessian_factor(self, y, out=None, stream=None, sparse=False):
+        """W = R(Y) with H = R^adj o R (Algorithm 5.3); `sparse` prunes the
+        clique tree per Y (§5.5), for Y with few nonzeros."""
         import torch
         if out is None:
             out = torch.empty_like(y)
-        chd_hessian_factor(self._h, y, out, self.sym.nnz, stream)
+        (chd_hessian_factor_sparse if sparse else chd_hessian_factor)(self._h, y, out, self.sym.nnz, stream)
         return out
 
     def hessian_factor_adj(self, w, out=None, stream=None):

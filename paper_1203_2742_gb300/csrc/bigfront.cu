@@ -521,14 +521,17 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int v) {
   }
   return lo;
 }
-__global__ void __launch_bounds__(BT) mk_extend_add(SymDev S, int k, double* ws, int64_t sws, int tiles) {
+__global__ void __launch_bounds__(BT) mk_extend_add(SymDev S, int k, double* ws, int64_t sws, int tiles,
+                                                    const uint8_t* act) {
   const int tm = (blockIdx.x / tiles) * GT, tn = (blockIdx.x % tiles) * GT;
   if (tn > tm) return;
   ws += blockIdx.z * sws;
+  if (act) act += blockIdx.z * S.nsn;
   const int Jp = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]);
   double* F = ws + S.f_off[k];
   for (int64_t q = S.ea_ptr[k]; q < S.ea_ptr[k + 1]; ++q) {
     const int c = S.ea[q];
+    if (act && !act[c]) continue;  // pruned child (§5.5): its update block is zero
     const int nc = (int)(S.sn_ptr[c + 1] - S.sn_ptr[c]);
     const int Jc = (int)(S.rows_ptr[c + 1] - S.rows_ptr[c]);
     const int ac = Jc - nc;
@@ -630,11 +633,12 @@ inline Front front(const chd_symbolic* s, int k) {
   return f;
 }
 
-void assemble_children(const chd_symbolic* s, const Ctx& st, int batch, int k, double* ws, int64_t sws) {
+void assemble_children(const chd_symbolic* s, const Ctx& st, int batch, int k, double* ws, int64_t sws,
+                       const uint8_t* act = nullptr) {
   if (s->ea_ptr[k + 1] == s->ea_ptr[k]) return;
   const int J = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k]);
   const int t = (J + GT - 1) / GT;
-  mk_extend_add<<<dim3(t * t, 1, batch), BT, 0, st>>>(s->dev, k, ws, sws, t);
+  mk_extend_add<<<dim3(t * t, 1, batch), BT, 0, st>>>(s->dev, k, ws, sws, t, act);
   chd_launch::count_launch();
 }
 void gather_parent(const chd_symbolic* s, const Ctx& st, int batch, const Front& f, double* ws, int64_t sws) {
@@ -684,7 +688,7 @@ void gradient_front(const chd_symbolic* s, const Ctx& st, int k, const double* W
 }
 
 void hess_up_front(const chd_symbolic* s, const Ctx& st, int m, int k, const double* Wc, const double* Vd,
-                   const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
+                   const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws, const uint8_t* act) {
   Front f = front(s, k);
   const int J = f.J, n = f.n, a = f.a;
   const int64_t sw = s->dev.f_total;
@@ -695,7 +699,7 @@ void hess_up_front(const chd_symbolic* s, const Ctx& st, int m, int k, const dou
   CscRO L{W, J, n};
   CHD_EW(mk_csc_to_front, (int64_t)J * n, m, st, F, sw, J, n, Y + f.base, ldy);
   if (a > 0) CHD_EW(mk_copy, (int64_t)a * a, m, st, F + n + (int64_t)n * J, sw, J, nullptr, 0, 0, a, a, 0.0, 0.0, 1, 0);
-  assemble_children(s, st, m, k, ws, sw);
+  assemble_children(s, st, m, k, ws, sw, act);
   if (a > 0) {
     CHD_EW(mk_copy, (int64_t)a * n, m, st, T1 + n, sw, J, F + n, sw, J, a, n, 1.0, 0.0, 0, 0);
     gemm(st, m, a, n, n, -1.0, L, 0, SymL{F, J}, sw, 1.0, Dn{T1 + n, J}, sw, false);
@@ -1295,9 +1299,13 @@ void big_gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xc
   chd::big::gradient_front(s, chd::big::make_ctx(st, xs, xcap), k, Wc, Sc, g, Vd, ws);
 }
 void big_hess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
-                 const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
+                 const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws,
+                 const uint8_t* act) {
+  // a leaf group has no children; with `act` (pruned Hessian factor) a dense
+  // front still runs, skipping pruned children, and gives exact zeros where
+  // its own subtree is pruned
   if (s->grp_of[k] >= 0) return chd::big::group_hess_up(s, chd::big::make_ctx(st, xs, xcap), m, s->grp_of[k], Wc, Vd, Y, ldy, T, ldt, ws);
-  chd::big::hess_up_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, Vd, Y, ldy, T, ldt, ws);
+  chd::big::hess_up_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, Vd, Y, ldy, T, ldt, ws, act);
 }
 void big_hess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
                    double* T, int64_t ldt, double* ws) {

@@ -28,11 +28,13 @@ void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
 void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* Qd,
            double* ws, int64_t* status);
 void hess_up_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Vd,
-                  const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
+                  const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws, const uint8_t* act);
+void prune_mask(const chd_symbolic* s, cudaStream_t st, int m, const double* Y, int64_t ldy, int32_t* cnt,
+                uint8_t* act);
 void hess_down_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, double* T,
                     int64_t ldt, double* ws);
 void rtrans(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, int dir, const double* Lc,
-            const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws);
+            const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws, const uint8_t* act);
 void product(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Lc, double* X, double* ws);
 int64_t schur_scratch(const chd_symbolic* s, int m);
 void schur(const chd_symbolic* s, cudaStream_t st, int m, const double* A, int64_t lda, const double* T, int64_t ldt,
@@ -153,6 +155,24 @@ chd_status ensure_ws(chd_factor* f, int64_t rhs) {
   if (rc != CHD_OK) return rc;
   f->ws = static_cast<double*>(p);
   f->ws_rhs = rhs;
+  return CHD_OK;
+}
+
+// per (right-hand side, front) counts and flags of the pruned Hessian factor
+chd_status ensure_act(chd_factor* f, int64_t rhs) {
+  if (f->act_rhs >= rhs) return CHD_OK;
+  if (f->act_buf) {
+    cudaStreamSynchronize(f->stream);
+    cudaFree(f->act_buf);
+    f->act_buf = nullptr;
+    f->act_rhs = 0;
+  }
+  void* p = nullptr;
+  const size_t bytes = (size_t)f->sym->nsn * 5 * (size_t)rhs;
+  chd_status rc = cuda_ok(cudaMalloc(&p, std::max<size_t>(bytes, 256)));
+  if (rc != CHD_OK) return rc;
+  f->act_buf = p;
+  f->act_rhs = rhs;
   return CHD_OK;
 }
 
@@ -523,8 +543,10 @@ chd_status chd_hessian(chd_factor* f, int m, const double* y, int64_t ldy, doubl
   return CHD_OK;
 }
 
-chd_status chd_hessian_factor(chd_factor* f, int m, const double* y, int64_t ldy, double* w, int64_t ldw,
-                              void* stream) {
+// W = R(Y); with `prune`, per right-hand side only the fronts whose
+// subtrees hold nonzeros of Y run (§5.5), the rest of W is zero
+static chd_status hessian_factor(chd_factor* f, int m, const double* y, int64_t ldy, double* w, int64_t ldw,
+                                 void* stream, bool prune) {
   if (!f || m < 0 || (m > 0 && (!y || !w))) return CHD_ERR_INVALID;
   const int64_t nnz = f->sym->colptr[f->sym->n];
   if (m > 1 && (ldy < nnz || ldw < nnz)) return CHD_ERR_INVALID;
@@ -535,22 +557,42 @@ chd_status chd_hessian_factor(chd_factor* f, int m, const double* y, int64_t ldy
   const int64_t chunk = rhs_chunk(f, m);
   rc = ensure_ws(f, chunk);
   if (rc == CHD_OK) rc = ensure_inv_v(f);
+  if (rc == CHD_OK && prune) rc = ensure_act(f, chunk);
   if (rc != CHD_OK) return rc;
+  const int64_t nsn = f->sym->nsn;
+  int32_t* cnt = prune ? static_cast<int32_t*>(f->act_buf) : nullptr;
+  uint8_t* act = prune ? reinterpret_cast<uint8_t*>(cnt + nsn * f->act_rhs) : nullptr;
   for (int64_t i = 0; i < m; i += chunk) {
     const int mc = (int)std::min<int64_t>(chunk, m - i);
     GraphKey key;
     key.p[0] = y + i * ldy;
     key.p[1] = w + i * ldw;
+    key.p[2] = act;
     key.v[0] = mc;
     key.v[1] = ldy;
     key.v[2] = ldw;
-    rc = run_sequence(f, G_HFACTOR, key, [&](cudaStream_t st) {
-      chd_launch::hess_up_pass(f->sym, st, &f->ex, mc, f->Wc, f->Vd, y + i * ldy, ldy, w + i * ldw, ldw, f->ws);
-      chd_launch::rtrans(f->sym, st, &f->ex, mc, 0, f->Lc, f->Dd, f->Qd, w + i * ldw, ldw, f->ws);
+    double* wi = w + i * ldw;
+    rc = run_sequence(f, prune ? G_HFACTOR_SPARSE : G_HFACTOR, key, [&](cudaStream_t st) {
+      if (prune) {
+        cudaMemset2DAsync(wi, (size_t)(mc > 1 ? ldw : nnz) * 8, 0, (size_t)nnz * 8, (size_t)mc, st);
+        chd_launch::prune_mask(f->sym, st, mc, y + i * ldy, ldy, cnt, act);
+      }
+      chd_launch::hess_up_pass(f->sym, st, &f->ex, mc, f->Wc, f->Vd, y + i * ldy, ldy, wi, ldw, f->ws, act);
+      chd_launch::rtrans(f->sym, st, &f->ex, mc, 0, f->Lc, f->Dd, f->Qd, wi, ldw, f->ws, act);
     });
     if (rc != CHD_OK) return rc;
   }
   return CHD_OK;
+}
+
+chd_status chd_hessian_factor(chd_factor* f, int m, const double* y, int64_t ldy, double* w, int64_t ldw,
+                              void* stream) {
+  return hessian_factor(f, m, y, ldy, w, ldw, stream, false);
+}
+
+chd_status chd_hessian_factor_sparse(chd_factor* f, int m, const double* y, int64_t ldy, double* w, int64_t ldw,
+                                     void* stream) {
+  return hessian_factor(f, m, y, ldy, w, ldw, stream, true);
 }
 
 chd_status chd_hessian_factor_adj(chd_factor* f, int m, const double* w, int64_t ldw, double* t, int64_t ldt,
@@ -580,7 +622,7 @@ chd_status chd_hessian_factor_adj(chd_factor* f, int m, const double* w, int64_t
       if (ti != wi)
         cudaMemcpy2DAsync(ti, (size_t)(mc > 1 ? ldt : nnz) * 8, wi, (size_t)(mc > 1 ? ldw : nnz) * 8,
                           (size_t)nnz * 8, (size_t)mc, cudaMemcpyDeviceToDevice, st);
-      chd_launch::rtrans(f->sym, st, &f->ex, mc, 1, f->Lc, f->Dd, f->Qd, ti, ldt, f->ws);
+      chd_launch::rtrans(f->sym, st, &f->ex, mc, 1, f->Lc, f->Dd, f->Qd, ti, ldt, f->ws, nullptr);
       chd_launch::hess_down_pass(f->sym, st, &f->ex, mc, f->Wc, ti, ldt, f->ws);
     });
     if (rc != CHD_OK) return rc;
@@ -743,6 +785,13 @@ chd_status chd_factor_release_workspace(chd_factor* f) {
     f->ws = nullptr;
     f->ws_rhs = 0;
   }
+  if (f->act_buf) {
+    chd_status rc = cuda_ok(cudaStreamSynchronize(f->stream));
+    if (rc != CHD_OK) return rc;
+    cudaFree(f->act_buf);
+    f->act_buf = nullptr;
+    f->act_rhs = 0;
+  }
   return CHD_OK;
 }
 
@@ -774,6 +823,7 @@ void chd_factor_free(chd_factor* f) {
   if (f->g_in) cudaEventDestroy(f->g_in);
   if (f->g_out) cudaEventDestroy(f->g_out);
   if (f->ws) cudaFree(f->ws);
+  if (f->act_buf) cudaFree(f->act_buf);
   if (f->inst_sum) cudaFree(f->inst_sum);
   if (f->block) cudaFree(f->block);
   delete f;
@@ -817,6 +867,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   size_t iCf = add(s->cta_fronts.data(), s->cta_fronts.size() * 4);
   size_t iWf = add(s->warp_fronts.data(), s->warp_fronts.size() * 4);
   size_t iPf = add(s->plain_fronts.data(), s->plain_fronts.size() * 4);
+  size_t iSl = add(s->sub_lo.data(), s->sub_lo.size() * 4);
+  size_t iSh = add(s->sub_hi.data(), s->sub_hi.size() * 4);
   size_t iIs = add(s->inst_sn.data(), s->inst_sn.size() * 8);
   std::vector<char> host(off, 0);
   for (auto& p : pcs)
@@ -877,6 +929,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   d.warp_count = (int64_t)s->warp_fronts.size();
   d.plain_fronts = reinterpret_cast<const int32_t*>(b + pcs[iPf].off);
   d.plain_count = (int64_t)s->plain_fronts.size();
+  d.sub_lo = reinterpret_cast<const int32_t*>(b + pcs[iSl].off);
+  d.sub_hi = reinterpret_cast<const int32_t*>(b + pcs[iSh].off);
   d.inst_sn = reinterpret_cast<const int64_t*>(b + pcs[iIs].off);
   d.ninst = (int64_t)s->inst_sn.size() - 1;
   d.f_total = s->f_off[s->nsn];

@@ -56,6 +56,13 @@ struct SymDev {
   int64_t warp_count = 0;
   const int32_t* plain_fronts = nullptr;  // fronts of the warp, wide and CTA tiers (no dense, no group)
   int64_t plain_count = 0;
+  // fronts whose update blocks reach front k's: [sub_lo[k], sub_hi[k]] (its
+  // subtree, plus the other members when k heads a leaf group)
+  const int32_t* sub_lo = nullptr;
+  const int32_t* sub_hi = nullptr;
+  // pruned Hessian factor (§5.5): per right-hand side y, act[y * nsn + k] != 0
+  // iff Y has a nonzero in the columns of that range; null: every front active
+  const uint8_t* act = nullptr;
   const int64_t* inst_sn = nullptr;       // instances x supernode ranges
   int64_t ninst = 1;
   int64_t f_total = 0;               // workspace doubles per right-hand side
@@ -100,6 +107,7 @@ struct chd_symbolic {
   std::vector<int32_t> warp_fronts;
   std::vector<int32_t> big_fronts;
   std::vector<int32_t> plain_fronts;
+  std::vector<int32_t> sub_lo, sub_hi;
   double flops[5] = {0, 0, 0, 0, 0};
   // independent instances analysed together (chd_analyze_batch): instance i
   // owns columns [inst_n[i], inst_n[i+1]), values [inst_nnz[i], inst_nnz[i+1])
@@ -157,6 +165,7 @@ enum GraphKind {
   G_PRODUCT,
   G_HFACTOR,
   G_HFACTOR_ADJ,
+  G_HFACTOR_SPARSE,
   G_KINDS
 };
 
@@ -172,7 +181,8 @@ struct chd_factor {
   double* Dd = nullptr;
   double* Vd = nullptr;
   double* Rd = nullptr;      // per front, once have_R: V_k^{-1} (lower), or chol(V_k) for dense-tier fronts
-  double* Qd = nullptr;      // per front, once have_R: chol(V_k) (lower; Hessian factor R, §5.4)
+  double* Qd = nullptr;      // per front, once have_R: Cholesky factor of P V_k P (P the order reversal),
+                             // i.e. the upper factor Q of V_k = Q Q^T held reversed (Hessian factor, §5.4)
   double* ldet = nullptr;
   double* scalar = nullptr;  // [0] log det
   int64_t* status = nullptr; // [0] code, [1] supernode, [2] column
@@ -180,6 +190,8 @@ struct chd_factor {
   Exec ex;                   // dense-tier streams and split-K scratch
   double* inst_sum = nullptr;  // per-instance log det sums (batched symbolic objects)
   int64_t ws_rhs = 0;        // capacity in right-hand sides
+  void* act_buf = nullptr;   // pruned Hessian factor: int32 counts, then uint8 flags, per (RHS, front)
+  int64_t act_rhs = 0;       // capacity of act_buf in right-hand sides
   size_t ws_limit = 0;       // caller's cap on the workspace (0: library default)
   bool have_S = false;
   bool have_R = false;

@@ -349,9 +349,11 @@ __device__ FrontInfo front_info(const SymDev& S, int k, double* ws) {
 // Extend-add of every child's update matrix (the A x A block of the child's
 // front) into this front: F += E_{J A_c} U_c E_{J A_c}^T  (children in a
 // fixed order, entries of one child touch distinct positions).
-__device__ void extend_add_children(const SymDev& S, const FrontInfo& f, double* ws, double sign) {
+__device__ void extend_add_children(const SymDev& S, const FrontInfo& f, double* ws, double sign,
+                                    const uint8_t* act = nullptr) {
   for (int64_t q = S.ea_ptr[f.k]; q < S.ea_ptr[f.k + 1]; ++q) {
     const int c = S.ea[q];
+    if (act && !act[c]) continue;  // pruned subtree: its update block is zero
     const int nc = (int)(S.sn_ptr[c + 1] - S.sn_ptr[c]);
     const int Jc = (int)(S.rows_ptr[c + 1] - S.rows_ptr[c]);
     const int ac = Jc - nc;
@@ -465,13 +467,13 @@ __device__ void gradient_front(const SymDev& S, int k, const double* Wc, double*
 // M_NN = D^{-1} K_NN D^{-1}, M_AN = V K_AN D^{-1}; M is written to the
 // output array (CSC), U' stays in the front for the parent.
 __device__ void hess_up_front(const SymDev& S, int k, const double* Wc, const double* Vd,
-                              const double* Y, double* T, double* ws) {
+                              const double* Y, double* T, double* ws, const uint8_t* act) {
   FrontInfo f = front_info(S, k, ws);
   const int J = f.J, n = f.n, a = f.a;
   csc_to_front(f.F, J, n, Y + f.base);
   zero_lower(f.F, J, a, n);
   __syncthreads();
-  extend_add_children(S, f, ws, 1.0);
+  extend_add_children(S, f, ws, 1.0, act);
   const double* W = Wc + f.base;
   CscRO L{W, J, n};
   // T1[n:J] = K_AN = Yh_AN - L Yh_NN
@@ -751,8 +753,12 @@ __global__ void __launch_bounds__(NT) k_hess_up(SymDev S, int task0, const doubl
                                                 double* T, int64_t ldt, double* ws) {
   const int t = task0 + blockIdx.x;
   const int64_t y = blockIdx.y;
-  for (int q = S.task_ptr[t]; q < S.task_ptr[t + 1]; ++q)
-    hess_up_front(S, S.task_fronts[q], Wc, Vd, Y + y * ldy, T + y * ldt, ws + y * S.f_total);
+  const uint8_t* act = S.act ? S.act + y * S.nsn : nullptr;
+  for (int q = S.task_ptr[t]; q < S.task_ptr[t + 1]; ++q) {
+    const int k = S.task_fronts[q];
+    if (act && !act[k]) continue;  // pruned (§5.5): K, U' and M are zero here
+    hess_up_front(S, k, Wc, Vd, Y + y * ldy, T + y * ldt, ws + y * S.f_total, act);
+  }
 }
 __global__ void __launch_bounds__(NT) k_hess_down(SymDev S, int task0, const double* Wc, double* T,
                                                   int64_t ldt, double* ws) {
@@ -781,7 +787,61 @@ __global__ void __launch_bounds__(NT) k_ihess_up(SymDev S, int task0, const doub
 __global__ void __launch_bounds__(NT) k_rtrans(SymDev S, int dir, const double* Lc, const double* Qd, double* Z,
                                                int64_t ldz, double* ws) {
   const int64_t y = blockIdx.y;
-  rtrans_front(S, S.plain_fronts[blockIdx.x], dir, Lc, Qd, Z + y * ldz, ws + y * S.f_total);
+  const int k = S.plain_fronts[blockIdx.x];
+  if (S.act && !S.act[y * S.nsn + k]) return;  // pruned: M = W = 0 here
+  rtrans_front(S, k, dir, Lc, Qd, Z + y * ldz, ws + y * S.f_total);
+}
+
+// Sparse arguments (§5.5): front k of right-hand side y is active when Y has
+// a nonzero in the columns of the fronts whose update blocks reach k
+// ([sub_lo[k], sub_hi[k]], contiguous in the postorder).  cnt[y][k] first
+// flags a nonzero among front k's own values, then holds the prefix sums.
+__global__ void __launch_bounds__(NT) k_front_nz(SymDev S, const double* Y, int64_t ldy, int32_t* cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t k = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+  if (k >= S.nsn) return;
+  const int64_t y = blockIdx.y;
+  const double* v = Y + y * ldy;
+  const int64_t b = S.colptr[S.sn_ptr[k]], e = S.colptr[S.sn_ptr[k + 1]];
+  bool nz = false;
+  for (int64_t i = b + lane; i < e && !nz; i += 32) nz = v[i] != 0.0;
+  nz = __any_sync(0xffffffffu, nz);
+  if (lane == 0) cnt[y * S.nsn + k] = nz ? 1 : 0;
+}
+constexpr int kScanT = 1024;
+__global__ void __launch_bounds__(kScanT) k_active(SymDev S, int32_t* cnt, uint8_t* act) {
+  __shared__ int32_t wsum[kScanT / 32];
+  const int64_t y = blockIdx.x;
+  int32_t* c = cnt + y * S.nsn;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t carry = 0;
+  for (int64_t k0 = 0; k0 < S.nsn; k0 += kScanT) {
+    const int64_t k = k0 + threadIdx.x;
+    int32_t v = k < S.nsn ? c[k] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+      int32_t x = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+      }
+      wsum[lane] = x;
+    }
+    __syncthreads();
+    v += carry + (w > 0 ? wsum[w - 1] : 0);
+    if (k < S.nsn) c[k] = v;
+    carry += wsum[kScanT / 32 - 1];
+    __syncthreads();
+  }
+  for (int64_t k = threadIdx.x; k < S.nsn; k += kScanT) {
+    const int32_t lo = S.sub_lo[k], hi = S.sub_hi[k];
+    act[y * S.nsn + k] = (c[hi] - (lo > 0 ? c[lo - 1] : 0)) > 0 ? 1 : 0;
+  }
 }
 // all CTA-tier fronts at once, one CTA each
 __global__ void __launch_bounds__(NT) k_complete(SymDev S, const double* Sin, double* Lc, double* Wc, double* Dd,
@@ -935,7 +995,8 @@ void big_product(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xca
 void big_gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Wc,
                   double* Sc, double* g, double* Vd, double* ws);
 void big_hess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
-                 const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
+                 const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws,
+                 const uint8_t* act);
 void big_hess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
                    double* T, int64_t ldt, double* ws);
 void big_ihess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k,
@@ -955,7 +1016,8 @@ void warp_factor(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const d
 void warp_gradient(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Wc, double* Sc,
                    double* g, double* Vd, double* ws);
 void warp_hess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
-                  const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
+                  const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws,
+                  const uint8_t* act);
 void warp_hess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* T,
                     int64_t ldt, double* ws);
 void warp_ihess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
@@ -973,7 +1035,8 @@ void warp_factor(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const d
 void warp_gradient(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Wc, double* Sc,
                    double* g, double* Vd, double* ws);
 void warp_hess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
-                  const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws);
+                  const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws,
+                  const uint8_t* act);
 void warp_hess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* T,
                     int64_t ldt, double* ws);
 void warp_ihess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
@@ -1096,18 +1159,20 @@ void gradient(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
   }
 }
 void hess_up_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Vd,
-                  const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
+                  const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws, const uint8_t* act) {
   const int nl = (int)s->lvl_ptr.size() - 1;
+  SymDev D = s->dev;
+  D.act = act;
   for (int l = 0; l < nl; ++l) {
     Level v = level(s, l);
     BigFork bf{ex, st};
     bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-      big_hess_up(s, bs, xs, xc, m, big_front(s, v, i), Wc, Vd, Y, ldy, T, ldt, ws);
+      big_hess_up(s, bs, xs, xc, m, big_front(s, v, i), Wc, Vd, Y, ldy, T, ldt, ws, act);
     });
-    if (v.nwarp) w32::warp_hess_up(s, st, v.t0, v.nwarp, m, Wc, Vd, Y, ldy, T, ldt, ws);
-    if (v.nw64) w64::warp_hess_up(s, st, v.tw, v.nw64, m, Wc, Vd, Y, ldy, T, ldt, ws);
+    if (v.nwarp) w32::warp_hess_up(s, st, v.t0, v.nwarp, m, Wc, Vd, Y, ldy, T, ldt, ws, act);
+    if (v.nw64) w64::warp_hess_up(s, st, v.tw, v.nw64, m, Wc, Vd, Y, ldy, T, ldt, ws, act);
     if (v.ncta) {
-      k_hess_up<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Vd, Y, ldy, T, ldt, ws);
+      k_hess_up<<<dim3(v.ncta, m), NT, 0, st>>>(D, v.tc, Wc, Vd, Y, ldy, T, ldt, ws);
       count();
     }
     bf.join_now();
@@ -1133,15 +1198,24 @@ void hess_down_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int 
 }
 void hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Vd,
              const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
-  hess_up_pass(s, st, ex, m, Wc, Vd, Y, ldy, T, ldt, ws);
+  hess_up_pass(s, st, ex, m, Wc, Vd, Y, ldy, T, ldt, ws, nullptr);
   hess_down_pass(s, st, ex, m, Wc, T, ldt, ws);
 }
 // M <-> W for every front (independent fronts): plain fronts in one launch,
 // dense fronts and leaf groups on the side streams
 void big_rtrans(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, int dir,
                 const double* Lc, const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws);
+// per right-hand side and front: active for the pruned Hessian factor
+void prune_mask(const chd_symbolic* s, cudaStream_t st, int m, const double* Y, int64_t ldy, int32_t* cnt,
+                uint8_t* act) {
+  if (s->nsn == 0 || m == 0) return;
+  k_front_nz<<<dim3((unsigned)((s->nsn + NT / 32 - 1) / (NT / 32)), m), NT, 0, st>>>(s->dev, Y, ldy, cnt);
+  count();
+  k_active<<<m, kScanT, 0, st>>>(s->dev, cnt, act);
+  count();
+}
 void rtrans(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, int dir, const double* Lc,
-            const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws) {
+            const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws, const uint8_t* act) {
   std::vector<int32_t> dense = s->big_fronts;
   for (int64_t g0 : s->grp_first) dense.push_back((int32_t)g0);
   BigFork bf{ex, st};
@@ -1149,7 +1223,9 @@ void rtrans(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, int d
     big_rtrans(s, bs, xs, xc, m, dense[i], dir, Lc, Dd, Qd, Z, ldz, ws);
   });
   if (s->dev.plain_count > 0) {
-    k_rtrans<<<dim3((unsigned)s->dev.plain_count, m), NT, 0, st>>>(s->dev, dir, Lc, Qd, Z, ldz, ws);
+    SymDev D = s->dev;
+    D.act = act;
+    k_rtrans<<<dim3((unsigned)s->dev.plain_count, m), NT, 0, st>>>(D, dir, Lc, Qd, Z, ldz, ws);
     count();
   }
   bf.join_now();

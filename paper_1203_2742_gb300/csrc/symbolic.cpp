@@ -604,6 +604,21 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
       if (tier[t] == 2) s->big_fronts.push_back((int32_t)t);
       if (tier[t] == 0 || tier[t] == 1 || tier[t] == 3) s->plain_fronts.push_back((int32_t)t);
     }
+    // subtree ranges (the numbering is a postorder: subtrees are contiguous);
+    // a leaf group's first member stands for the whole group
+    {
+      vector<int64_t> size(nsn, 1);
+      for (int64_t t = 0; t < nsn; ++t)
+        if (s->sn_par[t] >= 0) size[s->sn_par[t]] += size[t];
+      s->sub_lo.assign(nsn, 0);
+      s->sub_hi.assign(nsn, 0);
+      for (int64_t t = 0; t < nsn; ++t) {
+        s->sub_lo[t] = (int32_t)(t - size[t] + 1);
+        s->sub_hi[t] = (int32_t)t;
+      }
+      for (size_t g = 0; g < s->grp_first.size(); ++g)
+        s->sub_hi[s->grp_first[g]] = (int32_t)(s->grp_first[g] + s->grp_count[g] - 1);
+    }
     vector<double> W(nsn, 0.0);
     double total = 0;
     for (int64_t t = 0; t < nsn; ++t) {  // children precede parents

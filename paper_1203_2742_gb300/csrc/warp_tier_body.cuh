@@ -158,9 +158,10 @@ __device__ void store_front(const Fr& f, const Smem& m, double* dst, double scal
 // from its packed front in m.P, with its relative indices already in m.rel;
 // the others from their workspace fronts.
 __device__ void extend_add(const SymDev& S, const Fr& f, const Fr& prev, const Smem& m, const double* ws,
-                           int lane) {
+                           int lane, const uint8_t* act = nullptr) {
   const bool chain = f.flags & WM_PREV_CHILD;
   if (chain && (f.flags & WM_ONLY_CHILD_PREV)) {
+    if (act && !act[prev.k]) return;  // pruned child (§5.5): its update block is zero
     const int ac = prev.a, nc = prev.n, Jc = prev.J;
     for (int e = lane; e < ac * ac; e += TPF) {
       int r, s;
@@ -172,6 +173,7 @@ __device__ void extend_add(const SymDev& S, const Fr& f, const Fr& prev, const S
   }
   for (int q = f.ch_beg; q < f.ch_end; ++q) {
     const int c = S.ea[q];
+    if (act && !act[c]) continue;
     if (chain && c == prev.k) {
       const int ac = prev.a, nc = prev.n, Jc = prev.J;
       for (int e = lane; e < ac * ac; e += TPF) {
@@ -620,10 +622,11 @@ __device__ void gradient_front(const SymDev& S, const Fr& f, const Fr& prev, con
 }
 
 __device__ void hess_up_front(const SymDev& S, const Fr& f, const Fr& prev, const double* Wc, const double* Vd,
-                              const double* Y, double* T, const double* ws, const Smem& m, int lane) {
+                              const double* Y, double* T, const double* ws, const Smem& m, int lane,
+                              const uint8_t* act) {
   const int J = f.J, n = f.n, a = f.a;
   load_up(S, f, prev, m, Y, m.F, Wc, false, lane);
-  extend_add(S, f, prev, m, ws, lane);
+  extend_add(S, f, prev, m, ws, lane, act);
   // V_k (lower, packed) into the previous front's buffer, free from here on
   stage_lower_async(m.P, Vd + f.v_off, a, lane);
   // A2 = K_AN = Y_AN - L Y_NN
@@ -986,12 +989,14 @@ __global__ void __launch_bounds__(WPB * TPF) kw_gradient(SymDev S, int task0, in
 }
 __global__ void __launch_bounds__(WPB * TPF) kw_hess_up(SymDev S, int task0, int task_end, const double* Wc,
                                                        const double* Vd, const double* Y, int64_t ldy, double* T,
-                                                       int64_t ldt, double* ws) {
+                                                       int64_t ldt, double* ws, const uint8_t* act) {
   WARP_TASK_PROLOGUE
   const int64_t y = blockIdx.y;
   double* wsy = ws + y * S.f_total;
+  const uint8_t* ay = act ? act + y * S.nsn : nullptr;
   walk_up(S, t, wsy, w, [&](const Fr& f, const Fr& prev, const Smem& m) {
-    hess_up_front(S, f, prev, Wc, Vd, Y + y * ldy, T + y * ldt, wsy, m, lane);
+    if (ay && !ay[f.k]) return;  // pruned (§5.5): K, U' and M are zero here
+    hess_up_front(S, f, prev, Wc, Vd, Y + y * ldy, T + y * ldt, wsy, m, lane, ay);
   });
 }
 __global__ void __launch_bounds__(WPB * TPF) kw_hess_down(SymDev S, int task0, int task_end, const double* Wc,
@@ -1059,8 +1064,9 @@ void warp_gradient(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const
   chd_launch::count_launch();
 }
 void warp_hess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
-                  const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws) {
-  kw_hess_up<<<wgrid(nt, m), WPB * TPF, 0, st>>>(s->dev, t0, t0 + nt, Wc, Vd, Y, ldy, T, ldt, ws);
+                  const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws,
+                  const uint8_t* act) {
+  kw_hess_up<<<wgrid(nt, m), WPB * TPF, 0, st>>>(s->dev, t0, t0 + nt, Wc, Vd, Y, ldy, T, ldt, ws, act);
   chd_launch::count_launch();
 }
 void warp_hess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* T,

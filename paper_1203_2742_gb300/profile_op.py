@@ -63,7 +63,8 @@ def main(argv=None):
     import torch
     ap = argparse.ArgumentParser()
     ap.add_argument("workload", choices=sorted(DEFAULT_M))
-    ap.add_argument("op", choices=("factor", "gradient", "hessian", "inv_hessian", "completion", "all"))
+    ap.add_argument("op", choices=("factor", "gradient", "hessian", "inv_hessian", "completion", "hfactor",
+                                   "hfactor_adj", "hfactor_2nz", "hfactor_2nz_sparse", "all"))
     ap.add_argument("--m", type=int, default=None)
     ap.add_argument("--no-graphs", action="store_true", help="launch every kernel directly (no CUDA graphs)")
     ap.add_argument("--big-rows", type=int, default=0, help="dense-tier cutover |J| (0: library default)")
@@ -84,6 +85,12 @@ def main(argv=None):
     fac = sym.factor(x)
     g = torch.empty_like(x)
     t = torch.empty_like(ys)
+    wr = torch.empty_like(ys)
+    # sparse arguments (§5.5): two nonzero lower entries per Y at random positions
+    y2 = np.zeros((m, sym.nnz))
+    for i in range(m):
+        y2[i, rng.choice(sym.nnz, size=2, replace=False)] = rng.uniform(-1.0, 1.0, size=2)
+    y2 = dev(y2)
     cfac, _ = sym.complete(s)
     if a.no_graphs:
         fac.set_graphs(False)
@@ -94,6 +101,10 @@ def main(argv=None):
         "hessian": lambda: fac.hessian(ys, out=t),
         "inv_hessian": lambda: fac.inv_hessian(ys, out=t),
         "completion": lambda: cfac.recomplete(s, want_fstar=False),
+        "hfactor": lambda: fac.hessian_factor(ys, out=wr),
+        "hfactor_adj": lambda: fac.hessian_factor_adj(ys, out=wr),
+        "hfactor_2nz": lambda: fac.hessian_factor(y2, out=wr),
+        "hfactor_2nz_sparse": lambda: fac.hessian_factor(y2, out=wr, sparse=True),
     }
     import time
     for rnd in range(2):  # the second round captures the CUDA graphs the timed round replays

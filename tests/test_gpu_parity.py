@@ -204,6 +204,80 @@ def test_hessian_factor(name):
         assert c.err(ta[i], want_a[i]) < TOL
 
 
+def _figure_case(case, big):
+    """Figure 1's pattern in the library's order (a postorder of the same
+    elimination tree: the factors, the ordered sets I_j and so R(Y) only get
+    permuted), Y with the figure's nonzero, and the map of W's nonzeros back
+    to the figure's numbering."""
+    from tests.test_oracle_dense import fig_spy_w
+    pattern, cases = fig_spy_w()
+    c = Case(pattern, seed=97, big=big)
+    perm = np.asarray(c.sym.perm)  # perm[new] = old
+    rr, cc = OD.pattern_pairs(c.n, c.cp, c.ri)
+    orr, occ = np.maximum(perm[rr], perm[cc]), np.minimum(perm[rr], perm[cc])
+    y = np.where((orr == cases[case]["y"][0]) & (occ == cases[case]["y"][1]), 1.0, 0.0)
+    assert y.sum() == 1.0
+
+    def spy_orig(w):
+        big_ = np.abs(w) > 1e-12 * np.abs(w).max()
+        return {(int(a), int(b)) for a, b, t in zip(orr, occ, big_) if t}
+    return c, y, spy_orig, cases[case]["w"]
+
+
+@pytest.mark.parametrize("case", ["a", "b"])
+@pytest.mark.parametrize("big", [None, (4, 2)])
+def test_hessian_factor_sparsity_of_figure(case, big):
+    """Figure fig-spy-W (§5.5): the nonzeros of R(Y) on Figure 1's pattern for
+    a Y with one nonzero, through the per-task tiers and through the dense
+    tier (low thresholds)."""
+    c, y, spy_orig, want = _figure_case(case, big)
+    f = c.sym.factor(c.dev(c.x))
+    w = c.host(f.hessian_factor(c.dev(y)))
+    assert spy_orig(w) == want
+    assert c.err(w, OD.hessian_factor(c.n, c.cp, c.ri, c.x, [y])[0]) < TOL
+
+
+def sparse_args(c, count, k, rng):
+    """`count` matrices on V with `k` nonzero lower entries each at random
+    positions (the sparse arguments of §5.5), values uniform[-1, 1]."""
+    nnz = len(c.ri)
+    out = np.zeros((count, nnz))
+    for i in range(count):
+        pos = rng.choice(nnz, size=min(k, nnz), replace=False)
+        out[i, pos] = rng.uniform(-1.0, 1.0, size=len(pos))
+    return out
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_hessian_factor_sparse_arguments(name):
+    """R(Y) with the clique tree pruned per Y (§5.5) equals the oracle's R(Y)
+    for Y with two nonzeros (the paper's experiment), a dense Y and Y = 0,
+    in one batch."""
+    c = CASES[name]()
+    f = c.sym.factor(c.dev(c.x))
+    ys = np.concatenate([sparse_args(c, 4, 2, c.rng), W.uniform_sym(c.n, c.cp, c.ri, c.rng, count=1),
+                         np.zeros((1, len(c.ri)))])
+    wp = c.host(f.hessian_factor(c.dev(ys), sparse=True))
+    want = OD.hessian_factor(c.n, c.cp, c.ri, c.x, list(ys[:5]))
+    for i in range(5):
+        assert c.err(wp[i], want[i]) < TOL
+    assert not np.any(wp[5])  # Y = 0: every front pruned, W = 0 exactly
+    # the pruned and the full computation agree on the same batch
+    wf = c.host(f.hessian_factor(c.dev(ys)))
+    for i in range(6):
+        assert c.err(wp[i], wf[i]) < 1e-13 or not np.any(wf[i])
+
+
+@pytest.mark.parametrize("case", ["a", "b"])
+def test_hessian_factor_sparse_figure(case):
+    """Figure fig-spy-W through the pruned path."""
+    c, y, spy_orig, want = _figure_case(case, None)
+    f = c.sym.factor(c.dev(c.x))
+    w = c.host(f.hessian_factor(c.dev(y), sparse=True))
+    assert spy_orig(w) == want
+    assert c.err(w, OD.hessian_factor(c.n, c.cp, c.ri, c.x, [y])[0]) < TOL
+
+
 @pytest.mark.parametrize("name", ["grid14_nd", "dense_tier_er", "arrow150_w48", "wide_front"])
 def test_schur_by_hessian_factor(name):
     """H_ij = R(A_i) . R(A_j) (§5.4) equals A_i . H(A_j)."""

@@ -453,3 +453,43 @@ def test_hessian_factor_dense_2x2_by_hand():
     d22 = c - b * b / a
     w = OD.hessian_factor(n, cp, ri, x, [y])[0]
     np.testing.assert_allclose(w, [0.0, np.sqrt(a) / a / np.sqrt(d22), (-2 * b / a) / d22], rtol=1e-14, atol=1e-15)
+
+
+def fig_spy_w():
+    """Figure 1's pattern and the W = R(Y) sparsity of Figure fig-spy-W."""
+    import os
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    pairs = np.loadtxt(os.path.join(gold, "fig1_pattern.txt"), dtype=np.int64, comments="#")
+    pattern = W.lower_csc_from_pairs(17, pairs[:, 0], pairs[:, 1])
+    cases, cur = {}, None
+    with open(os.path.join(gold, "fig_spy_W.txt")) as f:
+        for line in f:
+            tok = line.split("#")[0].split()
+            if not tok:
+                continue
+            if tok[0] == "case":
+                cur = cases.setdefault(tok[1], {"y": None, "w": set()})
+            elif tok[0] == "y":
+                cur["y"] = (int(tok[1]), int(tok[2]))
+            else:
+                cur["w"].add((int(tok[1]), int(tok[2])))
+    return pattern, cases
+
+
+def spy(n, cp, ri, w, rel=1e-12):
+    rr, cc = OD.pattern_pairs(n, cp, ri)
+    big = np.abs(w) > rel * np.abs(w).max()
+    return {(int(r), int(c)) for r, c, b in zip(rr, cc, big) if b}
+
+
+@pytest.mark.parametrize("case", ["a", "b"])
+def test_hessian_factor_sparsity_of_figure(case):
+    """Figure fig-spy-W (§5.5): nonzeros of R(Y) for a Y with one nonzero; in
+    case b the zero at (2, 1) next to the nonzero at (3, 1) holds only for
+    the upper triangular R_j of Algorithm 5.3."""
+    (n, cp, ri), cases = fig_spy_w()
+    x = W.diag_dominant(n, cp, ri, np.random.default_rng(97))
+    rr, cc = OD.pattern_pairs(n, cp, ri)
+    y = np.where((rr == cases[case]["y"][0]) & (cc == cases[case]["y"][1]), 1.0, 0.0)
+    w = OD.hessian_factor(n, cp, ri, x, [y])[0]
+    assert spy(n, cp, ri, w) == cases[case]["w"]
