@@ -330,12 +330,17 @@ void chd_factor_free(chd_factor* fac);
 /*
  * Workspace control of a factor object (device memory the library holds for
  * the per-front workspace of Hessian-type calls; it grows to the largest
- * batch of right-hand sides a call processes at once).
+ * batch of right-hand sides a call processes at once).  The workspace is a
+ * stream-ordered allocation (cudaMallocAsync / cudaFreeAsync) on the stream
+ * of the call that grows or releases it, so neither synchronises the device;
+ * successive calls on one factor object must be ordered (one stream, or
+ * synchronised by the caller).
  *   chd_factor_set_workspace_limit: cap it at `bytes` (0 = library default,
  *     48 GiB); larger batches are processed in chunks, at least one
  *     right-hand side at a time.
- *   chd_factor_release_workspace: synchronise the factor's stream and free
- *     the workspace (the next call allocates it again).
+ *   chd_factor_release_workspace: free the workspace, ordered after the
+ *     work already issued on the factor's last stream (the next call
+ *     allocates it again).
  *   chd_factor_workspace_bytes: bytes currently held.
  */
 chd_status chd_factor_set_workspace_limit(chd_factor* fac, size_t bytes);

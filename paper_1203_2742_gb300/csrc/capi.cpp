@@ -26,7 +26,7 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
 void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Sin, double* Lc,
               double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
 void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* Qd,
-           double* ws, int64_t* status);
+           double* ws, int64_t* status, int what);
 void hess_up_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Vd,
                   const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws, const uint8_t* act);
 void prune_mask(const chd_symbolic* s, cudaStream_t st, int m, const double* Y, int64_t ldy, int32_t* cnt,
@@ -141,17 +141,19 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
   return CHD_OK;
 }
 
+// Workspaces are stream-ordered allocations on the calling stream: growing or
+// releasing one never synchronises the device, so calls on other factors
+// (other streams) keep running.
 chd_status ensure_ws(chd_factor* f, int64_t rhs) {
   if (f->ws_rhs >= rhs) return CHD_OK;
   if (f->ws) {
-    cudaStreamSynchronize(f->stream);
-    cudaFree(f->ws);
+    cudaFreeAsync(f->ws, f->stream);
     f->ws = nullptr;
     f->ws_rhs = 0;
   }
   void* p = nullptr;
   const size_t bytes = (size_t)f->sym->dev.f_total * 8 * (size_t)rhs;
-  chd_status rc = cuda_ok(cudaMalloc(&p, std::max<size_t>(bytes, 256)));
+  chd_status rc = cuda_ok(cudaMallocAsync(&p, std::max<size_t>(bytes, 256), f->stream));
   if (rc != CHD_OK) return rc;
   f->ws = static_cast<double*>(p);
   f->ws_rhs = rhs;
@@ -162,14 +164,13 @@ chd_status ensure_ws(chd_factor* f, int64_t rhs) {
 chd_status ensure_act(chd_factor* f, int64_t rhs) {
   if (f->act_rhs >= rhs) return CHD_OK;
   if (f->act_buf) {
-    cudaStreamSynchronize(f->stream);
-    cudaFree(f->act_buf);
+    cudaFreeAsync(f->act_buf, f->stream);
     f->act_buf = nullptr;
     f->act_rhs = 0;
   }
   void* p = nullptr;
   const size_t bytes = (size_t)f->sym->nsn * 5 * (size_t)rhs;
-  chd_status rc = cuda_ok(cudaMalloc(&p, std::max<size_t>(bytes, 256)));
+  chd_status rc = cuda_ok(cudaMallocAsync(&p, std::max<size_t>(bytes, 256), f->stream));
   if (rc != CHD_OK) return rc;
   f->act_buf = p;
   f->act_rhs = rhs;
@@ -276,14 +277,23 @@ chd_status ensure_projected_inverse(chd_factor* f) {
   return rc;
 }
 
-// chol(V_k) (Qd) and V_k^{-1} or its factor (Rd) of every front, once per
-// factor; needs the projected inverse.
+// V_k^{-1} (Rd) of every front, once per factor; needs the projected inverse.
 chd_status ensure_inv_v(chd_factor* f) {
   if (f->have_R) return CHD_OK;
   chd_status rc = run_sequence(f, G_INV_V, GraphKey{}, [&](cudaStream_t st) {
-    chd_launch::inv_v(f->sym, st, &f->ex, f->Vd, f->Rd, f->Qd, f->ws, f->status);
+    chd_launch::inv_v(f->sym, st, &f->ex, f->Vd, f->Rd, f->Qd, f->ws, f->status, 1);
   });
   if (rc == CHD_OK) f->have_R = true;
+  return rc;
+}
+// the reversed upper factors of every V_k (Qd) for the Hessian factor, once
+// per factor; needs the projected inverse.
+chd_status ensure_q(chd_factor* f) {
+  if (f->have_Q) return CHD_OK;
+  chd_status rc = run_sequence(f, G_Q, GraphKey{}, [&](cudaStream_t st) {
+    chd_launch::inv_v(f->sym, st, &f->ex, f->Vd, f->Rd, f->Qd, f->ws, f->status, 2);
+  });
+  if (rc == CHD_OK) f->have_Q = true;
   return rc;
 }
 
@@ -459,7 +469,7 @@ chd_status chd_refactor(chd_factor* f, const double* x, void* stream) {
   f->stream = static_cast<cudaStream_t>(stream);
   chd_status rc = ensure_ws(f, 1);
   if (rc != CHD_OK) return rc;
-  f->have_S = f->have_R = false;
+  f->have_S = f->have_R = f->have_Q = false;
   rc = cuda_ok(cudaMemsetAsync(f->status, 0, 4 * 8, f->stream));
   if (rc != CHD_OK) return rc;
   GraphKey key;
@@ -556,7 +566,7 @@ static chd_status hessian_factor(chd_factor* f, int m, const double* y, int64_t 
   if (rc != CHD_OK) return rc;
   const int64_t chunk = rhs_chunk(f, m);
   rc = ensure_ws(f, chunk);
-  if (rc == CHD_OK) rc = ensure_inv_v(f);
+  if (rc == CHD_OK) rc = ensure_q(f);
   if (rc == CHD_OK && prune) rc = ensure_act(f, chunk);
   if (rc != CHD_OK) return rc;
   const int64_t nsn = f->sym->nsn;
@@ -606,7 +616,7 @@ chd_status chd_hessian_factor_adj(chd_factor* f, int m, const double* w, int64_t
   if (rc != CHD_OK) return rc;
   const int64_t chunk = rhs_chunk(f, m);
   rc = ensure_ws(f, chunk);
-  if (rc == CHD_OK) rc = ensure_inv_v(f);
+  if (rc == CHD_OK) rc = ensure_q(f);
   if (rc != CHD_OK) return rc;
   for (int64_t i = 0; i < m; i += chunk) {
     const int mc = (int)std::min<int64_t>(chunk, m - i);
@@ -679,6 +689,7 @@ chd_status chd_recomplete(chd_factor* f, const double* sv, void* stream, double*
   if (rc != CHD_OK) return rc;
   f->have_S = true;
   f->have_R = false;  // Rd holds chol(V_k) here; V_k^{-1} is formed on first use
+  f->have_Q = false;
   if (fstar) {
     double ld = 0;
     rc = chd_logdet(f, &ld);
@@ -779,16 +790,14 @@ chd_status chd_factor_set_graphs(chd_factor* f, int on) {
 chd_status chd_factor_release_workspace(chd_factor* f) {
   if (!f) return CHD_ERR_INVALID;
   if (f->ws) {
-    chd_status rc = cuda_ok(cudaStreamSynchronize(f->stream));
+    chd_status rc = cuda_ok(cudaFreeAsync(f->ws, f->stream));
     if (rc != CHD_OK) return rc;
-    cudaFree(f->ws);
     f->ws = nullptr;
     f->ws_rhs = 0;
   }
   if (f->act_buf) {
-    chd_status rc = cuda_ok(cudaStreamSynchronize(f->stream));
+    chd_status rc = cuda_ok(cudaFreeAsync(f->act_buf, f->stream));
     if (rc != CHD_OK) return rc;
-    cudaFree(f->act_buf);
     f->act_buf = nullptr;
     f->act_rhs = 0;
   }

@@ -166,6 +166,7 @@ enum GraphKind {
   G_HFACTOR,
   G_HFACTOR_ADJ,
   G_HFACTOR_SPARSE,
+  G_Q,
   G_KINDS
 };
 
@@ -180,8 +181,8 @@ struct chd_factor {
   double* Sc = nullptr;
   double* Dd = nullptr;
   double* Vd = nullptr;
-  double* Rd = nullptr;      // per front, once have_R: V_k^{-1} (lower), or chol(V_k) for dense-tier fronts
-  double* Qd = nullptr;      // per front, once have_R: Cholesky factor of P V_k P (P the order reversal),
+  double* Rd = nullptr;      // per front, once have_R: V_k^{-1} (lower)
+  double* Qd = nullptr;      // per front, once have_Q: Cholesky factor of P V_k P (P the order reversal),
                              // i.e. the upper factor Q of V_k = Q Q^T held reversed (Hessian factor, §5.4)
   double* ldet = nullptr;
   double* scalar = nullptr;  // [0] log det
@@ -195,6 +196,7 @@ struct chd_factor {
   size_t ws_limit = 0;       // caller's cap on the workspace (0: library default)
   bool have_S = false;
   bool have_R = false;
+  bool have_Q = false;
   // CUDA graphs of the launch sequences, replayed on the private stream gs
   bool graphs_on = true;
   cudaStream_t gs = nullptr;

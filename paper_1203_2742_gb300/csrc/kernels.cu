@@ -17,8 +17,8 @@
 //   Wc  (CSC)  : [D_NN^{-1}; L_AN]
 //   Dd  (n x n): D_NN
 //   Vd  (a x a): V_k = S_{A_k A_k}  (Algorithm 7.2)
-//   Rd  (a x a): V_k^{-1} (lower triangle; inverse Hessian, §5.3) for the
-//                warp and CTA tiers, R = chol(V_k) for dense-tier fronts
+//   Rd  (a x a): V_k^{-1} (lower triangle; inverse Hessian, §5.3)
+//   Qd  (a x a): chol(P V_k P), P the order reversal (Hessian factor, §5.4)
 //   Sc  (CSC)  : S = P(X^{-1})
 #include <cuda_runtime.h>
 
@@ -853,8 +853,10 @@ __global__ void __launch_bounds__(NT) k_complete(SymDev S, const double* Sin, do
 // Inverses of the cached V_k (inverse Hessian step 2), one CTA per front of
 // `front_list` (no dependencies between fronts; big fronts use the dense
 // tier): R = chol(V), R^{-1} in the front's workspace, V^{-1} = R^{-T} R^{-1}.
+// what & 1: V_k^{-1} into Rd (inverse Hessian); what & 2: chol(P V_k P) into
+// Qd (Hessian factor)
 __global__ void __launch_bounds__(NT) k_inv_v(SymDev S, const double* Vd, double* Rd, double* Qd, double* ws,
-                                              int64_t* st, const int32_t* front_list) {
+                                              int64_t* st, const int32_t* front_list, int what) {
   const int k = front_list[blockIdx.x];
   const int n = (int)(S.sn_ptr[k + 1] - S.sn_ptr[k]);
   const int a = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]) - n;
@@ -864,18 +866,23 @@ __global__ void __launch_bounds__(NT) k_inv_v(SymDev S, const double* Vd, double
   const double* V = Vd + S.v_off[k];
   // Hessian factor (§5.4): V = Q Q^T with Q upper triangular, kept as
   // Q' = chol(P V P) = P Q P, P the order reversal
-  double* Qk = Qd + S.v_off[k];
-  for (int e = threadIdx.x; e < a * a; e += NT) {
-    const int r = e % a, c = e / a;
-    if (r >= c) Qk[r + (int64_t)c * a] = V[(a - 1 - c) + (int64_t)(a - 1 - r) * a];
+  if (what & 2) {
+    double* Qk = Qd + S.v_off[k];
+    for (int e = threadIdx.x; e < a * a; e += NT) {
+      const int r = e % a, c = e / a;
+      if (r >= c) Qk[r + (int64_t)c * a] = V[(a - 1 - c) + (int64_t)(a - 1 - r) * a];
+    }
+    __syncthreads();
+    cta_potrf_partial(Qk, a, a, a, st, CHD_ERR_NOT_PD, k, -1);
   }
-  copy_lower(R, a, V, a, a);
-  set_identity(Ri, a, a);
-  __syncthreads();
-  cta_potrf_partial(Qk, a, a, a, st, CHD_ERR_NOT_PD, k, -1);
-  cta_potrf_partial(R, a, a, a, st, CHD_ERR_NOT_PD, k, -1);
-  cta_trsm_rLT(a, a, DnTW{Ri, a}, R, a);  // Ri = R^{-1}
-  cta_gemm(a, a, a, 1.0, TriLT{Ri, a}, TriL{Ri, a}, 0.0, Dn{R, a}, true);
+  if (what & 1) {
+    copy_lower(R, a, V, a, a);
+    set_identity(Ri, a, a);
+    __syncthreads();
+    cta_potrf_partial(R, a, a, a, st, CHD_ERR_NOT_PD, k, -1);
+    cta_trsm_rLT(a, a, DnTW{Ri, a}, R, a);  // Ri = R^{-1}
+    cta_gemm(a, a, a, 1.0, TriLT{Ri, a}, TriL{Ri, a}, 0.0, Dn{R, a}, true);
+  }
 }
 // Deterministic sum of the per-front log det contributions.
 __global__ void k_sum(const double* v, int64_t m, double* out) {
@@ -1284,18 +1291,18 @@ void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
   bf.join_now();
 }
 void big_inv_v(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Vd,
-               double* Rd, double* Qd, double* ws, int64_t* status);
+               double* Rd, double* Qd, double* ws, int64_t* status, int what);
 void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* Qd,
-           double* ws, int64_t* status) {
+           double* ws, int64_t* status, int what) {
   std::vector<int> bigs;
   for (int64_t k = 0; k < s->nsn; ++k)
     if (s->is_big[k]) bigs.push_back((int)k);
   BigFork bf{ex, st};
   bf.run((int)bigs.size(), [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-    big_inv_v(s, bs, xs, xc, bigs[i], Vd, Rd, Qd, ws, status);
+    big_inv_v(s, bs, xs, xc, bigs[i], Vd, Rd, Qd, ws, status, what);
   });
   if (s->dev.small_count > 0) {
-    k_inv_v<<<(int)s->dev.small_count, NT, 0, st>>>(s->dev, Vd, Rd, Qd, ws, status, s->dev.small_fronts);
+    k_inv_v<<<(int)s->dev.small_count, NT, 0, st>>>(s->dev, Vd, Rd, Qd, ws, status, s->dev.small_fronts, what);
     count();
   }
   bf.join_now();

@@ -55,6 +55,7 @@ class PatternState:
     fac: object = None
     cfac: object = None
     lock: threading.Lock = field(default_factory=threading.Lock)
+    busy: bool = False  # a worker runs a call on this pattern (guarded by Server.cv)
     ws_bytes_per_rhs: int = 0
 
 
@@ -138,11 +139,15 @@ class Server:
             self.cv.notify_all()
 
     def _take(self):
-        """Next admissible request (FIFO among those that fit), plus, when
-        batching, the waiting same-pattern requests of the same kind."""
+        """Next admissible request (FIFO among those whose pattern is idle and
+        that fit), plus, when batching, the waiting same-pattern requests of
+        the same kind.  A request on a pattern another worker is running waits
+        in the queue, so workers never block on a pattern's lock."""
         with self.cv:
             while True:
                 for i, req in enumerate(self.queue):
+                    if self.states[req.pattern].busy:
+                        continue
                     need = self.footprint(req)
                     if self.in_use + need <= self.budget or self.in_use == 0:
                         del self.queue[i]
@@ -161,14 +166,16 @@ class Server:
                                     keep.append(r2)
                             self.queue = keep
                         self.in_use += need
+                        self.states[req.pattern].busy = True
                         return group, need
                 if self.closed and not self.queue:
                     return None, 0
                 self.cv.wait(timeout=0.05)
 
-    def _release(self, need):
+    def _release(self, need, pattern):
         with self.cv:
             self.in_use -= need
+            self.states[pattern].busy = False
             self.cv.notify_all()
 
     def _run_group(self, group, stream):
@@ -223,7 +230,7 @@ class Server:
                 for r in group:
                     r.start, r.done, r.result, r.batched_with = t, t, e, len(group)
             finally:
-                self._release(need)
+                self._release(need, group[0].pattern)
                 with self.cv:
                     self.completed.extend(group)
 
