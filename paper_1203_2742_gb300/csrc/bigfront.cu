@@ -760,10 +760,13 @@ void ihess_down_front(const chd_symbolic* s, const Ctx& st, int m, int k, const 
   gemm(st, m, n, n, n, 1.0, Dn{T1, J}, sw, SymL{D, n}, 0, 0.0, Dn{T2, J}, sw, false);
   gemm(st, m, n, n, n, 1.0, SymL{D, n}, 0, Dn{T2, J}, sw, 0.0, Csc{Yout + f.base, J, 0}, ldy, true);
   if (a > 0) {
-    // K_AN = V^{-1} (M_AN D), V^{-1} formed once per factor
+    // K_AN = V^{-1} (M_AN D) = R^{-T} R^{-1} (M_AN D) with R = chol(V) cached
+    // per factor: two blocked triangular solves on the transposed block
+    const double* R = Rd + s->v_off[k];
     gemm(st, m, a, n, n, 1.0, Dn{T1 + n, J}, sw, SymL{D, n}, 0, 0.0, Dn{T2 + n, J}, sw, false);
-    gemm(st, m, a, n, a, 1.0, SymL{Rd + s->v_off[k], a}, 0, Dn{T2 + n, J}, sw, 0.0, Csc{Yout + f.base, J, n}, ldy,
-         false);
+    trsm_rLT(st, m, n, a, DnTW{T2 + n, J}, sw, R, a);
+    trsm_rL(st, m, n, a, DnTW{T2 + n, J}, sw, R, a);
+    CHD_EW(mk_front_to_csc, (int64_t)J * n, m, st, Yout + f.base, ldy, T2, sw, J, J, n, n, J, 1.0);
   }
 }
 
@@ -1336,8 +1339,8 @@ void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const doub
   if (s->grp_of[k] >= 0) return;  // a leaf group reads S itself
   chd::big::complete_load_front(s, chd::big::make_ctx(st, nullptr, 0), k, Sin, ws);
 }
-// V_k^{-1} (lower, into Rd) of the cached V_k = S_{A_k A_k} of one big front,
-// and the reversed upper factor of V_k (into Qd).
+// Cholesky factor R of the cached V_k = S_{A_k A_k} of one big front (lower,
+// into Rd), and the reversed upper factor of V_k (into Qd).
 void big_inv_v(const chd_symbolic* s, cudaStream_t stream, double* xs, int64_t xcap, int k, const double* Vd,
                double* Rd, double* Qd, double* ws, int64_t* status, int what) {
   using namespace chd;
@@ -1346,17 +1349,14 @@ void big_inv_v(const chd_symbolic* s, cudaStream_t stream, double* xs, int64_t x
   const int n = (int)(s->sn_ptr[k + 1] - s->sn_ptr[k]);
   const int a = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k]) - n;
   if (a == 0) return;
+  (void)ws;
   if (what & 1) {
+    // R = chol(V): the inverse-Hessian calls apply V^{-1} = R^{-T} R^{-1} by
+    // two blocked triangular solves (forming V^{-1} costs 2a^3/3 more flops
+    // per factor, more than the solves of a call save)
     double* R = Rd + s->v_off[k];
     CHD_EW(mk_copy, (int64_t)a * a, 1, st, R, 0, a, Vd + s->v_off[k], 0, a, a, a, 1.0, 0.0, 1, 0);
     potrf_partial(st, R, a, a, a, status, CHD_ERR_NOT_PD, k, -1);
-    // V^{-1} = R^{-T} R^{-1}: Ri = R^{-1} in the front's workspace, the
-    // product back into R.  Formed once per factor, it turns the two blocked
-    // triangular solves per inverse-Hessian call into one product.
-    double* Ri = ws + s->f_off[k];
-    CHD_EW(mk_identity, (int64_t)a * a, 1, st, Ri, a, a);
-    trsm_rLT(st, 1, a, a, DnTW{Ri, a}, 0, R, a);
-    gemm(st, 1, a, a, a, 1.0, TriLT{Ri, a}, 0, TriL{Ri, a}, 0, 0.0, Dn{R, a}, 0, true);
   }
   if (what & 2) {
     // the upper factor Q of V = Q Q^T (Hessian factor, §5.4), held as

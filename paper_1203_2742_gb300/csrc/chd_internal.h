@@ -181,7 +181,7 @@ struct chd_factor {
   double* Sc = nullptr;
   double* Dd = nullptr;
   double* Vd = nullptr;
-  double* Rd = nullptr;      // per front, once have_R: V_k^{-1} (lower)
+  double* Rd = nullptr;      // per front, once have_R: V_k^{-1} (lower), or chol(V_k) for dense-tier fronts
   double* Qd = nullptr;      // per front, once have_Q: Cholesky factor of P V_k P (P the order reversal),
                              // i.e. the upper factor Q of V_k = Q Q^T held reversed (Hessian factor, §5.4)
   double* ldet = nullptr;

@@ -17,7 +17,8 @@
 //   Wc  (CSC)  : [D_NN^{-1}; L_AN]
 //   Dd  (n x n): D_NN
 //   Vd  (a x a): V_k = S_{A_k A_k}  (Algorithm 7.2)
-//   Rd  (a x a): V_k^{-1} (lower triangle; inverse Hessian, §5.3)
+//   Rd  (a x a): V_k^{-1} (lower triangle; inverse Hessian, §5.3) for the
+//                warp and CTA tiers, R = chol(V_k) for dense-tier fronts
 //   Qd  (a x a): chol(P V_k P), P the order reversal (Hessian factor, §5.4)
 //   Sc  (CSC)  : S = P(X^{-1})
 #include <cuda_runtime.h>
