@@ -139,35 +139,17 @@ class Server:
             self.cv.notify_all()
 
     def _take(self):
-        """Next admissible request (FIFO among those whose pattern is idle and
-        that fit), plus, when batching, the waiting same-pattern requests of
-        the same kind.  A request on a pattern another worker is running waits
-        in the queue, so workers never block on a pattern's lock."""
+        """Next admissible request plus its batch (see ``pick``); waits while
+        nothing can be admitted."""
         with self.cv:
             while True:
-                for i, req in enumerate(self.queue):
-                    if self.states[req.pattern].busy:
-                        continue
-                    need = self.footprint(req)
-                    if self.in_use + need <= self.budget or self.in_use == 0:
-                        del self.queue[i]
-                        group = [req]
-                        if self.batching and req.op in ("hessian", "inv_hessian"):
-                            rhs = req.m
-                            keep = collections.deque()
-                            while self.queue:
-                                r2 = self.queue.popleft()
-                                if (r2.op == req.op and r2.pattern == req.pattern
-                                        and rhs + r2.m <= self.max_batch_rhs):
-                                    group.append(r2)
-                                    rhs += r2.m
-                                    need += self.footprint(r2)
-                                else:
-                                    keep.append(r2)
-                            self.queue = keep
-                        self.in_use += need
-                        self.states[req.pattern].busy = True
-                        return group, need
+                got = pick(self.queue, lambda p: self.states[p].busy, self.footprint, self.in_use, self.budget,
+                           self.batching, self.max_batch_rhs)
+                if got is not None:
+                    group, need, self.queue = got
+                    self.in_use += need
+                    self.states[group[0].pattern].busy = True
+                    return group, need
                 if self.closed and not self.queue:
                     return None, 0
                 self.cv.wait(timeout=0.05)
@@ -245,6 +227,42 @@ class Server:
         self.close()
         for t in self.threads:
             t.join()
+
+
+def pick(queue, busy, footprint, in_use, budget, batching, max_batch_rhs):
+    """Admission and batching decision of the server (host logic only).
+
+    The first request in FIFO order whose pattern is idle (``busy(pattern)``
+    false) and whose footprint fits the budget (or that comes when nothing is
+    in flight) is taken; when batching, the waiting Hessian or
+    inverse-Hessian requests of the same kind on the same pattern join it
+    while their right-hand sides total at most ``max_batch_rhs``.  Returns
+    (group, bytes, remaining queue), or None when nothing can be admitted.
+    A request on a busy pattern stays queued, so a worker never waits for a
+    pattern another worker is running.
+    """
+    for i, req in enumerate(queue):
+        if busy(req.pattern):
+            continue
+        need = footprint(req)
+        if in_use + need > budget and in_use != 0:
+            continue
+        rest = collections.deque(r for j, r in enumerate(queue) if j != i)
+        group = [req]
+        if batching and req.op in ("hessian", "inv_hessian"):
+            rhs = req.m
+            keep = collections.deque()
+            while rest:
+                r2 = rest.popleft()
+                if r2.op == req.op and r2.pattern == req.pattern and rhs + r2.m <= max_batch_rhs:
+                    group.append(r2)
+                    rhs += r2.m
+                    need += footprint(r2)
+                else:
+                    keep.append(r2)
+            rest = keep
+        return group, need, rest
+    return None
 
 
 def poisson_trace(npatterns, rate, duration, mix, rng, nnz_of, max_m=16):
