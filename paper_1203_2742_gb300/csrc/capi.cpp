@@ -582,14 +582,16 @@ static chd_status hessian_factor(chd_factor* f, int m, const double* y, int64_t 
     key.v[1] = ldy;
     key.v[2] = ldw;
     double* wi = w + i * ldw;
+    cudaError_t ce = cudaSuccess;
     rc = run_sequence(f, prune ? G_HFACTOR_SPARSE : G_HFACTOR, key, [&](cudaStream_t st) {
       if (prune) {
-        cudaMemset2DAsync(wi, (size_t)(mc > 1 ? ldw : nnz) * 8, 0, (size_t)nnz * 8, (size_t)mc, st);
+        ce = cudaMemset2DAsync(wi, (size_t)(mc > 1 ? ldw : nnz) * 8, 0, (size_t)nnz * 8, (size_t)mc, st);
         chd_launch::prune_mask(f->sym, st, mc, y + i * ldy, ldy, cnt, act);
       }
       chd_launch::hess_up_pass(f->sym, st, &f->ex, mc, f->Wc, f->Vd, y + i * ldy, ldy, wi, ldw, f->ws, act);
       chd_launch::rtrans(f->sym, st, &f->ex, mc, 0, f->Lc, f->Dd, f->Qd, wi, ldw, f->ws, act);
     });
+    if (rc == CHD_OK && ce != cudaSuccess) rc = cuda_ok(ce);
     if (rc != CHD_OK) return rc;
   }
   return CHD_OK;
@@ -628,13 +630,15 @@ chd_status chd_hessian_factor_adj(chd_factor* f, int m, const double* w, int64_t
     key.v[2] = ldt;
     double* ti = t + i * ldt;
     const double* wi = w + i * ldw;
+    cudaError_t ce = cudaSuccess;
     rc = run_sequence(f, G_HFACTOR_ADJ, key, [&](cudaStream_t st) {
       if (ti != wi)
-        cudaMemcpy2DAsync(ti, (size_t)(mc > 1 ? ldt : nnz) * 8, wi, (size_t)(mc > 1 ? ldw : nnz) * 8,
-                          (size_t)nnz * 8, (size_t)mc, cudaMemcpyDeviceToDevice, st);
+        ce = cudaMemcpy2DAsync(ti, (size_t)(mc > 1 ? ldt : nnz) * 8, wi, (size_t)(mc > 1 ? ldw : nnz) * 8,
+                               (size_t)nnz * 8, (size_t)mc, cudaMemcpyDeviceToDevice, st);
       chd_launch::rtrans(f->sym, st, &f->ex, mc, 1, f->Lc, f->Dd, f->Qd, ti, ldt, f->ws, nullptr);
       chd_launch::hess_down_pass(f->sym, st, &f->ex, mc, f->Wc, ti, ldt, f->ws);
     });
+    if (rc == CHD_OK && ce != cudaSuccess) rc = cuda_ok(ce);
     if (rc != CHD_OK) return rc;
   }
   return CHD_OK;

@@ -58,3 +58,56 @@ def test_budget_admission():
     group, need, _ = pick(q(big), lambda p: False, fp, 0, 100, True, 64)
     assert [r.rid for r in group] == [0] and need == 500
     assert pick(q(big), lambda p: False, fp, 600, 1000, True, 64) is None
+
+
+def test_take_release_with_threads_on_host():
+    """The server's own _take/_release with worker threads and no device:
+    every request is taken exactly once, same-pattern Hessians are batched,
+    and no two workers hold one pattern at the same time."""
+    import threading
+    import time
+    from paper_1203_2742_gb300.serve import PatternState, Server
+
+    srv = Server.__new__(Server)  # host fields only: no factors, no device memory
+    srv.batching = True
+    srv.max_batch_rhs = 64
+    srv.states = [PatternState(sym=None, x=None, s=None) for _ in range(3)]
+    srv.budget = 10 ** 9
+    srv.in_use = 0
+    srv.cv = threading.Condition()
+    srv.queue = collections.deque()
+    srv.closed = False
+    srv.footprint = lambda req: 8 * req.m
+    reqs = [Request("hessian" if i % 2 else "factor", i % 3, 0.0, m=1 + i % 4, rid=i) for i in range(60)]
+    for r in reqs:
+        srv.queue.append(r)
+    taken, holders, lock, errors = [], {}, threading.Lock(), []
+
+    def worker():
+        while True:
+            group, need = srv._take()
+            if group is None:
+                return
+            p = group[0].pattern
+            with lock:
+                if holders.get(p):
+                    errors.append(p)
+                holders[p] = True
+                taken.extend(group)
+            time.sleep(0.001)
+            with lock:
+                holders[p] = False
+            srv._release(need, p)
+
+    ts = [threading.Thread(target=worker) for _ in range(4)]
+    for t in ts:
+        t.start()
+    srv.close = lambda: None
+    with srv.cv:
+        srv.closed = True
+        srv.cv.notify_all()
+    for t in ts:
+        t.join(timeout=30)
+    assert not errors
+    assert sorted(r.rid for r in taken) == list(range(60))
+    assert srv.in_use == 0 and not any(s.busy for s in srv.states)
