@@ -79,7 +79,12 @@ typedef struct {
   int32_t split_cols;      /* supernodes wider than 1.5 x split_cols columns are split into a
                               chain of supernodes of split_cols columns (V unchanged);
                               0 = default 256, negative = never split */
-  int32_t reserved[5];
+  int32_t chain_runs;      /* 1: runs of at least 8 one-column fronts with contiguous rows
+                              and the same |A_k| <= 64 (band chains) get their own
+                              chain-tier kernels for factor, gradient and Hessian (the
+                              other operations run them in the warp tier); 0 (default):
+                              off */
+  int32_t reserved[4];
 } chd_opts;
 
 /* Fill `opts` with the defaults: natural order, relax 0, tie_last 1, default
@@ -161,6 +166,22 @@ chd_status chd_symbolic_supernodes(const chd_symbolic* sym, const int64_t** snod
  * per right-hand side, out[4] completion.
  */
 chd_status chd_symbolic_flops(const chd_symbolic* sym, double out[5]);
+
+/*
+ * The launch schedule built by the analysis (host arrays owned by `sym`,
+ * valid until chd_symbolic_free).  A task is a list of fronts one worker
+ * processes in order, children before parents; the tasks of a level depend
+ * only on tasks of lower levels.  Level l holds tasks lvl_ptr[l] ..
+ * lvl_ptr[l+1]-1 of task_ptr (nlevels+1 entries), in this order: chain runs
+ * with |J| <= 32, chain runs with |J| <= 64, warp-tier, wide warp-tier,
+ * CTA-tier tasks and dense-tier fronts; lvl_counts[5*l .. 5*l+4] are the
+ * counts of those kinds except the CTA tier.  Task q holds the fronts
+ * task_fronts[task_ptr[q] .. task_ptr[q+1]-1].  For tests and tools.
+ * Errors: CHD_ERR_INVALID for NULL arguments.
+ */
+chd_status chd_symbolic_schedule(const chd_symbolic* sym, int64_t* nlevels, int64_t* ntasks,
+                                 const int32_t** lvl_ptr, const int32_t** lvl_counts,
+                                 const int32_t** task_ptr, const int32_t** task_fronts);
 
 void chd_symbolic_free(chd_symbolic* sym);
 

@@ -40,7 +40,7 @@ class ChdError(RuntimeError):
 class chd_opts(C.Structure):
     _fields_ = [("ordering", C.c_int32), ("user_perm", C.POINTER(C.c_int64)), ("relax", C.c_int32),
                 ("tie_last", C.c_int32), ("big_rows", C.c_int32), ("big_cols", C.c_int32),
-                ("split_cols", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("split_cols", C.c_int32), ("chain_runs", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 _p = C.c_void_p
@@ -88,6 +88,9 @@ _lib.chd_product.argtypes = [_p, _p, _p]
 _lib.chd_product.restype = C.c_int
 _lib.chd_schur.argtypes = [_p, C.c_int, _p, C.c_int64, _p, C.c_int64, _p, _p]
 _lib.chd_schur.restype = C.c_int
+_lib.chd_symbolic_schedule.argtypes = [_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)] + [
+    C.POINTER(C.POINTER(C.c_int32))] * 4
+_lib.chd_symbolic_schedule.restype = C.c_int
 for _f in ("chd_hessian_factor", "chd_hessian_factor_adj", "chd_hessian_factor_sparse"):
     getattr(_lib, _f).argtypes = [_p, C.c_int, _p, _i64, _p, _i64, _p]
     getattr(_lib, _f).restype = C.c_int
@@ -133,7 +136,7 @@ def _dptr(t, what, nnz=None, rows=None):
 # ---------------------------------------------------------------------------
 
 def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0,
-                big_cols=0, split_cols=0):
+                big_cols=0, split_cols=0, chain_runs=False):
     colptr = np.ascontiguousarray(colptr, dtype=np.int64)
     rowind = np.ascontiguousarray(rowind, dtype=np.int32)
     o = chd_opts()
@@ -149,13 +152,15 @@ def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_l
     o.big_rows = int(big_rows)
     o.big_cols = int(big_cols)
     o.split_cols = int(split_cols)
+    o.chain_runs = 1 if chain_runs else 0
     out = _p()
     rc = _lib.chd_analyze(int(n), colptr.ctypes.data, rowind.ctypes.data, C.byref(o), C.byref(out))
     _check(rc, "chd_analyze")
     return out
 
 
-def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big_cols=0, split_cols=0):
+def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big_cols=0, split_cols=0,
+          chain_runs=False):
     o = chd_opts()
     _lib.chd_opts_default(C.byref(o))
     o.ordering = ORDERINGS[ordering]
@@ -169,6 +174,7 @@ def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big
     o.big_rows = int(big_rows)
     o.big_cols = int(big_cols)
     o.split_cols = int(split_cols)
+    o.chain_runs = 1 if chain_runs else 0
     return o, keep
 
 
@@ -390,10 +396,10 @@ class Symbolic:
     """Owner of a ``chd_symbolic``: the analysed pattern and its clique tree."""
 
     def __init__(self, n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True,
-                 big_rows=0, big_cols=0, split_cols=0):
+                 big_rows=0, big_cols=0, split_cols=0, chain_runs=False):
         self._h = chd_analyze(n, colptr, rowind, ordering=ordering, perm=perm, relax=relax,
                               tie_last=tie_last, big_rows=big_rows, big_cols=big_cols,
-                              split_cols=split_cols)
+                              split_cols=split_cols, chain_runs=chain_runs)
         info = chd_symbolic_info(self._h)
         self.n = info["n"]
         self.nnz = info["nnz"]
@@ -410,6 +416,9 @@ class Symbolic:
     def instances(self):
         """(n_off, nnz_off): column and value ranges of the instances."""
         return chd_symbolic_batch_info(self._h)
+
+    def schedule(self):
+        return chd_symbolic_schedule(self._h)
 
     def supernodes(self):
         return chd_symbolic_supernodes(self._h, self.nsuper)
@@ -429,6 +438,21 @@ class Symbolic:
         if h:
             chd_symbolic_free(h)
             self._h = None
+
+
+def chd_symbolic_schedule(sym):
+    """The analysis' launch schedule: dict of numpy arrays lvl_ptr, lvl_counts
+    (nlevels x 5: chain runs |J| <= 32, chain runs |J| <= 64, warp, wide warp,
+    dense), task_ptr, task_fronts."""
+    nl, nt = C.c_int64(), C.c_int64()
+    ptrs = [C.POINTER(C.c_int32)() for _ in range(4)]
+    _check(_lib.chd_symbolic_schedule(sym, C.byref(nl), C.byref(nt), *[C.byref(p) for p in ptrs]),
+           "chd_symbolic_schedule")
+    L, T = nl.value, nt.value
+    arr = lambda p, k: np.ctypeslib.as_array(p, shape=(k,)).copy() if k > 0 else np.zeros(0, np.int32)
+    task_ptr = arr(ptrs[2], T + 1)
+    return {"lvl_ptr": arr(ptrs[0], L + 1), "lvl_counts": arr(ptrs[1], 5 * L).reshape(L, 5),
+            "task_ptr": task_ptr, "task_fronts": arr(ptrs[3], int(task_ptr[-1]) if T > 0 else 0)}
 
 
 class SymbolicBatch(Symbolic):

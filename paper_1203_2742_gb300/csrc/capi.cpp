@@ -437,6 +437,18 @@ chd_status chd_symbolic_supernodes(const chd_symbolic* s, const int64_t** snode_
   return CHD_OK;
 }
 
+chd_status chd_symbolic_schedule(const chd_symbolic* s, int64_t* nlevels, int64_t* ntasks, const int32_t** lvl_ptr,
+                                 const int32_t** lvl_counts, const int32_t** task_ptr, const int32_t** task_fronts) {
+  if (!s || !nlevels || !ntasks || !lvl_ptr || !lvl_counts || !task_ptr || !task_fronts) return CHD_ERR_INVALID;
+  *nlevels = (int64_t)s->lvl_ptr.size() - 1;
+  *ntasks = (int64_t)s->task_ptr.size() - 1;
+  *lvl_ptr = s->lvl_ptr.data();
+  *lvl_counts = s->lvl_counts.data();
+  *task_ptr = s->task_ptr.data();
+  *task_fronts = s->task_fronts.data();
+  return CHD_OK;
+}
+
 chd_status chd_symbolic_flops(const chd_symbolic* s, double out[5]) {
   if (!s || !out) return CHD_ERR_INVALID;
   for (int i = 0; i < 5; ++i) out[i] = s->flops[i];

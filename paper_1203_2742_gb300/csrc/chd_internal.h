@@ -97,7 +97,13 @@ struct chd_symbolic {
   // per level: the last lvl_big[l] tasks of the level are single big fronts
   // run by the multi-CTA dense tier
   std::vector<int32_t> lvl_big;
-  // per level: the first lvl_warp[l] tasks are warp-tier tasks (|J| <= 32),
+  // per level: the first lvl_r32[l] + lvl_r64[l] tasks are chain-tier runs
+  // (|J| <= 32, then |J| <= 64; all zero unless chain_runs)
+  std::vector<int32_t> lvl_r32, lvl_r64;
+  // per level l, five counts at 5*l: chain runs (|J| <= 32), chain runs
+  // (|J| <= 64), warp, wide warp and dense-tier tasks (chd_symbolic_schedule)
+  std::vector<int32_t> lvl_counts;
+  // per level, after the runs: lvl_warp[l] warp-tier tasks (|J| <= 32),
   // the next lvl_w64[l] wide warp-tier tasks (|J| <= 64)
   std::vector<int32_t> lvl_warp, lvl_w64;
   std::vector<char> is_big;  // per supernode

@@ -1016,6 +1016,16 @@ void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xc
                   double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
                   int64_t* status);
 
+// chain-tier launches (chain_tier.cu): runs of one-column band fronts
+void chain_factor(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* X, double* Lc, double* Wc,
+                  double* Dd, double* ws, double* ldet, int64_t* status);
+void chain_gradient(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Wc, double* Sc, double* g,
+                    double* Vd, double* ws);
+void chain_hess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, const double* Vd,
+                   const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws, const uint8_t* act);
+void chain_hess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* T,
+                     int64_t ldt, double* ws);
+
 // warp-tier launches (warp_tier.cu): w32 for |J| <= 32, w64 for |J| <= 64
 namespace w32 {
 void warp_product(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Lc, double* X, double* ws);
@@ -1094,11 +1104,15 @@ struct BigFork {
 // [tw, tw + nw64) of the wide warp tier (|J| <= 64), then [tc, tc + ncta) of
 // the CTA tier, then nbig single big fronts of the dense tier.
 struct Level {
+  int tr, nr32, nr64;  // chain runs: [tr, tr + nr32) |J| <= 32, then nr64 with |J| <= 64
   int t0, nwarp, tw, nw64, tc, ncta, nbig;
 };
 static inline Level level(const chd_symbolic* s, int l) {
   Level v;
-  v.t0 = s->lvl_ptr[l];
+  v.tr = s->lvl_ptr[l];
+  v.nr32 = s->lvl_r32.empty() ? 0 : s->lvl_r32[l];
+  v.nr64 = s->lvl_r64.empty() ? 0 : s->lvl_r64[l];
+  v.t0 = v.tr + v.nr32 + v.nr64;
   const int nt = s->lvl_ptr[l + 1] - v.t0;
   v.nwarp = s->lvl_warp[l];
   v.nw64 = s->lvl_w64[l];
@@ -1121,6 +1135,7 @@ void factor(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double
     bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
       big_factor(s, bs, xs, xc, big_front(s, v, i), X, Lc, Wc, Dd, ws, ldet, status);
     });
+    if (v.nr32 + v.nr64) chain_factor(s, st, v.tr, v.nr32 + v.nr64, X, Lc, Wc, Dd, ws, ldet, status);
     if (v.nwarp) w32::warp_factor(s, st, v.t0, v.nwarp, X, Lc, Wc, Dd, ws, ldet, status);
     if (v.nw64) w64::warp_factor(s, st, v.tw, v.nw64, X, Lc, Wc, Dd, ws, ldet, status);
     if (v.ncta) {
@@ -1139,6 +1154,8 @@ void product(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doubl
     bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
       big_product(s, bs, xs, xc, big_front(s, v, i), Lc, X, ws);
     });
+    if (v.nr32) w32::warp_product(s, st, v.tr, v.nr32, Lc, X, ws);
+    if (v.nr64) w64::warp_product(s, st, v.tr + v.nr32, v.nr64, Lc, X, ws);
     if (v.nwarp) w32::warp_product(s, st, v.t0, v.nwarp, Lc, X, ws);
     if (v.nw64) w64::warp_product(s, st, v.tw, v.nw64, Lc, X, ws);
     if (v.ncta) {
@@ -1161,6 +1178,7 @@ void gradient(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
       k_gradient<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Wc, Sc, g, Vd, ws);
       count();
     }
+    if (v.nr32 + v.nr64) chain_gradient(s, st, v.tr, v.nr32 + v.nr64, Wc, Sc, g, Vd, ws);
     if (v.nwarp) w32::warp_gradient(s, st, v.t0, v.nwarp, Wc, Sc, g, Vd, ws);
     if (v.nw64) w64::warp_gradient(s, st, v.tw, v.nw64, Wc, Sc, g, Vd, ws);
     bf.join_now();
@@ -1177,6 +1195,7 @@ void hess_up_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m,
     bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
       big_hess_up(s, bs, xs, xc, m, big_front(s, v, i), Wc, Vd, Y, ldy, T, ldt, ws, act);
     });
+    if (v.nr32 + v.nr64) chain_hess_up(s, st, v.tr, v.nr32 + v.nr64, m, Wc, Vd, Y, ldy, T, ldt, ws, act);
     if (v.nwarp) w32::warp_hess_up(s, st, v.t0, v.nwarp, m, Wc, Vd, Y, ldy, T, ldt, ws, act);
     if (v.nw64) w64::warp_hess_up(s, st, v.tw, v.nw64, m, Wc, Vd, Y, ldy, T, ldt, ws, act);
     if (v.ncta) {
@@ -1199,6 +1218,7 @@ void hess_down_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int 
       k_hess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, T, ldt, ws);
       count();
     }
+    if (v.nr32 + v.nr64) chain_hess_down(s, st, v.tr, v.nr32 + v.nr64, m, Wc, T, ldt, ws);
     if (v.nwarp) w32::warp_hess_down(s, st, v.t0, v.nwarp, m, Wc, T, ldt, ws);
     if (v.nw64) w64::warp_hess_down(s, st, v.tw, v.nw64, m, Wc, T, ldt, ws);
     bf.join_now();
@@ -1251,6 +1271,8 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
       k_ihess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
       count();
     }
+    if (v.nr32) w32::warp_ihess_down(s, st, v.tr, v.nr32, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    if (v.nr64) w64::warp_ihess_down(s, st, v.tr + v.nr32, v.nr64, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
     if (v.nwarp) w32::warp_ihess_down(s, st, v.t0, v.nwarp, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
     if (v.nw64) w64::warp_ihess_down(s, st, v.tw, v.nw64, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
     bf.join_now();
@@ -1261,6 +1283,8 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
     bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
       big_ihess_up(s, bs, xs, xc, m, big_front(s, v, i), Wc, Y, ldy, ws);
     });
+    if (v.nr32) w32::warp_ihess_up(s, st, v.tr, v.nr32, m, Wc, Y, ldy, ws);
+    if (v.nr64) w64::warp_ihess_up(s, st, v.tr + v.nr32, v.nr64, m, Wc, Y, ldy, ws);
     if (v.nwarp) w32::warp_ihess_up(s, st, v.t0, v.nwarp, m, Wc, Y, ldy, ws);
     if (v.nw64) w64::warp_ihess_up(s, st, v.tw, v.nw64, m, Wc, Y, ldy, ws);
     if (v.ncta) {

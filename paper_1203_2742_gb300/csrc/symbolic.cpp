@@ -638,6 +638,47 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     vector<vector<int32_t>> tasks;
     vector<int64_t> tlevel;
     vector<int> ttier;
+    // chain runs (option chain_runs): maximal sequences t0 < ... < t1 of
+    // one-column fronts with rows {j, j+1, .., j+a}, the same a (1..64), each
+    // the only child of the next, t0 a leaf; at least kMinRun fronts.  Each
+    // run is one task of task tier 5 (|J| <= 32) or 6 (|J| <= 64).
+    constexpr int64_t kMinRun = 8;
+    vector<int64_t> run_of(nsn, -1);
+    if (opts.chain_runs > 0) {
+      auto a_of = [&](int64_t t) { return (s->rows_ptr[t + 1] - s->rows_ptr[t]) - (s->sn_ptr[t + 1] - s->sn_ptr[t]); };
+      auto nkids = [&](int64_t t) { return s->ch_ptr[t + 1] - s->ch_ptr[t]; };
+      auto fits = [&](int64_t t) {
+        if (s->sn_ptr[t + 1] - s->sn_ptr[t] != 1 || s->is_big[t] || s->grp_of[t] >= 0) return false;
+        const int64_t a = a_of(t);
+        if (a < 1 || a > 64) return false;
+        for (int64_t i = 0; i <= a; ++i)
+          if (s->rows[s->rows_ptr[t] + i] != s->sn_ptr[t] + i) return false;
+        return true;
+      };
+      int64_t t = 0;
+      while (t < nsn) {
+        if (!fits(t) || nkids(t) != 0) {
+          ++t;
+          continue;
+        }
+        int64_t u = t;
+        while (u + 1 < nsn && s->sn_par[u] == u + 1 && fits(u + 1) && a_of(u + 1) == a_of(t) && nkids(u + 1) == 1)
+          ++u;
+        if (u - t + 1 >= kMinRun) {
+          const int64_t id = (int64_t)tasks.size();
+          vector<int32_t> seq;
+          for (int64_t v = t; v <= u; ++v) {
+            seq.push_back((int32_t)v);
+            run_of[v] = id;
+            task_of[v] = id;
+          }
+          tasks.push_back(seq);
+          tlevel.push_back(0);
+          ttier.push_back(a_of(t) + 1 <= 32 ? 5 : 6);
+        }
+        t = u + 1;
+      }
+    }
     // Supernode numbering is a postorder of the clique tree (children precede
     // parents, subtrees are contiguous), so the subtree of t is [t - size(t) + 1, t].
     vector<int64_t> sub(nsn, 1);
@@ -648,7 +689,12 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
       int64_t p = s->sn_par[t];
       if (p >= 0 && !top[p]) continue;
       vector<int32_t> seq;
-      for (int64_t u = t - sub[t] + 1; u <= t; ++u) { seq.push_back((int32_t)u); task_of[u] = (int64_t)tasks.size(); }
+      for (int64_t u = t - sub[t] + 1; u <= t; ++u) {
+        if (run_of[u] >= 0) continue;  // in its own chain-run task
+        seq.push_back((int32_t)u);
+        task_of[u] = (int64_t)tasks.size();
+      }
+      if (seq.empty()) continue;
       tasks.push_back(seq);
       tlevel.push_back(0);
       ttier.push_back(0);
@@ -657,7 +703,7 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     for (int64_t t = 0; t < nsn; ++t)
       if (top[t] && s->sn_par[t] >= 0) { ntopkids[s->sn_par[t]]++; onlykid[s->sn_par[t]] = t; }
     for (int64_t t = 0; t < nsn; ++t) {
-      if (!top[t]) continue;
+      if (!top[t] || run_of[t] >= 0) continue;
       if (tier[t] == 4) {  // leaf group: one task, run with the dense fronts
         const int64_t g0 = s->grp_first[s->grp_of[t]];
         if (g0 == t) {
@@ -670,7 +716,7 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
         }
         continue;
       }
-      if (ntopkids[t] == 1 && tier[t] != 2 && tier[onlykid[t]] == tier[t]) {
+      if (ntopkids[t] == 1 && tier[t] != 2 && tier[onlykid[t]] == tier[t] && run_of[onlykid[t]] < 0) {
         int64_t tk = task_of[onlykid[t]];
         tasks[tk].push_back((int32_t)t);
         task_of[t] = tk;
@@ -698,12 +744,16 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     s->task_ptr.assign(1, 0);
     s->task_fronts.clear();
     s->lvl_ptr.assign(1, 0);
+    s->lvl_r32.clear();
+    s->lvl_r64.clear();
+    s->lvl_counts.clear();
     s->lvl_warp.clear();
     s->lvl_w64.clear();
     s->lvl_big.clear();
     for (int64_t l = 0; l < nlev; ++l) {
-      int32_t cnt[4] = {0, 0, 0, 0};
-      for (int tr : {0, 3, 1, 2}) {  // warp, wide warp, CTA tasks, then dense fronts
+      int32_t cnt[7] = {0, 0, 0, 0, 0, 0, 0};
+      // chain runs, warp, wide warp, CTA tasks, then dense fronts
+      for (int tr : {5, 6, 0, 3, 1, 2}) {
         for (int64_t q : bylev[l]) {
           if (ttier[q] != tr) continue;
           for (int32_t f : tasks[q]) s->task_fronts.push_back(f);
@@ -712,6 +762,9 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
         }
       }
       s->lvl_ptr.push_back((int32_t)(s->task_ptr.size() - 1));
+      s->lvl_r32.push_back(cnt[5]);
+      s->lvl_r64.push_back(cnt[6]);
+      for (int c : {cnt[5], cnt[6], cnt[0], cnt[3], cnt[2]}) s->lvl_counts.push_back(c);
       s->lvl_warp.push_back(cnt[0]);
       s->lvl_w64.push_back(cnt[3]);
       s->lvl_big.push_back(cnt[2]);

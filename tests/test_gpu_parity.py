@@ -308,6 +308,59 @@ def test_schur_complement(name):
     assert np.linalg.eigvalsh(0.5 * (H + H.T)).min() > 0  # H is positive definite
 
 
+CHAIN_CASES = {
+    "band200_w8": lambda: W.band(200, 8),      # |J| = 9: one run of 191 fronts
+    "band300_w40": lambda: W.band(300, 40),    # |J| = 41
+    "band120_w63": lambda: W.band(120, 63),    # |J| = 64, the largest window
+    "band90_w1": lambda: W.band(90, 1),        # a = 1
+}
+
+
+@pytest.mark.parametrize("name", list(CHAIN_CASES))
+def test_chain_runs(name):
+    """The chain tier (sliding windows along runs of one-column band fronts)
+    against the oracle, and against the same pattern without the option:
+    factor, log det, gradient, Hessian, inverse Hessian, product, Hessian
+    factor (plain and pruned) and its adjoint."""
+    B = lib()
+    pattern = CHAIN_CASES[name]()
+    rng = np.random.default_rng(41)
+    on = B.Symbolic(*pattern, chain_runs=True)
+    off = B.Symbolic(*pattern)
+    assert np.array_equal(on.colptr, off.colptr) and np.array_equal(on.rowind, off.rowind)
+    n, cp, ri = on.n, on.colptr, on.rowind
+    x = W.diag_dominant(n, cp, ri, rng)
+    ys = W.uniform_sym(n, cp, ri, rng, count=3)
+    y2 = np.zeros_like(ys)
+    for i in range(3):
+        y2[i, rng.choice(len(ri), size=2, replace=False)] = rng.uniform(-1.0, 1.0, size=2)
+    c = Case(pattern, seed=41)
+    dev = c.dev
+    res = {}
+    for key, sym in (("on", on), ("off", off)):
+        f = sym.factor(dev(x))
+        l, d = f.export()
+        res[key] = dict(logdet=f.logdet(), l=c.host(l), d=c.host(d), g=c.host(f.gradient()),
+                        t=c.host(f.hessian(dev(ys))), yi=c.host(f.inv_hessian(dev(ys))), xp=c.host(f.product()),
+                        w=c.host(f.hessian_factor(dev(ys))), w2=c.host(f.hessian_factor(dev(y2), sparse=True)),
+                        ta=c.host(f.hessian_factor_adj(dev(ys))))
+    err = lambda a, b: OD.rel_err(n, cp, ri, a, b)
+    for key in ("g", "l", "xp"):
+        assert err(res["on"][key], res["off"][key]) < 1e-12, key
+    assert abs(res["on"]["logdet"] - res["off"]["logdet"]) <= 1e-12 * max(1.0, abs(res["off"]["logdet"]))
+    for key in ("t", "yi", "w", "w2", "ta"):
+        for i in range(3):
+            assert err(res["on"][key][i], res["off"][key][i]) < 1e-11, key
+    # and the oracle
+    assert abs(res["on"]["logdet"] - OD.logdet(n, cp, ri, x)) <= 1e-10 * max(1.0, abs(OD.logdet(n, cp, ri, x)))
+    assert err(res["on"]["g"], OD.gradient(n, cp, ri, x)) < TOL
+    want = OD.hessian(n, cp, ri, x, list(ys))
+    wantw = OD.hessian_factor(n, cp, ri, x, list(ys))
+    for i in range(3):
+        assert err(res["on"]["t"][i], want[i]) < TOL
+        assert err(res["on"]["w"][i], wantw[i]) < TOL
+
+
 def test_planted_condition_1e6():
     def planted(s, rng):
         x, _, _ = W.planted_factor(s.n, s.colptr, s.rowind, rng, dmin=1e-6, dmax=1.0)

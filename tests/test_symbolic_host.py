@@ -163,3 +163,94 @@ def test_batch_analysis_equals_single_analyses():
         assert ni == s1.n
         assert (perm == s1.perm).all()
         assert (cp == s1.colptr).all() and (ri == s1.rowind).all()
+
+
+# ---------------------------------------------------------------------------
+# launch schedule: tasks and levels
+# ---------------------------------------------------------------------------
+
+SCHEDULE_CASES = {
+    "band200_w8": lambda B, cr: B.Symbolic(*W.band(200, 8), chain_runs=cr),
+    "band300_w40": lambda B, cr: B.Symbolic(*W.band(300, 40), chain_runs=cr),
+    "band500_w70": lambda B, cr: B.Symbolic(*W.band(500, 70), chain_runs=cr),
+    "arrow150_w48": lambda B, cr: B.Symbolic(*W.arrow(150, 48), chain_runs=cr),
+    "grid20_nd": lambda B, cr: B.Symbolic(*W.permute(W.grid2d(20, 20), W.nested_dissection((20, 20), leaf=6)),
+                                          chain_runs=cr),
+    "er400_mindeg": lambda B, cr: B.Symbolic(*W.erdos_renyi(400, 0.02, np.random.default_rng(3)),
+                                             ordering="mindeg", chain_runs=cr),
+    "dense_tier_er": lambda B, cr: B.Symbolic(*W.erdos_renyi(300, 0.02, np.random.default_rng(5)),
+                                              ordering="mindeg", relax=16, big_rows=40, big_cols=20,
+                                              chain_runs=cr),
+    "batch": lambda B, cr: B.SymbolicBatch([W.band(120, 6), W.grid2d(8, 8), W.band(90, 30)],
+                                           chain_runs=cr),
+}
+
+
+@pytest.mark.parametrize("chain", [False, True])
+@pytest.mark.parametrize("name", list(SCHEDULE_CASES))
+def test_schedule_invariants(name, chain):
+    """Every front in exactly one task (a leaf group through its first
+    member); children before parents inside a task; a task only depends on
+    tasks of lower levels; chain runs (only with the option) are runs of
+    one-column fronts with contiguous rows, one a, 1 <= a <= 64, each the
+    only child of the next, starting at a leaf."""
+    B = lib()
+    sym = SCHEDULE_CASES[name](B, chain)
+    sp, par, rp, rows = sym.supernodes()
+    nsn = len(sp) - 1
+    d = sym.schedule()
+    lp, lc, tp, tf = d["lvl_ptr"], d["lvl_counts"], d["task_ptr"], d["task_fronts"]
+    assert len(set(tf.tolist())) == len(tf)
+    task_of = np.full(nsn, -1, np.int64)
+    for q in range(len(tp) - 1):
+        task_of[tf[tp[q]:tp[q + 1]]] = q
+    # fronts outside the lists: members of a leaf group, after their first
+    # member (one-column leaves of one parent with the same A)
+    A_of = lambda k: rows[rp[k] + (sp[k + 1] - sp[k]):rp[k + 1]].tolist()
+    for k in range(nsn):
+        if task_of[k] < 0:
+            g0 = k - 1
+            while task_of[g0] < 0:
+                g0 -= 1
+            for g in range(g0, k + 1):
+                assert sp[g + 1] - sp[g] == 1 and par[g] == par[k] and A_of(g) == A_of(k)
+            task_of[k] = task_of[g0]
+    level_of = np.empty(len(tp) - 1, np.int64)
+    for l in range(len(lp) - 1):
+        level_of[lp[l]:lp[l + 1]] = l
+    pos = np.full(nsn, -1, np.int64)
+    pos[tf] = np.arange(len(tf))
+    nkids = np.zeros(nsn, np.int64)
+    for k in range(nsn):
+        if par[k] >= 0:
+            nkids[par[k]] += 1
+            if task_of[par[k]] == task_of[k]:
+                assert pos[k] < pos[par[k]] or pos[k] < 0
+            else:
+                assert level_of[task_of[k]] < level_of[task_of[par[k]]]
+    nrun = 0
+    for l in range(len(lp) - 1):
+        r32, r64, warp, w64, big = lc[l]
+        assert r32 + r64 + warp + w64 + big <= lp[l + 1] - lp[l]
+        if not chain:
+            assert r32 == 0 and r64 == 0
+        for i in range(r32 + r64):
+            q = lp[l] + i
+            fr = tf[tp[q]:tp[q + 1]]
+            nrun += 1
+            assert len(fr) >= 8 and np.array_equal(fr, np.arange(fr[0], fr[0] + len(fr)))
+            a = int(rp[fr[0] + 1] - rp[fr[0]]) - 1
+            assert 1 <= a <= 64 and ((a + 1 <= 32) == (i < r32))
+            assert nkids[fr[0]] == 0
+            for j, k in enumerate(fr):
+                assert sp[k + 1] - sp[k] == 1
+                J = rows[rp[k]:rp[k + 1]]
+                assert np.array_equal(J, np.arange(sp[k], sp[k] + a + 1))
+                if j + 1 < len(fr):
+                    assert par[k] == k + 1
+                if j > 0:
+                    assert nkids[k] == 1
+    if chain and name in ("band200_w8", "band300_w40"):
+        assert nrun >= 1  # the band chains are found (a <= 64)
+    if name == "band500_w70":
+        assert nrun == 0  # a = 70 > 64: no chain tier
