@@ -1330,8 +1330,7 @@ void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xc
   chd::big::complete_front(s, chd::big::make_ctx(st, xs, xcap), k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
 }
 void big_rtrans(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, int dir,
-                const double* Lc, const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws) {
-  (void)Dd;
+                const double* Lc, const double* Qd, double* Z, int64_t ldz, double* ws) {
   if (s->grp_of[k] >= 0) return chd::big::group_rtrans(s, chd::big::make_ctx(st, xs, xcap), m, s->grp_of[k], dir, Lc, Qd, Z, ldz, ws);
   chd::big::rtrans_front(s, chd::big::make_ctx(st, xs, xcap), m, k, dir, Lc, Qd, Z, ldz, ws);
 }

@@ -34,7 +34,7 @@ void prune_mask(const chd_symbolic* s, cudaStream_t st, int m, const double* Y, 
 void hess_down_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, double* T,
                     int64_t ldt, double* ws);
 void rtrans(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, int dir, const double* Lc,
-            const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws, const uint8_t* act);
+            const double* Qd, double* Z, int64_t ldz, double* ws, const uint8_t* act);
 void product(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Lc, double* X, double* ws);
 int64_t schur_scratch(const chd_symbolic* s, int m);
 void schur(const chd_symbolic* s, cudaStream_t st, int m, const double* A, int64_t lda, const double* T, int64_t ldt,
@@ -601,7 +601,7 @@ static chd_status hessian_factor(chd_factor* f, int m, const double* y, int64_t 
         chd_launch::prune_mask(f->sym, st, mc, y + i * ldy, ldy, cnt, act);
       }
       chd_launch::hess_up_pass(f->sym, st, &f->ex, mc, f->Wc, f->Vd, y + i * ldy, ldy, wi, ldw, f->ws, act);
-      chd_launch::rtrans(f->sym, st, &f->ex, mc, 0, f->Lc, f->Dd, f->Qd, wi, ldw, f->ws, act);
+      chd_launch::rtrans(f->sym, st, &f->ex, mc, 0, f->Lc, f->Qd, wi, ldw, f->ws, act);
     });
     if (rc == CHD_OK && ce != cudaSuccess) rc = cuda_ok(ce);
     if (rc != CHD_OK) return rc;
@@ -647,7 +647,7 @@ chd_status chd_hessian_factor_adj(chd_factor* f, int m, const double* w, int64_t
       if (ti != wi)
         ce = cudaMemcpy2DAsync(ti, (size_t)(mc > 1 ? ldt : nnz) * 8, wi, (size_t)(mc > 1 ? ldw : nnz) * 8,
                                (size_t)nnz * 8, (size_t)mc, cudaMemcpyDeviceToDevice, st);
-      chd_launch::rtrans(f->sym, st, &f->ex, mc, 1, f->Lc, f->Dd, f->Qd, ti, ldt, f->ws, nullptr);
+      chd_launch::rtrans(f->sym, st, &f->ex, mc, 1, f->Lc, f->Qd, ti, ldt, f->ws, nullptr);
       chd_launch::hess_down_pass(f->sym, st, &f->ex, mc, f->Wc, ti, ldt, f->ws);
     });
     if (rc == CHD_OK && ce != cudaSuccess) rc = cuda_ok(ce);

@@ -1232,7 +1232,7 @@ void hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, cons
 // M <-> W for every front (independent fronts): plain fronts in one launch,
 // dense fronts and leaf groups on the side streams
 void big_rtrans(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, int dir,
-                const double* Lc, const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws);
+                const double* Lc, const double* Qd, double* Z, int64_t ldz, double* ws);
 // per right-hand side and front: active for the pruned Hessian factor
 void prune_mask(const chd_symbolic* s, cudaStream_t st, int m, const double* Y, int64_t ldy, int32_t* cnt,
                 uint8_t* act) {
@@ -1243,12 +1243,12 @@ void prune_mask(const chd_symbolic* s, cudaStream_t st, int m, const double* Y, 
   count();
 }
 void rtrans(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, int dir, const double* Lc,
-            const double* Dd, const double* Qd, double* Z, int64_t ldz, double* ws, const uint8_t* act) {
+            const double* Qd, double* Z, int64_t ldz, double* ws, const uint8_t* act) {
   std::vector<int32_t> dense = s->big_fronts;
   for (int64_t g0 : s->grp_first) dense.push_back((int32_t)g0);
   BigFork bf{ex, st};
   bf.run((int)dense.size(), [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-    big_rtrans(s, bs, xs, xc, m, dense[i], dir, Lc, Dd, Qd, Z, ldz, ws);
+    big_rtrans(s, bs, xs, xc, m, dense[i], dir, Lc, Qd, Z, ldz, ws);
   });
   if (s->dev.plain_count > 0) {
     SymDev D = s->dev;
