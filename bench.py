@@ -41,9 +41,11 @@ METRIC = "Hessian evals/s"
 UNIT = "evals/s"
 # FP64 roofline of the front arithmetic: 152 SMs x 2.07 GHz x 2 FMA per clock per SM
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
-# DRAM bytes (read + write) of one Hessian call, from one ncu capture of that call
-# (profiles/dram_traffic_hessian_er5000.md); None where no capture was taken
-TRAFFIC_PER_HESSIAN_CALL = {"er5000": 6.39e9}
+# DRAM bytes (read + write) of one Hessian call, from one ncu capture of the
+# current kernels; None where there is none.  (The er5000 capture in
+# profiles/dram_traffic_hessian_er5000.md, 6.39 GB, predates the activity-mask
+# checks added to the bottom-up kernels, so it is not reported as current.)
+TRAFFIC_PER_HESSIAN_CALL = {}
 
 
 def make_workload(name):
