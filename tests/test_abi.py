@@ -45,3 +45,42 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
         raise AssertionError("expected CHD_ERR_INVALID")
     except B.ChdError as e:
         assert e.code == B.CHD_ERR_INVALID
+
+
+def test_null_handles_are_rejected_without_a_gpu():
+    """Every numeric entry point checks its handles before any device work:
+    a NULL factor or symbolic object gives CHD_ERR_INVALID."""
+    B = lib()
+    so = ctypes.CDLL(B.library_path())
+    N = None
+    i64 = ctypes.c_int64
+    one = ctypes.c_int(1)
+    out = ctypes.c_void_p()
+    calls = {
+        "chd_factor_new": (N, N, N, ctypes.byref(out)),
+        "chd_refactor": (N, N, N),
+        "chd_logdet": (N, ctypes.byref(ctypes.c_double())),
+        "chd_logdet_batch": (N, N),
+        "chd_gradient": (N, N, N),
+        "chd_hessian": (N, one, N, i64(0), N, i64(0), N),
+        "chd_hessian_noalloc": (N, one, N, i64(0), N, i64(0), N),
+        "chd_inv_hessian": (N, one, N, i64(0), N, i64(0), N),
+        "chd_hessian_factor": (N, one, N, i64(0), N, i64(0), N),
+        "chd_hessian_factor_adj": (N, one, N, i64(0), N, i64(0), N),
+        "chd_hessian_factor_sparse": (N, one, N, i64(0), N, i64(0), N),
+        "chd_complete": (N, N, N, ctypes.byref(out), N),
+        "chd_recomplete": (N, N, N, N),
+        "chd_product": (N, N, N),
+        "chd_schur": (N, one, N, i64(0), N, i64(0), N, N),
+        "chd_factor_set_graphs": (N, one),
+        "chd_factor_set_workspace_limit": (N, ctypes.c_size_t(0)),
+        "chd_factor_release_workspace": (N,),
+        "chd_factor_workspace_bytes": (N, ctypes.byref(ctypes.c_size_t())),
+        "chd_symbolic_schedule": (N,) + tuple(ctypes.byref(x) for x in (i64(), i64())) + (N,) * 4,
+    }
+    for name, args in calls.items():
+        f = getattr(so, name)
+        f.restype = ctypes.c_int
+        assert f(*args) == B.CHD_ERR_INVALID, name
+    so.chd_factor_free(N)
+    so.chd_symbolic_free(N)
