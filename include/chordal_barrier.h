@@ -81,9 +81,10 @@ typedef struct {
                               0 = default 256, negative = never split */
   int32_t chain_runs;      /* 1: runs of at least 8 one-column fronts with contiguous rows
                               and the same |A_k| <= 64 (band chains) get their own
-                              chain-tier kernels for factor, gradient and Hessian (the
-                              other operations run them in the warp tier); 0 (default):
-                              off */
+                              chain-tier kernels for factor, gradient, Hessian and Hessian
+                              factor (the other operations run them in the warp tier);
+                              2: as 1 and the inverse Hessian's passes too (experimental:
+                              not yet verified on a GPU); 0 (default): off */
   int32_t reserved[4];
 } chd_opts;
 

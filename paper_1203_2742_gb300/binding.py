@@ -152,7 +152,7 @@ def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_l
     o.big_rows = int(big_rows)
     o.big_cols = int(big_cols)
     o.split_cols = int(split_cols)
-    o.chain_runs = 1 if chain_runs else 0
+    o.chain_runs = int(chain_runs)
     out = _p()
     rc = _lib.chd_analyze(int(n), colptr.ctypes.data, rowind.ctypes.data, C.byref(o), C.byref(out))
     _check(rc, "chd_analyze")
@@ -174,7 +174,7 @@ def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big
     o.big_rows = int(big_rows)
     o.big_cols = int(big_cols)
     o.split_cols = int(split_cols)
-    o.chain_runs = 1 if chain_runs else 0
+    o.chain_runs = int(chain_runs)
     return o, keep
 
 

@@ -316,6 +316,121 @@ __global__ void __launch_bounds__(CT) kc_hess_down(SymDev S, int task0, const do
   }
 }
 
+// Algorithm 5.2 step 1-2 for one-column fronts (top-down): with the window
+// V' (the input T on A_j x A_j, gathered from the parent's T-front),
+// M_A = T_A + V' L_A, M_jj = T_jj + L_A^T (T_A + M_A), K_jj = D M_jj D,
+// K_A = V^{-1} (M_A D) (V^{-1} per front, formed by the inverse-Hessian
+// setup); the child's window is [T_jj T_A^T; T_A V'] on its rows.
+__global__ void __launch_bounds__(CT) kc_ihess_down(SymDev S, int task0, const double* Wc, const double* Dd,
+                                                   const double* Rd, const double* Tin, int64_t ldt, double* Y,
+                                                   int64_t ldy, double* ws) {
+  __shared__ double V[WS][WS + 1];
+  __shared__ double lw[WS];
+  __shared__ double tt[WS];
+  __shared__ double ma[WS];
+  const Run R = run_of(S, task0 + blockIdx.x);
+  const int64_t y = blockIdx.y;
+  Tin += y * ldt;
+  Y += y * ldy;
+  ws += y * S.f_total;
+  const int a = R.a, tid = threadIdx.x;
+  gather_window(S, R, ws, V, tid);
+  const int64_t top = R.base0 + (int64_t)(R.L - 1) * (a + 1);
+  double wv = tid <= a ? Wc[top + tid] : 0.0;
+  double tv = tid <= a ? Tin[top + tid] : 0.0;
+  __syncthreads();
+  for (int i = R.L - 1; i >= 0; --i) {
+    const int64_t base = R.base0 + (int64_t)i * (a + 1);
+    if (tid <= a) {
+      lw[tid] = wv;
+      tt[tid] = tv;
+    }
+    if (i > 0 && tid <= a) {
+      wv = Wc[base - (a + 1) + tid];
+      tv = Tin[base - (a + 1) + tid];
+    }
+    __syncthreads();
+    const double wr = window_row_dot(V, i + 1, a, lw + 1, tid);
+    if (tid % TPR == 0 && tid / TPR < a) ma[tid / TPR] = tt[1 + tid / TPR] + wr;
+    __syncthreads();
+    const double dd = Dd[R.d0 + 4 * (int64_t)i];
+    const double mnn = tt[0] + all_sum(a, [&](int r) { return lw[1 + r] * (tt[1 + r] + ma[r]); }, tid);
+    if (tid == 0) Y[base] = dd * (mnn * dd);
+    {
+      const int r = tid / TPR, part = tid % TPR;
+      const double* Rb = Rd + R.v0 + (int64_t)i * R.vstride;
+      double acc = 0.0;
+      if (r < a)
+        for (int s = part; s < a; s += TPR)
+          acc = fma(__ldg(Rb + (r >= s ? r + (int64_t)s * a : s + (int64_t)r * a)), ma[s] * dd, acc);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (part == 0 && r < a) Y[base + 1 + r] = acc;
+    }
+    const int si = slot(i);
+    if (tid == 0) V[si][si] = tt[0];
+    for (int r = tid; r < a - 1; r += CT) {
+      V[si][slot(i + 1 + r)] = tt[1 + r];
+      V[slot(i + 1 + r)][si] = tt[1 + r];
+    }
+    __syncthreads();
+  }
+}
+
+// Algorithm 5.2 step 3 for one-column fronts (bottom-up): with K from the
+// top-down pass and F the child's U' on this front's rows,
+// P = K_A + L_A K_jj / 2, Y_jj = K_jj - F_jj, Y_A = 2 P - K_A - F_A,
+// U' = F_AA - (P L_A^T + L_A P^T).
+__global__ void __launch_bounds__(CT) kc_ihess_up(SymDev S, int task0, const double* Wc, double* Y, int64_t ldy,
+                                                 double* ws) {
+  __shared__ double U[WS][WS + 1];
+  __shared__ double lw[WS];
+  __shared__ double kk[WS];
+  __shared__ double ff[WS];
+  __shared__ double pp[WS];
+  const Run R = run_of(S, task0 + blockIdx.x);
+  const int64_t y = blockIdx.y;
+  Y += y * ldy;
+  ws += y * S.f_total;
+  const int a = R.a, tid = threadIdx.x;
+  for (int e = tid; e < WS * (WS + 1); e += CT) (&U[0][0])[e] = 0.0;
+  double kv = tid <= a ? Y[R.base0 + tid] : 0.0;
+  double wv = tid <= a ? Wc[R.base0 + tid] : 0.0;
+  __syncthreads();
+  for (int i = 0; i < R.L; ++i) {
+    const int64_t base = R.base0 + (int64_t)i * (a + 1);
+    if (tid <= a) {
+      kk[tid] = kv;
+      lw[tid] = wv;
+      ff[tid] = U[slot(i + tid)][slot(i)];
+    }
+    if (i + 1 < R.L && tid <= a) {
+      kv = Y[base + (a + 1) + tid];
+      wv = Wc[base + (a + 1) + tid];
+    }
+    __syncthreads();
+    if (tid < a) pp[tid] = fma(0.5 * lw[1 + tid], kk[0], kk[1 + tid]);
+    __syncthreads();
+    if (tid <= a) Y[base + tid] = tid == 0 ? kk[0] - ff[0] : 2.0 * pp[tid - 1] - kk[tid] - ff[tid];
+    for (int e = tid; e < a * a; e += CT) {
+      const int p = e / a, q = e - (e / a) * a;
+      U[slot(i + 1 + p)][slot(i + 1 + q)] -= fma(pp[p], lw[1 + q], lw[1 + p] * pp[q]);
+    }
+    const int si = slot(i);
+    for (int e = tid; e < WS; e += CT) {
+      U[si][e] = 0.0;
+      U[e][si] = 0.0;
+    }
+    __syncthreads();
+  }
+  double* G = ws + R.f0 + (int64_t)(R.L - 1) * R.fstride;
+  const int J = a + 1;
+  for (int e = tid; e < a * a; e += CT) {
+    const int p = e / a, q = e - (e / a) * a;
+    if (p >= q) G[(1 + p) + (int64_t)(1 + q) * J] = U[slot(R.L + p)][slot(R.L + q)];
+  }
+}
+
 }  // namespace chain
 }  // namespace chd
 
@@ -339,6 +454,17 @@ void chain_hess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m
 void chain_hess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* T,
                      int64_t ldt, double* ws) {
   kc_hess_down<<<dim3(nt, m), CT, 0, st>>>(s->dev, t0, Wc, T, ldt, ws);
+  count_launch();
+}
+void chain_ihess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
+                      const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy,
+                      double* ws) {
+  kc_ihess_down<<<dim3(nt, m), CT, 0, st>>>(s->dev, t0, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+  count_launch();
+}
+void chain_ihess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* Y,
+                    int64_t ldy, double* ws) {
+  kc_ihess_up<<<dim3(nt, m), CT, 0, st>>>(s->dev, t0, Wc, Y, ldy, ws);
   count_launch();
 }
 }  // namespace chd_launch

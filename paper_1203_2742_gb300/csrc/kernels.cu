@@ -1025,6 +1025,11 @@ void chain_hess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m
                    const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws, const uint8_t* act);
 void chain_hess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* T,
                      int64_t ldt, double* ws);
+void chain_ihess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc,
+                      const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy,
+                      double* ws);
+void chain_ihess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* Y,
+                    int64_t ldy, double* ws);
 
 // warp-tier launches (warp_tier.cu): w32 for |J| <= 32, w64 for |J| <= 64
 namespace w32 {
@@ -1271,8 +1276,12 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
       k_ihess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
       count();
     }
-    if (v.nr32) w32::warp_ihess_down(s, st, v.tr, v.nr32, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
-    if (v.nr64) w64::warp_ihess_down(s, st, v.tr + v.nr32, v.nr64, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    if (s->chain_mode >= 2 && v.nr32 + v.nr64) {
+      chain_ihess_down(s, st, v.tr, v.nr32 + v.nr64, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    } else {
+      if (v.nr32) w32::warp_ihess_down(s, st, v.tr, v.nr32, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+      if (v.nr64) w64::warp_ihess_down(s, st, v.tr + v.nr32, v.nr64, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    }
     if (v.nwarp) w32::warp_ihess_down(s, st, v.t0, v.nwarp, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
     if (v.nw64) w64::warp_ihess_down(s, st, v.tw, v.nw64, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
     bf.join_now();
@@ -1283,8 +1292,12 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
     bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
       big_ihess_up(s, bs, xs, xc, m, big_front(s, v, i), Wc, Y, ldy, ws);
     });
-    if (v.nr32) w32::warp_ihess_up(s, st, v.tr, v.nr32, m, Wc, Y, ldy, ws);
-    if (v.nr64) w64::warp_ihess_up(s, st, v.tr + v.nr32, v.nr64, m, Wc, Y, ldy, ws);
+    if (s->chain_mode >= 2 && v.nr32 + v.nr64) {
+      chain_ihess_up(s, st, v.tr, v.nr32 + v.nr64, m, Wc, Y, ldy, ws);
+    } else {
+      if (v.nr32) w32::warp_ihess_up(s, st, v.tr, v.nr32, m, Wc, Y, ldy, ws);
+      if (v.nr64) w64::warp_ihess_up(s, st, v.tr + v.nr32, v.nr64, m, Wc, Y, ldy, ws);
+    }
     if (v.nwarp) w32::warp_ihess_up(s, st, v.t0, v.nwarp, m, Wc, Y, ldy, ws);
     if (v.nw64) w64::warp_ihess_up(s, st, v.tw, v.nw64, m, Wc, Y, ldy, ws);
     if (v.ncta) {

@@ -361,6 +361,27 @@ def test_chain_runs(name):
         assert err(res["on"]["w"][i], wantw[i]) < TOL
 
 
+@pytest.mark.skip(reason="chain_runs=2 (chain kernels for the inverse Hessian) has not run on a GPU yet")
+@pytest.mark.parametrize("name", list(CHAIN_CASES))
+def test_chain_runs_inverse_hessian(name):
+    """chain_runs=2: the inverse Hessian's passes in the chain tier, against
+    the oracle and against the warp-tier path."""
+    B = lib()
+    pattern = CHAIN_CASES[name]()
+    rng = np.random.default_rng(43)
+    on = B.Symbolic(*pattern, chain_runs=2)
+    off = B.Symbolic(*pattern)
+    n, cp, ri = on.n, on.colptr, on.rowind
+    x = W.diag_dominant(n, cp, ri, rng)
+    ts = W.uniform_sym(n, cp, ri, rng, count=3)
+    c = Case(pattern, seed=43)
+    yi = {k: c.host(sym.factor(c.dev(x)).inv_hessian(c.dev(ts))) for k, sym in (("on", on), ("off", off))}
+    want = OD.inv_hessian_dense(n, cp, ri, x, list(ts))
+    for i in range(3):
+        assert OD.rel_err(n, cp, ri, yi["on"][i], yi["off"][i]) < 1e-11
+        assert OD.rel_err(n, cp, ri, yi["on"][i], want[i]) < TOL
+
+
 def test_planted_condition_1e6():
     def planted(s, rng):
         x, _, _ = W.planted_factor(s.n, s.colptr, s.rowind, rng, dmin=1e-6, dmax=1.0)
