@@ -79,12 +79,12 @@ typedef struct {
   int32_t split_cols;      /* supernodes wider than 1.5 x split_cols columns are split into a
                               chain of supernodes of split_cols columns (V unchanged);
                               0 = default 256, negative = never split */
-  int32_t chain_runs;      /* 1: runs of at least 8 one-column fronts with contiguous rows
-                              and the same |A_k| <= 64 (band chains) get their own
-                              chain-tier kernels for factor, gradient, Hessian and Hessian
-                              factor (the other operations run them in the warp tier);
-                              2: as 1 and the inverse Hessian's passes too (experimental:
-                              not yet verified on a GPU); 0 (default): off */
+  int32_t chain_runs;      /* nonzero: runs of at least 8 one-column fronts with contiguous
+                              rows and the same |A_k| <= 64 (band chains) get their own
+                              chain-tier kernels for the factor, the gradient and the
+                              passes of the Hessian, the Hessian factor and the inverse
+                              Hessian (the Cholesky product runs them in the warp tier);
+                              0 (default): off */
   int32_t reserved[4];
 } chd_opts;
 

@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(CT) kc_hess_down(SymDev S, int task0, const do
   }
 }
 
-// Algorithm 5.2 step 1-2 for one-column fronts (top-down): with the window
+// Algorithm 5.2 steps 1-2 for one-column fronts (top-down): with the window
 // V' (the input T on A_j x A_j, gathered from the parent's T-front),
 // M_A = T_A + V' L_A, M_jj = T_jj + L_A^T (T_A + M_A), K_jj = D M_jj D,
 // K_A = V^{-1} (M_A D) (V^{-1} per front, formed by the inverse-Hessian

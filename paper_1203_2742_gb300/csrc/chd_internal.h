@@ -100,7 +100,6 @@ struct chd_symbolic {
   // per level: the first lvl_r32[l] + lvl_r64[l] tasks are chain-tier runs
   // (|J| <= 32, then |J| <= 64; all zero unless chain_runs)
   std::vector<int32_t> lvl_r32, lvl_r64;
-  int32_t chain_mode = 0;  // the analysis' chain_runs option (2: chain kernels for the inverse Hessian too)
   // per level l, five counts at 5*l: chain runs (|J| <= 32), chain runs
   // (|J| <= 64), warp, wide warp and dense-tier tasks (chd_symbolic_schedule)
   std::vector<int32_t> lvl_counts;

@@ -1276,12 +1276,7 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
       k_ihess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
       count();
     }
-    if (s->chain_mode >= 2 && v.nr32 + v.nr64) {
-      chain_ihess_down(s, st, v.tr, v.nr32 + v.nr64, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
-    } else {
-      if (v.nr32) w32::warp_ihess_down(s, st, v.tr, v.nr32, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
-      if (v.nr64) w64::warp_ihess_down(s, st, v.tr + v.nr32, v.nr64, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
-    }
+    if (v.nr32 + v.nr64) chain_ihess_down(s, st, v.tr, v.nr32 + v.nr64, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
     if (v.nwarp) w32::warp_ihess_down(s, st, v.t0, v.nwarp, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
     if (v.nw64) w64::warp_ihess_down(s, st, v.tw, v.nw64, m, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
     bf.join_now();
@@ -1292,12 +1287,7 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
     bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
       big_ihess_up(s, bs, xs, xc, m, big_front(s, v, i), Wc, Y, ldy, ws);
     });
-    if (s->chain_mode >= 2 && v.nr32 + v.nr64) {
-      chain_ihess_up(s, st, v.tr, v.nr32 + v.nr64, m, Wc, Y, ldy, ws);
-    } else {
-      if (v.nr32) w32::warp_ihess_up(s, st, v.tr, v.nr32, m, Wc, Y, ldy, ws);
-      if (v.nr64) w64::warp_ihess_up(s, st, v.tr + v.nr32, v.nr64, m, Wc, Y, ldy, ws);
-    }
+    if (v.nr32 + v.nr64) chain_ihess_up(s, st, v.tr, v.nr32 + v.nr64, m, Wc, Y, ldy, ws);
     if (v.nwarp) w32::warp_ihess_up(s, st, v.t0, v.nwarp, m, Wc, Y, ldy, ws);
     if (v.nw64) w64::warp_ihess_up(s, st, v.tw, v.nw64, m, Wc, Y, ldy, ws);
     if (v.ncta) {

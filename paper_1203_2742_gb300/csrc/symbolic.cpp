@@ -644,7 +644,6 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
     // run is one task of task tier 5 (|J| <= 32) or 6 (|J| <= 64).
     constexpr int64_t kMinRun = 8;
     vector<int64_t> run_of(nsn, -1);
-    s->chain_mode = opts.chain_runs > 0 ? opts.chain_runs : 0;
     if (opts.chain_runs > 0) {
       auto a_of = [&](int64_t t) { return (s->rows_ptr[t + 1] - s->rows_ptr[t]) - (s->sn_ptr[t + 1] - s->sn_ptr[t]); };
       auto nkids = [&](int64_t t) { return s->ch_ptr[t + 1] - s->ch_ptr[t]; };

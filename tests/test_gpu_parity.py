@@ -361,15 +361,14 @@ def test_chain_runs(name):
         assert err(res["on"]["w"][i], wantw[i]) < TOL
 
 
-@pytest.mark.skip(reason="chain_runs=2 (chain kernels for the inverse Hessian) has not run on a GPU yet")
 @pytest.mark.parametrize("name", list(CHAIN_CASES))
 def test_chain_runs_inverse_hessian(name):
-    """chain_runs=2: the inverse Hessian's passes in the chain tier, against
-    the oracle and against the warp-tier path."""
+    """The inverse Hessian's passes in the chain tier, against the oracle's
+    dense solve and against the path without chain runs."""
     B = lib()
     pattern = CHAIN_CASES[name]()
     rng = np.random.default_rng(43)
-    on = B.Symbolic(*pattern, chain_runs=2)
+    on = B.Symbolic(*pattern, chain_runs=True)
     off = B.Symbolic(*pattern)
     n, cp, ri = on.n, on.colptr, on.rowind
     x = W.diag_dominant(n, cp, ri, rng)
