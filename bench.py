@@ -41,6 +41,16 @@ METRIC = "Hessian evals/s"
 UNIT = "evals/s"
 # FP64 roofline of the front arithmetic: 152 SMs x 2.07 GHz x 2 FMA per clock per SM
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+# measured HBM copy bandwidth of the GB300s (generated file), else
+# the fallback figure of an earlier measurement
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
 # DRAM bytes (read + write) of one Hessian call, from one ncu capture of the
 # current kernels; None where there is none.  (The er5000 capture in
 # profiles/dram_traffic_hessian_er5000.md, 6.39 GB, predates the activity-mask
@@ -299,6 +309,13 @@ def analysed_pattern_host(wl):
 # exchange step); the job's time is the slowest rank's
 # ---------------------------------------------------------------------------
 
+def hbm_line(bytes_per_call, ms):
+    peak, src = hbm_peak_gbs()
+    gbs = bytes_per_call / (ms * 1e-3) / 1e9
+    return {"algorithmic_bytes_per_call": bytes_per_call, "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": gbs / peak, "peak_source": src}
+
+
 def replica_max_ms(dev_ms, device):
     """Max over the ranks of the timed region's device milliseconds."""
     import torch
@@ -520,6 +537,12 @@ def run_ours(args, wl, rank, world, local_rank):
             "gpu_launches": int(launches),
             "clocks": clocks,
             "ops_ms": {k: round(v, 4) for k, v in ops_ms.items()},
+            # every operation in evals/s (Hessian-type calls: m evaluations per call)
+            "ops_evals_per_s": {k: (count * m if k in ("hessian", "inv_hessian") else count) / (v * 1e-3)
+                                for k, v in ops_ms.items()},
+            # the memory side of the roofline: algorithmic bytes of one Hessian call (Y read and
+            # T written, m matrices on V, plus one read of the factor's L and S) over its time
+            "hbm": hbm_line(8.0 * (2 * m * nnz + 2 * nnz), ops_ms["hessian"]),
             "instances": count,
             "autotune": tune,
             "batched_vs_one_at_a_time": sequential,
