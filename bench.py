@@ -246,6 +246,38 @@ def run_reference(args, wl):
                 "e2e": {"value": cpu["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
+    if wl["name"] == "serve":
+        # the serving trace's Hessian requests, timed on the oracle: the same
+        # pool, rate, mix and seed as the GPU arm (request values are not
+        # drawn here, so the request list is a draw of the same process, not
+        # the identical list)
+        from paper_1203_2742_gb300 import build
+        build.build()
+        from paper_1203_2742_gb300 import binding as B
+        from paper_1203_2742_gb300 import serve
+        pool = []
+        for (pat, perm) in wl["pool"]:
+            sym = B.Symbolic(*pat, perm=perm) if perm is not None else B.Symbolic(*pat)
+            x, _, s_ = workload_values(dict(wl, m=1), sym.n, sym.colptr, sym.rowind)
+            pool.append((sym, x, s_))
+        trace = serve.poisson_trace(len(pool), wl["rate"], args.serve_seconds, wl["mix"],
+                                    np.random.default_rng(wl["seed"]), lambda i: 0, max_m=wl["m"])
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        times, cpu = [], None
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            cpu = serve_cpu_baseline(pool, trace, cores, budget_s=5.0)
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        line = {"metric": METRIC, "value": cpu["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": wl["desc"], "trace_seconds": args.serve_seconds, "requests": len(trace),
+                           "patterns": len(pool), "parallelism": "host cores"},
+                "cpu_baseline": cpu,
+                "e2e": {"value": cpu["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     n, cp, ri = analysed_pattern_host(wl)
     x, ys, _ = workload_values(wl, n, cp, ri)
     m = wl["m"]
