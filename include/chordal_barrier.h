@@ -400,9 +400,10 @@ chd_status chd_factor_set_graphs(chd_factor* fac, int on);
  *           chd_gradient or chd_hessian on it once before); it is read only
  *   m, y_dev, ldy, t_dev, ldt   as for chd_hessian (device pointers, caller-owned)
  *   stream  cudaStream_t as void*
- * Returns CHD_ERR_INVALID when the projected inverse is not cached, or when
+ * Returns CHD_ERR_INVALID when the projected inverse is not cached, when
  * m times the pattern's per-right-hand-side workspace exceeds the 2 Mi
- * doubles (small and medium patterns fit; use chd_hessian otherwise);
+ * doubles (small and medium patterns fit; use chd_hessian otherwise), or
+ * when m > 65535 (chd_hessian splits larger batches itself);
  * CHD_ERR_CUDA if a CUDA call fails.  It calls no cudaMalloc, cudaFree or
  * other allocating routine.
  * Set-up: the first call on each device looks up the array's device

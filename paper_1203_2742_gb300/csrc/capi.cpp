@@ -177,11 +177,15 @@ chd_status ensure_act(chd_factor* f, int64_t rhs) {
   return CHD_OK;
 }
 
+// Right-hand sides processed per launch sequence: bounded by the workspace
+// cap and by the grid dimension that indexes them (blockIdx.y or .z, at
+// most 65535).
+constexpr int64_t kMaxRhsPerLaunch = 65535;
 int64_t rhs_chunk(const chd_factor* f, int m) {
   const size_t per = std::max<size_t>((size_t)f->sym->dev.f_total * 8, 1);
   const size_t cap = f->ws_limit ? std::min(f->ws_limit, kWorkspaceCap) : kWorkspaceCap;
   int64_t c = (int64_t)(cap / per);
-  return std::max<int64_t>(1, std::min<int64_t>(c, m));
+  return std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(c, m), kMaxRhsPerLaunch));
 }
 
 chd_status launch_status() { return cuda_ok(cudaGetLastError()); }

@@ -72,6 +72,7 @@ extern "C" chd_status chd_hessian_noalloc(chd_factor* f, int m, const double* y,
   // Reject what does not fit the fixed workspace.
   const int64_t per_rhs = f->sym->dev.f_total;
   if (per_rhs <= 0 || per_rhs > kNoAllocWorkspaceDoubles / m) return CHD_ERR_INVALID;
+  if (m > 65535) return CHD_ERR_INVALID;  // one launch sequence indexes the RHS in a grid dimension
   double* ws = nullptr;
   const chd_status rc = workspace_address(&ws);
   if (rc != CHD_OK) return rc;
