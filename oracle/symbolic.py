@@ -226,3 +226,29 @@ def clique_tree_alg61(I, parent, tie="last"):
     for k in N:
         par.setdefault(k, -1)
     return N, A, par, snode_of
+
+
+def supernodal_pattern(n, I, snode_ptr):
+    """Pattern of a partition of the columns into contiguous supernodes
+    (§6.2, §7): every column j of supernode [f, l) holds the rows
+    {j, .., l-1} together with the ancestor set A = I_{l-1} of the
+    supernode's last column.  With the fundamental partition of a filled
+    pattern this is the pattern itself; with a relaxed partition (chains of
+    the elimination tree merged into one supernode) it adds the explicit
+    zeros that make the merged columns share one structure.
+
+    I: filled strictly-lower rows per column (``fill``); snode_ptr: first
+    column of each supernode and n at the end.  Returns (colptr, rowind) of
+    the lower CSC, diagonal included, rows increasing.
+    """
+    colptr = [0]
+    rows = []
+    for k in range(len(snode_ptr) - 1):
+        f, l = int(snode_ptr[k]), int(snode_ptr[k + 1])
+        A = np.asarray(I[l - 1], dtype=np.int64)
+        for j in range(f, l):
+            col = np.concatenate([np.arange(j, l, dtype=np.int64), A])
+            rows.append(col)
+            colptr.append(colptr[-1] + len(col))
+    rowind = np.concatenate(rows).astype(np.int32) if rows else np.zeros(0, np.int32)
+    return np.asarray(colptr, dtype=np.int64), rowind

@@ -175,6 +175,33 @@ def test_hessian_self_adjoint_positive(name):
     assert OD.sym_dot(n, cp, ri, y1, t1) > 0
 
 
+@pytest.mark.parametrize("name", list(PATTERNS))
+def test_hessian_entries(name):
+    """Entries of X^{-1} Y X^{-1} one by one: X diagonal gives
+    Y_ij / (x_i x_j) (closed form), a central difference of the gradient
+    -P(X^{-1}) along Y gives H(Y) at the same positions, and the entries
+    agree with the whole projected product."""
+    p = PATTERNS[name]()
+    n, cp, ri = p
+    r, c = OD.pattern_pairs(n, cp, ri)
+    rng = np.random.default_rng(21)
+    y = W.uniform_sym(n, cp, ri, rng)[0]
+    sel = rng.choice(len(r), size=min(40, len(r)), replace=False)
+    dx = rng.uniform(0.5, 2.0, size=n)
+    xd = np.where(r == c, dx[r], 0.0)
+    Zd = OD.inverse(n, cp, ri, xd)
+    got = OD.hessian_entries(n, cp, ri, Zd, y, r[sel], c[sel])
+    np.testing.assert_allclose(got, y[sel] / (dx[r[sel]] * dx[c[sel]]), rtol=1e-13)
+    x = spd_values(p, 22)
+    Z = OD.inverse(n, cp, ri, x)
+    got = OD.hessian_entries(n, cp, ri, Z, y, r[sel], c[sel])
+    h = 1e-5
+    fd = (OD.gradient(n, cp, ri, x + h * y) - OD.gradient(n, cp, ri, x - h * y)) / (2 * h)
+    scale = np.abs(fd).max()
+    assert np.abs(got - fd[sel]).max() < 1e-7 * scale
+    np.testing.assert_allclose(got, OD.hessian(n, cp, ri, x, [y], Z=Z)[0][sel], rtol=1e-11, atol=1e-14 * scale)
+
+
 def test_hessian_matrix_consistent():
     p = PATTERNS["grid"]()
     n, cp, ri = p
@@ -247,6 +274,40 @@ def test_completion_newton_vs_cliquesum(name):
         d = W.uniform_sym(n, cp, ri, rng)[0]
         xp = xc + 1e-3 * d
         assert -OD.sym_dot(n, cp, ri, s, xp) + OD.logdet(n, cp, ri, xp) <= val + 1e-12
+
+
+@pytest.mark.parametrize("name", list(PATTERNS))
+def test_completion_refined(name):
+    """Newton steps from the closed form reach the maximiser of
+    Eq. (e-dual-barrier-def) that Newton from diag(1/S_ii) reaches, and
+    satisfy P(X^{-1}) = S (Eq. (e-Xhat-eq)) to rounding."""
+    p = PATTERNS[name]()
+    n, cp, ri = p
+    s = gram_values(p, 15, c=0.01)
+    I, parent = OS.fill(n, OS.columns_from_csc(n, cp, ri))
+    cl, seps = OS.cliques_and_separators(I, parent)
+    xr = OD.completion_refined(n, cp, ri, s, cl, seps)
+    xn = OD.completion_newton(n, cp, ri, s)
+    assert OD.rel_err(n, cp, ri, xr, xn) < 1e-11
+    Z = np.linalg.inv(OD.to_dense(n, cp, ri, xr))
+    assert OD.rel_err(n, cp, ri, OD.project(n, cp, ri, Z), s) < 1e-13
+
+
+def test_completion_refined_removes_closed_form_residual():
+    """On a larger, ill-conditioned S (an Erdos-Renyi pattern under minimum
+    fill, S = P(G G^T + 0.01 I), cond(X-hat) about 1e5) the closed form's
+    residual ||P(X^{-1}) - S|| / ||S|| (about 3e-8) is brought to the
+    rounding floor of P(X^{-1}) by the Newton steps."""
+    rng = np.random.default_rng(16)
+    p = filled(W.erdos_renyi(400, 0.01, rng))
+    n, cp, ri = p
+    s = W.projected_gram(n, cp, ri, rng.standard_normal((n, 30)), 1e-2)
+    I, parent = OS.fill(n, OS.columns_from_csc(n, cp, ri))
+    cl, seps = OS.cliques_and_separators(I, parent)
+    res = lambda xv: OD.rel_err(n, cp, ri, OD.project(n, cp, ri, np.linalg.inv(OD.to_dense(n, cp, ri, xv))), s)
+    r0 = res(OD.completion_cliquesum(n, cp, ri, s, cl, seps))
+    r1 = res(OD.completion_refined(n, cp, ri, s, cl, seps))
+    assert r1 < 1e-3 * r0 and r1 < 1e-11
 
 
 def test_completion_tridiagonal_by_hand():
