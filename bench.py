@@ -39,6 +39,9 @@ import workloads as W  # noqa: E402
 
 METRIC = "Hessian evals/s"
 UNIT = "evals/s"
+# parity bound of every reported GPU number: relative Frobenius error in the
+# symmetric norm against the FP64 oracle (log det and f_*: |error| / max(1, |value|))
+TOL_PARITY = 1e-10
 # FP64 roofline of the front arithmetic: 152 SMs x 2.07 GHz x 2 FMA per clock per SM
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # measured HBM copy bandwidth of the GB300s (generated file), else
@@ -51,11 +54,10 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
-# DRAM bytes (read + write) of one Hessian call, from one ncu capture of the
-# current kernels; None where there is none.  (The er5000 capture in
-# profiles/dram_traffic_hessian_er5000.md, 6.39 GB, predates the activity-mask
-# checks added to the bottom-up kernels, so it is not reported as current.)
-TRAFFIC_PER_HESSIAN_CALL = {}
+# DRAM bytes (read + write) of one Hessian call, summed over the call's
+# launches in one ncu capture of the current kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum); absent where there is none.
+TRAFFIC_PER_HESSIAN_CALL = {"er5000": 6.377e9}
 
 
 def make_workload(name):
@@ -170,26 +172,29 @@ class ClockSampler:
 # reference arm: the CPU oracle on the host cores
 # ---------------------------------------------------------------------------
 
-def oracle_hessian_sample(wl, n, cp, ri, x, ys, count):
+def oracle_hessian_sample(wl, n, cp, ri, x, ys, count, keep=None):
     """Dense oracle: Z = X^{-1} once, then T = P(Z Y Z) for `count` of the Y's.
-    Returns (t_inverse, t_per_eval)."""
+    Returns (t_inverse, t_per_eval); with a dict `keep`, also stores Z and
+    the T's in it (for the accuracy record)."""
     from oracle import dense as OD
     t0 = time.perf_counter()
     Z = OD.inverse(n, cp, ri, x)
     t1 = time.perf_counter()
-    OD.hessian(n, cp, ri, x, list(ys[:count]), Z=Z)
+    T = OD.hessian(n, cp, ri, x, list(ys[:count]), Z=Z)
     t2 = time.perf_counter()
+    if keep is not None:
+        keep["Z"], keep["T"] = Z, T
     return t1 - t0, (t2 - t1) / count
 
 
-def oracle_hessian_repeated(wl, n, cp, ri, x, ys, count, budget_s=10.0):
+def oracle_hessian_repeated(wl, n, cp, ri, x, ys, count, budget_s=10.0, keep=None):
     """``oracle_hessian_sample`` repeated until `budget_s` seconds of CPU work
     are spent (at least once); medians of (t_inverse, t_per_eval) and the
     number of repetitions.  A small pattern takes milliseconds per sample,
     where one timing is mostly noise."""
     tz, te, spent = [], [], 0.0
     while spent < budget_s or not tz:
-        a, b = oracle_hessian_sample(wl, n, cp, ri, x, ys, count)
+        a, b = oracle_hessian_sample(wl, n, cp, ri, x, ys, count, keep=keep)
         tz.append(a)
         te.append(b)
         spent += a + count * b
@@ -221,17 +226,60 @@ def batch_cpu_baseline(sym, x, ys, m, cores, budget_s=15.0):
                       f"{sym.count} instances ({spent:.1f} s); extrapolated to all instances by n^3"}
 
 
+def oracle_pattern(pattern, perm=None, snode_ptr=None):
+    """The analysed pattern V computed by the oracle alone (no library): the
+    pattern permuted by perm (perm[new] = old), filled by the oracle's
+    elimination fill, and -- for a stored relaxed partition -- its
+    supernodal pattern.  For the Erdos-Renyi workload the stored analysis
+    reproduces the library's V exactly (host test); for the others this is
+    the same filled graph in the oracle's own numbering (the library also
+    postorders it), which draws the same value recipe on the same shape."""
+    from oracle import symbolic as OS
+    n = int(pattern[0])
+    p = W.permute(pattern, perm) if perm is not None else pattern
+    I, _ = OS.fill(n, OS.columns_from_csc(*p))
+    sp = np.arange(n + 1) if snode_ptr is None else snode_ptr
+    cp, ri = OS.supernodal_pattern(n, I, sp)
+    return n, cp, ri
+
+
+def reference_pattern(wl):
+    if wl["name"] == "er5000":
+        from workloads import analysed
+        pattern, perm, sp = analysed.load_er5000()
+        return oracle_pattern(pattern, perm, sp)
+    return oracle_pattern(wl["pattern"], wl["opts"].get("perm"))
+
+
+class OracleBatch:
+    """Block-diagonal union of independently analysed instances, in the
+    oracle's numbering (the reference arm's stand-in for the library's
+    batched symbolic object: the same attributes the CPU baseline reads)."""
+
+    def __init__(self, instances):
+        self.parts = [oracle_pattern(p, q) for p, q, _ in instances]
+        self.count = len(self.parts)
+        ns = [p[0] for p in self.parts]
+        zs = [len(p[2]) for p in self.parts]
+        self.n_off = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+        self.nnz_off = np.concatenate([[0], np.cumsum(zs)]).astype(np.int64)
+        self.n = int(self.n_off[-1])
+        self.colptr = np.concatenate([[0]] + [p[1][1:] + self.nnz_off[i] for i, p in enumerate(self.parts)])
+        self.rowind = np.concatenate([p[2] + self.n_off[i] for i, p in enumerate(self.parts)]).astype(np.int32)
+        self.nnz = int(self.nnz_off[-1])
+
+    def instance_pattern(self, i):
+        return self.parts[i], None
+
+
 def run_reference(args, wl):
-    from paper_1203_2742_gb300 import build as _b  # noqa: F401  (no GPU use)
-    # analyse with the library's host symbolic phase only when it is built;
-    # else use the oracle's own fill of the same ordering (natural/user orders)
+    """The CPU oracle on the host cores, on the same workload; loads no part
+    of the library (the analysed pattern comes from the oracle, see
+    ``oracle_pattern``)."""
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     if "batch" in wl:
-        from paper_1203_2742_gb300 import build
-        build.build()
-        from paper_1203_2742_gb300 import binding as B
-        sym = make_symbolic(B, wl)
+        sym = OracleBatch(wl["batch"])
         x, ys, _ = workload_values(wl, sym.n, sym.colptr, sym.rowind)
-        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         times, cpu = [], None
         for i in range(args.warmup + args.steps):
             t0 = time.perf_counter()
@@ -251,18 +299,16 @@ def run_reference(args, wl):
         # pool, rate, mix and seed as the GPU arm (request values are not
         # drawn here, so the request list is a draw of the same process, not
         # the identical list)
-        from paper_1203_2742_gb300 import build
-        build.build()
-        from paper_1203_2742_gb300 import binding as B
-        from paper_1203_2742_gb300 import serve
+        from types import SimpleNamespace
+        from paper_1203_2742_gb300 import serve  # host logic only (no library)
         pool = []
         for (pat, perm) in wl["pool"]:
-            sym = B.Symbolic(*pat, perm=perm) if perm is not None else B.Symbolic(*pat)
-            x, _, s_ = workload_values(dict(wl, m=1), sym.n, sym.colptr, sym.rowind)
+            n, cp, ri = oracle_pattern(pat, perm)
+            sym = SimpleNamespace(n=n, colptr=cp, rowind=ri, nnz=len(ri))
+            x, _, s_ = workload_values(dict(wl, m=1), n, cp, ri)
             pool.append((sym, x, s_))
         trace = serve.poisson_trace(len(pool), wl["rate"], args.serve_seconds, wl["mix"],
                                     np.random.default_rng(wl["seed"]), lambda i: 0, max_m=wl["m"])
-        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         times, cpu = [], None
         for i in range(args.warmup + args.steps):
             t0 = time.perf_counter()
@@ -278,10 +324,9 @@ def run_reference(args, wl):
                 "e2e": {"value": cpu["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
-    n, cp, ri = analysed_pattern_host(wl)
+    n, cp, ri = reference_pattern(wl)
     x, ys, _ = workload_values(wl, n, cp, ri)
     m = wl["m"]
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     sample_evals = min(2, m)
     times = []
     for i in range(args.warmup + args.steps):
@@ -298,7 +343,8 @@ def run_reference(args, wl):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": wl["desc"], "global_batch": m, "parallelism": "host cores"},
+        "config": {"workload": wl["desc"], "n": n, "nnz_filled": int(len(ri)), "rhs_per_step": m,
+                   "global_batch": m, "parallelism": "host cores", "l2": "host run"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"dense oracle: X^-1 then P(X^-1 Y X^-1) for {sample_evals} of the "
                                    f"{m} Y per step; value = {m}/(t_inverse + {m}*t_eval)"},
@@ -325,15 +371,6 @@ def tuned_config(B, wl):
         subset = list(range(0, len(wl["batch"]), 8))
         return autotune.tune(lambda **c: make_symbolic(B, wl, subset=subset, **c), wl["m"], reps=1)
     return autotune.tune(lambda **c: make_symbolic(B, wl, **c), wl["m"], reps=2)
-
-
-def analysed_pattern_host(wl):
-    """The analysed (filled, permuted) pattern from the library's host phase."""
-    from paper_1203_2742_gb300 import build
-    build.build()
-    from paper_1203_2742_gb300 import binding as B
-    sym = make_symbolic(B, wl)
-    return sym.n, sym.colptr, sym.rowind
 
 
 # ---------------------------------------------------------------------------
@@ -363,6 +400,41 @@ def replica_max_ms(dev_ms, device):
 def job_value(world, evals_per_step, steps, max_ms):
     """Whole-job throughput: every replica's evaluations over the slowest time."""
     return world * evals_per_step * steps / (max_ms * 1e-3)
+
+
+def accuracy_record(n, cp, ri, keep, ys, s, g, t, yi, logdet, fstar, xhat, x):
+    """Errors of the GPU outputs of the last end-to-end step against the FP64
+    oracle, on the CPU-baseline sample: the Hessian of the sampled Y's and
+    the gradient against the dense X^{-1} of the timed sample, log det
+    against the dense Cholesky factor, the inverse Hessian of the sampled
+    T = H(Y) against the oracle's clique-sum H^{-1} and, for every Y, the
+    round trip H^{-1}(H(Y)) = Y, and the completion by the residual of its
+    defining equation P(X-hat^{-1}) = S (Eq. (e-Xhat-eq)) with f_* =
+    log det X-hat - n.  Relative Frobenius errors in the symmetric norm."""
+    from oracle import dense as OD
+    from oracle import symbolic as OS
+    err = lambda a, b: float(OD.rel_err(n, cp, ri, a, b))
+    Z, T = keep["Z"], keep["T"]
+    k = len(T)
+    I = [np.asarray(ri[cp[j] + 1:cp[j + 1]], dtype=np.int64) for j in range(n)]
+    cl, seps = OS.cliques_and_separators(I, OS.etree(I))
+    want_ld = OD.logdet(n, cp, ri, x)
+    Xh = OD.to_dense(n, cp, ri, xhat)
+    ld_xh = float(2.0 * np.sum(np.log(np.diag(np.linalg.cholesky(Xh)))))
+    rec = {
+        "tolerance": TOL_PARITY,
+        "logdet": abs(logdet - want_ld) / max(1.0, abs(want_ld)),
+        "gradient": err(g, -OD.project(n, cp, ri, Z)),
+        "hessian": max(err(t[i], T[i]) for i in range(k)),
+        "inv_hessian": max(err(yi[i], OD.inv_hessian_cliquesum(n, cp, ri, x, t[i], cl, seps, S=Z))
+                           for i in range(k)),
+        "inv_hessian_roundtrip": max(err(yi[i], ys[i]) for i in range(len(ys))),
+        "completion_residual": err(OD.project(n, cp, ri, np.linalg.inv(Xh)), s),
+        "fstar": abs(fstar - (ld_xh - n)) / max(1.0, abs(fstar)),
+        "sample": f"Hessian and inverse Hessian of {k} of the {len(ys)} right-hand sides; round trip of all",
+    }
+    rec["pass"] = all(v <= TOL_PARITY for key, v in rec.items() if key not in ("tolerance", "sample"))
+    return rec
 
 
 # ---------------------------------------------------------------------------
@@ -397,7 +469,10 @@ def run_ours(args, wl, rank, world, local_rank):
     n, cp, ri, nnz = sym.n, sym.colptr, sym.rowind, sym.nnz
     m = wl["m"]
     x, ys, s = workload_values(wl, n, cp, ri)
-    fl = sym.flops()
+    # the method's flops are counted on the relaxed Algorithm 6.1 partition;
+    # splitting wide supernodes (a scheduling choice) executes more
+    fl_exec = sym.flops()
+    fl = make_symbolic(B, wl, **dict(cfg, split_cols=-1)).flops()
 
     # inputs resident in HBM
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
@@ -472,6 +547,7 @@ def run_ours(args, wl, rank, world, local_rank):
     fp64_peak = B.chd_probe_fp64_peak() / 1e3  # TFLOP/s
     hess_flops = fl["hessian"] * m
     achieved = hess_flops / (ops_ms["hessian"] * 1e-3) / 1e12
+    executed = fl_exec["hessian"] * m
     step_flops = fl["factor"] + fl["gradient"] + m * (fl["hessian"] + fl["inv_hessian"]) + fl["completion"]
 
     # ---- batched vs one instance at a time (the plain GPU path) ----
@@ -535,35 +611,46 @@ def run_ours(args, wl, rank, world, local_rank):
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         if count > 1:
             cpu = batch_cpu_baseline(sym, x, ys, m, cores)
         else:
             sample = min(2, m)
-            tz, te, reps = oracle_hessian_repeated(wl, n, cp, ri, x, ys, sample)
+            keep = {}
+            tz, te, reps = oracle_hessian_repeated(wl, n, cp, ri, x, ys, sample, keep=keep)
             cpu = {"value": m / (tz + m * te), "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"dense oracle X^-1 ({tz:.3g} s) then P(X^-1 Y X^-1) for {sample} of the {m} Y "
                              f"({te:.3g} s each), medians of {reps} repetitions (>= 10 s of CPU work or one); "
                              f"value = {m}/(t_inverse + {m}*t_eval)"}
+            xhat = fx.product().cpu().numpy()
+            accuracy = accuracy_record(n, cp, ri, keep, ys, s, hG.numpy(), hT.numpy(), hYI.numpy(),
+                                       results["logdet"], results["fstar"], xhat, x)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["desc"], "n": n, "nnz_filled": nnz, "supernodes": sym.nsuper,
+            "config": {"workload": wl["desc"], "n": n, "nnz_filled": nnz,
                        "rhs_per_step": m, "global_batch": world * evals_per_step,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MB write)"},
+            "supernodes": sym.nsuper,
             "roofline": {"bound": "alu",
                          "kernel": "one Hessian call (all its launches; the dense-tier FP64 products carry the flops)",
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_HESSIAN_CALL.get(wl["name"]),
+                         "flops_per_call": hess_flops,
+                         "flops_source": "sum over the fronts of the relaxed Algorithm 6.1 partition (unsplit) of "
+                                         "6a^2n + 8an^2 + 2n^3 per right-hand side, times m",
+                         "executed_flops_per_call": executed,
                          "peak_source": "FP64 FMA rate from unit counts and clock: 152 SMs x 2070 MHz x 4 flop/clk",
                          "peak_probe": fp64_peak, "frac_of_probe": achieved / fp64_peak,
                          "probe_source": "FP64 DFMA loop on all SMs (chd_probe_fp64_peak), same run"},
             "cpu_baseline": cpu,
+            "accuracy": accuracy,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),

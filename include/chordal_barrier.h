@@ -338,6 +338,14 @@ chd_status chd_error_detail(chd_factor* fac, int64_t* supernode, int64_t* column
    (host counter, for launch accounting). */
 int64_t chd_kernel_launches(void);
 
+/* Measurement utility (not an operation of the paper): number of dense-tier
+   products the library has split along their inner dimension since the
+   process started (each split product adds one reduction launch that sums
+   the partial products in a fixed order).  Host counter of directly issued
+   launches; replays of captured CUDA graphs do not add to it.  Tests use it
+   to check that a workload reaches the split path. */
+int64_t chd_split_k_launches(void);
+
 /*
  * Measurement utility (not an operation of the paper): FP64 fused
  * multiply-add throughput of the current device in GFLOP/s, from a kernel

@@ -70,6 +70,8 @@ _lib.chd_status_get.argtypes = [_p]
 _lib.chd_error_detail.argtypes = [_p, C.POINTER(_i64), C.POINTER(_i64)]
 _lib.chd_kernel_launches.argtypes = []
 _lib.chd_kernel_launches.restype = _i64
+_lib.chd_split_k_launches.argtypes = []
+_lib.chd_split_k_launches.restype = _i64
 _lib.chd_hessian_noalloc.argtypes = [_p, C.c_int, _p, _i64, _p, _i64, _p]
 _lib.chd_hessian_noalloc.restype = C.c_int
 _lib.chd_probe_fp64_peak.argtypes = [_p, C.POINTER(C.c_double)]
@@ -376,6 +378,10 @@ def chd_error_detail(fac):
 
 def chd_kernel_launches():
     return int(_lib.chd_kernel_launches())
+
+
+def chd_split_k_launches():
+    return int(_lib.chd_split_k_launches())
 
 
 def chd_probe_fp64_peak(stream=None):

@@ -17,6 +17,7 @@
 
 namespace chd_launch {
 void count_launch();
+void count_split_k();
 }
 
 namespace chd {
@@ -172,6 +173,7 @@ void gemm_cfg(const Ctx& st, int batch, int M, int N, int K, double alpha, MA A,
     mk_gemm_reduce<BM, BN><<<dim3(tiles, 1, batch), BT, 0, st>>>(M, N, alpha, beta, C, sC, lower ? 1 : 0, tn,
                                                                   tiles, nsplit, st.xs);
     chd_launch::count_launch();
+    chd_launch::count_split_k();
   }
 }
 

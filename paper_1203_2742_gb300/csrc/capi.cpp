@@ -13,6 +13,7 @@
 
 namespace chd_launch {
 int64_t launches();
+int64_t split_k_launches();
 void add_launches(int64_t d);
 void factor(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* X, double* Lc,
             double* Wc, double* Dd, double* ws, double* ldet, int64_t* status);
@@ -790,6 +791,7 @@ chd_status chd_error_detail(chd_factor* f, int64_t* supernode, int64_t* column) 
 }
 
 int64_t chd_kernel_launches(void) { return chd_launch::launches(); }
+int64_t chd_split_k_launches(void) { return chd_launch::split_k_launches(); }
 
 chd_status chd_factor_set_workspace_limit(chd_factor* f, size_t bytes) {
   if (!f) return CHD_ERR_INVALID;

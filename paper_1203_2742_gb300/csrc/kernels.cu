@@ -989,8 +989,11 @@ namespace chd_launch {
 using namespace chd;
 
 static int64_t g_launches = 0;
+static int64_t g_split_k = 0;
 int64_t launches() { return g_launches; }
 void count_launch() { ++g_launches; }
+int64_t split_k_launches() { return g_split_k; }
+void count_split_k() { ++g_split_k; }
 void add_launches(int64_t d) { g_launches += d; }
 
 static inline void count() { ++g_launches; }

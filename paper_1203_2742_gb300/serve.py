@@ -15,8 +15,9 @@ call with m = the sum of their right-hand sides (continuous batching).
 Calls on one pattern are serialised by a per-pattern lock (a factor object
 has one workspace); different patterns run concurrently.
 
-The server computes through the C ABI only (``binding``); it holds no
-numerical code of its own.
+The server computes through the C ABI only (the ``binding`` objects of the
+registered patterns); it holds no numerical code of its own.  The trace
+generator and the admission rule need no library (they are host logic).
 """
 from __future__ import annotations
 
@@ -26,8 +27,6 @@ import time
 from dataclasses import dataclass, field
 
 import numpy as np
-
-from . import binding as B
 
 OPS = ("factor", "gradient", "hessian", "inv_hessian", "completion")
 

@@ -46,3 +46,31 @@ def test_oracle_sample_repeats_to_its_budget():
     tz, te, reps = bench.oracle_hessian_repeated(w, n, cp, ri, x, ys, 1, budget_s=0.2)
     assert reps >= 1 and tz > 0 and te > 0
     assert time.perf_counter() - t0 >= 0.2 or reps == 1
+
+
+def test_reference_arm_loads_no_library():
+    """The CPU oracle's arm runs without the library: the analysed pattern
+    comes from the oracle (for the Erdos-Renyi workload from the stored
+    analysis, equal to the library's, see test_symbolic_host)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys, runpy; sys.argv = ['bench.py', '--impl', 'reference', '--workload', 'band200', "
+            "'--steps', '1', '--warmup', '3']\n"
+            "runpy.run_path('bench.py', run_name='__main__')\n"
+            "maps = open('/proc/self/maps').read()\n"
+            "print('LOADED', 'libchordal_barrier' in maps, any('binding' in m for m in sys.modules))\n")
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr
+    lines = out.stdout.strip().splitlines()
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["config"]["n"] == 200
+    assert lines[-1] == "LOADED False False"
+
+
+def test_reference_pattern_of_stored_analysis():
+    """The reference arm's Erdos-Renyi pattern has the workload's size."""
+    n, cp, ri = bench.reference_pattern(bench.make_workload("er5000"))
+    assert n == 5000 and len(cp) == n + 1 and cp[-1] == len(ri) == 1114524

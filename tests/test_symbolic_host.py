@@ -254,3 +254,81 @@ def test_schedule_invariants(name, chain):
         assert nrun >= 1  # the band chains are found (a <= 64)
     if name == "band500_w70":
         assert nrun == 0  # a = 70 > 64: no chain tier
+
+
+def _pairs_of(colptr, rowind):
+    cols = np.repeat(np.arange(len(colptr) - 1), np.diff(colptr))
+    return set(zip(np.asarray(rowind).astype(int).tolist(), cols.tolist()))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_supernodal_pattern_of_fundamental_partition(name):
+    """The oracle's supernodal pattern of Algorithm 6.1's partition of a
+    filled pattern is that pattern (§6.2: the columns of a supernode share
+    the ancestor set of its last column)."""
+    mk, ordering, permf = CASES[name]
+    pattern = mk()
+    n = pattern[0]
+    perm = permf() if permf else np.arange(n)
+    p2 = W.permute(pattern, perm)
+    I, parent = OS.fill(n, OS.columns_from_csc(*p2))
+    N, A, par, _ = OS.clique_tree_alg61(I, parent, tie="last")
+    # Algorithm 6.1's supernodes are contiguous only after a postorder; take
+    # the chain-contiguous ones of this order (columns k, k+1, .. each the
+    # only chain child of the next) by splitting at every break
+    sp = [0]
+    for j in range(1, n):
+        same = any(j in set(Nk) and (j - 1) in set(Nk) for Nk in N.values())
+        if not same:
+            sp.append(j)
+    sp.append(n)
+    cp, ri = OS.supernodal_pattern(n, I, sp)
+    want = {(int(r), k) for k in range(n) for r in I[k]} | {(k, k) for k in range(n)}
+    assert _pairs_of(cp, ri) == want
+
+
+def test_supernodal_pattern_of_merged_partition():
+    """Merging a chain of the elimination tree into one supernode: every
+    merged column gets the rows below it inside the supernode and the
+    ancestor set of the last column; the result contains V and is filled
+    (Eq. (e-filled)); the added entries are exactly the explicit zeros."""
+    # arrow with a band: columns 0..5 form chains with different structures
+    n, cp0, ri0 = W.band(12, 2)
+    I, parent = OS.fill(n, OS.columns_from_csc(n, cp0, ri0))
+    sp = [0, 4, 8, 12]  # supernodes {0..3}, {4..7}, {8..11}
+    cp, ri = OS.supernodal_pattern(n, I, sp)
+    got = _pairs_of(cp, ri)
+    # by hand: column j of [f, l) holds rows j..l-1 and I_{l-1} = {l, l+1} (l < 12)
+    want = set()
+    for f, l in ((0, 4), (4, 8), (8, 12)):
+        for j in range(f, l):
+            want |= {(r, j) for r in range(j, l)} | {(r, j) for r in (l, l + 1) if r < n}
+    assert got == want
+    assert _pairs_of(cp0, ri0) <= got
+    cols = [np.asarray(ri[cp[k] + 1:cp[k + 1]], dtype=np.int64) for k in range(n)]
+    assert OS.is_filled(n, cols)
+    # the band of half-bandwidth 2 with these blocks has no added entry in the
+    # first two columns of each block and one per block in column f+2 .. :
+    extra = got - _pairs_of(cp0, ri0)
+    assert extra == {(3, 0), (7, 4), (11, 8)} | {(r, j) for (f, l) in ((0, 4), (4, 8)) for j in range(f, l)
+                                                  for r in (l, l + 1) if r - j > 2}
+
+
+def test_stored_er5000_analysis():
+    """The stored analysis of the Erdos-Renyi workload (used by the CPU
+    oracle's timing arm, which does not load the library) is what the
+    library's minimum-degree ordering and relaxed supernodes give, and the
+    oracle's fill and supernodal pattern of it equal the library's V."""
+    from workloads import analysed
+    B = lib()
+    pattern, perm, sp = analysed.load_er5000()
+    sym = B.Symbolic(*pattern, ordering="mindeg", relax=16, split_cols=-1)
+    assert np.array_equal(np.asarray(sym.perm, dtype=np.int64), perm)
+    assert np.array_equal(np.asarray(sym.supernodes()[0], dtype=np.int64), sp)
+    n, cp, ri = W.permute(pattern, perm)
+    I, _ = OS.fill(n, OS.columns_from_csc(n, cp, ri))
+    vcp, vri = OS.supernodal_pattern(n, I, sp)
+    assert np.array_equal(vcp, sym.colptr) and np.array_equal(vri, sym.rowind)
+    # the split partition the benchmark may choose has the same pattern
+    sym2 = B.Symbolic(*pattern, ordering="mindeg", relax=16, split_cols=512)
+    assert np.array_equal(sym2.colptr, sym.colptr) and np.array_equal(sym2.rowind, sym.rowind)
