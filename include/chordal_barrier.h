@@ -85,7 +85,12 @@ typedef struct {
                               passes of the Hessian, the Hessian factor and the inverse
                               Hessian (the Cholesky product runs them in the warp tier);
                               0 (default): off */
-  int32_t reserved[4];
+  int32_t tc_products;     /* dense-tier products on the tensor cores (FP64-accurate digit
+                              products, see chd_dgemm_tc): 0 (default) = products of at
+                              least 64 x 64 outputs with inner dimension >= 32 and
+                              M N K >= 2^22 per right-hand side; 1 = every product of at
+                              least 64 x 16 outputs; -1 = never (FP64 units only) */
+  int32_t reserved[3];
 } chd_opts;
 
 /* Fill `opts` with the defaults: natural order, relax 0, tie_last 1, default
@@ -354,6 +359,31 @@ int64_t chd_split_k_launches(void);
  * the front kernels.  Allocates and frees one small device buffer.
  */
 chd_status chd_probe_fp64_peak(void* stream, double* gflops);
+
+/*
+ * Measurement and test utility (not an operation of the paper): C = beta C +
+ * alpha A B for column-major FP64 matrices on the device (A m x k, lda >= m;
+ * B k x n, ldb >= k; C m x n, ldc >= m) computed on the bf16 tensor cores
+ * by splitting A's rows and B's columns into eight 7-bit integer digits
+ * (error-free digit products, Ozaki et al. 2012) and summing the digit
+ * products by level in FP32 tensor-memory accumulators.  The error is of
+ * the order of an FP64 product's, 2^-53 k max_l |a_il| max_l |b_lj|, relative
+ * to row and column maxima.  The dense tier of the library uses the same
+ * kernels for its large products.  Allocates and frees scratch on `stream`
+ * (stream-ordered) and synchronises it.  Errors: CHD_ERR_INVALID for
+ * negative sizes or short leading dimensions, CHD_ERR_OOM, CHD_ERR_CUDA,
+ * CHD_ERR_TIMEOUT if a bounded wait inside the kernel ran out.
+ */
+chd_status chd_dgemm_tc(int64_t m, int64_t n, int64_t k, double alpha, const double* a, int64_t lda,
+                        const double* b, int64_t ldb, double beta, double* c, int64_t ldc, void* stream);
+
+/*
+ * Measurement utility (not an operation of the paper): throughput of raw
+ * bf16 tcgen05.mma (M = 128, N = 256, K = 16, FP32 accumulation) on every
+ * SM, in TFLOP/s, timed with CUDA events on `stream` (synchronises).  The
+ * denominator of the tensor-core roofline of chd_dgemm_tc.
+ */
+chd_status chd_probe_tc_bf16_peak(void* stream, double* tflops);
 
 void chd_factor_free(chd_factor* fac);
 

@@ -40,7 +40,8 @@ class ChdError(RuntimeError):
 class chd_opts(C.Structure):
     _fields_ = [("ordering", C.c_int32), ("user_perm", C.POINTER(C.c_int64)), ("relax", C.c_int32),
                 ("tie_last", C.c_int32), ("big_rows", C.c_int32), ("big_cols", C.c_int32),
-                ("split_cols", C.c_int32), ("chain_runs", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("split_cols", C.c_int32), ("chain_runs", C.c_int32), ("tc_products", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 _p = C.c_void_p
@@ -72,6 +73,11 @@ _lib.chd_kernel_launches.argtypes = []
 _lib.chd_kernel_launches.restype = _i64
 _lib.chd_split_k_launches.argtypes = []
 _lib.chd_split_k_launches.restype = _i64
+_lib.chd_dgemm_tc.argtypes = [_i64, _i64, _i64, C.c_double, C.c_void_p, _i64, C.c_void_p, _i64, C.c_double,
+                              C.c_void_p, _i64, C.c_void_p]
+_lib.chd_dgemm_tc.restype = C.c_int
+_lib.chd_probe_tc_bf16_peak.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
+_lib.chd_probe_tc_bf16_peak.restype = C.c_int
 _lib.chd_hessian_noalloc.argtypes = [_p, C.c_int, _p, _i64, _p, _i64, _p]
 _lib.chd_hessian_noalloc.restype = C.c_int
 _lib.chd_probe_fp64_peak.argtypes = [_p, C.POINTER(C.c_double)]
@@ -138,7 +144,7 @@ def _dptr(t, what, nnz=None, rows=None):
 # ---------------------------------------------------------------------------
 
 def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0,
-                big_cols=0, split_cols=0, chain_runs=False):
+                big_cols=0, split_cols=0, chain_runs=False, tc_products=0):
     colptr = np.ascontiguousarray(colptr, dtype=np.int64)
     rowind = np.ascontiguousarray(rowind, dtype=np.int32)
     o = chd_opts()
@@ -155,6 +161,7 @@ def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_l
     o.big_cols = int(big_cols)
     o.split_cols = int(split_cols)
     o.chain_runs = int(chain_runs)
+    o.tc_products = int(tc_products)
     out = _p()
     rc = _lib.chd_analyze(int(n), colptr.ctypes.data, rowind.ctypes.data, C.byref(o), C.byref(out))
     _check(rc, "chd_analyze")
@@ -162,7 +169,7 @@ def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_l
 
 
 def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big_cols=0, split_cols=0,
-          chain_runs=False):
+          chain_runs=False, tc_products=0):
     o = chd_opts()
     _lib.chd_opts_default(C.byref(o))
     o.ordering = ORDERINGS[ordering]
@@ -177,6 +184,7 @@ def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big
     o.big_cols = int(big_cols)
     o.split_cols = int(split_cols)
     o.chain_runs = int(chain_runs)
+    o.tc_products = int(tc_products)
     return o, keep
 
 
@@ -384,6 +392,32 @@ def chd_split_k_launches():
     return int(_lib.chd_split_k_launches())
 
 
+def chd_dgemm_tc(a, b, c=None, alpha=1.0, beta=0.0, stream=None):
+    """C = beta C + alpha A B on the tensor cores (FP64-level accuracy).
+    a (m x k), b (k x n), c (m x n): CUDA float64 tensors in column-major
+    order (transposed views of row-major tensors, ``t.T``) or None for c."""
+    import torch
+    m, k = a.shape
+    k2, n = b.shape
+    if k2 != k:
+        raise ValueError("inner dimensions differ")
+    if c is None:
+        c = torch.zeros((n, m), dtype=torch.float64, device=a.device).T
+    for t_, what in ((a, "a"), (b, "b"), (c, "c")):
+        if t_.dtype != torch.float64 or not t_.is_cuda or (t_.numel() and t_.stride(0) != 1):
+            raise ValueError(f"{what} must be a column-major CUDA float64 matrix")
+    ld = lambda t_: max(1, t_.stride(1) if t_.dim() == 2 and t_.shape[1] > 1 else t_.shape[0])
+    _check(_lib.chd_dgemm_tc(m, n, k, float(alpha), a.data_ptr(), ld(a), b.data_ptr(), ld(b), float(beta),
+                             c.data_ptr(), ld(c), _stream_ptr(stream)), "chd_dgemm_tc")
+    return c
+
+
+def chd_probe_tc_bf16_peak(stream=None):
+    v = C.c_double()
+    _check(_lib.chd_probe_tc_bf16_peak(_stream_ptr(stream), C.byref(v)), "chd_probe_tc_bf16_peak")
+    return v.value
+
+
 def chd_probe_fp64_peak(stream=None):
     v = C.c_double()
     _check(_lib.chd_probe_fp64_peak(_stream_ptr(stream), C.byref(v)), "chd_probe_fp64_peak")
@@ -402,10 +436,10 @@ class Symbolic:
     """Owner of a ``chd_symbolic``: the analysed pattern and its clique tree."""
 
     def __init__(self, n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True,
-                 big_rows=0, big_cols=0, split_cols=0, chain_runs=False):
+                 big_rows=0, big_cols=0, split_cols=0, chain_runs=False, tc_products=0):
         self._h = chd_analyze(n, colptr, rowind, ordering=ordering, perm=perm, relax=relax,
                               tie_last=tie_last, big_rows=big_rows, big_cols=big_cols,
-                              split_cols=split_cols, chain_runs=chain_runs)
+                              split_cols=split_cols, chain_runs=chain_runs, tc_products=tc_products)
         info = chd_symbolic_info(self._h)
         self.n = info["n"]
         self.nnz = info["nnz"]

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libchordal_barrier.so")
-SOURCES = ["symbolic.cpp", "capi.cpp", "kernels.cu", "bigfront.cu", "warp_tier.cu", "chain_tier.cu", "noalloc.cu"]
+SOURCES = ["symbolic.cpp", "capi.cpp", "kernels.cu", "bigfront.cu", "warp_tier.cu", "chain_tier.cu", "noalloc.cu",
+           "tc_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

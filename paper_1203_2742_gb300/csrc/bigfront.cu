@@ -14,6 +14,7 @@
 
 #include "chd_internal.h"
 #include "front_views.cuh"
+#include "tc_gemm.cuh"
 
 namespace chd_launch {
 void count_launch();
@@ -28,7 +29,7 @@ constexpr int GT = 64;   // GEMM output tile
 constexpr int GK = 16;   // GEMM k-chunk
 
 template <class V>
-__device__ __forceinline__ V shifted(V v, int64_t off) {
+__host__ __device__ __forceinline__ V shifted(V v, int64_t off) {
   v.p += off;
   return v;
 }
@@ -41,6 +42,10 @@ struct Ctx {
   double* xs;
   int64_t cap;  // doubles
   int* ctr;
+  void* tc = nullptr;          // tensor-core product scratch (digit planes)
+  size_t tc_cap = 0;
+  int64_t* status = nullptr;   // the factor's status
+  int tc_mode = -1;            // chd_opts.tc_products (-1: FP64 units only)
   operator cudaStream_t() const { return s; }
 };
 // A stream's scratch slice of xcap doubles: the first xcap - kCtrDoubles hold
@@ -49,6 +54,14 @@ constexpr int64_t kCtrDoubles = 8;
 inline Ctx make_ctx(cudaStream_t s, double* xs, int64_t xcap) {
   if (!xs || xcap <= kCtrDoubles) return Ctx{s, nullptr, 0, nullptr};
   return Ctx{s, xs, xcap - kCtrDoubles, reinterpret_cast<int*>(xs + (xcap - kCtrDoubles))};
+}
+inline Ctx make_ctx(const Slot& sl) {
+  Ctx c = make_ctx(sl.st, sl.xs, sl.xcap);
+  c.tc = sl.tc;
+  c.tc_cap = sl.tc_cap;
+  c.status = sl.status;
+  c.tc_mode = sl.tc_mode;
+  return c;
 }
 
 // ---------------------------------------------------------------------------
@@ -193,10 +206,47 @@ inline double balance(int64_t units) {
   return per > 0 ? (double)units / (double)(per * 152) : 0.0;
 }
 
+// Products large enough for the tensor cores run there (tc_gemm.cuh: FP64
+// accuracy from exact bf16 digit products), in as many right-hand sides at
+// once as the stream slot's scratch holds; everything else, and every
+// product on a slot without tensor-core scratch, runs on the FP64 units.
+// Default rule (tc_mode 0): the estimated tensor-core time -- a fixed cost
+// for its launches, the digit products (36 bf16 products of each output
+// tile), the FP64 assembly of every output (about a dozen FP64 operations)
+// and the digit planes' bytes -- below 0.8 of the FP64-unit time of the
+// product (2 M N K flops at about 0.9 TFLOP/s).
+inline bool tc_worth(const Ctx& st, int batch, int M, int N, int K) {
+  if (!st.tc || st.tc_mode < 0 || M < 64 || N < 16 || K < 1) return false;
+  if (st.tc_mode > 0) return true;
+  if (N < 32 || K < 32) return false;
+  const double mnk = static_cast<double>(M) * N * K * batch;
+  const double fp64 = 2.0 * mnk / 0.9e12;
+  const double tc = 15e-6 + mnk * 72.0 / 2.0e15 + static_cast<double>(M) * N * batch * 24.0 / 0.9e12 +
+                    static_cast<double>(M + N) * K * batch * 48.0 / 3.0e12;
+  return tc < 0.8 * fp64;
+}
+template <class MA, class MB, class MC>
+bool tc_products(const Ctx& st, int batch, int M, int N, int K, double alpha, MA A, int64_t sA, MB B, int64_t sB,
+                 double beta, MC C, int64_t sC, bool lower) {
+  const size_t one = tc::scratch_bytes(1, M, N, K);
+  int zc = one > 0 ? static_cast<int>(std::min<size_t>(static_cast<size_t>(batch), st.tc_cap / one)) : 0;
+  while (zc > 1 && tc::scratch_bytes(zc, M, N, K) > st.tc_cap) --zc;
+  if (zc < 1) return false;
+  for (int z0 = 0; z0 < batch; z0 += zc) {
+    const int nz = std::min(zc, batch - z0);
+    if (tc::gemm(st.s, st.tc, st.tc_cap, st.status, nz, M, N, K, alpha, shifted(A, z0 * sA), sA,
+                 shifted(B, z0 * sB), sB, beta, shifted(C, z0 * sC), sC, lower) != cudaSuccess)
+      return false;
+    for (int p = 0; p < 4 * std::max(1, (K + tc::KMAX - 1) / tc::KMAX); ++p) chd_launch::count_launch();
+  }
+  return true;
+}
+
 template <class MA, class MB, class MC>
 void gemm(const Ctx& st, int batch, int M, int N, int K, double alpha, MA A, int64_t sA, MB B, int64_t sB,
           double beta, MC C, int64_t sC, bool lower) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
+  if (tc_worth(st, batch, M, N, K) && tc_products(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower)) return;
   constexpr int64_t kFill = 2 * 152;
   if (N <= 8 && M > 64) gemm_cfg<128, 8, 4, 1>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
   else if (N <= 16 && M > 64) gemm_cfg<128, 16, 4, 2>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
@@ -218,47 +268,50 @@ void gemm(const Ctx& st, int batch, int M, int N, int K, double alpha, MA A, int
 
 // ---------------------------------------------------------------------------
 // Blocked right-looking Cholesky (panels of PP columns) and triangular
-// solves (panels of TW columns).  FP64 throughput per SM is low (about 1.6
-// lane-FMAs per clock), so the panel kernels give every SM only a few rows:
-// one warp per CTA, 8 rows per warp, 4 lanes per row (lane q of a row owns
-// the panel columns c = q mod 4), the substitution along the panel columns
-// exchanging each solved entry with a shuffle inside the 4-lane group.
+// solves (panels of TW columns).  On GB300 an SM retires about 1.6 FP64
+// lane-operations per clock, spread over its four sub-partitions: a single
+// warp issuing FP64 instructions keeps one sub-partition busy and leaves
+// three idle.  The panel kernels therefore run four warps per CTA and only
+// PR = 8 rows per CTA (two rows per warp, sixteen lanes per row, lane q
+// owning the panel columns c = q mod 16), so that a panel of R rows keeps
+// R / 2 warps issuing; the substitution along the panel columns passes each
+// solved entry within its 16-lane group by a shuffle.
 // ---------------------------------------------------------------------------
-constexpr int PP = 32;  // Cholesky panel width
-constexpr int TW = 64;  // triangular-solve panel width
-constexpr int PR = 8;   // panel rows per CTA
+constexpr int PP = 32;   // Cholesky panel width
+constexpr int TW = 64;   // triangular-solve panel width
+constexpr int PR = 8;    // panel rows per CTA
+constexpr int PT = 128;  // threads per panel CTA
 
-// Cholesky of the pb x pb (pb <= 32) lower block held by one warp, lane i
-// holding row i in registers (a[c] = A(i, c), c <= i); every column's
-// entries reach the other lanes by shuffles.  On return the lanes hold the
-// rows of C and rinv (shared) the reciprocal pivots.  A non-positive pivot
-// is recorded and replaced by 1.
-__device__ __forceinline__ void warp_potrf32(double (&a)[PP], double* rinv, int pb, int lane, int64_t* st,
-                                             int64_t code, int64_t snode, int64_t col) {
-#pragma unroll
-  for (int j = 0; j < PP; ++j) {
-    if (j < pb) {
-      double d = __shfl_sync(0xffffffffu, a[j], j);
+// Cooperative Cholesky of the pb x pb block held in shared memory (ld
+// PP + 1, identity beyond pb) by the CTA's PT threads: column by column,
+// pivot, scale of the column below it, rank-one update of the trailing
+// lower triangle.  On return Ls holds the lower factor C and rinv the
+// reciprocal pivots; a non-positive pivot is recorded and replaced by 1.
+// Every CTA of a launch computes the same values in the same order.
+__device__ __forceinline__ void cta_potrf32(double (*Ls)[PP + 1], double* rinv, int pb, int64_t* st, int64_t code,
+                                            int64_t snode, int64_t col) {
+  const int tid = threadIdx.x;
+  for (int j = 0; j < pb; ++j) {
+    if (tid == 0) {
+      double d = Ls[j][j];
       if (!(d > 0.0)) {
-        if (lane == 0) record_error(st, code, snode, col < 0 ? -1 : col + j);
+        record_error(st, code, snode, col < 0 ? -1 : col + j);
         d = 1.0;
       }
-      const double r = rsqrt(d);
-      const double l = a[j] * r;  // L(lane, j) for lane > j
-      if (lane == j) {
-        a[j] = sqrt(d);
-        rinv[j] = r;
-      } else if (lane > j) {
-        a[j] = l;
-      }
-#pragma unroll
-      for (int k = j + 1; k < PP; ++k) {
-        const double lk = __shfl_sync(0xffffffffu, l, k);
-        if (lane >= k) a[k] = fma(-l, lk, a[k]);
-      }
+      Ls[j][j] = sqrt(d);
+      rinv[j] = rsqrt(d);
     }
+    __syncthreads();
+    const double r = rinv[j];
+    for (int i = j + 1 + tid; i < pb; i += PT) Ls[i][j] *= r;
+    __syncthreads();
+    const int w = pb - j - 1;
+    for (int e = tid; e < w * w; e += PT) {
+      const int i = j + 1 + e % w, k = j + 1 + e / w;
+      if (k <= i) Ls[i][k] = fma(-Ls[i][j], Ls[k][j], Ls[i][k]);
+    }
+    __syncthreads();
   }
-  __syncwarp();
 }
 
 // One panel of the Cholesky of F (ld): the pb x pb block at (j0, j0) and the
@@ -268,58 +321,57 @@ __device__ __forceinline__ void warp_potrf32(double (&a)[PP], double* rinv, int 
 // counter -- when every CTA has read the unfactored block -- writes the
 // factored block back and resets the counter.  ctr == nullptr is allowed
 // for a single-CTA launch with R == 0.
-__global__ void __launch_bounds__(32) mk_potrf_panel(double* F, int64_t ld, int j0, int pb, int R, int* ctr,
+__global__ void __launch_bounds__(PT) mk_potrf_panel(double* F, int64_t ld, int j0, int pb, int R, int* ctr,
                                                      int64_t* st, int64_t code, int64_t snode, int64_t col0) {
   __shared__ double Ls[PP][PP + 1];
   __shared__ double rinv[PP];
   __shared__ int last;
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x;
   double* D = F + j0 + (int64_t)j0 * ld;
-  double a[PP];
-#pragma unroll
-  for (int c = 0; c < PP; ++c)
-    a[c] = (lane < pb && c < pb && lane >= c) ? D[lane + (int64_t)c * ld] : (c == lane ? 1.0 : 0.0);
-  __syncwarp();
-  if (lane == 0) {
+  for (int e = tid; e < PP * PP; e += PT) {
+    const int i = e % PP, c = e / PP;
+    Ls[i][c] = (i < pb && c < pb && i >= c) ? D[i + (int64_t)c * ld] : (i == c ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  if (tid == 0) {
     __threadfence();
     last = (ctr == nullptr) ? 1 : (atomicAdd(ctr, 1) == (int)gridDim.x - 1);
   }
-  warp_potrf32(a, rinv, pb, lane, st, code, snode, col0 < 0 ? -1 : col0 + j0);
-#pragma unroll
-  for (int c = 0; c < PP; ++c) Ls[lane][c] = a[c];
-  __syncwarp();
-  const int rr = lane >> 2, q = lane & 3;
-  const int i = blockIdx.x * PR + rr;
+  cta_potrf32(Ls, rinv, pb, st, code, snode, col0 < 0 ? -1 : col0 + j0);
+  const int lane = tid & 31, q = lane & 15;
+  const int i = blockIdx.x * PR + 2 * (tid >> 5) + (lane >> 4);
   const bool ok = i < R;
   double* Bi = F + (j0 + pb + (ok ? i : 0)) + (int64_t)j0 * ld;
-  double b[PP / 4];
+  double b[PP / 16];
 #pragma unroll
-  for (int u = 0; u < PP / 4; ++u) {
-    const int c = 4 * u + q;
+  for (int u = 0; u < PP / 16; ++u) {
+    const int c = 16 * u + q;
     b[u] = (ok && c < pb) ? Bi[(int64_t)c * ld] : 0.0;
   }
 #pragma unroll
   for (int c = 0; c < PP; ++c) {
     if (c < pb) {
-      double x = b[c / 4] * rinv[c];
-      x = __shfl_sync(0xffffffffu, x, (lane & ~3) | (c & 3));
-      if (q == (c & 3)) b[c / 4] = x;
+      double x = b[c / 16] * rinv[c];
+      x = __shfl_sync(0xffffffffu, x, (lane & 16) | (c & 15));
+      if (q == (c & 15)) b[c / 16] = x;
 #pragma unroll
-      for (int u = c / 4; u < PP / 4; ++u) {
-        const int t = 4 * u + q;
+      for (int u = c / 16; u < PP / 16; ++u) {
+        const int t = 16 * u + q;
         if (t > c && t < pb) b[u] = fma(-Ls[t][c], x, b[u]);
       }
     }
   }
 #pragma unroll
-  for (int u = 0; u < PP / 4; ++u) {
-    const int c = 4 * u + q;
+  for (int u = 0; u < PP / 16; ++u) {
+    const int c = 16 * u + q;
     if (ok && c < pb) Bi[(int64_t)c * ld] = b[u];
   }
   if (last) {
-    for (int c = 0; c < pb; ++c)
-      if (lane < pb && lane >= c) D[lane + (int64_t)c * ld] = Ls[lane][c];
-    if (lane == 0 && ctr) *ctr = 0;
+    for (int e = tid; e < pb * pb; e += PT) {
+      const int r = e % pb, c = e / pb;
+      if (r >= c) D[r + (int64_t)c * ld] = Ls[r][c];
+    }
+    if (tid == 0 && ctr) *ctr = 0;
   }
 }
 
@@ -327,38 +379,38 @@ __global__ void __launch_bounds__(32) mk_potrf_panel(double* F, int64_t ld, int 
 // [p0, p0+pb), pb <= TW, against the diagonal block L[p0.., p0..] (lower):
 //   fwd = 1:  B_p := B_p L_pp^{-T}      fwd = 0:  B_p := B_p L_pp^{-1}
 template <class MB>
-__global__ void __launch_bounds__(32) mk_trsm_panel(int R, MB B, int64_t sB, int p0, int pb, const double* L,
+__global__ void __launch_bounds__(PT) mk_trsm_panel(int R, MB B, int64_t sB, int p0, int pb, const double* L,
                                                     int64_t ld, int fwd) {
   __shared__ double Ls[TW][TW + 1];
   __shared__ double rinv[TW];
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x;
   B.p += (int64_t)blockIdx.z * sB;
-  for (int e = lane; e < pb * pb; e += 32) {
+  for (int e = tid; e < pb * pb; e += PT) {
     const int i = e % pb, j = e / pb;
     Ls[i][j] = i >= j ? L[(p0 + i) + (int64_t)(p0 + j) * ld] : 0.0;
   }
-  __syncwarp();
-  for (int c = lane; c < pb; c += 32) rinv[c] = 1.0 / Ls[c][c];
-  __syncwarp();
-  const int rr = lane >> 2, q = lane & 3;
-  const int r = blockIdx.x * PR + rr;
+  __syncthreads();
+  for (int c = tid; c < pb; c += PT) rinv[c] = 1.0 / Ls[c][c];
+  __syncthreads();
+  const int lane = tid & 31, q = lane & 15;
+  const int r = blockIdx.x * PR + 2 * (tid >> 5) + (lane >> 4);
   const bool ok = r < R;
-  double b[TW / 4];
+  double b[TW / 16];
 #pragma unroll
-  for (int u = 0; u < TW / 4; ++u) {
-    const int c = 4 * u + q;
+  for (int u = 0; u < TW / 16; ++u) {
+    const int c = 16 * u + q;
     b[u] = (ok && c < pb) ? B.at(r, p0 + c) : 0.0;
   }
   if (fwd) {
 #pragma unroll
     for (int c = 0; c < TW; ++c) {
       if (c < pb) {
-        double x = b[c / 4] * rinv[c];
-        x = __shfl_sync(0xffffffffu, x, (lane & ~3) | (c & 3));
-        if (q == (c & 3)) b[c / 4] = x;
+        double x = b[c / 16] * rinv[c];
+        x = __shfl_sync(0xffffffffu, x, (lane & 16) | (c & 15));
+        if (q == (c & 15)) b[c / 16] = x;
 #pragma unroll
-        for (int u = c / 4; u < TW / 4; ++u) {
-          const int t = 4 * u + q;
+        for (int u = c / 16; u < TW / 16; ++u) {
+          const int t = 16 * u + q;
           if (t > c && t < pb) b[u] = fma(-Ls[t][c], x, b[u]);
         }
       }
@@ -367,20 +419,20 @@ __global__ void __launch_bounds__(32) mk_trsm_panel(int R, MB B, int64_t sB, int
 #pragma unroll
     for (int c = TW - 1; c >= 0; --c) {
       if (c < pb) {
-        double x = b[c / 4] * rinv[c];
-        x = __shfl_sync(0xffffffffu, x, (lane & ~3) | (c & 3));
-        if (q == (c & 3)) b[c / 4] = x;
+        double x = b[c / 16] * rinv[c];
+        x = __shfl_sync(0xffffffffu, x, (lane & 16) | (c & 15));
+        if (q == (c & 15)) b[c / 16] = x;
 #pragma unroll
-        for (int u = 0; u <= c / 4; ++u) {
-          const int t = 4 * u + q;
+        for (int u = 0; u <= c / 16; ++u) {
+          const int t = 16 * u + q;
           if (t < c) b[u] = fma(-Ls[c][t], x, b[u]);
         }
       }
     }
   }
 #pragma unroll
-  for (int u = 0; u < TW / 4; ++u) {
-    const int c = 4 * u + q;
+  for (int u = 0; u < TW / 16; ++u) {
+    const int c = 16 * u + q;
     if (ok && c < pb) B.at(r, p0 + c) = b[u];
   }
 }
@@ -388,7 +440,7 @@ __global__ void __launch_bounds__(32) mk_trsm_panel(int R, MB B, int64_t sB, int
 template <class MB>
 void panel_solve(const Ctx& st, int batch, int R, MB B, int64_t sB, int p0, int pb, const double* L,
                  int64_t ld, int fwd) {
-  mk_trsm_panel<MB><<<dim3((R + PR - 1) / PR, 1, batch), 32, 0, st>>>(R, B, sB, p0, pb, L, ld, fwd);
+  mk_trsm_panel<MB><<<dim3((R + PR - 1) / PR, 1, batch), PT, 0, st>>>(R, B, sB, p0, pb, L, ld, fwd);
   chd_launch::count_launch();
 }
 
@@ -430,11 +482,11 @@ void potrf_partial(const Ctx& st, double* F, int64_t ld, int J, int n, int64_t* 
     const int pb = std::min(PP, n - j0);
     const int R = J - j0 - pb;
     if (st.ctr) {
-      mk_potrf_panel<<<std::max(1, (R + PR - 1) / PR), 32, 0, st>>>(F, ld, j0, pb, R, st.ctr, status, code,
+      mk_potrf_panel<<<std::max(1, (R + PR - 1) / PR), PT, 0, st>>>(F, ld, j0, pb, R, st.ctr, status, code,
                                                                       snode, col0);
       chd_launch::count_launch();
     } else {
-      mk_potrf_panel<<<1, 32, 0, st>>>(F, ld, j0, pb, 0, nullptr, status, code, snode, col0);
+      mk_potrf_panel<<<1, PT, 0, st>>>(F, ld, j0, pb, 0, nullptr, status, code, snode, col0);
       chd_launch::count_launch();
       if (R > 0) panel_solve(st, 1, R, Dn{F + j0 + pb, ld}, 0, j0, pb, F, ld, 1);
     }
@@ -1285,56 +1337,56 @@ void group_complete(const chd_symbolic* s, const Ctx& st, int g, const double* S
 
 namespace chd_launch {
 using chd::big::Ctx;
-void big_factor(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* X,
+void big_factor(const chd_symbolic* s, const Slot& sl, int k, const double* X,
                 double* Lc, double* Wc, double* Dd, double* ws, double* ldet, int64_t* status) {
-  if (s->grp_of[k] >= 0) return chd::big::group_factor(s, chd::big::make_ctx(st, xs, xcap), s->grp_of[k], X, Lc, Wc, Dd, ws, ldet, status);
-  chd::big::factor_front(s, chd::big::make_ctx(st, xs, xcap), k, X, Lc, Wc, Dd, ws, ldet, status);
+  if (s->grp_of[k] >= 0) return chd::big::group_factor(s, chd::big::make_ctx(sl), s->grp_of[k], X, Lc, Wc, Dd, ws, ldet, status);
+  chd::big::factor_front(s, chd::big::make_ctx(sl), k, X, Lc, Wc, Dd, ws, ldet, status);
 }
-void big_product(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Lc,
+void big_product(const chd_symbolic* s, const Slot& sl, int k, const double* Lc,
                  double* X, double* ws) {
-  if (s->grp_of[k] >= 0) return chd::big::group_product(s, chd::big::make_ctx(st, xs, xcap), s->grp_of[k], Lc, X, ws);
-  chd::big::product_front(s, chd::big::make_ctx(st, xs, xcap), k, Lc, X, ws);
+  if (s->grp_of[k] >= 0) return chd::big::group_product(s, chd::big::make_ctx(sl), s->grp_of[k], Lc, X, ws);
+  chd::big::product_front(s, chd::big::make_ctx(sl), k, Lc, X, ws);
 }
-void big_gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Wc,
+void big_gradient(const chd_symbolic* s, const Slot& sl, int k, const double* Wc,
                   double* Sc, double* g, double* Vd, double* ws) {
-  if (s->grp_of[k] >= 0) return chd::big::group_gradient(s, chd::big::make_ctx(st, xs, xcap), s->grp_of[k], Wc, Sc, g, Vd, ws);
-  chd::big::gradient_front(s, chd::big::make_ctx(st, xs, xcap), k, Wc, Sc, g, Vd, ws);
+  if (s->grp_of[k] >= 0) return chd::big::group_gradient(s, chd::big::make_ctx(sl), s->grp_of[k], Wc, Sc, g, Vd, ws);
+  chd::big::gradient_front(s, chd::big::make_ctx(sl), k, Wc, Sc, g, Vd, ws);
 }
-void big_hess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
+void big_hess_up(const chd_symbolic* s, const Slot& sl, int m, int k, const double* Wc,
                  const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws,
                  const uint8_t* act) {
   // a leaf group has no children; with `act` (pruned Hessian factor) a dense
   // front still runs, skipping pruned children, and gives exact zeros where
   // its own subtree is pruned
-  if (s->grp_of[k] >= 0) return chd::big::group_hess_up(s, chd::big::make_ctx(st, xs, xcap), m, s->grp_of[k], Wc, Vd, Y, ldy, T, ldt, ws);
-  chd::big::hess_up_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, Vd, Y, ldy, T, ldt, ws, act);
+  if (s->grp_of[k] >= 0) return chd::big::group_hess_up(s, chd::big::make_ctx(sl), m, s->grp_of[k], Wc, Vd, Y, ldy, T, ldt, ws);
+  chd::big::hess_up_front(s, chd::big::make_ctx(sl), m, k, Wc, Vd, Y, ldy, T, ldt, ws, act);
 }
-void big_hess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
+void big_hess_down(const chd_symbolic* s, const Slot& sl, int m, int k, const double* Wc,
                    double* T, int64_t ldt, double* ws) {
-  if (s->grp_of[k] >= 0) return chd::big::group_hess_down(s, chd::big::make_ctx(st, xs, xcap), m, s->grp_of[k], Wc, T, ldt, ws);
-  chd::big::hess_down_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, T, ldt, ws);
+  if (s->grp_of[k] >= 0) return chd::big::group_hess_down(s, chd::big::make_ctx(sl), m, s->grp_of[k], Wc, T, ldt, ws);
+  chd::big::hess_down_front(s, chd::big::make_ctx(sl), m, k, Wc, T, ldt, ws);
 }
-void big_ihess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k,
+void big_ihess_down(const chd_symbolic* s, const Slot& sl, int m, int k,
                     const double* Wc, const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y,
                     int64_t ldy, double* ws) {
-  if (s->grp_of[k] >= 0) return chd::big::group_ihess_down(s, chd::big::make_ctx(st, xs, xcap), m, s->grp_of[k], Wc, Dd, Rd, T, ldt, Y, ldy, ws);
-  chd::big::ihess_down_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+  if (s->grp_of[k] >= 0) return chd::big::group_ihess_down(s, chd::big::make_ctx(sl), m, s->grp_of[k], Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+  chd::big::ihess_down_front(s, chd::big::make_ctx(sl), m, k, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
 }
-void big_ihess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
+void big_ihess_up(const chd_symbolic* s, const Slot& sl, int m, int k, const double* Wc,
                   double* Y, int64_t ldy, double* ws) {
-  if (s->grp_of[k] >= 0) return chd::big::group_ihess_up(s, chd::big::make_ctx(st, xs, xcap), m, s->grp_of[k], Wc, Y, ldy, ws);
-  chd::big::ihess_up_front(s, chd::big::make_ctx(st, xs, xcap), m, k, Wc, Y, ldy, ws);
+  if (s->grp_of[k] >= 0) return chd::big::group_ihess_up(s, chd::big::make_ctx(sl), m, s->grp_of[k], Wc, Y, ldy, ws);
+  chd::big::ihess_up_front(s, chd::big::make_ctx(sl), m, k, Wc, Y, ldy, ws);
 }
-void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Sin,
+void big_complete(const chd_symbolic* s, const Slot& sl, int k, const double* Sin,
                   double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
                   int64_t* status) {
-  if (s->grp_of[k] >= 0) return chd::big::group_complete(s, chd::big::make_ctx(st, xs, xcap), s->grp_of[k], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
-  chd::big::complete_front(s, chd::big::make_ctx(st, xs, xcap), k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+  if (s->grp_of[k] >= 0) return chd::big::group_complete(s, chd::big::make_ctx(sl), s->grp_of[k], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+  chd::big::complete_front(s, chd::big::make_ctx(sl), k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
 }
-void big_rtrans(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, int dir,
+void big_rtrans(const chd_symbolic* s, const Slot& sl, int m, int k, int dir,
                 const double* Lc, const double* Qd, double* Z, int64_t ldz, double* ws) {
-  if (s->grp_of[k] >= 0) return chd::big::group_rtrans(s, chd::big::make_ctx(st, xs, xcap), m, s->grp_of[k], dir, Lc, Qd, Z, ldz, ws);
-  chd::big::rtrans_front(s, chd::big::make_ctx(st, xs, xcap), m, k, dir, Lc, Qd, Z, ldz, ws);
+  if (s->grp_of[k] >= 0) return chd::big::group_rtrans(s, chd::big::make_ctx(sl), m, s->grp_of[k], dir, Lc, Qd, Z, ldz, ws);
+  chd::big::rtrans_front(s, chd::big::make_ctx(sl), m, k, dir, Lc, Qd, Z, ldz, ws);
 }
 void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* ws) {
   if (s->grp_of[k] >= 0) return;  // a leaf group reads S itself
@@ -1342,11 +1394,11 @@ void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const doub
 }
 // Cholesky factor R of the cached V_k = S_{A_k A_k} of one big front (lower,
 // into Rd), and the reversed upper factor of V_k (into Qd).
-void big_inv_v(const chd_symbolic* s, cudaStream_t stream, double* xs, int64_t xcap, int k, const double* Vd,
+void big_inv_v(const chd_symbolic* s, const Slot& sl, int k, const double* Vd,
                double* Rd, double* Qd, double* ws, int64_t* status, int what) {
   using namespace chd;
   using namespace chd::big;
-  const Ctx st = chd::big::make_ctx(stream, xs, xcap);
+  const Ctx st = chd::big::make_ctx(sl);
   const int n = (int)(s->sn_ptr[k + 1] - s->sn_ptr[k]);
   const int a = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k]) - n;
   if (a == 0) return;

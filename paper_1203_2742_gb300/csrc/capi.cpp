@@ -14,6 +14,7 @@
 namespace chd_launch {
 int64_t launches();
 int64_t split_k_launches();
+size_t tc_scratch_bytes(int batch, int M, int N, int K);
 void add_launches(int64_t d);
 void factor(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* X, double* Lc,
             double* Wc, double* Dd, double* ws, double* ldet, int64_t* status);
@@ -94,6 +95,26 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
     for (int j = 0; j <= nside; ++j) xs_doubles += (size_t)slice_doubles(j);
     off = align_up(off + xs_doubles * 8);
   }
+  // tensor-core product scratch (digit planes): one slice for the caller's
+  // stream and for each side stream, sized for the largest dense front's
+  // products (up to eight right-hand sides at once on the caller's stream,
+  // two on a side stream; a call with more right-hand sides runs them in
+  // turn, and a product that does not fit runs on the FP64 units)
+  size_t tc_slice[kSideStreams + 1] = {};
+  const size_t otc = off;
+  if (any_big && s->tc_mode >= 0) {
+    int64_t jmax = 0;
+    for (int64_t k = 0; k < s->nsn; ++k)
+      if (s->is_big[k]) jmax = std::max<int64_t>(jmax, front_J(s, k));
+    if (jmax >= 64) {
+      const size_t need = chd_launch::tc_scratch_bytes(1, (int)jmax, (int)jmax, (int)jmax);
+      for (int j = 0; j <= nside; ++j) {
+        tc_slice[j] = align_up(std::min<size_t>(j == 0 ? (size_t(256) << 20) : (size_t(48) << 20),
+                                                (j == 0 ? 8 : 2) * need));
+        off += tc_slice[j];
+      }
+    }
+  }
   void* block = nullptr;
   chd_status rc = cuda_ok(cudaMalloc(&block, off));
   if (rc != CHD_OK) { delete f; return rc; }
@@ -109,6 +130,16 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
   f->ldet = reinterpret_cast<double*>(b + old);
   f->scalar = reinterpret_cast<double*>(b + osc);
   f->status = reinterpret_cast<int64_t*>(b + ost);
+  f->ex.status = f->status;
+  f->ex.tc_mode = s->tc_mode;
+  {
+    char* t = b + otc;
+    for (int j = 0; j <= kSideStreams; ++j) {
+      f->ex.tc[j] = tc_slice[j] ? t : nullptr;
+      f->ex.tc_cap[j] = tc_slice[j];
+      t += tc_slice[j];
+    }
+  }
   if (any_big) {
     double* x = reinterpret_cast<double*>(b + oxs);
     for (int j = 0; j <= nside; ++j) {

@@ -7,7 +7,7 @@
 #include <cstdint>
 #include <vector>
 
-#include "../../include/chordal_barrier.h"
+#include "chordal_barrier.h"
 
 // One record per position of the task lists (aligned with task_fronts):
 // what a warp needs to start a front with one load.  flags:
@@ -120,6 +120,7 @@ struct chd_symbolic {
   // and supernodes [inst_sn[i], inst_sn[i+1]) of the analysed numbering
   std::vector<int64_t> inst_n, inst_nnz, inst_sn;
   int64_t max_front = 0;
+  int tc_mode = 0;  // chd_opts.tc_products
   // device mirror
   SymDev dev;
   void* dev_buf = nullptr;
@@ -141,6 +142,24 @@ struct Exec {
   cudaEvent_t join[kSideStreams] = {};
   double* slice[kSideStreams + 1] = {};
   int64_t slice_cap[kSideStreams + 1] = {};
+  // scratch of the tensor-core products (digit planes), per stream slot
+  void* tc[kSideStreams + 1] = {};
+  size_t tc_cap[kSideStreams + 1] = {};
+  int64_t* status = nullptr;  // the factor's status (tensor-core timeouts)
+  int tc_mode = 0;
+};
+
+// What one dense-tier front sequence runs with: its stream, the split-K
+// scratch slice (may be null), the tensor-core scratch (may be null), the
+// factor's status and the tensor-core mode of the analysis.
+struct Slot {
+  cudaStream_t st = nullptr;
+  double* xs = nullptr;
+  int64_t xcap = 0;
+  void* tc = nullptr;
+  size_t tc_cap = 0;
+  int64_t* status = nullptr;
+  int tc_mode = 0;
 };
 
 // A captured launch sequence of one kind of call (see capi.cpp): the

@@ -999,23 +999,23 @@ void add_launches(int64_t d) { g_launches += d; }
 static inline void count() { ++g_launches; }
 
 // dense-tier sequences (bigfront.cu); xs/xcap: split-K scratch (may be null)
-void big_factor(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* X,
+void big_factor(const chd_symbolic* s, const Slot& sl, int k, const double* X,
                 double* Lc, double* Wc, double* Dd, double* ws, double* ldet, int64_t* status);
-void big_product(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Lc,
+void big_product(const chd_symbolic* s, const Slot& sl, int k, const double* Lc,
                  double* X, double* ws);
-void big_gradient(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Wc,
+void big_gradient(const chd_symbolic* s, const Slot& sl, int k, const double* Wc,
                   double* Sc, double* g, double* Vd, double* ws);
-void big_hess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
+void big_hess_up(const chd_symbolic* s, const Slot& sl, int m, int k, const double* Wc,
                  const double* Vd, const double* Y, int64_t ldy, double* T, int64_t ldt, double* ws,
                  const uint8_t* act);
-void big_hess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
+void big_hess_down(const chd_symbolic* s, const Slot& sl, int m, int k, const double* Wc,
                    double* T, int64_t ldt, double* ws);
-void big_ihess_down(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k,
+void big_ihess_down(const chd_symbolic* s, const Slot& sl, int m, int k,
                     const double* Wc, const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y,
                     int64_t ldy, double* ws);
-void big_ihess_up(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, const double* Wc,
+void big_ihess_up(const chd_symbolic* s, const Slot& sl, int m, int k, const double* Wc,
                   double* Y, int64_t ldy, double* ws);
-void big_complete(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Sin,
+void big_complete(const chd_symbolic* s, const Slot& sl, int k, const double* Sin,
                   double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
                   int64_t* status);
 
@@ -1085,10 +1085,22 @@ struct BigFork {
   template <class Body>
   void run(int count, Body&& body) {
     if (count <= 0) return;
-    double* xs0 = ex ? ex->slice[0] : nullptr;
-    const int64_t cap0 = ex ? ex->slice_cap[0] : 0;
+    auto slot = [&](int j, cudaStream_t bs) {
+      Slot sl;
+      sl.st = bs;
+      if (ex) {
+        sl.xs = ex->slice[j];
+        sl.xcap = ex->slice_cap[j];
+        sl.tc = ex->tc[j];
+        sl.tc_cap = ex->tc_cap[j];
+        sl.status = ex->status;
+        sl.tc_mode = ex->tc_mode;
+      }
+      return sl;
+    };
     if (!ex || ex->nside == 0 || count == 1) {
-      for (int i = 0; i < count; ++i) body(i, st, xs0, cap0);
+      const Slot sl = slot(0, st);
+      for (int i = 0; i < count; ++i) body(i, sl);
       return;
     }
     used = std::min(count, ex->nside);
@@ -1096,7 +1108,7 @@ struct BigFork {
     for (int j = 0; j < used; ++j) cudaStreamWaitEvent(ex->side[j], ex->fork, 0);
     for (int i = 0; i < count; ++i) {
       const int j = i % used;
-      body(i, ex->side[j], ex->slice[1 + j], ex->slice_cap[1 + j]);
+      body(i, slot(1 + j, ex->side[j]));
     }
   }
   void join_now() {
@@ -1140,8 +1152,8 @@ void factor(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double
   for (int l = 0; l < nl; ++l) {
     Level v = level(s, l);
     BigFork bf{ex, st};
-    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-      big_factor(s, bs, xs, xc, big_front(s, v, i), X, Lc, Wc, Dd, ws, ldet, status);
+    bf.run(v.nbig, [&](int i, const Slot& sl) {
+      big_factor(s, sl, big_front(s, v, i), X, Lc, Wc, Dd, ws, ldet, status);
     });
     if (v.nr32 + v.nr64) chain_factor(s, st, v.tr, v.nr32 + v.nr64, X, Lc, Wc, Dd, ws, ldet, status);
     if (v.nwarp) w32::warp_factor(s, st, v.t0, v.nwarp, X, Lc, Wc, Dd, ws, ldet, status);
@@ -1159,8 +1171,8 @@ void product(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doubl
   for (int l = 0; l < nl; ++l) {
     Level v = level(s, l);
     BigFork bf{ex, st};
-    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-      big_product(s, bs, xs, xc, big_front(s, v, i), Lc, X, ws);
+    bf.run(v.nbig, [&](int i, const Slot& sl) {
+      big_product(s, sl, big_front(s, v, i), Lc, X, ws);
     });
     if (v.nr32) w32::warp_product(s, st, v.tr, v.nr32, Lc, X, ws);
     if (v.nr64) w64::warp_product(s, st, v.tr + v.nr32, v.nr64, Lc, X, ws);
@@ -1179,8 +1191,8 @@ void gradient(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
     BigFork bf{ex, st};
-    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-      big_gradient(s, bs, xs, xc, big_front(s, v, i), Wc, Sc, g, Vd, ws);
+    bf.run(v.nbig, [&](int i, const Slot& sl) {
+      big_gradient(s, sl, big_front(s, v, i), Wc, Sc, g, Vd, ws);
     });
     if (v.ncta) {
       k_gradient<<<v.ncta, NT, 0, st>>>(s->dev, v.tc, Wc, Sc, g, Vd, ws);
@@ -1200,8 +1212,8 @@ void hess_up_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m,
   for (int l = 0; l < nl; ++l) {
     Level v = level(s, l);
     BigFork bf{ex, st};
-    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-      big_hess_up(s, bs, xs, xc, m, big_front(s, v, i), Wc, Vd, Y, ldy, T, ldt, ws, act);
+    bf.run(v.nbig, [&](int i, const Slot& sl) {
+      big_hess_up(s, sl, m, big_front(s, v, i), Wc, Vd, Y, ldy, T, ldt, ws, act);
     });
     if (v.nr32 + v.nr64) chain_hess_up(s, st, v.tr, v.nr32 + v.nr64, m, Wc, Vd, Y, ldy, T, ldt, ws, act);
     if (v.nwarp) w32::warp_hess_up(s, st, v.t0, v.nwarp, m, Wc, Vd, Y, ldy, T, ldt, ws, act);
@@ -1219,8 +1231,8 @@ void hess_down_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int 
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
     BigFork bf{ex, st};
-    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-      big_hess_down(s, bs, xs, xc, m, big_front(s, v, i), Wc, T, ldt, ws);
+    bf.run(v.nbig, [&](int i, const Slot& sl) {
+      big_hess_down(s, sl, m, big_front(s, v, i), Wc, T, ldt, ws);
     });
     if (v.ncta) {
       k_hess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, T, ldt, ws);
@@ -1239,7 +1251,7 @@ void hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, cons
 }
 // M <-> W for every front (independent fronts): plain fronts in one launch,
 // dense fronts and leaf groups on the side streams
-void big_rtrans(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int m, int k, int dir,
+void big_rtrans(const chd_symbolic* s, const Slot& sl, int m, int k, int dir,
                 const double* Lc, const double* Qd, double* Z, int64_t ldz, double* ws);
 // per right-hand side and front: active for the pruned Hessian factor
 void prune_mask(const chd_symbolic* s, cudaStream_t st, int m, const double* Y, int64_t ldy, int32_t* cnt,
@@ -1255,8 +1267,8 @@ void rtrans(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, int d
   std::vector<int32_t> dense = s->big_fronts;
   for (int64_t g0 : s->grp_first) dense.push_back((int32_t)g0);
   BigFork bf{ex, st};
-  bf.run((int)dense.size(), [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-    big_rtrans(s, bs, xs, xc, m, dense[i], dir, Lc, Qd, Z, ldz, ws);
+  bf.run((int)dense.size(), [&](int i, const Slot& sl) {
+    big_rtrans(s, sl, m, dense[i], dir, Lc, Qd, Z, ldz, ws);
   });
   if (s->dev.plain_count > 0) {
     SymDev D = s->dev;
@@ -1272,8 +1284,8 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
   for (int l = nl - 1; l >= 0; --l) {
     Level v = level(s, l);
     BigFork bf{ex, st};
-    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-      big_ihess_down(s, bs, xs, xc, m, big_front(s, v, i), Wc, Dd, Rd, T, ldt, Y, ldy, ws);
+    bf.run(v.nbig, [&](int i, const Slot& sl) {
+      big_ihess_down(s, sl, m, big_front(s, v, i), Wc, Dd, Rd, T, ldt, Y, ldy, ws);
     });
     if (v.ncta) {
       k_ihess_down<<<dim3(v.ncta, m), NT, 0, st>>>(s->dev, v.tc, Wc, Dd, Rd, T, ldt, Y, ldy, ws);
@@ -1287,8 +1299,8 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
   for (int l = 0; l < nl; ++l) {
     Level v = level(s, l);
     BigFork bf{ex, st};
-    bf.run(v.nbig, [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-      big_ihess_up(s, bs, xs, xc, m, big_front(s, v, i), Wc, Y, ldy, ws);
+    bf.run(v.nbig, [&](int i, const Slot& sl) {
+      big_ihess_up(s, sl, m, big_front(s, v, i), Wc, Y, ldy, ws);
     });
     if (v.nr32 + v.nr64) chain_ihess_up(s, st, v.tr, v.nr32 + v.nr64, m, Wc, Y, ldy, ws);
     if (v.nwarp) w32::warp_ihess_up(s, st, v.t0, v.nwarp, m, Wc, Y, ldy, ws);
@@ -1310,9 +1322,9 @@ void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
   std::vector<int32_t> bigs = s->big_fronts;  // dense fronts and leaf groups
   for (int64_t g0 : s->grp_first) bigs.push_back((int32_t)g0);
   BigFork bf{ex, st};
-  bf.run((int)bigs.size(), [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-    big_complete_load(s, bs, bigs[i], Sin, ws);
-    big_complete(s, bs, xs, xc, bigs[i], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+  bf.run((int)bigs.size(), [&](int i, const Slot& sl) {
+    big_complete_load(s, sl.st, bigs[i], Sin, ws);
+    big_complete(s, sl, bigs[i], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
   });
   if (s->dev.cta_count > 0) {
     k_complete<<<(int)s->dev.cta_count, NT, 0, st>>>(s->dev, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
@@ -1321,7 +1333,7 @@ void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const doub
   if (s->dev.warp_count > 0) w32::warp_complete_all(s, st, Sin, Lc, Wc, Dd, Vd, Rd, ldet, status);
   bf.join_now();
 }
-void big_inv_v(const chd_symbolic* s, cudaStream_t st, double* xs, int64_t xcap, int k, const double* Vd,
+void big_inv_v(const chd_symbolic* s, const Slot& sl, int k, const double* Vd,
                double* Rd, double* Qd, double* ws, int64_t* status, int what);
 void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* Qd,
            double* ws, int64_t* status, int what) {
@@ -1329,8 +1341,8 @@ void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double*
   for (int64_t k = 0; k < s->nsn; ++k)
     if (s->is_big[k]) bigs.push_back((int)k);
   BigFork bf{ex, st};
-  bf.run((int)bigs.size(), [&](int i, cudaStream_t bs, double* xs, int64_t xc) {
-    big_inv_v(s, bs, xs, xc, bigs[i], Vd, Rd, Qd, ws, status, what);
+  bf.run((int)bigs.size(), [&](int i, const Slot& sl) {
+    big_inv_v(s, sl, bigs[i], Vd, Rd, Qd, ws, status, what);
   });
   if (s->dev.small_count > 0) {
     k_inv_v<<<(int)s->dev.small_count, NT, 0, st>>>(s->dev, Vd, Rd, Qd, ws, status, s->dev.small_fronts, what);

@@ -257,6 +257,7 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
   if (n < 1 || !colptr || !rowind) return CHD_ERR_INVALID;
   vector<vector<int32_t>> adj;
   if (!build_adjacency(n, colptr, rowind, adj)) return CHD_ERR_INVALID;
+  s->tc_mode = opts.tc_products < 0 ? -1 : (opts.tc_products > 0 ? 1 : 0);
 
   // ---- ordering -----------------------------------------------------------
   vector<int64_t> perm0(n);

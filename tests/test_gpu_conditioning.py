@@ -44,6 +44,10 @@ CASES = {
     "cta_grid": (lambda: W.grid2d(24, 24), dict(perm=W.nested_dissection((24, 24), leaf=6))),
     "dense_full": (lambda: W.band(150, 149), dict(big_rows=64, big_cols=64)),
     "dense_arrow": (lambda: W.arrow(260, 100), dict(big_rows=90, big_cols=70)),
+    # the same dense-tier fronts with every product on the tensor cores
+    "tc_dense_full": (lambda: W.band(150, 149), dict(big_rows=64, big_cols=64, tc_products=1)),
+    "tc_dense_arrow": (lambda: W.arrow(260, 100), dict(big_rows=90, big_cols=70, tc_products=1)),
+    "tc_dense600": (lambda: W.band(600, 599), dict(split_cols=256, tc_products=1)),
 }
 
 TOL = 1e-8        # factor, log det, gradient, Hessian (spec bound at condition 1e6)

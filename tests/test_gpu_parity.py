@@ -24,10 +24,11 @@ def torch():
 
 
 class Case:
-    def __init__(self, pattern, ordering="natural", perm=None, relax=0, seed=0, x=None, big=None, split=0):
+    def __init__(self, pattern, ordering="natural", perm=None, relax=0, seed=0, x=None, big=None, split=0, tc=0):
         self.B = lib()
         kw = {} if big is None else dict(big_rows=big[0], big_cols=big[1])
         kw["split_cols"] = split
+        kw["tc_products"] = tc
         self.sym = self.B.Symbolic(*pattern, ordering=ordering, perm=perm, relax=relax, **kw)
         s = self.sym
         self.n, self.cp, self.ri = s.n, s.colptr, s.rowind
@@ -81,6 +82,16 @@ def small_cases():
         "band300_w40": lambda: Case(W.band(300, 40), seed=15),
         "arrow150_w48": lambda: Case(W.arrow(150, 48), seed=16),
         "band120_w63": lambda: Case(W.band(120, 63), seed=17),
+        # every dense-tier product with at least 64 x 16 outputs on the tensor
+        # cores (FP64-accurate digit products), on the dense-tier cases above
+        "tc_dense_grid": lambda: Case(W.grid2d(16, 16), ordering="user",
+                                      perm=W.nested_dissection((16, 16), leaf=6), seed=9, big=(20, 8), tc=1),
+        "tc_dense_er": lambda: Case(W.erdos_renyi(300, 0.02, np.random.default_rng(5)),
+                                    ordering="mindeg", relax=16, seed=10, big=(40, 20), tc=1),
+        "tc_dense_full": lambda: Case(W.band(150, 149), seed=11, big=(64, 64), tc=1),
+        "tc_dense_arrow": lambda: Case(W.arrow(260, 100), seed=12, big=(90, 70), tc=1),
+        "tc_split_dense": lambda: Case(W.band(150, 149), seed=13, big=(64, 64), split=24, tc=1),
+        "tc_wide_arrow": lambda: Case(W.arrow(400, 330), seed=18, tc=1),
     }
 
 
@@ -146,7 +157,7 @@ def test_completion(name):
     assert fx.status() == 0
     I, parent = OS.fill(c.n, OS.columns_from_csc(c.n, c.cp, c.ri))
     cl, seps = OS.cliques_and_separators(I, parent)
-    xh = OD.completion_cliquesum(c.n, c.cp, c.ri, s, cl, seps)
+    xh = OD.completion_refined(c.n, c.cp, c.ri, s, cl, seps)
     lv, dv, _ = OD.factor(c.n, c.cp, c.ri, xh)
     l, d = fx.export()
     np.testing.assert_allclose(c.host(d), dv, rtol=1e-10)
