@@ -212,32 +212,35 @@ inline double balance(int64_t units) {
 // product on a slot without tensor-core scratch, runs on the FP64 units.
 // Default rule (tc_mode 0): the estimated tensor-core time -- a fixed cost
 // for its launches, the digit products (36 bf16 products of each output
-// tile), the FP64 assembly of every output (about a dozen FP64 operations)
-// and the digit planes' bytes -- below 0.8 of the FP64-unit time of the
-// product (2 M N K flops at about 0.9 TFLOP/s).
-inline bool tc_worth(const Ctx& st, int batch, int M, int N, int K) {
+// tile), the assembly of every output (mostly integer work, one or two FP64
+// operations) and the digit planes' bytes (read twice, written once) --
+// below 0.8 of the FP64-unit time of the product (2 M N K flops at about
+// 0.9 TFLOP/s).
+inline bool tc_worth(const Ctx& st, int batch, int M, int N, int K, bool shared_a, bool shared_b) {
   if (!st.tc || st.tc_mode < 0 || M < 64 || N < 16 || K < 1) return false;
   if (st.tc_mode > 0) return true;
-  if (N < 32 || K < 32) return false;
-  const double mnk = static_cast<double>(M) * N * K * batch;
-  const double fp64 = 2.0 * mnk / 0.9e12;
-  const double tc = 15e-6 + mnk * 72.0 / 2.0e15 + static_cast<double>(M) * N * batch * 24.0 / 0.9e12 +
-                    static_cast<double>(M + N) * K * batch * 48.0 / 3.0e12;
+  if (K < 16) return false;
+  const double Mp = (M + 127) / 128 * 128.0, Np = (N + 31) / 32 * 32.0, Kp = (K + 31) / 32 * 32.0;
+  const double fp64 = 2.0 * M * N * static_cast<double>(K) * batch / 0.9e12;
+  const double digits = (Mp * (shared_a ? 1 : batch) + Np * (shared_b ? 1 : batch)) * Kp * 32.0 / 4.0e12;
+  const double tc = 15e-6 + Mp * Np * Kp * batch * 72.0 / 2.0e15 + Mp * Np * batch * 6.0 / 0.9e12 + digits;
   return tc < 0.8 * fp64;
 }
 template <class MA, class MB, class MC>
 bool tc_products(const Ctx& st, int batch, int M, int N, int K, double alpha, MA A, int64_t sA, MB B, int64_t sB,
                  double beta, MC C, int64_t sC, bool lower) {
-  const size_t one = tc::scratch_bytes(1, M, N, K);
-  int zc = one > 0 ? static_cast<int>(std::min<size_t>(static_cast<size_t>(batch), st.tc_cap / one)) : 0;
-  while (zc > 1 && tc::scratch_bytes(zc, M, N, K) > st.tc_cap) --zc;
+  auto bytes = [&](int z) { return tc::scratch_bytes(sA == 0 ? 1 : z, sB == 0 ? 1 : z, M, N, K); };
+  int zc = batch;
+  while (zc > 1 && bytes(zc) > st.tc_cap) zc = (zc + 1) / 2;
+  while (zc > 1 && bytes(zc) > st.tc_cap) --zc;
+  if (bytes(zc) > st.tc_cap) zc = 0;
   if (zc < 1) return false;
   for (int z0 = 0; z0 < batch; z0 += zc) {
     const int nz = std::min(zc, batch - z0);
     if (tc::gemm(st.s, st.tc, st.tc_cap, st.status, nz, M, N, K, alpha, shifted(A, z0 * sA), sA,
                  shifted(B, z0 * sB), sB, beta, shifted(C, z0 * sC), sC, lower) != cudaSuccess)
       return false;
-    for (int p = 0; p < 4 * std::max(1, (K + tc::KMAX - 1) / tc::KMAX); ++p) chd_launch::count_launch();
+    for (int p = 0; p < 3 * std::max(1, (K + tc::KMAX - 1) / tc::KMAX); ++p) chd_launch::count_launch();
   }
   return true;
 }
@@ -246,7 +249,7 @@ template <class MA, class MB, class MC>
 void gemm(const Ctx& st, int batch, int M, int N, int K, double alpha, MA A, int64_t sA, MB B, int64_t sB,
           double beta, MC C, int64_t sC, bool lower) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
-  if (tc_worth(st, batch, M, N, K) && tc_products(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower)) return;
+  if (tc_worth(st, batch, M, N, K, sA == 0, sB == 0) && tc_products(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower)) return;
   constexpr int64_t kFill = 2 * 152;
   if (N <= 8 && M > 64) gemm_cfg<128, 8, 4, 1>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
   else if (N <= 16 && M > 64) gemm_cfg<128, 16, 4, 2>(st, batch, M, N, K, alpha, A, sA, B, sB, beta, C, sC, lower);
@@ -445,29 +448,48 @@ void panel_solve(const Ctx& st, int batch, int R, MB B, int64_t sB, int p0, int 
 }
 
 
+// Two-level blocking: within an outer block of NBT (solves) or NBC
+// (Cholesky) columns the panels update only the block's own columns; the
+// columns beyond the block are updated once per block, by one product with
+// the block's width as inner dimension -- long enough for the tensor cores.
+constexpr int NBT = 256;  // outer block of the triangular solves (a multiple of TW)
+constexpr int NBC = 128;  // outer block of the Cholesky (a multiple of PP)
+
 // B := B L^{-T} (R x n view B, n x n lower L), blocked forward.
 template <class MB>
 void trsm_rLT(const Ctx& st, int batch, int R, int n, MB B, int64_t sB, const double* L, int64_t ld) {
   if (R <= 0 || n <= 0) return;
-  for (int p0 = 0; p0 < n; p0 += TW) {
-    const int pb = std::min(TW, n - p0);
-    panel_solve(st, batch, R, B, sB, p0, pb, L, ld, 1);
-    const int rest = n - p0 - pb;
+  for (int b0 = 0; b0 < n; b0 += NBT) {
+    const int bw = std::min(NBT, n - b0);
+    for (int p0 = b0; p0 < b0 + bw; p0 += TW) {
+      const int pb = std::min(TW, b0 + bw - p0);
+      panel_solve(st, batch, R, B, sB, p0, pb, L, ld, 1);
+      const int rest = b0 + bw - p0 - pb;
+      if (rest > 0)
+        gemm(st, batch, R, rest, pb, -1.0, colshift(B, p0), sB, DnT{L + (p0 + pb) + (int64_t)p0 * ld, ld}, 0,
+             1.0, colshift(B, p0 + pb), sB, false);
+    }
+    const int rest = n - b0 - bw;
     if (rest > 0)
-      gemm(st, batch, R, rest, pb, -1.0, colshift(B, p0), sB, DnT{L + (p0 + pb) + (int64_t)p0 * ld, ld}, 0,
-           1.0, colshift(B, p0 + pb), sB, false);
+      gemm(st, batch, R, rest, bw, -1.0, colshift(B, b0), sB, DnT{L + (b0 + bw) + (int64_t)b0 * ld, ld}, 0, 1.0,
+           colshift(B, b0 + bw), sB, false);
   }
 }
 // B := B L^{-1}, blocked backward.
 template <class MB>
 void trsm_rL(const Ctx& st, int batch, int R, int n, MB B, int64_t sB, const double* L, int64_t ld) {
   if (R <= 0 || n <= 0) return;
-  const int np = (n + TW - 1) / TW;
-  for (int p = np - 1; p >= 0; --p) {
-    const int p0 = p * TW, pb = std::min(TW, n - p0);
-    panel_solve(st, batch, R, B, sB, p0, pb, L, ld, 0);
-    if (p0 > 0)
-      gemm(st, batch, R, p0, pb, -1.0, colshift(B, p0), sB, Dn{const_cast<double*>(L) + p0, ld}, 0, 1.0,
+  for (int b0 = (n - 1) / NBT * NBT; b0 >= 0; b0 -= NBT) {
+    const int b1 = std::min(n, b0 + NBT);
+    for (int p0 = (b1 - 1 - b0) / TW * TW + b0; p0 >= b0; p0 -= TW) {
+      const int pb = std::min(TW, b1 - p0);
+      panel_solve(st, batch, R, B, sB, p0, pb, L, ld, 0);
+      if (p0 > b0)
+        gemm(st, batch, R, p0 - b0, pb, -1.0, colshift(B, p0), sB,
+             Dn{const_cast<double*>(L) + p0 + (int64_t)b0 * ld, ld}, 0, 1.0, colshift(B, b0), sB, false);
+    }
+    if (b0 > 0)
+      gemm(st, batch, R, b0, b1 - b0, -1.0, colshift(B, b0), sB, Dn{const_cast<double*>(L) + b0, ld}, 0, 1.0,
            colshift(B, 0), sB, false);
   }
 }
@@ -478,22 +500,33 @@ void trsm_rL(const Ctx& st, int batch, int R, int n, MB B, int64_t sB, const dou
 // a panel counter, else the diagonal block and the row solve separately.
 void potrf_partial(const Ctx& st, double* F, int64_t ld, int J, int n, int64_t* status, int64_t code,
                    int64_t snode, int64_t col0) {
-  for (int j0 = 0; j0 < n; j0 += PP) {
-    const int pb = std::min(PP, n - j0);
-    const int R = J - j0 - pb;
-    if (st.ctr) {
-      mk_potrf_panel<<<std::max(1, (R + PR - 1) / PR), PT, 0, st>>>(F, ld, j0, pb, R, st.ctr, status, code,
-                                                                      snode, col0);
-      chd_launch::count_launch();
-    } else {
-      mk_potrf_panel<<<1, PT, 0, st>>>(F, ld, j0, pb, 0, nullptr, status, code, snode, col0);
-      chd_launch::count_launch();
-      if (R > 0) panel_solve(st, 1, R, Dn{F + j0 + pb, ld}, 0, j0, pb, F, ld, 1);
+  for (int b0 = 0; b0 < n; b0 += NBC) {
+    const int bw = std::min(NBC, n - b0);
+    for (int j0 = b0; j0 < b0 + bw; j0 += PP) {
+      const int pb = std::min(PP, b0 + bw - j0);
+      const int R = J - j0 - pb;
+      if (st.ctr) {
+        mk_potrf_panel<<<std::max(1, (R + PR - 1) / PR), PT, 0, st>>>(F, ld, j0, pb, R, st.ctr, status, code,
+                                                                        snode, col0);
+        chd_launch::count_launch();
+      } else {
+        mk_potrf_panel<<<1, PT, 0, st>>>(F, ld, j0, pb, 0, nullptr, status, code, snode, col0);
+        chd_launch::count_launch();
+        if (R > 0) panel_solve(st, 1, R, Dn{F + j0 + pb, ld}, 0, j0, pb, F, ld, 1);
+      }
+      // update of the block's remaining columns (all rows below them)
+      const int rest = b0 + bw - j0 - pb;
+      if (rest > 0) {
+        double* P = F + (j0 + pb) + (int64_t)j0 * ld;
+        gemm(st, 1, R, rest, pb, -1.0, Dn{P, ld}, 0, DnT{P, ld}, 0, 1.0,
+             Dn{F + (j0 + pb) + (int64_t)(j0 + pb) * ld, ld}, 0, true);
+      }
     }
+    // trailing update beyond the block: F[b1:, b1:] -= P P^T, P = F[b1:, b0:b1]
+    const int b1 = b0 + bw, R = J - b1;
     if (R > 0) {
-      double* P = F + (j0 + pb) + (int64_t)j0 * ld;
-      gemm(st, 1, R, R, pb, -1.0, Dn{P, ld}, 0, DnT{P, ld}, 0, 1.0, Dn{F + (j0 + pb) + (int64_t)(j0 + pb) * ld, ld},
-           0, true);
+      double* P = F + b1 + (int64_t)b0 * ld;
+      gemm(st, 1, R, R, bw, -1.0, Dn{P, ld}, 0, DnT{P, ld}, 0, 1.0, Dn{F + b1 + (int64_t)b1 * ld, ld}, 0, true);
     }
   }
 }
@@ -814,13 +847,10 @@ void ihess_down_front(const chd_symbolic* s, const Ctx& st, int m, int k, const 
   gemm(st, m, n, n, n, 1.0, Dn{T1, J}, sw, SymL{D, n}, 0, 0.0, Dn{T2, J}, sw, false);
   gemm(st, m, n, n, n, 1.0, SymL{D, n}, 0, Dn{T2, J}, sw, 0.0, Csc{Yout + f.base, J, 0}, ldy, true);
   if (a > 0) {
-    // K_AN = V^{-1} (M_AN D) = R^{-T} R^{-1} (M_AN D) with R = chol(V) cached
-    // per factor: two blocked triangular solves on the transposed block
-    const double* R = Rd + s->v_off[k];
+    // K_AN = V^{-1} (M_AN D), V^{-1} formed once per factor
     gemm(st, m, a, n, n, 1.0, Dn{T1 + n, J}, sw, SymL{D, n}, 0, 0.0, Dn{T2 + n, J}, sw, false);
-    trsm_rLT(st, m, n, a, DnTW{T2 + n, J}, sw, R, a);
-    trsm_rL(st, m, n, a, DnTW{T2 + n, J}, sw, R, a);
-    CHD_EW(mk_front_to_csc, (int64_t)J * n, m, st, Yout + f.base, ldy, T2, sw, J, J, n, n, J, 1.0);
+    gemm(st, m, a, n, a, 1.0, SymL{Rd + s->v_off[k], a}, 0, Dn{T2 + n, J}, sw, 0.0, Csc{Yout + f.base, J, n}, ldy,
+         false);
   }
 }
 
@@ -1392,8 +1422,9 @@ void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const doub
   if (s->grp_of[k] >= 0) return;  // a leaf group reads S itself
   chd::big::complete_load_front(s, chd::big::make_ctx(st, nullptr, 0), k, Sin, ws);
 }
-// Cholesky factor R of the cached V_k = S_{A_k A_k} of one big front (lower,
-// into Rd), and the reversed upper factor of V_k (into Qd).
+// V_k^{-1} of the cached V_k = S_{A_k A_k} of one front (lower, into Rd),
+// and the reversed upper factor of V_k (into Qd), with the multi-CTA
+// kernels: for the dense tier and for other fronts with a large V_k.
 void big_inv_v(const chd_symbolic* s, const Slot& sl, int k, const double* Vd,
                double* Rd, double* Qd, double* ws, int64_t* status, int what) {
   using namespace chd;
@@ -1404,12 +1435,17 @@ void big_inv_v(const chd_symbolic* s, const Slot& sl, int k, const double* Vd,
   if (a == 0) return;
   (void)ws;
   if (what & 1) {
-    // R = chol(V): the inverse-Hessian calls apply V^{-1} = R^{-T} R^{-1} by
-    // two blocked triangular solves (forming V^{-1} costs 2a^3/3 more flops
-    // per factor, more than the solves of a call save)
+    // V^{-1} = W^T W with W = R^{-1}, R = chol(V): blocked Cholesky into the
+    // V^{-1} slot, W in the front's workspace, the product (a tensor-core
+    // product for large a) back into the slot.  Every inverse-Hessian call
+    // then applies V^{-1} with one product per front.
     double* R = Rd + s->v_off[k];
+    double* Wk = ws + s->f_off[k];  // a x a inside the front's J x J region
     CHD_EW(mk_copy, (int64_t)a * a, 1, st, R, 0, a, Vd + s->v_off[k], 0, a, a, a, 1.0, 0.0, 1, 0);
     potrf_partial(st, R, a, a, a, status, CHD_ERR_NOT_PD, k, -1);
+    CHD_EW(mk_identity, (int64_t)a * a, 1, st, Wk, a, a);
+    trsm_rLT(st, 1, a, a, DnTW{Wk, a}, 0, R, a);
+    gemm(st, 1, a, a, a, 1.0, TriLT{Wk, a}, 0, TriL{Wk, a}, 0, 0.0, Dn{R, a}, 0, true);
   }
   if (what & 2) {
     // the upper factor Q of V = Q Q^T (Hessian factor, §5.4), held as

@@ -152,6 +152,12 @@ struct Exec {
 // What one dense-tier front sequence runs with: its stream, the split-K
 // scratch slice (may be null), the tensor-core scratch (may be null), the
 // factor's status and the tensor-core mode of the analysis.
+// Fronts outside the dense tier whose ancestor set has at least this many
+// rows get V_k^{-1} from the multi-CTA kernels (blocked Cholesky, blocked
+// triangular inverse, tensor-core product) instead of one CTA: on one SM
+// the a^3 FP64 operations of a large V_k take milliseconds.
+constexpr int kInvVMulti = 96;
+
 struct Slot {
   cudaStream_t st = nullptr;
   double* xs = nullptr;

@@ -861,7 +861,7 @@ __global__ void __launch_bounds__(NT) k_inv_v(SymDev S, const double* Vd, double
   const int k = front_list[blockIdx.x];
   const int n = (int)(S.sn_ptr[k + 1] - S.sn_ptr[k]);
   const int a = (int)(S.rows_ptr[k + 1] - S.rows_ptr[k]) - n;
-  if (a == 0) return;
+  if (a == 0 || a >= kInvVMulti) return;  // large V_k: multi-CTA kernels (big_inv_v)
   double* R = Rd + S.v_off[k];
   double* Ri = ws + S.f_off[k];  // a x a scratch inside the front's J x J region
   const double* V = Vd + S.v_off[k];
@@ -1337,9 +1337,13 @@ void big_inv_v(const chd_symbolic* s, const Slot& sl, int k, const double* Vd,
                double* Rd, double* Qd, double* ws, int64_t* status, int what);
 void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* Qd,
            double* ws, int64_t* status, int what) {
+  // dense-tier fronts and the other fronts with a large V_k: multi-CTA
+  // kernels on the side streams; the rest: one CTA per front (k_inv_v)
   std::vector<int> bigs;
   for (int64_t k = 0; k < s->nsn; ++k)
     if (s->is_big[k]) bigs.push_back((int)k);
+  for (int32_t k : s->small_fronts)
+    if (front_J(s, k) - front_n(s, k) >= kInvVMulti) bigs.push_back((int)k);
   BigFork bf{ex, st};
   bf.run((int)bigs.size(), [&](int i, const Slot& sl) {
     big_inv_v(s, sl, bigs[i], Vd, Rd, Qd, ws, status, what);

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(128, 1) k_probe_mma(int reps, int* err) {
 }  // namespace chd
 
 namespace chd_launch {
-size_t tc_scratch_bytes(int batch, int M, int N, int K) { return chd::tc::scratch_bytes(batch, M, N, K); }
+size_t tc_scratch_bytes(int batch, int M, int N, int K) { return chd::tc::scratch_bytes(batch, batch, M, N, K); }
 }  // namespace chd_launch
 
 using namespace chd;

@@ -40,9 +40,10 @@
 // two stages); one thread issues the copies and the MMAs and signals
 // through mbarriers; tcgen05.commit releases a stage when its MMAs have
 // read it.  The epilogue reads the eight levels from TMEM (tcgen05.ld),
-// folds the small levels 5..7 in FP32, assembles levels 0..4 in FP64,
-// scales by the digit exponents and writes beta C + alpha AB through the
-// output view.  Every wait is bounded (about two seconds of the global
+// sums levels 0..3 exactly in an int64 and levels 4..7 in FP32, converts
+// once to FP64, scales by the digit exponents (an exponent add) and writes
+// beta C + alpha AB through the output view: one or two FP64 operations per
+// output instead of a dozen.  Every wait is bounded (about two seconds of the global
 // timer): on a timeout the kernel raises an error flag, waits (bounded) for
 // the copies it issued, frees its TMEM and returns.
 #pragma once
@@ -237,12 +238,14 @@ __global__ void __launch_bounds__(128) k_tc_amax(int M, int N, int K, int k0ff, 
   const int kb = blockIdx.y * SPLIT_K, ke = min(K, kb + SPLIT_K);
   double mx = 0.0;
   if ((int)blockIdx.x < ablocks) {
+    if (sA == 0 && z > 0) return;  // an operand shared by the batch is split once
     A.p += static_cast<int64_t>(z) * sA;
     const int r = blockIdx.x * 128 + threadIdx.x;
     if (r >= M) return;
     for (int k = kb; k < ke; ++k) mx = fmax(mx, fabs(A.at(r, k0ff + k)));
     if (mx > 0.0) atomicMax(amA + static_cast<int64_t>(z) * Mp + r, static_cast<unsigned long long>(__double_as_longlong(mx)));
   } else {
+    if (sB == 0 && z > 0) return;
     B.p += static_cast<int64_t>(z) * sB;
     const int c = (blockIdx.x - ablocks) * 128 + threadIdx.x;
     if (c >= N) return;
@@ -257,6 +260,7 @@ __global__ void __launch_bounds__(256) k_tc_digits(int M, int N, int K, int k0ff
                                                    int* exA, int* exB) {
   const int z = blockIdx.z;
   const bool isA = (int)blockIdx.x < ablocks;
+  if ((isA ? sA : sB) == 0 && z > 0) return;  // shared operand: split once
   const int r = (isA ? blockIdx.x : blockIdx.x - ablocks) * SPLIT_ROWS + (threadIdx.x & 31);
   const int k0 = blockIdx.y * SPLIT_K + 8 * (threadIdx.x >> 5);
   const int rows = isA ? Mp : Np, lim = isA ? M : N;
@@ -289,6 +293,14 @@ __global__ void __launch_bounds__(256) k_tc_digits(int M, int N, int K, int k0ff
 __device__ __forceinline__ double pow2(int e) {
   return (e > -1020 && e < 1020) ? __longlong_as_double(static_cast<int64_t>(e + 1023) << 52) : ldexp(1.0, e);
 }
+// v 2^e, exactly: an integer add to the exponent field when the result stays
+// normal, else an FP64 multiply
+__device__ __forceinline__ double times_pow2(double v, int e) {
+  const long long b = __double_as_longlong(v);
+  const int ex = static_cast<int>((b >> 52) & 0x7FF);
+  if (ex == 0 || ex + e <= 0 || ex + e >= 2047) return v * pow2(e);
+  return __longlong_as_double(b + (static_cast<long long>(e) << 52));
+}
 
 // ---------------------------------------------------------------------------
 // the product of the digit planes: one CTA per 128 x 32 tile of C and batch z
@@ -297,7 +309,7 @@ template <class MC>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int Kp,
               int Mp, int Np, const int* exA, const int* exB, double alpha, double beta, MC C, int64_t sC, int lower,
-              int tiles_n, int64_t* status) {
+              int tiles_n, int shA, int shB, int64_t* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   __shared__ __align__(8) uint64_t full[STAGES];
@@ -336,8 +348,8 @@ __global__ void __launch_bounds__(128, 1)
       const int st = c % STAGES;
       uint8_t* a = sm + st * (A_STAGE + B_STAGE);
       mbar_expect_tx(&full[st], A_STAGE + B_STAGE);
-      tma_load_3d(a, &mapA, &full[st], c * KC, tm, z * ND);
-      tma_load_3d(a + A_STAGE, &mapB, &full[st], c * KC, tn, z * ND);
+      tma_load_3d(a, &mapA, &full[st], c * KC, tm, (shA ? 0 : z) * ND);
+      tma_load_3d(a + A_STAGE, &mapB, &full[st], c * KC, tn, (shB ? 0 : z) * ND);
       ++loads;
     };
     bool ok = true;
@@ -389,7 +401,7 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   if (ready && !failed) {
     const int r = tm + warp * 32 + lane;
-    const int er = (r < Mp) ? exA[static_cast<int64_t>(z) * Mp + r] : 0;
+    const int er = (r < Mp) ? exA[static_cast<int64_t>(shA ? 0 : z) * Mp + r] : 0;
     const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
 #pragma unroll 1
     for (int g = 0; g < TN / 8; ++g) {
@@ -400,18 +412,24 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int cc = tn + g * 8 + j;
-        // levels 5..7 folded in FP32 onto level 4, levels 0..4 in FP64
+        // Levels 0..3 are exact integers (below 2^24 for K <= KMAX): their
+        // weighted sum I is exact in an int64 (|I| < 2^44), in units of
+        // 2^-21 of level 0.  Levels 4..7 fold in FP32 (their rounding is
+        // below 2^-50 of K max|a| max|b|) and join I with 11 fractional
+        // bits: the sum is X 2^-39, |X| < 2^62, converted once to FP64.
+        int64_t I = __float2int_rn(__uint_as_float(v[0][j]));
+#pragma unroll
+        for (int l = 1; l < 4; ++l) I = I * 128 + __float2int_rn(__uint_as_float(v[l][j]));
         float lo = __uint_as_float(v[7][j]);
         lo = fmaf(lo, 0.0078125f, __uint_as_float(v[6][j]));
         lo = fmaf(lo, 0.0078125f, __uint_as_float(v[5][j]));
         lo = fmaf(lo, 0.0078125f, __uint_as_float(v[4][j]));
-        double acc = static_cast<double>(lo);
-#pragma unroll
-        for (int l = 3; l >= 0; --l) acc = fma(acc, 0.0078125, static_cast<double>(__uint_as_float(v[l][j])));
+        const int64_t X = I * (int64_t(1) << 18) + __float2ll_rn(lo * 2048.0f);
         if (r < M && cc < N && (!lower || r >= cc)) {
-          const int ec = exB[static_cast<int64_t>(z) * Np + cc];
-          double out = alpha * (acc * pow2(er + ec - 14));
-          if (beta != 0.0) out = fma(beta, C.at(r, cc), out);
+          const int ec = exB[static_cast<int64_t>(shB ? 0 : z) * Np + cc];
+          double out = times_pow2(__ll2double_rn(X), er + ec - 53);
+          if (alpha != 1.0) out = alpha == -1.0 ? -out : alpha * out;
+          if (beta != 0.0) out = beta == 1.0 ? out + C.at(r, cc) : fma(beta, C.at(r, cc), out);
           C.at(r, cc) = out;
         }
       }
@@ -434,23 +452,26 @@ struct Layout {
   int Mp, Np, Kp;
   size_t offB, offEA, offEB, offMA, offMB, bytes;
 };
-inline Layout layout(int batch, int M, int N, int K) {
+// ba, bb: number of distinct A and B operands in the batch (1 when an
+// operand is shared by every product of the batch, else the batch size)
+inline Layout layout(int ba, int bb, int M, int N, int K) {
   Layout L;
   L.Mp = static_cast<int>(round_up(M, TM));
   L.Np = static_cast<int>(round_up(N, TN));
   L.Kp = static_cast<int>(round_up(K < KMAX ? K : KMAX, KC));
-  const size_t a = static_cast<size_t>(batch) * ND * L.Mp * L.Kp * 2;
-  const size_t b = static_cast<size_t>(batch) * ND * L.Np * L.Kp * 2;
+  const size_t a = static_cast<size_t>(ba) * ND * L.Mp * L.Kp * 2;
+  const size_t b = static_cast<size_t>(bb) * ND * L.Np * L.Kp * 2;
   L.offB = static_cast<size_t>(round_up(a, 256));
   L.offEA = L.offB + static_cast<size_t>(round_up(b, 256));
-  L.offEB = L.offEA + static_cast<size_t>(round_up(static_cast<int64_t>(batch) * L.Mp * 4, 256));
-  L.offMA = L.offEB + static_cast<size_t>(round_up(static_cast<int64_t>(batch) * L.Np * 4, 256));
-  L.offMB = L.offMA + static_cast<size_t>(round_up(static_cast<int64_t>(batch) * L.Mp * 8, 256));
-  L.bytes = L.offMB + static_cast<size_t>(round_up(static_cast<int64_t>(batch) * L.Np * 8, 256));
+  L.offEB = L.offEA + static_cast<size_t>(round_up(static_cast<int64_t>(ba) * L.Mp * 4, 256));
+  L.offMA = L.offEB + static_cast<size_t>(round_up(static_cast<int64_t>(bb) * L.Np * 4, 256));
+  L.offMB = L.offMA + static_cast<size_t>(round_up(static_cast<int64_t>(ba) * L.Mp * 8, 256));
+  L.bytes = L.offMB + static_cast<size_t>(round_up(static_cast<int64_t>(bb) * L.Np * 8, 256));
   return L;
 }
 // scratch bytes of one product (digit planes and exponents of one K piece)
-inline size_t scratch_bytes(int batch, int M, int N, int K) { return layout(batch, M, N, K).bytes; }
+inline size_t scratch_bytes(int batch, int M, int N, int K) { return layout(batch, batch, M, N, K).bytes; }
+inline size_t scratch_bytes(int ba, int bb, int M, int N, int K) { return layout(ba, bb, M, N, K).bytes; }
 
 // C = beta C + alpha A B (lower triangle of C only if `lower`) for `batch`
 // products at the given strides, with FP64-level accuracy on the tensor
@@ -461,7 +482,9 @@ template <class MA, class MB, class MC>
 cudaError_t gemm(cudaStream_t st, void* scratch, size_t scratch_cap, int64_t* status, int batch, int M, int N, int K,
                  double alpha, MA A, int64_t sA, MB B, int64_t sB, double beta, MC C, int64_t sC, bool lower) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
-  const Layout L = layout(batch, M, N, K);
+  const int shA = sA == 0 ? 1 : 0, shB = sB == 0 ? 1 : 0;
+  const int ba = shA ? 1 : batch, bb = shB ? 1 : batch;
+  const Layout L = layout(ba, bb, M, N, K);
   if (L.bytes > scratch_cap || batch * ND > 65535) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
@@ -477,8 +500,8 @@ cudaError_t gemm(cudaStream_t st, void* scratch, size_t scratch_cap, int64_t* st
   unsigned long long* mxA = reinterpret_cast<unsigned long long*>(base + L.offMA);
   unsigned long long* mxB = reinterpret_cast<unsigned long long*>(base + L.offMB);
   CUtensorMap mA, mB;
-  if (!make_plane_map(&mA, dA, L.Kp, L.Mp, static_cast<int64_t>(batch) * ND, TM) ||
-      !make_plane_map(&mB, dB, L.Kp, L.Np, static_cast<int64_t>(batch) * ND, TN))
+  if (!make_plane_map(&mA, dA, L.Kp, L.Mp, static_cast<int64_t>(ba) * ND, TM) ||
+      !make_plane_map(&mB, dB, L.Kp, L.Np, static_cast<int64_t>(bb) * ND, TN))
     return cudaErrorInvalidValue;
   const int tiles_m = L.Mp / TM, tiles_n = L.Np / TN;
   for (int k0 = 0; k0 < K || k0 == 0; k0 += KMAX) {
@@ -492,7 +515,8 @@ cudaError_t gemm(cudaStream_t st, void* scratch, size_t scratch_cap, int64_t* st
     k_tc_digits<MA, MB><<<dim3(dm + dn, L.Kp / SPLIT_K + (L.Kp % SPLIT_K ? 1 : 0), batch), 256, 0, st>>>(
         M, N, kk, k0, L.Mp, L.Np, L.Kp, dm, A, sA, B, sB, mxA, mxB, dA, dB, eA, eB);
     k_tc_gemm<MC><<<dim3(tiles_m * tiles_n, 1, batch), 128, SMEM_BYTES, st>>>(
-        mA, mB, M, N, L.Kp, L.Mp, L.Np, eA, eB, alpha, k0 == 0 ? beta : 1.0, C, sC, lower ? 1 : 0, tiles_n, status);
+        mA, mB, M, N, L.Kp, L.Mp, L.Np, eA, eB, alpha, k0 == 0 ? beta : 1.0, C, sC, lower ? 1 : 0, tiles_n, shA, shB,
+        status);
     if (K <= 0) break;
   }
   return cudaGetLastError();

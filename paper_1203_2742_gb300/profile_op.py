@@ -16,7 +16,8 @@ operations (default: 1, 8, 64, 8, 1 for the workloads above).
 Every operation runs twice as warm-up (the second round captures the CUDA
 graphs of the launch sequences); then the chosen ones run once more inside
 an NVTX range named "timed", so that a profiler can restrict its capture to
-them (``ncu --nvtx --nvtx-include "timed/"``).  --no-graphs launches every
+them (``ncu --nvtx --nvtx-include "timed/"``), each inside a nested range
+named after the operation (``--nvtx-include "timed/hessian/"``).  --no-graphs launches every
 kernel directly.
 """
 from __future__ import annotations
@@ -122,10 +123,12 @@ def main(argv=None):
     for name in (ops if a.op == "all" else [a.op]):
         l0 = B.chd_kernel_launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(name)  # "timed/<op>" for a profiler's per-operation filter
         e0.record()
         ops[name]()
         e1.record()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         times[name] = (round(e0.elapsed_time(e1), 4), B.chd_kernel_launches() - l0)
     torch.cuda.nvtx.range_pop()
     print(f"{a.workload} {a.op} m={m}: n={n} nnz={sym.nnz} supernodes={sym.nsuper}")
