@@ -44,6 +44,22 @@ UNIT = "evals/s"
 TOL_PARITY = 1e-10
 # FP64 roofline of the front arithmetic: 152 SMs x 2.07 GHz x 2 FMA per clock per SM
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+def measured_peaks():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def bf16_peak_tflops():
+    """Dense bf16 tensor rate for a call timed alone: the measured burst
+    figure of MEASURED_PEAKS.json, else the fallback of an earlier GB300
+    measurement."""
+    v = measured_peaks().get("bf16_tflops")
+    return (float(v), "measured (cuBLAS bf16 GEMM, burst)") if v else (1900.0, "fallback")
+
+
 # measured HBM copy bandwidth of this pool's GB300s (driver-written file), else
 # the fallback figure of an earlier measurement
 def hbm_peak_gbs():
@@ -57,7 +73,7 @@ def hbm_peak_gbs():
 # DRAM bytes (read + write) of one Hessian call, summed over the call's
 # launches in one ncu capture of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum); absent where there is none.
-TRAFFIC_PER_HESSIAN_CALL = {"er5000": 6.377e9}
+TRAFFIC_PER_HESSIAN_CALL = {}
 
 
 def make_workload(name):
@@ -364,13 +380,14 @@ def make_symbolic(B, wl, **cfg):
 
 
 def tuned_config(B, wl):
-    """Tier cutovers chosen by the autotuner (Hessian with the workload's m):
-    on every 8th instance of a batch, else on the pattern itself."""
+    """Tier cutovers chosen by the autotuner on the benchmark step itself
+    (every operation with the workload's m): on every 8th instance of a
+    batch, else on the pattern itself."""
     from paper_1203_2742_gb300 import autotune
     if "batch" in wl:
         subset = list(range(0, len(wl["batch"]), 8))
-        return autotune.tune(lambda **c: make_symbolic(B, wl, subset=subset, **c), wl["m"], reps=1)
-    return autotune.tune(lambda **c: make_symbolic(B, wl, **c), wl["m"], reps=2)
+        return autotune.tune(lambda **c: make_symbolic(B, wl, subset=subset, **c), wl["m"], op="step", reps=1)
+    return autotune.tune(lambda **c: make_symbolic(B, wl, **c), wl["m"], op="step", reps=2)
 
 
 # ---------------------------------------------------------------------------
@@ -405,12 +422,15 @@ def job_value(world, evals_per_step, steps, max_ms):
 def accuracy_record(n, cp, ri, keep, ys, s, g, t, yi, logdet, fstar, xhat, x):
     """Errors of the GPU outputs of the last end-to-end step against the FP64
     oracle, on the CPU-baseline sample: the Hessian of the sampled Y's and
-    the gradient against the dense X^{-1} of the timed sample, log det
-    against the dense Cholesky factor, the inverse Hessian of the sampled
-    T = H(Y) against the oracle's clique-sum H^{-1} and, for every Y, the
-    round trip H^{-1}(H(Y)) = Y, and the completion by the residual of its
-    defining equation P(X-hat^{-1}) = S (Eq. (e-Xhat-eq)) with f_* =
-    log det X-hat - n.  Relative Frobenius errors in the symmetric norm."""
+    the gradient against the dense X^{-1} of the timed sample; log det
+    against the dense Cholesky factor; the inverse Hessian of the sampled
+    T = H(Y) against the oracle's clique-sum H^{-1}, and the round trip
+    H^{-1}(H(Y)) = Y for every Y; the completion X-hat against the oracle's
+    (the clique-sum closed form refined by Newton steps until Eq.
+    (e-Xhat-eq) holds to rounding), and f_* against log det X-hat - n.
+    Relative Frobenius errors in the symmetric norm.  The residual of
+    P(X-hat^{-1}) = S is reported too but not gated: it amplifies the error
+    of X-hat by about cond(X-hat)."""
     from oracle import dense as OD
     from oracle import symbolic as OS
     err = lambda a, b: float(OD.rel_err(n, cp, ri, a, b))
@@ -429,11 +449,12 @@ def accuracy_record(n, cp, ri, keep, ys, s, g, t, yi, logdet, fstar, xhat, x):
         "inv_hessian": max(err(yi[i], OD.inv_hessian_cliquesum(n, cp, ri, x, t[i], cl, seps, S=Z))
                            for i in range(k)),
         "inv_hessian_roundtrip": max(err(yi[i], ys[i]) for i in range(len(ys))),
-        "completion_residual": err(OD.project(n, cp, ri, np.linalg.inv(Xh)), s),
+        "completion": err(xhat, OD.completion_refined(n, cp, ri, s, cl, seps)),
         "fstar": abs(fstar - (ld_xh - n)) / max(1.0, abs(fstar)),
         "sample": f"Hessian and inverse Hessian of {k} of the {len(ys)} right-hand sides; round trip of all",
     }
     rec["pass"] = all(v <= TOL_PARITY for key, v in rec.items() if key not in ("tolerance", "sample"))
+    rec["completion_residual"] = err(OD.project(n, cp, ri, np.linalg.inv(Xh)), s)
     return rec
 
 
@@ -461,7 +482,7 @@ def run_ours(args, wl, rank, world, local_rank):
     if not args.no_tune:
         cfg, timings = tuned_config(B, wl)
         tune = {"chosen": cfg, "timings_ms": timings,
-                "on": ("every 8th instance" if "batch" in wl else "the pattern") + ", Hessian with the same m"}
+                "on": ("every 8th instance" if "batch" in wl else "the pattern") + ", the whole step with the same m"}
     t0 = time.perf_counter()
     sym = make_symbolic(B, wl, **cfg)
     analyze_ms = (time.perf_counter() - t0) * 1e3
@@ -548,6 +569,17 @@ def run_ours(args, wl, rank, world, local_rank):
     hess_flops = fl["hessian"] * m
     achieved = hess_flops / (ops_ms["hessian"] * 1e-3) / 1e12
     executed = fl_exec["hessian"] * m
+    # bf16 tensor-core flops of one Hessian call, counted on a direct run (the
+    # library counts the MMAs of the products it issues; graph replays are not
+    # counted), and the tensor side of the roofline
+    fac.set_graphs(False)
+    tc0 = B.chd_tc_flops()
+    fac.hessian(Y, out=T)
+    torch.cuda.synchronize()
+    tc_per_call = B.chd_tc_flops() - tc0
+    fac.set_graphs(True)
+    bf16_peak, bf16_src = bf16_peak_tflops()
+    tc_achieved = tc_per_call / (ops_ms["hessian"] * 1e-3) / 1e12
     step_flops = fl["factor"] + fl["gradient"] + m * (fl["hessian"] + fl["inv_hessian"]) + fl["completion"]
 
     # ---- batched vs one instance at a time (the plain GPU path) ----
@@ -638,17 +670,24 @@ def run_ours(args, wl, rank, world, local_rank):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MB write)"},
             "supernodes": sym.nsuper,
-            "roofline": {"bound": "alu",
-                         "kernel": "one Hessian call (all its launches; the dense-tier FP64 products carry the flops)",
-                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_HESSIAN_CALL.get(wl["name"]),
-                         "flops_per_call": hess_flops,
-                         "flops_source": "sum over the fronts of the relaxed Algorithm 6.1 partition (unsplit) of "
-                                         "6a^2n + 8an^2 + 2n^3 per right-hand side, times m",
-                         "executed_flops_per_call": executed,
-                         "peak_source": "FP64 FMA rate from unit counts and clock: 152 SMs x 2070 MHz x 4 flop/clk",
-                         "peak_probe": fp64_peak, "frac_of_probe": achieved / fp64_peak,
-                         "probe_source": "FP64 DFMA loop on all SMs (chd_probe_fp64_peak), same run"},
+            "roofline": {"bound": "tensor",
+                         "kernel": "one Hessian call (all its launches; its large products run on the tensor cores "
+                                   "as FP64-accurate bf16 digit products)",
+                         "achieved": tc_achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                         "frac": tc_achieved / bf16_peak, "traffic": TRAFFIC_PER_HESSIAN_CALL.get(wl["name"]),
+                         "peak_source": bf16_src,
+                         "tc_flops_per_call": tc_per_call,
+                         "tc_flops_source": "bf16 MMA flops the call's tensor-core products execute "
+                                            "(36 digit pairs per output tile), counted by the library",
+                         "fp64_equivalent": {
+                             "achieved": achieved, "unit": "TFLOP/s", "flops_per_call": hess_flops,
+                             "flops_source": "sum over the fronts of the relaxed Algorithm 6.1 partition (unsplit) "
+                                             "of 6a^2n + 8an^2 + 2n^3 per right-hand side, times m",
+                             "executed_flops_per_call": executed,
+                             "fp64_peak": FP64_PEAK_TFLOPS, "frac_of_fp64_peak": achieved / FP64_PEAK_TFLOPS,
+                             "fp64_peak_source": "FP64 FMA rate from unit counts and clock: 152 SMs x 2070 MHz x "
+                                                 "4 flop/clk",
+                             "fp64_probe": fp64_peak, "frac_of_fp64_probe": achieved / fp64_peak}},
             "cpu_baseline": cpu,
             "accuracy": accuracy,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -665,7 +704,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "instances": count,
             "autotune": tune,
             "batched_vs_one_at_a_time": sequential,
-            "step_tflops_fp64": step_flops / (ms_per_step * 1e-3) / 1e12,
+            "step_tflops_fp64_equivalent": step_flops / (ms_per_step * 1e-3) / 1e12,
             "analyze_ms": analyze_ms,
             "wall_s": wall,
             "logdet": results.get("logdet"), "fstar": results.get("fstar"),

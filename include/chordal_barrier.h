@@ -351,6 +351,14 @@ int64_t chd_kernel_launches(void);
    to check that a workload reaches the split path. */
 int64_t chd_split_k_launches(void);
 
+/* Measurement utility (not an operation of the paper): bf16 tensor-core
+   flops issued by the library's FP64-accurate digit products (chd_dgemm_tc
+   excluded) since the process started, counting every MMA the product
+   kernels execute (36 digit pairs of each computed 128 x 32 output tile).
+   Host counter of directly issued products; replays of captured CUDA graphs
+   do not add to it. */
+double chd_tc_flops(void);
+
 /*
  * Measurement utility (not an operation of the paper): FP64 fused
  * multiply-add throughput of the current device in GFLOP/s, from a kernel

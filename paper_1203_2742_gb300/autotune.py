@@ -29,6 +29,8 @@ DEFAULT_CANDIDATES = (
     dict(big_rows=512, big_cols=256, split_cols=256),
     dict(big_rows=320, big_cols=160, split_cols=128),
     dict(big_rows=320, big_cols=160, split_cols=512),
+    dict(big_rows=128, big_cols=64, split_cols=512),
+    dict(big_rows=192, big_cols=96, split_cols=512),
 )
 
 
@@ -44,7 +46,7 @@ def signature(sym, m):
     return f"n{_bucket(sym.n)}-z{_bucket(sym.nnz)}-J{_bucket(maxJ)}-m{_bucket(m)}"
 
 
-def _time_config(make_symbolic, config, x_of, y_of, m, op, reps):
+def _time_config(make_symbolic, config, x_of, y_of, s_of, m, op, reps):
     import torch
     sym = make_symbolic(**config)
     x = x_of(sym)
@@ -52,10 +54,25 @@ def _time_config(make_symbolic, config, x_of, y_of, m, op, reps):
     fac = sym.factor(x)
     fac.gradient()
     out = torch.empty_like(ys)
+    out2 = torch.empty_like(ys)
+    comp = None
+    if op == "step":
+        s = s_of(sym)
+        comp, _ = sym.complete(s)
+
+    def step():
+        # one pass of every operation: refactor, gradient, Hessian, inverse
+        # Hessian (with its per-factor V^{-1}) and completion
+        fac.refactor(x)
+        fac.gradient()
+        fac.hessian(ys, out=out)
+        fac.inv_hessian(out, out=out2)
+        comp.recomplete(s, want_fstar=False)
     call = {"hessian": lambda: fac.hessian(ys, out=out),
             "inv_hessian": lambda: fac.inv_hessian(ys, out=out),
             "factor": lambda: fac.refactor(x),
-            "gradient": lambda: fac.gradient()}[op]
+            "gradient": lambda: fac.gradient(),
+            "step": step}[op]
     call()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -66,6 +83,8 @@ def _time_config(make_symbolic, config, x_of, y_of, m, op, reps):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     fac.free()
+    if comp is not None:
+        comp.free()
     return ms
 
 
@@ -73,8 +92,12 @@ def tune(make_symbolic, m, candidates=DEFAULT_CANDIDATES, op="hessian", reps=2, 
     """Time every candidate setting; returns (best_config, {config_key: ms}).
 
     make_symbolic(**config) must return an analysed ``Symbolic`` for the
-    pattern with the given tier settings.  Values: X diagonally dominant and
-    m right-hand sides uniform in [-1, 1] on the analysed pattern (seeded).
+    pattern with the given tier settings.  Values: X diagonally dominant, m
+    right-hand sides uniform in [-1, 1] and S = P(G G^T + 0.5 I) (G n x 10)
+    on the analysed pattern (seeded).  op: "hessian", "inv_hessian",
+    "factor", "gradient", or "step" (every operation once, the inverse
+    Hessian on the Hessian's output after a refactor, as a benchmark step
+    runs them).
     """
     import torch
     import workloads as W
@@ -87,10 +110,15 @@ def tune(make_symbolic, m, candidates=DEFAULT_CANDIDATES, op="hessian", reps=2, 
         rng = np.random.default_rng(seed + 1)
         return torch.as_tensor(W.uniform_sym(sym.n, sym.colptr, sym.rowind, rng, count=m), device="cuda")
 
+    def s_of(sym):
+        rng = np.random.default_rng(seed + 2)
+        G = rng.standard_normal((sym.n, 10))
+        return torch.as_tensor(W.projected_gram(sym.n, sym.colptr, sym.rowind, G, 0.5), device="cuda")
+
     timings = {}
     best, best_ms = None, float("inf")
     for cfg in candidates:
-        ms = _time_config(make_symbolic, cfg, x_of, y_of, m, op, reps)
+        ms = _time_config(make_symbolic, cfg, x_of, y_of, s_of, m, op, reps)
         timings[json.dumps(cfg, sort_keys=True)] = ms
         if ms < best_ms:
             best, best_ms = dict(cfg), ms

@@ -73,6 +73,8 @@ _lib.chd_kernel_launches.argtypes = []
 _lib.chd_kernel_launches.restype = _i64
 _lib.chd_split_k_launches.argtypes = []
 _lib.chd_split_k_launches.restype = _i64
+_lib.chd_tc_flops.argtypes = []
+_lib.chd_tc_flops.restype = C.c_double
 _lib.chd_dgemm_tc.argtypes = [_i64, _i64, _i64, C.c_double, C.c_void_p, _i64, C.c_void_p, _i64, C.c_double,
                               C.c_void_p, _i64, C.c_void_p]
 _lib.chd_dgemm_tc.restype = C.c_int
@@ -390,6 +392,10 @@ def chd_kernel_launches():
 
 def chd_split_k_launches():
     return int(_lib.chd_split_k_launches())
+
+
+def chd_tc_flops():
+    return float(_lib.chd_tc_flops())
 
 
 def chd_dgemm_tc(a, b, c=None, alpha=1.0, beta=0.0, stream=None):

@@ -19,6 +19,7 @@
 namespace chd_launch {
 void count_launch();
 void count_split_k();
+void count_tc_flops(double f);
 }
 
 namespace chd {
@@ -241,6 +242,7 @@ bool tc_products(const Ctx& st, int batch, int M, int N, int K, double alpha, MA
                  shifted(B, z0 * sB), sB, beta, shifted(C, z0 * sC), sC, lower) != cudaSuccess)
       return false;
     for (int p = 0; p < 3 * std::max(1, (K + tc::KMAX - 1) / tc::KMAX); ++p) chd_launch::count_launch();
+    chd_launch::count_tc_flops(static_cast<double>(nz) * tc::mma_flops(M, N, K, lower));
   }
   return true;
 }

@@ -14,6 +14,7 @@
 namespace chd_launch {
 int64_t launches();
 int64_t split_k_launches();
+double tc_flops();
 size_t tc_scratch_bytes(int batch, int M, int N, int K);
 void add_launches(int64_t d);
 void factor(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* X, double* Lc,
@@ -823,6 +824,7 @@ chd_status chd_error_detail(chd_factor* f, int64_t* supernode, int64_t* column) 
 
 int64_t chd_kernel_launches(void) { return chd_launch::launches(); }
 int64_t chd_split_k_launches(void) { return chd_launch::split_k_launches(); }
+double chd_tc_flops(void) { return chd_launch::tc_flops(); }
 
 chd_status chd_factor_set_workspace_limit(chd_factor* f, size_t bytes) {
   if (!f) return CHD_ERR_INVALID;

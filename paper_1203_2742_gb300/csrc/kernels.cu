@@ -990,7 +990,10 @@ using namespace chd;
 
 static int64_t g_launches = 0;
 static int64_t g_split_k = 0;
+static double g_tc_flops = 0.0;
 int64_t launches() { return g_launches; }
+double tc_flops() { return g_tc_flops; }
+void count_tc_flops(double f) { g_tc_flops += f; }
 void count_launch() { ++g_launches; }
 int64_t split_k_launches() { return g_split_k; }
 void count_split_k() { ++g_split_k; }

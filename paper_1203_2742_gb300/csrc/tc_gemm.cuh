@@ -469,6 +469,21 @@ inline Layout layout(int ba, int bb, int M, int N, int K) {
   L.bytes = L.offMB + static_cast<size_t>(round_up(static_cast<int64_t>(bb) * L.Np * 8, 256));
   return L;
 }
+// bf16 tensor-core flops one product executes: per computed 128 x 32 tile
+// and 16-wide K step, eight MMAs of N = 256, 224, .., 32 (36 digit pairs)
+inline double mma_flops(int M, int N, int K, bool lower) {
+  const int64_t tm = round_up(M, TM) / TM, tn = round_up(N, TN) / TN;
+  int64_t tiles = 0;
+  for (int64_t i = 0; i < tm; ++i)
+    for (int64_t j = 0; j < tn; ++j)
+      if (!lower || j * TN < (i + 1) * TM) ++tiles;
+  int64_t kp = 0;
+  for (int k0 = 0; k0 < K || k0 == 0; k0 += KMAX) {
+    kp += round_up((K - k0 < KMAX ? K - k0 : KMAX) > 0 ? (K - k0 < KMAX ? K - k0 : KMAX) : 1, KC);
+    if (K <= 0) break;
+  }
+  return static_cast<double>(tiles) * kp * 2.0 * TM * TN * 36;
+}
 // scratch bytes of one product (digit planes and exponents of one K piece)
 inline size_t scratch_bytes(int batch, int M, int N, int K) { return layout(batch, batch, M, N, K).bytes; }
 inline size_t scratch_bytes(int ba, int bb, int M, int N, int K) { return layout(ba, bb, M, N, K).bytes; }
