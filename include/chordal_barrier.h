@@ -79,12 +79,12 @@ typedef struct {
   int32_t split_cols;      /* supernodes wider than 1.5 x split_cols columns are split into a
                               chain of supernodes of split_cols columns (V unchanged);
                               0 = default 256, negative = never split */
-  int32_t chain_runs;      /* nonzero: runs of at least 8 one-column fronts with contiguous
-                              rows and the same |A_k| <= 64 (band chains) get their own
-                              chain-tier kernels for the factor, the gradient and the
-                              passes of the Hessian, the Hessian factor and the inverse
+  int32_t chain_runs;      /* nonzero (chd_opts_default): runs of at least 8 one-column fronts
+                              with contiguous rows and the same |A_k| <= 64 (band chains) get
+                              their own chain-tier kernels for the factor, the gradient and
+                              the passes of the Hessian, the Hessian factor and the inverse
                               Hessian (the Cholesky product runs them in the warp tier);
-                              0 (default): off */
+                              0: off */
   int32_t tc_products;     /* dense-tier products on the tensor cores (FP64-accurate digit
                               products, see chd_dgemm_tc): 0 (default) = products of at
                               least 64 x 64 outputs with inner dimension >= 32 and
@@ -94,7 +94,7 @@ typedef struct {
 } chd_opts;
 
 /* Fill `opts` with the defaults: natural order, relax 0, tie_last 1, default
-   dense-tier thresholds. */
+   dense-tier thresholds, chain runs on, tensor-core products by cost. */
 void chd_opts_default(chd_opts* opts);
 
 /*
@@ -392,6 +392,17 @@ chd_status chd_dgemm_tc(int64_t m, int64_t n, int64_t k, double alpha, const dou
  * denominator of the tensor-core roofline of chd_dgemm_tc.
  */
 chd_status chd_probe_tc_bf16_peak(void* stream, double* tflops);
+
+/*
+ * Measurement utility (not an operation of the paper): the arithmetic units
+ * the front kernels can use, on every SM of the current device, timed with
+ * CUDA events on `stream` (synchronises).  out[0]: FP64 FMA throughput
+ * (TFLOP/s, eight independent chains per thread); out[1]: FP64 warp-level
+ * MMA (mma.sync m8n8k4 .f64, TFLOP/s); out[2]: FP32 FMA throughput
+ * (TFLOP/s); out[3]: latency of a dependent FP64 FMA (ns).  Allocates and
+ * frees one small device buffer (stream-ordered).
+ */
+chd_status chd_probe_units(void* stream, double out[4]);
 
 void chd_factor_free(chd_factor* fac);
 

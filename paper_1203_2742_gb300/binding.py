@@ -80,6 +80,8 @@ _lib.chd_dgemm_tc.argtypes = [_i64, _i64, _i64, C.c_double, C.c_void_p, _i64, C.
 _lib.chd_dgemm_tc.restype = C.c_int
 _lib.chd_probe_tc_bf16_peak.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
 _lib.chd_probe_tc_bf16_peak.restype = C.c_int
+_lib.chd_probe_units.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
+_lib.chd_probe_units.restype = C.c_int
 _lib.chd_hessian_noalloc.argtypes = [_p, C.c_int, _p, _i64, _p, _i64, _p]
 _lib.chd_hessian_noalloc.restype = C.c_int
 _lib.chd_probe_fp64_peak.argtypes = [_p, C.POINTER(C.c_double)]
@@ -146,7 +148,7 @@ def _dptr(t, what, nnz=None, rows=None):
 # ---------------------------------------------------------------------------
 
 def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0,
-                big_cols=0, split_cols=0, chain_runs=False, tc_products=0):
+                big_cols=0, split_cols=0, chain_runs=True, tc_products=0):
     colptr = np.ascontiguousarray(colptr, dtype=np.int64)
     rowind = np.ascontiguousarray(rowind, dtype=np.int32)
     o = chd_opts()
@@ -171,7 +173,7 @@ def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_l
 
 
 def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big_cols=0, split_cols=0,
-          chain_runs=False, tc_products=0):
+          chain_runs=True, tc_products=0):
     o = chd_opts()
     _lib.chd_opts_default(C.byref(o))
     o.ordering = ORDERINGS[ordering]
@@ -418,6 +420,13 @@ def chd_dgemm_tc(a, b, c=None, alpha=1.0, beta=0.0, stream=None):
     return c
 
 
+def chd_probe_units(stream=None):
+    """dict: fp64_fma_tflops, fp64_mma_tflops, fp32_fma_tflops, fp64_fma_latency_ns."""
+    v = (C.c_double * 4)()
+    _check(_lib.chd_probe_units(_stream_ptr(stream), v), "chd_probe_units")
+    return {"fp64_fma_tflops": v[0], "fp64_mma_tflops": v[1], "fp32_fma_tflops": v[2], "fp64_fma_latency_ns": v[3]}
+
+
 def chd_probe_tc_bf16_peak(stream=None):
     v = C.c_double()
     _check(_lib.chd_probe_tc_bf16_peak(_stream_ptr(stream), C.byref(v)), "chd_probe_tc_bf16_peak")
@@ -442,7 +451,7 @@ class Symbolic:
     """Owner of a ``chd_symbolic``: the analysed pattern and its clique tree."""
 
     def __init__(self, n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True,
-                 big_rows=0, big_cols=0, split_cols=0, chain_runs=False, tc_products=0):
+                 big_rows=0, big_cols=0, split_cols=0, chain_runs=True, tc_products=0):
         self._h = chd_analyze(n, colptr, rowind, ordering=ordering, perm=perm, relax=relax,
                               tie_last=tie_last, big_rows=big_rows, big_cols=big_cols,
                               split_cols=split_cols, chain_runs=chain_runs, tc_products=tc_products)

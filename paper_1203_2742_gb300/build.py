@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libchordal_barrier.so")
 SOURCES = ["symbolic.cpp", "capi.cpp", "kernels.cu", "bigfront.cu", "warp_tier.cu", "chain_tier.cu", "noalloc.cu",
-           "tc_gemm.cu"]
+           "tc_gemm.cu", "probe_units.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

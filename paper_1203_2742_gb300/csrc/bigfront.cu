@@ -218,9 +218,9 @@ inline double balance(int64_t units) {
 // below 0.8 of the FP64-unit time of the product (2 M N K flops at about
 // 0.9 TFLOP/s).
 inline bool tc_worth(const Ctx& st, int batch, int M, int N, int K, bool shared_a, bool shared_b) {
-  if (!st.tc || st.tc_mode < 0 || M < 64 || N < 16 || K < 1) return false;
-  if (st.tc_mode > 0) return true;
-  if (K < 16) return false;
+  if (!st.tc || st.tc_mode < 0 || K < 1) return false;
+  if (st.tc_mode > 0) return M >= 64 && N >= 16;
+  if (M < 16 || K < 16) return false;
   const double Mp = (M + 127) / 128 * 128.0, Np = (N + 31) / 32 * 32.0, Kp = (K + 31) / 32 * 32.0;
   const double fp64 = 2.0 * M * N * static_cast<double>(K) * batch / 0.9e12;
   const double digits = (Mp * (shared_a ? 1 : batch) + Np * (shared_b ? 1 : batch)) * Kp * 32.0 / 4.0e12;

@@ -250,6 +250,7 @@ void chd_opts_default(chd_opts* o) {
   o->user_perm = nullptr;
   o->relax = 0;
   o->tie_last = 1;
+  o->chain_runs = 1;
 }
 
 chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* rowind,

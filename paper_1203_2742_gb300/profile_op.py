@@ -71,8 +71,8 @@ def main(argv=None):
     ap.add_argument("--big-rows", type=int, default=0, help="dense-tier cutover |J| (0: library default)")
     ap.add_argument("--big-cols", type=int, default=0, help="dense-tier cutover |N| (0: library default)")
     ap.add_argument("--split-cols", type=int, default=0, help="supernode split width (0: library default)")
-    ap.add_argument("--chain-runs", type=int, nargs="?", const=1, default=0,
-                    help="chain tier for runs of one-column band fronts")
+    ap.add_argument("--chain-runs", type=int, default=1, choices=(0, 1),
+                    help="chain tier for runs of one-column band fronts (library default: 1)")
     a = ap.parse_args(argv)
     m = a.m if a.m is not None else DEFAULT_M[a.workload]
     sym = symbolic_for(a.workload, big_rows=a.big_rows, big_cols=a.big_cols, split_cols=a.split_cols,

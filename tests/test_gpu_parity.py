@@ -337,7 +337,7 @@ def test_chain_runs(name):
     pattern = CHAIN_CASES[name]()
     rng = np.random.default_rng(41)
     on = B.Symbolic(*pattern, chain_runs=True)
-    off = B.Symbolic(*pattern)
+    off = B.Symbolic(*pattern, chain_runs=False)
     assert np.array_equal(on.colptr, off.colptr) and np.array_equal(on.rowind, off.rowind)
     n, cp, ri = on.n, on.colptr, on.rowind
     x = W.diag_dominant(n, cp, ri, rng)
@@ -380,7 +380,7 @@ def test_chain_runs_inverse_hessian(name):
     pattern = CHAIN_CASES[name]()
     rng = np.random.default_rng(43)
     on = B.Symbolic(*pattern, chain_runs=True)
-    off = B.Symbolic(*pattern)
+    off = B.Symbolic(*pattern, chain_runs=False)
     n, cp, ri = on.n, on.colptr, on.rowind
     x = W.diag_dominant(n, cp, ri, rng)
     ts = W.uniform_sym(n, cp, ri, rng, count=3)
