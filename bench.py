@@ -73,7 +73,7 @@ def hbm_peak_gbs():
 # DRAM bytes (read + write) of one Hessian call, summed over the call's
 # launches in one ncu capture of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum); absent where there is none.
-TRAFFIC_PER_HESSIAN_CALL = {}
+TRAFFIC_PER_HESSIAN_CALL = {"er5000": 9.716e9}
 
 
 def make_workload(name):
@@ -118,7 +118,7 @@ def make_workload(name):
     if name == "grid150":
         return dict(name=name, pattern=W.grid2d(150, 150),
                     opts=dict(perm=W.nested_dissection((150, 150), leaf=8)), m=64, seed=2,
-                    gram=(20, 0.5),
+                    gram=(20, 0.5), small=(W.grid2d(60, 60), W.nested_dissection((60, 60), leaf=8)),
                     desc="5-point grid 150x150 (n=22500), geometric nested dissection, "
                          "X diag-dominant, 64 Y, S=P(GG^T+0.5I) G 22500x20")
     raise SystemExit(f"unknown workload {name}")
@@ -369,6 +369,23 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def scaled_cpu_baseline(wl, n, cores, budget_s=10.0):
+    """Dense oracle timed on a smaller instance of the same recipe (the
+    workload's "small" pattern, analysed by the oracle alone), extrapolated
+    to the full pattern by the dense oracle's n^3 cost: for patterns whose
+    dense X^{-1} does not fit a bounded sample."""
+    pat, perm = wl["small"]
+    ns, cps, ris = oracle_pattern(pat, perm)
+    xs_, ys_, _ = workload_values(dict(wl, m=2), ns, cps, ris)
+    tz, te, reps = oracle_hessian_repeated(wl, ns, cps, ris, xs_, ys_, 2, budget_s=budget_s)
+    f = (float(n) / ns) ** 3
+    m = wl["m"]
+    return {"value": m / (f * (tz + m * te)), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"dense oracle X^-1 ({tz:.3g} s) and P(X^-1 Y X^-1) ({te:.3g} s per Y) on the same recipe at "
+                      f"n = {ns} ({reps} repetitions), extrapolated by (n/{ns})^3 = {f:.0f} to n = {n}; "
+                      f"value = {m}/(t_inverse + {m}*t_eval)"}
+
+
 def make_symbolic(B, wl, **cfg):
     if "batch" in wl:
         inst = wl["batch"] if "subset" not in cfg else [wl["batch"][i] for i in cfg.pop("subset")]
@@ -479,7 +496,10 @@ def run_ours(args, wl, rank, world, local_rank):
 
     tune = None
     cfg = {}
-    if not args.no_tune:
+    if args.tiers:
+        cfg = dict(big_rows=args.tiers[0], big_cols=args.tiers[1], split_cols=args.tiers[2])
+        tune = {"chosen": cfg, "timings_ms": None, "on": "given on the command line"}
+    elif not args.no_tune:
         cfg, timings = tuned_config(B, wl)
         tune = {"chosen": cfg, "timings_ms": timings,
                 "on": ("every 8th instance" if "batch" in wl else "the pattern") + ", the whole step with the same m"}
@@ -648,6 +668,8 @@ def run_ours(args, wl, rank, world, local_rank):
         cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         if count > 1:
             cpu = batch_cpu_baseline(sym, x, ys, m, cores)
+        elif "small" in wl:
+            cpu = scaled_cpu_baseline(wl, n, cores)
         else:
             sample = min(2, m)
             keep = {}
@@ -709,7 +731,8 @@ def run_ours(args, wl, rank, world, local_rank):
             "wall_s": wall,
             "logdet": results.get("logdet"), "fstar": results.get("fstar"),
         }
-        print(json.dumps(line), flush=True)
+        return line
+    return None
 
 
 def serve_cpu_baseline(pool, trace, cores, budget_s=15.0):
@@ -791,6 +814,28 @@ def run_serve(args, wl):
     print(json.dumps(line), flush=True)
 
 
+OTHER_KEYS = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "higher_is_better", "dtype", "config",
+              "roofline", "cpu_baseline", "accuracy", "e2e", "gpu_launches", "clocks", "ops_ms", "ops_evals_per_s",
+              "autotune", "batched_vs_one_at_a_time", "instances")
+
+
+def other_workloads(args, rank, world, local_rank):
+    """The 150 x 150 grid (64 right-hand sides) and the 256-instance batch,
+    measured in the same run with fewer timed steps, as nested records."""
+    import copy
+    import gc
+    import torch
+    out = {}
+    for name, steps in (("grid150", 3), ("batch256", 2)):
+        a = copy.copy(args)
+        a.steps, a.warmup = steps, 3
+        line = run_ours(a, make_workload(name), rank, world, local_rank)
+        out[name] = {k: line.get(k) for k in OTHER_KEYS}
+        gc.collect()
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -800,7 +845,11 @@ def main():
     ap.add_argument("--workload", default="er5000", choices=["er5000", "band200", "grid150", "batch256", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="library default tier cutovers instead of the autotuner's")
+    ap.add_argument("--tiers", type=int, nargs=3, metavar=("BIG_ROWS", "BIG_COLS", "SPLIT_COLS"), default=None,
+                    help="fixed tier cutovers and split width instead of the autotuner's")
     ap.add_argument("--serve-seconds", type=float, default=0.5, help="trace length of the serve workload")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the nested records of the grid and batch workloads (default line only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -823,7 +872,11 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, wl, rank, world, local_rank)
+        line = run_ours(args, wl, rank, world, local_rank)
+        if line is not None and world == 1 and args.workload == "er5000" and not args.no_others:
+            line["other_workloads"] = other_workloads(args, rank, world, local_rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
     finally:
         if world > 1:
             import torch.distributed as dist
