@@ -465,7 +465,10 @@ chd_status chd_factor_set_graphs(chd_factor* fac, int on);
  * other allocating routine.
  * Set-up: the first call on each device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.
+ * call before any stream capture.  The address is kept for the life of the
+ * process: after a cudaDeviceReset, which unloads the library's device
+ * code, it is stale, so do not use this entry point on a device after
+ * resetting it.
  * Sharing: all calls on a device share the one array and it keeps the
  * contents of the last call; calls whose kernels overlap on the GPU (on
  * different streams, or from several threads) race on it and give wrong

@@ -32,7 +32,8 @@ static __device__ __align__(256) double g_noalloc_ws[kNoAllocWorkspaceDoubles];
 
 // Host code must not use `g_noalloc_ws` as a pointer: on the host that name
 // is a stand-in, not the device address.  The device address is looked up
-// once per device (with that device current) and kept here.
+// once per device (with that device current) and kept here for the life of
+// the process (a cudaDeviceReset would make it stale; the header says so).
 constexpr int kMaxDevices = 64;
 std::mutex g_lock;
 double* g_ws_addr[kMaxDevices] = {};

@@ -456,3 +456,25 @@ def test_batched_rhs_strides_and_refactor():
     f.refactor(c.dev(x2))
     g = c.host(f.gradient())
     assert c.err(g, OD.gradient(c.n, c.cp, c.ri, x2)) < TOL
+
+
+def test_hessian_more_right_hand_sides_than_one_launch_indexes():
+    """chd_hessian runs m > 65535 right-hand sides (more than one grid
+    dimension indexes) in chunks: the same products as two separate calls."""
+    c = Case(W.band(4, 1), seed=31)
+    t_ = torch()
+    f = c.sym.factor(c.dev(c.x))
+    m = 65537
+    ys = c.rng.uniform(-1.0, 1.0, size=(m, c.sym.nnz))
+    Y = c.dev(ys)
+    T = t_.empty_like(Y)
+    c.B.chd_hessian(f.handle, Y, T, c.sym.nnz)
+    T1 = t_.empty_like(Y[:65535])
+    T2 = t_.empty_like(Y[65535:])
+    c.B.chd_hessian(f.handle, Y[:65535].contiguous(), T1, c.sym.nnz)
+    c.B.chd_hessian(f.handle, Y[65535:].contiguous(), T2, c.sym.nnz)
+    both = c.host(t_.cat([T1, T2]))
+    got = c.host(T)
+    assert np.array_equal(got, both)
+    want = OD.hessian(c.n, c.cp, c.ri, c.x, [ys[0], ys[-1]])
+    assert c.err(got[0], want[0]) < TOL and c.err(got[-1], want[1]) < TOL

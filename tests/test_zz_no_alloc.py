@@ -31,24 +31,49 @@ def _case(pattern, seed, **kw):
     return B, sym, fac, rng, dev
 
 
-@pytest.mark.parametrize("name", ["band", "grid_mixed_tiers"])
-def test_noalloc_matches_hessian_on_two_calls(name):
+CASES = {
+    "band_chain": lambda: _case(W.band(200, 8), 21),  # the chain tier (library default)
+    "band_warp": lambda: _case(W.band(200, 8), 25, chain_runs=False),
+    # warp, CTA and dense tiers all in play (low dense-tier thresholds)
+    "grid_mixed_tiers": lambda: _case(W.grid2d(16, 16), 22, perm=W.nested_dissection((16, 16), leaf=6),
+                                      big_rows=20, big_cols=8),
+    # one-column leaves of one parent processed as a leaf group, CTA-tier root
+    "arrow_leaf_group": lambda: _case(W.arrow(120, 40), 26),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_noalloc_matches_hessian_on_two_calls(name, side_stream):
+    """Two calls in a row (the second reuses the workspace the first left
+    behind) give the products of chd_hessian, on the default stream and on
+    a side stream; the calls change neither the factor's own workspace nor
+    the device's free memory."""
     import torch
-    if name == "band":
-        B, sym, fac, rng, dev = _case(W.band(200, 8), 21)
-    else:
-        # warp, CTA and dense tiers all in play (low dense-tier thresholds)
-        B, sym, fac, rng, dev = _case(W.grid2d(16, 16), 22, perm=W.nested_dissection((16, 16), leaf=6),
-                                      big_rows=20, big_cols=8)
+    B, sym, fac, rng, dev = CASES[name]()
     m = 3
-    for call in range(2):  # two calls in a row reuse the same fixed workspace
-        ys = dev(W.uniform_sym(sym.n, sym.colptr, sym.rowind, rng, count=m))
-        want = torch.empty_like(ys)
-        got = torch.full_like(ys, float("nan"))
-        B.chd_hessian(fac.handle, ys, want, sym.nnz)
-        B.chd_hessian_noalloc(fac.handle, ys, got, sym.nnz)
+    stream = torch.cuda.Stream() if side_stream else torch.cuda.current_stream()
+    ys = [dev(W.uniform_sym(sym.n, sym.colptr, sym.rowind, rng, count=m)) for _ in range(2)]
+    got = [torch.full_like(y, float("nan")) for y in ys]
+    # one call first: kernels a fresh process has not run yet are loaded now
+    warm = torch.empty_like(ys[0])
+    with torch.cuda.stream(stream):
+        B.chd_hessian_noalloc(fac.handle, ys[0], warm, sym.nnz, stream=stream)
+    torch.cuda.synchronize()
+    ws0 = fac.workspace_bytes()
+    free0, _ = torch.cuda.mem_get_info()
+    with torch.cuda.stream(stream):
+        for call in range(2):
+            B.chd_hessian_noalloc(fac.handle, ys[call], got[call], sym.nnz, stream=stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert fac.workspace_bytes() == ws0
+    assert free1 == free0
+    for call in range(2):
+        want = torch.empty_like(ys[call])
+        B.chd_hessian(fac.handle, ys[call], want, sym.nnz)
         torch.cuda.synchronize()
-        w, g = want.cpu().numpy(), got.cpu().numpy()
+        w, g = want.cpu().numpy(), got[call].cpu().numpy()
         for i in range(m):
             assert OD.rel_err(sym.n, sym.colptr, sym.rowind, g[i], w[i]) < TOL, (call, i)
 
@@ -73,3 +98,10 @@ def test_noalloc_rejects_what_does_not_fit_and_uncached_factors():
     with pytest.raises(B2.ChdError) as e2:
         B2.chd_hessian_noalloc(fac2.handle, ys2, out2, sym2.nnz)
     assert e2.value.code == B2.CHD_ERR_INVALID
+    # more right-hand sides than one launch sequence indexes are refused
+    B3, sym3, fac3, rng3, dev3 = _case(W.band(4, 1), 27)
+    ys3 = torch.zeros((65536, sym3.nnz), dtype=torch.float64, device="cuda")
+    out3 = torch.empty_like(ys3)
+    with pytest.raises(B3.ChdError) as e3:
+        B3.chd_hessian_noalloc(fac3.handle, ys3, out3, sym3.nnz)
+    assert e3.value.code == B3.CHD_ERR_INVALID
