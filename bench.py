@@ -399,12 +399,19 @@ def make_symbolic(B, wl, **cfg):
 def tuned_config(B, wl):
     """Tier cutovers chosen by the autotuner on the benchmark step itself
     (every operation with the workload's m): on every 8th instance of a
-    batch, else on the pattern itself."""
+    batch, else on the pattern itself; then, for a single pattern, the
+    per-front-shape tier table refined from them."""
     from paper_1203_2742_gb300 import autotune
     if "batch" in wl:
         subset = list(range(0, len(wl["batch"]), 8))
         return autotune.tune(lambda **c: make_symbolic(B, wl, subset=subset, **c), wl["m"], op="step", reps=1)
-    return autotune.tune(lambda **c: make_symbolic(B, wl, **c), wl["m"], op="step", reps=2)
+    mk = lambda **c: make_symbolic(B, wl, **c)
+    cfg, timings = autotune.tune(mk, wl["m"], op="step", reps=2)
+    table, trials, _ = autotune.refine_tiers(mk, cfg, wl["m"], timings[json.dumps(cfg, sort_keys=True)])
+    timings = dict(timings, tier_table_trials=trials)
+    if (table >= 0).any():
+        cfg = dict(cfg, tier_table=table)
+    return cfg, timings
 
 
 # ---------------------------------------------------------------------------
@@ -501,7 +508,11 @@ def run_ours(args, wl, rank, world, local_rank):
         tune = {"chosen": cfg, "timings_ms": None, "on": "given on the command line"}
     elif not args.no_tune:
         cfg, timings = tuned_config(B, wl)
-        tune = {"chosen": cfg, "timings_ms": timings,
+        chosen = {k: v for k, v in cfg.items() if k != "tier_table"}
+        if "tier_table" in cfg:
+            t_ = cfg["tier_table"]
+            chosen["tier_table"] = {f"n{i}-a{j}": int(t_[i, j]) for i, j in zip(*np.nonzero(t_ >= 0))}
+        tune = {"chosen": chosen, "timings_ms": timings,
                 "on": ("every 8th instance" if "batch" in wl else "the pattern") + ", the whole step with the same m"}
     t0 = time.perf_counter()
     sym = make_symbolic(B, wl, **cfg)
@@ -513,7 +524,7 @@ def run_ours(args, wl, rank, world, local_rank):
     # the method's flops are counted on the relaxed Algorithm 6.1 partition;
     # splitting wide supernodes (a scheduling choice) executes more
     fl_exec = sym.flops()
-    fl = make_symbolic(B, wl, **dict(cfg, split_cols=-1)).flops()
+    fl = make_symbolic(B, wl, **dict({k: v for k, v in cfg.items() if k != "tier_table"}, split_cols=-1)).flops()
 
     # inputs resident in HBM
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)

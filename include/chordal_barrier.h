@@ -65,6 +65,9 @@ typedef enum {
   CHD_ORDER_MINDEG = 2    /* minimum degree (exact degrees, smallest index on ties) */
 } chd_ordering;
 
+/* log2 buckets of the tier table of chd_opts (front sizes up to 4095) */
+#define CHD_TIER_BUCKETS 13
+
 typedef struct {
   int32_t ordering;        /* chd_ordering */
   const int64_t* user_perm;/* host, n entries, perm[new] = old; used when ordering == CHD_ORDER_USER */
@@ -86,11 +89,21 @@ typedef struct {
                               Hessian (the Cholesky product runs them in the warp tier);
                               0: off */
   int32_t tc_products;     /* dense-tier products on the tensor cores (FP64-accurate digit
-                              products, see chd_dgemm_tc): 0 (default) = products of at
-                              least 64 x 64 outputs with inner dimension >= 32 and
-                              M N K >= 2^22 per right-hand side; 1 = every product of at
-                              least 64 x 16 outputs; -1 = never (FP64 units only) */
+                              products, see chd_dgemm_tc): 0 (default) = a product runs there
+                              when a cost model of both paths (launches, digit products,
+                              output assembly, digit bytes against the FP64 units) predicts a
+                              gain; 1 = every product of at least 64 x 16 outputs; -1 = never
+                              (FP64 units only) */
   int32_t reserved[3];
+  const int32_t* tier_table;  /* host, CHD_TIER_BUCKETS^2 entries, or NULL: per front shape, the
+                              tier of a front with n_k columns and a_k ancestor rows is
+                              tier_table[b(n_k) * CHD_TIER_BUCKETS + b(a_k)] with
+                              b(v) = min(CHD_TIER_BUCKETS - 1, bit length of v) (b(0) = 0,
+                              b(1) = 1, b(2..3) = 2, ...): -1 = by big_rows / big_cols, 0 = a
+                              per-front tier (warp, wide warp or CTA by size), 1 = the dense
+                              tier.  Leaf groups and chain runs are not affected.  Only the
+                              distribution of the work changes, not the results beyond
+                              rounding. */
 } chd_opts;
 
 /* Fill `opts` with the defaults: natural order, relax 0, tie_last 1, default

@@ -1,4 +1,5 @@
-"""Autotuner for the tier cutovers of the front kernels.
+"""Autotuner for the tier cutovers of the front kernels and the per-front
+tier table.
 
 Which tier processes a front -- one warp (small fronts), one CTA (medium),
 or the multi-CTA dense tier (fronts with |J| >= big_rows or |N| >= big_cols)
@@ -88,17 +89,7 @@ def _time_config(make_symbolic, config, x_of, y_of, s_of, m, op, reps):
     return ms
 
 
-def tune(make_symbolic, m, candidates=DEFAULT_CANDIDATES, op="hessian", reps=2, seed=0):
-    """Time every candidate setting; returns (best_config, {config_key: ms}).
-
-    make_symbolic(**config) must return an analysed ``Symbolic`` for the
-    pattern with the given tier settings.  Values: X diagonally dominant, m
-    right-hand sides uniform in [-1, 1] and S = P(G G^T + 0.5 I) (G n x 10)
-    on the analysed pattern (seeded).  op: "hessian", "inv_hessian",
-    "factor", "gradient", or "step" (every operation once, the inverse
-    Hessian on the Hessian's output after a refactor, as a benchmark step
-    runs them).
-    """
+def _inputs(m, seed):
     import torch
     import workloads as W
 
@@ -114,7 +105,21 @@ def tune(make_symbolic, m, candidates=DEFAULT_CANDIDATES, op="hessian", reps=2, 
         rng = np.random.default_rng(seed + 2)
         G = rng.standard_normal((sym.n, 10))
         return torch.as_tensor(W.projected_gram(sym.n, sym.colptr, sym.rowind, G, 0.5), device="cuda")
+    return x_of, y_of, s_of
 
+
+def tune(make_symbolic, m, candidates=DEFAULT_CANDIDATES, op="hessian", reps=2, seed=0):
+    """Time every candidate setting; returns (best_config, {config_key: ms}).
+
+    make_symbolic(**config) must return an analysed ``Symbolic`` for the
+    pattern with the given tier settings.  Values: X diagonally dominant, m
+    right-hand sides uniform in [-1, 1] and S = P(G G^T + 0.5 I) (G n x 10)
+    on the analysed pattern (seeded).  op: "hessian", "inv_hessian",
+    "factor", "gradient", or "step" (every operation once, the inverse
+    Hessian on the Hessian's output after a refactor, as a benchmark step
+    runs them).
+    """
+    x_of, y_of, s_of = _inputs(m, seed)
     timings = {}
     best, best_ms = None, float("inf")
     for cfg in candidates:
@@ -125,8 +130,57 @@ def tune(make_symbolic, m, candidates=DEFAULT_CANDIDATES, op="hessian", reps=2, 
     return best, timings
 
 
+def front_buckets(sym):
+    """Per front: its (n_k, a_k) buckets of the tier table and its Hessian
+    flops per right-hand side (6 a^2 n + 8 a n^2 + 2 n^3)."""
+    sp, par, rp, rows = sym.supernodes()
+    n = np.diff(np.asarray(sp, dtype=np.int64))
+    a = np.diff(np.asarray(rp, dtype=np.int64)) - n
+    bn = np.array([B.tier_bucket(v) for v in n], dtype=np.int64)
+    ba = np.array([B.tier_bucket(v) for v in a], dtype=np.int64)
+    work = 6.0 * a * a * n + 8.0 * a * n * n + 2.0 * n ** 3
+    return n, a, bn, ba, work
+
+
+def refine_tiers(make_symbolic, config, m, base_ms, op="step", trials=6, reps=2, gain=0.02, seed=0):
+    """Per-front-shape refinement of the tier choice (a tier table, see
+    chd_opts.tier_table): starting from the global cutovers of `config`,
+    the `trials` buckets (n_k, a_k) that carry the most work among those
+    adjacent to the cutover (a bucket whose fronts sit within a factor of
+    two of big_rows or big_cols) are moved to the other tier one at a time,
+    and a move is kept when the timed operation gets faster by more than
+    `gain`.  Returns (table as a TIER_BUCKETS x TIER_BUCKETS int array,
+    {bucket: ms} of the trials, best ms)."""
+    x_of, y_of, s_of = _inputs(m, seed)
+    sym = make_symbolic(**config)
+    n, a, bn, ba, work = front_buckets(sym)
+    br = config.get("big_rows") or 320
+    bc = config.get("big_cols") or 160
+    J = n + a
+    dense = (J >= br) | (n >= bc)
+    near = ((J >= br // 2) & (J < 2 * br)) | ((n >= bc // 2) & (n < 2 * bc))
+    stats = {}
+    for i in np.flatnonzero(near):
+        key = (int(bn[i]), int(ba[i]))
+        w, d, c = stats.get(key, (0.0, 0, 0))
+        stats[key] = (w + work[i], d + int(dense[i]), c + 1)
+    order = sorted(stats, key=lambda k: -stats[k][0])[:trials]
+    table = -np.ones((B.TIER_BUCKETS, B.TIER_BUCKETS), dtype=np.int32)
+    best_ms, timings = base_ms, {}
+    for key in order:
+        w, d, c = stats[key]
+        trial = table.copy()
+        trial[key] = 0 if 2 * d >= c else 1
+        ms = _time_config(make_symbolic, dict(config, tier_table=trial), x_of, y_of, s_of, m, op, reps)
+        timings[f"n{key[0]}-a{key[1]}->{int(trial[key])}"] = ms
+        if ms < best_ms * (1.0 - gain):
+            table, best_ms = trial, ms
+    return table, timings, best_ms
+
+
 class Table:
-    """Persistent choices: signature -> tier settings (JSON file)."""
+    """Persistent choices: signature -> tier settings (JSON file).  A tier
+    table (per front shape) is stored as a nested list."""
 
     def __init__(self, path):
         self.path = path
@@ -137,10 +191,18 @@ class Table:
 
     def lookup(self, sig):
         e = self.entries.get(sig)
-        return dict(e["config"]) if e else None
+        if not e:
+            return None
+        cfg = dict(e["config"])
+        if "tier_table" in cfg:
+            cfg["tier_table"] = np.asarray(cfg["tier_table"], dtype=np.int32)
+        return cfg
 
     def store(self, sig, config, timings):
-        self.entries[sig] = {"config": config, "timings_ms": timings}
+        cfg = dict(config)
+        if "tier_table" in cfg:
+            cfg["tier_table"] = np.asarray(cfg["tier_table"]).tolist()
+        self.entries[sig] = {"config": cfg, "timings_ms": timings}
         if self.path:
             tmp = self.path + ".tmp"
             with open(tmp, "w") as f:
@@ -148,13 +210,19 @@ class Table:
             os.replace(tmp, self.path)
 
 
-def analyze_tuned(make_symbolic, m, table, op="hessian", candidates=DEFAULT_CANDIDATES):
+def analyze_tuned(make_symbolic, m, table, op="hessian", candidates=DEFAULT_CANDIDATES, refine=False):
     """Symbolic object with the table's settings for this pattern shape,
-    tuning (and recording) them first if the shape is new."""
+    tuning (and recording) them first if the shape is new; with `refine`,
+    the per-front-shape tier table is refined and recorded too."""
     probe = make_symbolic()
     sig = signature(probe, m)
     cfg = table.lookup(sig)
     if cfg is None:
         cfg, timings = tune(make_symbolic, m, candidates=candidates, op=op)
+        if refine:
+            t, trials, _ = refine_tiers(make_symbolic, cfg, m, timings[json.dumps(cfg, sort_keys=True)], op=op)
+            timings = dict(timings, tier_table_trials=trials)
+            if (t >= 0).any():
+                cfg = dict(cfg, tier_table=t)
         table.store(sig, cfg, timings)
     return make_symbolic(**cfg), cfg, sig

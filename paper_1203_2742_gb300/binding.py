@@ -41,7 +41,15 @@ class chd_opts(C.Structure):
     _fields_ = [("ordering", C.c_int32), ("user_perm", C.POINTER(C.c_int64)), ("relax", C.c_int32),
                 ("tie_last", C.c_int32), ("big_rows", C.c_int32), ("big_cols", C.c_int32),
                 ("split_cols", C.c_int32), ("chain_runs", C.c_int32), ("tc_products", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("reserved", C.c_int32 * 3), ("tier_table", C.POINTER(C.c_int32))]
+
+
+TIER_BUCKETS = 13
+
+
+def tier_bucket(v):
+    """Bucket of a front size in the tier table: its bit length, at most 12."""
+    return min(TIER_BUCKETS - 1, int(v).bit_length())
 
 
 _p = C.c_void_p
@@ -148,7 +156,7 @@ def _dptr(t, what, nnz=None, rows=None):
 # ---------------------------------------------------------------------------
 
 def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0,
-                big_cols=0, split_cols=0, chain_runs=True, tc_products=0):
+                big_cols=0, split_cols=0, chain_runs=True, tc_products=0, tier_table=None):
     colptr = np.ascontiguousarray(colptr, dtype=np.int64)
     rowind = np.ascontiguousarray(rowind, dtype=np.int32)
     o = chd_opts()
@@ -166,6 +174,12 @@ def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_l
     o.split_cols = int(split_cols)
     o.chain_runs = int(chain_runs)
     o.tc_products = int(tc_products)
+    tt = None
+    if tier_table is not None:
+        tt = np.ascontiguousarray(tier_table, dtype=np.int32).reshape(-1)
+        if tt.size != TIER_BUCKETS * TIER_BUCKETS:
+            raise ValueError("tier_table needs TIER_BUCKETS^2 entries")
+        o.tier_table = tt.ctypes.data_as(C.POINTER(C.c_int32))
     out = _p()
     rc = _lib.chd_analyze(int(n), colptr.ctypes.data, rowind.ctypes.data, C.byref(o), C.byref(out))
     _check(rc, "chd_analyze")
@@ -173,7 +187,7 @@ def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_l
 
 
 def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big_cols=0, split_cols=0,
-          chain_runs=True, tc_products=0):
+          chain_runs=True, tc_products=0, tier_table=None):
     o = chd_opts()
     _lib.chd_opts_default(C.byref(o))
     o.ordering = ORDERINGS[ordering]
@@ -189,6 +203,12 @@ def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big
     o.split_cols = int(split_cols)
     o.chain_runs = int(chain_runs)
     o.tc_products = int(tc_products)
+    if tier_table is not None:
+        tt = np.ascontiguousarray(tier_table, dtype=np.int32).reshape(-1)
+        if tt.size != TIER_BUCKETS * TIER_BUCKETS:
+            raise ValueError("tier_table needs TIER_BUCKETS^2 entries")
+        o.tier_table = tt.ctypes.data_as(C.POINTER(C.c_int32))
+        keep = (keep, tt)
     return o, keep
 
 
@@ -451,10 +471,11 @@ class Symbolic:
     """Owner of a ``chd_symbolic``: the analysed pattern and its clique tree."""
 
     def __init__(self, n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True,
-                 big_rows=0, big_cols=0, split_cols=0, chain_runs=True, tc_products=0):
+                 big_rows=0, big_cols=0, split_cols=0, chain_runs=True, tc_products=0, tier_table=None):
         self._h = chd_analyze(n, colptr, rowind, ordering=ordering, perm=perm, relax=relax,
                               tie_last=tie_last, big_rows=big_rows, big_cols=big_cols,
-                              split_cols=split_cols, chain_runs=chain_runs, tc_products=tc_products)
+                              split_cols=split_cols, chain_runs=chain_runs, tc_products=tc_products,
+                              tier_table=tier_table)
         info = chd_symbolic_info(self._h)
         self.n = info["n"]
         self.nnz = info["nnz"]

@@ -569,6 +569,19 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
       int64_t nn = s->sn_ptr[t + 1] - s->sn_ptr[t];
       int64_t J = s->rows_ptr[t + 1] - s->rows_ptr[t];
       s->is_big[t] = (J >= big_rows || nn >= big_cols) ? 1 : 0;
+      if (opts.tier_table) {
+        auto bucket = [](int64_t v) {
+          int b = 0;
+          while (v > 0 && b < CHD_TIER_BUCKETS - 1) {
+            ++b;
+            v >>= 1;
+          }
+          return b;
+        };
+        const int32_t e = opts.tier_table[bucket(nn) * CHD_TIER_BUCKETS + bucket(J - nn)];
+        if (e == 0) s->is_big[t] = 0;
+        if (e == 1) s->is_big[t] = 1;
+      }
       tier[t] = s->is_big[t] ? 2 : (nn <= 8 && J <= 32) ? 0 : (nn <= 8 && J <= 64) ? 3 : 1;
       if (s->grp_of[t] >= 0) {
         tier[t] = 4;

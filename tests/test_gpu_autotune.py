@@ -12,8 +12,16 @@ from tests.helpers import lib
 
 pytestmark = pytest.mark.gpu
 
+def _checker_table():
+    """A tier table that alternates the tier by bucket (dense where the
+    bucket indices have an odd sum, per-front tiers elsewhere)."""
+    t = np.fromfunction(lambda i, j: (i + j) % 2, (13, 13)).astype(np.int32)
+    return t
+
+
 CONFIGS = [dict(), dict(big_rows=16, big_cols=8), dict(big_rows=4096, big_cols=4096),
-           dict(split_cols=8), dict(big_rows=40, big_cols=12, split_cols=16)]
+           dict(split_cols=8), dict(big_rows=40, big_cols=12, split_cols=16),
+           dict(tier_table=_checker_table()), dict(tc_products=1, big_rows=16, big_cols=8)]
 
 
 @pytest.mark.parametrize("case", ["grid", "er"])
@@ -72,3 +80,33 @@ def test_tune_and_table(tmp_path):
     with open(path) as f:
         data = json.load(f)
     assert len(data[sig]["timings_ms"]) == len(cands)
+    # a tier table round-trips through the file
+    table.store("with-table", dict(cfg, tier_table=_checker_table()), {})
+    got = autotune.Table(path).lookup("with-table")
+    assert np.array_equal(got["tier_table"], _checker_table())
+
+
+def test_refine_tiers_returns_a_table_and_keeps_results():
+    """The per-front-shape refinement runs on a pattern with fronts on both
+    sides of the cutover, returns a valid table, and the table's analysis
+    gives the same Hessian as the default one."""
+    import torch
+    B = lib()
+    from paper_1203_2742_gb300 import autotune
+    pat = W.erdos_renyi(600, 0.01, np.random.default_rng(63))
+    make = lambda **cfg: B.Symbolic(*pat, ordering="mindeg", relax=8, **cfg)
+    cfg = dict(big_rows=64, big_cols=32)
+    best, timings = autotune.tune(make, 2, candidates=(cfg,), op="step", reps=1)
+    base = timings[json.dumps(cfg, sort_keys=True)]
+    table, trials, ms = autotune.refine_tiers(make, cfg, 2, base, trials=3, reps=1)
+    assert table.shape == (13, 13) and set(np.unique(table)) <= {-1, 0, 1}
+    assert len(trials) <= 3 and ms <= base
+    s0, s1 = make(**cfg), make(**cfg, tier_table=table)
+    rng = np.random.default_rng(64)
+    x = W.diag_dominant(s0.n, s0.colptr, s0.rowind, rng)
+    ys = W.uniform_sym(s0.n, s0.colptr, s0.rowind, rng, count=2)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    t0 = s0.factor(dev(x)).hessian(dev(ys)).cpu().numpy()
+    t1 = s1.factor(dev(x)).hessian(dev(ys)).cpu().numpy()
+    for j in range(2):
+        assert OD.rel_err(s0.n, s0.colptr, s0.rowind, t1[j], t0[j]) < 1e-12

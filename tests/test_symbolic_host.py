@@ -332,3 +332,29 @@ def test_stored_er5000_analysis():
     # the split partition the benchmark may choose has the same pattern
     sym2 = B.Symbolic(*pattern, ordering="mindeg", relax=16, split_cols=512)
     assert np.array_equal(sym2.colptr, sym.colptr) and np.array_equal(sym2.rowind, sym.rowind)
+
+
+def test_tier_table_assigns_tiers_by_front_shape():
+    """chd_opts.tier_table: all -1 reproduces the threshold rule; 1 in every
+    bucket sends every front to the dense tier, 0 none; a single bucket
+    moves exactly the fronts of that (n_k, a_k) bucket."""
+    B = lib()
+    pat = W.erdos_renyi(600, 0.01, np.random.default_rng(65))
+    kw = dict(ordering="mindeg", relax=8, big_rows=64, big_cols=32)
+    dense = lambda sym: int(sym.schedule()["lvl_counts"][:, 4].sum())
+    base = B.Symbolic(*pat, **kw)
+    nb = B.TIER_BUCKETS
+    assert dense(B.Symbolic(*pat, **kw, tier_table=-np.ones((nb, nb), np.int32))) == dense(base)
+    assert dense(B.Symbolic(*pat, **kw, tier_table=np.ones((nb, nb), np.int32))) == base.nsuper
+    assert dense(B.Symbolic(*pat, **kw, tier_table=np.zeros((nb, nb), np.int32))) == 0
+    sp, par, rp, rows = base.supernodes()
+    n = np.diff(sp)
+    a = np.diff(rp) - n
+    J = n + a
+    is_dense = (J >= 64) | (n >= 32)
+    keys = [(B.tier_bucket(x), B.tier_bucket(y)) for x, y in zip(n, a)]
+    k = next(key for key, d in zip(keys, is_dense) if d)  # a bucket holding a dense front
+    t = -np.ones((nb, nb), np.int32)
+    t[k] = 0
+    moved = sum(1 for key, d in zip(keys, is_dense) if d and key == k)
+    assert dense(B.Symbolic(*pat, **kw, tier_table=t)) == dense(base) - moved
