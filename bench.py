@@ -108,8 +108,8 @@ def make_workload(name):
                 pool.append((W.arrow(n, 32), None))
             else:
                 side = max(2, int(round(np.sqrt(n))))
-                pool.append((W.grid2d(side, side), W.nested_dissection((side, side), leaf=8)))
-        pool.append((W.grid3d(40, 40, 40), W.nested_dissection((40, 40, 40), leaf=8)))
+                pool.append((W.grid2d(side, side), (side, side)))
+        pool.append((W.grid3d(40, 40, 40), (40, 40, 40)))
         return dict(name=name, pool=pool, m=16, seed=4, gram=(20, 0.5), rate=2000.0,
                     mix={"factor": 0.1, "gradient": 0.2, "hessian": 0.5, "inv_hessian": 0.1, "completion": 0.1},
                     desc="serving: Poisson 2000 req/s over 32 resident patterns (n log-uniform 1k..60k: band, "
@@ -117,7 +117,7 @@ def make_workload(name):
                          "gradient, 50% Hessian (m ~ U{1..16}), 10% inverse Hessian, 10% completion")
     if name == "grid150":
         return dict(name=name, pattern=W.grid2d(150, 150),
-                    opts=dict(perm=W.nested_dissection((150, 150), leaf=8)), m=64, seed=2,
+                    opts=W.nd_options((150, 150)), ref_perm=W.nested_dissection((150, 150), leaf=8), m=64, seed=2,
                     gram=(20, 0.5), small=(W.grid2d(60, 60), W.nested_dissection((60, 60), leaf=8)),
                     desc="5-point grid 150x150 (n=22500), geometric nested dissection, "
                          "X diag-dominant, 64 Y, S=P(GG^T+0.5I) G 22500x20")
@@ -264,7 +264,7 @@ def reference_pattern(wl):
         from workloads import analysed
         pattern, perm, sp = analysed.load_er5000()
         return oracle_pattern(pattern, perm, sp)
-    return oracle_pattern(wl["pattern"], wl["opts"].get("perm"))
+    return oracle_pattern(wl["pattern"], wl.get("ref_perm"))
 
 
 class OracleBatch:
@@ -318,8 +318,8 @@ def run_reference(args, wl):
         from types import SimpleNamespace
         from paper_1203_2742_gb300 import serve  # host logic only (no library)
         pool = []
-        for (pat, perm) in wl["pool"]:
-            n, cp, ri = oracle_pattern(pat, perm)
+        for (pat, dims) in wl["pool"]:
+            n, cp, ri = oracle_pattern(pat, None if dims is None else W.nested_dissection(dims, leaf=8))
             sym = SimpleNamespace(n=n, colptr=cp, rowind=ri, nnz=len(ri))
             x, _, s_ = workload_values(dict(wl, m=1), n, cp, ri)
             pool.append((sym, x, s_))
@@ -390,9 +390,11 @@ def make_symbolic(B, wl, **cfg):
     if "batch" in wl:
         inst = wl["batch"] if "subset" not in cfg else [wl["batch"][i] for i in cfg.pop("subset")]
         pats = [p for p, _, _ in inst]
-        perms = [q for _, q, _ in inst]
-        ords = ["user" if q is not None else "natural" for q in perms]
-        return B.SymbolicBatch(pats, orderings=ords, perms=perms, **cfg)
+        ords = []
+        for p, _, kind in inst:
+            dims = W.grid_dims(kind, p[0])
+            ords.append(W.nd_options(dims) if dims else "natural")
+        return B.SymbolicBatch(pats, orderings=ords, **cfg)
     return B.Symbolic(*wl["pattern"], **wl["opts"], **cfg)
 
 
@@ -783,8 +785,8 @@ def run_serve(args, wl):
     from paper_1203_2742_gb300 import serve
     t0 = time.perf_counter()
     pool = []
-    for (pat, perm) in wl["pool"]:
-        sym = B.Symbolic(*pat, perm=perm) if perm is not None else B.Symbolic(*pat)
+    for (pat, dims) in wl["pool"]:
+        sym = B.Symbolic(*pat, **W.nd_options(dims)) if dims is not None else B.Symbolic(*pat)
         x, _, s = workload_values(dict(wl, m=1), sym.n, sym.colptr, sym.rowind)
         pool.append((sym, x, s))
     analyze_s = time.perf_counter() - t0

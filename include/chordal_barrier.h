@@ -62,7 +62,13 @@ typedef enum {
   CHD_ORDER_NATURAL = 0,  /* keep the given numbering (it must be a perfect
                              elimination order if no fill is wanted) */
   CHD_ORDER_USER = 1,     /* use opts.user_perm */
-  CHD_ORDER_MINDEG = 2    /* minimum degree (exact degrees, smallest index on ties) */
+  CHD_ORDER_MINDEG = 2,   /* minimum degree (exact degrees, smallest index on ties) */
+  CHD_ORDER_ND_GEOMETRIC = 3 /* geometric nested dissection of a grid of opts.nd_dims
+                             (vertex x + d0 (y + d1 z), d0 * d1 * d2 = n): the box is cut
+                             through the middle of its longest side (first such axis) by a
+                             one-vertex-thick plane; the lower half, the upper half and then
+                             the plane are ordered, recursively; boxes of at most nd_leaf
+                             vertices (or with all sides < 3) lexicographically, x fastest */
 } chd_ordering;
 
 /* log2 buckets of the tier table of chd_opts (front sizes up to 4095) */
@@ -94,7 +100,8 @@ typedef struct {
                               output assembly, digit bytes against the FP64 units) predicts a
                               gain; 1 = every product of at least 64 x 16 outputs; -1 = never
                               (FP64 units only) */
-  int32_t reserved[3];
+  int32_t nd_dims[3];      /* grid dimensions for CHD_ORDER_ND_GEOMETRIC (use 1 for a 2D grid) */
+  int32_t nd_leaf;         /* CHD_ORDER_ND_GEOMETRIC: largest box ordered without a cut; 0 = 8 */
   const int32_t* tier_table;  /* host, CHD_TIER_BUCKETS^2 entries, or NULL: per front shape, the
                               tier of a front with n_k columns and a_k ancestor rows is
                               tier_table[b(n_k) * CHD_TIER_BUCKETS + b(a_k)] with

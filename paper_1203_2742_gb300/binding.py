@@ -28,7 +28,7 @@ CHD_OK, CHD_ERR_INVALID, CHD_ERR_NOT_PD, CHD_ERR_NOT_COMPLETABLE, CHD_ERR_OOM, C
     CHD_ERR_TIMEOUT = range(7)
 _STATUS_NAMES = {0: "CHD_OK", 1: "CHD_ERR_INVALID", 2: "CHD_ERR_NOT_PD", 3: "CHD_ERR_NOT_COMPLETABLE",
                  4: "CHD_ERR_OOM", 5: "CHD_ERR_CUDA", 6: "CHD_ERR_TIMEOUT"}
-ORDERINGS = {"natural": 0, "user": 1, "mindeg": 2}
+ORDERINGS = {"natural": 0, "user": 1, "mindeg": 2, "nd_geometric": 3}
 
 
 class ChdError(RuntimeError):
@@ -41,7 +41,7 @@ class chd_opts(C.Structure):
     _fields_ = [("ordering", C.c_int32), ("user_perm", C.POINTER(C.c_int64)), ("relax", C.c_int32),
                 ("tie_last", C.c_int32), ("big_rows", C.c_int32), ("big_cols", C.c_int32),
                 ("split_cols", C.c_int32), ("chain_runs", C.c_int32), ("tc_products", C.c_int32),
-                ("reserved", C.c_int32 * 3), ("tier_table", C.POINTER(C.c_int32))]
+                ("nd_dims", C.c_int32 * 3), ("nd_leaf", C.c_int32), ("tier_table", C.POINTER(C.c_int32))]
 
 
 TIER_BUCKETS = 13
@@ -155,39 +155,23 @@ def _dptr(t, what, nnz=None, rows=None):
 # C-named entry points
 # ---------------------------------------------------------------------------
 
-def chd_analyze(n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0,
-                big_cols=0, split_cols=0, chain_runs=True, tc_products=0, tier_table=None):
+def chd_analyze(n, colptr, rowind, **options):
+    """Symbolic analysis of one pattern; options as for `_opts`."""
     colptr = np.ascontiguousarray(colptr, dtype=np.int64)
     rowind = np.ascontiguousarray(rowind, dtype=np.int32)
-    o = chd_opts()
-    _lib.chd_opts_default(C.byref(o))
-    o.ordering = ORDERINGS[ordering]
-    keep = None
-    if perm is not None:
-        keep = np.ascontiguousarray(perm, dtype=np.int64)
-        o.user_perm = keep.ctypes.data_as(C.POINTER(C.c_int64))
-        o.ordering = ORDERINGS["user"]
-    o.relax = int(relax)
-    o.tie_last = 1 if tie_last else 0
-    o.big_rows = int(big_rows)
-    o.big_cols = int(big_cols)
-    o.split_cols = int(split_cols)
-    o.chain_runs = int(chain_runs)
-    o.tc_products = int(tc_products)
-    tt = None
-    if tier_table is not None:
-        tt = np.ascontiguousarray(tier_table, dtype=np.int32).reshape(-1)
-        if tt.size != TIER_BUCKETS * TIER_BUCKETS:
-            raise ValueError("tier_table needs TIER_BUCKETS^2 entries")
-        o.tier_table = tt.ctypes.data_as(C.POINTER(C.c_int32))
+    o, keep = _opts(**options)
     out = _p()
     rc = _lib.chd_analyze(int(n), colptr.ctypes.data, rowind.ctypes.data, C.byref(o), C.byref(out))
     _check(rc, "chd_analyze")
+    del keep
     return out
 
 
 def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big_cols=0, split_cols=0,
-          chain_runs=True, tc_products=0, tier_table=None):
+          chain_runs=True, tc_products=0, tier_table=None, nd_dims=None, nd_leaf=0):
+    """chd_opts from keyword options (and the host arrays it points to).
+    ordering: "natural", "mindeg", "nd_geometric" (with nd_dims = grid
+    dimensions, one to three of them) or "user" (implied by perm)."""
     o = chd_opts()
     _lib.chd_opts_default(C.byref(o))
     o.ordering = ORDERINGS[ordering]
@@ -196,6 +180,10 @@ def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big
         keep = np.ascontiguousarray(perm, dtype=np.int64)
         o.user_perm = keep.ctypes.data_as(C.POINTER(C.c_int64))
         o.ordering = ORDERINGS["user"]
+    if ordering == "nd_geometric":
+        dims = [int(d) for d in nd_dims] + [1] * (3 - len(nd_dims))
+        o.nd_dims[:] = dims
+        o.nd_leaf = int(nd_leaf)
     o.relax = int(relax)
     o.tie_last = 1 if tie_last else 0
     o.big_rows = int(big_rows)
@@ -216,8 +204,10 @@ def chd_analyze_batch(patterns, orderings=None, perms=None, **shared):
     """Analyse independent patterns together (one block-diagonal union).
 
     patterns: list of (n, colptr, rowind); orderings / perms: per-instance
-    lists (None for natural order); shared options (relax, big_rows, ...)
-    are taken from the first instance's options.
+    lists (None for natural order; an ordering is a name or a dict of
+    ordering options, e.g. {"ordering": "nd_geometric", "nd_dims": (k, k)});
+    shared options (relax, big_rows, ...) are taken from the first
+    instance's options.
     """
     count = len(patterns)
     orderings = orderings or ["natural"] * count
@@ -230,7 +220,8 @@ def chd_analyze_batch(patterns, orderings=None, perms=None, **shared):
     OA = chd_opts * count
     oa = OA()
     for i in range(count):
-        o, k = _opts(orderings[i], perms[i], **shared)
+        oi = orderings[i] if isinstance(orderings[i], dict) else {"ordering": orderings[i]}
+        o, k = _opts(perm=perms[i], **oi, **shared)
         oa[i] = o
         keep.append(k)
     cp_ptrs = (C.c_void_p * count)(*[c.ctypes.data for c in cps])
@@ -470,12 +461,12 @@ def chd_factor_free(fac):
 class Symbolic:
     """Owner of a ``chd_symbolic``: the analysed pattern and its clique tree."""
 
-    def __init__(self, n, colptr, rowind, ordering="natural", perm=None, relax=0, tie_last=True,
-                 big_rows=0, big_cols=0, split_cols=0, chain_runs=True, tc_products=0, tier_table=None):
-        self._h = chd_analyze(n, colptr, rowind, ordering=ordering, perm=perm, relax=relax,
-                              tie_last=tie_last, big_rows=big_rows, big_cols=big_cols,
-                              split_cols=split_cols, chain_runs=chain_runs, tc_products=tc_products,
-                              tier_table=tier_table)
+    def __init__(self, n, colptr, rowind, **options):
+        """options: ordering ("natural", "mindeg", "nd_geometric" with
+        nd_dims and nd_leaf), perm (a user ordering), relax, tie_last,
+        big_rows, big_cols, split_cols, chain_runs, tc_products, tier_table
+        (the fields of chd_opts)."""
+        self._h = chd_analyze(n, colptr, rowind, **options)
         info = chd_symbolic_info(self._h)
         self.n = info["n"]
         self.nnz = info["nnz"]

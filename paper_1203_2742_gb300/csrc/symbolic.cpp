@@ -216,13 +216,50 @@ vector<int64_t> chain_postorder(int64_t n, const vector<int64_t>& parent, const 
 
 }  // namespace
 
-// Ordering of one pattern by its options (natural, user, minimum degree);
-// validates the pattern.  perm[new] = old.
-chd_status chd_order_pattern(int64_t n, const int64_t* colptr, const int32_t* rowind, const chd_opts& opts,
-                             std::vector<int64_t>& perm) {
-  if (n < 1 || !colptr || !rowind) return CHD_ERR_INVALID;
-  vector<vector<int32_t>> adj;
-  if (!build_adjacency(n, colptr, rowind, adj)) return CHD_ERR_INVALID;
+namespace {
+
+// Lexicographic order (x fastest) of the box [lo, hi).
+void lex_box(const int64_t* dims, const int64_t* lo, const int64_t* hi, vector<int64_t>& out) {
+  for (int64_t z = lo[2]; z < hi[2]; ++z)
+    for (int64_t y = lo[1]; y < hi[1]; ++y)
+      for (int64_t x = lo[0]; x < hi[0]; ++x) out.push_back(x + dims[0] * (y + dims[1] * z));
+}
+
+// Geometric nested dissection of a grid whose vertex (x, y, z) has index
+// x + dims[0] (y + dims[1] z): the box is cut along its longest side (the
+// first such axis on ties) by the plane through its middle; both halves are
+// ordered first, the lower one before the upper one, then the plane
+// (lexicographically).  Boxes of at most `leaf` vertices, or whose longest
+// side is shorter than 3, are ordered lexicographically.  The separators are
+// eliminated last, so the fill stays inside the halves and the separators.
+void nd_box(const int64_t* dims, const int64_t* lo, const int64_t* hi, int64_t leaf, vector<int64_t>& out) {
+  int64_t ext[3], size = 1;
+  for (int d = 0; d < 3; ++d) {
+    ext[d] = hi[d] - lo[d];
+    size *= ext[d];
+  }
+  if (size == 0) return;
+  int ax = 0;
+  for (int d = 1; d < 3; ++d)
+    if (ext[d] > ext[ax]) ax = d;
+  if (size <= leaf || ext[ax] < 3) {
+    lex_box(dims, lo, hi, out);
+    return;
+  }
+  const int64_t mid = lo[ax] + ext[ax] / 2;
+  int64_t h1[3] = {hi[0], hi[1], hi[2]}, l2[3] = {lo[0], lo[1], lo[2]};
+  int64_t sl[3] = {lo[0], lo[1], lo[2]}, sh[3] = {hi[0], hi[1], hi[2]};
+  h1[ax] = mid;
+  l2[ax] = mid + 1;
+  sl[ax] = mid;
+  sh[ax] = mid + 1;
+  nd_box(dims, lo, h1, leaf, out);
+  nd_box(dims, l2, hi, leaf, out);
+  lex_box(dims, sl, sh, out);
+}
+
+// Ordering of a pattern by its options; perm[new] = old.
+chd_status order_of(int64_t n, const vector<vector<int32_t>>& adj, const chd_opts& opts, vector<int64_t>& perm) {
   perm.assign(n, 0);
   if (opts.ordering == CHD_ORDER_NATURAL) {
     std::iota(perm.begin(), perm.end(), 0);
@@ -237,10 +274,29 @@ chd_status chd_order_pattern(int64_t n, const int64_t* colptr, const int32_t* ro
     }
   } else if (opts.ordering == CHD_ORDER_MINDEG) {
     perm = minimum_degree(n, adj);
+  } else if (opts.ordering == CHD_ORDER_ND_GEOMETRIC) {
+    const int64_t dims[3] = {opts.nd_dims[0], opts.nd_dims[1], opts.nd_dims[2]};
+    if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || dims[0] * dims[1] * dims[2] != n) return CHD_ERR_INVALID;
+    const int64_t lo[3] = {0, 0, 0};
+    perm.clear();
+    perm.reserve(n);
+    nd_box(dims, lo, dims, opts.nd_leaf > 0 ? opts.nd_leaf : 8, perm);
   } else {
     return CHD_ERR_INVALID;
   }
   return CHD_OK;
+}
+
+}  // namespace
+
+// Ordering of one pattern by its options; validates the pattern.
+// perm[new] = old.
+chd_status chd_order_pattern(int64_t n, const int64_t* colptr, const int32_t* rowind, const chd_opts& opts,
+                             std::vector<int64_t>& perm) {
+  if (n < 1 || !colptr || !rowind) return CHD_ERR_INVALID;
+  vector<vector<int32_t>> adj;
+  if (!build_adjacency(n, colptr, rowind, adj)) return CHD_ERR_INVALID;
+  return order_of(n, adj, opts, perm);
 }
 
 void chd_opts_default(chd_opts* o) {
@@ -261,23 +317,8 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
   s->tc_mode = opts.tc_products < 0 ? -1 : (opts.tc_products > 0 ? 1 : 0);
 
   // ---- ordering -----------------------------------------------------------
-  vector<int64_t> perm0(n);
-  if (opts.ordering == CHD_ORDER_NATURAL) {
-    std::iota(perm0.begin(), perm0.end(), 0);
-  } else if (opts.ordering == CHD_ORDER_USER) {
-    if (!opts.user_perm) return CHD_ERR_INVALID;
-    vector<char> seen(n, 0);
-    for (int64_t i = 0; i < n; ++i) {
-      int64_t v = opts.user_perm[i];
-      if (v < 0 || v >= n || seen[v]) return CHD_ERR_INVALID;
-      seen[v] = 1;
-      perm0[i] = v;
-    }
-  } else if (opts.ordering == CHD_ORDER_MINDEG) {
-    perm0 = minimum_degree(n, adj);
-  } else {
-    return CHD_ERR_INVALID;
-  }
+  vector<int64_t> perm0;
+  if (chd_status rc = order_of(n, adj, opts, perm0)) return rc;
 
   // ---- pass 1: fill + Algorithm 6.1 chains -> contiguous postorder --------
   vector<vector<int32_t>> low, I;

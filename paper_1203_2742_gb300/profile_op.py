@@ -47,16 +47,17 @@ def symbolic_for(name, **tiers):
         return B.Symbolic(*W.erdos_renyi(5000, 0.001, np.random.default_rng(1)), ordering="mindeg", relax=16,
                           **tiers)
     if name == "grid150":
-        return B.Symbolic(*W.grid2d(150, 150), perm=W.nested_dissection((150, 150), leaf=8), **tiers)
+        return B.Symbolic(*W.grid2d(150, 150), **W.nd_options((150, 150)), **tiers)
     if name == "dense1500":
         return B.Symbolic(*W.band(1500, 1499), **tiers)
     if name == "grid3d40":
-        return B.Symbolic(*W.grid3d(40, 40, 40), perm=W.nested_dissection((40, 40, 40), leaf=8), **tiers)
+        return B.Symbolic(*W.grid3d(40, 40, 40), **W.nd_options((40, 40, 40)), **tiers)
     if name == "band20k_w61":
         return B.Symbolic(*W.band(20000, 61), **tiers)
     if name == "batch256":
         inst = W.batch_mix(256, 3)
-        return B.SymbolicBatch([p for p, _, _ in inst], perms=[q for _, q, _ in inst], **tiers)
+        ords = [W.nd_options(W.grid_dims(k, p[0])) if k == "grid" else "natural" for p, _, k in inst]
+        return B.SymbolicBatch([p for p, _, _ in inst], orderings=ords, **tiers)
     raise SystemExit(f"unknown workload {name}")
 
 

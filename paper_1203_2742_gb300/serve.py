@@ -159,6 +159,15 @@ class Server:
             self.states[pattern].busy = False
             self.cv.notify_all()
 
+    def run(self, req, stream=None):
+        """Serve one request now, on `stream` (default: the current stream),
+        outside the queue: the same code path a worker takes for a batch of
+        one.  Fills req.start, req.done and req.result and returns the result."""
+        if self.t0 is None:
+            self.t0 = time.perf_counter()
+        self._run_group([req], stream if stream is not None else self.torch.cuda.current_stream())
+        return req.result
+
     def _run_group(self, group, stream):
         torch = self.torch
         req = group[0]

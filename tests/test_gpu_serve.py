@@ -24,7 +24,6 @@ def _pool(rng):
 
 
 def test_results_same_alone_and_in_the_mix():
-    import torch
     from paper_1203_2742_gb300 import serve
     rng = np.random.default_rng(51)
     pool = _pool(rng)
@@ -44,8 +43,7 @@ def test_results_same_alone_and_in_the_mix():
     alone.warm()
     for r in trace:
         solo = serve.Request(op=r.op, pattern=r.pattern, arrival=0.0, data=r.data, m=r.m, rid=r.rid)
-        alone.t0 = 0.0 if alone.t0 is None else alone.t0
-        alone._run_group([solo], torch.cuda.current_stream())
+        alone.run(solo)
         a, b = np.asarray(solo.result, dtype=np.float64), np.asarray(r.result, dtype=np.float64)
         assert a.shape == b.shape, r.op
         if r.op in ("hessian", "inv_hessian"):

@@ -358,3 +358,64 @@ def test_tier_table_assigns_tiers_by_front_shape():
     t[k] = 0
     moved = sum(1 for key, d in zip(keys, is_dense) if d and key == k)
     assert dense(B.Symbolic(*pat, **kw, tier_table=t)) == dense(base) - moved
+
+
+# ---------------------------------------------------------------------------
+# geometric nested dissection inside the analysis
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,leaf", [((9, 9), 8), ((14, 14), 6), ((7, 3, 4), 8), ((5, 5, 5), 8),
+                                       ((1, 30), 4), ((150, 150), 8)])
+def test_nested_dissection_ordering_in_analysis(dims, leaf):
+    """ordering="nd_geometric" gives the same analysis (perm, filled pattern,
+    supernodes) as the input generator's nested-dissection permutation
+    handed over as a user ordering: two independent codings of one rule."""
+    B = lib()
+    pat = W.grid2d(*dims) if len(dims) == 2 else W.grid3d(*dims)
+    s1 = B.Symbolic(*pat, ordering="nd_geometric", nd_dims=dims, nd_leaf=leaf)
+    s2 = B.Symbolic(*pat, perm=W.nested_dissection(dims, leaf=leaf))
+    assert (s1.perm == s2.perm).all()
+    assert (s1.colptr == s2.colptr).all() and (s1.rowind == s2.rowind).all()
+    for x, y in zip(s1.supernodes(), s2.supernodes()):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_nested_dissection_separators_and_fill():
+    """On a k x k grid the top separator (the middle column, k vertices) is
+    eliminated last and lies in the root clique (Algorithm 6.1 joins one
+    half's separator to it: their columns have |I| one apart), and the fill
+    stays O(n log n): far below the natural order's band fill of about n k."""
+    B = lib()
+    k = 63
+    pat = W.grid2d(k, k)
+    s = B.Symbolic(*pat, ordering="nd_geometric", nd_dims=(k, k))
+    assert sorted((np.asarray(s.perm[-k:]) % k).tolist()) == [k // 2] * k
+    sp, par, rp, rows = s.supernodes()
+    root = int(np.flatnonzero(np.asarray(par) < 0)[0])
+    assert sp[root + 1] == k * k and sp[root + 1] - sp[root] == k + k // 2  # + a half's separator row
+    assert rp[root + 1] - rp[root] == sp[root + 1] - sp[root]
+    nat = B.Symbolic(*pat)
+    assert s.nnz < 0.4 * nat.nnz
+    assert s.nnz < 2 * k * k * np.log2(k * k)
+
+
+def test_nested_dissection_rejects_wrong_dimensions():
+    B = lib()
+    with pytest.raises(B.ChdError):
+        B.Symbolic(*W.grid2d(6, 6), ordering="nd_geometric", nd_dims=(6, 5))
+    with pytest.raises(B.ChdError):
+        B.Symbolic(*W.grid2d(6, 6), ordering="nd_geometric", nd_dims=(36, 0, 1))
+
+
+def test_batch_with_nested_dissection_orderings():
+    """Per-instance ordering options in a batch analysis."""
+    B = lib()
+    pats = [W.grid2d(12, 12), W.band(40, 3), W.grid3d(4, 5, 3)]
+    ords = [{"ordering": "nd_geometric", "nd_dims": (12, 12), "nd_leaf": 6}, "natural",
+            {"ordering": "nd_geometric", "nd_dims": (4, 5, 3)}]
+    sb = B.SymbolicBatch(pats, orderings=ords)
+    perms = [W.nested_dissection((12, 12), leaf=6), None, W.nested_dissection((4, 5, 3), leaf=8)]
+    for i, (p, q) in enumerate(zip(pats, perms)):
+        (ni, cp, ri), perm = sb.instance_pattern(i)
+        s1 = B.Symbolic(*p, perm=q)
+        assert (perm == s1.perm).all() and (cp == s1.colptr).all() and (ri == s1.rowind).all()

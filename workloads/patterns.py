@@ -175,6 +175,21 @@ def pattern_hash(pattern):
     return h.hexdigest()[:16]
 
 
+def nd_options(dims, leaf=8):
+    """The analysis options that make the library order a grid of `dims` by
+    the same geometric nested dissection as nested_dissection(dims, leaf)."""
+    return {"ordering": "nd_geometric", "nd_dims": tuple(int(d) for d in dims), "nd_leaf": int(leaf)}
+
+
+def grid_dims(kind, n):
+    """Grid dimensions of a batch_mix instance of this kind and size (None
+    for the families that keep their natural order)."""
+    if kind != "grid":
+        return None
+    side = int(round(np.sqrt(n)))
+    return (side, side)
+
+
 def batch_mix(count, seed, nmin=300, nmax=30000):
     """Independent instances for batched runs: n log-uniform in [nmin, nmax],
     a third each band (half-bandwidth uniform in 4..64), block arrow (arrow
