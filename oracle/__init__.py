@@ -15,6 +15,9 @@ Modules
                      (e-dual-barrier-def)).
 ``symbolic``      -- filled pattern, elimination tree, monotone degrees,
                      cliques, supernode partitions (§2, §6, Algorithm 6.1).
+``factored``      -- the completion with factored update matrices, step by
+                     step (Algorithm 4.3 in the supernodal form of §7.2),
+                     pinned against ``dense``'s completion.
 
 Value layout shared with the library API: a symmetric matrix on the pattern V
 is stored as the lower-triangular compressed columns (CSC) of V, rows sorted
