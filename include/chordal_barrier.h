@@ -111,10 +111,21 @@ typedef struct {
                               tier.  Leaf groups and chain runs are not affected.  Only the
                               distribution of the work changes, not the results beyond
                               rounding. */
+  int32_t completion;      /* chd_complete / chd_recomplete: 0 (default) = every front
+                              factors its V_k = S_{A_k A_k} itself (the fronts are
+                              independent); 1 = factored update matrices (Algorithm 4.3, and
+                              its supernodal form at the end of §7.2): the factor V_k = R_k R_k^T
+                              is propagated from the parent, parents first, by deleting rows of
+                              R_parent and re-triangularising them with Householder
+                              reflections; the rows of A_k inside N_parent are added by a
+                              triangular solve and a Cholesky factorisation.  Same result up to
+                              rounding; the factors R_k are kept (the Hessian factor of the
+                              completion reuses them). */
 } chd_opts;
 
 /* Fill `opts` with the defaults: natural order, relax 0, tie_last 1, default
-   dense-tier thresholds, chain runs on, tensor-core products by cost. */
+   dense-tier thresholds, chain runs on, tensor-core products by cost,
+   independent completion fronts. */
 void chd_opts_default(chd_opts* opts);
 
 /*
@@ -192,6 +203,18 @@ chd_status chd_symbolic_supernodes(const chd_symbolic* sym, const int64_t** snod
  * per right-hand side, out[4] completion.
  */
 chd_status chd_symbolic_flops(const chd_symbolic* sym, double out[5]);
+
+/*
+ * The part of the completion that the two forms of chd_opts.completion do
+ * differently, in flops summed over the fronts: out[0] = the Cholesky
+ * factorisations of every V_k = S_{A_k A_k} (a_k^3 / 3, independent form);
+ * out[1] = the factored form's propagation: the Householder reduction of the
+ * rows of R_parent kept for A_k (4 x length x rows per reflection), the
+ * triangular solve, update and Cholesky factorisation of the rows of A_k in
+ * N_parent.  out[2] = the number of depth levels (of the clique tree) with
+ * fronts to propagate, which run one after another.  Host only.
+ */
+chd_status chd_completion_flops(const chd_symbolic* sym, double out[3]);
 
 /*
  * The launch schedule built by the analysis (host arrays owned by `sym`,

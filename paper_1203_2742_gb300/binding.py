@@ -41,7 +41,8 @@ class chd_opts(C.Structure):
     _fields_ = [("ordering", C.c_int32), ("user_perm", C.POINTER(C.c_int64)), ("relax", C.c_int32),
                 ("tie_last", C.c_int32), ("big_rows", C.c_int32), ("big_cols", C.c_int32),
                 ("split_cols", C.c_int32), ("chain_runs", C.c_int32), ("tc_products", C.c_int32),
-                ("nd_dims", C.c_int32 * 3), ("nd_leaf", C.c_int32), ("tier_table", C.POINTER(C.c_int32))]
+                ("nd_dims", C.c_int32 * 3), ("nd_leaf", C.c_int32), ("tier_table", C.POINTER(C.c_int32)),
+                ("completion", C.c_int32)]
 
 
 TIER_BUCKETS = 13
@@ -64,6 +65,8 @@ _lib.chd_symbolic_info.argtypes = [_p, C.POINTER(_i64), C.POINTER(_i64), C.POINT
                                    C.POINTER(_p), C.POINTER(_i64)]
 _lib.chd_symbolic_supernodes.argtypes = [_p, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]
 _lib.chd_symbolic_flops.argtypes = [_p, C.POINTER(C.c_double)]
+_lib.chd_completion_flops.argtypes = [_p, C.POINTER(C.c_double)]
+_lib.chd_completion_flops.restype = C.c_int
 _lib.chd_symbolic_free.argtypes = [_p]
 _lib.chd_symbolic_free.restype = None
 _lib.chd_factor_new.argtypes = [_p, _p, _p, C.POINTER(_p)]
@@ -168,10 +171,12 @@ def chd_analyze(n, colptr, rowind, **options):
 
 
 def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big_cols=0, split_cols=0,
-          chain_runs=True, tc_products=0, tier_table=None, nd_dims=None, nd_leaf=0):
+          chain_runs=True, tc_products=0, tier_table=None, nd_dims=None, nd_leaf=0, completion="independent"):
     """chd_opts from keyword options (and the host arrays it points to).
     ordering: "natural", "mindeg", "nd_geometric" (with nd_dims = grid
-    dimensions, one to three of them) or "user" (implied by perm)."""
+    dimensions, one to three of them) or "user" (implied by perm);
+    completion: "independent" (every front factors its V_k) or "factored"
+    (update matrices propagated from the parents, Algorithm 4.3)."""
     o = chd_opts()
     _lib.chd_opts_default(C.byref(o))
     o.ordering = ORDERINGS[ordering]
@@ -191,6 +196,7 @@ def _opts(ordering="natural", perm=None, relax=0, tie_last=True, big_rows=0, big
     o.split_cols = int(split_cols)
     o.chain_runs = int(chain_runs)
     o.tc_products = int(tc_products)
+    o.completion = {"independent": 0, "factored": 1}[completion]
     if tier_table is not None:
         tt = np.ascontiguousarray(tier_table, dtype=np.int32).reshape(-1)
         if tt.size != TIER_BUCKETS * TIER_BUCKETS:
@@ -276,6 +282,14 @@ def chd_symbolic_flops(sym):
     out = (C.c_double * 5)()
     _check(_lib.chd_symbolic_flops(sym, out), "chd_symbolic_flops")
     return dict(factor=out[0], gradient=out[1], hessian=out[2], inv_hessian=out[3], completion=out[4])
+
+
+def chd_completion_flops(sym):
+    """The two completion forms' differing work: Cholesky of every V_k
+    (independent) against the factored propagation, and its level count."""
+    out = (C.c_double * 3)()
+    _check(_lib.chd_completion_flops(sym, out), "chd_completion_flops")
+    return dict(independent=out[0], factored=out[1], levels=int(out[2]))
 
 
 def chd_symbolic_free(sym):
@@ -492,6 +506,9 @@ class Symbolic:
 
     def flops(self):
         return chd_symbolic_flops(self._h)
+
+    def completion_flops(self):
+        return chd_completion_flops(self._h)
 
     def factor(self, x, stream=None):
         return Factor(self, chd_factor_new(self._h, x, self.nnz, stream))

@@ -15,6 +15,7 @@
 #include "chd_internal.h"
 #include "front_views.cuh"
 #include "tc_gemm.cuh"
+#include "fc_body.cuh"
 
 namespace chd_launch {
 void count_launch();
@@ -666,6 +667,35 @@ __global__ void __launch_bounds__(BT) mk_gather_saa(SymDev S, int k, const doubl
     if (r >= c) F[(n + r) + (int64_t)(n + c) * J] = Sin[csc_find(S, __ldg(A + r), __ldg(A + c))];
   }
 }
+// rows r and R-1-r of the R x C block B (ld) exchanged
+__global__ void __launch_bounds__(BT) mk_rev_rows(double* B, int64_t ld, int R, int C) {
+  const int h = R / 2;
+  const int64_t tot = (int64_t)h * C;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % h), c = (int)(e / h);
+    double* x = B + r + (int64_t)c * ld;
+    double* y = B + (R - 1 - r) + (int64_t)c * ld;
+    const double t = *x;
+    *x = *y;
+    *y = t;
+  }
+}
+// factored update matrices (fc_body.cuh): the gather of front k
+__global__ void __launch_bounds__(BT) mk_fc_gather(SymDev S, int k, const double* Sin, double* Gq, double* fcs) {
+  const fc::Info f = fc::info(S, k);
+  const int64_t tot = fc::gather_count(f);
+  const double* Gp = Gq + S.v_off[f.p];
+  double* X = fcs + S.fc_off[k];
+  double* G = Gq + S.v_off[k];
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT)
+    fc::gather_one(f, e, Sin, Gp, f.Jp - f.np, X, G);
+}
+// ... and its Householder reduction (a chain of dependent reflections: one CTA)
+constexpr int FCT = 1024;
+__global__ void __launch_bounds__(FCT) k_fc_reduce(SymDev S, int k, double* Gq, double* fcs, int64_t* st) {
+  const fc::Info f = fc::info(S, k);
+  fc::reduce(f, fcs + S.fc_off[k], Gq + S.v_off[k], st);
+}
 __global__ void k_logdet_diag(const double* F, int64_t ld, int n, double* out) {
   __shared__ double red[BT];
   double s = 0.0;
@@ -950,8 +980,12 @@ void complete_load_front(const chd_symbolic* s, const Ctx& st, int k, const doub
   CHD_EW(mk_csc_to_front, (int64_t)f.J * f.n, 1, st, ws + f.foff, 0, f.J, f.n, Sin + f.base, 0);
 }
 
+// With Gq (factored update matrices, Algorithm 4.3): G = P R_k P of
+// V_k = R_k R_k^T from Gq instead of chol(V_k); the solves run on S_AN and
+// L_AN with reversed rows (Z^T Z is unchanged).
 void complete_front(const chd_symbolic* s, const Ctx& st, int k, const double* Sin, double* Lc, double* Wc,
-                    double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
+                    double* Dd, double* Vd, double* Rd, const double* Gq, double* ws, double* ldet,
+                    int64_t* status) {
   Front f = front(s, k);
   const int J = f.J, n = f.n, a = f.a;
   double* F = ws + f.foff;
@@ -959,12 +993,15 @@ void complete_front(const chd_symbolic* s, const Ctx& st, int k, const double* S
   double* T2 = T1 + (int64_t)J * n;
   // the S-front F was loaded by complete_load_front
   double* V = Vd + s->v_off[k];
-  double* R = Rd + s->v_off[k];
+  double* R = Gq ? const_cast<double*>(Gq) + s->v_off[k] : Rd + s->v_off[k];
   if (a > 0) {
     CHD_EW(mk_copy, (int64_t)a * a, 1, st, V, 0, a, F + n + (int64_t)n * J, 0, J, a, a, 1.0, 0.0, 1, 0);
-    CHD_EW(mk_copy, (int64_t)a * a, 1, st, R, 0, a, F + n + (int64_t)n * J, 0, J, a, a, 1.0, 0.0, 1, 0);
-    potrf_partial(st, R, a, a, a, status, CHD_ERR_NOT_COMPLETABLE, k, -1);
+    if (!Gq) {
+      CHD_EW(mk_copy, (int64_t)a * a, 1, st, R, 0, a, F + n + (int64_t)n * J, 0, J, a, a, 1.0, 0.0, 1, 0);
+      potrf_partial(st, R, a, a, a, status, CHD_ERR_NOT_COMPLETABLE, k, -1);
+    }
     CHD_EW(mk_copy, (int64_t)a * n, 1, st, T1 + n, 0, J, F + n, 0, J, a, n, 1.0, 0.0, 0, 0);
+    if (Gq) CHD_EW(mk_rev_rows, (int64_t)(a / 2) * n, 1, st, T1 + n, J, a, n);
     trsm_rLT(st, 1, n, a, DnTW{T1 + n, J}, 0, R, a);  // Z = R^{-1} S_AN
   }
   CHD_EW(mk_copy, (int64_t)n * n, 1, st, T1, 0, J, F, 0, J, n, n, 1.0, 0.0, 1, 0);
@@ -972,6 +1009,7 @@ void complete_front(const chd_symbolic* s, const Ctx& st, int k, const double* S
     gemm(st, 1, n, n, a, -1.0, DnT{T1 + n, J}, 0, Dn{T1 + n, J}, 0, 1.0, Dn{T1, J}, 0, true);  // P
     CHD_EW(mk_copy, (int64_t)a * n, 1, st, T2 + n, 0, J, T1 + n, 0, J, a, n, -1.0, 0.0, 0, 0);
     trsm_rL(st, 1, n, a, DnTW{T2 + n, J}, 0, R, a);  // L_AN = -R^{-T} Z
+    if (Gq) CHD_EW(mk_rev_rows, (int64_t)(a / 2) * n, 1, st, T2 + n, J, a, n);
   }
   CHD_EW(mk_front_to_csc, (int64_t)J * n, 1, st, Wc + f.base, 0, T1, 0, J, J, n, 0, n, 1.0);
   if (a > 0) CHD_EW(mk_front_to_csc, (int64_t)J * n, 1, st, Wc + f.base, 0, T2, 0, J, J, n, n, J, 1.0);
@@ -1346,22 +1384,59 @@ void group_ihess_up(const chd_symbolic* s, const Ctx& st, int m, int g, const do
   gemm(st, m, G.a, G.a, G.L, -1.0, Lb, 0, DnT{P, G.a}, sw, 1.0, U, sw, true);
 }
 void group_complete(const chd_symbolic* s, const Ctx& st, int g, const double* Sin, double* Lc, double* Wc,
-                    double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
+                    double* Dd, double* Vd, double* Rd, const double* Gq, double* ws, double* ldet,
+                    int64_t* status) {
   const Group G = group(s, g);
   double* V = Vd + G.v0;
-  double* R = Rd + G.v0;
+  double* R = Gq ? const_cast<double*>(Gq) + G.v0 : Rd + G.v0;
   double* Z = ws + G.f1;
-  CHD_EW(mg_gather_saa, (int64_t)G.a * G.a, 1, st, s->dev, G.rows, G.a, Sin, V, R);
-  potrf_partial(st, R, G.a, G.a, G.a, status, CHD_ERR_NOT_COMPLETABLE, G.c0, -1);
+  CHD_EW(mg_gather_saa, (int64_t)G.a * G.a, 1, st, s->dev, G.rows, G.a, Sin, V, Rd + G.v0);
+  if (!Gq) potrf_partial(st, R, G.a, G.a, G.a, status, CHD_ERR_NOT_COMPLETABLE, G.c0, -1);
   // Z = R^{-1} S_AN for all leaves, then P per leaf, then L_AN = -R^{-T} Z
+  // (with Gq: G = P R_k P and the rows of S_AN and L_AN reversed)
   CHD_EW(mk_copy, (int64_t)G.a * G.L, 1, st, Z, 0, G.a, Sin + G.base0 + 1, 0, G.J, G.a, G.L, 1.0, 0.0, 0, 0);
+  if (Gq) CHD_EW(mk_rev_rows, (int64_t)(G.a / 2) * G.L, 1, st, Z, G.a, G.a, G.L);
   trsm_rLT(st, 1, G.L, G.a, DnTW{Z, G.a}, 0, R, G.a);
   mg_comp_mid<<<leaf_grid(G.L, 1), BT, 0, st>>>(Sin, Wc, Z, G.base0, G.J, G.L);
   chd_launch::count_launch();
   trsm_rL(st, 1, G.L, G.a, DnTW{Z, G.a}, 0, R, G.a);
+  if (Gq) CHD_EW(mk_rev_rows, (int64_t)(G.a / 2) * G.L, 1, st, Z, G.a, G.a, G.L);
   mg_comp_finish<<<leaf_grid(G.L, 1), BT, 0, st>>>(Lc, Wc, Dd, ldet, Z, G.base0, G.J, G.L, G.c0, G.d0, G.col0,
                                                    status);
   chd_launch::count_launch();
+}
+
+// Factored update matrices (Algorithm 4.3) for front k of the dense tier,
+// its parent's G done: gather, the Householder reduction of the rows kept
+// from G_parent, then M = S~ L^{-T}, G~ = chol(A~ - M M^T) with the blocked
+// multi-CTA kernels (fc_body.cuh has the layout).
+void fc_front(const chd_symbolic* s, const Ctx& st, int k, const double* Sin, double* Gq, double* fcs,
+              int64_t* status) {
+  const int64_t nk = s->sn_ptr[k + 1] - s->sn_ptr[k];
+  const int a = (int)(s->rows_ptr[k + 1] - s->rows_ptr[k] - nk);
+  const int64_t p = s->sn_par[k];
+  const int np = (int)(s->sn_ptr[p + 1] - s->sn_ptr[p]);
+  const int Jp = (int)(s->rows_ptr[p + 1] - s->rows_ptr[p]);
+  const int32_t* rel = s->rel.data() + s->rows_ptr[k] + nk;
+  int q = 0;
+  for (int r = 0; r < a; ++r) q += rel[r] >= np ? 1 : 0;
+  const int w = q > 0 ? Jp - rel[a - q] : 0;
+  const int pp = a - q;
+  double* G = Gq + s->v_off[k];
+  CHD_EW(mk_fc_gather, (int64_t)q * w + (int64_t)pp * a, 1, st, s->dev, k, Sin, Gq, fcs);
+  if (q > 0) {
+    k_fc_reduce<<<1, FCT, 0, st>>>(s->dev, k, Gq, fcs, status);
+    chd_launch::count_launch();
+  }
+  if (pp > 0) {
+    double* M = G + q;
+    double* At = G + q + (int64_t)q * a;
+    if (q > 0) {
+      trsm_rLT(st, 1, pp, q, Dn{M, a}, 0, G, a);
+      gemm(st, 1, pp, pp, q, -1.0, Dn{M, a}, 0, DnT{M, a}, 0, 1.0, Dn{At, a}, 0, true);
+    }
+    potrf_partial(st, At, a, pp, pp, status, CHD_ERR_NOT_COMPLETABLE, k, -1);
+  }
 }
 
 }  // namespace big
@@ -1410,10 +1485,14 @@ void big_ihess_up(const chd_symbolic* s, const Slot& sl, int m, int k, const dou
   chd::big::ihess_up_front(s, chd::big::make_ctx(sl), m, k, Wc, Y, ldy, ws);
 }
 void big_complete(const chd_symbolic* s, const Slot& sl, int k, const double* Sin,
-                  double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
-                  int64_t* status) {
-  if (s->grp_of[k] >= 0) return chd::big::group_complete(s, chd::big::make_ctx(sl), s->grp_of[k], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
-  chd::big::complete_front(s, chd::big::make_ctx(sl), k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+                  double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, const double* Gq, double* ws,
+                  double* ldet, int64_t* status) {
+  if (s->grp_of[k] >= 0) return chd::big::group_complete(s, chd::big::make_ctx(sl), s->grp_of[k], Sin, Lc, Wc, Dd, Vd, Rd, Gq, ws, ldet, status);
+  chd::big::complete_front(s, chd::big::make_ctx(sl), k, Sin, Lc, Wc, Dd, Vd, Rd, Gq, ws, ldet, status);
+}
+void big_fc(const chd_symbolic* s, const Slot& sl, int k, const double* Sin, double* Gq, double* fcs,
+            int64_t* status) {
+  chd::big::fc_front(s, chd::big::make_ctx(sl), k, Sin, Gq, fcs, status);
 }
 void big_rtrans(const chd_symbolic* s, const Slot& sl, int m, int k, int dir,
                 const double* Lc, const double* Qd, double* Z, int64_t ldz, double* ws) {

@@ -27,7 +27,8 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
                  const double* Dd, const double* Rd, const double* T, int64_t ldt, double* Y, int64_t ldy,
                  double* ws);
 void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Sin, double* Lc,
-              double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status);
+              double* Wc, double* Dd, double* Vd, double* Rd, double* Gq, double* fcs, double* ws, double* ldet,
+              int64_t* status);
 void inv_v(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Vd, double* Rd, double* Qd,
            double* ws, int64_t* status, int what);
 void hess_up_pass(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, const double* Wc, const double* Vd,
@@ -492,6 +493,17 @@ chd_status chd_symbolic_flops(const chd_symbolic* s, double out[5]) {
   return CHD_OK;
 }
 
+chd_status chd_completion_flops(const chd_symbolic* s, double out[3]) {
+  if (!s || !out) return CHD_ERR_INVALID;
+  out[0] = s->fc_flops[0];
+  out[1] = s->fc_flops[1];
+  int levels = 0;
+  for (size_t l = 0; l + 1 < s->fc_lvl.size(); ++l)
+    levels += (s->fc_lvl[l + 1] > s->fc_lvl[l] || s->fc_big_lvl[l + 1] > s->fc_big_lvl[l]) ? 1 : 0;
+  out[2] = (double)levels;
+  return CHD_OK;
+}
+
 void chd_symbolic_free(chd_symbolic* s) {
   if (!s) return;
   if (s->dev_buf) cudaFree(s->dev_buf);
@@ -732,17 +744,30 @@ chd_status chd_recomplete(chd_factor* f, const double* sv, void* stream, double*
   if (rc == CHD_OK) rc = cuda_ok(cudaMemsetAsync(f->status, 0, 4 * 8, f->stream));
   if (rc == CHD_OK)
     rc = cuda_ok(cudaMemcpyAsync(f->Sc, sv, (size_t)s->colptr[s->n] * 8, cudaMemcpyDeviceToDevice, f->stream));
+  // factored update matrices: scratch of the Householder reductions (the
+  // largest level's), allocated once per factor object
+  const bool factored = s->completion_mode == 1;
+  if (rc == CHD_OK && factored && !f->fcs && s->fc_total > 0) {
+    if (cudaMalloc(reinterpret_cast<void**>(&f->fcs), (size_t)s->fc_total * 8) != cudaSuccess) {
+      cudaGetLastError();
+      f->fcs = nullptr;
+      rc = CHD_ERR_OOM;
+    }
+  }
   if (rc == CHD_OK) {
     GraphKey key;
     key.p[0] = sv;
     rc = run_sequence(f, G_COMPLETE, key, [&](cudaStream_t st) {
-      chd_launch::complete(s, st, &f->ex, sv, f->Lc, f->Wc, f->Dd, f->Vd, f->Rd, f->ws, f->ldet, f->status);
+      chd_launch::complete(s, st, &f->ex, sv, f->Lc, f->Wc, f->Dd, f->Vd, f->Rd, factored ? f->Qd : nullptr, f->fcs,
+                           f->ws, f->ldet, f->status);
     });
   }
   if (rc != CHD_OK) return rc;
   f->have_S = true;
-  f->have_R = false;  // Rd holds chol(V_k) here; V_k^{-1} is formed on first use
-  f->have_Q = false;
+  f->have_R = false;  // Rd holds chol(V_k) or nothing here; V_k^{-1} is formed on first use
+  // the factored form leaves G_k = P R_k P = chol(P V_k P) in Qd: the Hessian
+  // factor's upper factors of V_k
+  f->have_Q = factored;
   if (fstar) {
     double ld = 0;
     rc = chd_logdet(f, &ld);
@@ -887,6 +912,7 @@ void chd_factor_free(chd_factor* f) {
   if (f->g_in) cudaEventDestroy(f->g_in);
   if (f->g_out) cudaEventDestroy(f->g_out);
   if (f->ws) cudaFree(f->ws);
+  if (f->fcs) cudaFree(f->fcs);
   if (f->act_buf) cudaFree(f->act_buf);
   if (f->inst_sum) cudaFree(f->inst_sum);
   if (f->block) cudaFree(f->block);
@@ -934,6 +960,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   size_t iSl = add(s->sub_lo.data(), s->sub_lo.size() * 4);
   size_t iSh = add(s->sub_hi.data(), s->sub_hi.size() * 4);
   size_t iIs = add(s->inst_sn.data(), s->inst_sn.size() * 8);
+  size_t iFo = add(s->fc_off.data(), s->fc_off.size() * 8);
+  size_t iFf = add(s->fc_fronts.data(), s->fc_fronts.size() * 4);
   std::vector<char> host(off, 0);
   for (auto& p : pcs)
     if (p.bytes) std::memcpy(host.data() + p.off, p.src, p.bytes);
@@ -996,6 +1024,8 @@ chd_status chd_symbolic_upload(chd_symbolic* s) {
   d.sub_lo = reinterpret_cast<const int32_t*>(b + pcs[iSl].off);
   d.sub_hi = reinterpret_cast<const int32_t*>(b + pcs[iSh].off);
   d.inst_sn = reinterpret_cast<const int64_t*>(b + pcs[iIs].off);
+  d.fc_off = reinterpret_cast<const int64_t*>(b + pcs[iFo].off);
+  d.fc_fronts = reinterpret_cast<const int32_t*>(b + pcs[iFf].off);
   d.ninst = (int64_t)s->inst_sn.size() - 1;
   d.f_total = s->f_off[s->nsn];
   d.d_total = s->d_off[s->nsn];

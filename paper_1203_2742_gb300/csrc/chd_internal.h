@@ -63,6 +63,8 @@ struct SymDev {
   // pruned Hessian factor (§5.5): per right-hand side y, act[y * nsn + k] != 0
   // iff Y has a nonzero in the columns of that range; null: every front active
   const uint8_t* act = nullptr;
+  const int64_t* fc_off = nullptr;        // factored completion: scratch offsets (per front)
+  const int32_t* fc_fronts = nullptr;     // factored completion: CTA-handled fronts by level
   const int64_t* inst_sn = nullptr;       // instances x supernode ranges
   int64_t ninst = 1;
   int64_t f_total = 0;               // workspace doubles per right-hand side
@@ -121,6 +123,18 @@ struct chd_symbolic {
   std::vector<int64_t> inst_n, inst_nnz, inst_sn;
   int64_t max_front = 0;
   int tc_mode = 0;  // chd_opts.tc_products
+  // completion with factored update matrices (chd_opts.completion = 1):
+  // fronts with a_k > 0 by depth in the clique tree, parents first; the
+  // per-front sequence runs one CTA per front (fc_fronts, level l at
+  // [fc_lvl[l], fc_lvl[l+1])) or the dense tier (fc_big, fc_big_lvl);
+  // fc_off: scratch offset (doubles) of the front's reduction within its
+  // level; fc_total: largest level's scratch; fc_flops: Cholesky of every
+  // V_k (independent form) and the factored form's arithmetic
+  int completion_mode = 0;
+  std::vector<int64_t> fc_off;
+  std::vector<int32_t> fc_fronts, fc_lvl, fc_big, fc_big_lvl;
+  int64_t fc_total = 0;
+  double fc_flops[2] = {0, 0};
   // device mirror
   SymDev dev;
   void* dev_buf = nullptr;
@@ -219,6 +233,7 @@ struct chd_factor {
   double* scalar = nullptr;  // [0] log det
   int64_t* status = nullptr; // [0] code, [1] supernode, [2] column
   double* ws = nullptr;      // per-right-hand-side front workspace
+  double* fcs = nullptr;     // factored completion: scratch of the reductions (own allocation)
   Exec ex;                   // dense-tier streams and split-K scratch
   double* inst_sum = nullptr;  // per-instance log det sums (batched symbolic objects)
   int64_t ws_rhs = 0;        // capacity in right-hand sides

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "chd_internal.h"
+#include "fc_body.cuh"
 #include "front_views.cuh"
 
 namespace chd {
@@ -652,6 +653,21 @@ __device__ void ihess_up_front(const SymDev& S, int k, const double* Wc, double*
   __syncthreads();
 }
 
+// rows r and R-1-r of the R x C block B (ld) exchanged, CTA-wide
+__device__ void reverse_rows(double* B, int64_t ld, int R, int C) {
+  __syncthreads();
+  const int h = R / 2;
+  for (int e = threadIdx.x; e < h * C; e += NT) {
+    const int r = e % h, c = e / h;
+    double* x = B + r + (int64_t)c * ld;
+    double* y = B + (R - 1 - r) + (int64_t)c * ld;
+    const double t = *x;
+    *x = *y;
+    *y = t;
+  }
+  __syncthreads();
+}
+
 // Algorithm 7.3 for one front (each front needs only S and V_k = S_AA):
 // R = chol(V), Z = R^{-1} S_AN, P = S_NN - Z^T Z = D_NN^{-1},
 // L_AN = -R^{-T} Z, D_NN = P^{-1}, C = chol(D_NN), B = L_AN C.
@@ -670,21 +686,25 @@ __device__ void complete_load_front(const SymDev& S, int k, const double* Sin, d
   __syncthreads();
 }
 
-// Algorithm 7.3 arithmetic for one front whose S-front is loaded.
+// Algorithm 7.3 arithmetic for one front whose S-front is loaded.  With Gq
+// (completion with factored update matrices), G = P R_k P of V_k = R_k R_k^T
+// is read from Gq instead of factoring V_k: the solves then run on S_AN and
+// L_AN with their rows in reversed order (Z^T Z is unchanged).
 __device__ void complete_front(const SymDev& S, int k, const double* Sin, double* Lc, double* Wc,
-                               double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
+                               double* Dd, double* Vd, double* Rd, const double* Gq, double* ws, double* ldet,
                                int64_t* st) {
   FrontInfo f = front_info(S, k, ws);
   const int J = f.J, n = f.n, a = f.a;
   double* V = Vd + S.v_off[k];
-  double* R = Rd + S.v_off[k];
+  double* R = Gq ? const_cast<double*>(Gq) + S.v_off[k] : Rd + S.v_off[k];
   copy_lower(V, a, f.F + n + (int64_t)n * J, J, a);
-  copy_lower(R, a, f.F + n + (int64_t)n * J, J, a);
+  if (!Gq) copy_lower(R, a, f.F + n + (int64_t)n * J, J, a);
   __syncthreads();
-  if (a > 0) cta_potrf_partial(R, a, a, a, st, CHD_ERR_NOT_COMPLETABLE, k, -1);
+  if (a > 0 && !Gq) cta_potrf_partial(R, a, a, a, st, CHD_ERR_NOT_COMPLETABLE, k, -1);
   // T1[n:J] = Z = R^{-1} S_AN
   copy_rect(f.T1 + n, J, f.F + n, J, a, n);
   __syncthreads();
+  if (Gq) reverse_rows(f.T1 + n, J, a, n);
   if (a > 0) cta_trsm_rLT(n, a, DnTW{f.T1 + n, J}, R, a);
   // T1[0:n] (lower) = P = S_NN - Z^T Z
   copy_lower(f.T1, J, f.F, J, n);
@@ -697,6 +717,7 @@ __device__ void complete_front(const SymDev& S, int k, const double* Sin, double
   }
   __syncthreads();
   if (a > 0) cta_trsm_rL(n, a, DnTW{f.T2 + n, J}, R, a);
+  if (Gq) reverse_rows(f.T2 + n, J, a, n);
   // Wc = [P; L_AN]
   for (int e = threadIdx.x; e < J * n; e += NT) {
     int r = e % J, c = e / J;
@@ -846,10 +867,40 @@ __global__ void __launch_bounds__(kScanT) k_active(SymDev S, int32_t* cnt, uint8
 }
 // all CTA-tier fronts at once, one CTA each
 __global__ void __launch_bounds__(NT) k_complete(SymDev S, const double* Sin, double* Lc, double* Wc, double* Dd,
-                                                 double* Vd, double* Rd, double* ws, double* ldet, int64_t* st) {
+                                                 double* Vd, double* Rd, const double* Gq, double* ws, double* ldet,
+                                                 int64_t* st) {
   const int k = S.cta_fronts[blockIdx.x];
   complete_load_front(S, k, Sin, ws);
-  complete_front(S, k, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, st);
+  complete_front(S, k, Sin, Lc, Wc, Dd, Vd, Rd, Gq, ws, ldet, st);
+}
+// Completion with factored update matrices, one level of the clique tree
+// (parents done): G_k = P R_k P of every front of fc_fronts[first ..], one
+// CTA each (fc_body.cuh): gather, Householder reduction of the rows kept
+// from G_parent, then M = S~ L^{-T} and G~ = chol(A~ - M M^T).
+__global__ void __launch_bounds__(NT) k_fc(SymDev S, int first, const double* Sin, double* Gq, double* fcs,
+                                           int64_t* st) {
+  const int k = S.fc_fronts[first + blockIdx.x];
+  const fc::Info f = fc::info(S, k);
+  double* G = Gq + S.v_off[k];
+  double* X = fcs + S.fc_off[k];
+  const double* Gp = Gq + S.v_off[f.p];
+  const int ap = f.Jp - f.np;
+  const int64_t tot = fc::gather_count(f);
+  for (int64_t e = threadIdx.x; e < tot; e += NT) fc::gather_one(f, e, Sin, Gp, ap, X, G);
+  __syncthreads();
+  if (f.q > 0) fc::reduce(f, X, G, st);
+  const int pp = f.a - f.q;
+  if (pp > 0) {
+    double* M = G + f.q;
+    double* At = G + f.q + (int64_t)f.q * f.a;
+    if (f.q > 0) {
+      cta_trsm_rLT(pp, f.q, Dn{M, f.a}, G, f.a);
+      __syncthreads();
+      cta_gemm(pp, pp, f.q, -1.0, Dn{M, f.a}, DnT{M, f.a}, 1.0, Dn{At, f.a}, true);
+      __syncthreads();
+    }
+    cta_potrf_partial(At, f.a, pp, pp, st, CHD_ERR_NOT_COMPLETABLE, k, -1);
+  }
 }
 // Inverses of the cached V_k (inverse Hessian step 2), one CTA per front of
 // `front_list` (no dependencies between fronts; big fronts use the dense
@@ -1019,8 +1070,8 @@ void big_ihess_down(const chd_symbolic* s, const Slot& sl, int m, int k,
 void big_ihess_up(const chd_symbolic* s, const Slot& sl, int m, int k, const double* Wc,
                   double* Y, int64_t ldy, double* ws);
 void big_complete(const chd_symbolic* s, const Slot& sl, int k, const double* Sin,
-                  double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, double* ws, double* ldet,
-                  int64_t* status);
+                  double* Lc, double* Wc, double* Dd, double* Vd, double* Rd, const double* Gq, double* ws,
+                  double* ldet, int64_t* status);
 
 // chain-tier launches (chain_tier.cu): runs of one-column band fronts
 void chain_factor(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* X, double* Lc, double* Wc,
@@ -1055,7 +1106,7 @@ void warp_ihess_down(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int
 void warp_ihess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m, const double* Wc, double* Y,
                    int64_t ldy, double* ws);
 void warp_complete_all(const chd_symbolic* s, cudaStream_t st, const double* Sin, double* Lc, double* Wc,
-                       double* Dd, double* Vd, double* Rd, double* ldet, int64_t* status);
+                       double* Dd, double* Vd, double* Rd, const double* Gq, double* ldet, int64_t* status);
 }  // namespace w32
 namespace w64 {
 void warp_product(const chd_symbolic* s, cudaStream_t st, int t0, int nt, const double* Lc, double* X, double* ws);
@@ -1320,20 +1371,41 @@ void inv_hessian(const chd_symbolic* s, cudaStream_t st, const Exec* ex, int m, 
 // front is independent: the big fronts run on the side streams, all CTA-tier
 // fronts in one launch and all warp-tier fronts in one launch, concurrently.
 void big_complete_load(const chd_symbolic* s, cudaStream_t st, int k, const double* Sin, double* ws);
+void big_fc(const chd_symbolic* s, const Slot& sl, int k, const double* Sin, double* Gq, double* fcs,
+            int64_t* status);
+// Algorithm 7.3 over all fronts (independent).  With Gq (chd_opts.completion
+// = 1), first the factored update matrices of Algorithm 4.3: G_k = P R_k P
+// for every front, level by level from the roots (one launch of k_fc per
+// level, dense-tier sequences on the side streams), then the fronts use G_k.
 void complete(const chd_symbolic* s, cudaStream_t st, const Exec* ex, const double* Sin, double* Lc, double* Wc,
-              double* Dd, double* Vd, double* Rd, double* ws, double* ldet, int64_t* status) {
+              double* Dd, double* Vd, double* Rd, double* Gq, double* fcs, double* ws, double* ldet,
+              int64_t* status) {
+  if (Gq) {
+    const int levels = (int)s->fc_lvl.size() - 1;
+    for (int l = 0; l < levels; ++l) {
+      const int b0 = s->fc_big_lvl[l], b1 = s->fc_big_lvl[l + 1];
+      const int c0 = s->fc_lvl[l], c1 = s->fc_lvl[l + 1];
+      BigFork bf{ex, st};
+      bf.run(b1 - b0, [&](int i, const Slot& sl) { big_fc(s, sl, s->fc_big[b0 + i], Sin, Gq, fcs, status); });
+      if (c1 > c0) {
+        k_fc<<<c1 - c0, NT, 0, st>>>(s->dev, c0, Sin, Gq, fcs, status);
+        count();
+      }
+      bf.join_now();
+    }
+  }
   std::vector<int32_t> bigs = s->big_fronts;  // dense fronts and leaf groups
   for (int64_t g0 : s->grp_first) bigs.push_back((int32_t)g0);
   BigFork bf{ex, st};
   bf.run((int)bigs.size(), [&](int i, const Slot& sl) {
     big_complete_load(s, sl.st, bigs[i], Sin, ws);
-    big_complete(s, sl, bigs[i], Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+    big_complete(s, sl, bigs[i], Sin, Lc, Wc, Dd, Vd, Rd, Gq, ws, ldet, status);
   });
   if (s->dev.cta_count > 0) {
-    k_complete<<<(int)s->dev.cta_count, NT, 0, st>>>(s->dev, Sin, Lc, Wc, Dd, Vd, Rd, ws, ldet, status);
+    k_complete<<<(int)s->dev.cta_count, NT, 0, st>>>(s->dev, Sin, Lc, Wc, Dd, Vd, Rd, Gq, ws, ldet, status);
     count();
   }
-  if (s->dev.warp_count > 0) w32::warp_complete_all(s, st, Sin, Lc, Wc, Dd, Vd, Rd, ldet, status);
+  if (s->dev.warp_count > 0) w32::warp_complete_all(s, st, Sin, Lc, Wc, Dd, Vd, Rd, Gq, ldet, status);
   bf.join_now();
 }
 void big_inv_v(const chd_symbolic* s, const Slot& sl, int k, const double* Vd,

@@ -309,12 +309,87 @@ void chd_opts_default(chd_opts* o) {
   o->chain_runs = 1;
 }
 
+// Plan of the completion with factored update matrices (Algorithm 4.3 in the
+// supernodal form of §7.2): V_k = R_k R_k^T is propagated from the parent p
+// of k.  Of A_k, the q_k rows in A_p (positions >= n_p of J_p) take their
+// factor from rows of R_p, re-triangularised by Householder reflections; the
+// p_k = a_k - q_k rows in N_p are added by a triangular solve and a Cholesky
+// factorisation.  Held reversed (G_k = P R_k P lower, P the order reversal),
+// row t < q_k of G_k comes from row rho_t = J_p - 1 - pos(A_k[a_k - 1 - t])
+// of G_p; the reduction works on the q_k x w_k rows, w_k = rho_{q_k - 1} + 1.
+// Fronts are grouped by depth in the clique tree (parents first); a leaf
+// group's members share one A_k and are handled by its first member.  Per
+// depth level the scratch of the reductions is laid out front after front.
+// Flop counts: the independent form's Cholesky of every V_k (a^3/3) against
+// the factored form (reflections, solve, update and Cholesky of the p_k
+// block).
+void factored_completion_plan(chd_symbolic* s) {
+  const int64_t nsn = s->nsn;
+  s->fc_off.assign(nsn, 0);
+  s->fc_fronts.clear();
+  s->fc_lvl.assign(1, 0);
+  s->fc_big.clear();
+  s->fc_big_lvl.assign(1, 0);
+  s->fc_total = 0;
+  s->fc_flops[0] = s->fc_flops[1] = 0.0;
+  vector<int32_t> depth(nsn, 0);
+  int32_t maxd = 0;
+  for (int64_t k = nsn - 1; k >= 0; --k) {
+    const int64_t p = s->sn_par[k];
+    depth[k] = p >= 0 ? depth[p] + 1 : 0;
+    maxd = std::max(maxd, depth[k]);
+  }
+  vector<vector<int32_t>> by_depth(maxd + 1);
+  for (int64_t k = 0; k < nsn; ++k) {
+    const int64_t nk = s->sn_ptr[k + 1] - s->sn_ptr[k];
+    const int64_t a = s->rows_ptr[k + 1] - s->rows_ptr[k] - nk;
+    const bool member = s->grp_of[k] >= 0 && s->grp_first[s->grp_of[k]] != k;
+    if (a == 0 || member) continue;
+    by_depth[depth[k]].push_back((int32_t)k);
+  }
+  for (int32_t d = 0; d <= maxd; ++d) {
+    int64_t used = 0;
+    for (int32_t k : by_depth[d]) {
+      const int64_t nk = s->sn_ptr[k + 1] - s->sn_ptr[k];
+      const int64_t a = s->rows_ptr[k + 1] - s->rows_ptr[k] - nk;
+      const int64_t p = s->sn_par[k];
+      const int64_t np = s->sn_ptr[p + 1] - s->sn_ptr[p];
+      const int64_t Jp = s->rows_ptr[p + 1] - s->rows_ptr[p];
+      const int32_t* rel = s->rel.data() + s->rows_ptr[k] + nk;
+      int64_t q = 0;
+      for (int64_t r = 0; r < a; ++r) q += rel[r] >= np ? 1 : 0;
+      const int64_t w = q > 0 ? Jp - rel[a - q] : 0;
+      s->fc_off[k] = used;
+      used += (q * w + 3) & ~int64_t(3);
+      const double da = (double)a, dq = (double)q, dp = (double)(a - q);
+      double hh = 0.0;
+      for (int64_t t = 0; t < q; ++t) {
+        const int64_t rho = Jp - 1 - rel[a - 1 - t];
+        if (rho > t) hh += 4.0 * (double)(rho - t + 1) * (double)(q - t);
+      }
+      s->fc_flops[0] += da * da * da / 3;
+      s->fc_flops[1] += hh + dp * dq * dq + dp * dp * dq + dp * dp * dp / 3;
+      // the reflections are a sequential chain: the dense tier takes fronts
+      // with a large reduction or a large p-block
+      if (s->is_big[k] || a > 256)
+        s->fc_big.push_back(k);
+      else
+        s->fc_fronts.push_back(k);
+    }
+    s->fc_total = std::max(s->fc_total, used);
+    s->fc_lvl.push_back((int32_t)s->fc_fronts.size());
+    s->fc_big_lvl.push_back((int32_t)s->fc_big.size());
+  }
+}
+
 chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* rowind,
                               const chd_opts& opts, chd_symbolic* s) {
   if (n < 1 || !colptr || !rowind) return CHD_ERR_INVALID;
   vector<vector<int32_t>> adj;
   if (!build_adjacency(n, colptr, rowind, adj)) return CHD_ERR_INVALID;
   s->tc_mode = opts.tc_products < 0 ? -1 : (opts.tc_products > 0 ? 1 : 0);
+  if (opts.completion < 0 || opts.completion > 1) return CHD_ERR_INVALID;
+  s->completion_mode = opts.completion;
 
   // ---- ordering -----------------------------------------------------------
   vector<int64_t> perm0;
@@ -852,5 +927,6 @@ chd_status chd_symbolic_build(int64_t n, const int64_t* colptr, const int32_t* r
       }
     }
   }
+  factored_completion_plan(s);
   return CHD_OK;
 }

@@ -797,9 +797,12 @@ __device__ void ihess_up_front(const SymDev& S, const Fr& f, const Fr& prev, con
 
 // S-front of the completion: S_NN and S_AN from the input's columns N_k,
 // V_k = S_{A_k A_k} from its later columns (a submatrix of S, Algorithm 7.3),
-// so the front depends on no other front.
+// so the front depends on no other front.  With Gq (factored update
+// matrices, Algorithm 4.3) the factor G = P R_k P of V_k = R_k R_k^T comes
+// from Gq and the solves run on S_AN and L_AN with reversed rows.
 __device__ void complete_front(const SymDev& S, int k, const double* Sin, double* Lc, double* Wc, double* Dd,
-                               double* Vd, double* Rd, double* ldet, int64_t* st, const Smem& m, int lane) {
+                               double* Vd, double* Rd, const double* Gq, double* ldet, int64_t* st, const Smem& m,
+                               int lane) {
   Fr f = fr(S, k, nullptr);
   const int J = f.J, n = f.n, a = f.a;
   const int32_t* A = S.rows + S.rows_ptr[k] + n;
@@ -820,17 +823,27 @@ __device__ void complete_front(const SymDev& S, int k, const double* Sin, double
   }
   fsync();
   PkBlk Rv{m.F, J, n};
-  if (a > 0) wpotrf(a, Rv, m.rv, st, CHD_ERR_NOT_COMPLETABLE, k, -1, lane);
-  for (int e = lane; e < a * a; e += TPF) {
-    int r, s;
-    divmod(e, a, r, s);
-    if (r >= s) R[r + s * a] = m.F[pk(J, n + r, n + s)];
+  if (Gq) {
+    const double* G = Gq + S.v_off[k];
+    for (int e = lane; e < a * a; e += TPF) {
+      int r, s;
+      divmod(e, a, r, s);
+      if (r >= s) m.F[pk(J, n + r, n + s)] = G[r + s * a];
+    }
+    for (int r = lane; r < a; r += TPF) m.rv[r] = 1.0 / G[r + r * a];
+  } else {
+    if (a > 0) wpotrf(a, Rv, m.rv, st, CHD_ERR_NOT_COMPLETABLE, k, -1, lane);
+    for (int e = lane; e < a * a; e += TPF) {
+      int r, s;
+      divmod(e, a, r, s);
+      if (r >= s) R[r + s * a] = m.F[pk(J, n + r, n + s)];
+    }
   }
-  // A1 = Z = R^{-1} S_AN
+  // A1 = Z = R^{-1} S_AN (rows reversed with Gq)
   for (int e = lane; e < a * n; e += TPF) {
     int r, c;
     divmod(e, a, r, c);
-    m.A1[r + c * WJ] = m.F[pk(J, n + r, c)];
+    m.A1[r + c * WJ] = m.F[pk(J, n + (Gq ? a - 1 - r : r), c)];
   }
   fsync();
   if (a > 0) wtrsm_r(n, a, BkTW{m.A1, WJ}, Rv, m.rv, true, lane);
@@ -850,6 +863,17 @@ __device__ void complete_front(const SymDev& S, int k, const double* Sin, double
   }
   fsync();
   if (a > 0) wtrsm_r(n, a, BkTW{m.A2, WJ}, Rv, m.rv, false, lane);
+  if (Gq) {  // L_AN back to the order of A_k
+    const int h = a / 2;
+    for (int e = lane; e < h * n; e += TPF) {
+      int r, c;
+      divmod(e, h, r, c);
+      const double t = m.A2[r + c * WJ];
+      m.A2[r + c * WJ] = m.A2[(a - 1 - r) + c * WJ];
+      m.A2[(a - 1 - r) + c * WJ] = t;
+    }
+    fsync();
+  }
   double* W = Wc + f.base;
   for (int e = lane; e < n * n; e += TPF) {
     int r, c;
@@ -1031,13 +1055,13 @@ __global__ void __launch_bounds__(WPB * TPF) kw_ihess_up(SymDev S, int task0, in
 // all warp-tier fronts at once, one warp each (the completion has no
 // dependencies between fronts)
 __global__ void __launch_bounds__(WPB * TPF) kw_complete(SymDev S, const double* Sin, double* Lc, double* Wc,
-                                                        double* Dd, double* Vd, double* Rd, double* ldet,
-                                                        int64_t* st) {
+                                                        double* Dd, double* Vd, double* Rd, const double* Gq,
+                                                        double* ldet, int64_t* st) {
   const int w = threadIdx.x / TPF, lane = threadIdx.x % TPF;
   const int64_t i = (int64_t)blockIdx.x * WPB + w;
   if (i >= S.warp_count) return;
   const Smem m = smem_for_warp(w, 0);
-  complete_front(S, S.warp_fronts[i], Sin, Lc, Wc, Dd, Vd, Rd, ldet, st, m, lane);
+  complete_front(S, S.warp_fronts[i], Sin, Lc, Wc, Dd, Vd, Rd, Gq, ldet, st, m, lane);
 }
 #endif
 
@@ -1087,8 +1111,9 @@ void warp_ihess_up(const chd_symbolic* s, cudaStream_t st, int t0, int nt, int m
 }
 #if WT_J == 32
 void warp_complete_all(const chd_symbolic* s, cudaStream_t st, const double* Sin, double* Lc, double* Wc,
-                       double* Dd, double* Vd, double* Rd, double* ldet, int64_t* status) {
-  kw_complete<<<wgrid((int)s->dev.warp_count, 1), WPB * TPF, 0, st>>>(s->dev, Sin, Lc, Wc, Dd, Vd, Rd, ldet, status);
+                       double* Dd, double* Vd, double* Rd, const double* Gq, double* ldet, int64_t* status) {
+  kw_complete<<<wgrid((int)s->dev.warp_count, 1), WPB * TPF, 0, st>>>(s->dev, Sin, Lc, Wc, Dd, Vd, Rd, Gq, ldet,
+                                                                      status);
   chd_launch::count_launch();
 }
 #endif

@@ -76,11 +76,14 @@ def test_not_positive_definite_reported(name):
     assert OD.rel_err(n, cp, ri, g, OD.gradient(n, cp, ri, x_ok)) < 1e-10
 
 
+@pytest.mark.parametrize("completion", ["independent", "factored"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_not_completable_reported(name):
+def test_not_completable_reported(name, completion):
+    """Both completion forms: the factored one (Algorithm 4.3) meets the
+    failing pivot while propagating R_k or in the front's own Cholesky."""
     B = lib()
     mk, opts, col = CASES[name]
-    sym = B.Symbolic(*mk(), **opts)
+    sym = B.Symbolic(*mk(), completion=completion, **opts)
     n, cp, ri = sym.n, sym.colptr, sym.rowind
     rng = np.random.default_rng(6)
     s_ok = W.projected_gram(n, cp, ri, rng.standard_normal((n, 10)), 0.5)

@@ -24,9 +24,10 @@ def torch():
 
 
 class Case:
-    def __init__(self, pattern, ordering="natural", perm=None, relax=0, seed=0, x=None, big=None, split=0, tc=0):
+    def __init__(self, pattern, ordering="natural", perm=None, relax=0, seed=0, x=None, big=None, split=0, tc=0,
+                 **extra):
         self.B = lib()
-        kw = {} if big is None else dict(big_rows=big[0], big_cols=big[1])
+        kw = dict(extra) if big is None else dict(extra, big_rows=big[0], big_cols=big[1])
         kw["split_cols"] = split
         kw["tc_products"] = tc
         self.sym = self.B.Symbolic(*pattern, ordering=ordering, perm=perm, relax=relax, **kw)
@@ -51,47 +52,48 @@ class Case:
         return OD.rel_err(self.n, self.cp, self.ri, a, ref)
 
 
-def small_cases():
+def small_cases(**extra):
+    """The parity cases; `extra` analysis options go to every one."""
     return {
-        "band200_w8": lambda: Case(W.band(200, 8), seed=0),
-        "band40_w1": lambda: Case(W.band(40, 1), seed=1),
-        "arrow60_w7": lambda: Case(W.arrow(60, 7), seed=2),
+        "band200_w8": lambda: Case(W.band(200, 8), seed=0, **extra),
+        "band40_w1": lambda: Case(W.band(40, 1), seed=1, **extra),
+        "arrow60_w7": lambda: Case(W.arrow(60, 7), seed=2, **extra),
         "grid14_nd": lambda: Case(W.grid2d(14, 14), ordering="user",
-                                  perm=W.nested_dissection((14, 14), leaf=6), seed=3),
+                                  perm=W.nested_dissection((14, 14), leaf=6), seed=3, **extra),
         "grid3d_5": lambda: Case(W.grid3d(5, 5, 5), ordering="user",
-                                 perm=W.nested_dissection((5, 5, 5), leaf=8), seed=4),
+                                 perm=W.nested_dissection((5, 5, 5), leaf=8), seed=4, **extra),
         "er300_mindeg_relax16": lambda: Case(W.erdos_renyi(300, 0.02, np.random.default_rng(5)),
-                                             ordering="mindeg", relax=16, seed=5),
-        "dense70": lambda: Case(W.band(70, 69), seed=6),
-        "diag30": lambda: Case(W.band(30, 0), seed=7),
-        "wide_front": lambda: Case(W.arrow(200, 120), seed=8),
+                                             ordering="mindeg", relax=16, seed=5, **extra),
+        "dense70": lambda: Case(W.band(70, 69), seed=6, **extra),
+        "diag30": lambda: Case(W.band(30, 0), seed=7, **extra),
+        "wide_front": lambda: Case(W.arrow(200, 120), seed=8, **extra),
         # the same kinds of pattern with low thresholds, so that many fronts run
         # through the multi-CTA dense tier and hand over to and from the per-task tier
         "dense_tier_grid": lambda: Case(W.grid2d(16, 16), ordering="user",
-                                        perm=W.nested_dissection((16, 16), leaf=6), seed=9, big=(20, 8)),
+                                        perm=W.nested_dissection((16, 16), leaf=6), seed=9, **extra, big=(20, 8)),
         "dense_tier_er": lambda: Case(W.erdos_renyi(300, 0.02, np.random.default_rng(5)),
-                                      ordering="mindeg", relax=16, seed=10, big=(40, 20)),
-        "dense_tier_full": lambda: Case(W.band(150, 149), seed=11, big=(64, 64)),
-        "dense_tier_arrow": lambda: Case(W.arrow(260, 100), seed=12, big=(90, 70)),
+                                      ordering="mindeg", relax=16, seed=10, **extra, big=(40, 20)),
+        "dense_tier_full": lambda: Case(W.band(150, 149), seed=11, **extra, big=(64, 64)),
+        "dense_tier_arrow": lambda: Case(W.arrow(260, 100), seed=12, **extra, big=(90, 70)),
         # wide supernodes split into chains (dense, CTA and warp pieces)
-        "split_dense": lambda: Case(W.band(150, 149), seed=13, big=(64, 64), split=24),
-        "split_arrow": lambda: Case(W.arrow(200, 90), seed=14, split=8),
+        "split_dense": lambda: Case(W.band(150, 149), seed=13, **extra, big=(64, 64), split=24),
+        "split_arrow": lambda: Case(W.arrow(200, 90), seed=14, **extra, split=8),
         # wide warp tier (|N| <= 8, 32 < |J| <= 64, chains only): two chains
         # handing over to the CTA tier at the root, and thin leaves of one parent
         # (CTA tier)
-        "band300_w40": lambda: Case(W.band(300, 40), seed=15),
-        "arrow150_w48": lambda: Case(W.arrow(150, 48), seed=16),
-        "band120_w63": lambda: Case(W.band(120, 63), seed=17),
+        "band300_w40": lambda: Case(W.band(300, 40), seed=15, **extra),
+        "arrow150_w48": lambda: Case(W.arrow(150, 48), seed=16, **extra),
+        "band120_w63": lambda: Case(W.band(120, 63), seed=17, **extra),
         # every dense-tier product with at least 64 x 16 outputs on the tensor
         # cores (FP64-accurate digit products), on the dense-tier cases above
         "tc_dense_grid": lambda: Case(W.grid2d(16, 16), ordering="user",
-                                      perm=W.nested_dissection((16, 16), leaf=6), seed=9, big=(20, 8), tc=1),
+                                      perm=W.nested_dissection((16, 16), leaf=6), seed=9, **extra, big=(20, 8), tc=1),
         "tc_dense_er": lambda: Case(W.erdos_renyi(300, 0.02, np.random.default_rng(5)),
-                                    ordering="mindeg", relax=16, seed=10, big=(40, 20), tc=1),
-        "tc_dense_full": lambda: Case(W.band(150, 149), seed=11, big=(64, 64), tc=1),
-        "tc_dense_arrow": lambda: Case(W.arrow(260, 100), seed=12, big=(90, 70), tc=1),
-        "tc_split_dense": lambda: Case(W.band(150, 149), seed=13, big=(64, 64), split=24, tc=1),
-        "tc_wide_arrow": lambda: Case(W.arrow(400, 330), seed=18, tc=1),
+                                    ordering="mindeg", relax=16, seed=10, **extra, big=(40, 20), tc=1),
+        "tc_dense_full": lambda: Case(W.band(150, 149), seed=11, **extra, big=(64, 64), tc=1),
+        "tc_dense_arrow": lambda: Case(W.arrow(260, 100), seed=12, **extra, big=(90, 70), tc=1),
+        "tc_split_dense": lambda: Case(W.band(150, 149), seed=13, **extra, big=(64, 64), split=24, tc=1),
+        "tc_wide_arrow": lambda: Case(W.arrow(400, 330), seed=18, **extra, tc=1),
     }
 
 

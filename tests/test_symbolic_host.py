@@ -419,3 +419,25 @@ def test_batch_with_nested_dissection_orderings():
         (ni, cp, ri), perm = sb.instance_pattern(i)
         s1 = B.Symbolic(*p, perm=q)
         assert (perm == s1.perm).all() and (cp == s1.colptr).all() and (ri == s1.rowind).all()
+
+
+def test_factored_completion_plan_flops():
+    """The factored completion's propagation work (Algorithm 4.3: one
+    reflection per kept row whose columns were mixed, then the rows of A_k in
+    N_parent) against the independent Cholesky of every V_k (a^3 / 3).  On a
+    band each front drops one row of its parent's factor: the reflections
+    cost O(a^2) per front, less than a^3 / 3 once a is large (w = 40), more
+    for a narrow band (w = 8, where the per-row constant dominates).  Split
+    supernodes delete no rows: only the N_parent block remains."""
+    B = lib()
+    f40 = B.Symbolic(*W.band(300, 40), completion="factored").completion_flops()
+    assert 0 < f40["factored"] < 0.5 * f40["independent"]
+    # independent: 259 one-column fronts with a = 40 below the root (its 41 columns, a = 0)
+    assert f40["independent"] == pytest.approx(259 * 40 ** 3 / 3)
+    f8 = B.Symbolic(*W.band(300, 8), completion="factored").completion_flops()
+    assert f8["factored"] > f8["independent"]
+    # a band propagates along one chain: one level per front below the root
+    assert f40["levels"] == 259
+    fs = B.Symbolic(*W.band(150, 149), big_rows=64, big_cols=64, split_cols=24,
+                    completion="factored").completion_flops()
+    assert fs["factored"] < fs["independent"]
