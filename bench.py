@@ -598,6 +598,24 @@ def run_ours(args, wl, rank, world, local_rank):
         "inv_hessian": time_op(lambda: fac.inv_hessian(T, out=YI), reps),
         "completion": time_op(lambda: fx.recomplete(S, want_fstar=False), reps),
     }
+    # ---- the two completion forms (chd_opts.completion): independent fronts
+    # (the step above) and factored update matrices (Algorithm 4.3) ----
+    sym_f = make_symbolic(B, wl, **dict(cfg, completion="factored"))
+    fxf, _ = sym_f.complete(S)
+    for _ in range(2):
+        fxf.recomplete(S, want_fstar=False)
+    fact_ms = time_op(lambda: fxf.recomplete(S, want_fstar=False), reps)
+    xf, xi = fxf.product(), fx.product()
+    cflops = sym_f.completion_flops()
+    completion_forms = {
+        "independent_ms": ops_ms["completion"], "factored_ms": fact_ms,
+        "flops_chol_v": cflops["independent"], "flops_factored_propagation": cflops["factored"],
+        "propagation_levels": cflops["levels"],
+        "xhat_rel_diff": float(torch.linalg.vector_norm(xf - xi) / torch.linalg.vector_norm(xi)),
+        "note": "flops: the part the forms do differently (Cholesky of every V_k against the propagation of "
+                "V_k = R_k R_k^T from the parent); the rest of the completion is common",
+    }
+    del fxf, sym_f, xf, xi
     fp64_peak = B.chd_probe_fp64_peak() / 1e3  # TFLOP/s
     hess_flops = fl["hessian"] * m
     achieved = hess_flops / (ops_ms["hessian"] * 1e-3) / 1e12
@@ -737,6 +755,7 @@ def run_ours(args, wl, rank, world, local_rank):
             # T written, m matrices on V, plus one read of the factor's L and S) over its time
             "hbm": hbm_line(8.0 * (2 * m * nnz + 2 * nnz), ops_ms["hessian"]),
             "instances": count,
+            "completion_forms": completion_forms,
             "autotune": tune,
             "batched_vs_one_at_a_time": sequential,
             "step_tflops_fp64_equivalent": step_flops / (ms_per_step * 1e-3) / 1e12,
@@ -829,7 +848,7 @@ def run_serve(args, wl):
 
 OTHER_KEYS = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "higher_is_better", "dtype", "config",
               "roofline", "cpu_baseline", "accuracy", "e2e", "gpu_launches", "clocks", "ops_ms", "ops_evals_per_s",
-              "autotune", "batched_vs_one_at_a_time", "instances")
+              "autotune", "batched_vs_one_at_a_time", "instances", "completion_forms")
 
 
 def other_workloads(args, rank, world, local_rank):

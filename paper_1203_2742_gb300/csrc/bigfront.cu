@@ -690,11 +690,24 @@ __global__ void __launch_bounds__(BT) mk_fc_gather(SymDev S, int k, const double
   for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT)
     fc::gather_one(f, e, Sin, Gp, f.Jp - f.np, X, G);
 }
-// ... and its Householder reduction (a chain of dependent reflections: one CTA)
-constexpr int FCT = 1024;
-__global__ void __launch_bounds__(FCT) k_fc_reduce(SymDev S, int k, double* Gq, double* fcs, int64_t* st) {
+// ... its Householder reduction in panels of fc::NB rows: one panel among
+// itself (one CTA), its reflectors V and T after X in the front's scratch
+__global__ void __launch_bounds__(BT) k_fc_panel(SymDev S, int k, int t0, int t1, int L, double* fcs, int64_t* st) {
   const fc::Info f = fc::info(S, k);
-  fc::reduce(f, fcs + S.fc_off[k], Gq + S.v_off[k], st);
+  double* X = fcs + S.fc_off[k];
+  double* V = X + (int64_t)f.q * f.w;
+  fc::panel(f, X, t0, t1, L, V, V + (int64_t)f.w * fc::NB, st);
+}
+// ... and the reduced X's lower triangle into G_k's first q columns
+__global__ void __launch_bounds__(BT) mk_fc_copy(SymDev S, int k, double* Gq, const double* fcs) {
+  const fc::Info f = fc::info(S, k);
+  const double* X = fcs + S.fc_off[k];
+  double* G = Gq + S.v_off[k];
+  const int64_t tot = (int64_t)f.q * f.q;
+  for (int64_t e = blockIdx.x * (int64_t)EW + threadIdx.x; e < min(tot, (blockIdx.x + 1) * (int64_t)EW); e += BT) {
+    const int r = (int)(e % f.q), c = (int)(e / f.q);
+    if (r >= c) G[r + (int64_t)c * f.a] = X[(int64_t)r * f.w + c];
+  }
 }
 __global__ void k_logdet_diag(const double* F, int64_t ld, int n, double* out) {
   __shared__ double red[BT];
@@ -1407,9 +1420,12 @@ void group_complete(const chd_symbolic* s, const Ctx& st, int g, const double* S
 }
 
 // Factored update matrices (Algorithm 4.3) for front k of the dense tier,
-// its parent's G done: gather, the Householder reduction of the rows kept
-// from G_parent, then M = S~ L^{-T}, G~ = chol(A~ - M M^T) with the blocked
-// multi-CTA kernels (fc_body.cuh has the layout).
+// its parent's G done: gather; the Householder reduction of the rows kept
+// from G_parent in panels of fc::NB rows (a panel with nothing to annihilate
+// launches nothing), the rows below each panel updated by
+// X[t1:, C] -= (X[t1:, C] V T) V^T over the panel's columns C; then
+// M = S~ L^{-T}, G~ = chol(A~ - M M^T) with the blocked multi-CTA kernels
+// (fc_body.cuh has the layout).
 void fc_front(const chd_symbolic* s, const Ctx& st, int k, const double* Sin, double* Gq, double* fcs,
               int64_t* status) {
   const int64_t nk = s->sn_ptr[k + 1] - s->sn_ptr[k];
@@ -1425,8 +1441,32 @@ void fc_front(const chd_symbolic* s, const Ctx& st, int k, const double* Sin, do
   double* G = Gq + s->v_off[k];
   CHD_EW(mk_fc_gather, (int64_t)q * w + (int64_t)pp * a, 1, st, s->dev, k, Sin, Gq, fcs);
   if (q > 0) {
-    k_fc_reduce<<<1, FCT, 0, st>>>(s->dev, k, Gq, fcs, status);
-    chd_launch::count_launch();
+    constexpr int NB = fc::NB;
+    double* X = fcs + s->fc_off[k];
+    double* V = X + (int64_t)q * w;
+    double* T = V + (int64_t)w * NB;
+    double* VT = T + NB * NB;
+    double* Y = VT + (int64_t)w * NB;
+    auto rho = [&](int t) { return Jp - 1 - rel[a - 1 - t]; };
+    for (int t0 = 0; t0 < q; t0 += NB) {
+      const int t1 = std::min(q, t0 + NB);
+      bool any = false;
+      for (int t = t0; t < t1 && !any; ++t) any = rho(t) > t;
+      if (!any) continue;
+      const int L = rho(t1 - 1) - t0 + 1;
+      k_fc_panel<<<1, BT, 0, st>>>(s->dev, k, t0, t1, L, fcs, status);
+      chd_launch::count_launch();
+      if (t1 < q) {
+        // X row-major (ld w): rows t1.., columns t0.. as the transpose of a
+        // column-major block
+        const int rows = q - t1;
+        double* Xb = X + (int64_t)t1 * w + t0;
+        gemm(st, 1, L, NB, NB, 1.0, Dn{V, L}, 0, Dn{T, NB}, 0, 0.0, Dn{VT, L}, 0, false);
+        gemm(st, 1, rows, NB, L, 1.0, DnT{Xb, w}, 0, Dn{VT, L}, 0, 0.0, Dn{Y, rows}, 0, false);
+        gemm(st, 1, rows, L, NB, -1.0, Dn{Y, rows}, 0, DnT{V, L}, 0, 1.0, DnTW{Xb, w}, 0, false);
+      }
+    }
+    CHD_EW(mk_fc_copy, (int64_t)q * q, 1, st, s->dev, k, Gq, fcs);
   }
   if (pp > 0) {
     double* M = G + q;

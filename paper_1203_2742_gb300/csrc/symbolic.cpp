@@ -359,8 +359,14 @@ void factored_completion_plan(chd_symbolic* s) {
       int64_t q = 0;
       for (int64_t r = 0; r < a; ++r) q += rel[r] >= np ? 1 : 0;
       const int64_t w = q > 0 ? Jp - rel[a - q] : 0;
+      // the reflections are a sequential chain: the dense tier takes fronts
+      // with a large reduction or a large p-block, in panels of 32 rows
+      // (scratch: X, then the panel's reflectors V, its T, V T and the
+      // trailing rows' product)
+      const bool big = s->is_big[k] || a > 256;
       s->fc_off[k] = used;
       used += (q * w + 3) & ~int64_t(3);
+      if (big && q > 0) used += 32 * (2 * w + q + 32);
       const double da = (double)a, dq = (double)q, dp = (double)(a - q);
       double hh = 0.0;
       for (int64_t t = 0; t < q; ++t) {
@@ -369,9 +375,7 @@ void factored_completion_plan(chd_symbolic* s) {
       }
       s->fc_flops[0] += da * da * da / 3;
       s->fc_flops[1] += hh + dp * dq * dq + dp * dp * dq + dp * dp * dp / 3;
-      // the reflections are a sequential chain: the dense tier takes fronts
-      // with a large reduction or a large p-block
-      if (s->is_big[k] || a > 256)
+      if (big)
         s->fc_big.push_back(k);
       else
         s->fc_fronts.push_back(k);
