@@ -105,6 +105,8 @@ _lib.chd_factor_workspace_bytes.argtypes = [_p, C.POINTER(C.c_size_t)]
 _lib.chd_factor_workspace_bytes.restype = C.c_int
 _lib.chd_factor_set_graphs.argtypes = [_p, C.c_int]
 _lib.chd_factor_set_graphs.restype = C.c_int
+_lib.chd_factor_set_graph_limit.argtypes = [_p, C.c_int64]
+_lib.chd_factor_set_graph_limit.restype = C.c_int
 _lib.chd_factor_free.argtypes = [_p]
 _lib.chd_factor_free.restype = None
 _lib.chd_product.argtypes = [_p, _p, _p]
@@ -665,6 +667,10 @@ class Factor:
     def set_graphs(self, on):
         """Replay repeated calls with the same arguments from CUDA graphs (default on)."""
         _check(_lib.chd_factor_set_graphs(self._h, 1 if on else 0), "chd_factor_set_graphs")
+
+    def set_graph_limit(self, launches):
+        """Longest launch sequence captured into a graph (default 2^20)."""
+        _check(_lib.chd_factor_set_graph_limit(self._h, int(launches)), "chd_factor_set_graph_limit")
 
     def workspace_bytes(self):
         v = C.c_size_t()

@@ -255,7 +255,6 @@ void drop_graph(GraphSlot& g) {
 
 // Sequences longer than this are never captured: instantiating a graph of
 // tens of thousands of nodes costs seconds, more than replays save.
-constexpr int64_t kGraphMaxLaunches = 8192;
 
 template <class Body>
 chd_status run_sequence(chd_factor* f, GraphKind kind, GraphKey key, Body&& body) {
@@ -273,7 +272,7 @@ chd_status run_sequence(chd_factor* f, GraphKind kind, GraphKey key, Body&& body
     g.seen = true;
     g.capture_failed = false;
   }
-  if (!same || g.capture_failed || g.launches > kGraphMaxLaunches) {
+  if (!same || g.capture_failed || g.launches > f->graph_limit) {
     const int64_t l0 = chd_launch::launches();
     body(f->stream);
     g.launches = chd_launch::launches() - l0;  // length of the direct run
@@ -864,6 +863,12 @@ chd_status chd_factor_set_graphs(chd_factor* f, int on) {
     for (auto& g : f->graphs) drop_graph(g);
   }
   f->graphs_on = on && f->gs && f->g_in && f->g_out;
+  return CHD_OK;
+}
+
+chd_status chd_factor_set_graph_limit(chd_factor* f, int64_t max_launches) {
+  if (!f || max_launches < 0) return CHD_ERR_INVALID;
+  f->graph_limit = max_launches;
   return CHD_OK;
 }
 

@@ -76,6 +76,39 @@ __device__ __forceinline__ double window_row_dot(const double (*W)[WS + 1], int 
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);
   return acc;
 }
+// The thread's share of row tid / TPR of the symmetric a x a block B (lower
+// triangle stored column-major, ld a): entries s = part, part + TPR, ...
+// loaded into registers at once (independent loads, one memory latency),
+// so that a step can issue them before its synchronised work and use them
+// after it.  Zero beyond a.
+constexpr int PF = AMAX / TPR;
+struct RowPart {
+  double v[PF];
+};
+__device__ __forceinline__ RowPart load_row_part(const double* B, int a, int tid) {
+  RowPart p;
+  const int r = tid / TPR, part = tid % TPR;
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    const int s = part + u * TPR;
+    p.v[u] = (r < a && s < a) ? __ldg(B + (r >= s ? r + (int64_t)s * a : s + (int64_t)r * a)) : 0.0;
+  }
+  return p;
+}
+// sum over the row's entries of v[s] * x[s] * scale, reduced over the TPR
+// threads of the row (valid where tid % TPR == 0)
+__device__ __forceinline__ double row_part_dot(const RowPart& p, const double* x, int a, double scale, int tid) {
+  const int part = tid % TPR;
+  double acc = 0.0;
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    const int s = part + u * TPR;
+    if (s < a) acc = fma(p.v[u], x[s] * scale, acc);
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  return acc;
+}
 // sum over r < a of term(r), the same value in every thread (each warp
 // reduces all terms)
 template <class Term>
@@ -231,6 +264,8 @@ __global__ void __launch_bounds__(CT) kc_hess_up(SymDev S, int task0, const doub
       wv = Wc[base + (a + 1) + tid];
     }
     if (ay && !ay[i]) continue;  // the same decision in every thread
+    // V_i's row part, loaded now and used after the window update
+    const RowPart vrow = load_row_part(Vd + R.v0 + (int64_t)i * R.vstride, a, tid);
     if (tid <= a) {
       h[tid] = ycur + U[slot(i + tid)][slot(i)];
       lw[tid] = wcur;
@@ -245,14 +280,8 @@ __global__ void __launch_bounds__(CT) kc_hess_up(SymDev S, int task0, const doub
     }
     // M_A = V (K_A / D): V_i from its stored block (lower, ld a)
     {
-      const int r = tid / TPR, part = tid % TPR;
-      const double* Vb = Vd + R.v0 + (int64_t)i * R.vstride;
-      double acc = 0.0;
-      if (r < a)
-        for (int s = part; s < a; s += TPR) acc = fma(__ldg(Vb + (r >= s ? r + (int64_t)s * a : s + (int64_t)r * a)), kk[s], acc);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      if (part == 0 && r < a) T[base + 1 + r] = acc * dinv;
+      const double acc = row_part_dot(vrow, kk, a, 1.0, tid);
+      if (tid % TPR == 0 && tid / TPR < a) T[base + 1 + tid / TPR] = acc * dinv;
     }
     if (tid == 0) T[base] = dinv * h0 * dinv;
     const int si = slot(i);
@@ -349,6 +378,8 @@ __global__ void __launch_bounds__(CT) kc_ihess_down(SymDev S, int task0, const d
       wv = Wc[base - (a + 1) + tid];
       tv = Tin[base - (a + 1) + tid];
     }
+    // V_i^{-1}'s row part, loaded now and used after the window products
+    const RowPart rrow = load_row_part(Rd + R.v0 + (int64_t)i * R.vstride, a, tid);
     __syncthreads();
     const double wr = window_row_dot(V, i + 1, a, lw + 1, tid);
     if (tid % TPR == 0 && tid / TPR < a) ma[tid / TPR] = tt[1 + tid / TPR] + wr;
@@ -357,15 +388,8 @@ __global__ void __launch_bounds__(CT) kc_ihess_down(SymDev S, int task0, const d
     const double mnn = tt[0] + all_sum(a, [&](int r) { return lw[1 + r] * (tt[1 + r] + ma[r]); }, tid);
     if (tid == 0) Y[base] = dd * (mnn * dd);
     {
-      const int r = tid / TPR, part = tid % TPR;
-      const double* Rb = Rd + R.v0 + (int64_t)i * R.vstride;
-      double acc = 0.0;
-      if (r < a)
-        for (int s = part; s < a; s += TPR)
-          acc = fma(__ldg(Rb + (r >= s ? r + (int64_t)s * a : s + (int64_t)r * a)), ma[s] * dd, acc);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      if (part == 0 && r < a) Y[base + 1 + r] = acc;
+      const double acc = row_part_dot(rrow, ma, a, dd, tid);
+      if (tid % TPR == 0 && tid / TPR < a) Y[base + 1 + tid / TPR] = acc;
     }
     const int si = slot(i);
     if (tid == 0) V[si][si] = tt[0];

@@ -74,12 +74,16 @@ def main(argv=None):
     ap.add_argument("--split-cols", type=int, default=0, help="supernode split width (0: library default)")
     ap.add_argument("--chain-runs", type=int, default=1, choices=(0, 1),
                     help="chain tier for runs of one-column band fronts (library default: 1)")
+    ap.add_argument("--tc-products", type=int, default=0, choices=(-1, 0, 1),
+                    help="dense-tier products on the tensor cores: -1 never, 0 by the cost model, 1 always")
+    ap.add_argument("--graph-limit", type=int, default=None,
+                    help="longest launch sequence captured into a CUDA graph (library default 2^20)")
     ap.add_argument("--completion", default="independent", choices=("independent", "factored"),
                     help="completion form (factored: update matrices propagated from the parents)")
     a = ap.parse_args(argv)
     m = a.m if a.m is not None else DEFAULT_M[a.workload]
     sym = symbolic_for(a.workload, big_rows=a.big_rows, big_cols=a.big_cols, split_cols=a.split_cols,
-                       chain_runs=a.chain_runs, completion=a.completion)
+                       chain_runs=a.chain_runs, completion=a.completion, tc_products=a.tc_products)
     n, cp, ri = sym.n, sym.colptr, sym.rowind
     rng = np.random.default_rng(0)
 
@@ -102,6 +106,9 @@ def main(argv=None):
     if a.no_graphs:
         fac.set_graphs(False)
         cfac.set_graphs(False)
+    if a.graph_limit is not None:
+        fac.set_graph_limit(a.graph_limit)
+        cfac.set_graph_limit(a.graph_limit)
     ops = {
         "factor": lambda: fac.refactor(x),
         "gradient": lambda: fac.gradient(out=g),
