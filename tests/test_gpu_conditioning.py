@@ -55,6 +55,25 @@ TOL_INV = 1e-8    # inverse Hessian and completion, see the module docstring
 
 
 @pytest.mark.parametrize("name", list(CASES))
+def test_condition_1e6_factored_completion(name):
+    """The completion with factored update matrices (Algorithm 4.3) at
+    condition 1e6: S = P(X^{-1}) of the planted X, whose completion is X."""
+    B = lib()
+    mk, opts = CASES[name]
+    sym = B.Symbolic(*mk(), completion="factored", **opts)
+    n, cp, ri = sym.n, sym.colptr, sym.rowind
+    rng = np.random.default_rng(11)
+    x, l0, d0 = W.planted_factor(n, cp, ri, rng, dmin=1e-6, dmax=1.0)
+    err = lambda a, b: OD.rel_err(n, cp, ri, a, b)
+    s = OD.projected_inverse(n, cp, ri, x)
+    fx, _ = sym.complete(dev(s))
+    assert fx.status() == 0
+    lh, dh = fx.export()
+    assert err(host(lh), l0) < TOL_INV
+    np.testing.assert_allclose(host(dh), d0, rtol=TOL_INV)
+
+
+@pytest.mark.parametrize("name", list(CASES))
 def test_condition_1e6_all_operations(name):
     B = lib()
     mk, opts = CASES[name]

@@ -195,6 +195,24 @@ def test_er5000_full_size(er5000, cfg):
     assert abs(fstar - w["fstar"]) <= TOL * max(1.0, abs(w["fstar"]))
 
 
+def test_er5000_factored_completion(er5000):
+    """The completion with factored update matrices (Algorithm 4.3) on the
+    benchmark's Erdos-Renyi workload with its tier setting, all entries."""
+    import bench
+    B = lib()
+    E = er5000
+    n, cp, ri, w = E["n"], E["cp"], E["ri"], E["want"]
+    sym = bench.make_symbolic(B, E["wl"], big_rows=192, big_cols=96, split_cols=512, completion="factored")
+    fx, fstar = sym.complete(dev(E["s"]))
+    assert fx.status() == 0
+    lh, dh = fx.export()
+    err = lambda a, b: OD.rel_err(n, cp, ri, a, b)
+    np.testing.assert_allclose(host(dh), w["dh"], rtol=1e-10)
+    assert err(host(lh), w["lh"]) < TOL
+    assert err(host(fx.product()), w["xh"]) < TOL
+    assert abs(fstar - w["fstar"]) <= TOL * max(1.0, abs(w["fstar"]))
+
+
 def test_er5000_reaches_split_products():
     """The Erdos-Renyi workload of the benchmark runs split products (its
     dense-tier fronts with few columns and long ancestor sets) under every
