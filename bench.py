@@ -406,14 +406,20 @@ def tuned_config(B, wl):
     from paper_1203_2742_gb300 import autotune
     if "batch" in wl:
         subset = list(range(0, len(wl["batch"]), 8))
-        return autotune.tune(lambda **c: make_symbolic(B, wl, subset=subset, **c), wl["m"], op="step", reps=1)
+        mk = lambda **c: make_symbolic(B, wl, subset=subset, **c)
+        cfg, timings = autotune.tune(mk, wl["m"], op="step", reps=1)
+        cfg, tc_ms = autotune.refine_tc(mk, cfg, wl["m"], timings[json.dumps(cfg, sort_keys=True)], reps=1)
+        return cfg, dict(timings, fp64_units_only_trial=tc_ms)
     mk = lambda **c: make_symbolic(B, wl, **c)
     cfg, timings = autotune.tune(mk, wl["m"], op="step", reps=2)
-    table, trials, _ = autotune.refine_tiers(mk, cfg, wl["m"], timings[json.dumps(cfg, sort_keys=True)])
+    base = timings[json.dumps(cfg, sort_keys=True)]
+    table, trials, best = autotune.refine_tiers(mk, cfg, wl["m"], base)
     timings = dict(timings, tier_table_trials=trials)
     if (table >= 0).any():
         cfg = dict(cfg, tier_table=table)
-    return cfg, timings
+        base = best
+    cfg, tc_ms = autotune.refine_tc(mk, cfg, wl["m"], base)
+    return cfg, dict(timings, fp64_units_only_trial=tc_ms)
 
 
 # ---------------------------------------------------------------------------

@@ -95,12 +95,11 @@ typedef struct {
                               Hessian (the Cholesky product runs them in the warp tier);
                               0: off */
   int32_t tc_products;     /* dense-tier products on the tensor cores (FP64-accurate digit
-                              products, see chd_dgemm_tc): 0 (default) = a product of at
-                              least one wave of 152 tiles of 128 x 32 outputs runs there when
-                              a cost model of both paths (launches, digit products, output
-                              assembly, digit bytes against the FP64 units) predicts a gain;
-                              1 = every product of at least 64 x 16 outputs; -1 = never (FP64
-                              units only) */
+                              products, see chd_dgemm_tc): 0 (default) = a product runs there
+                              when a cost model of both paths (launches, digit products,
+                              output assembly, digit bytes against the FP64 units) predicts a
+                              gain for the product alone; 1 = every product of at least
+                              64 x 16 outputs; -1 = never (FP64 units only) */
   int32_t nd_dims[3];      /* grid dimensions for CHD_ORDER_ND_GEOMETRIC (use 1 for a 2D grid) */
   int32_t nd_leaf;         /* CHD_ORDER_ND_GEOMETRIC: largest box ordered without a cut; 0 = 8 */
   const int32_t* tier_table;  /* host, CHD_TIER_BUCKETS^2 entries, or NULL: per front shape, the

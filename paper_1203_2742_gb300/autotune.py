@@ -130,6 +130,18 @@ def tune(make_symbolic, m, candidates=DEFAULT_CANDIDATES, op="hessian", reps=2, 
     return best, timings
 
 
+def refine_tc(make_symbolic, config, m, base_ms, op="step", reps=2, gain=0.02, seed=0):
+    """The tensor-core choice on top of the chosen tiers: the library's cost
+    model judges each dense-tier product alone; where many fronts share the
+    GPU the FP64 units can be faster.  Times `config` with tc_products = -1
+    (FP64 units only) and returns (config, ms of the trial): the trial's
+    setting when it is more than `gain` faster than base_ms."""
+    x_of, y_of, s_of = _inputs(m, seed)
+    trial = dict(config, tc_products=-1)
+    ms = _time_config(make_symbolic, trial, x_of, y_of, s_of, m, op, reps)
+    return (trial if ms < (1.0 - gain) * base_ms else dict(config)), ms
+
+
 def front_buckets(sym):
     """Per front: its (n_k, a_k) buckets of the tier table and its Hessian
     flops per right-hand side (6 a^2 n + 8 a n^2 + 2 n^3)."""

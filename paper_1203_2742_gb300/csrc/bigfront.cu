@@ -217,16 +217,14 @@ inline double balance(int64_t units) {
 // tile), the assembly of every output (mostly integer work, one or two FP64
 // operations) and the digit planes' bytes (read twice, written once) --
 // below 0.8 of the FP64-unit time of the product (2 M N K flops at about
-// 0.9 TFLOP/s), for products of at least one wave of 128 x 32 output tiles
-// (152): smaller ones, which share the GPU with the other streams' fronts,
-// measured slower on the tensor cores (256 independent patterns, fronts of
-// |J| up to 240: Hessian 388 ms with them, 350 ms without).
+// 0.9 TFLOP/s).  The model sees one product alone: where many fronts share
+// the GPU (many small independent patterns) the FP64 units can be faster,
+// and the autotuner then turns the tensor cores off (tc_products = -1).
 inline bool tc_worth(const Ctx& st, int batch, int M, int N, int K, bool shared_a, bool shared_b) {
   if (!st.tc || st.tc_mode < 0 || K < 1) return false;
   if (st.tc_mode > 0) return M >= 64 && N >= 16;
   if (M < 16 || K < 16) return false;
   const double Mp = (M + 127) / 128 * 128.0, Np = (N + 31) / 32 * 32.0, Kp = (K + 31) / 32 * 32.0;
-  if ((Mp / 128.0) * (Np / 32.0) * batch < 152.0) return false;
   const double fp64 = 2.0 * M * N * static_cast<double>(K) * batch / 0.9e12;
   const double digits = (Mp * (shared_a ? 1 : batch) + Np * (shared_b ? 1 : batch)) * Kp * 32.0 / 4.0e12;
   const double tc = 15e-6 + Mp * Np * Kp * batch * 72.0 / 2.0e15 + Mp * Np * batch * 6.0 / 0.9e12 + digits;

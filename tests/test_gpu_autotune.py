@@ -110,3 +110,26 @@ def test_refine_tiers_returns_a_table_and_keeps_results():
     t1 = s1.factor(dev(x)).hessian(dev(ys)).cpu().numpy()
     for j in range(2):
         assert OD.rel_err(s0.n, s0.colptr, s0.rowind, t1[j], t0[j]) < 1e-12
+
+
+def test_refine_tc_chooses_a_setting_and_keeps_results():
+    """The tensor-core trial: the returned setting is the given one or the
+    same with FP64 units only, and both give the same Hessian."""
+    import torch
+    B = lib()
+    from paper_1203_2742_gb300 import autotune
+    pat = W.band(500, 499)
+    make = lambda **cfg: B.Symbolic(*pat, **cfg)
+    cfg = dict(big_rows=64, big_cols=32, split_cols=128)
+    best, timings = autotune.tune(make, 4, candidates=(cfg,), op="step", reps=1)
+    chosen, ms = autotune.refine_tc(make, cfg, 4, timings[json.dumps(cfg, sort_keys=True)], reps=1)
+    assert ms > 0 and chosen in (cfg, dict(cfg, tc_products=-1))
+    s0, s1 = make(**cfg), make(**cfg, tc_products=-1)
+    rng = np.random.default_rng(65)
+    x = W.diag_dominant(s0.n, s0.colptr, s0.rowind, rng)
+    ys = W.uniform_sym(s0.n, s0.colptr, s0.rowind, rng, count=4)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    t0 = s0.factor(dev(x)).hessian(dev(ys)).cpu().numpy()
+    t1 = s1.factor(dev(x)).hessian(dev(ys)).cpu().numpy()
+    for j in range(4):
+        assert OD.rel_err(s0.n, s0.colptr, s0.rowind, t1[j], t0[j]) < 1e-12
