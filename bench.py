@@ -542,6 +542,10 @@ def run_ours(args, wl, rank, world, local_rank):
     YI = torch.empty((m, nnz), dtype=torch.float64, device=dev)
     fac = sym.factor(X)
     fx, _ = sym.complete(S)
+    # every step repeats its calls on the same buffers: capture even long
+    # launch sequences (the batch's calls hold 11-26 thousand launches)
+    fac.set_graph_limit(1 << 20)
+    fx.set_graph_limit(1 << 20)
     flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)  # > L2
 
     results = {}
@@ -820,6 +824,8 @@ def run_serve(args, wl):
     trace = serve.poisson_trace(len(pool), wl["rate"], duration, wl["mix"], rng, lambda i: pool[i][0].nnz,
                                 max_m=wl["m"])
     launches0 = B.chd_kernel_launches()
+    # served: continuous batching on 8 streams; one at a time: each request
+    # alone on the same path
     srv = serve.Server(pool, workers=8, batching=True)
     srv.warm()
     sampler = ClockSampler(0)
@@ -827,7 +833,11 @@ def run_serve(args, wl):
     stats, done = serve.replay(srv, trace)
     clocks = sampler.stop()
     launches = B.chd_kernel_launches() - launches0
+    srv.free()
     srv = None
+    import gc
+    gc.collect()
+    torch.cuda.synchronize()
     torch.cuda.empty_cache()
     one = serve.Server(pool, workers=1, batching=False)
     one.warm()

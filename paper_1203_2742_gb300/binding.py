@@ -669,7 +669,7 @@ class Factor:
         _check(_lib.chd_factor_set_graphs(self._h, 1 if on else 0), "chd_factor_set_graphs")
 
     def set_graph_limit(self, launches):
-        """Longest launch sequence captured into a graph (default 2^20)."""
+        """Longest launch sequence captured into a graph (default 8192)."""
         _check(_lib.chd_factor_set_graph_limit(self._h, int(launches)), "chd_factor_set_graph_limit")
 
     def workspace_bytes(self):

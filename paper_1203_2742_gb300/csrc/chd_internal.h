@@ -245,7 +245,7 @@ struct chd_factor {
   bool have_Q = false;
   // CUDA graphs of the launch sequences, replayed on the private stream gs
   bool graphs_on = true;
-  int64_t graph_limit = int64_t(1) << 20;  // longest launch sequence that is captured
+  int64_t graph_limit = 8192;  // longest launch sequence that is captured
   cudaStream_t gs = nullptr;
   cudaEvent_t g_in = nullptr, g_out = nullptr;
   GraphSlot graphs[G_KINDS];

@@ -77,7 +77,7 @@ def main(argv=None):
     ap.add_argument("--tc-products", type=int, default=0, choices=(-1, 0, 1),
                     help="dense-tier products on the tensor cores: -1 never, 0 by the cost model, 1 always")
     ap.add_argument("--graph-limit", type=int, default=None,
-                    help="longest launch sequence captured into a CUDA graph (library default 2^20)")
+                    help="longest launch sequence captured into a CUDA graph (library default 8192)")
     ap.add_argument("--completion", default="independent", choices=("independent", "factored"),
                     help="completion form (factored: update matrices propagated from the parents)")
     a = ap.parse_args(argv)

@@ -15,6 +15,18 @@ call with m = the sum of their right-hand sides (continuous batching).
 Calls on one pattern are serialised by a per-pattern lock (a factor object
 has one workspace); different patterns run concurrently.
 
+With ``rhs_block`` set, a batch of Hessian-type requests runs in calls of
+exactly ``rhs_block`` right-hand sides (the last one zero-padded) through
+device and pinned host buffers that each pattern keeps, the gradient writes
+a kept buffer, and the workspaces stay allocated: every call of a kind on a
+pattern then has the same arguments, so from its third call on the library
+replays it from a CUDA graph (one launch of the graph instead of the call's
+kernel launches from the host); these factor objects capture sequences of up
+to ``graph_limit`` launches.  This suits pools of small and medium patterns;
+with very large ones (millions of nonzeros, hundreds of thousands of
+launches per call) the padding, the captures and the kept workspaces cost
+more than they save, and the plain path (the default) is faster.
+
 The server computes through the C ABI only (the ``binding`` objects of the
 registered patterns); it holds no numerical code of its own.  The trace
 generator and the admission rule need no library (they are host logic).
@@ -53,6 +65,13 @@ class PatternState:
     s: object          # device values of S (fixed per pattern)
     fac: object = None
     cfac: object = None
+    # kept buffers of the fixed-shape calls (rhs_block): device input and
+    # output, pinned host staging, the gradient's output
+    buf_in: object = None
+    buf_out: object = None
+    host_in: object = None
+    host_out: object = None
+    g_out: object = None
     lock: threading.Lock = field(default_factory=threading.Lock)
     busy: bool = False  # a worker runs a call on this pattern (guarded by Server.cv)
     ws_bytes_per_rhs: int = 0
@@ -68,11 +87,13 @@ class Server:
     """
 
     def __init__(self, patterns, workers=8, budget_bytes=None, batching=True, max_batch_rhs=64,
-                 keep_workspace_bytes=1 << 30):
+                 keep_workspace_bytes=1 << 30, rhs_block=None, graph_limit=1 << 20):
         import torch
         self.torch = torch
         self.batching = batching
         self.max_batch_rhs = max_batch_rhs
+        self.rhs_block = rhs_block
+        self.graph_limit = graph_limit
         self.states = []
         for sym, x, s in patterns:
             d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
@@ -85,8 +106,12 @@ class Server:
             free, _ = torch.cuda.mem_get_info()
             budget_bytes = int(0.5 * free)
         self.budget = budget_bytes
-        # per-request workspace cap: a worker's share of the budget
-        self.ws_limit = max(1, budget_bytes // max(1, workers))
+        # per-request workspace cap: a worker's share of the budget; with kept
+        # workspaces (rhs_block) every pattern keeps its own, so each gets a
+        # pattern's share (the library then runs a call's right-hand sides in
+        # chunks that fit)
+        share = len(self.states) if rhs_block else workers
+        self.ws_limit = max(1, budget_bytes // max(1, share))
         self.keep_ws = keep_workspace_bytes
         self.in_use = 0
         self.nworkers = workers
@@ -100,22 +125,38 @@ class Server:
     # -- resident state -------------------------------------------------------
     def warm(self):
         """Factor every pattern once (resident factors) and cache S for Hessians."""
+        torch = self.torch
         for st in self.states:
             st.fac = st.sym.factor(st.x)
             st.fac.set_workspace_limit(self.ws_limit)
             st.fac.gradient()
             st.cfac, _ = st.sym.complete(st.s)
             st.cfac.set_workspace_limit(self.ws_limit)
-            for f in (st.fac, st.cfac):
-                if f.workspace_bytes() > self.keep_ws:
-                    f.release_workspace()
+            if self.rhs_block:
+                # fixed arguments per call kind: even the longest launch
+                # sequences are captured once and replayed
+                st.fac.set_graph_limit(self.graph_limit)
+                st.cfac.set_graph_limit(self.graph_limit)
+                b, nnz = self.rhs_block, st.sym.nnz
+                st.buf_in = torch.zeros((b, nnz), dtype=torch.float64, device="cuda")
+                st.buf_out = torch.empty((b, nnz), dtype=torch.float64, device="cuda")
+                st.host_in = torch.zeros((b, nnz), dtype=torch.float64).pin_memory()
+                st.host_out = torch.empty((b, nnz), dtype=torch.float64).pin_memory()
+                st.g_out = torch.empty(nnz, dtype=torch.float64, device="cuda")
+            else:
+                for f in (st.fac, st.cfac):
+                    if f.workspace_bytes() > self.keep_ws:
+                        f.release_workspace()
         self.torch.cuda.synchronize()
 
     def footprint(self, req):
         """Device bytes a request may hold: its inputs and outputs and the
         workspace of the right-hand sides the library processes at once
-        (it works in chunks of at most 48 GiB of workspace)."""
+        (it works in chunks of at most 48 GiB of workspace).  With kept
+        buffers and workspaces (rhs_block) the request allocates nothing."""
         st = self.states[req.pattern]
+        if self.rhs_block:
+            return 0
         nnz = st.sym.nnz
         per = max(st.ws_bytes_per_rhs, 1)
         chunk = max(1, self.ws_limit // per)
@@ -179,11 +220,13 @@ class Server:
                 st.fac.refactor(st.x, stream=stream)
                 res = [st.fac.logdet()]
             elif req.op == "gradient":
-                g = torch.empty(nnz, dtype=torch.float64, device="cuda")
+                g = st.g_out if st.g_out is not None else torch.empty(nnz, dtype=torch.float64, device="cuda")
                 st.fac.gradient(out=g, stream=stream)
                 res = [g.cpu().numpy()]
             elif req.op == "completion":
                 res = [st.cfac.recomplete(st.s, stream=stream)]
+            elif self.rhs_block:
+                res = self._run_blocks(st, group, req.op, stream)
             else:
                 host = np.concatenate([r.data.reshape(r.m, nnz) for r in group], axis=0)
                 inp = torch.as_tensor(host, dtype=torch.float64).pin_memory().to("cuda", non_blocking=True)
@@ -198,13 +241,39 @@ class Server:
                     res.append(allr[o:o + r.m])
                     o += r.m
             stream.synchronize()
-            # keep the resident memory of idle patterns small
-            for f in (st.fac, st.cfac):
-                if f.workspace_bytes() > self.keep_ws:
-                    f.release_workspace()
+            # keep the resident memory of idle patterns small (kept buffers:
+            # the workspaces stay, so that the next call replays its graph)
+            if not self.rhs_block:
+                for f in (st.fac, st.cfac):
+                    if f.workspace_bytes() > self.keep_ws:
+                        f.release_workspace()
             done = self.now()
         for r, v in zip(group, res if len(res) == len(group) else res * len(group)):
             r.start, r.done, r.result, r.batched_with = start, done, v, len(group)
+
+    def _run_blocks(self, st, group, op, stream):
+        """The group's right-hand sides in calls of exactly rhs_block through
+        the pattern's kept buffers (zero rows pad the last call)."""
+        b, nnz = self.rhs_block, st.sym.nnz
+        host = np.concatenate([r.data.reshape(r.m, nnz) for r in group], axis=0)
+        out = np.empty_like(host)
+        hin, hout = st.host_in.numpy(), st.host_out.numpy()
+        call = st.fac.hessian if op == "hessian" else st.fac.inv_hessian
+        for r0 in range(0, host.shape[0], b):
+            mc = min(b, host.shape[0] - r0)
+            hin[:mc] = host[r0:r0 + mc]
+            if mc < b:
+                hin[mc:] = 0.0
+            st.buf_in.copy_(st.host_in, non_blocking=True)
+            call(st.buf_in, out=st.buf_out, stream=stream)
+            st.host_out.copy_(st.buf_out, non_blocking=True)
+            stream.synchronize()
+            out[r0:r0 + mc] = hout[:mc]
+        res, o = [], 0
+        for r in group:
+            res.append(out[o:o + r.m])
+            o += r.m
+        return res
 
     def _worker(self):
         torch = self.torch
@@ -235,6 +304,15 @@ class Server:
         self.close()
         for t in self.threads:
             t.join()
+
+    def free(self):
+        """Drop the resident factors and kept buffers (the worker threads
+        must have finished)."""
+        self.threads = []
+        for st in self.states:
+            st.fac = st.cfac = None
+            st.buf_in = st.buf_out = st.host_in = st.host_out = st.g_out = None
+        self.states = []
 
 
 def pick(queue, busy, footprint, in_use, budget, batching, max_batch_rhs):

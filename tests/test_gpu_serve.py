@@ -23,7 +23,12 @@ def _pool(rng):
     return pool
 
 
-def test_results_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("rhs_block", [None, 4])
+def test_results_same_alone_and_in_the_mix(rhs_block):
+    """In the mix (6 streams, batching; with rhs_block, calls of a fixed
+    shape through kept buffers, replayed from CUDA graphs after their second
+    call) every result equals the same request served alone on the plain
+    path, and the Hessians equal the oracle's."""
     from paper_1203_2742_gb300 import serve
     rng = np.random.default_rng(51)
     pool = _pool(rng)
@@ -31,7 +36,7 @@ def test_results_same_alone_and_in_the_mix():
     trace = serve.poisson_trace(len(pool), 4000.0, 0.05, mix, rng, lambda i: pool[i][0].nnz, max_m=6)
     assert len(trace) > 100
     # in the mix: 6 streams, batching, everything submitted in a burst
-    srv = serve.Server(pool, workers=6, batching=True)
+    srv = serve.Server(pool, workers=6, batching=True, rhs_block=rhs_block)
     srv.warm()
     for r in trace:
         r.arrival = 0.0
