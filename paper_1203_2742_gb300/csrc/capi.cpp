@@ -177,7 +177,11 @@ chd_status alloc_factor(chd_symbolic* s, cudaStream_t stream, chd_factor** out) 
 
 // Workspaces are stream-ordered allocations on the calling stream: growing or
 // releasing one never synchronises the device, so calls on other factors
-// (other streams) keep running.
+// (other streams) keep running.  Each ends with a guard region of 1 MiB that
+// no front uses: a stream-ordered allocation can end where the pool's mapped
+// memory ends, and a read just past the last front's region must not reach
+// unmapped memory.
+constexpr size_t kWsGuard = size_t(1) << 20;
 chd_status ensure_ws(chd_factor* f, int64_t rhs) {
   if (f->ws_rhs >= rhs) return CHD_OK;
   if (f->ws) {
@@ -186,8 +190,8 @@ chd_status ensure_ws(chd_factor* f, int64_t rhs) {
     f->ws_rhs = 0;
   }
   void* p = nullptr;
-  const size_t bytes = (size_t)f->sym->dev.f_total * 8 * (size_t)rhs;
-  chd_status rc = cuda_ok(cudaMallocAsync(&p, std::max<size_t>(bytes, 256), f->stream));
+  const size_t bytes = (size_t)f->sym->dev.f_total * 8 * (size_t)rhs + kWsGuard;
+  chd_status rc = cuda_ok(cudaMallocAsync(&p, bytes, f->stream));
   if (rc != CHD_OK) return rc;
   f->ws = static_cast<double*>(p);
   f->ws_rhs = rhs;
@@ -203,8 +207,8 @@ chd_status ensure_act(chd_factor* f, int64_t rhs) {
     f->act_rhs = 0;
   }
   void* p = nullptr;
-  const size_t bytes = (size_t)f->sym->nsn * 5 * (size_t)rhs;
-  chd_status rc = cuda_ok(cudaMallocAsync(&p, std::max<size_t>(bytes, 256), f->stream));
+  const size_t bytes = (size_t)f->sym->nsn * 5 * (size_t)rhs + kWsGuard;
+  chd_status rc = cuda_ok(cudaMallocAsync(&p, bytes, f->stream));
   if (rc != CHD_OK) return rc;
   f->act_buf = p;
   f->act_rhs = rhs;
