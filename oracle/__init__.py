@@ -18,6 +18,9 @@ Modules
 ``factored``      -- the completion with factored update matrices, step by
                      step (Algorithm 4.3 in the supernodal form of §7.2),
                      pinned against ``dense``'s completion.
+``multifrontal``  -- the paper's scalar multifrontal algorithms, step by step
+                     (Algorithms 3.1, 3.2, 4.1, 4.2, 5.1, 5.2), pinned
+                     against ``dense``'s definitions.
 
 Value layout shared with the library API: a symmetric matrix on the pattern V
 is stored as the lower-triangular compressed columns (CSC) of V, rows sorted
