@@ -217,6 +217,23 @@ chd_status chd_symbolic_flops(const chd_symbolic* sym, double out[5]);
 chd_status chd_completion_flops(const chd_symbolic* sym, double out[3]);
 
 /*
+ * The plan of the completion with factored update matrices (host arrays
+ * owned by `sym`, valid until chd_symbolic_free; built by every analysis,
+ * used when chd_opts.completion = 1).  Depth levels of the clique tree,
+ * roots first: level l propagates the fronts fc_fronts[fc_lvl[l] ..
+ * fc_lvl[l+1]) one CTA each and fc_big[fc_big_lvl[l] .. fc_big_lvl[l+1]) on
+ * the dense tier.  fc_off[k] (nsn entries) is front k's scratch offset in
+ * doubles within its level's scratch of at most fc_total doubles: q_k w_k
+ * for the rows of the parent's factor it reduces, plus
+ * 32 (2 w_k + q_k + 32) for a dense-tier front with q_k > 0 (its panels'
+ * reflectors, T, V T and the trailing product).  Host only; for tests and
+ * tools.  Errors: CHD_ERR_INVALID for NULL arguments.
+ */
+chd_status chd_completion_plan(const chd_symbolic* sym, int64_t* nlevels, int64_t* fc_total, const int64_t** fc_off,
+                               const int32_t** fc_lvl, const int32_t** fc_fronts, const int32_t** fc_big_lvl,
+                               const int32_t** fc_big);
+
+/*
  * The launch schedule built by the analysis (host arrays owned by `sym`,
  * valid until chd_symbolic_free).  A task is a list of fronts one worker
  * processes in order, children before parents; the tasks of a level depend

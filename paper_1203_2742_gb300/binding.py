@@ -67,6 +67,7 @@ _lib.chd_symbolic_supernodes.argtypes = [_p, C.POINTER(_p), C.POINTER(_p), C.POI
 _lib.chd_symbolic_flops.argtypes = [_p, C.POINTER(C.c_double)]
 _lib.chd_completion_flops.argtypes = [_p, C.POINTER(C.c_double)]
 _lib.chd_completion_flops.restype = C.c_int
+_lib.chd_completion_plan.restype = C.c_int
 _lib.chd_symbolic_free.argtypes = [_p]
 _lib.chd_symbolic_free.restype = None
 _lib.chd_factor_new.argtypes = [_p, _p, _p, C.POINTER(_p)]
@@ -294,6 +295,21 @@ def chd_completion_flops(sym):
     return dict(independent=out[0], factored=out[1], levels=int(out[2]))
 
 
+def chd_completion_plan(sym, nsn):
+    """The factored completion's plan: dict of numpy arrays fc_off (per
+    front), fc_lvl, fc_fronts, fc_big_lvl, fc_big, and fc_total."""
+    nl, tot = C.c_int64(), C.c_int64()
+    off = C.POINTER(C.c_int64)()
+    ptrs = [C.POINTER(C.c_int32)() for _ in range(4)]
+    _check(_lib.chd_completion_plan(sym, C.byref(nl), C.byref(tot), C.byref(off), *[C.byref(p) for p in ptrs]),
+           "chd_completion_plan")
+    L = nl.value
+    arr = lambda p, k: np.ctypeslib.as_array(p, shape=(k,)).copy() if k > 0 else np.zeros(0, np.int64)
+    lvl, big_lvl = arr(ptrs[0], L + 1), arr(ptrs[2], L + 1)
+    return {"fc_off": arr(off, nsn), "fc_lvl": lvl, "fc_fronts": arr(ptrs[1], int(lvl[-1])),
+            "fc_big_lvl": big_lvl, "fc_big": arr(ptrs[3], int(big_lvl[-1])), "fc_total": tot.value}
+
+
 def chd_symbolic_free(sym):
     _lib.chd_symbolic_free(sym)
 
@@ -511,6 +527,9 @@ class Symbolic:
 
     def completion_flops(self):
         return chd_completion_flops(self._h)
+
+    def completion_plan(self):
+        return chd_completion_plan(self._h, self.nsuper)
 
     def factor(self, x, stream=None):
         return Factor(self, chd_factor_new(self._h, x, self.nnz, stream))

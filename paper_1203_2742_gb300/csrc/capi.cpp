@@ -496,6 +496,21 @@ chd_status chd_symbolic_flops(const chd_symbolic* s, double out[5]) {
   return CHD_OK;
 }
 
+chd_status chd_completion_plan(const chd_symbolic* s, int64_t* nlevels, int64_t* fc_total, const int64_t** fc_off,
+                               const int32_t** fc_lvl, const int32_t** fc_fronts, const int32_t** fc_big_lvl,
+                               const int32_t** fc_big) {
+  if (!s || !nlevels || !fc_total || !fc_off || !fc_lvl || !fc_fronts || !fc_big_lvl || !fc_big)
+    return CHD_ERR_INVALID;
+  *nlevels = (int64_t)s->fc_lvl.size() - 1;
+  *fc_total = s->fc_total;
+  *fc_off = s->fc_off.data();
+  *fc_lvl = s->fc_lvl.data();
+  *fc_fronts = s->fc_fronts.data();
+  *fc_big_lvl = s->fc_big_lvl.data();
+  *fc_big = s->fc_big.data();
+  return CHD_OK;
+}
+
 chd_status chd_completion_flops(const chd_symbolic* s, double out[3]) {
   if (!s || !out) return CHD_ERR_INVALID;
   out[0] = s->fc_flops[0];

@@ -441,3 +441,85 @@ def test_factored_completion_plan_flops():
     fs = B.Symbolic(*W.band(150, 149), big_rows=64, big_cols=64, split_cols=24,
                     completion="factored").completion_flops()
     assert fs["factored"] < fs["independent"]
+
+
+# ---------------------------------------------------------------------------
+# the factored completion's plan: what its kernels index, checked on the host
+# ---------------------------------------------------------------------------
+
+PLAN_CASES = {
+    "er5000": lambda B: B.Symbolic(*_er5000_pattern(), big_rows=192, big_cols=96, split_cols=512),
+    "grid150": lambda B: B.Symbolic(*W.grid2d(150, 150), **W.nd_options((150, 150))),
+    "grid3d_12": lambda B: B.Symbolic(*W.grid3d(12, 12, 12), **W.nd_options((12, 12, 12)), big_rows=64, big_cols=32),
+    "arrow_groups": lambda B: B.Symbolic(*W.arrow(300, 40)),
+    "split_dense": lambda B: B.Symbolic(*W.band(700, 699), split_cols=256),
+    "band": lambda B: B.Symbolic(*W.band(400, 20)),
+    "batch": lambda B: B.SymbolicBatch([W.band(120, 6), W.grid2d(14, 14), W.arrow(90, 30)]),
+}
+
+
+def _er5000_pattern():
+    from workloads import analysed
+    pattern, perm, sp = analysed.load_er5000()
+    n, cp, ri = pattern
+    return n, cp, ri
+
+
+@pytest.mark.parametrize("name", list(PLAN_CASES))
+def test_factored_completion_plan_layout(name):
+    """Every front with ancestors (a leaf group through its first member) is
+    planned once, after its parent's level; q_k (rows of A_k in A_parent)
+    and the gather width w_k recomputed from the clique tree give each
+    front's scratch need, and the ranges of one level neither overlap nor
+    pass the level scratch (fc_total); the kernels' parent rows
+    rho = J_p - 1 - pos stay inside the parent's a_p x a_p factor."""
+    B = lib()
+    sym = PLAN_CASES[name](B)
+    sp, par, rp, rows = [np.asarray(v) for v in sym.supernodes()]
+    nsn = len(sp) - 1
+    plan = sym.completion_plan()
+    tf = sym.schedule()["task_fronts"]
+    member = np.ones(nsn, dtype=bool)
+    member[tf] = False  # fronts outside the task lists: leaf-group members after the first
+    level = np.full(nsn, -1)
+    big = np.zeros(nsn, dtype=bool)
+    lv, fr, blv, bg = plan["fc_lvl"], plan["fc_fronts"], plan["fc_big_lvl"], plan["fc_big"]
+    for l in range(len(lv) - 1):
+        for k in fr[lv[l]:lv[l + 1]]:
+            assert level[k] < 0
+            level[k] = l
+        for k in bg[blv[l]:blv[l + 1]]:
+            assert level[k] < 0
+            level[k], big[k] = l, True
+    used = {}
+    for k in range(nsn):
+        n_k = sp[k + 1] - sp[k]
+        a = rp[k + 1] - rp[k] - n_k
+        if a == 0 or member[k]:
+            assert level[k] < 0
+            continue
+        assert level[k] >= 0, k
+        p = par[k]
+        a_p = rp[p + 1] - rp[p] - (sp[p + 1] - sp[p])
+        if a_p > 0 and not member[p]:
+            assert level[p] < level[k]
+        Jk, Jp = rows[rp[k]:rp[k + 1]], rows[rp[p]:rp[p + 1]]
+        pos = np.searchsorted(Jp, Jk[n_k:])
+        assert np.array_equal(Jp[pos], Jk[n_k:])  # A_k inside J_p
+        n_p = sp[p + 1] - sp[p]
+        q = int((pos >= n_p).sum())
+        w = len(Jp) - pos[a - q] if q else 0
+        if q:
+            rho = len(Jp) - 1 - pos[a - 1 - np.arange(q)]
+            assert rho.min() >= 0 and rho.max() < a_p and w == rho.max() + 1
+            assert np.all(np.diff(rho) > 0)
+        need = (q * w + 3) // 4 * 4 + (32 * (2 * w + q + 32) if big[k] and q else 0)
+        if a > 256:
+            assert big[k]
+        used.setdefault(level[k], []).append((int(plan["fc_off"][k]), need))
+    for l, ranges in used.items():
+        ranges.sort()
+        for (o1, n1), (o2, _) in zip(ranges, ranges[1:]):
+            assert o1 + n1 <= o2
+        o, n_ = ranges[-1]
+        assert o + n_ <= plan["fc_total"]
