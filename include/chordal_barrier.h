@@ -217,6 +217,14 @@ chd_status chd_symbolic_flops(const chd_symbolic* sym, double out[5]);
 chd_status chd_completion_flops(const chd_symbolic* sym, double out[3]);
 
 /*
+ * Per-front offsets of the analysis (host arrays of nsn + 1 entries owned
+ * by `sym`, valid until chd_symbolic_free): f_off into the per-right-hand-
+ * side workspace (front k owns [f_off[k], f_off[k+1]) doubles: its J x J
+ * front and two J x n temporaries), d_off into the D_NN blocks (n x n) and
+ * v_off into the V_k blocks (a x a; a leaf group's members share their
+ * first member's).  Host only; for tests and tools.  Errors:
+ * CHD_ERR_INVALID for NULL arguments.
+ *
  * The plan of the completion with factored update matrices (host arrays
  * owned by `sym`, valid until chd_symbolic_free; built by every analysis,
  * used when chd_opts.completion = 1).  Depth levels of the clique tree,
@@ -229,6 +237,8 @@ chd_status chd_completion_flops(const chd_symbolic* sym, double out[3]);
  * reflectors, T, V T and the trailing product).  Host only; for tests and
  * tools.  Errors: CHD_ERR_INVALID for NULL arguments.
  */
+chd_status chd_symbolic_offsets(const chd_symbolic* sym, const int64_t** f_off, const int64_t** d_off,
+                                const int64_t** v_off);
 chd_status chd_completion_plan(const chd_symbolic* sym, int64_t* nlevels, int64_t* fc_total, const int64_t** fc_off,
                                const int32_t** fc_lvl, const int32_t** fc_fronts, const int32_t** fc_big_lvl,
                                const int32_t** fc_big);

@@ -68,6 +68,7 @@ _lib.chd_symbolic_flops.argtypes = [_p, C.POINTER(C.c_double)]
 _lib.chd_completion_flops.argtypes = [_p, C.POINTER(C.c_double)]
 _lib.chd_completion_flops.restype = C.c_int
 _lib.chd_completion_plan.restype = C.c_int
+_lib.chd_symbolic_offsets.restype = C.c_int
 _lib.chd_symbolic_free.argtypes = [_p]
 _lib.chd_symbolic_free.restype = None
 _lib.chd_factor_new.argtypes = [_p, _p, _p, C.POINTER(_p)]
@@ -293,6 +294,13 @@ def chd_completion_flops(sym):
     out = (C.c_double * 3)()
     _check(_lib.chd_completion_flops(sym, out), "chd_completion_flops")
     return dict(independent=out[0], factored=out[1], levels=int(out[2]))
+
+
+def chd_symbolic_offsets(sym, nsn):
+    """Per-front offsets (nsn + 1 each): f_off (workspace), d_off, v_off."""
+    ptrs = [C.POINTER(C.c_int64)() for _ in range(3)]
+    _check(_lib.chd_symbolic_offsets(sym, *[C.byref(p) for p in ptrs]), "chd_symbolic_offsets")
+    return [np.ctypeslib.as_array(p, shape=(nsn + 1,)).copy() for p in ptrs]
 
 
 def chd_completion_plan(sym, nsn):
@@ -530,6 +538,10 @@ class Symbolic:
 
     def completion_plan(self):
         return chd_completion_plan(self._h, self.nsuper)
+
+    def offsets(self):
+        """(f_off, d_off, v_off) of the analysis."""
+        return chd_symbolic_offsets(self._h, self.nsuper)
 
     def factor(self, x, stream=None):
         return Factor(self, chd_factor_new(self._h, x, self.nnz, stream))

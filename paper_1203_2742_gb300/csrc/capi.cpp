@@ -496,6 +496,15 @@ chd_status chd_symbolic_flops(const chd_symbolic* s, double out[5]) {
   return CHD_OK;
 }
 
+chd_status chd_symbolic_offsets(const chd_symbolic* s, const int64_t** f_off, const int64_t** d_off,
+                                const int64_t** v_off) {
+  if (!s || !f_off || !d_off || !v_off) return CHD_ERR_INVALID;
+  *f_off = s->f_off.data();
+  *d_off = s->d_off.data();
+  *v_off = s->v_off.data();
+  return CHD_OK;
+}
+
 chd_status chd_completion_plan(const chd_symbolic* s, int64_t* nlevels, int64_t* fc_total, const int64_t** fc_off,
                                const int32_t** fc_lvl, const int32_t** fc_fronts, const int32_t** fc_big_lvl,
                                const int32_t** fc_big) {

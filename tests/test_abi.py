@@ -76,6 +76,7 @@ def test_null_handles_are_rejected_without_a_gpu():
         "chd_factor_set_graph_limit": (N, i64(0)),
         "chd_completion_flops": (N, N),
         "chd_completion_plan": (N,) + (N,) * 7,
+        "chd_symbolic_offsets": (N, N, N, N),
         "chd_factor_set_workspace_limit": (N, ctypes.c_size_t(0)),
         "chd_factor_release_workspace": (N,),
         "chd_factor_workspace_bytes": (N, ctypes.byref(ctypes.c_size_t())),

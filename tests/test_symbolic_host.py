@@ -523,3 +523,39 @@ def test_factored_completion_plan_layout(name):
             assert o1 + n1 <= o2
         o, n_ = ranges[-1]
         assert o + n_ <= plan["fc_total"]
+
+
+@pytest.mark.parametrize("name", list(PLAN_CASES))
+def test_front_regions_hold_what_the_kernels_index(name):
+    """Front k's workspace region holds its J x J front and two J x n
+    temporaries, its D_NN block n x n and its V_k block a x a (a leaf
+    group's members share the first member's, and the group's scratch --
+    V and an a x L block of the members -- fits in the members' regions)."""
+    B = lib()
+    sym = PLAN_CASES[name](B)
+    sp, par, rp, rows = [np.asarray(v) for v in sym.supernodes()]
+    nsn = len(sp) - 1
+    f_off, d_off, v_off = sym.offsets()
+    n = np.diff(sp)
+    J = np.diff(rp)
+    a = J - n
+    assert np.all(np.diff(f_off) >= J * J + 2 * J * n)
+    assert np.all(np.diff(d_off) >= n * n)
+    tf = sym.schedule()["task_fronts"]
+    member = np.ones(nsn, dtype=bool)
+    member[tf] = False
+    dv = np.diff(v_off)
+    assert np.all(dv[~member] >= (a * a)[~member])
+    k = 0
+    while k < nsn:
+        if k + 1 < nsn and member[k + 1]:
+            c0, L = k, 1
+            while k + L < nsn and member[k + L]:
+                L += 1
+            assert np.all(n[c0:c0 + L] == 1) and np.all(a[c0:c0 + L] == a[c0])
+            assert np.all(v_off[c0 + 1:c0 + L + 1] == v_off[c0 + 1])  # one shared V slot
+            aa = int(a[c0])
+            assert aa * aa + aa * L <= f_off[c0 + L] - f_off[c0 + 1]
+            k += L
+        else:
+            k += 1
