@@ -21,6 +21,9 @@ Modules
 ``multifrontal``  -- the paper's scalar multifrontal algorithms, step by step
                      (Algorithms 3.1, 3.2, 4.1, 4.2, 5.1, 5.2), pinned
                      against ``dense``'s definitions.
+``supernodal``    -- the supernodal block algorithms (Algorithms 7.1-7.3 and
+                     the block forms of 5.1 and 5.2 the paper omits), pinned
+                     against ``dense``'s definitions on several partitions.
 
 Value layout shared with the library API: a symmetric matrix on the pattern V
 is stored as the lower-triangular compressed columns (CSC) of V, rows sorted
