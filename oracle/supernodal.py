@@ -30,7 +30,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .dense import to_dense
+from .dense import reverse_cholesky, to_dense
 from .factored import partition
 
 
@@ -128,10 +128,9 @@ def completion(n, colptr, rowind, s, snode_ptr):
     return L, D
 
 
-def hessian(n, colptr, rowind, L, D, S, y, snode_ptr):
-    """Block form of Algorithm 5.1 (module docstring): T = P(X^{-1} Y X^{-1})."""
-    Y = to_dense(n, colptr, rowind, y)
-    N, A, par, ch = _tree(n, colptr, rowind, snode_ptr)
+def _hessian_step1(Y, L, N, A, ch):
+    """Step 1 of the block Hessian, children first: [K_NN K_AN^T; K_AN U'_j]
+    = [I 0; -L_AN I] (Y-front + sum E U'_i E^T) [I -L_AN^T; 0 I]."""
     ns = len(N)
     KNN, KAN, Up = [None] * ns, [None] * ns, [None] * ns
     for j in range(ns):
@@ -148,6 +147,15 @@ def hessian(n, colptr, rowind, L, D, S, y, snode_ptr):
         Am[nn:, :nn] = -L[np.ix_(Aj, Nj)]
         G = Am @ F @ Am.T
         KNN[j], KAN[j], Up[j] = G[:nn, :nn], G[nn:, :nn], G[nn:, nn:]
+    return KNN, KAN
+
+
+def hessian(n, colptr, rowind, L, D, S, y, snode_ptr):
+    """Block form of Algorithm 5.1 (module docstring): T = P(X^{-1} Y X^{-1})."""
+    Y = to_dense(n, colptr, rowind, y)
+    N, A, par, ch = _tree(n, colptr, rowind, snode_ptr)
+    ns = len(N)
+    KNN, KAN = _hessian_step1(Y, L, N, A, ch)
     MNN, MAN = [None] * ns, [None] * ns
 
     def step2(j, Vj):
@@ -217,3 +225,65 @@ def inv_hessian(n, colptr, rowind, L, D, S, t, snode_ptr):
         Y[np.ix_(Aj, Nj)] = F[nn:, :nn]
         Up[j] = -F[nn:, nn:]
     return Y
+
+
+def hessian_factor(n, colptr, rowind, L, D, S, y, snode_ptr):
+    """Block form of W = R(Y) (Algorithm 5.3, §5.4): K from the block
+    Hessian's step 1, then per supernode, with D_NN = C C^T (C lower) and
+    V = S_{AA} = Q Q^T (Q upper, the factor §5.4 prescribes):
+    W_NN = C^{-1} K_NN C^{-T} (its lower triangle) and W_AN = Q^T K_AN C^{-T}.
+    Returns W as a dense lower triangular matrix on V."""
+    Y = to_dense(n, colptr, rowind, y)
+    N, A, par, ch = _tree(n, colptr, rowind, snode_ptr)
+    ns = len(N)
+    KNN, KAN = _hessian_step1(Y, L, N, A, ch)
+    W = np.zeros((n, n))
+    for j in range(ns):
+        Nj, Aj = N[j], A[j]
+        C = np.linalg.cholesky(D[np.ix_(Nj, Nj)])
+        Ci = np.linalg.inv(C)
+        W[np.ix_(Nj, Nj)] = np.tril(Ci @ KNN[j] @ Ci.T)
+        if len(Aj):
+            Q = reverse_cholesky(S[np.ix_(Aj, Aj)])
+            W[np.ix_(Aj, Nj)] = Q.T @ KAN[j] @ Ci.T
+    return W
+
+
+def hessian_factor_adj(n, colptr, rowind, L, D, S, w, snode_ptr):
+    """Block form of T = R^adj(W) (Algorithm 5.4): per supernode
+    M_NN = C^{-T} W_NN C^{-1} (W_NN symmetric from its lower triangle) and
+    M_AN = Q W_AN C^{-1}, then the block Hessian's step 3."""
+    Wl = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), np.diff(np.asarray(colptr)))
+    Wl[np.asarray(rowind, dtype=np.int64), rows] = w
+    N, A, par, ch = _tree(n, colptr, rowind, snode_ptr)
+    ns = len(N)
+    MNN, MAN = [None] * ns, [None] * ns
+    for j in range(ns):
+        Nj, Aj = N[j], A[j]
+        C = np.linalg.cholesky(D[np.ix_(Nj, Nj)])
+        Ci = np.linalg.inv(C)
+        Wn = Wl[np.ix_(Nj, Nj)]
+        Wn = Wn + np.tril(Wn, -1).T
+        MNN[j] = Ci.T @ Wn @ Ci
+        if len(Aj):
+            Q = reverse_cholesky(S[np.ix_(Aj, Aj)])
+            MAN[j] = Q @ Wl[np.ix_(Aj, Nj)] @ Ci
+        else:
+            MAN[j] = np.zeros((0, len(Nj)))
+    T = np.zeros((n, n))
+
+    def step3(j, Vp):
+        Nj, Aj = N[j], A[j]
+        nn = len(Nj)
+        Mf = np.block([[MNN[j], MAN[j].T], [MAN[j], Vp]])
+        Bm = np.eye(nn + len(Aj))
+        Bm[:nn, nn:] = -L[np.ix_(Aj, Nj)].T
+        Tf = Bm @ Mf @ Bm.T
+        T[np.ix_(Nj, Nj)] = Tf[:nn, :nn]
+        T[np.ix_(Aj, Nj)] = Tf[nn:, :nn]
+        T[np.ix_(Nj, Aj)] = Tf[:nn, nn:]
+        return Tf
+
+    _parents_first(N, A, ch, step3)
+    return T

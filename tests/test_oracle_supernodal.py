@@ -54,3 +54,25 @@ def test_block_hessian_and_inverse(name):
         assert err(_vals(n, cp, ri, T), want[k]) < 1e-12
         Y = OSN.inv_hessian(n, cp, ri, L, D, S, _vals(n, cp, ri, T), sp)
         assert err(_vals(n, cp, ri, Y), ys[k]) < 1e-11
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_block_hessian_factor_equals_the_per_column_one(name):
+    """Reading of §5.4 in block form: W_NN = C^{-1} K_NN C^{-T} (lower) and
+    W_AN = Q^T K_AN C^{-T} give the per-column W of Algorithm 5.3 on every
+    partition, and R^adj(R(Y)) = H(Y)."""
+    n, cp, ri, sp = _case(name)
+    rng = np.random.default_rng(13)
+    x = W.diag_dominant(n, cp, ri, rng)
+    L, D = OSN.factor(n, cp, ri, x, sp)
+    S = OD.to_dense(n, cp, ri, OD.projected_inverse(n, cp, ri, x))
+    err = lambda a, b: OD.rel_err(n, cp, ri, a, b)
+    ys = W.uniform_sym(n, cp, ri, rng, count=2)
+    want_w = OD.hessian_factor(n, cp, ri, x, list(ys))
+    want_t = OD.hessian(n, cp, ri, x, list(ys))
+    for k in range(2):
+        Wb = OSN.hessian_factor(n, cp, ri, L, D, S, ys[k], sp)
+        wv = _vals(n, cp, ri, Wb)  # lower entries on V
+        assert err(wv, want_w[k]) < 1e-12
+        T = OSN.hessian_factor_adj(n, cp, ri, L, D, S, wv, sp)
+        assert err(_vals(n, cp, ri, T), want_t[k]) < 1e-12
