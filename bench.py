@@ -889,8 +889,11 @@ def other_workloads(args, rank, world, local_rank):
     for name, steps in (("grid150", 3), ("batch256", 2)):
         a = copy.copy(args)
         a.steps, a.warmup = steps, 3
-        line = run_ours(a, make_workload(name), rank, world, local_rank)
-        out[name] = {k: line.get(k) for k in OTHER_KEYS}
+        try:
+            line = run_ours(a, make_workload(name), rank, world, local_rank)
+            out[name] = {k: line.get(k) for k in OTHER_KEYS}
+        except Exception as e:  # a nested record must not cost the default line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
         gc.collect()
         torch.cuda.empty_cache()
     return out
